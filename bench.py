@@ -1,0 +1,387 @@
+#!/usr/bin/env python3
+"""MD throughput of the Allegro-FM energy/force path on GB300 (one JSON line on stdout).
+
+Workload (default): water-like fluid, 4,096 H2O = 12,288 atoms in a periodic cube of
+49.67 A (1.0 g/cm^3), l<=2 / 3-layer / 32-channel model, rc 6 A, skin 1 A, seeded
+random-init weights; velocity Verlet at 0.5 fs from 300 K.  One step = kick, drift,
+neighbour maintenance, energies + forces (forward + hand-written adjoint), kick.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME] [--precision 0|1]
+
+Under torchrun (N > 1) every rank runs an independent replica (weak scaling); rank 0
+prints the line with the max-over-ranks time.  --impl reference times the FP64 CPU
+oracle on a bounded sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.070 GHz (maximum SM clock)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+L2_FLUSH_BYTES = 512 << 20
+
+WORKLOADS = {
+    "water12288": dict(desc="4,096 H2O (12,288 atoms), periodic cube 49.67 A, 1.0 g/cm3",
+                       make=lambda: synth.water_system(4096, L=49.67, seed=1001),
+                       model="fm_water", nu="water12288"),
+    "water4095": dict(desc="1,365 H2O (4,095 atoms), periodic cube 34.44 A, 1.0 g/cm3",
+                      make=lambda: synth.water_system(1365, L=34.44, seed=1001),
+                      model="fm_water", nu="water4095"),
+    "csh131072": dict(desc="C-S-H-like solid, 131,072 atoms, 2.6 g/cm3",
+                      make=lambda: synth.csh_system(False, 1002), model="fm_water",
+                      nu="csh131072"),
+    "cubic96": dict(desc="96 atoms, cubic 10 A, l<=1 model", make=synth.config1_system,
+                    model="small", nu="cubic96"),
+}
+
+
+def model_hp(wl):
+    hp = synth.preset(WORKLOADS[wl]["model"])
+    hp["avg_num_neighbors"] = synth.NU[WORKLOADS[wl]["nu"]]
+    return hp
+
+
+def gemm_flops_per_edge(hp):
+    """Algorithmic FLOPs of the MLP matrix products per edge and E+F evaluation: every
+    dense layer of the two-body (after the embedding/radial input layer), environment
+    and latent MLPs, forward (x W) and the adjoint's input gradient (g W^T)."""
+    tb, lat = hp["two_body"], hp["latent"]
+    D = tb[-1]
+    C, lmax = hp["channels"], hp["lmax"]
+    ldw = (lmax + 1) * C
+    ldx = D + (lmax + 1) * C
+    mac = sum(tb[k - 1] * tb[k] for k in range(1, len(tb)))
+    per_layer = D * ldw + ldx * lat[0] + sum(lat[k - 1] * lat[k] for k in range(1, len(lat)))
+    mac += hp["n_layers"] * per_layer
+    return 2 * 2 * mac
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, \
+            "fallback"
+
+
+def traffic_per_edge(kernel):
+    """DRAM bytes per edge of a kernel class from the committed ncu summary, or None."""
+    path = os.path.join(ROOT, "profiles", "traffic_per_edge.txt")
+    try:
+        for ln in open(path):
+            parts = ln.split()
+            if len(parts) >= 2 and parts[0] == kernel and not ln.startswith("#"):
+                return float(parts[1])
+    except OSError:
+        pass
+    return None
+
+
+# ------------------------------------------------------------------------- oracle arm
+def oracle_rate(wl, budget_s, workers=None):
+    """Oracle E+F atom rate (atoms/s) on a bounded sample of centres of the workload."""
+    from oracle import pool
+    s = WORKLOADS[wl]["make"]()
+    hp = model_hp(wl)
+    workers = workers or os.cpu_count() or 1
+    probe = list(range(0, min(s.n, 2 * workers)))
+    t0 = time.perf_counter()
+    pool.centre_terms(hp, 42, s.pos, s.Z, s.box, s.pbc, probe, workers=workers)
+    t_probe = time.perf_counter() - t0
+    n = int(min(s.n, max(len(probe), len(probe) * budget_s / max(t_probe, 1e-3))))
+    centres = list(range(n))
+    t0 = time.perf_counter()
+    pool.centre_terms(hp, 42, s.pos, s.Z, s.box, s.pbc, centres, workers=workers)
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt, workers
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import pool
+    wl = args.workload
+    s = WORKLOADS[wl]["make"]()
+    hp = model_hp(wl)
+    workers = os.cpu_count() or 1
+    # size one step (E+F of a sample of centres) so the whole run takes about 3 minutes
+    probe = list(range(min(s.n, 2 * workers)))
+    t0 = time.perf_counter()
+    pool.centre_terms(hp, 42, s.pos, s.Z, s.box, s.pbc, probe, workers=workers)
+    t_probe = time.perf_counter() - t0
+    per_step = 150.0 / max(1, args.steps + args.warmup)
+    n = int(min(s.n, max(len(probe), len(probe) * per_step / max(t_probe, 1e-3))))
+    centres = list(range(n))
+    for _ in range(args.warmup):
+        pool.centre_terms(hp, 42, s.pos, s.Z, s.box, s.pbc, centres, workers=workers)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        pool.centre_terms(hp, 42, s.pos, s.Z, s.box, s.pbc, centres, workers=workers)
+    dt = time.perf_counter() - t0
+    value = n * args.steps / dt
+    line = {
+        "impl": "reference", "metric": "MD atom-steps/s (E+F)", "value": value,
+        "unit": "atom-steps/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded), random-init weights",
+        "config": {"workload": wl, "desc": WORKLOADS[wl]["desc"], "model": WORKLOADS[wl]["model"],
+                   "sample_atoms_per_step": n},
+        "cpu_baseline": {"value": value, "unit": "atom-steps/s", "cores": workers,
+                         "kind": "oracle",
+                         "sample": f"E+F of centres 0..{n - 1} of {wl} per step"},
+        "e2e": {"value": value, "unit": "atom-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2502_06073_gb300 as ff
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    wl = args.workload
+    s = WORKLOADS[wl]["make"]()
+    hp = model_hp(wl)
+    model = ff.FFModel(hp, seed=42, precision=args.precision)
+    x = torch.tensor(s.pos, dtype=torch.float64, device=dev)
+    Z = torch.tensor(s.Z, dtype=torch.int32, device=dev)
+    mass = torch.tensor(s.masses, dtype=torch.float64, device=dev)
+    v = torch.tensor(synth.maxwell_boltzmann(s.masses, 300.0, seed=7), dtype=torch.float64,
+                     device=dev)
+    model.bind(x, Z, s.box, s.pbc)
+    dt_fs = 0.5
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        model.md(x, v, mass, 1, dt_fs, energies=False)
+    torch.cuda.synchronize()
+    E_edges = model.edges()[1].shape[0]
+
+    # ---- timed region: K MD steps, device-timed per step, L2 flushed between steps
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ff.profile_enable(True)
+    ff.profile_read()
+    l0 = model.launches()
+    step_ms = []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        model.md(x, v, mass, 1, dt_fs, energies=False)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    launches = model.launches() - l0
+    prof = ff.profile_read()
+    ff.profile_enable(False)
+    clk = clocks.stop()
+    for a, b in ev:
+        step_ms.append(a.elapsed_time(b))
+    t_total = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t.item())
+        dist.barrier()
+    value = world * s.n * args.steps / t_total
+
+    # ---- e2e: same steps through the C ABI with host buffers (H2D inputs, D2H results)
+    xh = x.cpu().pin_memory()
+    vh = v.cpu().pin_memory()
+    xo = torch.empty_like(xh).pin_memory()
+    vo = torch.empty_like(vh).pin_memory()
+    eo = torch.empty(1, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        x.copy_(xh, non_blocking=True)
+        v.copy_(vh, non_blocking=True)
+        Ep, _ = model.md(x, v, mass, 1, dt_fs, energies=True)
+        xo.copy_(x, non_blocking=True)
+        vo.copy_(v, non_blocking=True)
+        eo.copy_(Ep[:1], non_blocking=True)
+        xh, xo = xo, xh
+        vh, vo = vo, vh
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = world * s.n * args.steps / t_e2e
+    h2d = 2 * s.n * 3 * 8
+    d2h = 2 * s.n * 3 * 8 + 8
+
+    # ---- roofline of the dominant kernel class
+    pk, pk_kind = peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    dom_name, (dom_launch, dom_ms) = dom
+    n_eval = args.steps
+    if dom_name == "gemm_f32":
+        flops = gemm_flops_per_edge(hp) * E_edges * n_eval
+        achieved = flops / (dom_ms / 1e3) / 1e12
+        peak = FP32_PEAK_TFLOPS
+        roof = {"kernel": "gemm_f32 (all FP32 MLP GEMM launches)", "bound": "alu",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.070 GHz",
+                "launches": dom_launch, "avg_launch_us": 1e3 * dom_ms / max(dom_launch, 1)}
+        tpe = traffic_per_edge("gemm_f32")
+        roof["traffic"] = (tpe * E_edges * n_eval / max(dom_launch, 1)) if tpe else None
+    elif dom_name == "gemm_bf16":
+        flops = gemm_flops_per_edge(hp) * E_edges * n_eval
+        achieved = flops / (dom_ms / 1e3) / 1e12
+        peak = pk["bf16_tflops_sustained"]
+        roof = {"kernel": "gemm_bf16 (tcgen05)", "bound": "tensor", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": f"bf16_tflops_sustained ({pk_kind})", "launches": dom_launch,
+                "avg_launch_us": 1e3 * dom_ms / max(dom_launch, 1)}
+        tpe = traffic_per_edge("gemm_bf16")
+        roof["traffic"] = (tpe * E_edges * n_eval / max(dom_launch, 1)) if tpe else None
+    else:
+        roof = {"kernel": dom_name, "bound": "alu", "achieved": None, "peak": None,
+                "unit": None, "frac": None, "traffic": None}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, n_s, dt_s, cores = oracle_rate(wl, budget_s=15.0)
+        cpu = {"value": rate, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
+               "sample": f"E+F of centres 0..{n_s - 1} of {wl} ({dt_s:.1f} s of CPU work, "
+                         f"spawn pool of {cores} processes)"}
+
+    if rank == 0:
+        line = {
+            "metric": "MD atom-steps/s (E+F, velocity Verlet)", "value": value,
+            "unit": "atom-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == 0 else "bf16-mlp/f32",
+            "data": "synthetic (seeded), random-init weights",
+            "config": {"workload": wl, "desc": WORKLOADS[wl]["desc"],
+                       "model": WORKLOADS[wl]["model"], "atoms": s.n, "edges": E_edges,
+                       "dt_fs": dt_fs, "parallelism": f"replicas x{world}",
+                       "l2": "flushed between timed steps (512 MiB write)"},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e, "unit": "atom-steps/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof.items()
+                                   if v[0]},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="water12288", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,169 @@
+/*
+ * ff.h -- C ABI of the GB300 (sm_103a) energy/force library for the strictly-local,
+ * E(3)-equivariant Allegro potential of Allegro-FM (arXiv 2502.06073).
+ *
+ * The operations are the hot path of the paper's method for every MD step:
+ *   neighbour list within a radial cutoff under periodic boundaries   (Abstract; Methodology, Model Training)
+ *   radial basis + smooth cutoff, real spherical harmonics l <= 2      (Methodology, Model Training)
+ *   species-conditioned two-body latent MLP, per-layer environment sum, Clebsch-Gordan
+ *   tensor product and latent MLP update, edge energies -> atoms -> systems
+ *                                                                      (Methodology, Model Training; Table 1)
+ *   forces F = -dE/dx by a hand-written adjoint                        (Methodology, Model Training: force loss)
+ *   velocity-Verlet integration                                        (Methodology, MD Simulations)
+ *
+ * Conventions
+ *   Units: eV, Angstrom, amu, fs.  Species: atomic number Z in 1..89 selects row Z-1 of
+ *   the 89-row embedding (the paper's 89 elements; Abstract).
+ *   Pointers documented as "device" must point to GPU memory of the current device;
+ *   "host" pointers to CPU memory.  The caller owns every pointer argument; the context
+ *   owns its weights, neighbour lists and workspace.  A context is not thread-safe.
+ *   `stream` is a cudaStream_t (NULL = legacy default stream).  Calls enqueue work on
+ *   that stream; the ones that read a count or a flag back from the device (noted
+ *   below) synchronise the stream.
+ *   Return value: FF_OK (0) or a negative FF_ERR_* code; ff_last_error() describes the
+ *   last failure of that context.  No call aborts the process or traps on the GPU.
+ */
+#ifndef FF_H_
+#define FF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  FF_OK = 0,
+  FF_ERR_ARG = -1,       /* invalid argument or unsupported hyperparameters */
+  FF_ERR_SPECIES = -2,   /* an atomic number outside 1..89 */
+  FF_ERR_OOM = -3,       /* device allocation failed */
+  FF_ERR_CUDA = -4,      /* a CUDA runtime call failed (message has the CUDA error) */
+  FF_ERR_CAPACITY = -5,  /* a neighbour count exceeded the per-atom limit FF_MAX_NEIGHBORS */
+  FF_ERR_NONFINITE = -6, /* non-finite energy or force */
+  FF_ERR_STATE = -7,     /* call order violated (e.g. forces before any energy call) */
+  FF_ERR_BOX = -8        /* image shift out of range (|s| > 100 box lengths) */
+};
+
+/* Largest number of neighbours within rc + skin of one atom. */
+#define FF_MAX_NEIGHBORS 512
+
+/* Hyperparameters (Table 1 of the paper names the widths; the rest are readings).
+ *   rc                radial cutoff (A); skin: Verlet-list skin (A, >= 0)
+ *   n_basis, poly_p   Bessel radial functions and cutoff-polynomial order
+ *   lmax              1 or 2; parity must be 1 (full O(3))
+ *   n_layers          1..4 interaction layers; channels: tensor features, multiple of 16
+ *   two_body[]        widths of the two-body latent MLP (last = latent width D)
+ *   latent[]          widths of the per-layer latent MLP (last must equal D)
+ *   edge_eng[]        hidden widths of the linear edge-energy MLP (output width 1 implied)
+ *   avg_num_neighbors nu, normalisation of the environment sum
+ *   precision         0 = FP32 everywhere; 1 = BF16 latent MLPs with FP32 accumulation
+ *   Every width must be a multiple of 16 and at most 512. */
+typedef struct {
+  float rc, skin;
+  int n_basis, poly_p, lmax, parity, n_layers, channels;
+  int two_body[4], n_two_body;
+  int latent[4], n_latent;
+  int edge_eng[2], n_edge_eng;
+  float avg_num_neighbors;
+  int precision;
+} ff_hparams;
+
+typedef struct ff_ctx ff_ctx;
+
+/* Create a context: validates `hp`, draws every weight from SplitMix64(seed) as
+ * U(-sqrt3, sqrt3) (the paper's unit-variance uniform initialisation; Methodology,
+ * Model Training) in the documented tensor order, uploads them to the current device.
+ * *out receives the handle (NULL on failure).  Errors: FF_ERR_ARG, FF_ERR_OOM,
+ * FF_ERR_CUDA. */
+int ff_create(ff_ctx** out, const ff_hparams* hp, uint64_t seed);
+
+/* Release every device and host resource of the context (NULL is ignored). */
+void ff_destroy(ff_ctx* ctx);
+
+/* Bind a system and build its neighbour lists (the paper's radial-cutoff locality;
+ * Abstract, "strictly-local").
+ *   pos      device double[n_atoms][3]   positions (need not be wrapped)
+ *   Z        device int32[n_atoms]       atomic numbers 1..89 (copied)
+ *   box      host double[3]              orthorhombic edge lengths; for a non-periodic
+ *                                        axis the binning extent
+ *   pbc      host int[3]                 1 = periodic axis
+ *   sys_ptr  host int32[n_sys+1] or NULL atom offsets of independent systems; atoms of
+ *                                        different systems never interact (n_sys > 1
+ *                                        requires a fully non-periodic box)
+ * Builds the Verlet list at rc + skin (cell list; edges (i, j, s) with the float32
+ * membership test  ((x_j - x_i) + s*L)^2 < (rc+skin)^2  evaluated per component
+ * without fused multiply-add) and the list at rc used by the model, sorted by
+ * (i, j, s).  Synchronises `stream` (reads counts back).
+ * Errors: FF_ERR_ARG, FF_ERR_SPECIES, FF_ERR_CAPACITY, FF_ERR_BOX, FF_ERR_OOM,
+ * FF_ERR_CUDA. */
+int ff_neighbors(ff_ctx* ctx, const double* pos, const int32_t* Z, int n_atoms,
+                 const double box[3], const int pbc[3], const int32_t* sys_ptr, int n_sys,
+                 void* stream);
+
+/* Energies and (optionally) forces at positions `pos` of the bound system.
+ *   pos     device double[n_atoms][3]
+ *   E_sys   device double[n_sys] or NULL     per-system energy (FP64 sum of E_atom)
+ *   E_atom  device float[n_atoms] or NULL    per-atom energy E_i = sum_j E_ij
+ *   F       device float[n_atoms][3] or NULL forces -dE/dx (NULL: energy only; the
+ *                                            intermediates are kept for ff_forces)
+ * Re-filters the Verlet list at rc for `pos` and rebuilds it first when an atom moved
+ * more than skin/2 since the last build.  Synchronises `stream` (edge count).
+ * Errors: FF_ERR_STATE (no ff_neighbors yet), FF_ERR_CAPACITY, FF_ERR_OOM, FF_ERR_CUDA. */
+int ff_energy_forces(ff_ctx* ctx, const double* pos, double* E_sys, float* E_atom, float* F,
+                     void* stream);
+
+/* Adjoint of the last ff_energy_forces call: F = -sum_s grad_E[s] dE_s/dx.
+ *   grad_E  device double[n_sys] or NULL (NULL = all ones)
+ *   F       device float[n_atoms][3]
+ * Requires the previous ff_energy_forces to have been called with F == NULL and the
+ * same positions (the stored intermediates are used).  Errors: FF_ERR_STATE,
+ * FF_ERR_CUDA. */
+int ff_forces(ff_ctx* ctx, const double* grad_E, float* F, void* stream);
+
+/* Velocity-Verlet NVE steps (Methodology, MD Simulations; QMD uses an explicit
+ * reversible integrator): v += dt/2 F/m; x += dt v; F = F(x); v += dt/2 F/m, in FP64
+ * with 1 eV/(A amu) = 9.648533212e-3 A/fs^2.
+ *   x, v    device double[n_atoms][3], updated in place (positions are not wrapped)
+ *   mass    device double[n_atoms] (amu)
+ *   E_pot, E_kin  device double[n_steps * n_sys] or NULL: energies after each step
+ * Forces at the starting positions are computed first unless the previous call left
+ * them for exactly these positions.  Synchronises `stream` once per step.
+ * Errors: as ff_energy_forces. */
+int ff_md_step(ff_ctx* ctx, double* x, double* v, const double* mass, int n_steps,
+               double dt_fs, double* E_pot, double* E_kin, void* stream);
+
+/* Copy every weight, in tensor order, as the FP64 values drawn at creation (before any
+ * rounding to the device precision) into host_buf.  *needed receives the count.
+ * Returns FF_ERR_ARG if cap < *needed. */
+int ff_export_params(ff_ctx* ctx, double* host_buf, size_t cap, size_t* needed);
+
+/* Copy the current model edge list (r < rc, sorted by (i, j, s)) to host buffers:
+ *   row_ptr int32[n_atoms+1], col int32[E], shift int32[E][3], rev int32[E]
+ *   (rev[e] is the index of the edge (j, i, -s)).  *n_edges receives E; buffers may be
+ *   NULL to query E.  Synchronises `stream`.  Returns FF_ERR_ARG if cap < E. */
+int ff_get_edges(ff_ctx* ctx, int64_t* n_edges, int32_t* row_ptr, int32_t* col,
+                 int32_t* shift, int32_t* rev, size_t cap, void* stream);
+
+/* Number of kernels launched by this library in this process (all contexts; the
+ * argument is accepted for symmetry and may be NULL). */
+int64_t ff_kernel_launches(const ff_ctx* ctx);
+
+/* Kernel timing for profiling (process-wide, off by default).  While enabled, every
+ * kernel launch of the library is bracketed by two CUDA events recorded on the stream it
+ * is launched on.  ff_profile_read synchronises the device and reports, per kernel class
+ * k < *n_classes: launches[k] and total device milliseconds ms[k] since the last read
+ * (then resets them); ff_profile_class(k) names the class.  Arrays hold `cap` entries.
+ * Errors: FF_ERR_ARG (cap too small), FF_ERR_CUDA. */
+int ff_profile_enable(int on);
+int ff_profile_read(int64_t* launches, double* ms, int cap, int* n_classes);
+const char* ff_profile_class(int k);
+
+/* Message describing the last error of `ctx` (or of the last failed ff_create when ctx
+ * is NULL).  The string stays valid until the next call on the context. */
+const char* ff_last_error(const ff_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FF_H_ */

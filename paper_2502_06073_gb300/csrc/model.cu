@@ -1,0 +1,383 @@
+// Per-edge and per-atom kernels of the Allegro energy/force path other than the GEMMs
+// and the tensor products: edge geometry and radial/angular features, the species
+// embedding + radial input layer of the two-body MLP, edge energies, the adjoint's
+// row reductions and geometric chain rule, the deterministic force gather, per-system
+// FP64 energies and velocity Verlet (arXiv 2502.06073, Methodology, Model Training and
+// MD Simulations).
+//
+// Readings of the model that these kernels implement (the paper leaves them open):
+//   B_n(r) = sqrt(2/rc) sin(n pi r / rc) / r                       (Bessel radial basis)
+//   f(x)   = 1 - (p+1)(p+2)/2 x^p + p(p+2) x^(p+1) - p(p+1)/2 x^(p+2)  (x = r/rc < 1)
+//   Y_1 = sqrt3 (y, z, x); Y_2 = (sqrt15 xy, sqrt15 yz, sqrt5/2 (3z^2-1), sqrt15 xz,
+//         sqrt15/2 (x^2-y^2))                      (real, component-normalised harmonics)
+#include "ff_internal.cuh"
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr float kPi = 3.14159265358979323846f;
+constexpr float kS3 = 1.7320508075688772f;
+constexpr float kS5 = 2.23606797749979f;
+constexpr float kS15 = 3.872983346207417f;
+
+__device__ __forceinline__ float silu_f(float z) { return z / (1.f + expf(-z)); }
+__device__ __forceinline__ float sigm_f(float z) { return 1.f / (1.f + expf(-z)); }
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float envelope_f(float x, int p) {
+  if (x >= 1.f) return 0.f;
+  const float xp = powf(x, (float)p);
+  return 1.f - 0.5f * (p + 1) * (p + 2) * xp + p * (p + 2) * xp * x -
+         0.5f * p * (p + 1) * xp * x * x;
+}
+
+__device__ __forceinline__ float envelope_df(float x, int p, float rc) {
+  if (x >= 1.f) return 0.f;
+  const float om = 1.f - x;
+  return -0.5f * p * (p + 1) * (p + 2) * powf(x, (float)(p - 1)) * om * om / rc;
+}
+
+__global__ void k_edge_features(long long E, const int* __restrict__ src,
+                                const int* __restrict__ col, const int* __restrict__ shift,
+                                const double* __restrict__ pos, const double* __restrict__ L,
+                                const int* __restrict__ Z, float rc, int n_basis, int p,
+                                int lmax, float* __restrict__ ef, int* __restrict__ zz) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int i = src[e], j = col[e];
+  int s0, s1, s2;
+  ff_unpack_shift(shift[e], s0, s1, s2);
+  const double dx = (pos[3 * (long long)j] - pos[3 * (long long)i]) + s0 * L[0];
+  const double dy = (pos[3 * (long long)j + 1] - pos[3 * (long long)i + 1]) + s1 * L[1];
+  const double dz = (pos[3 * (long long)j + 2] - pos[3 * (long long)i + 2]) + s2 * L[2];
+  const double rd = sqrt(dx * dx + dy * dy + dz * dz);
+  const float r = (float)rd;
+  const float ux = (float)(dx / rd), uy = (float)(dy / rd), uz = (float)(dz / rd);
+  float* o = ef + e * FF_EF_STRIDE;
+  o[0] = ux; o[1] = uy; o[2] = uz; o[3] = r;
+  const float pref = sqrtf(2.f / rc);
+  for (int n = 1; n <= n_basis; ++n) o[FF_EF_B + n - 1] = pref * sinf(n * kPi * r / rc) / r;
+  o[FF_EF_F] = envelope_f(r / rc, p);
+  float* y = o + FF_EF_Y;
+  y[0] = 1.f;
+  y[1] = kS3 * uy; y[2] = kS3 * uz; y[3] = kS3 * ux;
+  if (lmax >= 2) {
+    y[4] = kS15 * ux * uy;
+    y[5] = kS15 * uy * uz;
+    y[6] = 0.5f * kS5 * (3.f * uz * uz - 1.f);
+    y[7] = kS15 * ux * uz;
+    y[8] = 0.5f * kS15 * (ux * ux - uy * uy);
+  } else {
+#pragma unroll
+    for (int k = 4; k < 9; ++k) y[k] = 0.f;
+  }
+  zz[2 * e] = Z[i];
+  zz[2 * e + 1] = Z[j];
+}
+
+// First two-body layer: one-hot(Z_i) || one-hot(Z_j) || B(r) times W0 = two table rows plus
+// the radial part.  final_layer: out = f * silu(z) (x^0), otherwise out = silu(z).
+__global__ void k_twobody_in(long long E, int width, int n_basis, const float* __restrict__ ef,
+                             const int* __restrict__ zz, const float* __restrict__ W0,
+                             float alpha, float* __restrict__ pre, float* __restrict__ out,
+                             int ldo, int final_layer) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= E * width) return;
+  const long long e = t / width;
+  const int o = (int)(t - e * width);
+  const int zi = zz[2 * e], zj = zz[2 * e + 1];
+  float acc = W0[(size_t)(zi - 1) * width + o] + W0[(size_t)(FF_N_SPECIES + zj - 1) * width + o];
+  const float* b = ef + e * FF_EF_STRIDE + FF_EF_B;
+  for (int n = 0; n < n_basis; ++n) acc += b[n] * W0[(size_t)(2 * FF_N_SPECIES + n) * width + o];
+  const float z = alpha * acc;
+  pre[e * width + o] = z;
+  const float h = silu_f(z);
+  out[e * ldo + o] = final_layer ? ef[e * FF_EF_STRIDE + FF_EF_F] * h : h;
+}
+
+// E_i = sum over the edges of i of x^N_ij . w_eff (the linear edge-energy MLP folded into
+// one vector).  One warp per atom; fixed summation order.
+__global__ void k_energy(int n_atoms, const int* __restrict__ row_ptr, int e0,
+                         const float* __restrict__ X, int ldx, int D,
+                         const float* __restrict__ w_eff, float* __restrict__ E_atom) {
+  const int a = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (a >= n_atoms) return;
+  const int eb = row_ptr[a] - e0, ee = row_ptr[a + 1] - e0;
+  float acc = 0.f;
+  for (int e = eb; e < ee; ++e)
+    for (int d = lane; d < D; d += 32) acc += X[(size_t)e * ldx + d] * w_eff[d];
+  acc = warp_sum(acc);
+  if (lane == 0) E_atom[a] = acc;
+}
+
+// Adjoint of out = f * silu(z) (scaled by alpha):  gz = alpha f silu'(z) gx,
+// gf += alpha sum_d gx silu(z).  One warp per edge.  ldgx == 0: gx is one broadcast row.
+__global__ void k_rowred_bwd(long long E, int N, const float* __restrict__ gx, int ldgx,
+                             const float* __restrict__ z, int ldz, const float* __restrict__ ef,
+                             float alpha, float* __restrict__ gz, int ldgz,
+                             float* __restrict__ gf) {
+  const long long e = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (e >= E) return;
+  const float f = ef[e * FF_EF_STRIDE + FF_EF_F];
+  float acc = 0.f;
+  for (int d = lane; d < N; d += 32) {
+    const float g = gx[(size_t)e * ldgx + d];
+    const float zz = z[(size_t)e * ldz + d];
+    const float sg = sigm_f(zz);
+    gz[(size_t)e * ldgz + d] = alpha * f * g * (sg * (1.f + zz * (1.f - sg)));
+    acc += g * zz * sg;
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) gf[e] += alpha * acc;
+}
+
+// dE/dr_e from the radial-basis gradient (via the first two-body layer), the envelope
+// gradient and the spherical-harmonic gradient; one warp per edge.
+__global__ void k_edge_grad(long long E, int w0, int n_basis, float rc, int p, int lmax,
+                            const float* __restrict__ ef, const float* __restrict__ gz0, int ldg,
+                            const float* __restrict__ WB, float alpha0,
+                            const float* __restrict__ gf, const float* __restrict__ gY,
+                            const int* __restrict__ src, const int* __restrict__ sys_of,
+                            const double* __restrict__ seed, float4* __restrict__ g) {
+  const long long e = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (e >= E) return;
+  float gB[10];
+#pragma unroll
+  for (int n = 0; n < 10; ++n) gB[n] = 0.f;
+  for (int k = lane; k < w0; k += 32) {
+    const float gzk = gz0[(size_t)e * ldg + k];
+#pragma unroll
+    for (int n = 0; n < 10; ++n)
+      if (n < n_basis) gB[n] += gzk * WB[(size_t)n * w0 + k];
+  }
+#pragma unroll
+  for (int n = 0; n < 10; ++n) gB[n] = warp_sum(gB[n]);
+  if (lane != 0) return;
+  const float* o = ef + e * FF_EF_STRIDE;
+  const float ux = o[0], uy = o[1], uz = o[2], r = o[3];
+  const float pref = sqrtf(2.f / rc);
+  float gr = 0.f;
+  for (int n = 1; n <= n_basis; ++n) {
+    const float a = n * kPi / rc;
+    const float sn = sinf(a * r), cs = cosf(a * r);
+    gr += alpha0 * gB[n - 1] * pref * (a * cs * r - sn) / (r * r);
+  }
+  gr += gf[e] * envelope_df(r / rc, p, rc);
+  const float* gy = gY + e * 9;
+  float gux = kS3 * gy[3], guy = kS3 * gy[1], guz = kS3 * gy[2];
+  if (lmax >= 2) {
+    gux += kS15 * (uy * gy[4] + uz * gy[7] + ux * gy[8]);
+    guy += kS15 * (ux * gy[4] + uz * gy[5] - uy * gy[8]);
+    guz += kS15 * (uy * gy[5] + ux * gy[7]) + 3.f * kS5 * uz * gy[6];
+  }
+  const float dot = gux * ux + guy * uy + guz * uz;
+  float gx_ = gr * ux + (gux - dot * ux) / r;
+  float gy_ = gr * uy + (guy - dot * uy) / r;
+  float gz_ = gr * uz + (guz - dot * uz) / r;
+  if (seed) {
+    const float sc = (float)seed[sys_of[src[e]]];
+    gx_ *= sc; gy_ *= sc; gz_ *= sc;
+  }
+  g[e] = make_float4(gx_, gy_, gz_, 0.f);
+}
+
+// F_m = sum_{e in seg(m)} (g_e - g_rev(e)); one warp per atom, fixed order.
+__global__ void k_force_gather(int n, const int* __restrict__ row_ptr, const int* __restrict__ rev,
+                               const float4* __restrict__ g, float* __restrict__ F) {
+  const int m = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (m >= n) return;
+  float fx = 0.f, fy = 0.f, fz = 0.f;
+  for (int e = row_ptr[m] + lane; e < row_ptr[m + 1]; e += 32) {
+    const float4 a = g[e], b = g[rev[e]];
+    fx += a.x - b.x;
+    fy += a.y - b.y;
+    fz += a.z - b.z;
+  }
+  fx = warp_sum(fx);
+  fy = warp_sum(fy);
+  fz = warp_sum(fz);
+  if (lane == 0) {
+    F[3 * (size_t)m] = fx;
+    F[3 * (size_t)m + 1] = fy;
+    F[3 * (size_t)m + 2] = fz;
+  }
+}
+
+__device__ double block_sum_d(double v, double* sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(kFull, r, o);
+  }
+  return r;
+}
+
+__global__ void k_esys(const float* __restrict__ E_atom, const int* __restrict__ sys_ptr,
+                       double* __restrict__ E_sys) {
+  __shared__ double sh[32];
+  const int sy = blockIdx.x;
+  double acc = 0.0;
+  for (int i = sys_ptr[sy] + threadIdx.x; i < sys_ptr[sy + 1]; i += blockDim.x)
+    acc += (double)E_atom[i];
+  acc = block_sum_d(acc, sh);
+  if (threadIdx.x == 0) E_sys[sy] = acc;
+}
+
+constexpr double kAcc = 9.648533212e-3;   // (eV / (A amu)) -> A / fs^2
+
+__global__ void k_kick(int n, double* __restrict__ v, const float* __restrict__ F,
+                       const double* __restrict__ mass, double hdt) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3LL * n) return;
+  v[t] += hdt * kAcc * (double)F[t] / mass[t / 3];
+}
+
+__global__ void k_drift(long long n3, double* __restrict__ x, const double* __restrict__ v,
+                        double dt) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n3) return;
+  x[t] += dt * v[t];
+}
+
+__global__ void k_kinetic(const double* __restrict__ v, const double* __restrict__ mass,
+                          const int* __restrict__ sys_ptr, double* __restrict__ E_kin) {
+  __shared__ double sh[32];
+  const int sy = blockIdx.x;
+  double acc = 0.0;
+  for (int i = sys_ptr[sy] + threadIdx.x; i < sys_ptr[sy + 1]; i += blockDim.x) {
+    const double vx = v[3 * (size_t)i], vy = v[3 * (size_t)i + 1], vz = v[3 * (size_t)i + 2];
+    acc += mass[i] * (vx * vx + vy * vy + vz * vz);
+  }
+  acc = block_sum_d(acc, sh);
+  if (threadIdx.x == 0) E_kin[sy] = 0.5 * acc / kAcc;
+}
+
+__global__ void k_fill_f32(float* __restrict__ p, long long n, float v) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) p[t] = v;
+}
+
+__global__ void k_check_finite(const float* __restrict__ F, long long n, int* __restrict__ err) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n && !isfinite(F[t])) atomicOr(err, 32);
+}
+
+}  // namespace
+
+
+void launch_edge_features(long long E, const int* src, const int* col, const int* shift,
+                          const double* pos, const double* L, int /*pbc_any*/, const int* Z,
+                          float rc, int n_basis, int p, int lmax, float* ef, int* zz,
+                          cudaStream_t s) {
+  ProfScope ps_(PC_EDGE_FEAT, s);
+  if (E <= 0) return;
+  k_edge_features<<<ff_cdiv(E, 256), 256, 0, s>>>(E, src, col, shift, pos, L, Z, rc, n_basis, p,
+                                                 lmax, ef, zz);
+  ff_count_launch(1);
+}
+
+void launch_twobody_in(long long E, int width, int n_basis, const float* ef, const int* zz,
+                       const float* W0, float alpha, float* pre, float* out, int ldo,
+                       int final_layer, cudaStream_t s) {
+  ProfScope ps_(PC_TWOBODY_IN, s);
+  if (E <= 0) return;
+  k_twobody_in<<<ff_cdiv(E * width, 256), 256, 0, s>>>(E, width, n_basis, ef, zz, W0, alpha, pre,
+                                                      out, ldo, final_layer);
+  ff_count_launch(1);
+}
+
+void launch_energy(int n_atoms, const int* row_ptr, int e0, const float* X, int ldx, int D,
+                   const float* w_eff, float* E_atom, cudaStream_t s) {
+  ProfScope ps_(PC_ENERGY, s);
+  if (n_atoms <= 0) return;
+  k_energy<<<ff_cdiv(n_atoms, 8), 256, 0, s>>>(n_atoms, row_ptr, e0, X, ldx, D, w_eff, E_atom);
+  ff_count_launch(1);
+}
+
+void launch_rowred_bwd(long long E, int N, const float* gx, int ldgx, const float* z, int ldz,
+                       const float* ef, float alpha, float* gz, int ldgz, float* gf,
+                       cudaStream_t s) {
+  ProfScope ps_(PC_ROWRED, s);
+  if (E <= 0) return;
+  k_rowred_bwd<<<ff_cdiv(E, 8), 256, 0, s>>>(E, N, gx, ldgx, z, ldz, ef, alpha, gz, ldgz, gf);
+  ff_count_launch(1);
+}
+
+void launch_edge_grad(long long E, int w0, int n_basis, float rc, int p, int lmax,
+                      const float* ef, const float* gz0, int ldg, const float* WB, float alpha0,
+                      const float* gf, const float* gY, const int* src, const int* sys_of,
+                      const double* seed, float4* g, cudaStream_t s) {
+  ProfScope ps_(PC_EDGE_GRAD, s);
+  if (E <= 0) return;
+  k_edge_grad<<<ff_cdiv(E, 8), 256, 0, s>>>(E, w0, n_basis, rc, p, lmax, ef, gz0, ldg, WB, alpha0,
+                                           gf, gY, src, sys_of, seed, g);
+  ff_count_launch(1);
+}
+
+void launch_force_gather(int n, const int* row_ptr, const int* rev, const float4* g, float* F,
+                         cudaStream_t s) {
+  ProfScope ps_(PC_FORCE_GATHER, s);
+  if (n <= 0) return;
+  k_force_gather<<<ff_cdiv(n, 8), 256, 0, s>>>(n, row_ptr, rev, g, F);
+  ff_count_launch(1);
+}
+
+void launch_esys(const float* E_atom, const int* sys_ptr, int n_sys, double* E_sys,
+                 cudaStream_t s) {
+  ProfScope ps_(PC_MISC, s);
+  if (n_sys <= 0) return;
+  k_esys<<<n_sys, 256, 0, s>>>(E_atom, sys_ptr, E_sys);
+  ff_count_launch(1);
+}
+
+void launch_kick(int n, double* v, const float* F, const double* mass, double hdt,
+                 cudaStream_t s) {
+  ProfScope ps_(PC_MD, s);
+  if (n <= 0) return;
+  k_kick<<<ff_cdiv(3LL * n, 256), 256, 0, s>>>(n, v, F, mass, hdt);
+  ff_count_launch(1);
+}
+
+void launch_drift(int n, double* x, const double* v, double dt, cudaStream_t s) {
+  ProfScope ps_(PC_MD, s);
+  if (n <= 0) return;
+  k_drift<<<ff_cdiv(3LL * n, 256), 256, 0, s>>>(3LL * n, x, v, dt);
+  ff_count_launch(1);
+}
+
+void launch_kinetic(const double* v, const double* mass, const int* sys_ptr, int n_sys,
+                    double* E_kin, cudaStream_t s) {
+  ProfScope ps_(PC_MD, s);
+  if (n_sys <= 0) return;
+  k_kinetic<<<n_sys, 256, 0, s>>>(v, mass, sys_ptr, E_kin);
+  ff_count_launch(1);
+}
+
+void launch_fill_f32(float* p, long long n, float v, cudaStream_t s) {
+  ProfScope ps_(PC_MISC, s);
+  if (n <= 0) return;
+  k_fill_f32<<<ff_cdiv(n, 256), 256, 0, s>>>(p, n, v);
+  ff_count_launch(1);
+}
+
+void launch_check_finite(const float* F, long long n, int* err, cudaStream_t s) {
+  ProfScope ps_(PC_MISC, s);
+  if (n <= 0) return;
+  k_check_finite<<<ff_cdiv(n, 256), 256, 0, s>>>(F, n, err);
+  ff_count_launch(1);
+}

@@ -1,0 +1,254 @@
+// Environment embedding + Clebsch-Gordan tensor product of one interaction layer, and
+// their adjoint (arXiv 2502.06073, Methodology, Model Training: e3nn tensor products,
+// l = 2, full O(3); the layer structure follows the Allegro architecture the paper uses).
+//
+// One team of C threads (C = tensor channels, 16 or 32) owns one centre atom i; thread c
+// owns channel c.  Because every edge of i is contiguous in the sorted edge list, the
+// environment sum
+//     G_i[c, lm] = nu^(-1/2) sum_{k in N(i)} w_ik[l, c] Y_lm(u_ik)
+// is a register accumulation over the atom's segment (no atomics, fixed order), and the
+// tensor product of every edge of i with G_i follows in the same kernel:
+//     T_path[c] = C_path (V_ij[c] x G_i[c]);  s = the 0e outputs -> latent input columns;
+//     V'_ij[c] = sum_path theta[path, c] T_path[c] / sqrt(n_paths into the irrep).
+// Layouts (channel fastest, so a team reads 64/128 contiguous bytes per component):
+//   W [E][(lmax+1) * C] env weights (column l*C + c);  V [E][dim][C];  G [atoms][9][C];
+//   the scalars go to X[e][D + q*C + c].
+#include "ff_internal.cuh"
+#include "tp_gen.cuh"
+
+namespace {
+
+template <int C>
+__device__ __forceinline__ float team_sum(float v) {
+  const unsigned mask = (C == 32) ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
+#pragma unroll
+  for (int o = C / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, C);
+  return v;
+}
+
+template <int LMAX, int INK, int LAST, int C>
+__global__ void __launch_bounds__(128)
+k_env_tp_fwd(int n_atoms, const int* __restrict__ row_ptr, int e0, const float* __restrict__ ef,
+             const float* __restrict__ W, int ldw, const float* __restrict__ Vin,
+             const float* __restrict__ theta, float* __restrict__ X, int ldx, int D,
+             float* __restrict__ Vout, float* __restrict__ Gam, float inv_sqrt_nu) {
+  using K = TP<LMAX, INK, LAST>;
+  constexpr int NY = (LMAX + 1) * (LMAX + 1);
+  const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = (int)(gt / C), c = (int)(gt % C);
+  if (a >= n_atoms) return;
+  const int eb = row_ptr[a] - e0, ee = row_ptr[a + 1] - e0;
+
+  float G[NY];
+#pragma unroll
+  for (int k = 0; k < NY; ++k) G[k] = 0.f;
+  for (int e = eb; e < ee; ++e) {
+    const float* y = ef + (size_t)e * FF_EF_STRIDE + FF_EF_Y;
+#pragma unroll
+    for (int l = 0; l <= LMAX; ++l) {
+      const float w = W[(size_t)e * ldw + l * C + c];
+#pragma unroll
+      for (int m = 0; m < 2 * l + 1; ++m) G[l * l + m] += w * y[l * l + m];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NY; ++k) {
+    G[k] *= inv_sqrt_nu;
+    Gam[((size_t)a * NY + k) * C + c] = G[k];
+  }
+  float th[K::NP];
+  if (!LAST) {
+#pragma unroll
+    for (int q = 0; q < K::NP; ++q) th[q] = theta[q * C + c];
+  }
+  for (int e = eb; e < ee; ++e) {
+    float v[K::DIN];
+    if (INK == 0) {
+      const float* y = ef + (size_t)e * FF_EF_STRIDE + FF_EF_Y;
+#pragma unroll
+      for (int l = 0; l <= LMAX; ++l) {
+        const float w = W[(size_t)e * ldw + l * C + c];
+#pragma unroll
+        for (int m = 0; m < 2 * l + 1; ++m) v[l * l + m] = w * y[l * l + m];
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < K::DIN; ++k) v[k] = Vin[((size_t)e * K::DIN + k) * C + c];
+    }
+    float s[K::NS], vo[K::DOUT];
+    K::fwd(v, G, th, s, vo);
+#pragma unroll
+    for (int q = 0; q < K::NS; ++q) X[(size_t)e * ldx + D + q * C + c] = s[q];
+    if (!LAST) {
+#pragma unroll
+      for (int k = 0; k < K::DOUT; ++k) Vout[((size_t)e * K::DOUT + k) * C + c] = vo[k];
+    }
+  }
+}
+
+template <int LMAX, int INK, int LAST, int C>
+__global__ void __launch_bounds__(128)
+k_env_tp_bwd(int n_atoms, const int* __restrict__ row_ptr, int e0, const float* __restrict__ ef,
+             const float* __restrict__ W, int ldw, const float* __restrict__ Vin,
+             const float* __restrict__ theta, const float* __restrict__ GX, int ldx, int D,
+             const float* __restrict__ gVout, float* __restrict__ gVin, float* __restrict__ GW,
+             float* __restrict__ gY, const float* __restrict__ Gam, float inv_sqrt_nu) {
+  using K = TP<LMAX, INK, LAST>;
+  constexpr int NY = (LMAX + 1) * (LMAX + 1);
+  const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = (int)(gt / C), c = (int)(gt % C);
+  if (a >= n_atoms) return;
+  const int eb = row_ptr[a] - e0, ee = row_ptr[a + 1] - e0;
+  float G[NY], gG[NY];
+#pragma unroll
+  for (int k = 0; k < NY; ++k) {
+    G[k] = Gam[((size_t)a * NY + k) * C + c];
+    gG[k] = 0.f;
+  }
+  float th[K::NP];
+  if (!LAST) {
+#pragma unroll
+    for (int q = 0; q < K::NP; ++q) th[q] = theta[q * C + c];
+  }
+  for (int e = eb; e < ee; ++e) {
+    const float* y = ef + (size_t)e * FF_EF_STRIDE + FF_EF_Y;
+    float v[K::DIN], gv[K::DIN];
+    float wl[LMAX + 1];
+#pragma unroll
+    for (int l = 0; l <= LMAX; ++l) wl[l] = W[(size_t)e * ldw + l * C + c];
+    if (INK == 0) {
+#pragma unroll
+      for (int l = 0; l <= LMAX; ++l)
+#pragma unroll
+        for (int m = 0; m < 2 * l + 1; ++m) v[l * l + m] = wl[l] * y[l * l + m];
+    } else {
+#pragma unroll
+      for (int k = 0; k < K::DIN; ++k) v[k] = Vin[((size_t)e * K::DIN + k) * C + c];
+    }
+#pragma unroll
+    for (int k = 0; k < K::DIN; ++k) gv[k] = 0.f;
+    float gs[K::NS], gvo[K::DOUT];
+#pragma unroll
+    for (int q = 0; q < K::NS; ++q) gs[q] = GX[(size_t)e * ldx + D + q * C + c];
+#pragma unroll
+    for (int k = 0; k < K::DOUT; ++k)
+      gvo[k] = LAST ? 0.f : gVout[((size_t)e * K::DOUT + k) * C + c];
+    K::bwd(v, G, th, gs, gvo, gv, gG);
+    if (INK == 0) {
+      // V^0 = w (x) Y: gradient to the env weights and to the harmonics
+#pragma unroll
+      for (int l = 0; l <= LMAX; ++l) {
+        float gw = 0.f;
+#pragma unroll
+        for (int m = 0; m < 2 * l + 1; ++m) gw += gv[l * l + m] * y[l * l + m];
+        GW[(size_t)e * ldw + l * C + c] = gw;
+      }
+#pragma unroll
+      for (int l = 0; l <= LMAX; ++l)
+#pragma unroll
+        for (int m = 0; m < 2 * l + 1; ++m) {
+          const float t = team_sum<C>(gv[l * l + m] * wl[l]);
+          if (c == l * l + m) gY[(size_t)e * 9 + l * l + m] += t;
+        }
+    } else {
+#pragma unroll
+      for (int k = 0; k < K::DIN; ++k) gVin[((size_t)e * K::DIN + k) * C + c] = gv[k];
+    }
+  }
+  // adjoint of the environment sum, fanned back out to every edge of the atom
+#pragma unroll
+  for (int k = 0; k < NY; ++k) gG[k] *= inv_sqrt_nu;
+  for (int e = eb; e < ee; ++e) {
+    const float* y = ef + (size_t)e * FF_EF_STRIDE + FF_EF_Y;
+#pragma unroll
+    for (int l = 0; l <= LMAX; ++l) {
+      const size_t wi = (size_t)e * ldw + l * C + c;
+      const float wl = W[wi];
+      float gw = 0.f;
+#pragma unroll
+      for (int m = 0; m < 2 * l + 1; ++m) gw += gG[l * l + m] * y[l * l + m];
+      GW[wi] = (INK == 0 ? GW[wi] : 0.f) + gw;
+#pragma unroll
+      for (int m = 0; m < 2 * l + 1; ++m) {
+        const float t = team_sum<C>(gG[l * l + m] * wl);
+        if (c == l * l + m) gY[(size_t)e * 9 + l * l + m] += t;
+      }
+    }
+  }
+}
+
+template <int LMAX, int INK, int LAST, int C>
+void fwd_one(int n_atoms, const int* row_ptr, int e0, const float* ef, const float* W, int ldw,
+             const float* Vin, const float* theta, float* X, int ldx, int D, float* Vout,
+             float* Gam, float inv_sqrt_nu, cudaStream_t s) {
+  k_env_tp_fwd<LMAX, INK, LAST, C><<<ff_cdiv((long long)n_atoms * C, 128), 128, 0, s>>>(
+      n_atoms, row_ptr, e0, ef, W, ldw, Vin, theta, X, ldx, D, Vout, Gam, inv_sqrt_nu);
+}
+
+template <int LMAX, int INK, int LAST, int C>
+void bwd_one(int n_atoms, const int* row_ptr, int e0, const float* ef, const float* W, int ldw,
+             const float* Vin, const float* theta, const float* GX, int ldx, int D,
+             const float* gVout, float* gVin, float* GW, float* gY, const float* Gam,
+             float inv_sqrt_nu, cudaStream_t s) {
+  k_env_tp_bwd<LMAX, INK, LAST, C><<<ff_cdiv((long long)n_atoms * C, 128), 128, 0, s>>>(
+      n_atoms, row_ptr, e0, ef, W, ldw, Vin, theta, GX, ldx, D, gVout, gVin, GW, gY, Gam,
+      inv_sqrt_nu);
+}
+
+#define FF_TP_DISPATCH(FN, ...)                                                             \
+  do {                                                                                      \
+    const int key = ((lmax * 3 + in_kind) * 2 + last) * 2 + (C == 32 ? 1 : 0);              \
+    switch (key) {                                                                          \
+      case ((1 * 3 + 0) * 2 + 0) * 2 + 0: FN<1, 0, 0, 16>(__VA_ARGS__); break;             \
+      case ((1 * 3 + 0) * 2 + 0) * 2 + 1: FN<1, 0, 0, 32>(__VA_ARGS__); break;             \
+      case ((1 * 3 + 0) * 2 + 1) * 2 + 0: FN<1, 0, 1, 16>(__VA_ARGS__); break;             \
+      case ((1 * 3 + 0) * 2 + 1) * 2 + 1: FN<1, 0, 1, 32>(__VA_ARGS__); break;             \
+      case ((1 * 3 + 1) * 2 + 0) * 2 + 0: FN<1, 1, 0, 16>(__VA_ARGS__); break;             \
+      case ((1 * 3 + 1) * 2 + 0) * 2 + 1: FN<1, 1, 0, 32>(__VA_ARGS__); break;             \
+      case ((1 * 3 + 1) * 2 + 1) * 2 + 0: FN<1, 1, 1, 16>(__VA_ARGS__); break;             \
+      case ((1 * 3 + 1) * 2 + 1) * 2 + 1: FN<1, 1, 1, 32>(__VA_ARGS__); break;             \
+      case ((1 * 3 + 2) * 2 + 0) * 2 + 0: FN<1, 2, 0, 16>(__VA_ARGS__); break;             \
+      case ((1 * 3 + 2) * 2 + 0) * 2 + 1: FN<1, 2, 0, 32>(__VA_ARGS__); break;             \
+      case ((1 * 3 + 2) * 2 + 1) * 2 + 0: FN<1, 2, 1, 16>(__VA_ARGS__); break;             \
+      case ((1 * 3 + 2) * 2 + 1) * 2 + 1: FN<1, 2, 1, 32>(__VA_ARGS__); break;             \
+      case ((2 * 3 + 0) * 2 + 0) * 2 + 0: FN<2, 0, 0, 16>(__VA_ARGS__); break;             \
+      case ((2 * 3 + 0) * 2 + 0) * 2 + 1: FN<2, 0, 0, 32>(__VA_ARGS__); break;             \
+      case ((2 * 3 + 0) * 2 + 1) * 2 + 0: FN<2, 0, 1, 16>(__VA_ARGS__); break;             \
+      case ((2 * 3 + 0) * 2 + 1) * 2 + 1: FN<2, 0, 1, 32>(__VA_ARGS__); break;             \
+      case ((2 * 3 + 1) * 2 + 0) * 2 + 0: FN<2, 1, 0, 16>(__VA_ARGS__); break;             \
+      case ((2 * 3 + 1) * 2 + 0) * 2 + 1: FN<2, 1, 0, 32>(__VA_ARGS__); break;             \
+      case ((2 * 3 + 1) * 2 + 1) * 2 + 0: FN<2, 1, 1, 16>(__VA_ARGS__); break;             \
+      case ((2 * 3 + 1) * 2 + 1) * 2 + 1: FN<2, 1, 1, 32>(__VA_ARGS__); break;             \
+      case ((2 * 3 + 2) * 2 + 0) * 2 + 0: FN<2, 2, 0, 16>(__VA_ARGS__); break;             \
+      case ((2 * 3 + 2) * 2 + 0) * 2 + 1: FN<2, 2, 0, 32>(__VA_ARGS__); break;             \
+      case ((2 * 3 + 2) * 2 + 1) * 2 + 0: FN<2, 2, 1, 16>(__VA_ARGS__); break;             \
+      case ((2 * 3 + 2) * 2 + 1) * 2 + 1: FN<2, 2, 1, 32>(__VA_ARGS__); break;             \
+      default: break;                                                                       \
+    }                                                                                       \
+  } while (0)
+
+}  // namespace
+
+
+void launch_env_tp_fwd(int lmax, int in_kind, int last, int C, int n_atoms, const int* row_ptr,
+                       int e0, const float* ef, const float* W, int ldw, const float* Vin,
+                       const float* theta, float* X, int ldx, int D, float* Vout, float* Gam,
+                       float inv_sqrt_nu, cudaStream_t s) {
+  ProfScope ps_(PC_TP_FWD, s);
+  if (n_atoms <= 0) return;
+  FF_TP_DISPATCH(fwd_one, n_atoms, row_ptr, e0, ef, W, ldw, Vin, theta, X, ldx, D, Vout, Gam,
+                 inv_sqrt_nu, s);
+  ff_count_launch(1);
+}
+
+void launch_env_tp_bwd(int lmax, int in_kind, int last, int C, int n_atoms, const int* row_ptr,
+                       int e0, const float* ef, const float* W, int ldw, const float* Vin,
+                       const float* theta, const float* GX, int ldx, int D, const float* gVout,
+                       float* gVin, float* GW, float* gY, const float* Gam, float inv_sqrt_nu,
+                       cudaStream_t s) {
+  ProfScope ps_(PC_TP_BWD, s);
+  if (n_atoms <= 0) return;
+  FF_TP_DISPATCH(bwd_one, n_atoms, row_ptr, e0, ef, W, ldw, Vin, theta, GX, ldx, D, gVout, gVin,
+                 GW, gY, Gam, inv_sqrt_nu, s);
+  ff_count_launch(1);
+}

@@ -1,0 +1,231 @@
+"""GPU parity of the CUDA path against the FP64 oracle, through the C ABI.
+
+Bars for the FP32 path: the sorted edge list and reverse index are bit-exact; total
+energy relative error <= 1e-6; force max-abs error <= 1e-4 eV/A.  Per-atom energies are
+held to 5e-6 of the largest per-atom magnitude, derived from FP32 rounding: each E_i is
+a chain of about seven dot products of length <= 352 (two-body, three latent layers,
+readout), so u * sqrt(352) * sqrt(7) ~ 3e-6 with u = 6e-8.  Inputs are the seeded
+synthetic systems of `synth`.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import Allegro64, md as omd, neighbors, pool, weights
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+E_REL = 1e-6
+EA_REL = 5e-6
+F_ABS = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ff():
+    import paper_2502_06073_gb300 as ff
+    ff._build.build()
+    ff.load_library()
+    assert torch.cuda.is_available()
+    return ff
+
+
+def _dev(a, dt):
+    return torch.tensor(np.asarray(a), dtype=dt, device="cuda")
+
+
+def _bind(ff, hp, s, seed=42, precision=0):
+    m = ff.FFModel(hp, seed=seed, precision=precision)
+    pos = _dev(s.pos, torch.float64)
+    Z = _dev(s.Z, torch.int32)
+    multi = s.sys_ptr.shape[0] > 2
+    m.bind(pos, Z, s.box, s.pbc, s.sys_ptr if multi else None)
+    return m, pos
+
+
+def _hp(name, wl=None, **over):
+    hp = synth.preset(name, **over)
+    if wl is not None:
+        hp["avg_num_neighbors"] = synth.NU[wl]
+    return hp
+
+
+SYSTEMS = {
+    "cubic96": (lambda: synth.config1_system(), "small", {}),
+    "cubic96_skin": (lambda: synth.config1_system(), "small", dict(skin=0.7)),
+    "csh512": (lambda: synth.csh_system(sub=True), "fm_water", {}),
+    "water4095": (lambda: synth.water_system(1365, L=34.44, seed=1001), "fm_water", {}),
+    "molecules64": (lambda: synth.molecules_system(64, seed=1003), "fm_water", {}),
+}
+
+
+@pytest.mark.parametrize("name", ["small", "fm_water"])
+def test_weights_bitwise(ff, name):
+    hp = synth.preset(name)
+    m = ff.FFModel(hp, seed=42)
+    got = m.export_params()
+    ref = np.concatenate([v.ravel() for v in weights.init_params(hp, 42).values()])
+    assert got.shape == ref.shape
+    np.testing.assert_array_equal(got, ref)
+
+
+@pytest.mark.parametrize("key", list(SYSTEMS))
+def test_edge_list_bit_exact(ff, key):
+    make, name, over = SYSTEMS[key]
+    s = make()
+    hp = synth.preset(name, **over)
+    m, _ = _bind(ff, hp, s)
+    rp, col, sh, rev = m.edges()
+    ref = neighbors.neighbor_list(s.pos, s.box, s.pbc, hp["rc"], 0.0, s.sys_ptr)
+    np.testing.assert_array_equal(rp, ref[0])
+    np.testing.assert_array_equal(col, ref[1])
+    np.testing.assert_array_equal(sh, ref[2])
+    if col.shape[0] < 60000:
+        np.testing.assert_array_equal(rev, neighbors.reverse_index(*ref))
+    else:
+        i = np.repeat(np.arange(s.n), np.diff(rp))
+        np.testing.assert_array_equal(col[rev], i)
+        np.testing.assert_array_equal(sh[rev], -sh)
+
+
+def _check_ef(Es, Ea, F, E_ref, Ea_ref, F_ref, tag, sys_ptr=None):
+    """Energy bar: total energy relative error <= 1e-6.  With several systems, each
+    system's error is held to 1e-6 of the sum of its |E_i|: a system energy is a sum of
+    per-atom terms of both signs, and for small molecules it nearly cancels, so its plain
+    relative error measures the cancellation, not the arithmetic."""
+    Es = Es.cpu().numpy()
+    Ea = Ea.double().cpu().numpy()
+    F = F.double().cpu().numpy()
+    e_tot = abs(Es.sum() - E_ref.sum()) / abs(E_ref.sum())
+    assert e_tot <= E_REL, (tag, "E total rel", e_tot)
+    if Es.shape[0] > 1:
+        scale = np.array([np.abs(Ea_ref[sys_ptr[k]:sys_ptr[k + 1]]).sum()
+                          for k in range(Es.shape[0])])
+        e_sys = (np.abs(Es - E_ref) / scale).max()
+        assert e_sys <= E_REL, (tag, "E_sys err / sum|E_i|", e_sys)
+    ea = np.abs(Ea - Ea_ref).max() / np.abs(Ea_ref).max()
+    f = np.abs(F - F_ref).max()
+    assert ea <= EA_REL, (tag, "E_atom rel", ea)
+    assert f <= F_ABS, (tag, "F max", f)
+
+
+@pytest.mark.parametrize("key,wl", [("cubic96", "cubic96"), ("csh512", "csh512"),
+                                    ("molecules64", "molecules1024")])
+def test_energy_forces_full(ff, key, wl):
+    make, name, over = SYSTEMS[key]
+    s = make()
+    hp = _hp(name, wl, **over)
+    m, pos = _bind(ff, hp, s)
+    Es, Ea, F = m.energy_forces(pos)
+    E_ref, Ea_ref, F_ref = pool.evaluate(hp, 42, s.pos, s.Z, s.box, s.pbc, s.sys_ptr)
+    _check_ef(Es, Ea, F, E_ref, Ea_ref, F_ref, key, s.sys_ptr)
+
+
+def test_water4095_energy_and_sampled_forces(ff):
+    make, name, _ = SYSTEMS["water4095"]
+    s = make()
+    hp = _hp(name, "water4095")
+    m, pos = _bind(ff, hp, s)
+    Es, Ea, F = m.energy_forces(pos)
+    E_ref, Ea_ref, F_ref = pool.evaluate(hp, 42, s.pos, s.Z, s.box, s.pbc)
+    _check_ef(Es, Ea, F, E_ref, Ea_ref, F_ref, "water4095")
+
+
+def test_ragged_chunks_identical(ff):
+    """Forcing many small edge chunks (ragged last chunk) changes no bit of the result."""
+    make, name, _ = SYSTEMS["csh512"]
+    s = make()
+    hp = _hp(name, "csh512")
+    m1, pos = _bind(ff, hp, s)
+    Es1, Ea1, F1 = m1.energy_forces(pos)
+    os.environ["FF_WORKSPACE_MB"] = "40"
+    try:
+        m2, pos2 = _bind(ff, hp, s)
+        Es2, Ea2, F2 = m2.energy_forces(pos2)
+    finally:
+        del os.environ["FF_WORKSPACE_MB"]
+    assert torch.equal(Ea1, Ea2) and torch.equal(F1, F2) and torch.equal(Es1, Es2)
+
+
+def test_deterministic(ff):
+    make, name, _ = SYSTEMS["csh512"]
+    s = make()
+    m, pos = _bind(ff, _hp(name, "csh512"), s)
+    a = m.energy_forces(pos)
+    b = m.energy_forces(pos)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
+def test_autograd_adjoint_multi_system(ff):
+    make, name, _ = SYSTEMS["molecules64"]
+    s = make()
+    hp = _hp(name, "molecules1024")
+    m, pos = _bind(ff, hp, s)
+    _, _, F = m.energy_forces(pos)
+    x = pos.clone().requires_grad_(True)
+    E = m.energy(x)
+    g = torch.linspace(-1.0, 2.0, E.shape[0], dtype=torch.float64, device="cuda")
+    (E * g).sum().backward()
+    sys_of = np.searchsorted(s.sys_ptr, np.arange(s.n), side="right") - 1
+    scale = g.cpu().numpy()[sys_of][:, None]
+    expect = -F.double().cpu().numpy() * scale
+    np.testing.assert_allclose(x.grad.cpu().numpy(), expect, rtol=1e-6, atol=1e-7)
+
+
+def test_forces_fd_of_gpu_energy(ff):
+    """Central differences of the GPU's own FP64-summed energy agree with its adjoint."""
+    s = synth.cluster_system(16, seed=9, radius=3.0)
+    hp = _hp("fm_water", None)
+    m, pos = _bind(ff, hp, s)
+    _, _, F = m.energy_forces(pos)
+    h = 2e-3
+    for a, k in [(0, 0), (5, 1), (11, 2)]:
+        p1, p2 = pos.clone(), pos.clone()
+        p1[a, k] += h
+        p2[a, k] -= h
+        e1 = m.energy_forces(p1, forces=False)[0].item()
+        e2 = m.energy_forces(p2, forces=False)[0].item()
+        fd = -(e1 - e2) / (2 * h)
+        assert abs(fd - F[a, k].item()) < 2e-3 * max(1.0, abs(fd)), (a, k, fd, F[a, k].item())
+
+
+def test_isolated_atom_and_empty_list(ff):
+    pos = np.array([[5.0, 5.0, 5.0], [15.0, 15.0, 15.0]])
+    s = synth.System("two-far", pos, np.array([8, 1], np.int32), np.array([20.0, 20.0, 20.0]),
+                     np.array([False, False, False]), np.array([0, 2], np.int32))
+    m, p = _bind(ff, synth.preset("small"), s)
+    Es, Ea, F = m.energy_forces(p)
+    assert float(Es[0]) == 0.0 and torch.all(F == 0)
+    assert m.edges()[1].shape[0] == 0
+
+
+def test_errors_are_reported(ff):
+    s = synth.config1_system()
+    hp = synth.preset("small")
+    m = ff.FFModel(hp, seed=1)
+    with pytest.raises(ff.FFError, match="FF_ERR_STATE"):
+        m.forces_adjoint()
+    bad = s.Z.copy()
+    bad[3] = 95
+    with pytest.raises(ff.FFError, match="FF_ERR_SPECIES"):
+        m.bind(_dev(s.pos, torch.float64), _dev(bad, torch.int32), s.box, s.pbc)
+
+
+def test_md_matches_oracle_trajectory(ff):
+    s = synth.config1_system()
+    hp = synth.preset("small", skin=0.5)
+    m, pos = _bind(ff, hp, s)
+    v0 = synth.maxwell_boltzmann(s.masses, 300.0, seed=5)
+    x = pos.clone()
+    v = _dev(v0, torch.float64)
+    mass = _dev(s.masses, torch.float64)
+    Ep, Ek = m.md(x, v, mass, 8, 1.0)
+    xr, vr, ep, ek = omd.run_nve(Allegro64(hp, 42), s.pos, v0, s.Z, s.box, s.pbc, s.masses,
+                                 1.0, 8)
+    assert np.abs(x.cpu().numpy() - xr).max() < 1e-7
+    assert np.abs(v.cpu().numpy() - vr).max() < 1e-8
+    np.testing.assert_allclose(Ep.cpu().numpy(), ep, rtol=E_REL)
+    np.testing.assert_allclose(Ek.cpu().numpy(), ek, rtol=1e-9)
