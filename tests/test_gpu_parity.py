@@ -228,4 +228,6 @@ def test_md_matches_oracle_trajectory(ff):
     assert np.abs(x.cpu().numpy() - xr).max() < 1e-7
     assert np.abs(v.cpu().numpy() - vr).max() < 1e-8
     np.testing.assert_allclose(Ep.cpu().numpy(), ep, rtol=E_REL)
-    np.testing.assert_allclose(Ek.cpu().numpy(), ek, rtol=1e-9)
+    # FP32 forces (error ~2e-7 eV/A) shift each velocity by ~dt*dF/m ~ 1e-9 A/fs per step
+    # against |v| ~ 0.02 A/fs: kinetic energies agree to ~1e-7 after 8 steps
+    np.testing.assert_allclose(Ek.cpu().numpy(), ek, rtol=1e-6)
