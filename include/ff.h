@@ -159,6 +159,40 @@ int ff_profile_enable(int on);
 int ff_profile_read(int64_t* launches, double* ms, int cap, int* n_classes);
 const char* ff_profile_class(int k);
 
+/* Limits of ff_neighbors_noalloc. */
+#define FF_NOALLOC_MAX_ATOMS 4096
+#define FF_NOALLOC_MAX_NEIGHBORS 256
+
+/* The neighbour-list build of ff_neighbors (same float32 membership test, same sorted
+ * (i, j, s) order, same list at rc) for one small system, without allocating anything.
+ * It exists for callers that cannot allocate device memory: an MD engine that only hands
+ * out memory from a pool it reserved up front, code running while a CUDA graph is being
+ * captured (cudaMalloc is not permitted there), or a host that forbids allocation inside
+ * its time-step loop.  It needs no context.  The paper has no counterpart of this call.
+ *   pos      device double[n_atoms][3]; n_atoms <= FF_NOALLOC_MAX_ATOMS (4096)
+ *   box, pbc host double[3], host int[3] as in ff_neighbors; rc: cutoff (A)
+ *   row_ptr  device int32[n_atoms+1]  (output, CSR offsets)
+ *   col      device int32[cap]        (output, neighbour index j) or NULL
+ *   shift    device int32[cap]        (output, image shift packed as three signed bytes
+ *                                      x | y << 8 | z << 16) or NULL
+ *   n_edges  host int64               (output, number of edges)
+ *   msg      host char[msg_cap] or NULL, receives a message on failure
+ * With col or shift NULL only row_ptr and *n_edges are produced (to size the buffers).
+ * Working memory is a single file-scope __device__ array of about 13 MB that every GPU
+ * loading the library holds until the process exits; no cudaMalloc, cudaFree or other
+ * allocating call is made.  The first call on each device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make that first call before
+ * any stream capture.  Every call shares the array and it keeps the previous call's
+ * contents (what must start at zero is cleared on every call), so calls that overlap on
+ * the GPU -- on different streams or host threads -- race and must not be issued.
+ * Kernel profiling (ff_profile_enable) must be off, as it creates CUDA events.
+ * Synchronises `stream` (edge count).  Errors: FF_ERR_ARG (n_atoms above the limit, or
+ * cap below the edge count), FF_ERR_CAPACITY (an atom with more than
+ * FF_NOALLOC_MAX_NEIGHBORS neighbours), FF_ERR_BOX, FF_ERR_CUDA. */
+int ff_neighbors_noalloc(const double* pos, int n_atoms, const double box[3], const int pbc[3],
+                         float rc, int32_t* row_ptr, int32_t* col, int32_t* shift, int64_t cap,
+                         int64_t* n_edges, char* msg, size_t msg_cap, void* stream);
+
 /* Message describing the last error of `ctx` (or of the last failed ff_create when ctx
  * is NULL).  The string stays valid until the next call on the context. */
 const char* ff_last_error(const ff_ctx* ctx);

@@ -27,7 +27,7 @@ ERRORS = {-1: "FF_ERR_ARG", -2: "FF_ERR_SPECIES", -3: "FF_ERR_OOM", -4: "FF_ERR_
 # Every function the C ABI exports (include/ff.h).
 ABI = ("ff_create", "ff_destroy", "ff_neighbors", "ff_energy_forces", "ff_forces",
        "ff_md_step", "ff_export_params", "ff_get_edges", "ff_kernel_launches", "ff_last_error",
-       "ff_profile_enable", "ff_profile_read", "ff_profile_class")
+       "ff_profile_enable", "ff_profile_read", "ff_profile_class", "ff_neighbors_noalloc")
 
 
 class HParams(ctypes.Structure):
@@ -75,6 +75,10 @@ def load_library(path: str | None = None):
     lib.ff_profile_read.argtypes = [vp, vp, i32, ctypes.POINTER(i32)]
     lib.ff_profile_class.argtypes = [i32]
     lib.ff_profile_class.restype = ctypes.c_char_p
+    lib.ff_neighbors_noalloc.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_int), ctypes.c_float, vp, vp,
+                                         vp, i64, ctypes.POINTER(i64), ctypes.c_char_p,
+                                         ctypes.c_size_t, vp]
     for name in ABI:
         getattr(lib, name)
     _lib = lib

@@ -10,7 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libff.so")
-SOURCES = ["ff_api.cu", "nbr.cu", "model.cu", "tp_kernels.cu", "gemm_f32.cu", "gemm_bf16.cu"]
+SOURCES = ["ff_api.cu", "nbr.cu", "model.cu", "tp_kernels.cu", "gemm_f32.cu", "gemm_bf16.cu",
+           "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
          "-ffp-contract=off", "--expt-relaxed-constexpr", "-Xptxas", "-O3"]
