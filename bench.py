@@ -72,6 +72,39 @@ def gemm_flops_per_edge(hp):
     return 2 * 2 * mac
 
 
+def gemm_bytes_per_edge(hp, precision):
+    """Compulsory HBM bytes per edge of all MLP GEMM launches of one E+F evaluation: each
+    operand read once, each epilogue input read once, each output written once, in the
+    storage types of the path (FP32 everywhere for precision 0; BF16 GEMM operands plus
+    the FP32 pre-activations, residual stream and gradients for precision 1)."""
+    tb, lat = hp["two_body"], hp["latent"]
+    D = tb[-1]
+    C, lmax, NL = hp["channels"], hp["lmax"], hp["n_layers"]
+    ldw = (lmax + 1) * C
+    ldx = D + (lmax + 1) * C
+    sa = 2 if precision == 1 else 4          # bytes of a GEMM operand element
+    cp = 2 if precision == 1 else 0          # extra bf16 copy of the residual stream
+    b = 0
+    for k in range(1, len(tb)):              # two-body hidden layers
+        b += tb[k - 1] * sa + tb[k] * 4
+        b += (tb[k] * 4 + tb[k] * cp + 4) if k == len(tb) - 1 else tb[k] * sa
+    for _ in range(NL):
+        b += D * sa + ldw * 4                # environment projection
+        fan = ldx
+        for k, w in enumerate(lat):
+            b += fan * sa + w * 4
+            b += (2 * D * 4 + D * cp + 4) if k == len(lat) - 1 else w * sa
+            fan = w
+    for L in range(NL, 0, -1):               # adjoint
+        for k in range(len(lat) - 1, 0, -1):
+            b += lat[k] * sa + lat[k - 1] * 4 + lat[k - 1] * sa
+        b += lat[0] * sa + (0 if L == NL else D * 4) + ldx * 4
+        b += ldw * sa + 2 * D * 4
+    for k in range(len(tb) - 1, 0, -1):
+        b += tb[k] * sa + tb[k - 1] * 4 + tb[k - 1] * (sa if k > 1 else 4)
+    return b
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
@@ -148,22 +181,38 @@ def traffic_per_edge(kernel):
 
 
 # ------------------------------------------------------------------------- oracle arm
-def oracle_rate(wl, budget_s, workers=None):
-    """Oracle E+F atom rate (atoms/s) on a bounded sample of centres of the workload."""
-    from oracle import pool
+def oracle_leg(wl, pos, F_gpu, n_atoms=24, workers=None):
+    """Time the FP64 oracle (spawn pool over all host cores) on the centres that the
+    forces of `n_atoms` sampled atoms need, and compare those forces with F_gpu."""
+    from oracle import neighbors, pool
     s = WORKLOADS[wl]["make"]()
     hp = model_hp(wl)
     workers = workers or os.cpu_count() or 1
-    probe = list(range(0, min(s.n, 2 * workers)))
+    atoms = np.linspace(0, s.n - 1, n_atoms).astype(int).tolist()
+    nl = neighbors.neighbor_list(pos, s.box, s.pbc, hp["rc"], 0.0, centres=atoms)
+    need = set(atoms)
+    for m in atoms:
+        need.update(int(j) for j in nl[m][0])
+    centres = sorted(need)
     t0 = time.perf_counter()
-    pool.centre_terms(hp, 42, s.pos, s.Z, s.box, s.pbc, probe, workers=workers)
-    t_probe = time.perf_counter() - t0
-    n = int(min(s.n, max(len(probe), len(probe) * budget_s / max(t_probe, 1e-3))))
-    centres = list(range(n))
-    t0 = time.perf_counter()
-    pool.centre_terms(hp, 42, s.pos, s.Z, s.box, s.pbc, centres, workers=workers)
+    terms = pool.centre_terms(hp, 42, pos, s.Z, s.box, s.pbc, centres, workers=workers)
     dt = time.perf_counter() - t0
-    return n / dt, n, dt, workers
+    d = []
+    for m in atoms:
+        Fm = terms[m][3].sum(axis=0)
+        for i in sorted(set(int(j) for j in nl[m][0])):
+            col, g = terms[i][1], terms[i][3]
+            Fm = Fm - g[col == m].sum(axis=0)
+        d.append(F_gpu[m] - Fm)
+    d = np.array(d)
+    cpu = {"value": len(centres) / dt, "unit": "atom-steps/s", "cores": workers,
+           "kind": "oracle",
+           "sample": f"E+F of {len(centres)} centres of {wl} (the neighbourhoods of {n_atoms} "
+                     f"atoms), {dt:.1f} s on a spawn pool of {workers} processes"}
+    ferr = {"rmse_meV_per_A": float(np.sqrt((d ** 2).mean()) * 1e3),
+            "max_meV_per_A": float(np.abs(d).max() * 1e3),
+            "sample": f"forces on {n_atoms} atoms at the final positions vs the FP64 oracle"}
+    return cpu, ferr
 
 
 def run_reference(args):
@@ -242,29 +291,36 @@ def run_ours(args):
     E_edges = model.edges()[1].shape[0]
 
     # ---- timed region: K MD steps, device-timed per step, L2 flushed between steps
+    def timed_steps(profile):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        if profile:
+            ff.profile_enable(True)
+            ff.profile_read()
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            model.md(x, v, mass, 1, dt_fs, energies=False)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        prof = None
+        if profile:
+            prof = ff.profile_read()
+            ff.profile_enable(False)
+        return [a.elapsed_time(b) for a, b in ev], prof
+
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    ff.profile_enable(True)
-    ff.profile_read()
     l0 = model.launches()
-    step_ms = []
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    for k in range(args.steps):
-        flush.zero_()
-        ev[k][0].record(stream)
-        model.md(x, v, mass, 1, dt_fs, energies=False)
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
+    step_ms, _ = timed_steps(False)
     launches = model.launches() - l0
-    prof = ff.profile_read()
-    ff.profile_enable(False)
     clk = clocks.stop()
-    for a, b in ev:
-        step_ms.append(a.elapsed_time(b))
+    # the same number of steps again with every launch bracketed by events (per-kernel
+    # durations for the roofline; kept out of the headline timing)
+    prof_ms, prof = timed_steps(True)
     t_total = sum(step_ms) / 1e3
     if world > 1:
         t = torch.tensor([t_total], dtype=torch.float64, device=dev)
@@ -319,25 +375,40 @@ def run_ours(args):
         tpe = traffic_per_edge("gemm_f32")
         roof["traffic"] = (tpe * E_edges * n_eval / max(dom_launch, 1)) if tpe else None
     elif dom_name == "gemm_bf16":
+        # tensor-core GEMMs with FP32 epilogue streams: the HBM ceiling is the lower one
         flops = gemm_flops_per_edge(hp) * E_edges * n_eval
-        achieved = flops / (dom_ms / 1e3) / 1e12
-        peak = pk["bf16_tflops_sustained"]
-        roof = {"kernel": "gemm_bf16 (tcgen05)", "bound": "tensor", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": f"bf16_tflops_sustained ({pk_kind})", "launches": dom_launch,
-                "avg_launch_us": 1e3 * dom_ms / max(dom_launch, 1)}
+        byts = gemm_bytes_per_edge(hp, 1) * E_edges * n_eval
+        t_s = dom_ms / 1e3
+        t_tensor = flops / (pk["bf16_tflops_sustained"] * 1e12)
+        t_hbm = byts / (pk["hbm_gbs"] * 1e9)
+        if t_hbm >= t_tensor:
+            achieved, peak = byts / t_s / 1e9, pk["hbm_gbs"]
+            roof = {"kernel": "gemm_bf16 (tcgen05, all MLP GEMM launches)", "bound": "hbm",
+                    "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "peak_source": f"hbm_gbs ({pk_kind})"}
+        else:
+            achieved, peak = flops / t_s / 1e12, pk["bf16_tflops_sustained"]
+            roof = {"kernel": "gemm_bf16 (tcgen05, all MLP GEMM launches)", "bound": "tensor",
+                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak,
+                    "peak_source": f"bf16_tflops_sustained ({pk_kind})"}
+        roof.update({"tensor_tflops": flops / t_s / 1e12,
+                     "tensor_frac": flops / t_s / 1e12 / pk["bf16_tflops_sustained"],
+                     "algorithmic_bytes_per_edge": gemm_bytes_per_edge(hp, 1),
+                     "launches": dom_launch, "avg_launch_us": 1e3 * dom_ms / max(dom_launch, 1)})
         tpe = traffic_per_edge("gemm_bf16")
         roof["traffic"] = (tpe * E_edges * n_eval / max(dom_launch, 1)) if tpe else None
     else:
         roof = {"kernel": dom_name, "bound": "alu", "achieved": None, "peak": None,
                 "unit": None, "frac": None, "traffic": None}
 
-    cpu = None
+    # ---- CPU-baseline leg: the FP64 oracle on a bounded sample of this workload (the
+    # neighbourhoods of a few atoms at the final positions), timed; the same oracle
+    # results give the force error of this run's path on those atoms
+    cpu = ferr = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, n_s, dt_s, cores = oracle_rate(wl, budget_s=15.0)
-        cpu = {"value": rate, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
-               "sample": f"E+F of centres 0..{n_s - 1} of {wl} ({dt_s:.1f} s of CPU work, "
-                         f"spawn pool of {cores} processes)"}
+        _, _, F = model.energy_forces(x, E_atom=False)
+        cpu, ferr = oracle_leg(wl, x.cpu().numpy(), F.double().cpu().numpy())
 
     if rank == 0:
         line = {
@@ -359,6 +430,8 @@ def run_ours(args):
             "clocks": clk,
             "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof.items()
                                    if v[0]},
+            "profiled_ms_per_step": sum(prof_ms) / args.steps,
+            "force_error": ferr,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -372,7 +445,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="water12288", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--precision", type=int, default=1, choices=[0, 1],
+                    help="1: BF16 tensor-core MLPs (default); 0: plain FP32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

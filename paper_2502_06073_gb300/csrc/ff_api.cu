@@ -120,6 +120,15 @@ struct ff_ctx {
   float* theta[FF_MAX_LAYERS + 1] = {nullptr};
   float* Wlat[FF_MAX_LAYERS + 1][4] = {{nullptr}}; float* WlatT[FF_MAX_LAYERS + 1][4] = {{nullptr}};
   float* w_eff = nullptr;
+  // bf16 weight copies for the tensor-core path: W [in][out] (adjoint operand) and
+  // W^T [out][in] (forward operand)
+  __nv_bfloat16* wbuf_b = nullptr;
+  __nv_bfloat16* W2b_b[4] = {nullptr}; __nv_bfloat16* W2bT_b[4] = {nullptr};
+  __nv_bfloat16* Wenv_b[FF_MAX_LAYERS + 1] = {nullptr};
+  __nv_bfloat16* WenvT_b[FF_MAX_LAYERS + 1] = {nullptr};
+  __nv_bfloat16* Wlat_b[FF_MAX_LAYERS + 1][4] = {{nullptr}};
+  __nv_bfloat16* WlatT_b[FF_MAX_LAYERS + 1][4] = {{nullptr}};
+  bool gemm_fail = false;
   // system
   int n = 0, n_sys = 0, pbc[3] = {0, 0, 0};
   double box[3] = {0, 0, 0};
@@ -160,6 +169,12 @@ struct ff_ctx {
   float* Gam[FF_MAX_LAYERS + 1] = {nullptr};
   float* GX[2] = {nullptr}; float* GZ[2] = {nullptr}; float* gV[2] = {nullptr};
   float* GW = nullptr; float* gY = nullptr; float* gf = nullptr;
+  // bf16 GEMM operands of the tensor-core path
+  __nv_bfloat16* h2bb[4] = {nullptr};
+  __nv_bfloat16* hlatb[FF_MAX_LAYERS + 1][4] = {{nullptr}};
+  __nv_bfloat16* Xb[FF_MAX_LAYERS + 1] = {nullptr};
+  __nv_bfloat16* GZb[2] = {nullptr};
+  __nv_bfloat16* GWb = nullptr;
   // state of the last evaluation
   bool state_valid = false;
   int state_chunks = 0;
@@ -352,6 +367,43 @@ int upload_weights(ff_ctx* c) {
   FF_TRY(dalloc(c, &c->wbuf, host.size()));
   FF_CK(c, cudaMemcpy(c->wbuf, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice));
   for (auto& f : fix) *f.first = c->wbuf + f.second;
+  if (c->hp.precision != 1) return FF_OK;
+  // bf16 copies (rounded once from the FP64 draws) for the tensor-core GEMMs
+  std::vector<__nv_bfloat16> hb;
+  std::vector<std::pair<__nv_bfloat16**, size_t>> fixb;
+  auto putb = [&](__nv_bfloat16** dst, const Tensor* t, bool transpose) {
+    const size_t base = hb.size();
+    const size_t n = (size_t)t->rows * t->cols;
+    hb.resize(base + ((n + 127) / 128) * 128, __float2bfloat16_rn(0.f));
+    for (int r = 0; r < t->rows; ++r)
+      for (int q = 0; q < t->cols; ++q) {
+        const float v = (float)c->params[t->off + (size_t)r * t->cols + q];
+        if (!transpose) hb[base + (size_t)r * t->cols + q] = __float2bfloat16_rn(v);
+        else hb[base + (size_t)q * t->rows + r] = __float2bfloat16_rn(v);
+      }
+    fixb.push_back({dst, base});
+  };
+  for (int k = 0; k < c->n2b; ++k) {
+    const Tensor* t = find_tensor(c, "W2b." + std::to_string(k));
+    if (k > 0) {
+      putb(&c->W2b_b[k], t, false);
+      putb(&c->W2bT_b[k], t, true);
+    }
+  }
+  for (int L = 1; L <= c->NL; ++L) {
+    const Tensor* t = find_tensor(c, "Wenv." + std::to_string(L));
+    putb(&c->Wenv_b[L], t, false);
+    putb(&c->WenvT_b[L], t, true);
+    for (int k = 0; k < c->nlat; ++k) {
+      const Tensor* tl = find_tensor(c, "Wlat." + std::to_string(L) + "." + std::to_string(k));
+      putb(&c->Wlat_b[L][k], tl, false);
+      putb(&c->WlatT_b[L][k], tl, true);
+    }
+  }
+  FF_TRY(dalloc(c, &c->wbuf_b, hb.size()));
+  FF_CK(c, cudaMemcpy(c->wbuf_b, hb.data(), hb.size() * sizeof(__nv_bfloat16),
+                      cudaMemcpyHostToDevice));
+  for (auto& f : fixb) *f.first = c->wbuf_b + f.second;
   return FF_OK;
 }
 
@@ -370,18 +422,31 @@ int ensure_workspace(ff_ctx* c, long long ecap, int acap) {
   free_workspace(c);
   const ff_hparams& hp = c->hp;
   std::vector<std::pair<void**, size_t>> plan;   // (pointer, bytes)
+  const bool tc = hp.precision == 1;
   auto f32 = [&](float** p, long long count) { plan.push_back({(void**)p, (size_t)count * 4}); };
+  auto b16 = [&](__nv_bfloat16** p, long long count) {
+    plan.push_back({(void**)p, (size_t)count * 2});
+  };
   f32(&c->ef, ecap * FF_EF_STRIDE);
   plan.push_back({(void**)&c->zz, (size_t)ecap * 8});
   for (int k = 0; k < c->n2b; ++k) {
     f32(&c->z2b[k], ecap * hp.two_body[k]);
-    if (k < c->n2b - 1) f32(&c->h2b[k], ecap * hp.two_body[k]);
+    if (k < c->n2b - 1) {
+      if (tc) b16(&c->h2bb[k], ecap * hp.two_body[k]);
+      else f32(&c->h2b[k], ecap * hp.two_body[k]);
+    }
   }
-  for (int L = 0; L <= c->NL; ++L) f32(&c->X[L], ecap * c->ldx);
+  for (int L = 0; L <= c->NL; ++L) {
+    f32(&c->X[L], ecap * c->ldx);
+    if (tc) b16(&c->Xb[L], ecap * c->ldx);
+  }
   for (int L = 1; L <= c->NL; ++L) {
     for (int k = 0; k < c->nlat; ++k) {
       f32(&c->zlat[L][k], ecap * hp.latent[k]);
-      if (k < c->nlat - 1) f32(&c->hlat[L][k], ecap * hp.latent[k]);
+      if (k < c->nlat - 1) {
+        if (tc) b16(&c->hlatb[L][k], ecap * hp.latent[k]);
+        else f32(&c->hlat[L][k], ecap * hp.latent[k]);
+      }
     }
     f32(&c->Wv[L], ecap * c->ldw);
     if (L < c->NL) f32(&c->V[L], ecap * (long long)c->layer_dout[L] * c->C);
@@ -395,6 +460,11 @@ int ensure_workspace(ff_ctx* c, long long ecap, int acap) {
   f32(&c->GW, ecap * c->ldw);
   f32(&c->gY, ecap * 9);
   f32(&c->gf, ecap);
+  if (tc) {
+    b16(&c->GZb[0], ecap * c->maxw);
+    b16(&c->GZb[1], ecap * c->maxw);
+    b16(&c->GWb, ecap * c->ldw);
+  }
   size_t total = 0;
   for (auto& p : plan) total += (p.second + 255) & ~(size_t)255;
   void* base = nullptr;
@@ -427,6 +497,8 @@ size_t bytes_per_edge(const ff_ctx* c) {
   }
   b += 2 * ((size_t)c->ldx + c->maxw + (size_t)c->maxdim * c->C) * 4;
   b += (size_t)c->ldw * 4 + 9 * 4 + 4;
+  if (hp.precision == 1)   // bf16 operands (the fp32 hidden activations are not kept)
+    b += (size_t)(c->NL + 1) * c->ldx * 2 + 2 * (size_t)c->maxw * 2 + (size_t)c->ldw * 2;
   return b;
 }
 
@@ -450,6 +522,7 @@ int read_flags(ff_ctx* c, cudaStream_t s) {
     if (e & 1) return set_err(c, FF_ERR_CAPACITY, "neighbour count above the per-atom limit");
     if (e & 8) return set_err(c, FF_ERR_STATE, "reverse edge missing (asymmetric list)");
     if (e & 32) return set_err(c, FF_ERR_NONFINITE, "non-finite force");
+    if (e & 64) return set_err(c, FF_ERR_CUDA, "tensor-core GEMM pipeline wait timed out");
   }
   return FF_OK;
 }
@@ -587,8 +660,21 @@ void plan_chunks(const ff_ctx* c, long long cap, std::vector<int>& starts) {
   }
 }
 
+// C = alpha A B with the precision of the context: FP32 CUDA-core GEMM (A32, W32 [K][N])
+// or BF16 tensor-core GEMM (Ab, Wt_b = W^T [N][K]).
+void mlp_gemm(ff_ctx* c, int mode, long long M, int N, int K, const float* A32,
+              const __nv_bfloat16* Ab, int lda, const float* W32, const __nv_bfloat16* Wt_b,
+              const EpiParams& ep, cudaStream_t s) {
+  if (c->hp.precision == 0) {
+    launch_gemm_f32(mode, (int)M, N, K, A32, lda, W32, N, ep, s);
+  } else if (!launch_gemm_bf16(mode, (int)M, N, K, Ab, lda, Wt_b, K, ep, c->flags, s)) {
+    c->gemm_fail = true;
+  }
+}
+
 void forward_chunk(ff_ctx* c, const double* pos, int a0, int a1, float* E_atom, cudaStream_t s) {
   const ff_hparams& hp = c->hp;
+  const bool tc = hp.precision == 1;
   const int e0 = c->row_ptr_h[a0];
   const long long Ec = (long long)c->row_ptr_h[a1] - e0;
   const int* rp = c->row_ptr + a0;
@@ -601,22 +687,26 @@ void forward_chunk(ff_ctx* c, const double* pos, int a0, int a1, float* E_atom, 
   const float a0f = (float)(1.0 / sqrt((double)(2 * FF_N_SPECIES + hp.n_basis)));
   if (c->n2b == 1) {
     launch_twobody_in(Ec, w0, hp.n_basis, c->ef, c->zz, c->W2b[0], a0f, c->z2b[0], c->X[0],
-                      c->ldx, 1, s);
+                      c->ldx, tc ? c->Xb[0] : nullptr, c->ldx, 1, s);
   } else {
-    launch_twobody_in(Ec, w0, hp.n_basis, c->ef, c->zz, c->W2b[0], a0f, c->z2b[0], c->h2b[0],
-                      w0, 0, s);
+    launch_twobody_in(Ec, w0, hp.n_basis, c->ef, c->zz, c->W2b[0], a0f, c->z2b[0],
+                      tc ? nullptr : c->h2b[0], w0, tc ? c->h2bb[0] : nullptr, w0, 0, s);
     for (int k = 1; k < c->n2b; ++k) {
       const int win = hp.two_body[k - 1], wout = hp.two_body[k];
+      const bool last = k == c->n2b - 1;
       EpiParams ep{};
       ep.alpha = (float)(1.0 / sqrt((double)win));
       ep.pre = c->z2b[k]; ep.ldp = wout;
-      if (k == c->n2b - 1) {
+      if (last) {
         ep.out = c->X[0]; ep.ldo = c->ldx; ep.f = fptr; ep.ldf = FF_EF_STRIDE;
-        launch_gemm_f32(EPI_SILU_F, (int)Ec, wout, win, c->h2b[k - 1], win, c->W2b[k], wout, ep, s);
+        if (tc) { ep.outb = c->Xb[0]; ep.ldob = c->ldx; }
+      } else if (tc) {
+        ep.outb = c->h2bb[k]; ep.ldob = wout;
       } else {
         ep.out = c->h2b[k]; ep.ldo = wout;
-        launch_gemm_f32(EPI_SILU, (int)Ec, wout, win, c->h2b[k - 1], win, c->W2b[k], wout, ep, s);
       }
+      mlp_gemm(c, last ? EPI_SILU_F : EPI_SILU, Ec, wout, win, c->h2b[k - 1], c->h2bb[k - 1], win,
+               c->W2b[k], c->W2bT_b[k], ep, s);
     }
   }
   const float inv_sqrt_nu = (float)(1.0 / sqrt((double)hp.avg_num_neighbors));
@@ -624,33 +714,39 @@ void forward_chunk(ff_ctx* c, const double* pos, int a0, int a1, float* E_atom, 
     EpiParams ep{};
     ep.alpha = (float)(1.0 / sqrt((double)c->D));
     ep.out = c->Wv[L]; ep.ldo = c->ldw;
-    launch_gemm_f32(EPI_STORE, (int)Ec, c->ldw, c->D, c->X[L - 1], c->ldx, c->Wenv[L], c->ldw, ep, s);
+    mlp_gemm(c, EPI_STORE, Ec, c->ldw, c->D, c->X[L - 1], c->Xb[L - 1], c->ldx, c->Wenv[L],
+             c->WenvT_b[L], ep, s);
     const int last = L == c->NL ? 1 : 0;
     launch_env_tp_fwd(c->lmax, std::min(L - 1, 2), last, c->C, na, rp, e0, c->ef, c->Wv[L],
                       c->ldw, L >= 2 ? c->V[L - 1] : nullptr, last ? nullptr : c->theta[L],
                       c->X[L - 1], c->ldx, c->D, last ? nullptr : c->V[L], c->Gam[L], inv_sqrt_nu,
                       s);
-    const float* A = c->X[L - 1];
-    int fan = c->ldx;
+    if (tc) launch_cvt_bf16(c->X[L - 1], c->ldx, c->Xb[L - 1], c->ldx, Ec, c->D, c->ns * c->C, s);
+    const float* A32 = c->X[L - 1];
+    const __nv_bfloat16* Ab = c->Xb[L - 1];
+    int fan = c->ldx, lda = c->ldx;
     for (int k = 0; k < c->nlat; ++k) {
       const int wout = hp.latent[k];
+      const bool lastk = k == c->nlat - 1;
       EpiParams el{};
       el.alpha = (float)(1.0 / sqrt((double)fan));
       el.pre = c->zlat[L][k]; el.ldp = wout;
-      if (k == c->nlat - 1) {
+      if (lastk) {
         el.out = c->X[L]; el.ldo = c->ldx;
         el.res = c->X[L - 1]; el.ldr = c->ldx;
         el.f = fptr; el.ldf = FF_EF_STRIDE;
         el.beta = (float)(1.0 / sqrt(2.0));
-        launch_gemm_f32(EPI_SILU_RES, (int)Ec, wout, fan, A, fan == c->ldx ? c->ldx : fan,
-                        c->Wlat[L][k], wout, el, s);
+        if (tc) { el.outb = c->Xb[L]; el.ldob = c->ldx; }
+      } else if (tc) {
+        el.outb = c->hlatb[L][k]; el.ldob = wout;
       } else {
         el.out = c->hlat[L][k]; el.ldo = wout;
-        launch_gemm_f32(EPI_SILU, (int)Ec, wout, fan, A, fan == c->ldx ? c->ldx : fan,
-                        c->Wlat[L][k], wout, el, s);
-        A = c->hlat[L][k];
       }
-      fan = wout;
+      mlp_gemm(c, lastk ? EPI_SILU_RES : EPI_SILU, Ec, wout, fan, A32, Ab, lda, c->Wlat[L][k],
+               c->WlatT_b[L][k], el, s);
+      A32 = c->hlat[L][k];
+      Ab = c->hlatb[L][k];
+      fan = lda = wout;
     }
   }
   launch_energy(na, rp, e0, c->X[c->NL], c->ldx, c->D, c->w_eff, E_atom + a0, s);
@@ -658,6 +754,7 @@ void forward_chunk(ff_ctx* c, const double* pos, int a0, int a1, float* E_atom, 
 
 void backward_chunk(ff_ctx* c, int a0, int a1, const double* seed, cudaStream_t s) {
   const ff_hparams& hp = c->hp;
+  const bool tc = hp.precision == 1;
   const int e0 = c->row_ptr_h[a0];
   const long long Ec = (long long)c->row_ptr_h[a1] - e0;
   if (Ec <= 0) return;
@@ -673,15 +770,17 @@ void backward_chunk(ff_ctx* c, int a0, int a1, const double* seed, cudaStream_t 
   for (int L = c->NL; L >= 1; --L) {
     const int kl = c->nlat - 1;
     launch_rowred_bwd(Ec, hp.latent[kl], gx, ldgx, c->zlat[L][kl], hp.latent[kl], c->ef, r2,
-                      c->GZ[0], hp.latent[kl], c->gf, s);
+                      tc ? nullptr : c->GZ[0], hp.latent[kl], tc ? c->GZb[0] : nullptr, c->gf,
+                      s);
     int gzb = 0;
     for (int k = kl; k >= 1; --k) {
       EpiParams ep{};
       ep.alpha = (float)(1.0 / sqrt((double)hp.latent[k - 1]));
-      ep.out = c->GZ[gzb ^ 1]; ep.ldo = hp.latent[k - 1];
+      if (tc) { ep.outb = c->GZb[gzb ^ 1]; ep.ldob = hp.latent[k - 1]; }
+      else { ep.out = c->GZ[gzb ^ 1]; ep.ldo = hp.latent[k - 1]; }
       ep.z = c->zlat[L][k - 1]; ep.ldz = hp.latent[k - 1];
-      launch_gemm_f32(EPI_DSILU, (int)Ec, hp.latent[k - 1], hp.latent[k], c->GZ[gzb], hp.latent[k],
-                      c->WlatT[L][k], hp.latent[k - 1], ep, s);
+      mlp_gemm(c, EPI_DSILU, Ec, hp.latent[k - 1], hp.latent[k], c->GZ[gzb], c->GZb[gzb],
+               hp.latent[k], c->WlatT[L][k], c->Wlat_b[L][k], ep, s);
       gzb ^= 1;
     }
     {
@@ -689,37 +788,42 @@ void backward_chunk(ff_ctx* c, int a0, int a1, const double* seed, cudaStream_t 
       ep.alpha = (float)(1.0 / sqrt((double)c->ldx));
       ep.out = c->GX[cur]; ep.ldo = c->ldx;
       ep.res = gx; ep.ldr = ldgx; ep.beta = r2; ep.split = c->D;
-      launch_gemm_f32(EPI_RES, (int)Ec, c->ldx, hp.latent[0], c->GZ[gzb], hp.latent[0],
-                      c->WlatT[L][0], c->ldx, ep, s);
+      mlp_gemm(c, EPI_RES, Ec, c->ldx, hp.latent[0], c->GZ[gzb], c->GZb[gzb], hp.latent[0],
+               c->WlatT[L][0], c->Wlat_b[L][0], ep, s);
     }
     const int last = L == c->NL ? 1 : 0;
     launch_env_tp_bwd(c->lmax, std::min(L - 1, 2), last, c->C, na, rp, e0, c->ef, c->Wv[L],
                       c->ldw, L >= 2 ? c->V[L - 1] : nullptr, last ? nullptr : c->theta[L],
                       c->GX[cur], c->ldx, c->D, last ? nullptr : c->gV[gvb],
                       L >= 2 ? c->gV[gvb ^ 1] : nullptr, c->GW, c->gY, c->Gam[L], inv_sqrt_nu, s);
+    if (tc) launch_cvt_bf16(c->GW, c->ldw, c->GWb, c->ldw, Ec, 0, c->ldw, s);
     {
       EpiParams ep{};
       ep.alpha = (float)(1.0 / sqrt((double)c->D));
       ep.out = c->GX[cur]; ep.ldo = c->ldx;
-      launch_gemm_f32(EPI_ACC, (int)Ec, c->D, c->ldw, c->GW, c->ldw, c->WenvT[L], c->D, ep, s);
+      mlp_gemm(c, EPI_ACC, Ec, c->D, c->ldw, c->GW, c->GWb, c->ldw, c->WenvT[L], c->Wenv_b[L],
+               ep, s);
     }
     gx = c->GX[cur];
     ldgx = c->ldx;
     cur ^= 1;
     gvb ^= 1;
   }
-  // two-body MLP: x^0 = f * silu(z_last)
+  // two-body MLP: x^0 = f * silu(z_last); the last gradient (dE/dz_0) stays FP32
   const int kb = c->n2b - 1;
+  const bool b16_first = tc && kb >= 1;
   launch_rowred_bwd(Ec, hp.two_body[kb], gx, ldgx, c->z2b[kb], hp.two_body[kb], c->ef, 1.f,
-                    c->GZ[0], hp.two_body[kb], c->gf, s);
+                    b16_first ? nullptr : c->GZ[0], hp.two_body[kb],
+                    b16_first ? c->GZb[0] : nullptr, c->gf, s);
   int gzb = 0;
   for (int k = kb; k >= 1; --k) {
     EpiParams ep{};
     ep.alpha = (float)(1.0 / sqrt((double)hp.two_body[k - 1]));
-    ep.out = c->GZ[gzb ^ 1]; ep.ldo = hp.two_body[k - 1];
+    if (tc && k > 1) { ep.outb = c->GZb[gzb ^ 1]; ep.ldob = hp.two_body[k - 1]; }
+    else { ep.out = c->GZ[gzb ^ 1]; ep.ldo = hp.two_body[k - 1]; }
     ep.z = c->z2b[k - 1]; ep.ldz = hp.two_body[k - 1];
-    launch_gemm_f32(EPI_DSILU, (int)Ec, hp.two_body[k - 1], hp.two_body[k], c->GZ[gzb],
-                    hp.two_body[k], c->W2bT[k], hp.two_body[k - 1], ep, s);
+    mlp_gemm(c, EPI_DSILU, Ec, hp.two_body[k - 1], hp.two_body[k], c->GZ[gzb], c->GZb[gzb],
+             hp.two_body[k], c->W2bT[k], c->W2b_b[k], ep, s);
     gzb ^= 1;
   }
   const int w0 = hp.two_body[0];
@@ -753,6 +857,10 @@ int evaluate(ff_ctx* c, const double* pos, double* E_sys, float* E_atom, float* 
   if (E_sys) launch_esys(Ea, c->sys_ptr, c->n_sys, E_sys, s);
   if (forces) launch_force_gather(c->n, c->row_ptr, c->rev, c->g, F, s);
   FF_CK(c, cudaGetLastError());
+  if (c->gemm_fail) {
+    c->gemm_fail = false;
+    return set_err(c, FF_ERR_CUDA, "tensor-core GEMM launch could not be set up");
+  }
   c->state_valid = true;
   c->state_chunks = (int)starts.size() - 1;
   c->state_pos = pos;
@@ -770,6 +878,8 @@ int ff_create(ff_ctx** out, const ff_hparams* hp, uint64_t seed) {
   *out = nullptr;
   std::string why;
   if (!validate(*hp, why)) return set_err(nullptr, FF_ERR_ARG, why);
+  if (hp->precision == 1 && !gemm_bf16_available())
+    return set_err(nullptr, FF_ERR_ARG, "BF16 tensor-core path unavailable (no tensor-map encoder)");
   ff_ctx* c = new ff_ctx();
   c->hp = *hp;
   c->seed = seed;
@@ -800,7 +910,7 @@ void ff_destroy(ff_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
   free_workspace(c);
-  dfree(c->wbuf); dfree(c->Z); dfree(c->sys_ptr); dfree(c->sys_of); dfree(c->L_d); dfree(c->Lf_d);
+  dfree(c->wbuf); dfree(c->wbuf_b); dfree(c->Z); dfree(c->sys_ptr); dfree(c->sys_of); dfree(c->L_d); dfree(c->Lf_d);
   dfree(c->vl_j); dfree(c->vl_s); dfree(c->vl_cnt); dfree(c->cell_of); dfree(c->img); dfree(c->xf);
   dfree(c->cell_count); dfree(c->cell_start); dfree(c->cell_fill); dfree(c->cell_atoms);
   dfree(c->xref); dfree(c->cnt); dfree(c->row_ptr); dfree(c->col); dfree(c->shift); dfree(c->src);

@@ -65,16 +65,19 @@ struct EpiParams {
   const float* res; int ldr;     // residual source (ldr == 0: one row broadcast)
   const float* z; int ldz;       // pre-activation source (DSILU)
   int split;
+  __nv_bfloat16* outb; int ldob;  // optional bf16 copy of out (tensor-core GEMM only)
 };
 
 void launch_gemm_f32(int mode, int M, int N, int K, const float* A, int lda, const float* B,
                      int ldb, const EpiParams& ep, cudaStream_t s);
 
-// BF16 tensor-core GEMM (tcgen05): A bf16 [M][K] row-major, Bt bf16 [N][K] row-major.
+// BF16 tensor-core GEMM (tcgen05 + TMA): A bf16 [M][K] row-major, Bt = B^T bf16 [N][K]
+// row-major; N % 16 == 0, K, lda, ldb % 8 == 0, 16-byte aligned bases.  Returns false if
+// the launch could not be set up; a device-side timeout sets bit 64 of *err.
 bool gemm_bf16_available();
-void launch_gemm_bf16(int mode, int M, int N, int K, const __nv_bfloat16* A, int lda,
-                      const __nv_bfloat16* Bt, int ldb, const EpiParams& ep,
-                      __nv_bfloat16* out_bf16, int ldob, cudaStream_t s);
+bool launch_gemm_bf16(int mode, int M, int N, int K, const __nv_bfloat16* A, int lda,
+                      const __nv_bfloat16* Bt, int ldb, const EpiParams& ep, int* err,
+                      cudaStream_t s);
 
 // ----------------------------------------------------------------------------- neighbours
 struct NbrGrid {
@@ -116,7 +119,7 @@ void launch_edge_features(long long E, const int* src, const int* col, const int
                           cudaStream_t s);
 void launch_twobody_in(long long E, int width, int n_basis, const float* ef, const int* zz,
                        const float* W0, float alpha, float* pre, float* out, int ldo,
-                       int final_layer, cudaStream_t s);
+                       __nv_bfloat16* outb, int ldob, int final_layer, cudaStream_t s);
 void launch_env_tp_fwd(int lmax, int in_kind, int last, int C, int n_atoms,
                        const int* row_ptr, int e0, const float* ef, const float* W, int ldw,
                        const float* Vin, const float* theta, float* X, int ldx, int D,
@@ -129,8 +132,10 @@ void launch_env_tp_bwd(int lmax, int in_kind, int last, int C, int n_atoms,
 void launch_energy(int n_atoms, const int* row_ptr, int e0, const float* X, int ldx, int D,
                    const float* w_eff, float* E_atom, cudaStream_t s);
 void launch_rowred_bwd(long long E, int N, const float* gx, int ldgx, const float* z, int ldz,
-                       const float* ef, float alpha, float* gz, int ldgz, float* gf,
-                       cudaStream_t s);
+                       const float* ef, float alpha, float* gz, int ldgz, __nv_bfloat16* gzb,
+                       float* gf, cudaStream_t s);
+void launch_cvt_bf16(const float* src, int lds, __nv_bfloat16* dst, int ldd, long long rows,
+                     int col0, int ncols, cudaStream_t s);
 void launch_edge_grad(long long E, int w0, int n_basis, float rc, int p, int lmax,
                       const float* ef, const float* gz0, int ldg, const float* WB,
                       float alpha0, const float* gf, const float* gY, const int* src,

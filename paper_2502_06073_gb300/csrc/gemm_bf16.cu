@@ -1,8 +1,397 @@
-// BF16 tensor-core GEMM for the per-edge latent MLPs (precision mode 1).  Not built yet:
-// the entry points report the path as unavailable, and ff_create rejects precision 1.
+// BF16 tensor-core GEMM (tcgen05 + TMA) for the per-edge MLPs of precision mode 1:
+// C[M][N] = alpha * A[M][K] * B[K][N] with A (activations, one row per edge) and
+// Bt = B^T [N][K] both bf16 and K-contiguous, FP32 accumulation in tensor memory, and the
+// same fused element-wise epilogues as the FP32 path (SiLU, envelope, residual, SiLU').
+//
+// One CTA (4 warps) owns a 128-row tile and one slice of at most 256 output columns:
+//   warp 0 / lane 0   TMA producer: A and B K-chunks of 64 elements (128 B rows,
+//                     128-byte swizzle) into a ring of `stages` shared-memory stages;
+//   warp 1 / lane 0   MMA issuer: 4 x tcgen05.mma (M=128, N=slice, K=16) per chunk,
+//                     tcgen05.commit releases the stage, a final commit the accumulator;
+//   all 4 warps       epilogue: tcgen05.ld of their 32 TMEM lanes (= tile rows), 32
+//                     columns at a time, fused element-wise op, stores.
+// Every mbarrier wait is bounded; a timeout sets bit 64 of the error word and the CTA
+// drains what it issued, frees its tensor memory and returns.
+#include <cuda.h>   // CUtensorMap (types only; the encoder is fetched at run time)
+
+#include <mutex>
+
 #include "ff_internal.cuh"
 
-bool gemm_bf16_available() { return false; }
+namespace {
 
-void launch_gemm_bf16(int, int, int, int, const __nv_bfloat16*, int, const __nv_bfloat16*, int,
-                      const EpiParams&, __nv_bfloat16*, int, cudaStream_t) {}
+constexpr int TM = 128;
+constexpr int TK = 64;
+constexpr long kWaitLimit = 1L << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the completion of the phase with the given parity.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (long it = 0; it < kWaitLimit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (it > 32) __nanosleep(128);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"((unsigned long long)map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of 128 B,
+// 8-row core groups 1024 B apart; start address encoded in 16-byte units.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;              // leading byte offset (not used by swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
+  d |= (uint64_t)1 << 46;              // descriptor version
+  d |= (uint64_t)2 << 61;              // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major, M x N.
+__device__ __forceinline__ uint32_t instr_desc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ float silu_f(float z) { return z / (1.f + expf(-z)); }
+__device__ __forceinline__ float dsilu_f(float z) {
+  const float sg = 1.f / (1.f + expf(-z));
+  return sg * (1.f + z * (1.f - sg));
+}
+
+// Vectorised epilogue of 8 row-groups: lane l of a warp owns 4 consecutive columns of
+// rows r0 + 4i + (l >> 3), i = 0..7.  All loads of the batch are issued before any store.
+template <int MODE>
+__device__ __forceinline__ void epi_batch(const EpiParams& ep, const float4 (&acc)[8],
+                                          const int (&row)[8], int col, bool colok) {
+  float4 aux[8];
+  float fr[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const bool ok = colok && row[i] >= 0;
+    aux[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    fr[i] = 0.f;
+    if (!ok) continue;
+    const size_t r = (size_t)row[i];
+    if (MODE == EPI_SILU_RES || (MODE == EPI_RES && col < ep.split))
+      aux[i] = *reinterpret_cast<const float4*>(ep.res + r * ep.ldr + col);
+    if (MODE == EPI_DSILU) aux[i] = *reinterpret_cast<const float4*>(ep.z + r * ep.ldz + col);
+    if (MODE == EPI_ACC) aux[i] = *reinterpret_cast<const float4*>(ep.out + r * ep.ldo + col);
+    if (MODE == EPI_SILU_F || MODE == EPI_SILU_RES) fr[i] = ep.f[r * ep.ldf];
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    if (!colok || row[i] < 0) continue;
+    const size_t r = (size_t)row[i];
+    float v[4] = {ep.alpha * acc[i].x, ep.alpha * acc[i].y, ep.alpha * acc[i].z,
+                  ep.alpha * acc[i].w};
+    const float a4[4] = {aux[i].x, aux[i].y, aux[i].z, aux[i].w};
+    float o[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (MODE == EPI_STORE) o[j] = v[j];
+      else if (MODE == EPI_SILU) o[j] = silu_f(v[j]);
+      else if (MODE == EPI_SILU_F) o[j] = fr[i] * silu_f(v[j]);
+      else if (MODE == EPI_SILU_RES) o[j] = ep.beta * (a4[j] + fr[i] * silu_f(v[j]));
+      else if (MODE == EPI_DSILU) o[j] = v[j] * dsilu_f(a4[j]);
+      else if (MODE == EPI_RES) o[j] = v[j] + (col < ep.split ? ep.beta * a4[j] : 0.f);
+      else o[j] = a4[j] + v[j];
+    }
+    if (MODE == EPI_SILU || MODE == EPI_SILU_F || MODE == EPI_SILU_RES)
+      *reinterpret_cast<float4*>(ep.pre + r * ep.ldp + col) = make_float4(v[0], v[1], v[2], v[3]);
+    if (ep.out)
+      *reinterpret_cast<float4*>(ep.out + r * ep.ldo + col) = make_float4(o[0], o[1], o[2], o[3]);
+    if (ep.outb) {
+      __nv_bfloat162 lo = __floats2bfloat162_rn(o[0], o[1]);
+      __nv_bfloat162 hi = __floats2bfloat162_rn(o[2], o[3]);
+      uint2 pk;
+      pk.x = *reinterpret_cast<uint32_t*>(&lo);
+      pk.y = *reinterpret_cast<uint32_t*>(&hi);
+      *reinterpret_cast<uint2*>(ep.outb + r * ep.ldob + col) = pk;
+    }
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256, 2)
+k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M,
+          int N, int K, int n0, int nbw, int stages, EpiParams ep, int* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t a_bytes = TM * TK * 2;
+  const uint32_t b_bytes = (uint32_t)nbw * TK * 2;
+  const uint32_t st_bytes = a_bytes + b_bytes;
+  uint64_t* bars = (uint64_t*)(smem + (size_t)stages * st_bytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + stages;
+  uint64_t* accf = bars + 2 * stages;
+  uint32_t* tslot = (uint32_t*)(accf + 1);
+  __shared__ int s_fail;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * TM;
+  const uint32_t ncols = nbw <= 32 ? 32u : nbw <= 64 ? 64u : nbw <= 128 ? 128u : 256u;
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(accf), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tbase = *tslot;
+  const int nk = (K + TK - 1) / TK;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer
+    int issued = 0;
+    for (int kc = 0; kc < nk; ++kc) {
+      const int s = kc % stages;
+      if (kc >= stages && !mbar_wait(smem_u32(&empty[s]), ((kc / stages) - 1) & 1)) {
+        s_fail = 1;
+        break;
+      }
+      uint8_t* sa = smem + (size_t)s * st_bytes;
+      mbar_expect_tx(smem_u32(&full[s]), st_bytes);
+      tma_load_2d(smem_u32(sa), &tmA, kc * TK, m0, smem_u32(&full[s]));
+      tma_load_2d(smem_u32(sa + a_bytes), &tmB, kc * TK, n0, smem_u32(&full[s]));
+      ++issued;
+    }
+    // drain: the loads this thread issued land before the CTA may exit
+    for (int kc = issued - 1; kc >= 0 && kc >= issued - stages; --kc)
+      mbar_wait(smem_u32(&full[kc % stages]), (kc / stages) & 1);
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    const uint32_t idesc = instr_desc(TM, nbw);
+    for (int kc = 0; kc < nk; ++kc) {
+      const int s = kc % stages;
+      if (!mbar_wait(smem_u32(&full[s]), (kc / stages) & 1)) {
+        s_fail = 1;
+        break;
+      }
+      fence_after();
+      const uint8_t* sa = smem + (size_t)s * st_bytes;
+      const uint64_t da = smem_desc(smem_u32(sa));
+      const uint64_t db = smem_desc(smem_u32(sa + a_bytes));
+#pragma unroll
+      for (int kk = 0; kk < TK / 16; ++kk)
+        mma_bf16(tbase, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
+                 (kc > 0 || kk > 0) ? 1u : 0u);
+      mma_commit(smem_u32(&empty[s]));
+    }
+    mma_commit(smem_u32(accf));   // fires when every MMA issued above has completed
+  }
+  __syncwarp();
+
+  // ---- epilogue: 8 warps; warp w drains TMEM lane quadrant (w & 3) (tile rows
+  // 32(w&3)..+31) for every other 32-column chunk (w >> 2 picks the parity).  Each 32x32
+  // block goes through a shared tile (float4 groups XOR-swizzled by row, conflict-free
+  // both ways; it reuses the pipeline stages, free once the accumulator is complete) and
+  // leaves as float4 row segments, so one warp instruction covers 4 rows x 32 columns.
+  const bool ok = mbar_wait(smem_u32(accf), 0);
+  fence_after();
+  const int quad = warp & 3, half = warp >> 2;
+  float* tile = reinterpret_cast<float*>(smem) + warp * 32 * 32;
+  const int nchunks = (nbw + 31) / 32;
+  for (int ci = half; ci < nchunks; ci += 2) {
+    const int c0 = ci * 32;
+    float v[32];
+    tmem_ld32(tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+    for (int g4 = 0; g4 < 8; ++g4)
+      *reinterpret_cast<float4*>(&tile[lane * 32 + 4 * (g4 ^ (lane & 7))]) =
+          make_float4(v[4 * g4], v[4 * g4 + 1], v[4 * g4 + 2], v[4 * g4 + 3]);
+    __syncwarp();
+    const int gq = lane & 7, rsub = lane >> 3;
+    const int cl = c0 + 4 * gq;
+    const int col = n0 + cl;
+    float4 acc[8];
+    int rows[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int rl = 4 * i + rsub;
+      acc[i] = *reinterpret_cast<const float4*>(&tile[rl * 32 + 4 * (gq ^ (rl & 7))]);
+      const int row = m0 + quad * 32 + rl;
+      rows[i] = (ok && row < M) ? row : -1;
+    }
+    epi_batch<MODE>(ep, acc, rows, col, cl < nbw && col < N);
+    __syncwarp();
+  }
+  if (!ok && threadIdx.x == 0) s_fail = 1;
+  fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && s_fail) atomicOr(err, 64);
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(ncols)
+                 : "memory");
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encoder() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// 2-D bf16 tensor map over rows x cols (row stride ld elements), box 64 x box_rows,
+// 128-byte swizzle, zero fill out of bounds.
+bool make_map(CUtensorMap* m, const void* base, long long rows, int cols, int ld, int box_rows) {
+  EncodeTiledFn enc = encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+             es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+template <int MODE>
+bool launch_mode(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K, int n0,
+                 int nbw, int stages, size_t smem, const EpiParams& ep, int* err,
+                 cudaStream_t s) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(k_gemm_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024) != cudaSuccess)
+      return false;
+    attr_set = true;
+  }
+  k_gemm_tc<MODE><<<ff_cdiv(M, TM), 256, smem, s>>>(ta, tb, M, N, K, n0, nbw, stages, ep, err);
+  return true;
+}
+
+}  // namespace
+
+bool gemm_bf16_available() { return encoder() != nullptr; }
+
+bool launch_gemm_bf16(int mode, int M, int N, int K, const __nv_bfloat16* A, int lda,
+                      const __nv_bfloat16* Bt, int ldb, const EpiParams& ep, int* err,
+                      cudaStream_t s) {
+  ProfScope ps_(PC_GEMM_BF16, s);
+  if (M <= 0) return true;
+  if (N % 16 != 0 || K % 8 != 0 || lda % 8 != 0 || ldb % 8 != 0) return false;
+  for (int n0 = 0; n0 < N; n0 += 256) {
+    const int nbw = N - n0 < 256 ? N - n0 : 256;
+    CUtensorMap ta, tb;
+    if (!make_map(&ta, A, M, K, lda, TM) || !make_map(&tb, Bt, N, K, ldb, nbw)) return false;
+    const int stages = nbw > 128 ? 2 : 3;   // <= 98 KB: two CTAs per SM
+    const size_t smem = (size_t)stages * (TM * TK * 2 + (size_t)nbw * TK * 2) + 1024 + 256;
+    bool ok = false;
+    switch (mode) {
+      case EPI_STORE: ok = launch_mode<EPI_STORE>(ta, tb, M, N, K, n0, nbw, stages, smem, ep, err, s); break;
+      case EPI_SILU: ok = launch_mode<EPI_SILU>(ta, tb, M, N, K, n0, nbw, stages, smem, ep, err, s); break;
+      case EPI_SILU_F: ok = launch_mode<EPI_SILU_F>(ta, tb, M, N, K, n0, nbw, stages, smem, ep, err, s); break;
+      case EPI_SILU_RES: ok = launch_mode<EPI_SILU_RES>(ta, tb, M, N, K, n0, nbw, stages, smem, ep, err, s); break;
+      case EPI_DSILU: ok = launch_mode<EPI_DSILU>(ta, tb, M, N, K, n0, nbw, stages, smem, ep, err, s); break;
+      case EPI_RES: ok = launch_mode<EPI_RES>(ta, tb, M, N, K, n0, nbw, stages, smem, ep, err, s); break;
+      case EPI_ACC: ok = launch_mode<EPI_ACC>(ta, tb, M, N, K, n0, nbw, stages, smem, ep, err, s); break;
+      default: return false;
+    }
+    if (!ok) return false;
+    ff_count_launch(1);
+  }
+  return true;
+}

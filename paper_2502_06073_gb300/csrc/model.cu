@@ -85,7 +85,8 @@ __global__ void k_edge_features(long long E, const int* __restrict__ src,
 __global__ void k_twobody_in(long long E, int width, int n_basis, const float* __restrict__ ef,
                              const int* __restrict__ zz, const float* __restrict__ W0,
                              float alpha, float* __restrict__ pre, float* __restrict__ out,
-                             int ldo, int final_layer) {
+                             int ldo, __nv_bfloat16* __restrict__ outb, int ldob,
+                             int final_layer) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= E * width) return;
   const long long e = t / width;
@@ -97,7 +98,9 @@ __global__ void k_twobody_in(long long E, int width, int n_basis, const float* _
   const float z = alpha * acc;
   pre[e * width + o] = z;
   const float h = silu_f(z);
-  out[e * ldo + o] = final_layer ? ef[e * FF_EF_STRIDE + FF_EF_F] * h : h;
+  const float v = final_layer ? ef[e * FF_EF_STRIDE + FF_EF_F] * h : h;
+  if (out) out[e * ldo + o] = v;
+  if (outb) outb[e * ldob + o] = __float2bfloat16_rn(v);
 }
 
 // E_i = sum over the edges of i of x^N_ij . w_eff (the linear edge-energy MLP folded into
@@ -121,7 +124,7 @@ __global__ void k_energy(int n_atoms, const int* __restrict__ row_ptr, int e0,
 __global__ void k_rowred_bwd(long long E, int N, const float* __restrict__ gx, int ldgx,
                              const float* __restrict__ z, int ldz, const float* __restrict__ ef,
                              float alpha, float* __restrict__ gz, int ldgz,
-                             float* __restrict__ gf) {
+                             __nv_bfloat16* __restrict__ gzb, float* __restrict__ gf) {
   const long long e = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (e >= E) return;
@@ -131,7 +134,9 @@ __global__ void k_rowred_bwd(long long E, int N, const float* __restrict__ gx, i
     const float g = gx[(size_t)e * ldgx + d];
     const float zz = z[(size_t)e * ldz + d];
     const float sg = sigm_f(zz);
-    gz[(size_t)e * ldgz + d] = alpha * f * g * (sg * (1.f + zz * (1.f - sg)));
+    const float o = alpha * f * g * (sg * (1.f + zz * (1.f - sg)));
+    if (gz) gz[(size_t)e * ldgz + d] = o;
+    if (gzb) gzb[(size_t)e * ldgz + d] = __float2bfloat16_rn(o);
     acc += g * zz * sg;
   }
   acc = warp_sum(acc);
@@ -267,6 +272,16 @@ __global__ void k_kinetic(const double* __restrict__ v, const double* __restrict
   if (threadIdx.x == 0) E_kin[sy] = 0.5 * acc / kAcc;
 }
 
+// dst[r][col0 + c] = bf16(src[r][col0 + c]) for c < ncols
+__global__ void k_cvt_bf16(const float* __restrict__ src, int lds, __nv_bfloat16* __restrict__ dst,
+                           int ldd, long long rows, int col0, int ncols) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows * ncols) return;
+  const long long r = t / ncols;
+  const int c = col0 + (int)(t - r * ncols);
+  dst[r * ldd + c] = __float2bfloat16_rn(src[r * lds + c]);
+}
+
 __global__ void k_fill_f32(float* __restrict__ p, long long n, float v) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) p[t] = v;
@@ -293,11 +308,11 @@ void launch_edge_features(long long E, const int* src, const int* col, const int
 
 void launch_twobody_in(long long E, int width, int n_basis, const float* ef, const int* zz,
                        const float* W0, float alpha, float* pre, float* out, int ldo,
-                       int final_layer, cudaStream_t s) {
+                       __nv_bfloat16* outb, int ldob, int final_layer, cudaStream_t s) {
   ProfScope ps_(PC_TWOBODY_IN, s);
   if (E <= 0) return;
   k_twobody_in<<<ff_cdiv(E * width, 256), 256, 0, s>>>(E, width, n_basis, ef, zz, W0, alpha, pre,
-                                                      out, ldo, final_layer);
+                                                      out, ldo, outb, ldob, final_layer);
   ff_count_launch(1);
 }
 
@@ -310,11 +325,12 @@ void launch_energy(int n_atoms, const int* row_ptr, int e0, const float* X, int 
 }
 
 void launch_rowred_bwd(long long E, int N, const float* gx, int ldgx, const float* z, int ldz,
-                       const float* ef, float alpha, float* gz, int ldgz, float* gf,
-                       cudaStream_t s) {
+                       const float* ef, float alpha, float* gz, int ldgz, __nv_bfloat16* gzb,
+                       float* gf, cudaStream_t s) {
   ProfScope ps_(PC_ROWRED, s);
   if (E <= 0) return;
-  k_rowred_bwd<<<ff_cdiv(E, 8), 256, 0, s>>>(E, N, gx, ldgx, z, ldz, ef, alpha, gz, ldgz, gf);
+  k_rowred_bwd<<<ff_cdiv(E, 8), 256, 0, s>>>(E, N, gx, ldgx, z, ldz, ef, alpha, gz, ldgz, gzb,
+                                            gf);
   ff_count_launch(1);
 }
 
@@ -365,6 +381,14 @@ void launch_kinetic(const double* v, const double* mass, const int* sys_ptr, int
   ProfScope ps_(PC_MD, s);
   if (n_sys <= 0) return;
   k_kinetic<<<n_sys, 256, 0, s>>>(v, mass, sys_ptr, E_kin);
+  ff_count_launch(1);
+}
+
+void launch_cvt_bf16(const float* src, int lds, __nv_bfloat16* dst, int ldd, long long rows,
+                     int col0, int ncols, cudaStream_t s) {
+  ProfScope ps_(PC_MISC, s);
+  if (rows <= 0 || ncols <= 0) return;
+  k_cvt_bf16<<<ff_cdiv(rows * ncols, 256), 256, 0, s>>>(src, lds, dst, ldd, rows, col0, ncols);
   ff_count_launch(1);
 }
 

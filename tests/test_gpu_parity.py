@@ -231,3 +231,22 @@ def test_md_matches_oracle_trajectory(ff):
     # FP32 forces (error ~2e-7 eV/A) shift each velocity by ~dt*dF/m ~ 1e-9 A/fs per step
     # against |v| ~ 0.02 A/fs: kinetic energies agree to ~1e-7 after 8 steps
     np.testing.assert_allclose(Ek.cpu().numpy(), ek, rtol=1e-6)
+
+
+@pytest.mark.parametrize("key,wl", [("csh512", "csh512"), ("water4095", "water4095")])
+def test_bf16_tensor_core_path_error(ff, key, wl):
+    """Precision 1 (BF16 tensor-core MLPs, FP32 accumulation, FP32 elsewhere) against the
+    FP64 oracle.  Force bar: RMSE <= 5 meV/A (the stated target) and max <= 5 meV/A.
+    Energy bars from bf16 rounding (2^-8 relative per stored operand): per-atom error
+    <= 4e-3 of max|E_i|, total error <= 4e-3 of sum|E_i|."""
+    make, name, _ = SYSTEMS[key]
+    s = make()
+    hp = _hp(name, wl)
+    m, pos = _bind(ff, hp, s, precision=1)
+    Es, Ea, F = m.energy_forces(pos)
+    E_ref, Ea_ref, F_ref = pool.evaluate(hp, 42, s.pos, s.Z, s.box, s.pbc)
+    d = F.double().cpu().numpy() - F_ref
+    assert np.sqrt((d ** 2).mean()) <= 5e-3 and np.abs(d).max() <= 5e-3
+    Ea = Ea.double().cpu().numpy()
+    assert np.abs(Ea - Ea_ref).max() <= 4e-3 * np.abs(Ea_ref).max()
+    assert abs(Es.item() - E_ref[0]) <= 4e-3 * np.abs(Ea_ref).sum()
