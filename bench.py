@@ -107,7 +107,7 @@ def gemm_bytes_per_edge(hp, precision):
 
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
@@ -129,9 +129,13 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, which):
+        setattr(self, which, time.time())
 
     def stop(self):
+        """Summary of the samples taken between mark('t0') and mark('t1')."""
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -139,11 +143,13 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        t0 = getattr(self, "t0", 0.0)
+        t1 = getattr(self, "t1", float("inf"))
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 7:
+        for ts, ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")][1:]
+            if len(parts) < 7 or not (t0 - 0.25 <= ts <= t1 + 0.25):
                 continue
             try:
                 sm.append(float(parts[0]))
@@ -285,6 +291,10 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
+    # nvidia-smi starts before the warm-up: its start-up stalls the GPU for tens of ms
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(1.0)
     for _ in range(args.warmup):
         model.md(x, v, mass, 1, dt_fs, energies=False)
     torch.cuda.synchronize()
@@ -312,11 +322,11 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
+    clocks.mark("t0")
     l0 = model.launches()
     step_ms, _ = timed_steps(False)
     launches = model.launches() - l0
+    clocks.mark("t1")
     clk = clocks.stop()
     # the same number of steps again with every launch bracketed by events (per-kernel
     # durations for the roofline; kept out of the headline timing)
@@ -431,6 +441,7 @@ def run_ours(args):
             "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof.items()
                                    if v[0]},
             "profiled_ms_per_step": sum(prof_ms) / args.steps,
+            "step_ms": [round(t, 3) for t in step_ms],
             "force_error": ferr,
         }
         print(json.dumps(line), flush=True)

@@ -719,9 +719,8 @@ void forward_chunk(ff_ctx* c, const double* pos, int a0, int a1, float* E_atom, 
     const int last = L == c->NL ? 1 : 0;
     launch_env_tp_fwd(c->lmax, std::min(L - 1, 2), last, c->C, na, rp, e0, c->ef, c->Wv[L],
                       c->ldw, L >= 2 ? c->V[L - 1] : nullptr, last ? nullptr : c->theta[L],
-                      c->X[L - 1], c->ldx, c->D, last ? nullptr : c->V[L], c->Gam[L], inv_sqrt_nu,
-                      s);
-    if (tc) launch_cvt_bf16(c->X[L - 1], c->ldx, c->Xb[L - 1], c->ldx, Ec, c->D, c->ns * c->C, s);
+                      c->X[L - 1], tc ? c->Xb[L - 1] : nullptr, c->ldx, c->D,
+                      last ? nullptr : c->V[L], c->Gam[L], inv_sqrt_nu, s);
     const float* A32 = c->X[L - 1];
     const __nv_bfloat16* Ab = c->Xb[L - 1];
     int fan = c->ldx, lda = c->ldx;
@@ -795,8 +794,8 @@ void backward_chunk(ff_ctx* c, int a0, int a1, const double* seed, cudaStream_t 
     launch_env_tp_bwd(c->lmax, std::min(L - 1, 2), last, c->C, na, rp, e0, c->ef, c->Wv[L],
                       c->ldw, L >= 2 ? c->V[L - 1] : nullptr, last ? nullptr : c->theta[L],
                       c->GX[cur], c->ldx, c->D, last ? nullptr : c->gV[gvb],
-                      L >= 2 ? c->gV[gvb ^ 1] : nullptr, c->GW, c->gY, c->Gam[L], inv_sqrt_nu, s);
-    if (tc) launch_cvt_bf16(c->GW, c->ldw, c->GWb, c->ldw, Ec, 0, c->ldw, s);
+                      L >= 2 ? c->gV[gvb ^ 1] : nullptr, c->GW, tc ? c->GWb : nullptr, c->gY,
+                      c->Gam[L], inv_sqrt_nu, s);
     {
       EpiParams ep{};
       ep.alpha = (float)(1.0 / sqrt((double)c->D));

@@ -120,7 +120,9 @@ __global__ void k_energy(int n_atoms, const int* __restrict__ row_ptr, int e0,
 }
 
 // Adjoint of out = f * silu(z) (scaled by alpha):  gz = alpha f silu'(z) gx,
-// gf += alpha sum_d gx silu(z).  One warp per edge.  ldgx == 0: gx is one broadcast row.
+// gf += alpha sum_d gx silu(z).  One warp per edge; lane l owns the float4 column groups
+// l, l + 32, ... (N % 4 == 0, N <= 512); all loads of the row are issued first.
+// ldgx == 0: gx is one broadcast row.  gz (FP32) and/or gzb (BF16) receive the result.
 __global__ void k_rowred_bwd(long long E, int N, const float* __restrict__ gx, int ldgx,
                              const float* __restrict__ z, int ldz, const float* __restrict__ ef,
                              float alpha, float* __restrict__ gz, int ldgz,
@@ -129,15 +131,40 @@ __global__ void k_rowred_bwd(long long E, int N, const float* __restrict__ gx, i
   const int lane = threadIdx.x & 31;
   if (e >= E) return;
   const float f = ef[e * FF_EF_STRIDE + FF_EF_F];
+  const int ng = N >> 2;
+  float4 g4[4], z4[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int gi = lane + 32 * k;
+    if (gi < ng) {
+      g4[k] = *reinterpret_cast<const float4*>(gx + (size_t)e * ldgx + 4 * gi);
+      z4[k] = *reinterpret_cast<const float4*>(z + (size_t)e * ldz + 4 * gi);
+    }
+  }
   float acc = 0.f;
-  for (int d = lane; d < N; d += 32) {
-    const float g = gx[(size_t)e * ldgx + d];
-    const float zz = z[(size_t)e * ldz + d];
-    const float sg = sigm_f(zz);
-    const float o = alpha * f * g * (sg * (1.f + zz * (1.f - sg)));
-    if (gz) gz[(size_t)e * ldgz + d] = o;
-    if (gzb) gzb[(size_t)e * ldgz + d] = __float2bfloat16_rn(o);
-    acc += g * zz * sg;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int gi = lane + 32 * k;
+    if (gi >= ng) continue;
+    const float gv[4] = {g4[k].x, g4[k].y, g4[k].z, g4[k].w};
+    const float zv[4] = {z4[k].x, z4[k].y, z4[k].z, z4[k].w};
+    float o[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float sg = sigm_f(zv[j]);
+      o[j] = alpha * f * gv[j] * (sg * (1.f + zv[j] * (1.f - sg)));
+      acc += gv[j] * zv[j] * sg;
+    }
+    const size_t oi = (size_t)e * ldgz + 4 * gi;
+    if (gz) *reinterpret_cast<float4*>(gz + oi) = make_float4(o[0], o[1], o[2], o[3]);
+    if (gzb) {
+      __nv_bfloat162 lo = __floats2bfloat162_rn(o[0], o[1]);
+      __nv_bfloat162 hi = __floats2bfloat162_rn(o[2], o[3]);
+      uint2 pk;
+      pk.x = *reinterpret_cast<uint32_t*>(&lo);
+      pk.y = *reinterpret_cast<uint32_t*>(&hi);
+      *reinterpret_cast<uint2*>(gzb + oi) = pk;
+    }
   }
   acc = warp_sum(acc);
   if (lane == 0) gf[e] += alpha * acc;

@@ -30,8 +30,9 @@ template <int LMAX, int INK, int LAST, int C>
 __global__ void __launch_bounds__(128)
 k_env_tp_fwd(int n_atoms, const int* __restrict__ row_ptr, int e0, const float* __restrict__ ef,
              const float* __restrict__ W, int ldw, const float* __restrict__ Vin,
-             const float* __restrict__ theta, float* __restrict__ X, int ldx, int D,
-             float* __restrict__ Vout, float* __restrict__ Gam, float inv_sqrt_nu) {
+             const float* __restrict__ theta, float* __restrict__ X,
+             __nv_bfloat16* __restrict__ Xb, int ldx, int D, float* __restrict__ Vout,
+             float* __restrict__ Gam, float inv_sqrt_nu) {
   using K = TP<LMAX, INK, LAST>;
   constexpr int NY = (LMAX + 1) * (LMAX + 1);
   const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -78,7 +79,11 @@ k_env_tp_fwd(int n_atoms, const int* __restrict__ row_ptr, int e0, const float* 
     float s[K::NS], vo[K::DOUT];
     K::fwd(v, G, th, s, vo);
 #pragma unroll
-    for (int q = 0; q < K::NS; ++q) X[(size_t)e * ldx + D + q * C + c] = s[q];
+    for (int q = 0; q < K::NS; ++q) {
+      const size_t xi = (size_t)e * ldx + D + q * C + c;
+      if (Xb) Xb[xi] = __float2bfloat16_rn(s[q]);
+      else X[xi] = s[q];
+    }
     if (!LAST) {
 #pragma unroll
       for (int k = 0; k < K::DOUT; ++k) Vout[((size_t)e * K::DOUT + k) * C + c] = vo[k];
@@ -92,7 +97,8 @@ k_env_tp_bwd(int n_atoms, const int* __restrict__ row_ptr, int e0, const float* 
              const float* __restrict__ W, int ldw, const float* __restrict__ Vin,
              const float* __restrict__ theta, const float* __restrict__ GX, int ldx, int D,
              const float* __restrict__ gVout, float* __restrict__ gVin, float* __restrict__ GW,
-             float* __restrict__ gY, const float* __restrict__ Gam, float inv_sqrt_nu) {
+             __nv_bfloat16* __restrict__ GWb, float* __restrict__ gY,
+             const float* __restrict__ Gam, float inv_sqrt_nu) {
   using K = TP<LMAX, INK, LAST>;
   constexpr int NY = (LMAX + 1) * (LMAX + 1);
   const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -167,7 +173,9 @@ k_env_tp_bwd(int n_atoms, const int* __restrict__ row_ptr, int e0, const float* 
       float gw = 0.f;
 #pragma unroll
       for (int m = 0; m < 2 * l + 1; ++m) gw += gG[l * l + m] * y[l * l + m];
-      GW[wi] = (INK == 0 ? GW[wi] : 0.f) + gw;
+      const float tot = (INK == 0 ? GW[wi] : 0.f) + gw;
+      if (GWb) GWb[wi] = __float2bfloat16_rn(tot);
+      else GW[wi] = tot;
 #pragma unroll
       for (int m = 0; m < 2 * l + 1; ++m) {
         const float t = team_sum<C>(gG[l * l + m] * wl);
@@ -179,19 +187,19 @@ k_env_tp_bwd(int n_atoms, const int* __restrict__ row_ptr, int e0, const float* 
 
 template <int LMAX, int INK, int LAST, int C>
 void fwd_one(int n_atoms, const int* row_ptr, int e0, const float* ef, const float* W, int ldw,
-             const float* Vin, const float* theta, float* X, int ldx, int D, float* Vout,
-             float* Gam, float inv_sqrt_nu, cudaStream_t s) {
+             const float* Vin, const float* theta, float* X, __nv_bfloat16* Xb, int ldx, int D,
+             float* Vout, float* Gam, float inv_sqrt_nu, cudaStream_t s) {
   k_env_tp_fwd<LMAX, INK, LAST, C><<<ff_cdiv((long long)n_atoms * C, 128), 128, 0, s>>>(
-      n_atoms, row_ptr, e0, ef, W, ldw, Vin, theta, X, ldx, D, Vout, Gam, inv_sqrt_nu);
+      n_atoms, row_ptr, e0, ef, W, ldw, Vin, theta, X, Xb, ldx, D, Vout, Gam, inv_sqrt_nu);
 }
 
 template <int LMAX, int INK, int LAST, int C>
 void bwd_one(int n_atoms, const int* row_ptr, int e0, const float* ef, const float* W, int ldw,
              const float* Vin, const float* theta, const float* GX, int ldx, int D,
-             const float* gVout, float* gVin, float* GW, float* gY, const float* Gam,
-             float inv_sqrt_nu, cudaStream_t s) {
+             const float* gVout, float* gVin, float* GW, __nv_bfloat16* GWb, float* gY,
+             const float* Gam, float inv_sqrt_nu, cudaStream_t s) {
   k_env_tp_bwd<LMAX, INK, LAST, C><<<ff_cdiv((long long)n_atoms * C, 128), 128, 0, s>>>(
-      n_atoms, row_ptr, e0, ef, W, ldw, Vin, theta, GX, ldx, D, gVout, gVin, GW, gY, Gam,
+      n_atoms, row_ptr, e0, ef, W, ldw, Vin, theta, GX, ldx, D, gVout, gVin, GW, GWb, gY, Gam,
       inv_sqrt_nu);
 }
 
@@ -232,11 +240,11 @@ void bwd_one(int n_atoms, const int* row_ptr, int e0, const float* ef, const flo
 
 void launch_env_tp_fwd(int lmax, int in_kind, int last, int C, int n_atoms, const int* row_ptr,
                        int e0, const float* ef, const float* W, int ldw, const float* Vin,
-                       const float* theta, float* X, int ldx, int D, float* Vout, float* Gam,
-                       float inv_sqrt_nu, cudaStream_t s) {
+                       const float* theta, float* X, __nv_bfloat16* Xb, int ldx, int D,
+                       float* Vout, float* Gam, float inv_sqrt_nu, cudaStream_t s) {
   ProfScope ps_(PC_TP_FWD, s);
   if (n_atoms <= 0) return;
-  FF_TP_DISPATCH(fwd_one, n_atoms, row_ptr, e0, ef, W, ldw, Vin, theta, X, ldx, D, Vout, Gam,
+  FF_TP_DISPATCH(fwd_one, n_atoms, row_ptr, e0, ef, W, ldw, Vin, theta, X, Xb, ldx, D, Vout, Gam,
                  inv_sqrt_nu, s);
   ff_count_launch(1);
 }
@@ -244,11 +252,11 @@ void launch_env_tp_fwd(int lmax, int in_kind, int last, int C, int n_atoms, cons
 void launch_env_tp_bwd(int lmax, int in_kind, int last, int C, int n_atoms, const int* row_ptr,
                        int e0, const float* ef, const float* W, int ldw, const float* Vin,
                        const float* theta, const float* GX, int ldx, int D, const float* gVout,
-                       float* gVin, float* GW, float* gY, const float* Gam, float inv_sqrt_nu,
-                       cudaStream_t s) {
+                       float* gVin, float* GW, __nv_bfloat16* GWb, float* gY, const float* Gam,
+                       float inv_sqrt_nu, cudaStream_t s) {
   ProfScope ps_(PC_TP_BWD, s);
   if (n_atoms <= 0) return;
   FF_TP_DISPATCH(bwd_one, n_atoms, row_ptr, e0, ef, W, ldw, Vin, theta, GX, ldx, D, gVout, gVin,
-                 GW, gY, Gam, inv_sqrt_nu, s);
+                 GW, GWb, gY, Gam, inv_sqrt_nu, s);
   ff_count_launch(1);
 }
