@@ -417,8 +417,10 @@ void free_workspace(ff_ctx* c) {
 // Carve every per-chunk buffer from one allocation sized for `ecap` edges / `acap` atoms.
 int ensure_workspace(ff_ctx* c, long long ecap, int acap) {
   if (ecap <= c->wcap && acap <= c->acap) return FF_OK;
-  ecap = std::max(ecap, c->wcap);
-  acap = std::max(acap, c->acap);
+  // grow with headroom: edge counts drift from step to step in MD, and every regrowth is a
+  // free + malloc of the whole workspace
+  ecap = std::max(ecap + ecap / 8 + 4096, c->wcap);
+  acap = std::max(acap + acap / 16 + 64, c->acap);
   free_workspace(c);
   const ff_hparams& hp = c->hp;
   std::vector<std::pair<void**, size_t>> plan;   // (pointer, bytes)

@@ -171,35 +171,41 @@ __global__ void k_rowred_bwd(long long E, int N, const float* __restrict__ gx, i
 }
 
 // dE/dr_e from the radial-basis gradient (via the first two-body layer), the envelope
-// gradient and the spherical-harmonic gradient; one warp per edge.
+// gradient and the spherical-harmonic gradient.  One thread per edge; the radial rows of
+// the first two-body weight matrix sit in shared memory (read as broadcasts).
 __global__ void k_edge_grad(long long E, int w0, int n_basis, float rc, int p, int lmax,
                             const float* __restrict__ ef, const float* __restrict__ gz0, int ldg,
                             const float* __restrict__ WB, float alpha0,
                             const float* __restrict__ gf, const float* __restrict__ gY,
                             const int* __restrict__ src, const int* __restrict__ sys_of,
                             const double* __restrict__ seed, float4* __restrict__ g) {
-  const long long e = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
+  extern __shared__ float s_wb[];
+  for (int i = threadIdx.x; i < n_basis * w0; i += blockDim.x) s_wb[i] = WB[i];
+  __syncthreads();
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
   float gB[10];
 #pragma unroll
   for (int n = 0; n < 10; ++n) gB[n] = 0.f;
-  for (int k = lane; k < w0; k += 32) {
-    const float gzk = gz0[(size_t)e * ldg + k];
+  const float4* row = reinterpret_cast<const float4*>(gz0 + (size_t)e * ldg);
+  for (int k4 = 0; k4 < (w0 >> 2); ++k4) {
+    const float4 v = row[k4];
 #pragma unroll
-    for (int n = 0; n < 10; ++n)
-      if (n < n_basis) gB[n] += gzk * WB[(size_t)n * w0 + k];
+    for (int n = 0; n < 10; ++n) {
+      if (n < n_basis) {
+        const float* wr = s_wb + n * w0 + 4 * k4;
+        gB[n] += v.x * wr[0] + v.y * wr[1] + v.z * wr[2] + v.w * wr[3];
+      }
+    }
   }
-#pragma unroll
-  for (int n = 0; n < 10; ++n) gB[n] = warp_sum(gB[n]);
-  if (lane != 0) return;
   const float* o = ef + e * FF_EF_STRIDE;
   const float ux = o[0], uy = o[1], uz = o[2], r = o[3];
   const float pref = sqrtf(2.f / rc);
   float gr = 0.f;
   for (int n = 1; n <= n_basis; ++n) {
     const float a = n * kPi / rc;
-    const float sn = sinf(a * r), cs = cosf(a * r);
+    float sn, cs;
+    sincosf(a * r, &sn, &cs);
     gr += alpha0 * gB[n - 1] * pref * (a * cs * r - sn) / (r * r);
   }
   gr += gf[e] * envelope_df(r / rc, p, rc);
@@ -367,8 +373,8 @@ void launch_edge_grad(long long E, int w0, int n_basis, float rc, int p, int lma
                       const double* seed, float4* g, cudaStream_t s) {
   ProfScope ps_(PC_EDGE_GRAD, s);
   if (E <= 0) return;
-  k_edge_grad<<<ff_cdiv(E, 8), 256, 0, s>>>(E, w0, n_basis, rc, p, lmax, ef, gz0, ldg, WB, alpha0,
-                                           gf, gY, src, sys_of, seed, g);
+  k_edge_grad<<<ff_cdiv(E, 256), 256, (size_t)n_basis * w0 * sizeof(float), s>>>(
+      E, w0, n_basis, rc, p, lmax, ef, gz0, ldg, WB, alpha0, gf, gY, src, sys_of, seed, g);
   ff_count_launch(1);
 }
 

@@ -19,13 +19,43 @@
 namespace {
 
 template <int C>
+__device__ __forceinline__ unsigned team_mask() {
+  return (C == 32) ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
+}
+
+template <int C>
 __device__ __forceinline__ float team_sum(float v) {
-  const unsigned mask = (C == 32) ? 0xffffffffu : (0xffffu << (threadIdx.x & 16));
+  const unsigned mask = team_mask<C>();
 #pragma unroll
   for (int o = C / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, C);
   return v;
 }
 
+__device__ __forceinline__ void cp_async16(float* smem, const float* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Copy `nfl` floats (a multiple of 4; 16-byte aligned) with the C lanes of a team.
+template <int C>
+__device__ __forceinline__ void stage(float* dst, const float* src, int nfl, int c) {
+  for (int i = 4 * c; i < nfl; i += 4 * C) cp_async16(dst + i, src + i);
+}
+
+// Per-channel path weights of the block in shared memory, transposed to [c][path] so that
+// thread c reads its own weights at stride NP (no bank conflicts for odd NP).
+template <int NP, int C>
+__device__ __forceinline__ void load_theta(float* s_th, const float* __restrict__ theta) {
+  for (int i = threadIdx.x; i < NP * C; i += blockDim.x) s_th[(i % C) * NP + i / C] = theta[i];
+}
+
+// The per-edge rows [dim][C] of V (and of its gradient) are contiguous per edge and
+// consecutive edges of an atom are adjacent, so the team streams them through a
+// shared-memory double buffer with cp.async: edge e+1 is in flight while edge e is used.
 template <int LMAX, int INK, int LAST, int C>
 __global__ void __launch_bounds__(128)
 k_env_tp_fwd(int n_atoms, const int* __restrict__ row_ptr, int e0, const float* __restrict__ ef,
@@ -35,10 +65,19 @@ k_env_tp_fwd(int n_atoms, const int* __restrict__ row_ptr, int e0, const float* 
              float* __restrict__ Gam, float inv_sqrt_nu) {
   using K = TP<LMAX, INK, LAST>;
   constexpr int NY = (LMAX + 1) * (LMAX + 1);
-  const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int a = (int)(gt / C), c = (int)(gt % C);
+  constexpr int TEAMS = 128 / C;
+  constexpr int SIN = INK > 0 ? K::DIN * C : 4;
+  __shared__ __align__(16) float s_th[LAST ? 4 : K::NP * C];
+  __shared__ __align__(16) float s_in[TEAMS * 2 * SIN];
+  if (!LAST) load_theta<K::NP, C>(s_th, theta);
+  __syncthreads();
+  const int team = threadIdx.x / C, c = threadIdx.x % C;
+  const int a = blockIdx.x * TEAMS + team;
   if (a >= n_atoms) return;
   const int eb = row_ptr[a] - e0, ee = row_ptr[a + 1] - e0;
+  float* buf = s_in + team * 2 * SIN;
+  if (INK > 0 && eb < ee) stage<C>(buf, Vin + (size_t)eb * SIN, SIN, c);
+  cp_commit();
 
   float G[NY];
 #pragma unroll
@@ -57,12 +96,14 @@ k_env_tp_fwd(int n_atoms, const int* __restrict__ row_ptr, int e0, const float* 
     G[k] *= inv_sqrt_nu;
     Gam[((size_t)a * NY + k) * C + c] = G[k];
   }
-  float th[K::NP];
-  if (!LAST) {
-#pragma unroll
-    for (int q = 0; q < K::NP; ++q) th[q] = theta[q * C + c];
-  }
+  const float* th = s_th + c * K::NP;
   for (int e = eb; e < ee; ++e) {
+    const int cur = (e - eb) & 1;
+    if (INK > 0 && e + 1 < ee)
+      stage<C>(buf + (cur ^ 1) * SIN, Vin + (size_t)(e + 1) * SIN, SIN, c);
+    cp_commit();
+    cp_wait1();
+    __syncwarp(team_mask<C>());
     float v[K::DIN];
     if (INK == 0) {
       const float* y = ef + (size_t)e * FF_EF_STRIDE + FF_EF_Y;
@@ -74,7 +115,7 @@ k_env_tp_fwd(int n_atoms, const int* __restrict__ row_ptr, int e0, const float* 
       }
     } else {
 #pragma unroll
-      for (int k = 0; k < K::DIN; ++k) v[k] = Vin[((size_t)e * K::DIN + k) * C + c];
+      for (int k = 0; k < K::DIN; ++k) v[k] = buf[cur * SIN + k * C + c];
     }
     float s[K::NS], vo[K::DOUT];
     K::fwd(v, G, th, s, vo);
@@ -88,6 +129,7 @@ k_env_tp_fwd(int n_atoms, const int* __restrict__ row_ptr, int e0, const float* 
 #pragma unroll
       for (int k = 0; k < K::DOUT; ++k) Vout[((size_t)e * K::DOUT + k) * C + c] = vo[k];
     }
+    __syncwarp(team_mask<C>());
   }
 }
 
@@ -101,22 +143,38 @@ k_env_tp_bwd(int n_atoms, const int* __restrict__ row_ptr, int e0, const float* 
              const float* __restrict__ Gam, float inv_sqrt_nu) {
   using K = TP<LMAX, INK, LAST>;
   constexpr int NY = (LMAX + 1) * (LMAX + 1);
-  const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int a = (int)(gt / C), c = (int)(gt % C);
+  constexpr int TEAMS = 128 / C;
+  constexpr int SIN = INK > 0 ? K::DIN * C : 0;
+  constexpr int SOUT = LAST ? 0 : K::DOUT * C;
+  constexpr int SST = (SIN + SOUT) > 0 ? SIN + SOUT : 4;   // floats staged per edge
+  __shared__ __align__(16) float s_th[LAST ? 4 : K::NP * C];
+  __shared__ __align__(16) float s_in[TEAMS * 2 * SST];
+  if (!LAST) load_theta<K::NP, C>(s_th, theta);
+  __syncthreads();
+  const int team = threadIdx.x / C, c = threadIdx.x % C;
+  const int a = blockIdx.x * TEAMS + team;
   if (a >= n_atoms) return;
   const int eb = row_ptr[a] - e0, ee = row_ptr[a + 1] - e0;
+  float* buf = s_in + team * 2 * SST;
+  auto prefetch = [&](int e, int slot) {
+    if (SIN > 0) stage<C>(buf + slot * SST, Vin + (size_t)e * SIN, SIN, c);
+    if (SOUT > 0) stage<C>(buf + slot * SST + SIN, gVout + (size_t)e * SOUT, SOUT, c);
+  };
+  if (eb < ee) prefetch(eb, 0);
+  cp_commit();
   float G[NY], gG[NY];
 #pragma unroll
   for (int k = 0; k < NY; ++k) {
     G[k] = Gam[((size_t)a * NY + k) * C + c];
     gG[k] = 0.f;
   }
-  float th[K::NP];
-  if (!LAST) {
-#pragma unroll
-    for (int q = 0; q < K::NP; ++q) th[q] = theta[q * C + c];
-  }
+  const float* th = s_th + c * K::NP;
   for (int e = eb; e < ee; ++e) {
+    const int cur = (e - eb) & 1;
+    if (e + 1 < ee) prefetch(e + 1, cur ^ 1);
+    cp_commit();
+    cp_wait1();
+    __syncwarp(team_mask<C>());
     const float* y = ef + (size_t)e * FF_EF_STRIDE + FF_EF_Y;
     float v[K::DIN], gv[K::DIN];
     float wl[LMAX + 1];
@@ -129,7 +187,7 @@ k_env_tp_bwd(int n_atoms, const int* __restrict__ row_ptr, int e0, const float* 
         for (int m = 0; m < 2 * l + 1; ++m) v[l * l + m] = wl[l] * y[l * l + m];
     } else {
 #pragma unroll
-      for (int k = 0; k < K::DIN; ++k) v[k] = Vin[((size_t)e * K::DIN + k) * C + c];
+      for (int k = 0; k < K::DIN; ++k) v[k] = buf[cur * SST + k * C + c];
     }
 #pragma unroll
     for (int k = 0; k < K::DIN; ++k) gv[k] = 0.f;
@@ -137,8 +195,7 @@ k_env_tp_bwd(int n_atoms, const int* __restrict__ row_ptr, int e0, const float* 
 #pragma unroll
     for (int q = 0; q < K::NS; ++q) gs[q] = GX[(size_t)e * ldx + D + q * C + c];
 #pragma unroll
-    for (int k = 0; k < K::DOUT; ++k)
-      gvo[k] = LAST ? 0.f : gVout[((size_t)e * K::DOUT + k) * C + c];
+    for (int k = 0; k < K::DOUT; ++k) gvo[k] = LAST ? 0.f : buf[cur * SST + SIN + k * C + c];
     K::bwd(v, G, th, gs, gvo, gv, gG);
     if (INK == 0) {
       // V^0 = w (x) Y: gradient to the env weights and to the harmonics
@@ -160,6 +217,7 @@ k_env_tp_bwd(int n_atoms, const int* __restrict__ row_ptr, int e0, const float* 
 #pragma unroll
       for (int k = 0; k < K::DIN; ++k) gVin[((size_t)e * K::DIN + k) * C + c] = gv[k];
     }
+    __syncwarp(team_mask<C>());
   }
   // adjoint of the environment sum, fanned back out to every edge of the atom
 #pragma unroll
