@@ -48,6 +48,12 @@ WORKLOADS = {
                       nu="csh131072"),
     "cubic96": dict(desc="96 atoms, cubic 10 A, l<=1 model", make=synth.config1_system,
                     model="small", nu="cubic96"),
+    "sio2_4194304": dict(desc="SiO2-like solid, 4,194,304 atoms, 2.2 g/cm3, L = 398.75 A",
+                         make=lambda: synth.sio2_system(162, 4194304, 1004),
+                         model="fm_water", nu="sio2_4194304"),
+    "molecules1024": dict(desc="1,024 organic molecules (7-23 heavy atoms + H), non-periodic",
+                          make=lambda: synth.molecules_system(1024, 1003), model="fm_water",
+                          nu="molecules1024"),
 }
 
 
@@ -195,13 +201,14 @@ def oracle_leg(wl, pos, F_gpu, n_atoms=24, workers=None):
     hp = model_hp(wl)
     workers = workers or os.cpu_count() or 1
     atoms = np.linspace(0, s.n - 1, n_atoms).astype(int).tolist()
-    nl = neighbors.neighbor_list(pos, s.box, s.pbc, hp["rc"], 0.0, centres=atoms)
+    nl = neighbors.neighbor_list(pos, s.box, s.pbc, hp["rc"], 0.0, s.sys_ptr, centres=atoms)
     need = set(atoms)
     for m in atoms:
         need.update(int(j) for j in nl[m][0])
     centres = sorted(need)
     t0 = time.perf_counter()
-    terms = pool.centre_terms(hp, 42, pos, s.Z, s.box, s.pbc, centres, workers=workers)
+    terms = pool.centre_terms(hp, 42, pos, s.Z, s.box, s.pbc, centres, s.sys_ptr,
+                              workers=workers)
     dt = time.perf_counter() - t0
     d = []
     for m in atoms:
@@ -286,7 +293,8 @@ def run_ours(args):
     mass = torch.tensor(s.masses, dtype=torch.float64, device=dev)
     v = torch.tensor(synth.maxwell_boltzmann(s.masses, 300.0, seed=7), dtype=torch.float64,
                      device=dev)
-    model.bind(x, Z, s.box, s.pbc)
+    multi = s.sys_ptr.shape[0] > 2
+    model.bind(x, Z, s.box, s.pbc, s.sys_ptr if multi else None)
     dt_fs = 0.5
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()

@@ -160,6 +160,7 @@ struct ff_ctx {
   long long wcap = 0;
   int acap = 0;
   void* wsp = nullptr;
+  size_t wsp_bytes = 0;
   float* ef = nullptr; int* zz = nullptr;
   float* z2b[4] = {nullptr}; float* h2b[4] = {nullptr};
   float* X[FF_MAX_LAYERS + 1] = {nullptr};
@@ -178,6 +179,7 @@ struct ff_ctx {
   // state of the last evaluation
   bool state_valid = false;
   int state_chunks = 0;
+  std::vector<int> state_starts;   // chunk plan of the last evaluation
   const double* state_pos = nullptr;
   const double* md_force_pos = nullptr;
   long long md_force_gen = -1;
@@ -410,16 +412,17 @@ int upload_weights(ff_ctx* c) {
 void free_workspace(ff_ctx* c) {
   if (c->wsp) cudaFree(c->wsp);
   c->wsp = nullptr;
+  c->wsp_bytes = 0;
   c->wcap = 0;
   c->acap = 0;
 }
 
 // Carve every per-chunk buffer from one allocation sized for `ecap` edges / `acap` atoms.
-int ensure_workspace(ff_ctx* c, long long ecap, int acap) {
+int ensure_workspace(ff_ctx* c, long long ecap, int acap, long long budget_edges) {
   if (ecap <= c->wcap && acap <= c->acap) return FF_OK;
-  // grow with headroom: edge counts drift from step to step in MD, and every regrowth is a
-  // free + malloc of the whole workspace
-  ecap = std::max(ecap + ecap / 8 + 4096, c->wcap);
+  // grow with headroom (edge counts drift from step to step in MD, and every regrowth is
+  // a free + malloc of the whole workspace), but never beyond the chunk budget
+  ecap = std::max(std::min(ecap + ecap / 8 + 4096, std::max(budget_edges, ecap)), c->wcap);
   acap = std::max(acap + acap / 16 + 64, c->acap);
   free_workspace(c);
   const ff_hparams& hp = c->hp;
@@ -477,6 +480,7 @@ int ensure_workspace(ff_ctx* c, long long ecap, int acap) {
                                       " bytes failed: " + cudaGetErrorString(e));
   }
   c->wsp = base;
+  c->wsp_bytes = total;
   size_t off = 0;
   for (auto& p : plan) {
     *p.first = (char*)base + off;
@@ -504,13 +508,19 @@ size_t bytes_per_edge(const ff_ctx* c) {
   return b;
 }
 
+// Edges per chunk: 40 GB (or FF_WORKSPACE_MB) of workspace, at most 60 % of the device
+// memory that is free or already held by this context's workspace.  Independent of the
+// current capacity, so the plan cannot feed back into the allocation.
 long long chunk_edge_budget(const ff_ctx* c) {
   size_t budget = (size_t)40 << 30;
   if (const char* s = getenv("FF_WORKSPACE_MB")) budget = (size_t)atoll(s) << 20;
   size_t fr = 0, tot = 0;
-  if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) budget = std::min(budget, (size_t)(fr * 0.6));
+  if (cudaMemGetInfo(&fr, &tot) == cudaSuccess)
+    budget = std::min(budget, (size_t)((fr + c->wsp_bytes) * 0.6));
+  else
+    cudaGetLastError();
   long long e = (long long)(budget / bytes_per_edge(c));
-  return std::max(std::max(e, c->wcap), 4096LL);
+  return std::max(e, 4096LL);
 }
 
 int read_flags(ff_ctx* c, cudaStream_t s) {
@@ -846,7 +856,7 @@ int evaluate(ff_ctx* c, const double* pos, double* E_sys, float* E_atom, float* 
     maxc = std::max(maxc, (long long)c->row_ptr_h[starts[k + 1]] - c->row_ptr_h[starts[k]]);
     maxa = std::max(maxa, starts[k + 1] - starts[k]);
   }
-  FF_TRY(ensure_workspace(c, std::max(maxc, 1LL), std::max(maxa, 1)));
+  FF_TRY(ensure_workspace(c, std::max(maxc, 1LL), std::max(maxa, 1), budget));
   float* Ea = E_atom ? E_atom : c->E_atom;
   for (size_t k = 0; k + 1 < starts.size(); ++k) {
     forward_chunk(c, pos, starts[k], starts[k + 1], Ea, s);
@@ -864,6 +874,7 @@ int evaluate(ff_ctx* c, const double* pos, double* E_sys, float* E_atom, float* 
   }
   c->state_valid = true;
   c->state_chunks = (int)starts.size() - 1;
+  c->state_starts = starts;
   c->state_pos = pos;
   c->eval_gen++;
   return FF_OK;
@@ -1021,8 +1032,7 @@ int ff_forces(ff_ctx* c, const double* grad_E, float* F, void* stream) {
   if (c->state_chunks == 1) {
     backward_chunk(c, 0, c->n, grad_E, s);
   } else {
-    std::vector<int> starts;
-    plan_chunks(c, c->wcap, starts);
+    const std::vector<int>& starts = c->state_starts;   // the plan the workspace was sized for
     for (size_t k = 0; k + 1 < starts.size(); ++k) {
       forward_chunk(c, c->state_pos, starts[k], starts[k + 1], c->E_atom, s);
       backward_chunk(c, starts[k], starts[k + 1], grad_E, s);

@@ -26,9 +26,10 @@ FM512 = dict(FM64, channels=128, two_body=[128, 256, 512], latent=[512, 512, 512
 PRESETS = {"small": SMALL, "fm_water": FM_WATER, "fm64": FM64, "fm256": FM256,
            "fm512": FM512}
 
-# nu per workload (4/3*pi*rc^3*n rounded, rc = 6 A unless the preset says otherwise)
+# nu per workload: 4/3*pi*rc^3*n rounded for the bulk systems (rc = 6 A unless the preset
+# says otherwise); for the isolated molecules the batch mean of neighbours within 6 A
 NU = {"cubic96": 50.0, "water12288": 91.0, "water4095": 91.0, "csh131072": 82.0,
-      "csh512": 82.0, "sio2_4194304": 60.0, "sio2_4096": 60.0, "molecules1024": 12.0}
+      "csh512": 82.0, "sio2_4194304": 60.0, "sio2_4096": 60.0, "molecules1024": 33.0}
 
 
 def preset(name, **over):
