@@ -295,6 +295,8 @@ def run_ours(args):
                      device=dev)
     multi = s.sys_ptr.shape[0] > 2
     model.bind(x, Z, s.box, s.pbc, s.sys_ptr if multi else None)
+    if args.graph:
+        model.set_graph(True)
     dt_fs = 0.5
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -439,6 +441,8 @@ def run_ours(args):
             "config": {"workload": wl, "desc": WORKLOADS[wl]["desc"],
                        "model": WORKLOADS[wl]["model"], "atoms": s.n, "edges": E_edges,
                        "dt_fs": dt_fs, "parallelism": f"replicas x{world}",
+                       "path": "CUDA graph on the frozen Verlet list" if args.graph
+                               else "per-step filtered list",
                        "l2": "flushed between timed steps (512 MiB write)"},
             "roofline": roof,
             "cpu_baseline": cpu,
@@ -467,6 +471,8 @@ def main():
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1],
                     help="1: BF16 tensor-core MLPs (default); 0: plain FP32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--graph", action="store_true",
+                    help="MD steps replay a captured CUDA graph on the frozen Verlet list")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -133,6 +133,24 @@ int ff_forces(ff_ctx* ctx, const double* grad_E, float* F, void* stream);
 int ff_md_step(ff_ctx* ctx, double* x, double* v, const double* mass, int n_steps,
                double dt_fs, double* E_pot, double* E_kin, void* stream);
 
+/* Energies and (optionally) forces on a frozen edge list, replayed from a CUDA graph
+ * (the batched-evaluation path).  The model list is the whole Verlet list at rc + skin as
+ * built at the reference positions (edges beyond rc contribute exactly zero), so no
+ * neighbour work and no host synchronisation happen per call.  The first call for a set
+ * of (pos, E_sys, E_atom, F) pointers, and the first after a Verlet rebuild, evaluates
+ * once and captures the kernel sequence into a CUDA graph; later calls launch that graph
+ * on an internal stream ordered after and before `stream`.  Arguments as in
+ * ff_energy_forces.  Valid while every atom stays within skin/2 of its position at the
+ * last list build (the caller's responsibility; ff_neighbors rebuilds).  ff_forces does
+ * not apply to this call.  Errors: FF_ERR_STATE, FF_ERR_OOM, FF_ERR_CUDA. */
+int ff_energy_forces_graph(ff_ctx* ctx, const double* pos, double* E_sys, float* E_atom,
+                           float* F, void* stream);
+
+/* enable != 0: ff_md_step uses the frozen-list graph path: per step kick, drift, a
+ * displacement check (one flag read; rebuild + recapture when an atom moved more than
+ * skin/2), graph replay of E+F, kick.  enable == 0 (default): per-step filtered lists. */
+int ff_set_graph(ff_ctx* ctx, int enable);
+
 /* Copy every weight, in tensor order, as the FP64 values drawn at creation (before any
  * rounding to the device precision) into host_buf.  *needed receives the count.
  * Returns FF_ERR_ARG if cap < *needed. */

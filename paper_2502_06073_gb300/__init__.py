@@ -27,7 +27,8 @@ ERRORS = {-1: "FF_ERR_ARG", -2: "FF_ERR_SPECIES", -3: "FF_ERR_OOM", -4: "FF_ERR_
 # Every function the C ABI exports (include/ff.h).
 ABI = ("ff_create", "ff_destroy", "ff_neighbors", "ff_energy_forces", "ff_forces",
        "ff_md_step", "ff_export_params", "ff_get_edges", "ff_kernel_launches", "ff_last_error",
-       "ff_profile_enable", "ff_profile_read", "ff_profile_class", "ff_neighbors_noalloc")
+       "ff_profile_enable", "ff_profile_read", "ff_profile_class", "ff_neighbors_noalloc",
+       "ff_energy_forces_graph", "ff_set_graph")
 
 
 class HParams(ctypes.Structure):
@@ -63,6 +64,8 @@ def load_library(path: str | None = None):
     lib.ff_neighbors.argtypes = [vp, vp, vp, i32, ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_int), vp, i32, vp]
     lib.ff_energy_forces.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.ff_energy_forces_graph.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.ff_set_graph.argtypes = [vp, i32]
     lib.ff_forces.argtypes = [vp, vp, vp, vp]
     lib.ff_md_step.argtypes = [vp, vp, vp, vp, i32, ctypes.c_double, vp, vp, vp]
     lib.ff_export_params.argtypes = [vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
@@ -187,6 +190,21 @@ class FFModel:
                                        _stream(torch))
         self._check(rc)
         return Es, Ea, F
+
+    def energy_forces_graph(self, pos, Es=None, Ea=None, F=None):
+        """E (+F) on the frozen Verlet list through a captured CUDA graph.  Pass the same
+        output tensors on every call to replay the graph (new tensors recapture)."""
+        torch = _torch()
+        dev = pos.device
+        Es = Es if Es is not None else torch.empty(self.n_sys, dtype=torch.float64, device=dev)
+        rc = self.lib.ff_energy_forces_graph(self._h, _ptr(pos), _ptr(Es), _ptr(Ea), _ptr(F),
+                                             _stream(torch))
+        self._check(rc)
+        return Es, Ea, F
+
+    def set_graph(self, enable: bool = True):
+        """Make md() replay a captured CUDA graph on a frozen Verlet list."""
+        self._check(self.lib.ff_set_graph(self._h, 1 if enable else 0))
 
     def forces_adjoint(self, grad_E=None):
         torch = _torch()

@@ -44,6 +44,11 @@ ProfState& prof() {
 ProfScope::ProfScope(int cls_, cudaStream_t s_) : cls(cls_), idx(-1), s(s_) {
   ProfState& p = prof();
   if (!p.on) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return;
+  }
   std::lock_guard<std::mutex> g(p.mu);
   if (p.free_idx.empty()) {
     cudaEvent_t a, b;
@@ -180,6 +185,17 @@ struct ff_ctx {
   bool state_valid = false;
   int state_chunks = 0;
   std::vector<int> state_starts;   // chunk plan of the last evaluation
+  // frozen-list CUDA-graph mode
+  long long list_gen = 0;          // incremented by every Verlet-list build
+  bool list_fixed = false;         // the model list is the whole Verlet list (rc + skin)
+  long long fixed_gen = -1;
+  std::vector<int> fixed_starts;
+  bool graph_md = false;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const void* gkey[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  long long gkey_gen = -1;
   const double* state_pos = nullptr;
   const double* md_force_pos = nullptr;
   long long md_force_gen = -1;
@@ -508,11 +524,11 @@ size_t bytes_per_edge(const ff_ctx* c) {
   return b;
 }
 
-// Edges per chunk: 40 GB (or FF_WORKSPACE_MB) of workspace, at most 60 % of the device
+// Edges per chunk: 120 GB (or FF_WORKSPACE_MB) of workspace, at most 60 % of the device
 // memory that is free or already held by this context's workspace.  Independent of the
 // current capacity, so the plan cannot feed back into the allocation.
 long long chunk_edge_budget(const ff_ctx* c) {
-  size_t budget = (size_t)40 << 30;
+  size_t budget = (size_t)120 << 30;
   if (const char* s = getenv("FF_WORKSPACE_MB")) budget = (size_t)atoll(s) << 20;
   size_t fr = 0, tot = 0;
   if (cudaMemGetInfo(&fr, &tot) == cudaSuccess)
@@ -593,6 +609,7 @@ int build_verlet(ff_ctx* c, const double* pos, cudaStream_t s) {
       FF_CK(c, cudaMemcpyAsync(c->xref, pos, (size_t)c->n * 3 * sizeof(double),
                                cudaMemcpyDeviceToDevice, s));
       c->built = true;
+      c->list_gen++;
       return FF_OK;
     }
     // grow the per-atom capacity to the largest count seen and rebuild
@@ -610,9 +627,9 @@ int build_verlet(ff_ctx* c, const double* pos, cudaStream_t s) {
   return set_err(c, FF_ERR_CAPACITY, "neighbour capacity could not be established");
 }
 
-int filter_edges(ff_ctx* c, const double* pos, cudaStream_t s) {
+int filter_edges(ff_ctx* c, const double* pos, cudaStream_t s, float r2cut) {
   launch_pos_to_f32(pos, c->n, c->xf, s);
-  launch_filter(0, c->n, c->xf, c->Lf_d, c->rc2, c->vmax, c->vl_j, c->vl_s, c->vl_cnt, c->cnt,
+  launch_filter(0, c->n, c->xf, c->Lf_d, r2cut, c->vmax, c->vl_j, c->vl_s, c->vl_cnt, c->cnt,
                 nullptr, nullptr, nullptr, nullptr, s);
   launch_scan_i32(c->cnt, c->row_ptr, c->n, c->scan_tmp, s);
   FF_CK(c, cudaGetLastError());
@@ -630,7 +647,7 @@ int filter_edges(ff_ctx* c, const double* pos, cudaStream_t s) {
     FF_TRY(dalloc(c, &c->g, cap));
     c->ecap = cap;
   }
-  launch_filter(1, c->n, c->xf, c->Lf_d, c->rc2, c->vmax, c->vl_j, c->vl_s, c->vl_cnt, c->cnt,
+  launch_filter(1, c->n, c->xf, c->Lf_d, r2cut, c->vmax, c->vl_j, c->vl_s, c->vl_cnt, c->cnt,
                 c->row_ptr, c->col, c->shift, c->src, s);
   launch_rev_index(c->E, c->row_ptr, c->col, c->shift, c->src, c->rev, c->flags, s);
   FF_CK(c, cudaGetLastError());
@@ -650,7 +667,8 @@ int update_neighbors(ff_ctx* c, const double* pos, cudaStream_t s) {
     }
   }
   if (rebuild) FF_TRY(build_verlet(c, pos, s));
-  return filter_edges(c, pos, s);
+  c->list_fixed = false;
+  return filter_edges(c, pos, s, c->rc2);
 }
 
 // chunks of consecutive centre atoms with at most `cap` edges each
@@ -844,11 +862,9 @@ void backward_chunk(ff_ctx* c, int a0, int a1, const double* seed, cudaStream_t 
                    c->sys_of, seed, c->g + e0, s);
 }
 
-int evaluate(ff_ctx* c, const double* pos, double* E_sys, float* E_atom, float* F,
-             const double* seed, bool forces, cudaStream_t s) {
-  FF_TRY(update_neighbors(c, pos, s));
+// chunk plan for the current model list, workspace sized for it
+int plan_and_reserve(ff_ctx* c, std::vector<int>& starts) {
   const long long budget = chunk_edge_budget(c);
-  std::vector<int> starts;
   plan_chunks(c, budget, starts);
   long long maxc = 0;
   int maxa = 0;
@@ -856,7 +872,13 @@ int evaluate(ff_ctx* c, const double* pos, double* E_sys, float* E_atom, float* 
     maxc = std::max(maxc, (long long)c->row_ptr_h[starts[k + 1]] - c->row_ptr_h[starts[k]]);
     maxa = std::max(maxa, starts[k + 1] - starts[k]);
   }
-  FF_TRY(ensure_workspace(c, std::max(maxc, 1LL), std::max(maxa, 1), budget));
+  return ensure_workspace(c, std::max(maxc, 1LL), std::max(maxa, 1), budget);
+}
+
+// The model on the current list: per-chunk forward (+ adjoint), system energies, force
+// gather.  Enqueues work only (no synchronisation, no allocation), so it can be captured.
+int run_model(ff_ctx* c, const double* pos, double* E_sys, float* E_atom, float* F,
+              const double* seed, bool forces, const std::vector<int>& starts, cudaStream_t s) {
   float* Ea = E_atom ? E_atom : c->E_atom;
   for (size_t k = 0; k + 1 < starts.size(); ++k) {
     forward_chunk(c, pos, starts[k], starts[k + 1], Ea, s);
@@ -872,11 +894,104 @@ int evaluate(ff_ctx* c, const double* pos, double* E_sys, float* E_atom, float* 
     c->gemm_fail = false;
     return set_err(c, FF_ERR_CUDA, "tensor-core GEMM launch could not be set up");
   }
+  return FF_OK;
+}
+
+int evaluate(ff_ctx* c, const double* pos, double* E_sys, float* E_atom, float* F,
+             const double* seed, bool forces, cudaStream_t s) {
+  FF_TRY(update_neighbors(c, pos, s));
+  std::vector<int> starts;
+  FF_TRY(plan_and_reserve(c, starts));
+  FF_TRY(run_model(c, pos, E_sys, E_atom, F, seed, forces, starts, s));
   c->state_valid = true;
   c->state_chunks = (int)starts.size() - 1;
   c->state_starts = starts;
   c->state_pos = pos;
   c->eval_gen++;
+  return FF_OK;
+}
+
+void graph_reset(ff_ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
+  c->gkey_gen = -1;
+}
+
+// The whole Verlet list (rc + skin, as built at the reference positions) becomes the model
+// list: edges beyond rc contribute exactly zero (the envelope and its derivative vanish),
+// so it stays valid while every atom is within skin/2 of its reference position.
+int prepare_fixed(ff_ctx* c, cudaStream_t s) {
+  if (!c->built) FF_TRY(build_verlet(c, c->xref, s));
+  FF_TRY(filter_edges(c, c->xref, s, c->rl2));
+  FF_TRY(plan_and_reserve(c, c->fixed_starts));
+  c->list_fixed = true;
+  c->fixed_gen = c->list_gen;
+  graph_reset(c);
+  return FF_OK;
+}
+
+// E (+ F) on the frozen list through a CUDA graph: captured at the first call for a set of
+// pointers and list generation, replayed afterwards on an internal stream ordered after
+// (and before) the caller's stream.
+int graph_eval(ff_ctx* c, const double* pos, double* E_sys, float* E_atom, float* F,
+               cudaStream_t s) {
+  if (!c->list_fixed || c->fixed_gen != c->list_gen) FF_TRY(prepare_fixed(c, s));
+  if (!c->gstream) {
+    FF_CK(c, cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+    FF_CK(c, cudaEventCreateWithFlags(&c->ev_a, cudaEventDisableTiming));
+    FF_CK(c, cudaEventCreateWithFlags(&c->ev_b, cudaEventDisableTiming));
+  }
+  const bool forces = F != nullptr;
+  const void* key[5] = {pos, E_sys, E_atom, F, (const void*)(uintptr_t)forces};
+  bool same = c->gexec && c->gkey_gen == c->fixed_gen;
+  for (int k = 0; k < 5 && same; ++k) same = key[k] == c->gkey[k];
+  FF_CK(c, cudaEventRecord(c->ev_a, s));
+  FF_CK(c, cudaStreamWaitEvent(c->gstream, c->ev_a, 0));
+  if (same) {
+    FF_CK(c, cudaGraphLaunch(c->gexec, c->gstream));
+  } else {
+    graph_reset(c);
+    // this call's result comes from a plain run; the capture that follows records the
+    // same kernel sequence for the next calls (the capture does not execute anything)
+    FF_TRY(run_model(c, pos, E_sys, E_atom, F, nullptr, forces, c->fixed_starts, c->gstream));
+    cudaGraph_t g = nullptr;
+    FF_CK(c, cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
+    const int r = run_model(c, pos, E_sys, E_atom, F, nullptr, forces, c->fixed_starts,
+                            c->gstream);
+    const cudaError_t ec = cudaStreamEndCapture(c->gstream, &g);
+    if (r != FF_OK) {
+      if (g) cudaGraphDestroy(g);
+      return r;
+    }
+    if (ec != cudaSuccess || !g)
+      return set_err(c, FF_ERR_CUDA, std::string("graph capture failed: ") + cudaGetErrorString(ec));
+    const cudaError_t ei = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      c->gexec = nullptr;
+      return set_err(c, FF_ERR_CUDA, std::string("graph instantiation failed: ") +
+                                         cudaGetErrorString(ei));
+    }
+    for (int k = 0; k < 5; ++k) c->gkey[k] = key[k];
+    c->gkey_gen = c->fixed_gen;
+  }
+  FF_CK(c, cudaEventRecord(c->ev_b, c->gstream));
+  FF_CK(c, cudaStreamWaitEvent(s, c->ev_b, 0));
+  c->state_valid = false;       // the adjoint entry point needs a plain evaluation
+  c->eval_gen++;
+  return FF_OK;
+}
+
+// Rebuild the Verlet list when an atom moved more than skin/2 from its reference.
+int check_rebuild(ff_ctx* c, const double* x, cudaStream_t s) {
+  const double lim = 0.5 * (double)c->hp.skin;
+  launch_disp_check(x, c->xref, c->n, lim * lim, c->flags + 1, s);
+  FF_CK(c, cudaMemcpyAsync(c->flags_h + 1, c->flags + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FF_CK(c, cudaStreamSynchronize(s));
+  if (c->flags_h[1] || !c->built) {
+    FF_CK(c, cudaMemsetAsync(c->flags + 1, 0, sizeof(int), s));
+    FF_TRY(build_verlet(c, x, s));
+  }
   return FF_OK;
 }
 
@@ -921,6 +1036,10 @@ int ff_create(ff_ctx** out, const ff_hparams* hp, uint64_t seed) {
 void ff_destroy(ff_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
+  graph_reset(c);
+  if (c->gstream) cudaStreamDestroy(c->gstream);
+  if (c->ev_a) cudaEventDestroy(c->ev_a);
+  if (c->ev_b) cudaEventDestroy(c->ev_b);
   free_workspace(c);
   dfree(c->wbuf); dfree(c->wbuf_b); dfree(c->Z); dfree(c->sys_ptr); dfree(c->sys_of); dfree(c->L_d); dfree(c->Lf_d);
   dfree(c->vl_j); dfree(c->vl_s); dfree(c->vl_cnt); dfree(c->cell_of); dfree(c->img); dfree(c->xf);
@@ -1011,7 +1130,8 @@ int ff_neighbors(ff_ctx* c, const double* pos, const int32_t* Z, int n_atoms, co
   c->state_valid = false;
   c->md_force_pos = nullptr;
   FF_TRY(build_verlet(c, pos, s));
-  return filter_edges(c, pos, s);
+  c->list_fixed = false;
+  return filter_edges(c, pos, s, c->rc2);
 }
 
 int ff_energy_forces(ff_ctx* c, const double* pos, double* E_sys, float* E_atom, float* F,
@@ -1049,6 +1169,29 @@ int ff_md_step(ff_ctx* c, double* x, double* v, const double* mass, int n_steps,
   if (!c->bound) return set_err(c, FF_ERR_STATE, "ff_neighbors must be called first");
   if (!x || !v || !mass || n_steps < 0) return set_err(c, FF_ERR_ARG, "bad md arguments");
   cudaStream_t s = (cudaStream_t)stream;
+  if (c->graph_md) {
+    // frozen Verlet list + graph replay; the list is rebuilt (and the graph recaptured)
+    // when an atom has moved more than skin/2
+    if (!(c->md_force_pos == x && c->md_force_gen == c->eval_gen)) {
+      FF_TRY(check_rebuild(c, x, s));
+      FF_TRY(graph_eval(c, x, nullptr, nullptr, c->F_int, s));
+    }
+    for (int it = 0; it < n_steps; ++it) {
+      launch_kick(c->n, v, c->F_int, mass, 0.5 * dt_fs, s);
+      launch_drift(c->n, x, v, dt_fs, s);
+      FF_TRY(check_rebuild(c, x, s));
+      FF_TRY(graph_eval(c, x, E_pot ? c->esys_tmp : nullptr, nullptr, c->F_int, s));
+      if (E_pot)
+        FF_CK(c, cudaMemcpyAsync(E_pot + (size_t)it * c->n_sys, c->esys_tmp,
+                                 (size_t)c->n_sys * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      launch_kick(c->n, v, c->F_int, mass, 0.5 * dt_fs, s);
+      if (E_kin) launch_kinetic(v, mass, c->sys_ptr, c->n_sys, E_kin + (size_t)it * c->n_sys, s);
+    }
+    FF_CK(c, cudaGetLastError());
+    c->md_force_pos = x;
+    c->md_force_gen = c->eval_gen;
+    return FF_OK;
+  }
   if (!(c->md_force_pos == x && c->md_force_gen == c->eval_gen))
     FF_TRY(evaluate(c, x, nullptr, nullptr, c->F_int, nullptr, true, s));
   for (int it = 0; it < n_steps; ++it) {
@@ -1062,6 +1205,22 @@ int ff_md_step(ff_ctx* c, double* x, double* v, const double* mass, int n_steps,
   FF_CK(c, cudaGetLastError());
   c->md_force_pos = x;
   c->md_force_gen = c->eval_gen;
+  return FF_OK;
+}
+
+int ff_energy_forces_graph(ff_ctx* c, const double* pos, double* E_sys, float* E_atom,
+                           float* F, void* stream) {
+  if (!c) return FF_ERR_ARG;
+  if (!c->bound) return set_err(c, FF_ERR_STATE, "ff_neighbors must be called first");
+  if (!pos) return set_err(c, FF_ERR_ARG, "pos is null");
+  c->md_force_pos = nullptr;
+  return graph_eval(c, pos, E_sys, E_atom, F, (cudaStream_t)stream);
+}
+
+int ff_set_graph(ff_ctx* c, int enable) {
+  if (!c) return FF_ERR_ARG;
+  c->graph_md = enable != 0;
+  c->md_force_pos = nullptr;
   return FF_OK;
 }
 

@@ -293,3 +293,56 @@ def test_autograd_adjoint_with_several_chunks(ff):
     finally:
         del os.environ["FF_WORKSPACE_MB"]
     assert torch.equal(x.grad, (-F).double())
+
+
+@pytest.mark.parametrize("key,wl,prec", [("molecules64", "molecules1024", 1),
+                                         ("csh512", "csh512", 0)])
+def test_graph_path_matches_plain_path_and_replays(ff, key, wl, prec):
+    """The frozen-list CUDA-graph path (Verlet list at rc + skin, edges beyond rc add
+    exactly zero) against the plain path, then a replay after moving every atom in place
+    by up to 0.1 A (< skin/2) against a fresh plain evaluation at the new positions."""
+    make, name, _ = SYSTEMS[key]
+    s = make()
+    hp = _hp(name, wl)
+    m, pos = _bind(ff, hp, s, precision=prec)
+    Es = torch.empty(m.n_sys, dtype=torch.float64, device="cuda")
+    Ea = torch.empty(s.n, dtype=torch.float32, device="cuda")
+    F = torch.empty(s.n, 3, dtype=torch.float32, device="cuda")
+    ftol = F_ABS if prec == 0 else 2e-4
+
+    def check(positions):
+        ref = ff.FFModel(hp, seed=42, precision=prec)
+        ref.bind(positions, _dev(s.Z, torch.int32), s.box, s.pbc,
+                 s.sys_ptr if s.sys_ptr.shape[0] > 2 else None)
+        Er, Ear, Fr = ref.energy_forces(positions)
+        scale = Ear.abs().max().item()
+        assert (Ea - Ear).abs().max().item() <= 1e-5 * scale
+        assert (Es - Er).abs().max().item() <= 1e-5 * Ear.abs().sum().item()
+        assert (F - Fr).abs().max().item() <= ftol
+
+    m.energy_forces_graph(pos, Es, Ea, F)          # evaluates and captures
+    torch.cuda.synchronize()
+    check(pos.clone())
+    delta = torch.tensor(np.random.default_rng(4).uniform(-0.057, 0.057, size=(s.n, 3)),
+                         dtype=torch.float64, device="cuda")
+    pos.add_(delta)
+    m.energy_forces_graph(pos, Es, Ea, F)          # replays the graph
+    torch.cuda.synchronize()
+    check(pos.clone())
+
+
+def test_graph_md_matches_oracle_trajectory(ff):
+    s = synth.config1_system()
+    hp = synth.preset("small", skin=0.3)
+    m, pos = _bind(ff, hp, s)
+    m.set_graph(True)
+    v0 = synth.maxwell_boltzmann(s.masses, 3000.0, seed=5)     # hot: forces list rebuilds
+    x = pos.clone()
+    v = _dev(v0, torch.float64)
+    mass = _dev(s.masses, torch.float64)
+    Ep, Ek = m.md(x, v, mass, 12, 1.0)
+    xr, vr, ep, ek = omd.run_nve(Allegro64(hp, 42), s.pos, v0, s.Z, s.box, s.pbc, s.masses,
+                                 1.0, 12)
+    assert np.abs(x.cpu().numpy() - xr).max() < 1e-7
+    assert np.abs(v.cpu().numpy() - vr).max() < 1e-8
+    np.testing.assert_allclose(Ep.cpu().numpy(), ep, rtol=E_REL)
