@@ -146,6 +146,15 @@ int ff_md_step(ff_ctx* ctx, double* x, double* v, const double* mass, int n_step
 int ff_energy_forces_graph(ff_ctx* ctx, const double* pos, double* E_sys, float* E_atom,
                            float* F, void* stream);
 
+/* Autotuner of the tensor-core MLP GEMMs (precision 1): times complete E+F evaluations of
+ * the bound system at `pos` (device) for each edge-tile configuration -- output-column
+ * slice of 128 or 256 per CTA and 2, 3 or 4 shared-memory pipeline stages (which sets how
+ * many CTAs share an SM) -- keeps the fastest for this context and reports it
+ * (*slice, *stages; *ms_best = its mean evaluation time; any may be NULL).  For
+ * precision 0 nothing is timed.  Synchronises `stream`.  Errors: as ff_energy_forces. */
+int ff_autotune(ff_ctx* ctx, const double* pos, int* slice, int* stages, double* ms_best,
+                void* stream);
+
 /* enable != 0: ff_md_step uses the frozen-list graph path: per step kick, drift, a
  * displacement check (one flag read; rebuild + recapture when an atom moved more than
  * skin/2), graph replay of E+F, kick.  enable == 0 (default): per-step filtered lists. */

@@ -28,7 +28,7 @@ ERRORS = {-1: "FF_ERR_ARG", -2: "FF_ERR_SPECIES", -3: "FF_ERR_OOM", -4: "FF_ERR_
 ABI = ("ff_create", "ff_destroy", "ff_neighbors", "ff_energy_forces", "ff_forces",
        "ff_md_step", "ff_export_params", "ff_get_edges", "ff_kernel_launches", "ff_last_error",
        "ff_profile_enable", "ff_profile_read", "ff_profile_class", "ff_neighbors_noalloc",
-       "ff_energy_forces_graph", "ff_set_graph")
+       "ff_energy_forces_graph", "ff_set_graph", "ff_autotune")
 
 
 class HParams(ctypes.Structure):
@@ -66,6 +66,8 @@ def load_library(path: str | None = None):
     lib.ff_energy_forces.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.ff_energy_forces_graph.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.ff_set_graph.argtypes = [vp, i32]
+    lib.ff_autotune.argtypes = [vp, vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                ctypes.POINTER(ctypes.c_double), vp]
     lib.ff_forces.argtypes = [vp, vp, vp, vp]
     lib.ff_md_step.argtypes = [vp, vp, vp, vp, i32, ctypes.c_double, vp, vp, vp]
     lib.ff_export_params.argtypes = [vp, vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
@@ -201,6 +203,14 @@ class FFModel:
                                              _stream(torch))
         self._check(rc)
         return Es, Ea, F
+
+    def autotune(self, pos) -> dict:
+        """Pick the fastest tensor-core GEMM tile configuration for the bound system."""
+        torch = _torch()
+        sl, st, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        self._check(self.lib.ff_autotune(self._h, _ptr(pos), ctypes.byref(sl), ctypes.byref(st),
+                                         ctypes.byref(ms), _stream(torch)))
+        return {"slice": sl.value, "stages": st.value, "ms_per_evaluation": ms.value}
 
     def set_graph(self, enable: bool = True):
         """Make md() replay a captured CUDA graph on a frozen Verlet list."""

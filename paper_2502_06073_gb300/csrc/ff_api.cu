@@ -196,6 +196,8 @@ struct ff_ctx {
   cudaGraphExec_t gexec = nullptr;
   const void* gkey[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   long long gkey_gen = -1;
+  // tensor-core GEMM tile configuration (set by ff_autotune)
+  int tune_slice = 256, tune_stages = 0;
   const double* state_pos = nullptr;
   const double* md_force_pos = nullptr;
   long long md_force_gen = -1;
@@ -697,7 +699,8 @@ void mlp_gemm(ff_ctx* c, int mode, long long M, int N, int K, const float* A32,
               const EpiParams& ep, cudaStream_t s) {
   if (c->hp.precision == 0) {
     launch_gemm_f32(mode, (int)M, N, K, A32, lda, W32, N, ep, s);
-  } else if (!launch_gemm_bf16(mode, (int)M, N, K, Ab, lda, Wt_b, K, ep, c->flags, s)) {
+  } else if (!launch_gemm_bf16(mode, (int)M, N, K, Ab, lda, Wt_b, K, ep, c->flags, s,
+                               c->tune_slice, c->tune_stages)) {
     c->gemm_fail = true;
   }
 }
@@ -1215,6 +1218,53 @@ int ff_energy_forces_graph(ff_ctx* c, const double* pos, double* E_sys, float* E
   if (!pos) return set_err(c, FF_ERR_ARG, "pos is null");
   c->md_force_pos = nullptr;
   return graph_eval(c, pos, E_sys, E_atom, F, (cudaStream_t)stream);
+}
+
+int ff_autotune(ff_ctx* c, const double* pos, int* slice, int* stages, double* ms_best,
+                void* stream) {
+  if (!c) return FF_ERR_ARG;
+  if (!c->bound) return set_err(c, FF_ERR_STATE, "ff_neighbors must be called first");
+  if (!pos) return set_err(c, FF_ERR_ARG, "pos is null");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (c->hp.precision == 1) {
+    static const int cand[][2] = {{256, 2}, {256, 3}, {256, 4}, {128, 2}, {128, 3}, {128, 4}};
+    cudaEvent_t e0, e1;
+    FF_CK(c, cudaEventCreate(&e0));
+    FF_CK(c, cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bi = 0;
+    for (int k = 0; k < 6; ++k) {
+      c->tune_slice = cand[k][0];
+      c->tune_stages = cand[k][1];
+      FF_TRY(evaluate(c, pos, nullptr, nullptr, c->F_int, nullptr, true, s));   // warm-up
+      float tot = 0.f;
+      for (int r = 0; r < 3; ++r) {
+        // neighbour work and host synchronisation stay outside the timed region
+        FF_TRY(update_neighbors(c, pos, s));
+        std::vector<int> starts;
+        FF_TRY(plan_and_reserve(c, starts));
+        FF_CK(c, cudaEventRecord(e0, s));
+        FF_TRY(run_model(c, pos, nullptr, nullptr, c->F_int, nullptr, true, starts, s));
+        FF_CK(c, cudaEventRecord(e1, s));
+        FF_CK(c, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        FF_CK(c, cudaEventElapsedTime(&ms, e0, e1));
+        tot += ms;
+      }
+      if (tot < best) { best = tot; bi = k; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->tune_slice = cand[bi][0];
+    c->tune_stages = cand[bi][1];
+    if (ms_best) *ms_best = best / 3.0;
+    graph_reset(c);
+  }
+  if (slice) *slice = c->tune_slice;
+  if (stages) *stages = c->tune_stages;
+  c->state_valid = false;
+  c->md_force_pos = nullptr;
+  return FF_OK;
 }
 
 int ff_set_graph(ff_ctx* c, int enable) {

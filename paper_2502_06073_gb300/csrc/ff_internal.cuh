@@ -75,9 +75,11 @@ void launch_gemm_f32(int mode, int M, int N, int K, const float* A, int lda, con
 // row-major; N % 16 == 0, K, lda, ldb % 8 == 0, 16-byte aligned bases.  Returns false if
 // the launch could not be set up; a device-side timeout sets bit 64 of *err.
 bool gemm_bf16_available();
+// slice: output columns per CTA (128 or 256); stages_req: 2..4 pipeline stages, or 0
+// for the default (2 for 256-wide slices, 3 otherwise).
 bool launch_gemm_bf16(int mode, int M, int N, int K, const __nv_bfloat16* A, int lda,
                       const __nv_bfloat16* Bt, int ldb, const EpiParams& ep, int* err,
-                      cudaStream_t s);
+                      cudaStream_t s, int slice = 256, int stages_req = 0);
 
 // ----------------------------------------------------------------------------- neighbours
 struct NbrGrid {

@@ -369,15 +369,17 @@ bool gemm_bf16_available() { return encoder() != nullptr; }
 
 bool launch_gemm_bf16(int mode, int M, int N, int K, const __nv_bfloat16* A, int lda,
                       const __nv_bfloat16* Bt, int ldb, const EpiParams& ep, int* err,
-                      cudaStream_t s) {
+                      cudaStream_t s, int slice, int stages_req) {
   ProfScope ps_(PC_GEMM_BF16, s);
   if (M <= 0) return true;
   if (N % 16 != 0 || K % 8 != 0 || lda % 8 != 0 || ldb % 8 != 0) return false;
-  for (int n0 = 0; n0 < N; n0 += 256) {
-    const int nbw = N - n0 < 256 ? N - n0 : 256;
+  if (slice != 128 && slice != 256) slice = 256;
+  for (int n0 = 0; n0 < N; n0 += slice) {
+    const int nbw = N - n0 < slice ? N - n0 : slice;
     CUtensorMap ta, tb;
     if (!make_map(&ta, A, M, K, lda, TM) || !make_map(&tb, Bt, N, K, ldb, nbw)) return false;
-    const int stages = nbw > 128 ? 2 : 3;   // <= 98 KB: two CTAs per SM
+    // default: <= 98 KB of stages, two CTAs per SM; the autotuner may ask for 2..4
+    const int stages = (stages_req >= 2 && stages_req <= 4) ? stages_req : (nbw > 128 ? 2 : 3);
     const size_t smem = (size_t)stages * (TM * TK * 2 + (size_t)nbw * TK * 2) + 1024 + 256;
     bool ok = false;
     switch (mode) {

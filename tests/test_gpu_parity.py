@@ -346,3 +346,17 @@ def test_graph_md_matches_oracle_trajectory(ff):
     assert np.abs(x.cpu().numpy() - xr).max() < 1e-7
     assert np.abs(v.cpu().numpy() - vr).max() < 1e-8
     np.testing.assert_allclose(Ep.cpu().numpy(), ep, rtol=E_REL)
+
+
+def test_autotune_picks_a_valid_tile_and_keeps_results(ff):
+    make, name, _ = SYSTEMS["csh512"]
+    s = make()
+    hp = _hp(name, "csh512")
+    m, pos = _bind(ff, hp, s, precision=1)
+    _, Ea0, F0 = m.energy_forces(pos)
+    cfg = m.autotune(pos)
+    assert cfg["slice"] in (128, 256) and cfg["stages"] in (2, 3, 4)
+    assert cfg["ms_per_evaluation"] > 0
+    _, Ea1, F1 = m.energy_forces(pos)
+    # the tile shape changes no arithmetic: the K loop and the accumulation are the same
+    assert torch.equal(Ea0, Ea1) and torch.equal(F0, F1)
