@@ -52,7 +52,7 @@ enum {
  *   rc                radial cutoff (A); skin: Verlet-list skin (A, >= 0)
  *   n_basis, poly_p   Bessel radial functions and cutoff-polynomial order
  *   lmax              1 or 2; parity must be 1 (full O(3))
- *   n_layers          1..4 interaction layers; channels: tensor features, multiple of 16
+ *   n_layers          1..4 interaction layers; channels: tensor features, 16/32/64/128
  *   two_body[]        widths of the two-body latent MLP (last = latent width D)
  *   latent[]          widths of the per-layer latent MLP (last must equal D)
  *   edge_eng[]        hidden widths of the linear edge-energy MLP (output width 1 implied)

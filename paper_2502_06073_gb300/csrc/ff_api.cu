@@ -114,6 +114,7 @@ struct ff_ctx {
   // structure
   int D = 0, C = 0, lmax = 0, NL = 0, n2b = 0, nlat = 0, ns = 0, ldx = 0, ldw = 0, maxw = 0;
   int maxdim = 1;
+  int cgroups = 1;     // channel groups of 32 in the tensor-product kernels (C > 32)
   int layer_np[FF_MAX_LAYERS + 1] = {0}, layer_dout[FF_MAX_LAYERS + 1] = {0};
   int layer_din[FF_MAX_LAYERS + 1] = {0};
   std::vector<Tensor> tensors;
@@ -253,7 +254,9 @@ int validate(const ff_hparams& hp, std::string& why) {
   if (hp.lmax < 1 || hp.lmax > 2) { why = "lmax must be 1 or 2"; return 0; }
   if (hp.parity != 1) { why = "only parity = 1 (full O(3)) is supported"; return 0; }
   if (hp.n_layers < 1 || hp.n_layers > FF_MAX_LAYERS) { why = "n_layers must be in 1..4"; return 0; }
-  if (hp.channels != 16 && hp.channels != 32) { why = "channels must be 16 or 32"; return 0; }
+  if (hp.channels != 16 && hp.channels != 32 && hp.channels != 64 && hp.channels != 128) {
+    why = "channels must be 16, 32, 64 or 128"; return 0;
+  }
   if (hp.n_two_body < 1 || hp.n_two_body > 4) { why = "n_two_body must be in 1..4"; return 0; }
   if (hp.n_latent < 1 || hp.n_latent > 4) { why = "n_latent must be in 1..4"; return 0; }
   if (hp.n_edge_eng < 0 || hp.n_edge_eng > 2) { why = "n_edge_eng must be in 0..2"; return 0; }
@@ -282,6 +285,7 @@ void build_structure(ff_ctx* c) {
   c->ns = hp.lmax + 1;
   c->ldx = c->D + c->ns * c->C;
   c->ldw = (hp.lmax + 1) * c->C;
+  c->cgroups = c->C > 32 ? c->C / 32 : 1;
   c->maxw = c->ldx;
   for (int k = 0; k < hp.n_two_body; ++k) c->maxw = std::max(c->maxw, hp.two_body[k]);
   for (int k = 0; k < hp.n_latent; ++k) c->maxw = std::max(c->maxw, hp.latent[k]);
@@ -359,7 +363,8 @@ int upload_weights(ff_ctx* c) {
     const Tensor* t = find_tensor(c, "Wenv." + std::to_string(L));
     put(&c->Wenv[L], t, false);
     put(&c->WenvT[L], t, true);
-    if (L < c->NL) put(&c->theta[L], find_tensor(c, "theta." + std::to_string(L)), false);
+    // path weights transposed to [channel][path]: each thread reads its own row
+    if (L < c->NL) put(&c->theta[L], find_tensor(c, "theta." + std::to_string(L)), true);
     for (int k = 0; k < c->nlat; ++k) {
       const Tensor* tl = find_tensor(c, "Wlat." + std::to_string(L) + "." + std::to_string(k));
       put(&c->Wlat[L][k], tl, false);
@@ -481,7 +486,7 @@ int ensure_workspace(ff_ctx* c, long long ecap, int acap, long long budget_edges
     f32(&c->gV[b], ecap * (long long)c->maxdim * c->C);
   }
   f32(&c->GW, ecap * c->ldw);
-  f32(&c->gY, ecap * 9);
+  f32(&c->gY, ecap * 9 * c->cgroups);
   f32(&c->gf, ecap);
   if (tc) {
     b16(&c->GZb[0], ecap * c->maxw);
@@ -520,7 +525,7 @@ size_t bytes_per_edge(const ff_ctx* c) {
     if (L < c->NL) b += (size_t)c->layer_dout[L] * c->C * 4;
   }
   b += 2 * ((size_t)c->ldx + c->maxw + (size_t)c->maxdim * c->C) * 4;
-  b += (size_t)c->ldw * 4 + 9 * 4 + 4;
+  b += (size_t)c->ldw * 4 + 9 * 4 * (size_t)c->cgroups + 4;
   if (hp.precision == 1)   // bf16 operands (the fp32 hidden activations are not kept)
     b += (size_t)(c->NL + 1) * c->ldx * 2 + 2 * (size_t)c->maxw * 2 + (size_t)c->ldw * 2;
   return b;
@@ -793,7 +798,7 @@ void backward_chunk(ff_ctx* c, int a0, int a1, const double* seed, cudaStream_t 
   const int* rp = c->row_ptr + a0;
   const int na = a1 - a0;
   cudaMemsetAsync(c->gf, 0, (size_t)Ec * sizeof(float), s);
-  cudaMemsetAsync(c->gY, 0, (size_t)Ec * 9 * sizeof(float), s);
+  cudaMemsetAsync(c->gY, 0, (size_t)Ec * 9 * c->cgroups * sizeof(float), s);
   const float* gx = c->w_eff;
   int ldgx = 0;
   int cur = 0, gvb = 0;
@@ -861,8 +866,8 @@ void backward_chunk(ff_ctx* c, int a0, int a1, const double* seed, cudaStream_t 
   const int w0 = hp.two_body[0];
   const float a0f = (float)(1.0 / sqrt((double)(2 * FF_N_SPECIES + hp.n_basis)));
   launch_edge_grad(Ec, w0, hp.n_basis, hp.rc, hp.poly_p, c->lmax, c->ef, c->GZ[gzb], w0,
-                   c->W2b[0] + (size_t)2 * FF_N_SPECIES * w0, a0f, c->gf, c->gY, c->src + e0,
-                   c->sys_of, seed, c->g + e0, s);
+                   c->W2b[0] + (size_t)2 * FF_N_SPECIES * w0, a0f, c->gf, c->gY, c->cgroups,
+                   c->src + e0, c->sys_of, seed, c->g + e0, s);
 }
 
 // chunk plan for the current model list, workspace sized for it

@@ -141,8 +141,9 @@ void launch_cvt_bf16(const float* src, int lds, __nv_bfloat16* dst, int ldd, lon
                      int col0, int ncols, cudaStream_t s);
 void launch_edge_grad(long long E, int w0, int n_basis, float rc, int p, int lmax,
                       const float* ef, const float* gz0, int ldg, const float* WB,
-                      float alpha0, const float* gf, const float* gY, const int* src,
-                      const int* sys_of, const double* seed, float4* g, cudaStream_t s);
+                      float alpha0, const float* gf, const float* gY, int gy_groups,
+                      const int* src, const int* sys_of, const double* seed, float4* g,
+                      cudaStream_t s);
 void launch_force_gather(int n, const int* row_ptr, const int* rev, const float4* g,
                          float* F, cudaStream_t s);
 void launch_esys(const float* E_atom, const int* sys_ptr, int n_sys, double* E_sys,

@@ -177,8 +177,9 @@ __global__ void k_edge_grad(long long E, int w0, int n_basis, float rc, int p, i
                             const float* __restrict__ ef, const float* __restrict__ gz0, int ldg,
                             const float* __restrict__ WB, float alpha0,
                             const float* __restrict__ gf, const float* __restrict__ gY,
-                            const int* __restrict__ src, const int* __restrict__ sys_of,
-                            const double* __restrict__ seed, float4* __restrict__ g) {
+                            int gy_groups, const int* __restrict__ src,
+                            const int* __restrict__ sys_of, const double* __restrict__ seed,
+                            float4* __restrict__ g) {
   extern __shared__ float s_wb[];
   for (int i = threadIdx.x; i < n_basis * w0; i += blockDim.x) s_wb[i] = WB[i];
   __syncthreads();
@@ -209,7 +210,15 @@ __global__ void k_edge_grad(long long E, int w0, int n_basis, float rc, int p, i
     gr += alpha0 * gB[n - 1] * pref * (a * cs * r - sn) / (r * r);
   }
   gr += gf[e] * envelope_df(r / rc, p, rc);
-  const float* gy = gY + e * 9;
+  // harmonic gradients: partial sums of the channel groups, added in a fixed order
+  float gy[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) gy[k] = 0.f;
+  for (int q = 0; q < gy_groups; ++q) {
+    const float* p = gY + (e * gy_groups + q) * 9;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) gy[k] += p[k];
+  }
   float gux = kS3 * gy[3], guy = kS3 * gy[1], guz = kS3 * gy[2];
   if (lmax >= 2) {
     gux += kS15 * (uy * gy[4] + uz * gy[7] + ux * gy[8]);
@@ -369,12 +378,13 @@ void launch_rowred_bwd(long long E, int N, const float* gx, int ldgx, const floa
 
 void launch_edge_grad(long long E, int w0, int n_basis, float rc, int p, int lmax,
                       const float* ef, const float* gz0, int ldg, const float* WB, float alpha0,
-                      const float* gf, const float* gY, const int* src, const int* sys_of,
-                      const double* seed, float4* g, cudaStream_t s) {
+                      const float* gf, const float* gY, int gy_groups, const int* src,
+                      const int* sys_of, const double* seed, float4* g, cudaStream_t s) {
   ProfScope ps_(PC_EDGE_GRAD, s);
   if (E <= 0) return;
   k_edge_grad<<<ff_cdiv(E, 256), 256, (size_t)n_basis * w0 * sizeof(float), s>>>(
-      E, w0, n_basis, rc, p, lmax, ef, gz0, ldg, WB, alpha0, gf, gY, src, sys_of, seed, g);
+      E, w0, n_basis, rc, p, lmax, ef, gz0, ldg, WB, alpha0, gf, gY, gy_groups, src, sys_of,
+      seed, g);
   ff_count_launch(1);
 }
 

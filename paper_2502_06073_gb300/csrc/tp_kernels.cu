@@ -2,8 +2,8 @@
 // their adjoint (arXiv 2502.06073, Methodology, Model Training: e3nn tensor products,
 // l = 2, full O(3); the layer structure follows the Allegro architecture the paper uses).
 //
-// One team of C threads (C = tensor channels, 16 or 32) owns one centre atom i; thread c
-// owns channel c.  Because every edge of i is contiguous in the sorted edge list, the
+// One team of CT threads (16 or 32) owns one centre atom i and one group of CT channels
+// (C = 16: one team of 16; C = 32, 64, 128: C/32 teams of 32); thread owns channel c.  Because every edge of i is contiguous in the sorted edge list, the
 // environment sum
 //     G_i[c, lm] = nu^(-1/2) sum_{k in N(i)} w_ik[l, c] Y_lm(u_ik)
 // is a register accumulation over the atom's segment (no atomics, fixed order), and the
@@ -40,70 +40,70 @@ __device__ __forceinline__ void cp_async16(float* smem, const float* gmem) {
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// Copy `nfl` floats (a multiple of 4; 16-byte aligned) with the C lanes of a team.
-template <int C>
-__device__ __forceinline__ void stage(float* dst, const float* src, int nfl, int c) {
-  for (int i = 4 * c; i < nfl; i += 4 * C) cp_async16(dst + i, src + i);
-}
-
-// Per-channel path weights of the block in shared memory, transposed to [c][path] so that
-// thread c reads its own weights at stride NP (no bank conflicts for odd NP).
-template <int NP, int C>
-__device__ __forceinline__ void load_theta(float* s_th, const float* __restrict__ theta) {
-  for (int i = threadIdx.x; i < NP * C; i += blockDim.x) s_th[(i % C) * NP + i / C] = theta[i];
+// Copy `rows` rows of CT floats (16-byte aligned; source rows `stride` floats apart) into a
+// dense [rows][CT] shared buffer with the CT lanes of a team.
+template <int CT>
+__device__ __forceinline__ void stage(float* dst, const float* src, int rows, int stride,
+                                      int lane) {
+  constexpr int CH = CT / 4;   // 16-byte chunks per row
+  for (int i = lane; i < rows * CH; i += CT) {
+    const int r = i / CH, q = i - r * CH;
+    cp_async16(dst + r * CT + 4 * q, src + (size_t)r * stride + 4 * q);
+  }
 }
 
 // The per-edge rows [dim][C] of V (and of its gradient) are contiguous per edge and
 // consecutive edges of an atom are adjacent, so the team streams them through a
 // shared-memory double buffer with cp.async: edge e+1 is in flight while edge e is used.
-template <int LMAX, int INK, int LAST, int C>
+template <int LMAX, int INK, int LAST, int CT>
 __global__ void __launch_bounds__(128)
-k_env_tp_fwd(int n_atoms, const int* __restrict__ row_ptr, int e0, const float* __restrict__ ef,
-             const float* __restrict__ W, int ldw, const float* __restrict__ Vin,
-             const float* __restrict__ theta, float* __restrict__ X,
-             __nv_bfloat16* __restrict__ Xb, int ldx, int D, float* __restrict__ Vout,
-             float* __restrict__ Gam, float inv_sqrt_nu) {
+k_env_tp_fwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
+             const float* __restrict__ ef, const float* __restrict__ W, int ldw,
+             const float* __restrict__ Vin, const float* __restrict__ thetaT,
+             float* __restrict__ X, __nv_bfloat16* __restrict__ Xb, int ldx, int D,
+             float* __restrict__ Vout, float* __restrict__ Gam, float inv_sqrt_nu) {
   using K = TP<LMAX, INK, LAST>;
   constexpr int NY = (LMAX + 1) * (LMAX + 1);
-  constexpr int TEAMS = 128 / C;
-  constexpr int SIN = INK > 0 ? K::DIN * C : 4;
-  __shared__ __align__(16) float s_th[LAST ? 4 : K::NP * C];
+  constexpr int TEAMS = 128 / CT;
+  constexpr int SIN = INK > 0 ? K::DIN * CT : 4;
   __shared__ __align__(16) float s_in[TEAMS * 2 * SIN];
-  if (!LAST) load_theta<K::NP, C>(s_th, theta);
-  __syncthreads();
-  const int team = threadIdx.x / C, c = threadIdx.x % C;
-  const int a = blockIdx.x * TEAMS + team;
+  const int G = C / CT;
+  const int team = threadIdx.x / CT, lane = threadIdx.x % CT;
+  const long long tg = (long long)blockIdx.x * TEAMS + team;
+  const int a = (int)(tg / G), grp = (int)(tg - (long long)a * G);
   if (a >= n_atoms) return;
+  const int c = grp * CT + lane;
   const int eb = row_ptr[a] - e0, ee = row_ptr[a + 1] - e0;
   float* buf = s_in + team * 2 * SIN;
-  if (INK > 0 && eb < ee) stage<C>(buf, Vin + (size_t)eb * SIN, SIN, c);
+  const float* vin = Vin + grp * CT;
+  if (INK > 0 && eb < ee) stage<CT>(buf, vin + (size_t)eb * K::DIN * C, K::DIN, C, lane);
   cp_commit();
 
-  float G[NY];
+  float G_[NY];
 #pragma unroll
-  for (int k = 0; k < NY; ++k) G[k] = 0.f;
+  for (int k = 0; k < NY; ++k) G_[k] = 0.f;
   for (int e = eb; e < ee; ++e) {
     const float* y = ef + (size_t)e * FF_EF_STRIDE + FF_EF_Y;
 #pragma unroll
     for (int l = 0; l <= LMAX; ++l) {
       const float w = W[(size_t)e * ldw + l * C + c];
 #pragma unroll
-      for (int m = 0; m < 2 * l + 1; ++m) G[l * l + m] += w * y[l * l + m];
+      for (int m = 0; m < 2 * l + 1; ++m) G_[l * l + m] += w * y[l * l + m];
     }
   }
 #pragma unroll
   for (int k = 0; k < NY; ++k) {
-    G[k] *= inv_sqrt_nu;
-    Gam[((size_t)a * NY + k) * C + c] = G[k];
+    G_[k] *= inv_sqrt_nu;
+    Gam[((size_t)a * NY + k) * C + c] = G_[k];
   }
-  const float* th = s_th + c * K::NP;
+  const float* th = thetaT + (size_t)c * K::NP;
   for (int e = eb; e < ee; ++e) {
     const int cur = (e - eb) & 1;
     if (INK > 0 && e + 1 < ee)
-      stage<C>(buf + (cur ^ 1) * SIN, Vin + (size_t)(e + 1) * SIN, SIN, c);
+      stage<CT>(buf + (cur ^ 1) * SIN, vin + (size_t)(e + 1) * K::DIN * C, K::DIN, C, lane);
     cp_commit();
     cp_wait1();
-    __syncwarp(team_mask<C>());
+    __syncwarp(team_mask<CT>());
     float v[K::DIN];
     if (INK == 0) {
       const float* y = ef + (size_t)e * FF_EF_STRIDE + FF_EF_Y;
@@ -115,10 +115,10 @@ k_env_tp_fwd(int n_atoms, const int* __restrict__ row_ptr, int e0, const float* 
       }
     } else {
 #pragma unroll
-      for (int k = 0; k < K::DIN; ++k) v[k] = buf[cur * SIN + k * C + c];
+      for (int k = 0; k < K::DIN; ++k) v[k] = buf[cur * SIN + k * CT + lane];
     }
     float s[K::NS], vo[K::DOUT];
-    K::fwd(v, G, th, s, vo);
+    K::fwd(v, G_, th, s, vo);
 #pragma unroll
     for (int q = 0; q < K::NS; ++q) {
       const size_t xi = (size_t)e * ldx + D + q * C + c;
@@ -129,52 +129,58 @@ k_env_tp_fwd(int n_atoms, const int* __restrict__ row_ptr, int e0, const float* 
 #pragma unroll
       for (int k = 0; k < K::DOUT; ++k) Vout[((size_t)e * K::DOUT + k) * C + c] = vo[k];
     }
-    __syncwarp(team_mask<C>());
+    __syncwarp(team_mask<CT>());
   }
 }
 
-template <int LMAX, int INK, int LAST, int C>
+template <int LMAX, int INK, int LAST, int CT>
 __global__ void __launch_bounds__(128)
-k_env_tp_bwd(int n_atoms, const int* __restrict__ row_ptr, int e0, const float* __restrict__ ef,
-             const float* __restrict__ W, int ldw, const float* __restrict__ Vin,
-             const float* __restrict__ theta, const float* __restrict__ GX, int ldx, int D,
-             const float* __restrict__ gVout, float* __restrict__ gVin, float* __restrict__ GW,
-             __nv_bfloat16* __restrict__ GWb, float* __restrict__ gY,
-             const float* __restrict__ Gam, float inv_sqrt_nu) {
+k_env_tp_bwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
+             const float* __restrict__ ef, const float* __restrict__ W, int ldw,
+             const float* __restrict__ Vin, const float* __restrict__ thetaT,
+             const float* __restrict__ GX, int ldx, int D, const float* __restrict__ gVout,
+             float* __restrict__ gVin, float* __restrict__ GW, __nv_bfloat16* __restrict__ GWb,
+             float* __restrict__ gY, const float* __restrict__ Gam, float inv_sqrt_nu) {
   using K = TP<LMAX, INK, LAST>;
   constexpr int NY = (LMAX + 1) * (LMAX + 1);
-  constexpr int TEAMS = 128 / C;
-  constexpr int SIN = INK > 0 ? K::DIN * C : 0;
-  constexpr int SOUT = LAST ? 0 : K::DOUT * C;
+  constexpr int TEAMS = 128 / CT;
+  constexpr int SIN = INK > 0 ? K::DIN * CT : 0;
+  constexpr int SOUT = LAST ? 0 : K::DOUT * CT;
   constexpr int SST = (SIN + SOUT) > 0 ? SIN + SOUT : 4;   // floats staged per edge
-  __shared__ __align__(16) float s_th[LAST ? 4 : K::NP * C];
   __shared__ __align__(16) float s_in[TEAMS * 2 * SST];
-  if (!LAST) load_theta<K::NP, C>(s_th, theta);
-  __syncthreads();
-  const int team = threadIdx.x / C, c = threadIdx.x % C;
-  const int a = blockIdx.x * TEAMS + team;
+  const int G = C / CT;
+  const int team = threadIdx.x / CT, lane = threadIdx.x % CT;
+  const long long tg = (long long)blockIdx.x * TEAMS + team;
+  const int a = (int)(tg / G), grp = (int)(tg - (long long)a * G);
   if (a >= n_atoms) return;
+  const int c = grp * CT + lane;
   const int eb = row_ptr[a] - e0, ee = row_ptr[a + 1] - e0;
   float* buf = s_in + team * 2 * SST;
+  const float* vin = Vin + grp * CT;
+  const float* gvout = gVout + grp * CT;
   auto prefetch = [&](int e, int slot) {
-    if (SIN > 0) stage<C>(buf + slot * SST, Vin + (size_t)e * SIN, SIN, c);
-    if (SOUT > 0) stage<C>(buf + slot * SST + SIN, gVout + (size_t)e * SOUT, SOUT, c);
+    if (SIN > 0) stage<CT>(buf + slot * SST, vin + (size_t)e * K::DIN * C, K::DIN, C, lane);
+    if (SOUT > 0)
+      stage<CT>(buf + slot * SST + SIN, gvout + (size_t)e * K::DOUT * C, K::DOUT, C, lane);
   };
   if (eb < ee) prefetch(eb, 0);
   cp_commit();
-  float G[NY], gG[NY];
+  float G_[NY], gG[NY];
 #pragma unroll
   for (int k = 0; k < NY; ++k) {
-    G[k] = Gam[((size_t)a * NY + k) * C + c];
+    G_[k] = Gam[((size_t)a * NY + k) * C + c];
     gG[k] = 0.f;
   }
-  const float* th = s_th + c * K::NP;
+  const float* th = thetaT + (size_t)c * K::NP;
+  // harmonic gradients: one partial per channel group, summed later in a fixed order
+  float* gYg = gY + (size_t)grp * 9;
+  const int gstride = 9 * G;
   for (int e = eb; e < ee; ++e) {
     const int cur = (e - eb) & 1;
     if (e + 1 < ee) prefetch(e + 1, cur ^ 1);
     cp_commit();
     cp_wait1();
-    __syncwarp(team_mask<C>());
+    __syncwarp(team_mask<CT>());
     const float* y = ef + (size_t)e * FF_EF_STRIDE + FF_EF_Y;
     float v[K::DIN], gv[K::DIN];
     float wl[LMAX + 1];
@@ -187,7 +193,7 @@ k_env_tp_bwd(int n_atoms, const int* __restrict__ row_ptr, int e0, const float* 
         for (int m = 0; m < 2 * l + 1; ++m) v[l * l + m] = wl[l] * y[l * l + m];
     } else {
 #pragma unroll
-      for (int k = 0; k < K::DIN; ++k) v[k] = buf[cur * SST + k * C + c];
+      for (int k = 0; k < K::DIN; ++k) v[k] = buf[cur * SST + k * CT + lane];
     }
 #pragma unroll
     for (int k = 0; k < K::DIN; ++k) gv[k] = 0.f;
@@ -195,8 +201,8 @@ k_env_tp_bwd(int n_atoms, const int* __restrict__ row_ptr, int e0, const float* 
 #pragma unroll
     for (int q = 0; q < K::NS; ++q) gs[q] = GX[(size_t)e * ldx + D + q * C + c];
 #pragma unroll
-    for (int k = 0; k < K::DOUT; ++k) gvo[k] = LAST ? 0.f : buf[cur * SST + SIN + k * C + c];
-    K::bwd(v, G, th, gs, gvo, gv, gG);
+    for (int k = 0; k < K::DOUT; ++k) gvo[k] = LAST ? 0.f : buf[cur * SST + SIN + k * CT + lane];
+    K::bwd(v, G_, th, gs, gvo, gv, gG);
     if (INK == 0) {
       // V^0 = w (x) Y: gradient to the env weights and to the harmonics
 #pragma unroll
@@ -210,14 +216,14 @@ k_env_tp_bwd(int n_atoms, const int* __restrict__ row_ptr, int e0, const float* 
       for (int l = 0; l <= LMAX; ++l)
 #pragma unroll
         for (int m = 0; m < 2 * l + 1; ++m) {
-          const float t = team_sum<C>(gv[l * l + m] * wl[l]);
-          if (c == l * l + m) gY[(size_t)e * 9 + l * l + m] += t;
+          const float tt = team_sum<CT>(gv[l * l + m] * wl[l]);
+          if (lane == l * l + m) gYg[(size_t)e * gstride + l * l + m] += tt;
         }
     } else {
 #pragma unroll
       for (int k = 0; k < K::DIN; ++k) gVin[((size_t)e * K::DIN + k) * C + c] = gv[k];
     }
-    __syncwarp(team_mask<C>());
+    __syncwarp(team_mask<CT>());
   }
   // adjoint of the environment sum, fanned back out to every edge of the atom
 #pragma unroll
@@ -236,34 +242,36 @@ k_env_tp_bwd(int n_atoms, const int* __restrict__ row_ptr, int e0, const float* 
       else GW[wi] = tot;
 #pragma unroll
       for (int m = 0; m < 2 * l + 1; ++m) {
-        const float t = team_sum<C>(gG[l * l + m] * wl);
-        if (c == l * l + m) gY[(size_t)e * 9 + l * l + m] += t;
+        const float tt = team_sum<CT>(gG[l * l + m] * wl);
+        if (lane == l * l + m) gYg[(size_t)e * gstride + l * l + m] += tt;
       }
     }
   }
 }
 
-template <int LMAX, int INK, int LAST, int C>
-void fwd_one(int n_atoms, const int* row_ptr, int e0, const float* ef, const float* W, int ldw,
-             const float* Vin, const float* theta, float* X, __nv_bfloat16* Xb, int ldx, int D,
-             float* Vout, float* Gam, float inv_sqrt_nu, cudaStream_t s) {
-  k_env_tp_fwd<LMAX, INK, LAST, C><<<ff_cdiv((long long)n_atoms * C, 128), 128, 0, s>>>(
-      n_atoms, row_ptr, e0, ef, W, ldw, Vin, theta, X, Xb, ldx, D, Vout, Gam, inv_sqrt_nu);
+template <int LMAX, int INK, int LAST, int CT>
+void fwd_one(int n_atoms, int C, const int* row_ptr, int e0, const float* ef, const float* W,
+             int ldw, const float* Vin, const float* thetaT, float* X, __nv_bfloat16* Xb,
+             int ldx, int D, float* Vout, float* Gam, float inv_sqrt_nu, cudaStream_t s) {
+  const long long teams = (long long)n_atoms * (C / CT);
+  k_env_tp_fwd<LMAX, INK, LAST, CT><<<ff_cdiv(teams * CT, 128), 128, 0, s>>>(
+      n_atoms, C, row_ptr, e0, ef, W, ldw, Vin, thetaT, X, Xb, ldx, D, Vout, Gam, inv_sqrt_nu);
 }
 
-template <int LMAX, int INK, int LAST, int C>
-void bwd_one(int n_atoms, const int* row_ptr, int e0, const float* ef, const float* W, int ldw,
-             const float* Vin, const float* theta, const float* GX, int ldx, int D,
+template <int LMAX, int INK, int LAST, int CT>
+void bwd_one(int n_atoms, int C, const int* row_ptr, int e0, const float* ef, const float* W,
+             int ldw, const float* Vin, const float* thetaT, const float* GX, int ldx, int D,
              const float* gVout, float* gVin, float* GW, __nv_bfloat16* GWb, float* gY,
              const float* Gam, float inv_sqrt_nu, cudaStream_t s) {
-  k_env_tp_bwd<LMAX, INK, LAST, C><<<ff_cdiv((long long)n_atoms * C, 128), 128, 0, s>>>(
-      n_atoms, row_ptr, e0, ef, W, ldw, Vin, theta, GX, ldx, D, gVout, gVin, GW, GWb, gY, Gam,
-      inv_sqrt_nu);
+  const long long teams = (long long)n_atoms * (C / CT);
+  k_env_tp_bwd<LMAX, INK, LAST, CT><<<ff_cdiv(teams * CT, 128), 128, 0, s>>>(
+      n_atoms, C, row_ptr, e0, ef, W, ldw, Vin, thetaT, GX, ldx, D, gVout, gVin, GW, GWb, gY,
+      Gam, inv_sqrt_nu);
 }
 
 #define FF_TP_DISPATCH(FN, ...)                                                             \
   do {                                                                                      \
-    const int key = ((lmax * 3 + in_kind) * 2 + last) * 2 + (C == 32 ? 1 : 0);              \
+    const int key = ((lmax * 3 + in_kind) * 2 + last) * 2 + (C == 16 ? 0 : 1);              \
     switch (key) {                                                                          \
       case ((1 * 3 + 0) * 2 + 0) * 2 + 0: FN<1, 0, 0, 16>(__VA_ARGS__); break;             \
       case ((1 * 3 + 0) * 2 + 0) * 2 + 1: FN<1, 0, 0, 32>(__VA_ARGS__); break;             \
@@ -302,8 +310,8 @@ void launch_env_tp_fwd(int lmax, int in_kind, int last, int C, int n_atoms, cons
                        float* Vout, float* Gam, float inv_sqrt_nu, cudaStream_t s) {
   ProfScope ps_(PC_TP_FWD, s);
   if (n_atoms <= 0) return;
-  FF_TP_DISPATCH(fwd_one, n_atoms, row_ptr, e0, ef, W, ldw, Vin, theta, X, Xb, ldx, D, Vout, Gam,
-                 inv_sqrt_nu, s);
+  FF_TP_DISPATCH(fwd_one, n_atoms, C, row_ptr, e0, ef, W, ldw, Vin, theta, X, Xb, ldx, D, Vout,
+                 Gam, inv_sqrt_nu, s);
   ff_count_launch(1);
 }
 
@@ -314,7 +322,7 @@ void launch_env_tp_bwd(int lmax, int in_kind, int last, int C, int n_atoms, cons
                        float inv_sqrt_nu, cudaStream_t s) {
   ProfScope ps_(PC_TP_BWD, s);
   if (n_atoms <= 0) return;
-  FF_TP_DISPATCH(bwd_one, n_atoms, row_ptr, e0, ef, W, ldw, Vin, theta, GX, ldx, D, gVout, gVin,
-                 GW, GWb, gY, Gam, inv_sqrt_nu, s);
+  FF_TP_DISPATCH(bwd_one, n_atoms, C, row_ptr, e0, ef, W, ldw, Vin, theta, GX, ldx, D, gVout,
+                 gVin, GW, GWb, gY, Gam, inv_sqrt_nu, s);
   ff_count_launch(1);
 }

@@ -360,3 +360,22 @@ def test_autotune_picks_a_valid_tile_and_keeps_results(ff):
     _, Ea1, F1 = m.energy_forces(pos)
     # the tile shape changes no arithmetic: the K loop and the accumulation are the same
     assert torch.equal(Ea0, Ea1) and torch.equal(F0, F1)
+
+
+@pytest.mark.parametrize("model", ["fm64", "fm256", "fm512"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_table1_model_sizes(ff, model, precision):
+    """Allegro-FM64/256/512 hyperparameters of Table 1 (16/64/128 tensor channels, latent
+    [64]*3/[256]*3/[512]*3, two-body [16,32,64]/[64,128,256]/[128,256,512], 2 layers,
+    l = 2) on the 512-atom C-S-H box, FP32 and BF16 paths against the oracle."""
+    s = synth.csh_system(sub=True)
+    hp = synth.preset(model, avg_num_neighbors=synth.NU["csh512"], rc=5.2)
+    m, pos = _bind(ff, hp, s, precision=precision)
+    Es, Ea, F = m.energy_forces(pos)
+    E_ref, Ea_ref, F_ref = pool.evaluate(hp, 42, s.pos, s.Z, s.box, s.pbc)
+    if precision == 0:
+        _check_ef(Es, Ea, F, E_ref, Ea_ref, F_ref, model)
+    else:
+        d = F.double().cpu().numpy() - F_ref
+        assert np.sqrt((d ** 2).mean()) <= 5e-3 and np.abs(d).max() <= 5e-3
+        assert abs(Es.item() - E_ref[0]) <= 4e-3 * np.abs(Ea_ref).sum()
