@@ -121,6 +121,14 @@ int ff_energy_forces(ff_ctx* ctx, const double* pos, double* E_sys, float* E_ato
  * FF_ERR_CUDA. */
 int ff_forces(ff_ctx* ctx, const double* grad_E, float* F, void* stream);
 
+/* Virial of each system from the edge gradients of the last force evaluation (a
+ * ff_energy_forces / ff_energy_forces_graph call with F, or ff_forces without grad_E):
+ *   W[k][a][b] = -sum over edges e of system k of r_e,a g_e,b,  g_e = dE/dr_e  (eV)
+ * so dE/d(strain_ab) = -W[k][b][a] and the stress is -W / volume (the paper trains on
+ * stresses; Methodology, Model Training).  W: device double[n_sys][3][3].  FP64
+ * reduction in a fixed order.  Errors: FF_ERR_STATE (no force evaluation), FF_ERR_CUDA. */
+int ff_virial(ff_ctx* ctx, double* W, void* stream);
+
 /* Velocity-Verlet NVE steps (Methodology, MD Simulations; QMD uses an explicit
  * reversible integrator): v += dt/2 F/m; x += dt v; F = F(x); v += dt/2 F/m, in FP64
  * with 1 eV/(A amu) = 9.648533212e-3 A/fs^2.
@@ -159,6 +167,21 @@ int ff_autotune(ff_ctx* ctx, const double* pos, int* slice, int* stages, double*
  * displacement check (one flag read; rebuild + recapture when an atom moved more than
  * skin/2), graph replay of E+F, kick.  enable == 0 (default): per-step filtered lists. */
 int ff_set_graph(ff_ctx* ctx, int enable);
+
+/* Nose-Hoover NVT steps (the paper thermalises and heats its systems in the canonical
+ * ensemble with 0.5 fs steps; Methodology, MD Simulations): one thermostat per system with
+ * mass Q = g kB T tau^2 (g = 3 x atoms of the system) in the time-reversible splitting
+ *   NH(dt/2), v += dt/2 F/m, x += dt v, F = F(x), v += dt/2 F/m, NH(dt/2)
+ *   NH(h): xi += h/2 G; v *= exp(-xi h); eta += h xi; xi += h/2 G,  G = (2 KE - g kB T)/Q
+ * entirely on the device (FP64).
+ *   x, v, mass       as in ff_md_step;  T_K target temperature (K);  tau_fs (fs)
+ *   thermo           device double[n_sys][2] (xi in 1/fs, eta), in/out (start from zeros)
+ *   E_pot, E_kin, H  device double[n_steps * n_sys] or NULL: per step potential, kinetic and
+ *                    conserved extended energy H = E_pot + E_kin + Q xi^2/2 + g kB T eta
+ * Errors: as ff_md_step. */
+int ff_md_nvt(ff_ctx* ctx, double* x, double* v, const double* mass, int n_steps, double dt_fs,
+              double T_K, double tau_fs, double* thermo, double* E_pot, double* E_kin, double* H,
+              void* stream);
 
 /* Copy every weight, in tensor order, as the FP64 values drawn at creation (before any
  * rounding to the device precision) into host_buf.  *needed receives the count.

@@ -299,6 +299,31 @@ class Allegro64:
                           for k in range(len(sys_ptr) - 1)])
         return E_sys, E_atom, F
 
+    def virial(self, pos, Z, box, pbc, sys_ptr=None):
+        """Virial per system, W_ab = -sum_e r_e,a g_e,b (eV), g_e = dE/dr_e.
+
+        Under a homogeneous strain x -> (1 + eps) x (box included) every edge vector maps
+        to (1 + eps) r_e, so dE/d(eps_ab) = sum_e g_e,a r_e,b = -W_ba; the stress is
+        sigma = -W / V.  (The paper trains on stresses; Methodology, Model Training.)"""
+        pos = np.asarray(pos, dtype=np.float64)
+        n = pos.shape[0]
+        if sys_ptr is None:
+            sys_ptr = np.array([0, n])
+        nl = neighbors.neighbor_list(pos, box, pbc, self.hp["rc"], 0.0, sys_ptr)
+        row_ptr, col, shift = nl
+        W = np.zeros((len(sys_ptr) - 1, 3, 3))
+        sys_of = np.searchsorted(np.asarray(sys_ptr), np.arange(n), side="right") - 1
+        i = np.repeat(np.arange(n), np.diff(row_ptr))
+        if col.shape[0] == 0:
+            return W
+        rvec = self.edge_vectors(pos, box, i, col, shift)
+        _, t = self._forward(rvec, np.asarray(Z)[i], np.asarray(Z)[col], i, n)
+        g = self._backward(t, i, n)
+        for k in range(W.shape[0]):
+            m = sys_of[i] == k
+            W[k] = -rvec[m].T @ g[m]
+        return W
+
     def centre_terms(self, pos, Z, box, pbc, centres, sys_ptr=None):
         """Per-centre energy E_i and edge gradients g_e of the given centres only.
 

@@ -40,3 +40,44 @@ def run_nve(model, pos, vel, Z, box, pbc, masses, dt, n_steps):
         epot.append(float(E.sum()))
         ekin.append(kinetic(v, m))
     return x, v, np.array(epot), np.array(ekin)
+
+
+def _thermostat_half(v, m, xi, eta, dt, g, kT, Q):
+    """Nose-Hoover half step (dt/2) of the time-reversible Trotter splitting:
+    xi += dt/4 G; v *= exp(-xi dt/2); eta += dt/2 xi; xi += dt/4 G', with
+    G = (2 KE - g kT) / Q evaluated before and after the velocity scaling."""
+    ke = kinetic(v, m)
+    xi += 0.25 * dt * (2.0 * ke - g * kT) / Q
+    v *= np.exp(-0.5 * dt * xi)
+    eta += 0.5 * dt * xi
+    ke = kinetic(v, m)
+    xi += 0.25 * dt * (2.0 * ke - g * kT) / Q
+    return v, xi, eta
+
+
+def run_nvt(model, pos, vel, Z, box, pbc, masses, dt, n_steps, T, tau, xi=0.0, eta=0.0):
+    """Nose-Hoover NVT (the paper thermalises and heats its systems in the canonical
+    ensemble; Methodology, MD Simulations): one thermostat with mass Q = g kB T tau^2,
+    g = 3N degrees of freedom, around a velocity-Verlet step.  Returns
+    (x, v, E_pot, E_kin, H, xi, eta) with H = E_pot + E_kin + Q xi^2 / 2 + g kB T eta the
+    conserved extended energy (per step)."""
+    x = np.array(pos, dtype=np.float64)
+    v = np.array(vel, dtype=np.float64)
+    m = np.asarray(masses, dtype=np.float64)
+    g = 3 * x.shape[0]
+    kT = K_B * T
+    Q = g * kT * tau * tau
+    E, _, F = model.evaluate(x, Z, box, pbc)
+    epot, ekin, H = [], [], []
+    for _ in range(n_steps):
+        v, xi, eta = _thermostat_half(v, m, xi, eta, dt, g, kT, Q)
+        v += 0.5 * dt * ACC * F / m[:, None]
+        x += dt * v
+        E, _, F = model.evaluate(x, Z, box, pbc)
+        v += 0.5 * dt * ACC * F / m[:, None]
+        v, xi, eta = _thermostat_half(v, m, xi, eta, dt, g, kT, Q)
+        ke = kinetic(v, m)
+        epot.append(float(E.sum()))
+        ekin.append(ke)
+        H.append(float(E.sum()) + ke + 0.5 * Q * xi * xi + g * kT * eta)
+    return x, v, np.array(epot), np.array(ekin), np.array(H), xi, eta

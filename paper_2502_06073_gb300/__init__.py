@@ -28,7 +28,7 @@ ERRORS = {-1: "FF_ERR_ARG", -2: "FF_ERR_SPECIES", -3: "FF_ERR_OOM", -4: "FF_ERR_
 ABI = ("ff_create", "ff_destroy", "ff_neighbors", "ff_energy_forces", "ff_forces",
        "ff_md_step", "ff_export_params", "ff_get_edges", "ff_kernel_launches", "ff_last_error",
        "ff_profile_enable", "ff_profile_read", "ff_profile_class", "ff_neighbors_noalloc",
-       "ff_energy_forces_graph", "ff_set_graph", "ff_autotune")
+       "ff_energy_forces_graph", "ff_set_graph", "ff_autotune", "ff_virial", "ff_md_nvt")
 
 
 class HParams(ctypes.Structure):
@@ -66,6 +66,9 @@ def load_library(path: str | None = None):
     lib.ff_energy_forces.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.ff_energy_forces_graph.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.ff_set_graph.argtypes = [vp, i32]
+    lib.ff_virial.argtypes = [vp, vp, vp]
+    lib.ff_md_nvt.argtypes = [vp, vp, vp, vp, i32, ctypes.c_double, ctypes.c_double,
+                              ctypes.c_double, vp, vp, vp, vp, vp]
     lib.ff_autotune.argtypes = [vp, vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                 ctypes.POINTER(ctypes.c_double), vp]
     lib.ff_forces.argtypes = [vp, vp, vp, vp]
@@ -212,6 +215,13 @@ class FFModel:
                                          ctypes.byref(ms), _stream(torch)))
         return {"slice": sl.value, "stages": st.value, "ms_per_evaluation": ms.value}
 
+    def virial(self):
+        """Per-system virial W = -sum_e r_e (x) dE/dr_e, shape [n_sys, 3, 3] (eV)."""
+        torch = _torch()
+        W = torch.empty(self.n_sys, 3, 3, dtype=torch.float64, device="cuda")
+        self._check(self.lib.ff_virial(self._h, _ptr(W), _stream(torch)))
+        return W
+
     def set_graph(self, enable: bool = True):
         """Make md() replay a captured CUDA graph on a frozen Verlet list."""
         self._check(self.lib.ff_set_graph(self._h, 1 if enable else 0))
@@ -238,6 +248,19 @@ class FFModel:
                                  float(dt_fs), _ptr(Ep), _ptr(Ek), _stream(torch))
         self._check(rc)
         return Ep, Ek
+
+    def md_nvt(self, x, v, mass, n_steps, dt_fs, T, tau_fs, thermo=None):
+        """Nose-Hoover NVT steps; thermo (cuda float64 [n_sys, 2]) carries (xi, eta)."""
+        torch = _torch()
+        if thermo is None:
+            thermo = torch.zeros(self.n_sys, 2, dtype=torch.float64, device=x.device)
+        out = [torch.empty(n_steps * self.n_sys, dtype=torch.float64, device=x.device)
+               for _ in range(3)]
+        rc = self.lib.ff_md_nvt(self._h, _ptr(x), _ptr(v), _ptr(mass), int(n_steps),
+                                float(dt_fs), float(T), float(tau_fs), _ptr(thermo),
+                                _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), _stream(torch))
+        self._check(rc)
+        return out[0], out[1], out[2], thermo
 
     # ---------------------------------------------------------------- introspection
     def export_params(self) -> np.ndarray:

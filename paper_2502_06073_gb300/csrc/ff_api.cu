@@ -197,6 +197,10 @@ struct ff_ctx {
   cudaGraphExec_t gexec = nullptr;
   const void* gkey[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   long long gkey_gen = -1;
+  // edge gradients g of the last force evaluation (for the virial)
+  const double* g_pos = nullptr;
+  double* vir_part = nullptr;
+  double* nh_buf = nullptr;     // NVT scratch: kinetic energy and scale factor per system
   // tensor-core GEMM tile configuration (set by ff_autotune)
   int tune_slice = 256, tune_stages = 0;
   const double* state_pos = nullptr;
@@ -911,6 +915,7 @@ int evaluate(ff_ctx* c, const double* pos, double* E_sys, float* E_atom, float* 
   std::vector<int> starts;
   FF_TRY(plan_and_reserve(c, starts));
   FF_TRY(run_model(c, pos, E_sys, E_atom, F, seed, forces, starts, s));
+  c->g_pos = (forces && !seed) ? pos : nullptr;
   c->state_valid = true;
   c->state_chunks = (int)starts.size() - 1;
   c->state_starts = starts;
@@ -985,6 +990,7 @@ int graph_eval(ff_ctx* c, const double* pos, double* E_sys, float* E_atom, float
   }
   FF_CK(c, cudaEventRecord(c->ev_b, c->gstream));
   FF_CK(c, cudaStreamWaitEvent(s, c->ev_b, 0));
+  c->g_pos = forces ? pos : nullptr;
   c->state_valid = false;       // the adjoint entry point needs a plain evaluation
   c->eval_gen++;
   return FF_OK;
@@ -1054,7 +1060,7 @@ void ff_destroy(ff_ctx* c) {
   dfree(c->cell_count); dfree(c->cell_start); dfree(c->cell_fill); dfree(c->cell_atoms);
   dfree(c->xref); dfree(c->cnt); dfree(c->row_ptr); dfree(c->col); dfree(c->shift); dfree(c->src);
   dfree(c->rev); dfree(c->scan_tmp); dfree(c->flags); dfree(c->g); dfree(c->E_atom);
-  dfree(c->F_int); dfree(c->esys_tmp);
+  dfree(c->F_int); dfree(c->esys_tmp); dfree(c->vir_part); dfree(c->nh_buf);
   if (c->flags_h) cudaFreeHost(c->flags_h);
   delete c;
 }
@@ -1136,6 +1142,7 @@ int ff_neighbors(ff_ctx* c, const double* pos, const int32_t* Z, int n_atoms, co
   c->bound = true;
   c->built = false;
   c->state_valid = false;
+  c->g_pos = nullptr;
   c->md_force_pos = nullptr;
   FF_TRY(build_verlet(c, pos, s));
   c->list_fixed = false;
@@ -1167,6 +1174,19 @@ int ff_forces(ff_ctx* c, const double* grad_E, float* F, void* stream) {
     }
   }
   launch_force_gather(c->n, c->row_ptr, c->rev, c->g, F, s);
+  FF_CK(c, cudaGetLastError());
+  c->g_pos = grad_E ? nullptr : c->state_pos;
+  return FF_OK;
+}
+
+int ff_virial(ff_ctx* c, double* W, void* stream) {
+  if (!c) return FF_ERR_ARG;
+  if (!W) return set_err(c, FF_ERR_ARG, "W is null");
+  if (!c->g_pos)
+    return set_err(c, FF_ERR_STATE, "ff_virial needs a preceding force evaluation (unit seed)");
+  FF_TRY(dalloc(c, &c->vir_part, (size_t)c->n_sys * 32 * 9));
+  launch_virial(c->sys_ptr, c->n_sys, c->row_ptr, c->src, c->col, c->shift, c->g_pos, c->L_d,
+                c->g, c->vir_part, W, (cudaStream_t)stream);
   FF_CK(c, cudaGetLastError());
   return FF_OK;
 }
@@ -1276,6 +1296,44 @@ int ff_set_graph(ff_ctx* c, int enable) {
   if (!c) return FF_ERR_ARG;
   c->graph_md = enable != 0;
   c->md_force_pos = nullptr;
+  return FF_OK;
+}
+
+int ff_md_nvt(ff_ctx* c, double* x, double* v, const double* mass, int n_steps, double dt_fs,
+              double T_K, double tau_fs, double* thermo, double* E_pot, double* E_kin,
+              double* H, void* stream) {
+  if (!c) return FF_ERR_ARG;
+  if (!c->bound) return set_err(c, FF_ERR_STATE, "ff_neighbors must be called first");
+  if (!x || !v || !mass || !thermo || n_steps < 0 || !(T_K > 0.0) || !(tau_fs > 0.0))
+    return set_err(c, FF_ERR_ARG, "bad NVT arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  const double kT = 8.617333262e-5 * T_K;
+  FF_TRY(dalloc(c, &c->nh_buf, (size_t)c->n_sys * 2));
+  double* ke = c->nh_buf;
+  double* scale = c->nh_buf + c->n_sys;
+  if (!(c->md_force_pos == x && c->md_force_gen == c->eval_gen))
+    FF_TRY(evaluate(c, x, nullptr, nullptr, c->F_int, nullptr, true, s));
+  for (int it = 0; it < n_steps; ++it) {
+    launch_nh_half(c->n, c->n_sys, c->sys_ptr, c->sys_of, v, mass, ke, scale, thermo, dt_fs, kT,
+                   tau_fs, s);
+    launch_kick(c->n, v, c->F_int, mass, 0.5 * dt_fs, s);
+    launch_drift(c->n, x, v, dt_fs, s);
+    FF_TRY(evaluate(c, x, c->esys_tmp, nullptr, c->F_int, nullptr, true, s));
+    launch_kick(c->n, v, c->F_int, mass, 0.5 * dt_fs, s);
+    launch_nh_half(c->n, c->n_sys, c->sys_ptr, c->sys_of, v, mass, ke, scale, thermo, dt_fs, kT,
+                   tau_fs, s);
+    launch_kinetic(v, mass, c->sys_ptr, c->n_sys, ke, s);
+    const size_t o = (size_t)it * c->n_sys;
+    if (E_pot)
+      FF_CK(c, cudaMemcpyAsync(E_pot + o, c->esys_tmp, c->n_sys * sizeof(double),
+                               cudaMemcpyDeviceToDevice, s));
+    if (E_kin)
+      FF_CK(c, cudaMemcpyAsync(E_kin + o, ke, c->n_sys * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (H) launch_nh_energy(c->n_sys, c->sys_ptr, c->esys_tmp, ke, thermo, kT, tau_fs, H + o, s);
+  }
+  FF_CK(c, cudaGetLastError());
+  c->md_force_pos = x;
+  c->md_force_gen = c->eval_gen;
   return FF_OK;
 }
 

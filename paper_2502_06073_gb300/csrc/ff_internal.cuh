@@ -148,10 +148,20 @@ void launch_force_gather(int n, const int* row_ptr, const int* rev, const float4
                          float* F, cudaStream_t s);
 void launch_esys(const float* E_atom, const int* sys_ptr, int n_sys, double* E_sys,
                  cudaStream_t s);
+// W[k] = -sum over the edges of system k of r_e (x) g_e; part: n_sys * 32 * 9 doubles
+void launch_virial(const int* sys_ptr, int n_sys, const int* row_ptr, const int* src,
+                   const int* col, const int* shift, const double* pos, const double* L,
+                   const float4* g, double* part, double* W, cudaStream_t s);
 void launch_kick(int n, double* v, const float* F, const double* mass, double hdt,
                  cudaStream_t s);
 void launch_drift(int n, double* x, const double* v, double dt, cudaStream_t s);
 void launch_kinetic(const double* v, const double* mass, const int* sys_ptr, int n_sys,
                     double* E_kin, cudaStream_t s);
 void launch_fill_f32(float* p, long long n, float v, cudaStream_t s);
+// Nose-Hoover half step: KE per system, thermostat update (xi, eta in thermo[2k..]), v scaling
+void launch_nh_half(int n, int n_sys, const int* sys_ptr, const int* sys_of, double* v,
+                    const double* mass, double* ke, double* scale, double* thermo, double dt,
+                    double kT, double tau, cudaStream_t s);
+void launch_nh_energy(int n_sys, const int* sys_ptr, const double* epot, const double* ke,
+                      const double* thermo, double kT, double tau, double* H, cudaStream_t s);
 void launch_check_finite(const float* F, long long n, int* err, cudaStream_t s);

@@ -274,6 +274,53 @@ __device__ double block_sum_d(double v, double* sh) {
   return r;
 }
 
+// Virial partials: block b of system k sums r_e (x) g_e over slice b of the system's edges
+// (r_e recomputed in FP64 exactly as for the edge features), FP64, fixed reduction tree.
+constexpr int kVirBlocks = 32;
+__global__ void k_virial_part(const int* __restrict__ sys_ptr, const int* __restrict__ row_ptr,
+                              const int* __restrict__ src, const int* __restrict__ col,
+                              const int* __restrict__ shift, const double* __restrict__ pos,
+                              const double* __restrict__ L, const float4* __restrict__ g,
+                              double* __restrict__ part) {
+  __shared__ double sh[32];
+  const int k = blockIdx.y, b = blockIdx.x;
+  const long long e0 = row_ptr[sys_ptr[k]], e1 = row_ptr[sys_ptr[k + 1]];
+  const long long len = e1 - e0;
+  const long long lo = e0 + len * b / kVirBlocks, hi = e0 + len * (b + 1) / kVirBlocks;
+  double acc[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) acc[q] = 0.0;
+  for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+    const int i = src[e], j = col[e];
+    int s0, s1, s2;
+    ff_unpack_shift(shift[e], s0, s1, s2);
+    const double r[3] = {(pos[3 * (long long)j] - pos[3 * (long long)i]) + s0 * L[0],
+                         (pos[3 * (long long)j + 1] - pos[3 * (long long)i + 1]) + s1 * L[1],
+                         (pos[3 * (long long)j + 2] - pos[3 * (long long)i + 2]) + s2 * L[2]};
+    const float4 gv = g[e];
+    const double gg[3] = {gv.x, gv.y, gv.z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc[3 * a + c] += r[a] * gg[c];
+  }
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    const double v = block_sum_d(acc[q], sh);
+    if (threadIdx.x == 0) part[((size_t)k * kVirBlocks + b) * 9 + q] = v;
+    __syncthreads();
+  }
+}
+
+__global__ void k_virial_final(const double* __restrict__ part, int n_sys, double* __restrict__ W) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_sys * 9) return;
+  const int k = t / 9, q = t % 9;
+  double s = 0.0;
+  for (int b = 0; b < kVirBlocks; ++b) s += part[((size_t)k * kVirBlocks + b) * 9 + q];
+  W[t] = -s;
+}
+
 __global__ void k_esys(const float* __restrict__ E_atom, const int* __restrict__ sys_ptr,
                        double* __restrict__ E_sys) {
   __shared__ double sh[32];
@@ -322,6 +369,45 @@ __global__ void k_cvt_bf16(const float* __restrict__ src, int lds, __nv_bfloat16
   const long long r = t / ncols;
   const int c = col0 + (int)(t - r * ncols);
   dst[r * ldd + c] = __float2bfloat16_rn(src[r * lds + c]);
+}
+
+// Nose-Hoover half step per system from its kinetic energy: xi += dt/4 G; s = exp(-xi dt/2);
+// eta += dt/2 xi; xi += dt/4 G(KE s^2); G(KE) = (2 KE - g kT) / Q, Q = g kT tau^2, g = 3 N.
+__global__ void k_nh_update(int n_sys, const int* __restrict__ sys_ptr,
+                            const double* __restrict__ ke, double* __restrict__ thermo,
+                            double* __restrict__ scale, double dt, double kT, double tau) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_sys) return;
+  const double g = 3.0 * (sys_ptr[k + 1] - sys_ptr[k]);
+  if (g <= 0.0) { scale[k] = 1.0; return; }
+  const double Q = g * kT * tau * tau;
+  double xi = thermo[2 * k], eta = thermo[2 * k + 1];
+  xi += 0.25 * dt * (2.0 * ke[k] - g * kT) / Q;
+  const double s = exp(-0.5 * dt * xi);
+  eta += 0.5 * dt * xi;
+  xi += 0.25 * dt * (2.0 * ke[k] * s * s - g * kT) / Q;
+  thermo[2 * k] = xi;
+  thermo[2 * k + 1] = eta;
+  scale[k] = s;
+}
+
+__global__ void k_scale_v(long long n3, const int* __restrict__ sys_of,
+                          const double* __restrict__ scale, double* __restrict__ v) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n3) return;
+  v[t] *= scale[sys_of[t / 3]];
+}
+
+// conserved extended energy H = E_pot + E_kin + Q xi^2 / 2 + g kT eta per system
+__global__ void k_nh_energy(int n_sys, const int* __restrict__ sys_ptr,
+                            const double* __restrict__ epot, const double* __restrict__ ke,
+                            const double* __restrict__ thermo, double kT, double tau,
+                            double* __restrict__ H) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_sys) return;
+  const double g = 3.0 * (sys_ptr[k + 1] - sys_ptr[k]);
+  const double Q = g * kT * tau * tau;
+  H[k] = epot[k] + ke[k] + 0.5 * Q * thermo[2 * k] * thermo[2 * k] + g * kT * thermo[2 * k + 1];
 }
 
 __global__ void k_fill_f32(float* __restrict__ p, long long n, float v) {
@@ -396,6 +482,17 @@ void launch_force_gather(int n, const int* row_ptr, const int* rev, const float4
   ff_count_launch(1);
 }
 
+void launch_virial(const int* sys_ptr, int n_sys, const int* row_ptr, const int* src,
+                   const int* col, const int* shift, const double* pos, const double* L,
+                   const float4* g, double* part, double* W, cudaStream_t s) {
+  ProfScope ps_(PC_MISC, s);
+  if (n_sys <= 0) return;
+  k_virial_part<<<dim3(kVirBlocks, n_sys), 256, 0, s>>>(sys_ptr, row_ptr, src, col, shift, pos, L,
+                                                       g, part);
+  k_virial_final<<<ff_cdiv(n_sys * 9, 256), 256, 0, s>>>(part, n_sys, W);
+  ff_count_launch(2);
+}
+
 void launch_esys(const float* E_atom, const int* sys_ptr, int n_sys, double* E_sys,
                  cudaStream_t s) {
   ProfScope ps_(PC_MISC, s);
@@ -432,6 +529,25 @@ void launch_cvt_bf16(const float* src, int lds, __nv_bfloat16* dst, int ldd, lon
   ProfScope ps_(PC_MISC, s);
   if (rows <= 0 || ncols <= 0) return;
   k_cvt_bf16<<<ff_cdiv(rows * ncols, 256), 256, 0, s>>>(src, lds, dst, ldd, rows, col0, ncols);
+  ff_count_launch(1);
+}
+
+void launch_nh_half(int n, int n_sys, const int* sys_ptr, const int* sys_of, double* v,
+                    const double* mass, double* ke, double* scale, double* thermo, double dt,
+                    double kT, double tau, cudaStream_t s) {
+  if (n <= 0 || n_sys <= 0) return;
+  launch_kinetic(v, mass, sys_ptr, n_sys, ke, s);
+  ProfScope ps_(PC_MD, s);
+  k_nh_update<<<ff_cdiv(n_sys, 128), 128, 0, s>>>(n_sys, sys_ptr, ke, thermo, scale, dt, kT, tau);
+  k_scale_v<<<ff_cdiv(3LL * n, 256), 256, 0, s>>>(3LL * n, sys_of, scale, v);
+  ff_count_launch(2);
+}
+
+void launch_nh_energy(int n_sys, const int* sys_ptr, const double* epot, const double* ke,
+                      const double* thermo, double kT, double tau, double* H, cudaStream_t s) {
+  ProfScope ps_(PC_MD, s);
+  if (n_sys <= 0) return;
+  k_nh_energy<<<ff_cdiv(n_sys, 128), 128, 0, s>>>(n_sys, sys_ptr, epot, ke, thermo, kT, tau, H);
   ff_count_launch(1);
 }
 

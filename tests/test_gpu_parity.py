@@ -379,3 +379,34 @@ def test_table1_model_sizes(ff, model, precision):
         d = F.double().cpu().numpy() - F_ref
         assert np.sqrt((d ** 2).mean()) <= 5e-3 and np.abs(d).max() <= 5e-3
         assert abs(Es.item() - E_ref[0]) <= 4e-3 * np.abs(Ea_ref).sum()
+
+
+def test_nvt_matches_oracle_trajectory(ff):
+    s = synth.config1_system()
+    hp = synth.preset("small", skin=0.5)
+    m, pos = _bind(ff, hp, s)
+    v0 = synth.maxwell_boltzmann(s.masses, 100.0, seed=6)
+    x = pos.clone()
+    v = _dev(v0, torch.float64)
+    mass = _dev(s.masses, torch.float64)
+    Ep, Ek, H, thermo = m.md_nvt(x, v, mass, 8, 1.0, 600.0, 20.0)
+    xr, vr, ep, ek, hr, xi, eta = omd.run_nvt(Allegro64(hp, 42), s.pos, v0, s.Z, s.box, s.pbc,
+                                              s.masses, 1.0, 8, 600.0, 20.0)
+    assert np.abs(x.cpu().numpy() - xr).max() < 1e-7
+    assert np.abs(v.cpu().numpy() - vr).max() < 1e-8
+    np.testing.assert_allclose(Ep.cpu().numpy(), ep, rtol=E_REL)
+    np.testing.assert_allclose(Ek.cpu().numpy(), ek, rtol=1e-6)
+    np.testing.assert_allclose(H.cpu().numpy(), hr, rtol=1e-6)
+    np.testing.assert_allclose(thermo.cpu().numpy()[0], [xi, eta], rtol=1e-5, atol=1e-12)
+
+
+@pytest.mark.parametrize("precision,rtol", [(0, 1e-5), (1, 2e-2)])
+def test_virial_matches_oracle(ff, precision, rtol):
+    from oracle import Allegro64 as A
+    s = synth.csh_system(sub=True)
+    hp = _hp("fm_water", "csh512")
+    m, pos = _bind(ff, hp, s, precision=precision)
+    m.energy_forces(pos)
+    W = m.virial()[0].cpu().numpy()
+    Wr = A(hp, 42).virial(s.pos, s.Z, s.box, s.pbc)[0]
+    assert np.abs(W - Wr).max() <= rtol * np.abs(Wr).max(), (W, Wr)

@@ -203,3 +203,65 @@ def test_nve_energy_fluctuation_scales_dt2(small):
         et = ep + ek
         fl.append(et.max() - et.min())
     assert 3.0 < fl[0] / fl[1] < 5.0, fl
+
+
+def test_virial_matches_strain_derivative_cluster(small):
+    """Non-periodic cluster: every component of dE/d(eps) by central differences of a
+    homogeneous strain equals -W^T."""
+    s = synth.cluster_system(10, seed=12)
+    W = small.virial(s.pos, s.Z, s.box, s.pbc)[0]
+    c = s.pos.mean(axis=0)
+    h = 1e-5
+    for a in range(3):
+        for b in range(3):
+            eps = np.zeros((3, 3))
+            eps[a, b] = h
+            Ep = small.evaluate((s.pos - c) @ (np.eye(3) + eps).T + c, s.Z, s.box, s.pbc,
+                                forces=False)[0][0]
+            Em = small.evaluate((s.pos - c) @ (np.eye(3) - eps).T + c, s.Z, s.box, s.pbc,
+                                forces=False)[0][0]
+            assert abs((Ep - Em) / (2 * h) + W[b, a]) < 1e-7, (a, b)
+    np.testing.assert_allclose(W, W.T, atol=1e-10)      # rotation invariance
+
+
+def test_virial_matches_box_strain_periodic(small, cfg1):
+    """Periodic box: scaling one box edge together with the positions."""
+    s = cfg1[0]
+    W = small.virial(s.pos, s.Z, s.box, s.pbc)[0]
+    h = 1e-5
+    for a in range(3):
+        sc = np.ones(3)
+        sc[a] = 1 + h
+        Ep = small.evaluate(s.pos * sc, s.Z, s.box * sc, s.pbc, forces=False)[0][0]
+        sc[a] = 1 - h
+        Em = small.evaluate(s.pos * sc, s.Z, s.box * sc, s.pbc, forces=False)[0][0]
+        assert abs((Ep - Em) / (2 * h) + W[a, a]) < 1e-7, a
+
+
+def test_nvt_conserved_quantity_scales_dt2_and_large_q_is_nve(small):
+    s = synth.cluster_system(12, seed=8, radius=2.6)
+    m = s.masses
+    v0 = synth.maxwell_boltzmann(m, 900.0, seed=2)
+    fl = []
+    for dt, n in ((2.0, 20), (1.0, 40)):
+        *_, H, _, _ = md.run_nvt(small, s.pos, v0, s.Z, s.box, s.pbc, m, dt, n, 300.0, 20.0)
+        fl.append(H.max() - H.min())
+    assert 3.0 < fl[0] / fl[1] < 5.0, fl
+    # an infinitely heavy thermostat leaves the NVE trajectory
+    x1, v1, ep1, ek1, *_ = md.run_nvt(small, s.pos, v0, s.Z, s.box, s.pbc, m, 1.0, 10, 300.0, 1e12)
+    x2, v2, ep2, ek2 = md.run_nve(small, s.pos, v0, s.Z, s.box, s.pbc, m, 1.0, 10)
+    np.testing.assert_allclose(x1, x2, atol=1e-12)
+    np.testing.assert_allclose(v1, v2, atol=1e-12)
+
+
+def test_nvt_drives_temperature_towards_target(small):
+    """Nose-Hoover feedback sign: a cold start (50 K) under a 600 K thermostat heats up,
+    a hot start (6000 K) under a 300 K thermostat cools down."""
+    s = synth.cluster_system(12, seed=8, radius=2.6)
+    m = s.masses
+    v0 = synth.maxwell_boltzmann(m, 50.0, seed=2)
+    *_, ek, H, xi, _ = md.run_nvt(small, s.pos, v0, s.Z, s.box, s.pbc, m, 1.0, 30, 600.0, 10.0)
+    assert ek.max() > 2.0 * md.kinetic(v0, m)
+    v1 = synth.maxwell_boltzmann(m, 6000.0, seed=2)
+    *_, ek, H, xi, _ = md.run_nvt(small, s.pos, v1, s.Z, s.box, s.pbc, m, 1.0, 30, 300.0, 10.0)
+    assert ek.min() < 0.5 * md.kinetic(v1, m)
