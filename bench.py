@@ -51,6 +51,10 @@ WORKLOADS = {
     "sio2_4194304": dict(desc="SiO2-like solid, 4,194,304 atoms, 2.2 g/cm3, L = 398.75 A",
                          make=lambda: synth.sio2_system(162, 4194304, 1004),
                          model="fm_water", nu="sio2_4194304"),
+    "csh_np6326": dict(desc="C-S-H nanoparticle in H2O/CO2, 6,326 atoms (267 C, 90 Ca, 133 Si, "
+                            "2,577 O, 3,259 H), periodic (45.7 A)^3",
+                       make=lambda: synth.nanoparticle_mixture_system(1005), model="fm_water",
+                       nu="csh_np6326"),
     "molecules1024": dict(desc="1,024 organic molecules (7-23 heavy atoms + H), non-periodic",
                           make=lambda: synth.molecules_system(1024, 1003), model="fm_water",
                           nu="molecules1024"),
@@ -425,6 +429,17 @@ def run_ours(args):
         roof = {"kernel": dom_name, "bound": "alu", "achieved": None, "peak": None,
                 "unit": None, "frac": None, "traffic": None}
 
+    # ---- NVE energy drift (optional): linear fit of E_pot + E_kin per atom over a run
+    drift = None
+    if args.drift_steps > 0 and rank == 0:
+        Ep, Ek = model.md(x, v, mass, args.drift_steps, dt_fs, energies=True)
+        et = (Ep + Ek).cpu().numpy() / s.n
+        tt = np.arange(1, args.drift_steps + 1) * dt_fs * 1e-6            # ns
+        slope = float(np.polyfit(tt, et, 1)[0])
+        drift = {"eV_per_atom_per_ns": slope, "steps": args.drift_steps, "dt_fs": dt_fs,
+                 "fluctuation_eV_per_atom": float(et.std()),
+                 "E_tot_first_last_eV_per_atom": [float(et[0]), float(et[-1])]}
+
     # ---- CPU-baseline leg: the FP64 oracle on a bounded sample of this workload (the
     # neighbourhoods of a few atoms at the final positions), timed; the same oracle
     # results give the force error of this run's path on those atoms
@@ -459,6 +474,7 @@ def run_ours(args):
             "profiled_ms_per_step": sum(prof_ms) / args.steps,
             "step_ms": [round(t, 3) for t in step_ms],
             "force_error": ferr,
+            "nve_drift": drift,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -475,6 +491,8 @@ def main():
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1],
                     help="1: BF16 tensor-core MLPs (default); 0: plain FP32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--drift-steps", type=int, default=0,
+                    help="after timing, run this many NVE steps and fit the energy drift")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the tensor-core GEMM tile configuration before timing")
     ap.add_argument("--graph", action="store_true",

@@ -29,7 +29,8 @@ PRESETS = {"small": SMALL, "fm_water": FM_WATER, "fm64": FM64, "fm256": FM256,
 # nu per workload: 4/3*pi*rc^3*n rounded for the bulk systems (rc = 6 A unless the preset
 # says otherwise); for the isolated molecules the batch mean of neighbours within 6 A
 NU = {"cubic96": 50.0, "water12288": 91.0, "water4095": 91.0, "csh131072": 82.0,
-      "csh512": 82.0, "sio2_4194304": 60.0, "sio2_4096": 60.0, "molecules1024": 33.0}
+      "csh512": 82.0, "sio2_4194304": 60.0, "sio2_4096": 60.0, "molecules1024": 33.0,
+      "csh_np6326": 60.0}
 
 
 def preset(name, **over):

@@ -256,6 +256,89 @@ def molecules_system(n_mol=1024, seed=1003, noise=0.05):
                   dict(seed=seed))
 
 
+def nanoparticle_mixture_system(seed=1005):
+    """Stand-in for the paper's reactive MD system (Methodology, MD Simulations of C-S-H
+    Nanoparticle Reaction): 6,326 atoms -- 267 C, 90 Ca, 133 Si, 2,577 O, 3,259 H -- in a
+    periodic (45.7 A)^3 box, a C-S-H nanoparticle immersed in H2O and CO2.
+
+    Reading of the composition (the paper gives only the totals): all carbon is CO2 (267
+    molecules), the particle has Ca 90, Si 133 and the C-S-H ratio O/Si = 5.4 (718 O), the
+    rest of the oxygen is water (1,325 H2O) and the rest of the hydrogen (609) sits in
+    the particle.  The particle is a sphere of jittered lattice sites (2.228 A, the C-S-H
+    density) at the box centre; molecule centres are placed outside it by random
+    sequential addition (2.6 A exclusion), with random orientations.
+    """
+    rng = np.random.default_rng(seed)
+    L = 45.7
+    box = np.array([L, L, L])
+    n_np = {20: 90, 14: 133, 8: 718, 1: 609}
+    n_co2, n_h2o = 267, 1325
+    # particle: the sum(n_np) lattice sites closest to the centre
+    sp = 2.228
+    k = int(np.ceil(L / sp))
+    g = (np.stack(np.meshgrid(np.arange(k), np.arange(k), np.arange(k), indexing="ij"), -1)
+         .reshape(-1, 3) + 0.5) * sp
+    c = np.array([L / 2] * 3)
+    d = np.linalg.norm(g - c, axis=1)
+    n_p = sum(n_np.values())
+    sites = g[np.argsort(d, kind="stable")[:n_p]]
+    r_np = np.linalg.norm(sites - c, axis=1).max()
+    p_pos = sites + rng.normal(0.0, 0.1, size=sites.shape)
+    p_Z = np.concatenate([np.full(v, z) for z, v in n_np.items()])
+    rng.shuffle(p_Z)
+    # fluid molecules by random sequential addition outside the particle
+    kinds = np.array([0] * n_co2 + [1] * n_h2o)
+    rng.shuffle(kinds)
+    centres = []
+    dmin = 2.6
+    ncell = int(L // dmin)
+    cw = L / ncell
+    grid = {}
+    for _ in kinds:
+        for _try in range(10000):
+            p = rng.uniform(0.0, L, size=3)
+            dc = p - c
+            dc -= L * np.round(dc / L)
+            if np.linalg.norm(dc) < r_np + 1.8:
+                continue
+            cc = tuple((p // cw).astype(int) % ncell)
+            ok = True
+            for dx in (-1, 0, 1):
+                for dy in (-1, 0, 1):
+                    for dz in (-1, 0, 1):
+                        for q in grid.get(((cc[0] + dx) % ncell, (cc[1] + dy) % ncell,
+                                           (cc[2] + dz) % ncell), ()):
+                            dd = p - q
+                            dd -= L * np.round(dd / L)
+                            if dd @ dd < dmin * dmin:
+                                ok = False
+            if ok:
+                grid.setdefault(cc, []).append(p)
+                centres.append(p)
+                break
+        else:
+            raise RuntimeError("fluid packing failed")
+    f_pos, f_Z = [], []
+    for kind, p in zip(kinds, centres):
+        R = _random_rotation(rng)
+        if kind == 0:       # CO2: O=C=O, 1.16 A
+            ax = R @ np.array([1.0, 0.0, 0.0])
+            f_pos += [p, p + 1.16 * ax, p - 1.16 * ax]
+            f_Z += [6, 8, 8]
+        else:               # H2O
+            r1, r2 = rng.uniform(0.94, 0.98, size=2)
+            th = math.radians(rng.uniform(101.5, 107.5))
+            f_pos += [p, p + r1 * (R @ np.array([1.0, 0.0, 0.0])),
+                      p + r2 * (R @ np.array([math.cos(th), math.sin(th), 0.0]))]
+            f_Z += [8, 1, 1]
+    pos = np.concatenate([p_pos, np.array(f_pos)])
+    Z = np.concatenate([p_Z, np.array(f_Z)]).astype(np.int32)
+    pbc = np.array([True, True, True])
+    pos = _round_f32(pos, box, pbc)
+    return System("csh_np6326", pos, Z, box, pbc, np.array([0, pos.shape[0]], dtype=np.int32),
+                  dict(seed=seed, n_particle=n_p, r_particle=float(r_np)))
+
+
 def dimer_system(r, Zi=8, Zj=1, direction=(1.0, 0.0, 0.0), L=None):
     """Two atoms at distance r along `direction`; non-periodic unless L is given."""
     d = np.asarray(direction, dtype=np.float64)
@@ -309,6 +392,7 @@ def bench_workloads():
         "csh131072": dict(make=lambda: csh_system(False, 1002), model="fm_water"),
         "csh512": dict(make=lambda: csh_system(True, 1002), model="fm_water"),
         "molecules1024": dict(make=lambda: molecules_system(1024, 1003), model="fm_water"),
+        "csh_np6326": dict(make=lambda: nanoparticle_mixture_system(1005), model="fm_water"),
         "sio2_4194304": dict(make=lambda: sio2_system(162, 4194304, 1004), model="fm_water"),
         "sio2_4096": dict(make=lambda: sio2_system(16, 4096, 1004), model="fm_water"),
     }

@@ -410,3 +410,19 @@ def test_virial_matches_oracle(ff, precision, rtol):
     W = m.virial()[0].cpu().numpy()
     Wr = A(hp, 42).virial(s.pos, s.Z, s.box, s.pbc)[0]
     assert np.abs(W - Wr).max() <= rtol * np.abs(Wr).max(), (W, Wr)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_nanoparticle_mixture_system(ff, precision):
+    """The paper's reactive MD system shape (6,326 atoms, C-S-H particle in H2O/CO2): uneven
+    neighbour counts (36..82 per atom) across the particle surface."""
+    s = synth.nanoparticle_mixture_system()
+    hp = _hp("fm_water", "csh_np6326")
+    m, pos = _bind(ff, hp, s, precision=precision)
+    Es, Ea, F = m.energy_forces(pos)
+    E_ref, Ea_ref, F_ref = pool.evaluate(hp, 42, s.pos, s.Z, s.box, s.pbc)
+    if precision == 0:
+        _check_ef(Es, Ea, F, E_ref, Ea_ref, F_ref, "csh_np6326")
+    else:
+        d = F.double().cpu().numpy() - F_ref
+        assert np.sqrt((d ** 2).mean()) <= 5e-3 and np.abs(d).max() <= 5e-3
