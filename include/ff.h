@@ -46,7 +46,7 @@ enum {
 };
 
 /* Largest number of neighbours within rc + skin of one atom. */
-#define FF_MAX_NEIGHBORS 512
+#define FF_MAX_NEIGHBORS 1024
 
 /* Hyperparameters (Table 1 of the paper names the widths; the rest are readings).
  *   rc                radial cutoff (A); skin: Verlet-list skin (A, >= 0)
