@@ -92,9 +92,23 @@ inline double init_weight(uint64_t seed, uint64_t t, uint64_t k) {
   return sqrt(3.0) * (2.0 * u - 1.0);
 }
 
-const TPKindInfo* tp_kind(int lmax, int in_kind, int last) {
+// Input/output kind of layer L of n_layers (the tensor-product kernels' template keys):
+// output kind 2 for the last layer (0e only), 1 for the layer before it (natural-parity
+// irreps only: no other output reaches a 0e output of the last layer), 0 otherwise; input
+// kind 0 for the first layer, 3 (natural irreps from memory) for a last layer after it,
+// else 1 after the first layer and 2 after later ones.
+void layer_kinds(int L, int n_layers, int* ink, int* outk) {
+  *outk = L == n_layers ? 2 : (L == n_layers - 1 ? 1 : 0);
+  if (L == 1) *ink = 0;
+  else if (L == n_layers) *ink = 3;
+  else *ink = std::min(L - 1, 2);
+}
+
+const TPKindInfo* tp_kind(int lmax, int in_kind, int out_kind) {
+  const int irr = in_kind == 3 ? 0 : in_kind;
   for (int i = 0; i < kNumTPKinds; ++i)
-    if (kTPKinds[i].lmax == lmax && kTPKinds[i].in_kind == in_kind && kTPKinds[i].last == last)
+    if (kTPKinds[i].lmax == lmax && kTPKinds[i].in_kind == irr &&
+        kTPKinds[i].out_kind == out_kind)
       return &kTPKinds[i];
   return nullptr;
 }
@@ -117,6 +131,7 @@ struct ff_ctx {
   int cgroups = 1;     // channel groups of 32 in the tensor-product kernels (C > 32)
   int layer_np[FF_MAX_LAYERS + 1] = {0}, layer_dout[FF_MAX_LAYERS + 1] = {0};
   int layer_din[FF_MAX_LAYERS + 1] = {0};
+  int layer_ink[FF_MAX_LAYERS + 1] = {0}, layer_outk[FF_MAX_LAYERS + 1] = {0};
   std::vector<Tensor> tensors;
   std::vector<double> params;
   // device weights
@@ -295,7 +310,8 @@ void build_structure(ff_ctx* c) {
   for (int k = 0; k < hp.n_latent; ++k) c->maxw = std::max(c->maxw, hp.latent[k]);
   c->maxdim = 1;
   for (int L = 1; L <= c->NL; ++L) {
-    const TPKindInfo* k = tp_kind(c->lmax, std::min(L - 1, 2), L == c->NL ? 1 : 0);
+    layer_kinds(L, c->NL, &c->layer_ink[L], &c->layer_outk[L]);
+    const TPKindInfo* k = tp_kind(c->lmax, c->layer_ink[L], c->layer_outk[L]);
     c->layer_np[L] = k->n_paths;
     c->layer_din[L] = k->dim_in;
     c->layer_dout[L] = k->dim_out;
@@ -445,6 +461,10 @@ void free_workspace(ff_ctx* c) {
 }
 
 // Carve every per-chunk buffer from one allocation sized for `ecap` edges / `acap` atoms.
+// Harmonic-gradient slices per edge: one per (layer, channel group) for the fan-out of the
+// environment adjoint, plus one per channel group for the layer-1 term of V^0 = w (x) Y.
+int gy_slices(const ff_ctx* c) { return (c->NL + 1) * c->cgroups; }
+
 int ensure_workspace(ff_ctx* c, long long ecap, int acap, long long budget_edges) {
   if (ecap <= c->wcap && acap <= c->acap) return FF_OK;
   // grow with headroom (edge counts drift from step to step in MD, and every regrowth is
@@ -490,7 +510,7 @@ int ensure_workspace(ff_ctx* c, long long ecap, int acap, long long budget_edges
     f32(&c->gV[b], ecap * (long long)c->maxdim * c->C);
   }
   f32(&c->GW, ecap * c->ldw);
-  f32(&c->gY, ecap * 9 * c->cgroups);
+  f32(&c->gY, ecap * 9 * gy_slices(c));
   f32(&c->gf, ecap);
   if (tc) {
     b16(&c->GZb[0], ecap * c->maxw);
@@ -529,7 +549,7 @@ size_t bytes_per_edge(const ff_ctx* c) {
     if (L < c->NL) b += (size_t)c->layer_dout[L] * c->C * 4;
   }
   b += 2 * ((size_t)c->ldx + c->maxw + (size_t)c->maxdim * c->C) * 4;
-  b += (size_t)c->ldw * 4 + 9 * 4 * (size_t)c->cgroups + 4;
+  b += (size_t)c->ldw * 4 + 9 * 4 * (size_t)gy_slices(c) + 4;
   if (hp.precision == 1)   // bf16 operands (the fp32 hidden activations are not kept)
     b += (size_t)(c->NL + 1) * c->ldx * 2 + 2 * (size_t)c->maxw * 2 + (size_t)c->ldw * 2;
   return b;
@@ -759,8 +779,8 @@ void forward_chunk(ff_ctx* c, const double* pos, int a0, int a1, float* E_atom, 
     mlp_gemm(c, EPI_STORE, Ec, c->ldw, c->D, c->X[L - 1], c->Xb[L - 1], c->ldx, c->Wenv[L],
              c->WenvT_b[L], ep, s);
     const int last = L == c->NL ? 1 : 0;
-    launch_env_tp_fwd(c->lmax, std::min(L - 1, 2), last, c->C, na, rp, e0, c->ef, c->Wv[L],
-                      c->ldw, L >= 2 ? c->V[L - 1] : nullptr, last ? nullptr : c->theta[L],
+    launch_env_tp_fwd(c->lmax, c->layer_ink[L], c->layer_outk[L], c->C, na, rp, e0, c->ef,
+                      c->Wv[L], c->ldw, L >= 2 ? c->V[L - 1] : nullptr, last ? nullptr : c->theta[L],
                       c->X[L - 1], tc ? c->Xb[L - 1] : nullptr, c->ldx, c->D,
                       last ? nullptr : c->V[L], c->Gam[L], inv_sqrt_nu, s);
     const float* A32 = c->X[L - 1];
@@ -802,7 +822,6 @@ void backward_chunk(ff_ctx* c, int a0, int a1, const double* seed, cudaStream_t 
   const int* rp = c->row_ptr + a0;
   const int na = a1 - a0;
   cudaMemsetAsync(c->gf, 0, (size_t)Ec * sizeof(float), s);
-  cudaMemsetAsync(c->gY, 0, (size_t)Ec * 9 * c->cgroups * sizeof(float), s);
   const float* gx = c->w_eff;
   int ldgx = 0;
   int cur = 0, gvb = 0;
@@ -833,11 +852,13 @@ void backward_chunk(ff_ctx* c, int a0, int a1, const double* seed, cudaStream_t 
                c->WlatT[L][0], c->Wlat_b[L][0], ep, s);
     }
     const int last = L == c->NL ? 1 : 0;
-    launch_env_tp_bwd(c->lmax, std::min(L - 1, 2), last, c->C, na, rp, e0, c->ef, c->Wv[L],
-                      c->ldw, L >= 2 ? c->V[L - 1] : nullptr, last ? nullptr : c->theta[L],
+    launch_env_tp_bwd(c->lmax, c->layer_ink[L], c->layer_outk[L], c->C, na, rp, e0, c->ef,
+                      c->Wv[L], c->ldw, L >= 2 ? c->V[L - 1] : nullptr, last ? nullptr : c->theta[L],
                       c->GX[cur], c->ldx, c->D, last ? nullptr : c->gV[gvb],
-                      L >= 2 ? c->gV[gvb ^ 1] : nullptr, c->GW, tc ? c->GWb : nullptr, c->gY,
-                      c->Gam[L], inv_sqrt_nu, s);
+                      L >= 2 ? c->gV[gvb ^ 1] : nullptr, c->GW, tc ? c->GWb : nullptr,
+                      c->gY + (size_t)c->NL * c->cgroups * 9,
+                      c->gY + (size_t)(L - 1) * c->cgroups * 9, 9 * gy_slices(c), c->Gam[L],
+                      inv_sqrt_nu, s);
     {
       EpiParams ep{};
       ep.alpha = (float)(1.0 / sqrt((double)c->D));
@@ -870,7 +891,7 @@ void backward_chunk(ff_ctx* c, int a0, int a1, const double* seed, cudaStream_t 
   const int w0 = hp.two_body[0];
   const float a0f = (float)(1.0 / sqrt((double)(2 * FF_N_SPECIES + hp.n_basis)));
   launch_edge_grad(Ec, w0, hp.n_basis, hp.rc, hp.poly_p, c->lmax, c->ef, c->GZ[gzb], w0,
-                   c->W2b[0] + (size_t)2 * FF_N_SPECIES * w0, a0f, c->gf, c->gY, c->cgroups,
+                   c->W2b[0] + (size_t)2 * FF_N_SPECIES * w0, a0f, c->gf, c->gY, gy_slices(c),
                    c->src + e0, c->sys_of, seed, c->g + e0, s);
 }
 

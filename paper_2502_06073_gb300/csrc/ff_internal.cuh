@@ -122,16 +122,17 @@ void launch_edge_features(long long E, const int* src, const int* col, const int
 void launch_twobody_in(long long E, int width, int n_basis, const float* ef, const int* zz,
                        const float* W0, float alpha, float* pre, float* out, int ldo,
                        __nv_bfloat16* outb, int ldob, int final_layer, cudaStream_t s);
-void launch_env_tp_fwd(int lmax, int in_kind, int last, int C, int n_atoms,
+void launch_env_tp_fwd(int lmax, int in_kind, int out_kind, int C, int n_atoms,
                        const int* row_ptr, int e0, const float* ef, const float* W, int ldw,
                        const float* Vin, const float* theta, float* X, __nv_bfloat16* Xb,
                        int ldx, int D, float* Vout, float* Gam, float inv_sqrt_nu,
                        cudaStream_t s);
-void launch_env_tp_bwd(int lmax, int in_kind, int last, int C, int n_atoms,
+void launch_env_tp_bwd(int lmax, int in_kind, int out_kind, int C, int n_atoms,
                        const int* row_ptr, int e0, const float* ef, const float* W, int ldw,
                        const float* Vin, const float* theta, const float* GX, int ldx, int D,
                        const float* gVout, float* gVin, float* GW, __nv_bfloat16* GWb,
-                       float* gY, const float* Gam, float inv_sqrt_nu, cudaStream_t s);
+                       float* gY_v0, float* gY_env, int gy_stride, const float* Gam,
+                       float inv_sqrt_nu, cudaStream_t s);
 void launch_energy(int n_atoms, const int* row_ptr, int e0, const float* X, int ldx, int D,
                    const float* w_eff, float* E_atom, cudaStream_t s);
 void launch_rowred_bwd(long long E, int N, const float* gx, int ldgx, const float* z, int ldz,

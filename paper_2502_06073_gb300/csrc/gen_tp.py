@@ -13,8 +13,14 @@ Irreps are (l, p); per-channel feature vectors list their irreps by l and, withi
 natural parity (-1)^l first.  A layer couples every input irrep (l1, p1) with the
 environment irreps (l2, (-1)^l2), l2 = 0..lmax, into (l3, p1 (-1)^l2) for
 |l1 - l2| <= l3 <= min(l1 + l2, lmax); the last layer keeps only the 0e outputs.
-Layer kinds: in-kind 0 = natural irreps (first layer), 1 = the outputs of a first
-layer, 2 = the outputs of a later layer (all irreps reachable).
+Input kinds: 0 = natural irreps (first layer), 1 = the outputs of a first layer, 2 = the
+outputs of a later layer (all irreps reachable).
+Output kinds: 0 = every reachable irrep, 1 = natural-parity irreps only, 2 = 0e only (the
+last layer).  Kind 1 is the layer before the last: a 0e output of the last layer couples
+(l1, p1) with (l2, (-1)^l2) only for l1 = l2 and p1 = (-1)^l1, so the other outputs of
+that layer never reach the energy and are not computed.  Path weights keep the index of
+the path in the full list of the layer, and the 1/sqrt(n) mixing counts all paths into
+an irrep, so the kept outputs are exactly those of the full layer.
 
 Usage: python gen_tp.py [output path]   (default: tp_gen.cuh next to this file)
 """
@@ -137,6 +143,25 @@ def layer(in_irreps, lmax, last):
     return paths, canon([p[2] for p in paths])
 
 
+def natural(ir):
+    return ir[1] == (-1) ** ir[0]
+
+
+# (input kind, output kind) pairs the layers of a model with 1..4 layers use
+KINDS = ((0, 0), (0, 1), (0, 2), (1, 0), (1, 1), (2, 1))
+
+
+def layer_kinds(L, n_layers):
+    """(input kind, output kind) of layer L; input kind 3 = natural irreps read from the
+    previous layer's output (same products as input kind 0)."""
+    outk = 2 if L == n_layers else (1 if L == n_layers - 1 else 0)
+    if L == 1:
+        return 0, outk
+    if L == n_layers:
+        return 3, outk
+    return min(L - 1, 2), outk
+
+
 def in_irreps_of(lmax, in_kind):
     irr = [(l, (-1) ** l) for l in range(lmax + 1)]
     for _ in range(in_kind):
@@ -159,27 +184,31 @@ def fl(x):
     return s + "f"
 
 
-def gen_kind(lmax, in_kind, last):
+def gen_kind(lmax, in_kind, out_kind):
+    last = out_kind == 2
     irr_in = in_irreps_of(lmax, in_kind)
-    paths, outs = layer(irr_in, lmax, last)
+    full, full_outs = layer(irr_in, lmax, last)
+    n_into = {o: sum(1 for p in full if p[2] == o) for o in full_outs}
+    scal = [q for q, p in enumerate(full) if p[2] == (0, 1)]
+    # kept paths with their index in the full list (path weights, scalar order)
+    kept = [(q, p) for q, p in enumerate(full) if out_kind != 1 or natural(p[2])]
+    outs = [o for o in full_outs if out_kind != 1 or natural(o)]
     off_in, din = offsets(irr_in)
     off_out, dout = offsets(outs) if not last else ([], 0)
     goff = [l * l for l in range(lmax + 1)]
-    n_into = {o: sum(1 for p in paths if p[2] == o) for o in outs}
-    scal = [q for q, p in enumerate(paths) if p[2] == (0, 1)]
-    name = f"TP<{lmax}, {in_kind}, {int(last)}>"
+    name = f"TP<{lmax}, {in_kind}, {out_kind}>"
     lines = []
-    lines.append(f"template <> struct TP<{lmax}, {in_kind}, {int(last)}> {{")
+    lines.append(f"template <> struct TP<{lmax}, {in_kind}, {out_kind}> {{")
     lines.append(f"  // in irreps {irr_in}; out irreps {outs if not last else [(0, 1)]}")
-    lines.append(f"  static constexpr int NP = {len(paths)}, DIN = {din}, "
-                 f"DOUT = {max(dout, 1)}, NS = {len(scal)}, NPW = {0 if last else len(paths)};")
+    lines.append(f"  static constexpr int NP = {len(full)}, DIN = {din}, "
+                 f"DOUT = {max(dout, 1)}, NS = {len(scal)}, NPW = {0 if last else len(full)};")
     # forward
     lines.append("  static __device__ __forceinline__ void fwd(const float* __restrict__ v, "
                  "const float* __restrict__ g, const float* __restrict__ th, float* s, float* vo) {")
     if not last:
         lines.append(f"    #pragma unroll\n    for (int k = 0; k < {dout}; ++k) vo[k] = 0.f;")
     nnz_total = 0
-    for q, (i_in, l2, out) in enumerate(paths):
+    for q, (i_in, l2, out) in kept:
         l1 = irr_in[i_in][0]
         l3 = out[0]
         C = coupling_real(l1, l2, l3)
@@ -205,7 +234,7 @@ def gen_kind(lmax, in_kind, last):
                  "const float* __restrict__ g, const float* __restrict__ th, "
                  "const float* __restrict__ gs, const float* __restrict__ gvo, "
                  "float* gv, float* gg) {")
-    for q, (i_in, l2, out) in enumerate(paths):
+    for q, (i_in, l2, out) in kept:
         l1 = irr_in[i_in][0]
         l3 = out[0]
         C = coupling_real(l1, l2, l3)
@@ -229,35 +258,37 @@ def gen_kind(lmax, in_kind, last):
     lines.append("  }")
     lines.append(f"  static constexpr int NNZ = {nnz_total};")
     lines.append("};")
-    return name, lines, dict(np=len(paths), din=din, dout=dout, ns=len(scal), nnz=nnz_total,
-                             irr_in=irr_in, outs=outs)
+    return name, lines, dict(np=len(full), kept=len(kept), din=din, dout=dout, ns=len(scal),
+                             nnz=nnz_total, irr_in=irr_in, outs=outs)
 
 
 def main(out_path):
     body = []
     table = []
     for lmax in LMAX_SUPPORTED:
-        for in_kind in range(3):
-            for last in (False, True):
-                _, lines, info = gen_kind(lmax, in_kind, last)
-                body.extend(lines)
-                body.append("")
-                table.append((lmax, in_kind, int(last), info))
+        for in_kind, out_kind in KINDS:
+            _, lines, info = gen_kind(lmax, in_kind, out_kind)
+            body.extend(lines)
+            body.append("")
+            table.append((lmax, in_kind, out_kind, info))
     hdr = [
         "// Generated by gen_tp.py -- do not edit.  Unrolled real Clebsch-Gordan tensor",
         "// products (Racah formula + complex-to-real basis change), per channel.",
         "// fwd: T_path = C (v_in x g); s[] = 0e outputs; vo[] = sum theta_path T / sqrt(n).",
         "// bwd: given gs (d/ds) and gvo (d/dvo): gv += dT/dv^T gT, gg += dT/dg^T gT.",
+        "// Output kind 0: all reachable irreps, 1: natural-parity irreps, 2: 0e only.",
         "#pragma once",
         "",
-        "template <int LMAX, int INK, int LAST> struct TP;",
+        "template <int LMAX, int INK, int OUTK> struct TP;",
         "",
-        "struct TPKindInfo { int lmax, in_kind, last, n_paths, dim_in, dim_out, n_scalar, nnz; };",
+        "struct TPKindInfo {",
+        "  int lmax, in_kind, out_kind, n_paths, n_kept, dim_in, dim_out, n_scalar, nnz;",
+        "};",
         "static const TPKindInfo kTPKinds[] = {",
     ]
-    for (lmax, ink, last, info) in table:
-        hdr.append(f"  {{{lmax}, {ink}, {last}, {info['np']}, {info['din']}, {info['dout']}, "
-                   f"{info['ns']}, {info['nnz']}}},")
+    for (lmax, ink, outk, info) in table:
+        hdr.append(f"  {{{lmax}, {ink}, {outk}, {info['np']}, {info['kept']}, {info['din']}, "
+                   f"{info['dout']}, {info['ns']}, {info['nnz']}}},")
     hdr.append("};")
     hdr.append(f"static const int kNumTPKinds = {len(table)};")
     hdr.append("")

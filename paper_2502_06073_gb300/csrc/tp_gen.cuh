@@ -2,24 +2,27 @@
 // products (Racah formula + complex-to-real basis change), per channel.
 // fwd: T_path = C (v_in x g); s[] = 0e outputs; vo[] = sum theta_path T / sqrt(n).
 // bwd: given gs (d/ds) and gvo (d/dvo): gv += dT/dv^T gT, gg += dT/dg^T gT.
+// Output kind 0: all reachable irreps, 1: natural-parity irreps, 2: 0e only.
 #pragma once
 
-template <int LMAX, int INK, int LAST> struct TP;
+template <int LMAX, int INK, int OUTK> struct TP;
 
-struct TPKindInfo { int lmax, in_kind, last, n_paths, dim_in, dim_out, n_scalar, nnz; };
+struct TPKindInfo {
+  int lmax, in_kind, out_kind, n_paths, n_kept, dim_in, dim_out, n_scalar, nnz;
+};
 static const TPKindInfo kTPKinds[] = {
-  {1, 0, 0, 5, 4, 7, 2, 16},
-  {1, 0, 1, 2, 4, 0, 2, 4},
-  {1, 1, 0, 8, 7, 8, 2, 28},
-  {1, 1, 1, 2, 7, 0, 2, 4},
-  {1, 2, 0, 10, 8, 8, 2, 32},
-  {1, 2, 1, 2, 8, 0, 2, 4},
-  {2, 0, 0, 15, 9, 17, 3, 137},
-  {2, 0, 1, 3, 9, 0, 3, 9},
-  {2, 1, 0, 27, 17, 18, 3, 265},
-  {2, 1, 1, 3, 17, 0, 3, 9},
-  {2, 2, 0, 30, 18, 18, 3, 274},
-  {2, 2, 1, 3, 18, 0, 3, 9},
+  {1, 0, 0, 5, 5, 4, 7, 2, 16},
+  {1, 0, 1, 5, 4, 4, 4, 2, 10},
+  {1, 0, 2, 2, 2, 4, 0, 2, 4},
+  {1, 1, 0, 8, 8, 7, 8, 2, 28},
+  {1, 1, 1, 8, 5, 7, 4, 2, 16},
+  {1, 2, 1, 10, 5, 8, 4, 2, 16},
+  {2, 0, 0, 15, 15, 9, 17, 3, 137},
+  {2, 0, 1, 15, 11, 9, 9, 3, 83},
+  {2, 0, 2, 3, 3, 9, 0, 3, 9},
+  {2, 1, 0, 27, 27, 17, 18, 3, 265},
+  {2, 1, 1, 27, 15, 17, 9, 3, 137},
+  {2, 2, 1, 30, 15, 18, 9, 3, 137},
 };
 static const int kNumTPKinds = 12;
 
@@ -117,6 +120,78 @@ template <> struct TP<1, 0, 0> {
 };
 
 template <> struct TP<1, 0, 1> {
+  // in irreps [(0, 1), (1, -1)]; out irreps [(0, 1), (1, -1)]
+  static constexpr int NP = 5, DIN = 4, DOUT = 4, NS = 2, NPW = 5;
+  static __device__ __forceinline__ void fwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, float* s, float* vo) {
+    #pragma unroll
+    for (int k = 0; k < 4; ++k) vo[k] = 0.f;
+    { // path 0: (0, 1) x (0,1) -> (0, 1)
+      const float t0 = 1.0f * v[0] * g[0];
+      s[0] = t0;
+      const float w = th[0] * 0.7071067811865475f;
+      vo[0] += w * t0;
+    }
+    { // path 1: (0, 1) x (1,-1) -> (1, -1)
+      const float t0 = 0.9999999999999999f * v[0] * g[1];
+      const float t1 = 1.0000000000000002f * v[0] * g[2];
+      const float t2 = 0.9999999999999999f * v[0] * g[3];
+      const float w = th[1] * 0.7071067811865475f;
+      vo[1] += w * t0;
+      vo[2] += w * t1;
+      vo[3] += w * t2;
+    }
+    { // path 2: (1, -1) x (0,1) -> (1, -1)
+      const float t0 = 0.9999999999999999f * v[1] * g[0];
+      const float t1 = 1.0000000000000002f * v[2] * g[0];
+      const float t2 = 0.9999999999999999f * v[3] * g[0];
+      const float w = th[2] * 0.7071067811865475f;
+      vo[1] += w * t0;
+      vo[2] += w * t1;
+      vo[3] += w * t2;
+    }
+    { // path 3: (1, -1) x (1,-1) -> (0, 1)
+      const float t0 = 0.5773502691896257f * v[1] * g[1] + 0.5773502691896258f * v[2] * g[2] + 0.5773502691896257f * v[3] * g[3];
+      s[1] = t0;
+      const float w = th[3] * 0.7071067811865475f;
+      vo[0] += w * t0;
+    }
+  }
+  static __device__ __forceinline__ void bwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, const float* __restrict__ gs, const float* __restrict__ gvo, float* gv, float* gg) {
+    { // path 0
+      const float w = th[0] * 0.7071067811865475f;
+      const float gt0 = gs[0] + w * gvo[0];
+      gv[0] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[0];
+    }
+    { // path 1
+      const float w = th[1] * 0.7071067811865475f;
+      const float gt0 = w * gvo[1];
+      const float gt1 = w * gvo[2];
+      const float gt2 = w * gvo[3];
+      gv[0] += 0.9999999999999999f * gt0 * g[1]; gg[1] += 0.9999999999999999f * gt0 * v[0];
+      gv[0] += 1.0000000000000002f * gt1 * g[2]; gg[2] += 1.0000000000000002f * gt1 * v[0];
+      gv[0] += 0.9999999999999999f * gt2 * g[3]; gg[3] += 0.9999999999999999f * gt2 * v[0];
+    }
+    { // path 2
+      const float w = th[2] * 0.7071067811865475f;
+      const float gt0 = w * gvo[1];
+      const float gt1 = w * gvo[2];
+      const float gt2 = w * gvo[3];
+      gv[1] += 0.9999999999999999f * gt0 * g[0]; gg[0] += 0.9999999999999999f * gt0 * v[1];
+      gv[2] += 1.0000000000000002f * gt1 * g[0]; gg[0] += 1.0000000000000002f * gt1 * v[2];
+      gv[3] += 0.9999999999999999f * gt2 * g[0]; gg[0] += 0.9999999999999999f * gt2 * v[3];
+    }
+    { // path 3
+      const float w = th[3] * 0.7071067811865475f;
+      const float gt0 = gs[1] + w * gvo[0];
+      gv[1] += 0.5773502691896257f * gt0 * g[1]; gg[1] += 0.5773502691896257f * gt0 * v[1];
+      gv[2] += 0.5773502691896258f * gt0 * g[2]; gg[2] += 0.5773502691896258f * gt0 * v[2];
+      gv[3] += 0.5773502691896257f * gt0 * g[3]; gg[3] += 0.5773502691896257f * gt0 * v[3];
+    }
+  }
+  static constexpr int NNZ = 10;
+};
+
+template <> struct TP<1, 0, 2> {
   // in irreps [(0, 1), (1, -1)]; out irreps [(0, 1)]
   static constexpr int NP = 2, DIN = 4, DOUT = 1, NS = 2, NPW = 0;
   static __device__ __forceinline__ void fwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, float* s, float* vo) {
@@ -289,39 +364,11 @@ template <> struct TP<1, 1, 0> {
 };
 
 template <> struct TP<1, 1, 1> {
-  // in irreps [(0, 1), (1, -1), (1, 1)]; out irreps [(0, 1)]
-  static constexpr int NP = 2, DIN = 7, DOUT = 1, NS = 2, NPW = 0;
-  static __device__ __forceinline__ void fwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, float* s, float* vo) {
-    { // path 0: (0, 1) x (0,1) -> (0, 1)
-      const float t0 = 1.0f * v[0] * g[0];
-      s[0] = t0;
-    }
-    { // path 1: (1, -1) x (1,-1) -> (0, 1)
-      const float t0 = 0.5773502691896257f * v[1] * g[1] + 0.5773502691896258f * v[2] * g[2] + 0.5773502691896257f * v[3] * g[3];
-      s[1] = t0;
-    }
-  }
-  static __device__ __forceinline__ void bwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, const float* __restrict__ gs, const float* __restrict__ gvo, float* gv, float* gg) {
-    { // path 0
-      const float gt0 = gs[0];
-      gv[0] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[0];
-    }
-    { // path 1
-      const float gt0 = gs[1];
-      gv[1] += 0.5773502691896257f * gt0 * g[1]; gg[1] += 0.5773502691896257f * gt0 * v[1];
-      gv[2] += 0.5773502691896258f * gt0 * g[2]; gg[2] += 0.5773502691896258f * gt0 * v[2];
-      gv[3] += 0.5773502691896257f * gt0 * g[3]; gg[3] += 0.5773502691896257f * gt0 * v[3];
-    }
-  }
-  static constexpr int NNZ = 4;
-};
-
-template <> struct TP<1, 2, 0> {
-  // in irreps [(0, 1), (0, -1), (1, -1), (1, 1)]; out irreps [(0, 1), (0, -1), (1, -1), (1, 1)]
-  static constexpr int NP = 10, DIN = 8, DOUT = 8, NS = 2, NPW = 10;
+  // in irreps [(0, 1), (1, -1), (1, 1)]; out irreps [(0, 1), (1, -1)]
+  static constexpr int NP = 8, DIN = 7, DOUT = 4, NS = 2, NPW = 8;
   static __device__ __forceinline__ void fwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, float* s, float* vo) {
     #pragma unroll
-    for (int k = 0; k < 8; ++k) vo[k] = 0.f;
+    for (int k = 0; k < 4; ++k) vo[k] = 0.f;
     { // path 0: (0, 1) x (0,1) -> (0, 1)
       const float t0 = 1.0f * v[0] * g[0];
       s[0] = t0;
@@ -333,70 +380,33 @@ template <> struct TP<1, 2, 0> {
       const float t1 = 1.0000000000000002f * v[0] * g[2];
       const float t2 = 0.9999999999999999f * v[0] * g[3];
       const float w = th[1] * 0.5773502691896258f;
-      vo[2] += w * t0;
-      vo[3] += w * t1;
-      vo[4] += w * t2;
-    }
-    { // path 2: (0, -1) x (0,1) -> (0, -1)
-      const float t0 = 1.0f * v[1] * g[0];
-      const float w = th[2] * 0.7071067811865475f;
       vo[1] += w * t0;
+      vo[2] += w * t1;
+      vo[3] += w * t2;
     }
-    { // path 3: (0, -1) x (1,-1) -> (1, 1)
-      const float t0 = 0.9999999999999999f * v[1] * g[1];
-      const float t1 = 1.0000000000000002f * v[1] * g[2];
-      const float t2 = 0.9999999999999999f * v[1] * g[3];
-      const float w = th[3] * 0.5773502691896258f;
-      vo[5] += w * t0;
-      vo[6] += w * t1;
-      vo[7] += w * t2;
+    { // path 2: (1, -1) x (0,1) -> (1, -1)
+      const float t0 = 0.9999999999999999f * v[1] * g[0];
+      const float t1 = 1.0000000000000002f * v[2] * g[0];
+      const float t2 = 0.9999999999999999f * v[3] * g[0];
+      const float w = th[2] * 0.5773502691896258f;
+      vo[1] += w * t0;
+      vo[2] += w * t1;
+      vo[3] += w * t2;
     }
-    { // path 4: (1, -1) x (0,1) -> (1, -1)
-      const float t0 = 0.9999999999999999f * v[2] * g[0];
-      const float t1 = 1.0000000000000002f * v[3] * g[0];
-      const float t2 = 0.9999999999999999f * v[4] * g[0];
-      const float w = th[4] * 0.5773502691896258f;
-      vo[2] += w * t0;
-      vo[3] += w * t1;
-      vo[4] += w * t2;
-    }
-    { // path 5: (1, -1) x (1,-1) -> (0, 1)
-      const float t0 = 0.5773502691896257f * v[2] * g[1] + 0.5773502691896258f * v[3] * g[2] + 0.5773502691896257f * v[4] * g[3];
+    { // path 3: (1, -1) x (1,-1) -> (0, 1)
+      const float t0 = 0.5773502691896257f * v[1] * g[1] + 0.5773502691896258f * v[2] * g[2] + 0.5773502691896257f * v[3] * g[3];
       s[1] = t0;
-      const float w = th[5] * 0.7071067811865475f;
+      const float w = th[3] * 0.7071067811865475f;
       vo[0] += w * t0;
     }
-    { // path 6: (1, -1) x (1,-1) -> (1, 1)
-      const float t0 = 0.7071067811865476f * v[3] * g[3] + -0.7071067811865476f * v[4] * g[2];
-      const float t1 = -0.7071067811865476f * v[2] * g[3] + 0.7071067811865476f * v[4] * g[1];
-      const float t2 = 0.7071067811865476f * v[2] * g[2] + -0.7071067811865476f * v[3] * g[1];
-      const float w = th[6] * 0.5773502691896258f;
-      vo[5] += w * t0;
-      vo[6] += w * t1;
-      vo[7] += w * t2;
-    }
-    { // path 7: (1, 1) x (0,1) -> (1, 1)
-      const float t0 = 0.9999999999999999f * v[5] * g[0];
-      const float t1 = 1.0000000000000002f * v[6] * g[0];
-      const float t2 = 0.9999999999999999f * v[7] * g[0];
+    { // path 7: (1, 1) x (1,-1) -> (1, -1)
+      const float t0 = 0.7071067811865476f * v[5] * g[3] + -0.7071067811865476f * v[6] * g[2];
+      const float t1 = -0.7071067811865476f * v[4] * g[3] + 0.7071067811865476f * v[6] * g[1];
+      const float t2 = 0.7071067811865476f * v[4] * g[2] + -0.7071067811865476f * v[5] * g[1];
       const float w = th[7] * 0.5773502691896258f;
-      vo[5] += w * t0;
-      vo[6] += w * t1;
-      vo[7] += w * t2;
-    }
-    { // path 8: (1, 1) x (1,-1) -> (0, -1)
-      const float t0 = 0.5773502691896257f * v[5] * g[1] + 0.5773502691896258f * v[6] * g[2] + 0.5773502691896257f * v[7] * g[3];
-      const float w = th[8] * 0.7071067811865475f;
       vo[1] += w * t0;
-    }
-    { // path 9: (1, 1) x (1,-1) -> (1, -1)
-      const float t0 = 0.7071067811865476f * v[6] * g[3] + -0.7071067811865476f * v[7] * g[2];
-      const float t1 = -0.7071067811865476f * v[5] * g[3] + 0.7071067811865476f * v[7] * g[1];
-      const float t2 = 0.7071067811865476f * v[5] * g[2] + -0.7071067811865476f * v[6] * g[1];
-      const float w = th[9] * 0.5773502691896258f;
-      vo[2] += w * t0;
-      vo[3] += w * t1;
-      vo[4] += w * t2;
+      vo[2] += w * t1;
+      vo[3] += w * t2;
     }
   }
   static __device__ __forceinline__ void bwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, const float* __restrict__ gs, const float* __restrict__ gvo, float* gv, float* gg) {
@@ -407,32 +417,111 @@ template <> struct TP<1, 2, 0> {
     }
     { // path 1
       const float w = th[1] * 0.5773502691896258f;
-      const float gt0 = w * gvo[2];
-      const float gt1 = w * gvo[3];
-      const float gt2 = w * gvo[4];
+      const float gt0 = w * gvo[1];
+      const float gt1 = w * gvo[2];
+      const float gt2 = w * gvo[3];
       gv[0] += 0.9999999999999999f * gt0 * g[1]; gg[1] += 0.9999999999999999f * gt0 * v[0];
       gv[0] += 1.0000000000000002f * gt1 * g[2]; gg[2] += 1.0000000000000002f * gt1 * v[0];
       gv[0] += 0.9999999999999999f * gt2 * g[3]; gg[3] += 0.9999999999999999f * gt2 * v[0];
     }
     { // path 2
-      const float w = th[2] * 0.7071067811865475f;
+      const float w = th[2] * 0.5773502691896258f;
       const float gt0 = w * gvo[1];
-      gv[1] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[1];
+      const float gt1 = w * gvo[2];
+      const float gt2 = w * gvo[3];
+      gv[1] += 0.9999999999999999f * gt0 * g[0]; gg[0] += 0.9999999999999999f * gt0 * v[1];
+      gv[2] += 1.0000000000000002f * gt1 * g[0]; gg[0] += 1.0000000000000002f * gt1 * v[2];
+      gv[3] += 0.9999999999999999f * gt2 * g[0]; gg[0] += 0.9999999999999999f * gt2 * v[3];
     }
     { // path 3
-      const float w = th[3] * 0.5773502691896258f;
-      const float gt0 = w * gvo[5];
-      const float gt1 = w * gvo[6];
-      const float gt2 = w * gvo[7];
-      gv[1] += 0.9999999999999999f * gt0 * g[1]; gg[1] += 0.9999999999999999f * gt0 * v[1];
-      gv[1] += 1.0000000000000002f * gt1 * g[2]; gg[2] += 1.0000000000000002f * gt1 * v[1];
-      gv[1] += 0.9999999999999999f * gt2 * g[3]; gg[3] += 0.9999999999999999f * gt2 * v[1];
+      const float w = th[3] * 0.7071067811865475f;
+      const float gt0 = gs[1] + w * gvo[0];
+      gv[1] += 0.5773502691896257f * gt0 * g[1]; gg[1] += 0.5773502691896257f * gt0 * v[1];
+      gv[2] += 0.5773502691896258f * gt0 * g[2]; gg[2] += 0.5773502691896258f * gt0 * v[2];
+      gv[3] += 0.5773502691896257f * gt0 * g[3]; gg[3] += 0.5773502691896257f * gt0 * v[3];
+    }
+    { // path 7
+      const float w = th[7] * 0.5773502691896258f;
+      const float gt0 = w * gvo[1];
+      const float gt1 = w * gvo[2];
+      const float gt2 = w * gvo[3];
+      gv[4] += 0.7071067811865476f * gt2 * g[2]; gg[2] += 0.7071067811865476f * gt2 * v[4];
+      gv[4] += -0.7071067811865476f * gt1 * g[3]; gg[3] += -0.7071067811865476f * gt1 * v[4];
+      gv[5] += -0.7071067811865476f * gt2 * g[1]; gg[1] += -0.7071067811865476f * gt2 * v[5];
+      gv[5] += 0.7071067811865476f * gt0 * g[3]; gg[3] += 0.7071067811865476f * gt0 * v[5];
+      gv[6] += 0.7071067811865476f * gt1 * g[1]; gg[1] += 0.7071067811865476f * gt1 * v[6];
+      gv[6] += -0.7071067811865476f * gt0 * g[2]; gg[2] += -0.7071067811865476f * gt0 * v[6];
+    }
+  }
+  static constexpr int NNZ = 16;
+};
+
+template <> struct TP<1, 2, 1> {
+  // in irreps [(0, 1), (0, -1), (1, -1), (1, 1)]; out irreps [(0, 1), (1, -1)]
+  static constexpr int NP = 10, DIN = 8, DOUT = 4, NS = 2, NPW = 10;
+  static __device__ __forceinline__ void fwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, float* s, float* vo) {
+    #pragma unroll
+    for (int k = 0; k < 4; ++k) vo[k] = 0.f;
+    { // path 0: (0, 1) x (0,1) -> (0, 1)
+      const float t0 = 1.0f * v[0] * g[0];
+      s[0] = t0;
+      const float w = th[0] * 0.7071067811865475f;
+      vo[0] += w * t0;
+    }
+    { // path 1: (0, 1) x (1,-1) -> (1, -1)
+      const float t0 = 0.9999999999999999f * v[0] * g[1];
+      const float t1 = 1.0000000000000002f * v[0] * g[2];
+      const float t2 = 0.9999999999999999f * v[0] * g[3];
+      const float w = th[1] * 0.5773502691896258f;
+      vo[1] += w * t0;
+      vo[2] += w * t1;
+      vo[3] += w * t2;
+    }
+    { // path 4: (1, -1) x (0,1) -> (1, -1)
+      const float t0 = 0.9999999999999999f * v[2] * g[0];
+      const float t1 = 1.0000000000000002f * v[3] * g[0];
+      const float t2 = 0.9999999999999999f * v[4] * g[0];
+      const float w = th[4] * 0.5773502691896258f;
+      vo[1] += w * t0;
+      vo[2] += w * t1;
+      vo[3] += w * t2;
+    }
+    { // path 5: (1, -1) x (1,-1) -> (0, 1)
+      const float t0 = 0.5773502691896257f * v[2] * g[1] + 0.5773502691896258f * v[3] * g[2] + 0.5773502691896257f * v[4] * g[3];
+      s[1] = t0;
+      const float w = th[5] * 0.7071067811865475f;
+      vo[0] += w * t0;
+    }
+    { // path 9: (1, 1) x (1,-1) -> (1, -1)
+      const float t0 = 0.7071067811865476f * v[6] * g[3] + -0.7071067811865476f * v[7] * g[2];
+      const float t1 = -0.7071067811865476f * v[5] * g[3] + 0.7071067811865476f * v[7] * g[1];
+      const float t2 = 0.7071067811865476f * v[5] * g[2] + -0.7071067811865476f * v[6] * g[1];
+      const float w = th[9] * 0.5773502691896258f;
+      vo[1] += w * t0;
+      vo[2] += w * t1;
+      vo[3] += w * t2;
+    }
+  }
+  static __device__ __forceinline__ void bwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, const float* __restrict__ gs, const float* __restrict__ gvo, float* gv, float* gg) {
+    { // path 0
+      const float w = th[0] * 0.7071067811865475f;
+      const float gt0 = gs[0] + w * gvo[0];
+      gv[0] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[0];
+    }
+    { // path 1
+      const float w = th[1] * 0.5773502691896258f;
+      const float gt0 = w * gvo[1];
+      const float gt1 = w * gvo[2];
+      const float gt2 = w * gvo[3];
+      gv[0] += 0.9999999999999999f * gt0 * g[1]; gg[1] += 0.9999999999999999f * gt0 * v[0];
+      gv[0] += 1.0000000000000002f * gt1 * g[2]; gg[2] += 1.0000000000000002f * gt1 * v[0];
+      gv[0] += 0.9999999999999999f * gt2 * g[3]; gg[3] += 0.9999999999999999f * gt2 * v[0];
     }
     { // path 4
       const float w = th[4] * 0.5773502691896258f;
-      const float gt0 = w * gvo[2];
-      const float gt1 = w * gvo[3];
-      const float gt2 = w * gvo[4];
+      const float gt0 = w * gvo[1];
+      const float gt1 = w * gvo[2];
+      const float gt2 = w * gvo[3];
       gv[2] += 0.9999999999999999f * gt0 * g[0]; gg[0] += 0.9999999999999999f * gt0 * v[2];
       gv[3] += 1.0000000000000002f * gt1 * g[0]; gg[0] += 1.0000000000000002f * gt1 * v[3];
       gv[4] += 0.9999999999999999f * gt2 * g[0]; gg[0] += 0.9999999999999999f * gt2 * v[4];
@@ -444,39 +533,11 @@ template <> struct TP<1, 2, 0> {
       gv[3] += 0.5773502691896258f * gt0 * g[2]; gg[2] += 0.5773502691896258f * gt0 * v[3];
       gv[4] += 0.5773502691896257f * gt0 * g[3]; gg[3] += 0.5773502691896257f * gt0 * v[4];
     }
-    { // path 6
-      const float w = th[6] * 0.5773502691896258f;
-      const float gt0 = w * gvo[5];
-      const float gt1 = w * gvo[6];
-      const float gt2 = w * gvo[7];
-      gv[2] += 0.7071067811865476f * gt2 * g[2]; gg[2] += 0.7071067811865476f * gt2 * v[2];
-      gv[2] += -0.7071067811865476f * gt1 * g[3]; gg[3] += -0.7071067811865476f * gt1 * v[2];
-      gv[3] += -0.7071067811865476f * gt2 * g[1]; gg[1] += -0.7071067811865476f * gt2 * v[3];
-      gv[3] += 0.7071067811865476f * gt0 * g[3]; gg[3] += 0.7071067811865476f * gt0 * v[3];
-      gv[4] += 0.7071067811865476f * gt1 * g[1]; gg[1] += 0.7071067811865476f * gt1 * v[4];
-      gv[4] += -0.7071067811865476f * gt0 * g[2]; gg[2] += -0.7071067811865476f * gt0 * v[4];
-    }
-    { // path 7
-      const float w = th[7] * 0.5773502691896258f;
-      const float gt0 = w * gvo[5];
-      const float gt1 = w * gvo[6];
-      const float gt2 = w * gvo[7];
-      gv[5] += 0.9999999999999999f * gt0 * g[0]; gg[0] += 0.9999999999999999f * gt0 * v[5];
-      gv[6] += 1.0000000000000002f * gt1 * g[0]; gg[0] += 1.0000000000000002f * gt1 * v[6];
-      gv[7] += 0.9999999999999999f * gt2 * g[0]; gg[0] += 0.9999999999999999f * gt2 * v[7];
-    }
-    { // path 8
-      const float w = th[8] * 0.7071067811865475f;
-      const float gt0 = w * gvo[1];
-      gv[5] += 0.5773502691896257f * gt0 * g[1]; gg[1] += 0.5773502691896257f * gt0 * v[5];
-      gv[6] += 0.5773502691896258f * gt0 * g[2]; gg[2] += 0.5773502691896258f * gt0 * v[6];
-      gv[7] += 0.5773502691896257f * gt0 * g[3]; gg[3] += 0.5773502691896257f * gt0 * v[7];
-    }
     { // path 9
       const float w = th[9] * 0.5773502691896258f;
-      const float gt0 = w * gvo[2];
-      const float gt1 = w * gvo[3];
-      const float gt2 = w * gvo[4];
+      const float gt0 = w * gvo[1];
+      const float gt1 = w * gvo[2];
+      const float gt2 = w * gvo[3];
       gv[5] += 0.7071067811865476f * gt2 * g[2]; gg[2] += 0.7071067811865476f * gt2 * v[5];
       gv[5] += -0.7071067811865476f * gt1 * g[3]; gg[3] += -0.7071067811865476f * gt1 * v[5];
       gv[6] += -0.7071067811865476f * gt2 * g[1]; gg[1] += -0.7071067811865476f * gt2 * v[6];
@@ -485,35 +546,7 @@ template <> struct TP<1, 2, 0> {
       gv[7] += -0.7071067811865476f * gt0 * g[2]; gg[2] += -0.7071067811865476f * gt0 * v[7];
     }
   }
-  static constexpr int NNZ = 32;
-};
-
-template <> struct TP<1, 2, 1> {
-  // in irreps [(0, 1), (0, -1), (1, -1), (1, 1)]; out irreps [(0, 1)]
-  static constexpr int NP = 2, DIN = 8, DOUT = 1, NS = 2, NPW = 0;
-  static __device__ __forceinline__ void fwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, float* s, float* vo) {
-    { // path 0: (0, 1) x (0,1) -> (0, 1)
-      const float t0 = 1.0f * v[0] * g[0];
-      s[0] = t0;
-    }
-    { // path 1: (1, -1) x (1,-1) -> (0, 1)
-      const float t0 = 0.5773502691896257f * v[2] * g[1] + 0.5773502691896258f * v[3] * g[2] + 0.5773502691896257f * v[4] * g[3];
-      s[1] = t0;
-    }
-  }
-  static __device__ __forceinline__ void bwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, const float* __restrict__ gs, const float* __restrict__ gvo, float* gv, float* gg) {
-    { // path 0
-      const float gt0 = gs[0];
-      gv[0] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[0];
-    }
-    { // path 1
-      const float gt0 = gs[1];
-      gv[2] += 0.5773502691896257f * gt0 * g[1]; gg[1] += 0.5773502691896257f * gt0 * v[2];
-      gv[3] += 0.5773502691896258f * gt0 * g[2]; gg[2] += 0.5773502691896258f * gt0 * v[3];
-      gv[4] += 0.5773502691896257f * gt0 * g[3]; gg[3] += 0.5773502691896257f * gt0 * v[4];
-    }
-  }
-  static constexpr int NNZ = 4;
+  static constexpr int NNZ = 16;
 };
 
 template <> struct TP<2, 0, 0> {
@@ -912,6 +945,275 @@ template <> struct TP<2, 0, 0> {
 };
 
 template <> struct TP<2, 0, 1> {
+  // in irreps [(0, 1), (1, -1), (2, 1)]; out irreps [(0, 1), (1, -1), (2, 1)]
+  static constexpr int NP = 15, DIN = 9, DOUT = 9, NS = 3, NPW = 15;
+  static __device__ __forceinline__ void fwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, float* s, float* vo) {
+    #pragma unroll
+    for (int k = 0; k < 9; ++k) vo[k] = 0.f;
+    { // path 0: (0, 1) x (0,1) -> (0, 1)
+      const float t0 = 1.0f * v[0] * g[0];
+      s[0] = t0;
+      const float w = th[0] * 0.5773502691896258f;
+      vo[0] += w * t0;
+    }
+    { // path 1: (0, 1) x (1,-1) -> (1, -1)
+      const float t0 = 0.9999999999999999f * v[0] * g[1];
+      const float t1 = 1.0000000000000002f * v[0] * g[2];
+      const float t2 = 0.9999999999999999f * v[0] * g[3];
+      const float w = th[1] * 0.5f;
+      vo[1] += w * t0;
+      vo[2] += w * t1;
+      vo[3] += w * t2;
+    }
+    { // path 2: (0, 1) x (2,1) -> (2, 1)
+      const float t0 = 1.0f * v[0] * g[4];
+      const float t1 = 1.0f * v[0] * g[5];
+      const float t2 = 1.0000000000000002f * v[0] * g[6];
+      const float t3 = 1.0f * v[0] * g[7];
+      const float t4 = 1.0f * v[0] * g[8];
+      const float w = th[2] * 0.5f;
+      vo[4] += w * t0;
+      vo[5] += w * t1;
+      vo[6] += w * t2;
+      vo[7] += w * t3;
+      vo[8] += w * t4;
+    }
+    { // path 3: (1, -1) x (0,1) -> (1, -1)
+      const float t0 = 0.9999999999999999f * v[1] * g[0];
+      const float t1 = 1.0000000000000002f * v[2] * g[0];
+      const float t2 = 0.9999999999999999f * v[3] * g[0];
+      const float w = th[3] * 0.5f;
+      vo[1] += w * t0;
+      vo[2] += w * t1;
+      vo[3] += w * t2;
+    }
+    { // path 4: (1, -1) x (1,-1) -> (0, 1)
+      const float t0 = 0.5773502691896257f * v[1] * g[1] + 0.5773502691896258f * v[2] * g[2] + 0.5773502691896257f * v[3] * g[3];
+      s[1] = t0;
+      const float w = th[4] * 0.5773502691896258f;
+      vo[0] += w * t0;
+    }
+    { // path 6: (1, -1) x (1,-1) -> (2, 1)
+      const float t0 = -0.7071067811865475f * v[1] * g[3] + -0.7071067811865475f * v[3] * g[1];
+      const float t1 = -0.7071067811865476f * v[1] * g[2] + -0.7071067811865476f * v[2] * g[1];
+      const float t2 = 0.4082482904638631f * v[1] * g[1] + -0.8164965809277261f * v[2] * g[2] + 0.4082482904638631f * v[3] * g[3];
+      const float t3 = -0.7071067811865476f * v[2] * g[3] + -0.7071067811865476f * v[3] * g[2];
+      const float t4 = 0.7071067811865475f * v[1] * g[1] + -0.7071067811865475f * v[3] * g[3];
+      const float w = th[6] * 0.5f;
+      vo[4] += w * t0;
+      vo[5] += w * t1;
+      vo[6] += w * t2;
+      vo[7] += w * t3;
+      vo[8] += w * t4;
+    }
+    { // path 7: (1, -1) x (2,1) -> (1, -1)
+      const float t0 = -0.3162277660168379f * v[1] * g[6] + -0.547722557505166f * v[1] * g[8] + 0.547722557505166f * v[2] * g[5] + 0.547722557505166f * v[3] * g[4];
+      const float t1 = 0.547722557505166f * v[1] * g[5] + 0.632455532033676f * v[2] * g[6] + 0.547722557505166f * v[3] * g[7];
+      const float t2 = 0.547722557505166f * v[1] * g[4] + 0.547722557505166f * v[2] * g[7] + -0.3162277660168379f * v[3] * g[6] + 0.547722557505166f * v[3] * g[8];
+      const float w = th[7] * 0.5f;
+      vo[1] += w * t0;
+      vo[2] += w * t1;
+      vo[3] += w * t2;
+    }
+    { // path 9: (2, 1) x (0,1) -> (2, 1)
+      const float t0 = 1.0f * v[4] * g[0];
+      const float t1 = 1.0f * v[5] * g[0];
+      const float t2 = 1.0000000000000002f * v[6] * g[0];
+      const float t3 = 1.0f * v[7] * g[0];
+      const float t4 = 1.0f * v[8] * g[0];
+      const float w = th[9] * 0.5f;
+      vo[4] += w * t0;
+      vo[5] += w * t1;
+      vo[6] += w * t2;
+      vo[7] += w * t3;
+      vo[8] += w * t4;
+    }
+    { // path 10: (2, 1) x (1,-1) -> (1, -1)
+      const float t0 = 0.547722557505166f * v[4] * g[3] + 0.547722557505166f * v[5] * g[2] + -0.3162277660168379f * v[6] * g[1] + -0.547722557505166f * v[8] * g[1];
+      const float t1 = 0.547722557505166f * v[5] * g[1] + 0.632455532033676f * v[6] * g[2] + 0.547722557505166f * v[7] * g[3];
+      const float t2 = 0.547722557505166f * v[4] * g[1] + -0.3162277660168379f * v[6] * g[3] + 0.547722557505166f * v[7] * g[2] + 0.547722557505166f * v[8] * g[3];
+      const float w = th[10] * 0.5f;
+      vo[1] += w * t0;
+      vo[2] += w * t1;
+      vo[3] += w * t2;
+    }
+    { // path 12: (2, 1) x (2,1) -> (0, 1)
+      const float t0 = 0.4472135954999579f * v[4] * g[4] + 0.4472135954999579f * v[5] * g[5] + 0.44721359549995804f * v[6] * g[6] + 0.4472135954999579f * v[7] * g[7] + 0.4472135954999579f * v[8] * g[8];
+      s[2] = t0;
+      const float w = th[12] * 0.5773502691896258f;
+      vo[0] += w * t0;
+    }
+    { // path 14: (2, 1) x (2,1) -> (2, 1)
+      const float t0 = 0.5345224838248488f * v[4] * g[6] + -0.4629100498862757f * v[5] * g[7] + 0.5345224838248488f * v[6] * g[4] + -0.4629100498862757f * v[7] * g[5];
+      const float t1 = -0.4629100498862757f * v[4] * g[7] + -0.2672612419124244f * v[5] * g[6] + 0.4629100498862757f * v[5] * g[8] + -0.2672612419124244f * v[6] * g[5] + -0.4629100498862757f * v[7] * g[4] + 0.4629100498862757f * v[8] * g[5];
+      const float t2 = 0.5345224838248488f * v[4] * g[4] + -0.2672612419124244f * v[5] * g[5] + -0.5345224838248489f * v[6] * g[6] + -0.2672612419124244f * v[7] * g[7] + 0.5345224838248488f * v[8] * g[8];
+      const float t3 = -0.4629100498862757f * v[4] * g[5] + -0.4629100498862757f * v[5] * g[4] + -0.2672612419124244f * v[6] * g[7] + -0.2672612419124244f * v[7] * g[6] + -0.4629100498862757f * v[7] * g[8] + -0.4629100498862757f * v[8] * g[7];
+      const float t4 = 0.4629100498862757f * v[5] * g[5] + 0.5345224838248488f * v[6] * g[8] + -0.4629100498862757f * v[7] * g[7] + 0.5345224838248488f * v[8] * g[6];
+      const float w = th[14] * 0.5f;
+      vo[4] += w * t0;
+      vo[5] += w * t1;
+      vo[6] += w * t2;
+      vo[7] += w * t3;
+      vo[8] += w * t4;
+    }
+  }
+  static __device__ __forceinline__ void bwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, const float* __restrict__ gs, const float* __restrict__ gvo, float* gv, float* gg) {
+    { // path 0
+      const float w = th[0] * 0.5773502691896258f;
+      const float gt0 = gs[0] + w * gvo[0];
+      gv[0] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[0];
+    }
+    { // path 1
+      const float w = th[1] * 0.5f;
+      const float gt0 = w * gvo[1];
+      const float gt1 = w * gvo[2];
+      const float gt2 = w * gvo[3];
+      gv[0] += 0.9999999999999999f * gt0 * g[1]; gg[1] += 0.9999999999999999f * gt0 * v[0];
+      gv[0] += 1.0000000000000002f * gt1 * g[2]; gg[2] += 1.0000000000000002f * gt1 * v[0];
+      gv[0] += 0.9999999999999999f * gt2 * g[3]; gg[3] += 0.9999999999999999f * gt2 * v[0];
+    }
+    { // path 2
+      const float w = th[2] * 0.5f;
+      const float gt0 = w * gvo[4];
+      const float gt1 = w * gvo[5];
+      const float gt2 = w * gvo[6];
+      const float gt3 = w * gvo[7];
+      const float gt4 = w * gvo[8];
+      gv[0] += 1.0f * gt0 * g[4]; gg[4] += 1.0f * gt0 * v[0];
+      gv[0] += 1.0f * gt1 * g[5]; gg[5] += 1.0f * gt1 * v[0];
+      gv[0] += 1.0000000000000002f * gt2 * g[6]; gg[6] += 1.0000000000000002f * gt2 * v[0];
+      gv[0] += 1.0f * gt3 * g[7]; gg[7] += 1.0f * gt3 * v[0];
+      gv[0] += 1.0f * gt4 * g[8]; gg[8] += 1.0f * gt4 * v[0];
+    }
+    { // path 3
+      const float w = th[3] * 0.5f;
+      const float gt0 = w * gvo[1];
+      const float gt1 = w * gvo[2];
+      const float gt2 = w * gvo[3];
+      gv[1] += 0.9999999999999999f * gt0 * g[0]; gg[0] += 0.9999999999999999f * gt0 * v[1];
+      gv[2] += 1.0000000000000002f * gt1 * g[0]; gg[0] += 1.0000000000000002f * gt1 * v[2];
+      gv[3] += 0.9999999999999999f * gt2 * g[0]; gg[0] += 0.9999999999999999f * gt2 * v[3];
+    }
+    { // path 4
+      const float w = th[4] * 0.5773502691896258f;
+      const float gt0 = gs[1] + w * gvo[0];
+      gv[1] += 0.5773502691896257f * gt0 * g[1]; gg[1] += 0.5773502691896257f * gt0 * v[1];
+      gv[2] += 0.5773502691896258f * gt0 * g[2]; gg[2] += 0.5773502691896258f * gt0 * v[2];
+      gv[3] += 0.5773502691896257f * gt0 * g[3]; gg[3] += 0.5773502691896257f * gt0 * v[3];
+    }
+    { // path 6
+      const float w = th[6] * 0.5f;
+      const float gt0 = w * gvo[4];
+      const float gt1 = w * gvo[5];
+      const float gt2 = w * gvo[6];
+      const float gt3 = w * gvo[7];
+      const float gt4 = w * gvo[8];
+      gv[1] += 0.4082482904638631f * gt2 * g[1]; gg[1] += 0.4082482904638631f * gt2 * v[1];
+      gv[1] += 0.7071067811865475f * gt4 * g[1]; gg[1] += 0.7071067811865475f * gt4 * v[1];
+      gv[1] += -0.7071067811865476f * gt1 * g[2]; gg[2] += -0.7071067811865476f * gt1 * v[1];
+      gv[1] += -0.7071067811865475f * gt0 * g[3]; gg[3] += -0.7071067811865475f * gt0 * v[1];
+      gv[2] += -0.7071067811865476f * gt1 * g[1]; gg[1] += -0.7071067811865476f * gt1 * v[2];
+      gv[2] += -0.8164965809277261f * gt2 * g[2]; gg[2] += -0.8164965809277261f * gt2 * v[2];
+      gv[2] += -0.7071067811865476f * gt3 * g[3]; gg[3] += -0.7071067811865476f * gt3 * v[2];
+      gv[3] += -0.7071067811865475f * gt0 * g[1]; gg[1] += -0.7071067811865475f * gt0 * v[3];
+      gv[3] += -0.7071067811865476f * gt3 * g[2]; gg[2] += -0.7071067811865476f * gt3 * v[3];
+      gv[3] += 0.4082482904638631f * gt2 * g[3]; gg[3] += 0.4082482904638631f * gt2 * v[3];
+      gv[3] += -0.7071067811865475f * gt4 * g[3]; gg[3] += -0.7071067811865475f * gt4 * v[3];
+    }
+    { // path 7
+      const float w = th[7] * 0.5f;
+      const float gt0 = w * gvo[1];
+      const float gt1 = w * gvo[2];
+      const float gt2 = w * gvo[3];
+      gv[1] += 0.547722557505166f * gt2 * g[4]; gg[4] += 0.547722557505166f * gt2 * v[1];
+      gv[1] += 0.547722557505166f * gt1 * g[5]; gg[5] += 0.547722557505166f * gt1 * v[1];
+      gv[1] += -0.3162277660168379f * gt0 * g[6]; gg[6] += -0.3162277660168379f * gt0 * v[1];
+      gv[1] += -0.547722557505166f * gt0 * g[8]; gg[8] += -0.547722557505166f * gt0 * v[1];
+      gv[2] += 0.547722557505166f * gt0 * g[5]; gg[5] += 0.547722557505166f * gt0 * v[2];
+      gv[2] += 0.632455532033676f * gt1 * g[6]; gg[6] += 0.632455532033676f * gt1 * v[2];
+      gv[2] += 0.547722557505166f * gt2 * g[7]; gg[7] += 0.547722557505166f * gt2 * v[2];
+      gv[3] += 0.547722557505166f * gt0 * g[4]; gg[4] += 0.547722557505166f * gt0 * v[3];
+      gv[3] += -0.3162277660168379f * gt2 * g[6]; gg[6] += -0.3162277660168379f * gt2 * v[3];
+      gv[3] += 0.547722557505166f * gt1 * g[7]; gg[7] += 0.547722557505166f * gt1 * v[3];
+      gv[3] += 0.547722557505166f * gt2 * g[8]; gg[8] += 0.547722557505166f * gt2 * v[3];
+    }
+    { // path 9
+      const float w = th[9] * 0.5f;
+      const float gt0 = w * gvo[4];
+      const float gt1 = w * gvo[5];
+      const float gt2 = w * gvo[6];
+      const float gt3 = w * gvo[7];
+      const float gt4 = w * gvo[8];
+      gv[4] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[4];
+      gv[5] += 1.0f * gt1 * g[0]; gg[0] += 1.0f * gt1 * v[5];
+      gv[6] += 1.0000000000000002f * gt2 * g[0]; gg[0] += 1.0000000000000002f * gt2 * v[6];
+      gv[7] += 1.0f * gt3 * g[0]; gg[0] += 1.0f * gt3 * v[7];
+      gv[8] += 1.0f * gt4 * g[0]; gg[0] += 1.0f * gt4 * v[8];
+    }
+    { // path 10
+      const float w = th[10] * 0.5f;
+      const float gt0 = w * gvo[1];
+      const float gt1 = w * gvo[2];
+      const float gt2 = w * gvo[3];
+      gv[4] += 0.547722557505166f * gt2 * g[1]; gg[1] += 0.547722557505166f * gt2 * v[4];
+      gv[4] += 0.547722557505166f * gt0 * g[3]; gg[3] += 0.547722557505166f * gt0 * v[4];
+      gv[5] += 0.547722557505166f * gt1 * g[1]; gg[1] += 0.547722557505166f * gt1 * v[5];
+      gv[5] += 0.547722557505166f * gt0 * g[2]; gg[2] += 0.547722557505166f * gt0 * v[5];
+      gv[6] += -0.3162277660168379f * gt0 * g[1]; gg[1] += -0.3162277660168379f * gt0 * v[6];
+      gv[6] += 0.632455532033676f * gt1 * g[2]; gg[2] += 0.632455532033676f * gt1 * v[6];
+      gv[6] += -0.3162277660168379f * gt2 * g[3]; gg[3] += -0.3162277660168379f * gt2 * v[6];
+      gv[7] += 0.547722557505166f * gt2 * g[2]; gg[2] += 0.547722557505166f * gt2 * v[7];
+      gv[7] += 0.547722557505166f * gt1 * g[3]; gg[3] += 0.547722557505166f * gt1 * v[7];
+      gv[8] += -0.547722557505166f * gt0 * g[1]; gg[1] += -0.547722557505166f * gt0 * v[8];
+      gv[8] += 0.547722557505166f * gt2 * g[3]; gg[3] += 0.547722557505166f * gt2 * v[8];
+    }
+    { // path 12
+      const float w = th[12] * 0.5773502691896258f;
+      const float gt0 = gs[2] + w * gvo[0];
+      gv[4] += 0.4472135954999579f * gt0 * g[4]; gg[4] += 0.4472135954999579f * gt0 * v[4];
+      gv[5] += 0.4472135954999579f * gt0 * g[5]; gg[5] += 0.4472135954999579f * gt0 * v[5];
+      gv[6] += 0.44721359549995804f * gt0 * g[6]; gg[6] += 0.44721359549995804f * gt0 * v[6];
+      gv[7] += 0.4472135954999579f * gt0 * g[7]; gg[7] += 0.4472135954999579f * gt0 * v[7];
+      gv[8] += 0.4472135954999579f * gt0 * g[8]; gg[8] += 0.4472135954999579f * gt0 * v[8];
+    }
+    { // path 14
+      const float w = th[14] * 0.5f;
+      const float gt0 = w * gvo[4];
+      const float gt1 = w * gvo[5];
+      const float gt2 = w * gvo[6];
+      const float gt3 = w * gvo[7];
+      const float gt4 = w * gvo[8];
+      gv[4] += 0.5345224838248488f * gt2 * g[4]; gg[4] += 0.5345224838248488f * gt2 * v[4];
+      gv[4] += -0.4629100498862757f * gt3 * g[5]; gg[5] += -0.4629100498862757f * gt3 * v[4];
+      gv[4] += 0.5345224838248488f * gt0 * g[6]; gg[6] += 0.5345224838248488f * gt0 * v[4];
+      gv[4] += -0.4629100498862757f * gt1 * g[7]; gg[7] += -0.4629100498862757f * gt1 * v[4];
+      gv[5] += -0.4629100498862757f * gt3 * g[4]; gg[4] += -0.4629100498862757f * gt3 * v[5];
+      gv[5] += -0.2672612419124244f * gt2 * g[5]; gg[5] += -0.2672612419124244f * gt2 * v[5];
+      gv[5] += 0.4629100498862757f * gt4 * g[5]; gg[5] += 0.4629100498862757f * gt4 * v[5];
+      gv[5] += -0.2672612419124244f * gt1 * g[6]; gg[6] += -0.2672612419124244f * gt1 * v[5];
+      gv[5] += -0.4629100498862757f * gt0 * g[7]; gg[7] += -0.4629100498862757f * gt0 * v[5];
+      gv[5] += 0.4629100498862757f * gt1 * g[8]; gg[8] += 0.4629100498862757f * gt1 * v[5];
+      gv[6] += 0.5345224838248488f * gt0 * g[4]; gg[4] += 0.5345224838248488f * gt0 * v[6];
+      gv[6] += -0.2672612419124244f * gt1 * g[5]; gg[5] += -0.2672612419124244f * gt1 * v[6];
+      gv[6] += -0.5345224838248489f * gt2 * g[6]; gg[6] += -0.5345224838248489f * gt2 * v[6];
+      gv[6] += -0.2672612419124244f * gt3 * g[7]; gg[7] += -0.2672612419124244f * gt3 * v[6];
+      gv[6] += 0.5345224838248488f * gt4 * g[8]; gg[8] += 0.5345224838248488f * gt4 * v[6];
+      gv[7] += -0.4629100498862757f * gt1 * g[4]; gg[4] += -0.4629100498862757f * gt1 * v[7];
+      gv[7] += -0.4629100498862757f * gt0 * g[5]; gg[5] += -0.4629100498862757f * gt0 * v[7];
+      gv[7] += -0.2672612419124244f * gt3 * g[6]; gg[6] += -0.2672612419124244f * gt3 * v[7];
+      gv[7] += -0.2672612419124244f * gt2 * g[7]; gg[7] += -0.2672612419124244f * gt2 * v[7];
+      gv[7] += -0.4629100498862757f * gt4 * g[7]; gg[7] += -0.4629100498862757f * gt4 * v[7];
+      gv[7] += -0.4629100498862757f * gt3 * g[8]; gg[8] += -0.4629100498862757f * gt3 * v[7];
+      gv[8] += 0.4629100498862757f * gt1 * g[5]; gg[5] += 0.4629100498862757f * gt1 * v[8];
+      gv[8] += 0.5345224838248488f * gt4 * g[6]; gg[6] += 0.5345224838248488f * gt4 * v[8];
+      gv[8] += -0.4629100498862757f * gt3 * g[7]; gg[7] += -0.4629100498862757f * gt3 * v[8];
+      gv[8] += 0.5345224838248488f * gt2 * g[8]; gg[8] += 0.5345224838248488f * gt2 * v[8];
+    }
+  }
+  static constexpr int NNZ = 83;
+};
+
+template <> struct TP<2, 0, 2> {
   // in irreps [(0, 1), (1, -1), (2, 1)]; out irreps [(0, 1)]
   static constexpr int NP = 3, DIN = 9, DOUT = 1, NS = 3, NPW = 0;
   static __device__ __forceinline__ void fwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, float* s, float* vo) {
@@ -1673,51 +1975,11 @@ template <> struct TP<2, 1, 0> {
 };
 
 template <> struct TP<2, 1, 1> {
-  // in irreps [(0, 1), (1, -1), (1, 1), (2, 1), (2, -1)]; out irreps [(0, 1)]
-  static constexpr int NP = 3, DIN = 17, DOUT = 1, NS = 3, NPW = 0;
-  static __device__ __forceinline__ void fwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, float* s, float* vo) {
-    { // path 0: (0, 1) x (0,1) -> (0, 1)
-      const float t0 = 1.0f * v[0] * g[0];
-      s[0] = t0;
-    }
-    { // path 1: (1, -1) x (1,-1) -> (0, 1)
-      const float t0 = 0.5773502691896257f * v[1] * g[1] + 0.5773502691896258f * v[2] * g[2] + 0.5773502691896257f * v[3] * g[3];
-      s[1] = t0;
-    }
-    { // path 2: (2, 1) x (2,1) -> (0, 1)
-      const float t0 = 0.4472135954999579f * v[7] * g[4] + 0.4472135954999579f * v[8] * g[5] + 0.44721359549995804f * v[9] * g[6] + 0.4472135954999579f * v[10] * g[7] + 0.4472135954999579f * v[11] * g[8];
-      s[2] = t0;
-    }
-  }
-  static __device__ __forceinline__ void bwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, const float* __restrict__ gs, const float* __restrict__ gvo, float* gv, float* gg) {
-    { // path 0
-      const float gt0 = gs[0];
-      gv[0] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[0];
-    }
-    { // path 1
-      const float gt0 = gs[1];
-      gv[1] += 0.5773502691896257f * gt0 * g[1]; gg[1] += 0.5773502691896257f * gt0 * v[1];
-      gv[2] += 0.5773502691896258f * gt0 * g[2]; gg[2] += 0.5773502691896258f * gt0 * v[2];
-      gv[3] += 0.5773502691896257f * gt0 * g[3]; gg[3] += 0.5773502691896257f * gt0 * v[3];
-    }
-    { // path 2
-      const float gt0 = gs[2];
-      gv[7] += 0.4472135954999579f * gt0 * g[4]; gg[4] += 0.4472135954999579f * gt0 * v[7];
-      gv[8] += 0.4472135954999579f * gt0 * g[5]; gg[5] += 0.4472135954999579f * gt0 * v[8];
-      gv[9] += 0.44721359549995804f * gt0 * g[6]; gg[6] += 0.44721359549995804f * gt0 * v[9];
-      gv[10] += 0.4472135954999579f * gt0 * g[7]; gg[7] += 0.4472135954999579f * gt0 * v[10];
-      gv[11] += 0.4472135954999579f * gt0 * g[8]; gg[8] += 0.4472135954999579f * gt0 * v[11];
-    }
-  }
-  static constexpr int NNZ = 9;
-};
-
-template <> struct TP<2, 2, 0> {
-  // in irreps [(0, 1), (0, -1), (1, -1), (1, 1), (2, 1), (2, -1)]; out irreps [(0, 1), (0, -1), (1, -1), (1, 1), (2, 1), (2, -1)]
-  static constexpr int NP = 30, DIN = 18, DOUT = 18, NS = 3, NPW = 30;
+  // in irreps [(0, 1), (1, -1), (1, 1), (2, 1), (2, -1)]; out irreps [(0, 1), (1, -1), (2, 1)]
+  static constexpr int NP = 27, DIN = 17, DOUT = 9, NS = 3, NPW = 27;
   static __device__ __forceinline__ void fwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, float* s, float* vo) {
     #pragma unroll
-    for (int k = 0; k < 18; ++k) vo[k] = 0.f;
+    for (int k = 0; k < 9; ++k) vo[k] = 0.f;
     { // path 0: (0, 1) x (0,1) -> (0, 1)
       const float t0 = 1.0f * v[0] * g[0];
       s[0] = t0;
@@ -1729,9 +1991,9 @@ template <> struct TP<2, 2, 0> {
       const float t1 = 1.0000000000000002f * v[0] * g[2];
       const float t2 = 0.9999999999999999f * v[0] * g[3];
       const float w = th[1] * 0.4082482904638631f;
-      vo[2] += w * t0;
-      vo[3] += w * t1;
-      vo[4] += w * t2;
+      vo[1] += w * t0;
+      vo[2] += w * t1;
+      vo[3] += w * t2;
     }
     { // path 2: (0, 1) x (2,1) -> (2, 1)
       const float t0 = 1.0f * v[0] * g[4];
@@ -1740,280 +2002,133 @@ template <> struct TP<2, 2, 0> {
       const float t3 = 1.0f * v[0] * g[7];
       const float t4 = 1.0f * v[0] * g[8];
       const float w = th[2] * 0.4082482904638631f;
-      vo[8] += w * t0;
-      vo[9] += w * t1;
-      vo[10] += w * t2;
-      vo[11] += w * t3;
-      vo[12] += w * t4;
+      vo[4] += w * t0;
+      vo[5] += w * t1;
+      vo[6] += w * t2;
+      vo[7] += w * t3;
+      vo[8] += w * t4;
     }
-    { // path 3: (0, -1) x (0,1) -> (0, -1)
-      const float t0 = 1.0f * v[1] * g[0];
-      const float w = th[3] * 0.5773502691896258f;
+    { // path 3: (1, -1) x (0,1) -> (1, -1)
+      const float t0 = 0.9999999999999999f * v[1] * g[0];
+      const float t1 = 1.0000000000000002f * v[2] * g[0];
+      const float t2 = 0.9999999999999999f * v[3] * g[0];
+      const float w = th[3] * 0.4082482904638631f;
       vo[1] += w * t0;
+      vo[2] += w * t1;
+      vo[3] += w * t2;
     }
-    { // path 4: (0, -1) x (1,-1) -> (1, 1)
-      const float t0 = 0.9999999999999999f * v[1] * g[1];
-      const float t1 = 1.0000000000000002f * v[1] * g[2];
-      const float t2 = 0.9999999999999999f * v[1] * g[3];
-      const float w = th[4] * 0.4082482904638631f;
-      vo[5] += w * t0;
-      vo[6] += w * t1;
-      vo[7] += w * t2;
-    }
-    { // path 5: (0, -1) x (2,1) -> (2, -1)
-      const float t0 = 1.0f * v[1] * g[4];
-      const float t1 = 1.0f * v[1] * g[5];
-      const float t2 = 1.0000000000000002f * v[1] * g[6];
-      const float t3 = 1.0f * v[1] * g[7];
-      const float t4 = 1.0f * v[1] * g[8];
-      const float w = th[5] * 0.4082482904638631f;
-      vo[13] += w * t0;
-      vo[14] += w * t1;
-      vo[15] += w * t2;
-      vo[16] += w * t3;
-      vo[17] += w * t4;
-    }
-    { // path 6: (1, -1) x (0,1) -> (1, -1)
-      const float t0 = 0.9999999999999999f * v[2] * g[0];
-      const float t1 = 1.0000000000000002f * v[3] * g[0];
-      const float t2 = 0.9999999999999999f * v[4] * g[0];
-      const float w = th[6] * 0.4082482904638631f;
-      vo[2] += w * t0;
-      vo[3] += w * t1;
-      vo[4] += w * t2;
-    }
-    { // path 7: (1, -1) x (1,-1) -> (0, 1)
-      const float t0 = 0.5773502691896257f * v[2] * g[1] + 0.5773502691896258f * v[3] * g[2] + 0.5773502691896257f * v[4] * g[3];
+    { // path 4: (1, -1) x (1,-1) -> (0, 1)
+      const float t0 = 0.5773502691896257f * v[1] * g[1] + 0.5773502691896258f * v[2] * g[2] + 0.5773502691896257f * v[3] * g[3];
       s[1] = t0;
-      const float w = th[7] * 0.5773502691896258f;
+      const float w = th[4] * 0.5773502691896258f;
       vo[0] += w * t0;
     }
-    { // path 8: (1, -1) x (1,-1) -> (1, 1)
-      const float t0 = 0.7071067811865476f * v[3] * g[3] + -0.7071067811865476f * v[4] * g[2];
-      const float t1 = -0.7071067811865476f * v[2] * g[3] + 0.7071067811865476f * v[4] * g[1];
-      const float t2 = 0.7071067811865476f * v[2] * g[2] + -0.7071067811865476f * v[3] * g[1];
-      const float w = th[8] * 0.4082482904638631f;
-      vo[5] += w * t0;
-      vo[6] += w * t1;
-      vo[7] += w * t2;
+    { // path 6: (1, -1) x (1,-1) -> (2, 1)
+      const float t0 = -0.7071067811865475f * v[1] * g[3] + -0.7071067811865475f * v[3] * g[1];
+      const float t1 = -0.7071067811865476f * v[1] * g[2] + -0.7071067811865476f * v[2] * g[1];
+      const float t2 = 0.4082482904638631f * v[1] * g[1] + -0.8164965809277261f * v[2] * g[2] + 0.4082482904638631f * v[3] * g[3];
+      const float t3 = -0.7071067811865476f * v[2] * g[3] + -0.7071067811865476f * v[3] * g[2];
+      const float t4 = 0.7071067811865475f * v[1] * g[1] + -0.7071067811865475f * v[3] * g[3];
+      const float w = th[6] * 0.4082482904638631f;
+      vo[4] += w * t0;
+      vo[5] += w * t1;
+      vo[6] += w * t2;
+      vo[7] += w * t3;
+      vo[8] += w * t4;
     }
-    { // path 9: (1, -1) x (1,-1) -> (2, 1)
-      const float t0 = -0.7071067811865475f * v[2] * g[3] + -0.7071067811865475f * v[4] * g[1];
-      const float t1 = -0.7071067811865476f * v[2] * g[2] + -0.7071067811865476f * v[3] * g[1];
-      const float t2 = 0.4082482904638631f * v[2] * g[1] + -0.8164965809277261f * v[3] * g[2] + 0.4082482904638631f * v[4] * g[3];
-      const float t3 = -0.7071067811865476f * v[3] * g[3] + -0.7071067811865476f * v[4] * g[2];
-      const float t4 = 0.7071067811865475f * v[2] * g[1] + -0.7071067811865475f * v[4] * g[3];
-      const float w = th[9] * 0.4082482904638631f;
-      vo[8] += w * t0;
-      vo[9] += w * t1;
-      vo[10] += w * t2;
-      vo[11] += w * t3;
-      vo[12] += w * t4;
+    { // path 7: (1, -1) x (2,1) -> (1, -1)
+      const float t0 = -0.3162277660168379f * v[1] * g[6] + -0.547722557505166f * v[1] * g[8] + 0.547722557505166f * v[2] * g[5] + 0.547722557505166f * v[3] * g[4];
+      const float t1 = 0.547722557505166f * v[1] * g[5] + 0.632455532033676f * v[2] * g[6] + 0.547722557505166f * v[3] * g[7];
+      const float t2 = 0.547722557505166f * v[1] * g[4] + 0.547722557505166f * v[2] * g[7] + -0.3162277660168379f * v[3] * g[6] + 0.547722557505166f * v[3] * g[8];
+      const float w = th[7] * 0.4082482904638631f;
+      vo[1] += w * t0;
+      vo[2] += w * t1;
+      vo[3] += w * t2;
     }
-    { // path 10: (1, -1) x (2,1) -> (1, -1)
-      const float t0 = -0.3162277660168379f * v[2] * g[6] + -0.547722557505166f * v[2] * g[8] + 0.547722557505166f * v[3] * g[5] + 0.547722557505166f * v[4] * g[4];
-      const float t1 = 0.547722557505166f * v[2] * g[5] + 0.632455532033676f * v[3] * g[6] + 0.547722557505166f * v[4] * g[7];
-      const float t2 = 0.547722557505166f * v[2] * g[4] + 0.547722557505166f * v[3] * g[7] + -0.3162277660168379f * v[4] * g[6] + 0.547722557505166f * v[4] * g[8];
-      const float w = th[10] * 0.4082482904638631f;
-      vo[2] += w * t0;
-      vo[3] += w * t1;
-      vo[4] += w * t2;
-    }
-    { // path 11: (1, -1) x (2,1) -> (2, -1)
-      const float t0 = -0.408248290463863f * v[2] * g[5] + -0.816496580927726f * v[3] * g[8] + 0.408248290463863f * v[4] * g[7];
-      const float t1 = 0.408248290463863f * v[2] * g[4] + -0.408248290463863f * v[3] * g[7] + 0.7071067811865477f * v[4] * g[6] + 0.408248290463863f * v[4] * g[8];
-      const float t2 = 0.7071067811865477f * v[2] * g[7] + -0.7071067811865477f * v[4] * g[5];
-      const float t3 = -0.7071067811865477f * v[2] * g[6] + 0.408248290463863f * v[2] * g[8] + 0.408248290463863f * v[3] * g[5] + -0.408248290463863f * v[4] * g[4];
-      const float t4 = -0.408248290463863f * v[2] * g[7] + 0.816496580927726f * v[3] * g[4] + -0.408248290463863f * v[4] * g[5];
+    { // path 11: (1, 1) x (1,-1) -> (1, -1)
+      const float t0 = 0.7071067811865476f * v[5] * g[3] + -0.7071067811865476f * v[6] * g[2];
+      const float t1 = -0.7071067811865476f * v[4] * g[3] + 0.7071067811865476f * v[6] * g[1];
+      const float t2 = 0.7071067811865476f * v[4] * g[2] + -0.7071067811865476f * v[5] * g[1];
       const float w = th[11] * 0.4082482904638631f;
-      vo[13] += w * t0;
-      vo[14] += w * t1;
-      vo[15] += w * t2;
-      vo[16] += w * t3;
-      vo[17] += w * t4;
-    }
-    { // path 12: (1, 1) x (0,1) -> (1, 1)
-      const float t0 = 0.9999999999999999f * v[5] * g[0];
-      const float t1 = 1.0000000000000002f * v[6] * g[0];
-      const float t2 = 0.9999999999999999f * v[7] * g[0];
-      const float w = th[12] * 0.4082482904638631f;
-      vo[5] += w * t0;
-      vo[6] += w * t1;
-      vo[7] += w * t2;
-    }
-    { // path 13: (1, 1) x (1,-1) -> (0, -1)
-      const float t0 = 0.5773502691896257f * v[5] * g[1] + 0.5773502691896258f * v[6] * g[2] + 0.5773502691896257f * v[7] * g[3];
-      const float w = th[13] * 0.5773502691896258f;
       vo[1] += w * t0;
+      vo[2] += w * t1;
+      vo[3] += w * t2;
     }
-    { // path 14: (1, 1) x (1,-1) -> (1, -1)
-      const float t0 = 0.7071067811865476f * v[6] * g[3] + -0.7071067811865476f * v[7] * g[2];
-      const float t1 = -0.7071067811865476f * v[5] * g[3] + 0.7071067811865476f * v[7] * g[1];
-      const float t2 = 0.7071067811865476f * v[5] * g[2] + -0.7071067811865476f * v[6] * g[1];
+    { // path 14: (1, 1) x (2,1) -> (2, 1)
+      const float t0 = -0.408248290463863f * v[4] * g[5] + -0.816496580927726f * v[5] * g[8] + 0.408248290463863f * v[6] * g[7];
+      const float t1 = 0.408248290463863f * v[4] * g[4] + -0.408248290463863f * v[5] * g[7] + 0.7071067811865477f * v[6] * g[6] + 0.408248290463863f * v[6] * g[8];
+      const float t2 = 0.7071067811865477f * v[4] * g[7] + -0.7071067811865477f * v[6] * g[5];
+      const float t3 = -0.7071067811865477f * v[4] * g[6] + 0.408248290463863f * v[4] * g[8] + 0.408248290463863f * v[5] * g[5] + -0.408248290463863f * v[6] * g[4];
+      const float t4 = -0.408248290463863f * v[4] * g[7] + 0.816496580927726f * v[5] * g[4] + -0.408248290463863f * v[6] * g[5];
       const float w = th[14] * 0.4082482904638631f;
-      vo[2] += w * t0;
-      vo[3] += w * t1;
-      vo[4] += w * t2;
+      vo[4] += w * t0;
+      vo[5] += w * t1;
+      vo[6] += w * t2;
+      vo[7] += w * t3;
+      vo[8] += w * t4;
     }
-    { // path 15: (1, 1) x (1,-1) -> (2, -1)
-      const float t0 = -0.7071067811865475f * v[5] * g[3] + -0.7071067811865475f * v[7] * g[1];
-      const float t1 = -0.7071067811865476f * v[5] * g[2] + -0.7071067811865476f * v[6] * g[1];
-      const float t2 = 0.4082482904638631f * v[5] * g[1] + -0.8164965809277261f * v[6] * g[2] + 0.4082482904638631f * v[7] * g[3];
-      const float t3 = -0.7071067811865476f * v[6] * g[3] + -0.7071067811865476f * v[7] * g[2];
-      const float t4 = 0.7071067811865475f * v[5] * g[1] + -0.7071067811865475f * v[7] * g[3];
+    { // path 15: (2, 1) x (0,1) -> (2, 1)
+      const float t0 = 1.0f * v[7] * g[0];
+      const float t1 = 1.0f * v[8] * g[0];
+      const float t2 = 1.0000000000000002f * v[9] * g[0];
+      const float t3 = 1.0f * v[10] * g[0];
+      const float t4 = 1.0f * v[11] * g[0];
       const float w = th[15] * 0.4082482904638631f;
-      vo[13] += w * t0;
-      vo[14] += w * t1;
-      vo[15] += w * t2;
-      vo[16] += w * t3;
-      vo[17] += w * t4;
+      vo[4] += w * t0;
+      vo[5] += w * t1;
+      vo[6] += w * t2;
+      vo[7] += w * t3;
+      vo[8] += w * t4;
     }
-    { // path 16: (1, 1) x (2,1) -> (1, 1)
-      const float t0 = -0.3162277660168379f * v[5] * g[6] + -0.547722557505166f * v[5] * g[8] + 0.547722557505166f * v[6] * g[5] + 0.547722557505166f * v[7] * g[4];
-      const float t1 = 0.547722557505166f * v[5] * g[5] + 0.632455532033676f * v[6] * g[6] + 0.547722557505166f * v[7] * g[7];
-      const float t2 = 0.547722557505166f * v[5] * g[4] + 0.547722557505166f * v[6] * g[7] + -0.3162277660168379f * v[7] * g[6] + 0.547722557505166f * v[7] * g[8];
+    { // path 16: (2, 1) x (1,-1) -> (1, -1)
+      const float t0 = 0.547722557505166f * v[7] * g[3] + 0.547722557505166f * v[8] * g[2] + -0.3162277660168379f * v[9] * g[1] + -0.547722557505166f * v[11] * g[1];
+      const float t1 = 0.547722557505166f * v[8] * g[1] + 0.632455532033676f * v[9] * g[2] + 0.547722557505166f * v[10] * g[3];
+      const float t2 = 0.547722557505166f * v[7] * g[1] + -0.3162277660168379f * v[9] * g[3] + 0.547722557505166f * v[10] * g[2] + 0.547722557505166f * v[11] * g[3];
       const float w = th[16] * 0.4082482904638631f;
-      vo[5] += w * t0;
-      vo[6] += w * t1;
-      vo[7] += w * t2;
+      vo[1] += w * t0;
+      vo[2] += w * t1;
+      vo[3] += w * t2;
     }
-    { // path 17: (1, 1) x (2,1) -> (2, 1)
-      const float t0 = -0.408248290463863f * v[5] * g[5] + -0.816496580927726f * v[6] * g[8] + 0.408248290463863f * v[7] * g[7];
-      const float t1 = 0.408248290463863f * v[5] * g[4] + -0.408248290463863f * v[6] * g[7] + 0.7071067811865477f * v[7] * g[6] + 0.408248290463863f * v[7] * g[8];
-      const float t2 = 0.7071067811865477f * v[5] * g[7] + -0.7071067811865477f * v[7] * g[5];
-      const float t3 = -0.7071067811865477f * v[5] * g[6] + 0.408248290463863f * v[5] * g[8] + 0.408248290463863f * v[6] * g[5] + -0.408248290463863f * v[7] * g[4];
-      const float t4 = -0.408248290463863f * v[5] * g[7] + 0.816496580927726f * v[6] * g[4] + -0.408248290463863f * v[7] * g[5];
-      const float w = th[17] * 0.4082482904638631f;
-      vo[8] += w * t0;
-      vo[9] += w * t1;
-      vo[10] += w * t2;
-      vo[11] += w * t3;
-      vo[12] += w * t4;
-    }
-    { // path 18: (2, 1) x (0,1) -> (2, 1)
-      const float t0 = 1.0f * v[8] * g[0];
-      const float t1 = 1.0f * v[9] * g[0];
-      const float t2 = 1.0000000000000002f * v[10] * g[0];
-      const float t3 = 1.0f * v[11] * g[0];
-      const float t4 = 1.0f * v[12] * g[0];
-      const float w = th[18] * 0.4082482904638631f;
-      vo[8] += w * t0;
-      vo[9] += w * t1;
-      vo[10] += w * t2;
-      vo[11] += w * t3;
-      vo[12] += w * t4;
-    }
-    { // path 19: (2, 1) x (1,-1) -> (1, -1)
-      const float t0 = 0.547722557505166f * v[8] * g[3] + 0.547722557505166f * v[9] * g[2] + -0.3162277660168379f * v[10] * g[1] + -0.547722557505166f * v[12] * g[1];
-      const float t1 = 0.547722557505166f * v[9] * g[1] + 0.632455532033676f * v[10] * g[2] + 0.547722557505166f * v[11] * g[3];
-      const float t2 = 0.547722557505166f * v[8] * g[1] + -0.3162277660168379f * v[10] * g[3] + 0.547722557505166f * v[11] * g[2] + 0.547722557505166f * v[12] * g[3];
-      const float w = th[19] * 0.4082482904638631f;
-      vo[2] += w * t0;
-      vo[3] += w * t1;
-      vo[4] += w * t2;
-    }
-    { // path 20: (2, 1) x (1,-1) -> (2, -1)
-      const float t0 = -0.408248290463863f * v[9] * g[1] + 0.408248290463863f * v[11] * g[3] + -0.816496580927726f * v[12] * g[2];
-      const float t1 = 0.408248290463863f * v[8] * g[1] + 0.7071067811865477f * v[10] * g[3] + -0.408248290463863f * v[11] * g[2] + 0.408248290463863f * v[12] * g[3];
-      const float t2 = -0.7071067811865477f * v[9] * g[3] + 0.7071067811865477f * v[11] * g[1];
-      const float t3 = -0.408248290463863f * v[8] * g[3] + 0.408248290463863f * v[9] * g[2] + -0.7071067811865477f * v[10] * g[1] + 0.408248290463863f * v[12] * g[1];
-      const float t4 = 0.816496580927726f * v[8] * g[2] + -0.408248290463863f * v[9] * g[3] + -0.408248290463863f * v[11] * g[1];
-      const float w = th[20] * 0.4082482904638631f;
-      vo[13] += w * t0;
-      vo[14] += w * t1;
-      vo[15] += w * t2;
-      vo[16] += w * t3;
-      vo[17] += w * t4;
-    }
-    { // path 21: (2, 1) x (2,1) -> (0, 1)
-      const float t0 = 0.4472135954999579f * v[8] * g[4] + 0.4472135954999579f * v[9] * g[5] + 0.44721359549995804f * v[10] * g[6] + 0.4472135954999579f * v[11] * g[7] + 0.4472135954999579f * v[12] * g[8];
+    { // path 18: (2, 1) x (2,1) -> (0, 1)
+      const float t0 = 0.4472135954999579f * v[7] * g[4] + 0.4472135954999579f * v[8] * g[5] + 0.44721359549995804f * v[9] * g[6] + 0.4472135954999579f * v[10] * g[7] + 0.4472135954999579f * v[11] * g[8];
       s[2] = t0;
-      const float w = th[21] * 0.5773502691896258f;
+      const float w = th[18] * 0.5773502691896258f;
       vo[0] += w * t0;
     }
-    { // path 22: (2, 1) x (2,1) -> (1, 1)
-      const float t0 = 0.3162277660168379f * v[8] * g[5] + -0.3162277660168379f * v[9] * g[4] + -0.5477225575051661f * v[10] * g[7] + 0.5477225575051661f * v[11] * g[6] + -0.3162277660168379f * v[11] * g[8] + 0.3162277660168379f * v[12] * g[7];
-      const float t1 = 0.6324555320336758f * v[8] * g[8] + 0.3162277660168379f * v[9] * g[7] + -0.3162277660168379f * v[11] * g[5] + -0.6324555320336758f * v[12] * g[4];
-      const float t2 = -0.3162277660168379f * v[8] * g[7] + -0.5477225575051661f * v[9] * g[6] + -0.3162277660168379f * v[9] * g[8] + 0.5477225575051661f * v[10] * g[5] + 0.3162277660168379f * v[11] * g[4] + 0.3162277660168379f * v[12] * g[5];
-      const float w = th[22] * 0.4082482904638631f;
-      vo[5] += w * t0;
-      vo[6] += w * t1;
-      vo[7] += w * t2;
+    { // path 20: (2, 1) x (2,1) -> (2, 1)
+      const float t0 = 0.5345224838248488f * v[7] * g[6] + -0.4629100498862757f * v[8] * g[7] + 0.5345224838248488f * v[9] * g[4] + -0.4629100498862757f * v[10] * g[5];
+      const float t1 = -0.4629100498862757f * v[7] * g[7] + -0.2672612419124244f * v[8] * g[6] + 0.4629100498862757f * v[8] * g[8] + -0.2672612419124244f * v[9] * g[5] + -0.4629100498862757f * v[10] * g[4] + 0.4629100498862757f * v[11] * g[5];
+      const float t2 = 0.5345224838248488f * v[7] * g[4] + -0.2672612419124244f * v[8] * g[5] + -0.5345224838248489f * v[9] * g[6] + -0.2672612419124244f * v[10] * g[7] + 0.5345224838248488f * v[11] * g[8];
+      const float t3 = -0.4629100498862757f * v[7] * g[5] + -0.4629100498862757f * v[8] * g[4] + -0.2672612419124244f * v[9] * g[7] + -0.2672612419124244f * v[10] * g[6] + -0.4629100498862757f * v[10] * g[8] + -0.4629100498862757f * v[11] * g[7];
+      const float t4 = 0.4629100498862757f * v[8] * g[5] + 0.5345224838248488f * v[9] * g[8] + -0.4629100498862757f * v[10] * g[7] + 0.5345224838248488f * v[11] * g[6];
+      const float w = th[20] * 0.4082482904638631f;
+      vo[4] += w * t0;
+      vo[5] += w * t1;
+      vo[6] += w * t2;
+      vo[7] += w * t3;
+      vo[8] += w * t4;
     }
-    { // path 23: (2, 1) x (2,1) -> (2, 1)
-      const float t0 = 0.5345224838248488f * v[8] * g[6] + -0.4629100498862757f * v[9] * g[7] + 0.5345224838248488f * v[10] * g[4] + -0.4629100498862757f * v[11] * g[5];
-      const float t1 = -0.4629100498862757f * v[8] * g[7] + -0.2672612419124244f * v[9] * g[6] + 0.4629100498862757f * v[9] * g[8] + -0.2672612419124244f * v[10] * g[5] + -0.4629100498862757f * v[11] * g[4] + 0.4629100498862757f * v[12] * g[5];
-      const float t2 = 0.5345224838248488f * v[8] * g[4] + -0.2672612419124244f * v[9] * g[5] + -0.5345224838248489f * v[10] * g[6] + -0.2672612419124244f * v[11] * g[7] + 0.5345224838248488f * v[12] * g[8];
-      const float t3 = -0.4629100498862757f * v[8] * g[5] + -0.4629100498862757f * v[9] * g[4] + -0.2672612419124244f * v[10] * g[7] + -0.2672612419124244f * v[11] * g[6] + -0.4629100498862757f * v[11] * g[8] + -0.4629100498862757f * v[12] * g[7];
-      const float t4 = 0.4629100498862757f * v[9] * g[5] + 0.5345224838248488f * v[10] * g[8] + -0.4629100498862757f * v[11] * g[7] + 0.5345224838248488f * v[12] * g[6];
+    { // path 23: (2, -1) x (1,-1) -> (2, 1)
+      const float t0 = -0.408248290463863f * v[13] * g[1] + 0.408248290463863f * v[15] * g[3] + -0.816496580927726f * v[16] * g[2];
+      const float t1 = 0.408248290463863f * v[12] * g[1] + 0.7071067811865477f * v[14] * g[3] + -0.408248290463863f * v[15] * g[2] + 0.408248290463863f * v[16] * g[3];
+      const float t2 = -0.7071067811865477f * v[13] * g[3] + 0.7071067811865477f * v[15] * g[1];
+      const float t3 = -0.408248290463863f * v[12] * g[3] + 0.408248290463863f * v[13] * g[2] + -0.7071067811865477f * v[14] * g[1] + 0.408248290463863f * v[16] * g[1];
+      const float t4 = 0.816496580927726f * v[12] * g[2] + -0.408248290463863f * v[13] * g[3] + -0.408248290463863f * v[15] * g[1];
       const float w = th[23] * 0.4082482904638631f;
-      vo[8] += w * t0;
-      vo[9] += w * t1;
-      vo[10] += w * t2;
-      vo[11] += w * t3;
-      vo[12] += w * t4;
+      vo[4] += w * t0;
+      vo[5] += w * t1;
+      vo[6] += w * t2;
+      vo[7] += w * t3;
+      vo[8] += w * t4;
     }
-    { // path 24: (2, -1) x (0,1) -> (2, -1)
-      const float t0 = 1.0f * v[13] * g[0];
-      const float t1 = 1.0f * v[14] * g[0];
-      const float t2 = 1.0000000000000002f * v[15] * g[0];
-      const float t3 = 1.0f * v[16] * g[0];
-      const float t4 = 1.0f * v[17] * g[0];
-      const float w = th[24] * 0.4082482904638631f;
-      vo[13] += w * t0;
-      vo[14] += w * t1;
-      vo[15] += w * t2;
-      vo[16] += w * t3;
-      vo[17] += w * t4;
-    }
-    { // path 25: (2, -1) x (1,-1) -> (1, 1)
-      const float t0 = 0.547722557505166f * v[13] * g[3] + 0.547722557505166f * v[14] * g[2] + -0.3162277660168379f * v[15] * g[1] + -0.547722557505166f * v[17] * g[1];
-      const float t1 = 0.547722557505166f * v[14] * g[1] + 0.632455532033676f * v[15] * g[2] + 0.547722557505166f * v[16] * g[3];
-      const float t2 = 0.547722557505166f * v[13] * g[1] + -0.3162277660168379f * v[15] * g[3] + 0.547722557505166f * v[16] * g[2] + 0.547722557505166f * v[17] * g[3];
+    { // path 25: (2, -1) x (2,1) -> (1, -1)
+      const float t0 = 0.3162277660168379f * v[12] * g[5] + -0.3162277660168379f * v[13] * g[4] + -0.5477225575051661f * v[14] * g[7] + 0.5477225575051661f * v[15] * g[6] + -0.3162277660168379f * v[15] * g[8] + 0.3162277660168379f * v[16] * g[7];
+      const float t1 = 0.6324555320336758f * v[12] * g[8] + 0.3162277660168379f * v[13] * g[7] + -0.3162277660168379f * v[15] * g[5] + -0.6324555320336758f * v[16] * g[4];
+      const float t2 = -0.3162277660168379f * v[12] * g[7] + -0.5477225575051661f * v[13] * g[6] + -0.3162277660168379f * v[13] * g[8] + 0.5477225575051661f * v[14] * g[5] + 0.3162277660168379f * v[15] * g[4] + 0.3162277660168379f * v[16] * g[5];
       const float w = th[25] * 0.4082482904638631f;
-      vo[5] += w * t0;
-      vo[6] += w * t1;
-      vo[7] += w * t2;
-    }
-    { // path 26: (2, -1) x (1,-1) -> (2, 1)
-      const float t0 = -0.408248290463863f * v[14] * g[1] + 0.408248290463863f * v[16] * g[3] + -0.816496580927726f * v[17] * g[2];
-      const float t1 = 0.408248290463863f * v[13] * g[1] + 0.7071067811865477f * v[15] * g[3] + -0.408248290463863f * v[16] * g[2] + 0.408248290463863f * v[17] * g[3];
-      const float t2 = -0.7071067811865477f * v[14] * g[3] + 0.7071067811865477f * v[16] * g[1];
-      const float t3 = -0.408248290463863f * v[13] * g[3] + 0.408248290463863f * v[14] * g[2] + -0.7071067811865477f * v[15] * g[1] + 0.408248290463863f * v[17] * g[1];
-      const float t4 = 0.816496580927726f * v[13] * g[2] + -0.408248290463863f * v[14] * g[3] + -0.408248290463863f * v[16] * g[1];
-      const float w = th[26] * 0.4082482904638631f;
-      vo[8] += w * t0;
-      vo[9] += w * t1;
-      vo[10] += w * t2;
-      vo[11] += w * t3;
-      vo[12] += w * t4;
-    }
-    { // path 27: (2, -1) x (2,1) -> (0, -1)
-      const float t0 = 0.4472135954999579f * v[13] * g[4] + 0.4472135954999579f * v[14] * g[5] + 0.44721359549995804f * v[15] * g[6] + 0.4472135954999579f * v[16] * g[7] + 0.4472135954999579f * v[17] * g[8];
-      const float w = th[27] * 0.5773502691896258f;
       vo[1] += w * t0;
-    }
-    { // path 28: (2, -1) x (2,1) -> (1, -1)
-      const float t0 = 0.3162277660168379f * v[13] * g[5] + -0.3162277660168379f * v[14] * g[4] + -0.5477225575051661f * v[15] * g[7] + 0.5477225575051661f * v[16] * g[6] + -0.3162277660168379f * v[16] * g[8] + 0.3162277660168379f * v[17] * g[7];
-      const float t1 = 0.6324555320336758f * v[13] * g[8] + 0.3162277660168379f * v[14] * g[7] + -0.3162277660168379f * v[16] * g[5] + -0.6324555320336758f * v[17] * g[4];
-      const float t2 = -0.3162277660168379f * v[13] * g[7] + -0.5477225575051661f * v[14] * g[6] + -0.3162277660168379f * v[14] * g[8] + 0.5477225575051661f * v[15] * g[5] + 0.3162277660168379f * v[16] * g[4] + 0.3162277660168379f * v[17] * g[5];
-      const float w = th[28] * 0.4082482904638631f;
-      vo[2] += w * t0;
-      vo[3] += w * t1;
-      vo[4] += w * t2;
-    }
-    { // path 29: (2, -1) x (2,1) -> (2, -1)
-      const float t0 = 0.5345224838248488f * v[13] * g[6] + -0.4629100498862757f * v[14] * g[7] + 0.5345224838248488f * v[15] * g[4] + -0.4629100498862757f * v[16] * g[5];
-      const float t1 = -0.4629100498862757f * v[13] * g[7] + -0.2672612419124244f * v[14] * g[6] + 0.4629100498862757f * v[14] * g[8] + -0.2672612419124244f * v[15] * g[5] + -0.4629100498862757f * v[16] * g[4] + 0.4629100498862757f * v[17] * g[5];
-      const float t2 = 0.5345224838248488f * v[13] * g[4] + -0.2672612419124244f * v[14] * g[5] + -0.5345224838248489f * v[15] * g[6] + -0.2672612419124244f * v[16] * g[7] + 0.5345224838248488f * v[17] * g[8];
-      const float t3 = -0.4629100498862757f * v[13] * g[5] + -0.4629100498862757f * v[14] * g[4] + -0.2672612419124244f * v[15] * g[7] + -0.2672612419124244f * v[16] * g[6] + -0.4629100498862757f * v[16] * g[8] + -0.4629100498862757f * v[17] * g[7];
-      const float t4 = 0.4629100498862757f * v[14] * g[5] + 0.5345224838248488f * v[15] * g[8] + -0.4629100498862757f * v[16] * g[7] + 0.5345224838248488f * v[17] * g[6];
-      const float w = th[29] * 0.4082482904638631f;
-      vo[13] += w * t0;
-      vo[14] += w * t1;
-      vo[15] += w * t2;
-      vo[16] += w * t3;
-      vo[17] += w * t4;
+      vo[2] += w * t1;
+      vo[3] += w * t2;
     }
   }
   static __device__ __forceinline__ void bwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, const float* __restrict__ gs, const float* __restrict__ gvo, float* gv, float* gg) {
@@ -2024,20 +2139,20 @@ template <> struct TP<2, 2, 0> {
     }
     { // path 1
       const float w = th[1] * 0.4082482904638631f;
-      const float gt0 = w * gvo[2];
-      const float gt1 = w * gvo[3];
-      const float gt2 = w * gvo[4];
+      const float gt0 = w * gvo[1];
+      const float gt1 = w * gvo[2];
+      const float gt2 = w * gvo[3];
       gv[0] += 0.9999999999999999f * gt0 * g[1]; gg[1] += 0.9999999999999999f * gt0 * v[0];
       gv[0] += 1.0000000000000002f * gt1 * g[2]; gg[2] += 1.0000000000000002f * gt1 * v[0];
       gv[0] += 0.9999999999999999f * gt2 * g[3]; gg[3] += 0.9999999999999999f * gt2 * v[0];
     }
     { // path 2
       const float w = th[2] * 0.4082482904638631f;
-      const float gt0 = w * gvo[8];
-      const float gt1 = w * gvo[9];
-      const float gt2 = w * gvo[10];
-      const float gt3 = w * gvo[11];
-      const float gt4 = w * gvo[12];
+      const float gt0 = w * gvo[4];
+      const float gt1 = w * gvo[5];
+      const float gt2 = w * gvo[6];
+      const float gt3 = w * gvo[7];
+      const float gt4 = w * gvo[8];
       gv[0] += 1.0f * gt0 * g[4]; gg[4] += 1.0f * gt0 * v[0];
       gv[0] += 1.0f * gt1 * g[5]; gg[5] += 1.0f * gt1 * v[0];
       gv[0] += 1.0000000000000002f * gt2 * g[6]; gg[6] += 1.0000000000000002f * gt2 * v[0];
@@ -2045,37 +2160,405 @@ template <> struct TP<2, 2, 0> {
       gv[0] += 1.0f * gt4 * g[8]; gg[8] += 1.0f * gt4 * v[0];
     }
     { // path 3
-      const float w = th[3] * 0.5773502691896258f;
+      const float w = th[3] * 0.4082482904638631f;
       const float gt0 = w * gvo[1];
-      gv[1] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[1];
+      const float gt1 = w * gvo[2];
+      const float gt2 = w * gvo[3];
+      gv[1] += 0.9999999999999999f * gt0 * g[0]; gg[0] += 0.9999999999999999f * gt0 * v[1];
+      gv[2] += 1.0000000000000002f * gt1 * g[0]; gg[0] += 1.0000000000000002f * gt1 * v[2];
+      gv[3] += 0.9999999999999999f * gt2 * g[0]; gg[0] += 0.9999999999999999f * gt2 * v[3];
     }
     { // path 4
-      const float w = th[4] * 0.4082482904638631f;
-      const float gt0 = w * gvo[5];
-      const float gt1 = w * gvo[6];
-      const float gt2 = w * gvo[7];
-      gv[1] += 0.9999999999999999f * gt0 * g[1]; gg[1] += 0.9999999999999999f * gt0 * v[1];
-      gv[1] += 1.0000000000000002f * gt1 * g[2]; gg[2] += 1.0000000000000002f * gt1 * v[1];
-      gv[1] += 0.9999999999999999f * gt2 * g[3]; gg[3] += 0.9999999999999999f * gt2 * v[1];
-    }
-    { // path 5
-      const float w = th[5] * 0.4082482904638631f;
-      const float gt0 = w * gvo[13];
-      const float gt1 = w * gvo[14];
-      const float gt2 = w * gvo[15];
-      const float gt3 = w * gvo[16];
-      const float gt4 = w * gvo[17];
-      gv[1] += 1.0f * gt0 * g[4]; gg[4] += 1.0f * gt0 * v[1];
-      gv[1] += 1.0f * gt1 * g[5]; gg[5] += 1.0f * gt1 * v[1];
-      gv[1] += 1.0000000000000002f * gt2 * g[6]; gg[6] += 1.0000000000000002f * gt2 * v[1];
-      gv[1] += 1.0f * gt3 * g[7]; gg[7] += 1.0f * gt3 * v[1];
-      gv[1] += 1.0f * gt4 * g[8]; gg[8] += 1.0f * gt4 * v[1];
+      const float w = th[4] * 0.5773502691896258f;
+      const float gt0 = gs[1] + w * gvo[0];
+      gv[1] += 0.5773502691896257f * gt0 * g[1]; gg[1] += 0.5773502691896257f * gt0 * v[1];
+      gv[2] += 0.5773502691896258f * gt0 * g[2]; gg[2] += 0.5773502691896258f * gt0 * v[2];
+      gv[3] += 0.5773502691896257f * gt0 * g[3]; gg[3] += 0.5773502691896257f * gt0 * v[3];
     }
     { // path 6
       const float w = th[6] * 0.4082482904638631f;
-      const float gt0 = w * gvo[2];
-      const float gt1 = w * gvo[3];
-      const float gt2 = w * gvo[4];
+      const float gt0 = w * gvo[4];
+      const float gt1 = w * gvo[5];
+      const float gt2 = w * gvo[6];
+      const float gt3 = w * gvo[7];
+      const float gt4 = w * gvo[8];
+      gv[1] += 0.4082482904638631f * gt2 * g[1]; gg[1] += 0.4082482904638631f * gt2 * v[1];
+      gv[1] += 0.7071067811865475f * gt4 * g[1]; gg[1] += 0.7071067811865475f * gt4 * v[1];
+      gv[1] += -0.7071067811865476f * gt1 * g[2]; gg[2] += -0.7071067811865476f * gt1 * v[1];
+      gv[1] += -0.7071067811865475f * gt0 * g[3]; gg[3] += -0.7071067811865475f * gt0 * v[1];
+      gv[2] += -0.7071067811865476f * gt1 * g[1]; gg[1] += -0.7071067811865476f * gt1 * v[2];
+      gv[2] += -0.8164965809277261f * gt2 * g[2]; gg[2] += -0.8164965809277261f * gt2 * v[2];
+      gv[2] += -0.7071067811865476f * gt3 * g[3]; gg[3] += -0.7071067811865476f * gt3 * v[2];
+      gv[3] += -0.7071067811865475f * gt0 * g[1]; gg[1] += -0.7071067811865475f * gt0 * v[3];
+      gv[3] += -0.7071067811865476f * gt3 * g[2]; gg[2] += -0.7071067811865476f * gt3 * v[3];
+      gv[3] += 0.4082482904638631f * gt2 * g[3]; gg[3] += 0.4082482904638631f * gt2 * v[3];
+      gv[3] += -0.7071067811865475f * gt4 * g[3]; gg[3] += -0.7071067811865475f * gt4 * v[3];
+    }
+    { // path 7
+      const float w = th[7] * 0.4082482904638631f;
+      const float gt0 = w * gvo[1];
+      const float gt1 = w * gvo[2];
+      const float gt2 = w * gvo[3];
+      gv[1] += 0.547722557505166f * gt2 * g[4]; gg[4] += 0.547722557505166f * gt2 * v[1];
+      gv[1] += 0.547722557505166f * gt1 * g[5]; gg[5] += 0.547722557505166f * gt1 * v[1];
+      gv[1] += -0.3162277660168379f * gt0 * g[6]; gg[6] += -0.3162277660168379f * gt0 * v[1];
+      gv[1] += -0.547722557505166f * gt0 * g[8]; gg[8] += -0.547722557505166f * gt0 * v[1];
+      gv[2] += 0.547722557505166f * gt0 * g[5]; gg[5] += 0.547722557505166f * gt0 * v[2];
+      gv[2] += 0.632455532033676f * gt1 * g[6]; gg[6] += 0.632455532033676f * gt1 * v[2];
+      gv[2] += 0.547722557505166f * gt2 * g[7]; gg[7] += 0.547722557505166f * gt2 * v[2];
+      gv[3] += 0.547722557505166f * gt0 * g[4]; gg[4] += 0.547722557505166f * gt0 * v[3];
+      gv[3] += -0.3162277660168379f * gt2 * g[6]; gg[6] += -0.3162277660168379f * gt2 * v[3];
+      gv[3] += 0.547722557505166f * gt1 * g[7]; gg[7] += 0.547722557505166f * gt1 * v[3];
+      gv[3] += 0.547722557505166f * gt2 * g[8]; gg[8] += 0.547722557505166f * gt2 * v[3];
+    }
+    { // path 11
+      const float w = th[11] * 0.4082482904638631f;
+      const float gt0 = w * gvo[1];
+      const float gt1 = w * gvo[2];
+      const float gt2 = w * gvo[3];
+      gv[4] += 0.7071067811865476f * gt2 * g[2]; gg[2] += 0.7071067811865476f * gt2 * v[4];
+      gv[4] += -0.7071067811865476f * gt1 * g[3]; gg[3] += -0.7071067811865476f * gt1 * v[4];
+      gv[5] += -0.7071067811865476f * gt2 * g[1]; gg[1] += -0.7071067811865476f * gt2 * v[5];
+      gv[5] += 0.7071067811865476f * gt0 * g[3]; gg[3] += 0.7071067811865476f * gt0 * v[5];
+      gv[6] += 0.7071067811865476f * gt1 * g[1]; gg[1] += 0.7071067811865476f * gt1 * v[6];
+      gv[6] += -0.7071067811865476f * gt0 * g[2]; gg[2] += -0.7071067811865476f * gt0 * v[6];
+    }
+    { // path 14
+      const float w = th[14] * 0.4082482904638631f;
+      const float gt0 = w * gvo[4];
+      const float gt1 = w * gvo[5];
+      const float gt2 = w * gvo[6];
+      const float gt3 = w * gvo[7];
+      const float gt4 = w * gvo[8];
+      gv[4] += 0.408248290463863f * gt1 * g[4]; gg[4] += 0.408248290463863f * gt1 * v[4];
+      gv[4] += -0.408248290463863f * gt0 * g[5]; gg[5] += -0.408248290463863f * gt0 * v[4];
+      gv[4] += -0.7071067811865477f * gt3 * g[6]; gg[6] += -0.7071067811865477f * gt3 * v[4];
+      gv[4] += 0.7071067811865477f * gt2 * g[7]; gg[7] += 0.7071067811865477f * gt2 * v[4];
+      gv[4] += -0.408248290463863f * gt4 * g[7]; gg[7] += -0.408248290463863f * gt4 * v[4];
+      gv[4] += 0.408248290463863f * gt3 * g[8]; gg[8] += 0.408248290463863f * gt3 * v[4];
+      gv[5] += 0.816496580927726f * gt4 * g[4]; gg[4] += 0.816496580927726f * gt4 * v[5];
+      gv[5] += 0.408248290463863f * gt3 * g[5]; gg[5] += 0.408248290463863f * gt3 * v[5];
+      gv[5] += -0.408248290463863f * gt1 * g[7]; gg[7] += -0.408248290463863f * gt1 * v[5];
+      gv[5] += -0.816496580927726f * gt0 * g[8]; gg[8] += -0.816496580927726f * gt0 * v[5];
+      gv[6] += -0.408248290463863f * gt3 * g[4]; gg[4] += -0.408248290463863f * gt3 * v[6];
+      gv[6] += -0.7071067811865477f * gt2 * g[5]; gg[5] += -0.7071067811865477f * gt2 * v[6];
+      gv[6] += -0.408248290463863f * gt4 * g[5]; gg[5] += -0.408248290463863f * gt4 * v[6];
+      gv[6] += 0.7071067811865477f * gt1 * g[6]; gg[6] += 0.7071067811865477f * gt1 * v[6];
+      gv[6] += 0.408248290463863f * gt0 * g[7]; gg[7] += 0.408248290463863f * gt0 * v[6];
+      gv[6] += 0.408248290463863f * gt1 * g[8]; gg[8] += 0.408248290463863f * gt1 * v[6];
+    }
+    { // path 15
+      const float w = th[15] * 0.4082482904638631f;
+      const float gt0 = w * gvo[4];
+      const float gt1 = w * gvo[5];
+      const float gt2 = w * gvo[6];
+      const float gt3 = w * gvo[7];
+      const float gt4 = w * gvo[8];
+      gv[7] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[7];
+      gv[8] += 1.0f * gt1 * g[0]; gg[0] += 1.0f * gt1 * v[8];
+      gv[9] += 1.0000000000000002f * gt2 * g[0]; gg[0] += 1.0000000000000002f * gt2 * v[9];
+      gv[10] += 1.0f * gt3 * g[0]; gg[0] += 1.0f * gt3 * v[10];
+      gv[11] += 1.0f * gt4 * g[0]; gg[0] += 1.0f * gt4 * v[11];
+    }
+    { // path 16
+      const float w = th[16] * 0.4082482904638631f;
+      const float gt0 = w * gvo[1];
+      const float gt1 = w * gvo[2];
+      const float gt2 = w * gvo[3];
+      gv[7] += 0.547722557505166f * gt2 * g[1]; gg[1] += 0.547722557505166f * gt2 * v[7];
+      gv[7] += 0.547722557505166f * gt0 * g[3]; gg[3] += 0.547722557505166f * gt0 * v[7];
+      gv[8] += 0.547722557505166f * gt1 * g[1]; gg[1] += 0.547722557505166f * gt1 * v[8];
+      gv[8] += 0.547722557505166f * gt0 * g[2]; gg[2] += 0.547722557505166f * gt0 * v[8];
+      gv[9] += -0.3162277660168379f * gt0 * g[1]; gg[1] += -0.3162277660168379f * gt0 * v[9];
+      gv[9] += 0.632455532033676f * gt1 * g[2]; gg[2] += 0.632455532033676f * gt1 * v[9];
+      gv[9] += -0.3162277660168379f * gt2 * g[3]; gg[3] += -0.3162277660168379f * gt2 * v[9];
+      gv[10] += 0.547722557505166f * gt2 * g[2]; gg[2] += 0.547722557505166f * gt2 * v[10];
+      gv[10] += 0.547722557505166f * gt1 * g[3]; gg[3] += 0.547722557505166f * gt1 * v[10];
+      gv[11] += -0.547722557505166f * gt0 * g[1]; gg[1] += -0.547722557505166f * gt0 * v[11];
+      gv[11] += 0.547722557505166f * gt2 * g[3]; gg[3] += 0.547722557505166f * gt2 * v[11];
+    }
+    { // path 18
+      const float w = th[18] * 0.5773502691896258f;
+      const float gt0 = gs[2] + w * gvo[0];
+      gv[7] += 0.4472135954999579f * gt0 * g[4]; gg[4] += 0.4472135954999579f * gt0 * v[7];
+      gv[8] += 0.4472135954999579f * gt0 * g[5]; gg[5] += 0.4472135954999579f * gt0 * v[8];
+      gv[9] += 0.44721359549995804f * gt0 * g[6]; gg[6] += 0.44721359549995804f * gt0 * v[9];
+      gv[10] += 0.4472135954999579f * gt0 * g[7]; gg[7] += 0.4472135954999579f * gt0 * v[10];
+      gv[11] += 0.4472135954999579f * gt0 * g[8]; gg[8] += 0.4472135954999579f * gt0 * v[11];
+    }
+    { // path 20
+      const float w = th[20] * 0.4082482904638631f;
+      const float gt0 = w * gvo[4];
+      const float gt1 = w * gvo[5];
+      const float gt2 = w * gvo[6];
+      const float gt3 = w * gvo[7];
+      const float gt4 = w * gvo[8];
+      gv[7] += 0.5345224838248488f * gt2 * g[4]; gg[4] += 0.5345224838248488f * gt2 * v[7];
+      gv[7] += -0.4629100498862757f * gt3 * g[5]; gg[5] += -0.4629100498862757f * gt3 * v[7];
+      gv[7] += 0.5345224838248488f * gt0 * g[6]; gg[6] += 0.5345224838248488f * gt0 * v[7];
+      gv[7] += -0.4629100498862757f * gt1 * g[7]; gg[7] += -0.4629100498862757f * gt1 * v[7];
+      gv[8] += -0.4629100498862757f * gt3 * g[4]; gg[4] += -0.4629100498862757f * gt3 * v[8];
+      gv[8] += -0.2672612419124244f * gt2 * g[5]; gg[5] += -0.2672612419124244f * gt2 * v[8];
+      gv[8] += 0.4629100498862757f * gt4 * g[5]; gg[5] += 0.4629100498862757f * gt4 * v[8];
+      gv[8] += -0.2672612419124244f * gt1 * g[6]; gg[6] += -0.2672612419124244f * gt1 * v[8];
+      gv[8] += -0.4629100498862757f * gt0 * g[7]; gg[7] += -0.4629100498862757f * gt0 * v[8];
+      gv[8] += 0.4629100498862757f * gt1 * g[8]; gg[8] += 0.4629100498862757f * gt1 * v[8];
+      gv[9] += 0.5345224838248488f * gt0 * g[4]; gg[4] += 0.5345224838248488f * gt0 * v[9];
+      gv[9] += -0.2672612419124244f * gt1 * g[5]; gg[5] += -0.2672612419124244f * gt1 * v[9];
+      gv[9] += -0.5345224838248489f * gt2 * g[6]; gg[6] += -0.5345224838248489f * gt2 * v[9];
+      gv[9] += -0.2672612419124244f * gt3 * g[7]; gg[7] += -0.2672612419124244f * gt3 * v[9];
+      gv[9] += 0.5345224838248488f * gt4 * g[8]; gg[8] += 0.5345224838248488f * gt4 * v[9];
+      gv[10] += -0.4629100498862757f * gt1 * g[4]; gg[4] += -0.4629100498862757f * gt1 * v[10];
+      gv[10] += -0.4629100498862757f * gt0 * g[5]; gg[5] += -0.4629100498862757f * gt0 * v[10];
+      gv[10] += -0.2672612419124244f * gt3 * g[6]; gg[6] += -0.2672612419124244f * gt3 * v[10];
+      gv[10] += -0.2672612419124244f * gt2 * g[7]; gg[7] += -0.2672612419124244f * gt2 * v[10];
+      gv[10] += -0.4629100498862757f * gt4 * g[7]; gg[7] += -0.4629100498862757f * gt4 * v[10];
+      gv[10] += -0.4629100498862757f * gt3 * g[8]; gg[8] += -0.4629100498862757f * gt3 * v[10];
+      gv[11] += 0.4629100498862757f * gt1 * g[5]; gg[5] += 0.4629100498862757f * gt1 * v[11];
+      gv[11] += 0.5345224838248488f * gt4 * g[6]; gg[6] += 0.5345224838248488f * gt4 * v[11];
+      gv[11] += -0.4629100498862757f * gt3 * g[7]; gg[7] += -0.4629100498862757f * gt3 * v[11];
+      gv[11] += 0.5345224838248488f * gt2 * g[8]; gg[8] += 0.5345224838248488f * gt2 * v[11];
+    }
+    { // path 23
+      const float w = th[23] * 0.4082482904638631f;
+      const float gt0 = w * gvo[4];
+      const float gt1 = w * gvo[5];
+      const float gt2 = w * gvo[6];
+      const float gt3 = w * gvo[7];
+      const float gt4 = w * gvo[8];
+      gv[12] += 0.408248290463863f * gt1 * g[1]; gg[1] += 0.408248290463863f * gt1 * v[12];
+      gv[12] += 0.816496580927726f * gt4 * g[2]; gg[2] += 0.816496580927726f * gt4 * v[12];
+      gv[12] += -0.408248290463863f * gt3 * g[3]; gg[3] += -0.408248290463863f * gt3 * v[12];
+      gv[13] += -0.408248290463863f * gt0 * g[1]; gg[1] += -0.408248290463863f * gt0 * v[13];
+      gv[13] += 0.408248290463863f * gt3 * g[2]; gg[2] += 0.408248290463863f * gt3 * v[13];
+      gv[13] += -0.7071067811865477f * gt2 * g[3]; gg[3] += -0.7071067811865477f * gt2 * v[13];
+      gv[13] += -0.408248290463863f * gt4 * g[3]; gg[3] += -0.408248290463863f * gt4 * v[13];
+      gv[14] += -0.7071067811865477f * gt3 * g[1]; gg[1] += -0.7071067811865477f * gt3 * v[14];
+      gv[14] += 0.7071067811865477f * gt1 * g[3]; gg[3] += 0.7071067811865477f * gt1 * v[14];
+      gv[15] += 0.7071067811865477f * gt2 * g[1]; gg[1] += 0.7071067811865477f * gt2 * v[15];
+      gv[15] += -0.408248290463863f * gt4 * g[1]; gg[1] += -0.408248290463863f * gt4 * v[15];
+      gv[15] += -0.408248290463863f * gt1 * g[2]; gg[2] += -0.408248290463863f * gt1 * v[15];
+      gv[15] += 0.408248290463863f * gt0 * g[3]; gg[3] += 0.408248290463863f * gt0 * v[15];
+      gv[16] += 0.408248290463863f * gt3 * g[1]; gg[1] += 0.408248290463863f * gt3 * v[16];
+      gv[16] += -0.816496580927726f * gt0 * g[2]; gg[2] += -0.816496580927726f * gt0 * v[16];
+      gv[16] += 0.408248290463863f * gt1 * g[3]; gg[3] += 0.408248290463863f * gt1 * v[16];
+    }
+    { // path 25
+      const float w = th[25] * 0.4082482904638631f;
+      const float gt0 = w * gvo[1];
+      const float gt1 = w * gvo[2];
+      const float gt2 = w * gvo[3];
+      gv[12] += 0.3162277660168379f * gt0 * g[5]; gg[5] += 0.3162277660168379f * gt0 * v[12];
+      gv[12] += -0.3162277660168379f * gt2 * g[7]; gg[7] += -0.3162277660168379f * gt2 * v[12];
+      gv[12] += 0.6324555320336758f * gt1 * g[8]; gg[8] += 0.6324555320336758f * gt1 * v[12];
+      gv[13] += -0.3162277660168379f * gt0 * g[4]; gg[4] += -0.3162277660168379f * gt0 * v[13];
+      gv[13] += -0.5477225575051661f * gt2 * g[6]; gg[6] += -0.5477225575051661f * gt2 * v[13];
+      gv[13] += 0.3162277660168379f * gt1 * g[7]; gg[7] += 0.3162277660168379f * gt1 * v[13];
+      gv[13] += -0.3162277660168379f * gt2 * g[8]; gg[8] += -0.3162277660168379f * gt2 * v[13];
+      gv[14] += 0.5477225575051661f * gt2 * g[5]; gg[5] += 0.5477225575051661f * gt2 * v[14];
+      gv[14] += -0.5477225575051661f * gt0 * g[7]; gg[7] += -0.5477225575051661f * gt0 * v[14];
+      gv[15] += 0.3162277660168379f * gt2 * g[4]; gg[4] += 0.3162277660168379f * gt2 * v[15];
+      gv[15] += -0.3162277660168379f * gt1 * g[5]; gg[5] += -0.3162277660168379f * gt1 * v[15];
+      gv[15] += 0.5477225575051661f * gt0 * g[6]; gg[6] += 0.5477225575051661f * gt0 * v[15];
+      gv[15] += -0.3162277660168379f * gt0 * g[8]; gg[8] += -0.3162277660168379f * gt0 * v[15];
+      gv[16] += -0.6324555320336758f * gt1 * g[4]; gg[4] += -0.6324555320336758f * gt1 * v[16];
+      gv[16] += 0.3162277660168379f * gt2 * g[5]; gg[5] += 0.3162277660168379f * gt2 * v[16];
+      gv[16] += 0.3162277660168379f * gt0 * g[7]; gg[7] += 0.3162277660168379f * gt0 * v[16];
+    }
+  }
+  static constexpr int NNZ = 137;
+};
+
+template <> struct TP<2, 2, 1> {
+  // in irreps [(0, 1), (0, -1), (1, -1), (1, 1), (2, 1), (2, -1)]; out irreps [(0, 1), (1, -1), (2, 1)]
+  static constexpr int NP = 30, DIN = 18, DOUT = 9, NS = 3, NPW = 30;
+  static __device__ __forceinline__ void fwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, float* s, float* vo) {
+    #pragma unroll
+    for (int k = 0; k < 9; ++k) vo[k] = 0.f;
+    { // path 0: (0, 1) x (0,1) -> (0, 1)
+      const float t0 = 1.0f * v[0] * g[0];
+      s[0] = t0;
+      const float w = th[0] * 0.5773502691896258f;
+      vo[0] += w * t0;
+    }
+    { // path 1: (0, 1) x (1,-1) -> (1, -1)
+      const float t0 = 0.9999999999999999f * v[0] * g[1];
+      const float t1 = 1.0000000000000002f * v[0] * g[2];
+      const float t2 = 0.9999999999999999f * v[0] * g[3];
+      const float w = th[1] * 0.4082482904638631f;
+      vo[1] += w * t0;
+      vo[2] += w * t1;
+      vo[3] += w * t2;
+    }
+    { // path 2: (0, 1) x (2,1) -> (2, 1)
+      const float t0 = 1.0f * v[0] * g[4];
+      const float t1 = 1.0f * v[0] * g[5];
+      const float t2 = 1.0000000000000002f * v[0] * g[6];
+      const float t3 = 1.0f * v[0] * g[7];
+      const float t4 = 1.0f * v[0] * g[8];
+      const float w = th[2] * 0.4082482904638631f;
+      vo[4] += w * t0;
+      vo[5] += w * t1;
+      vo[6] += w * t2;
+      vo[7] += w * t3;
+      vo[8] += w * t4;
+    }
+    { // path 6: (1, -1) x (0,1) -> (1, -1)
+      const float t0 = 0.9999999999999999f * v[2] * g[0];
+      const float t1 = 1.0000000000000002f * v[3] * g[0];
+      const float t2 = 0.9999999999999999f * v[4] * g[0];
+      const float w = th[6] * 0.4082482904638631f;
+      vo[1] += w * t0;
+      vo[2] += w * t1;
+      vo[3] += w * t2;
+    }
+    { // path 7: (1, -1) x (1,-1) -> (0, 1)
+      const float t0 = 0.5773502691896257f * v[2] * g[1] + 0.5773502691896258f * v[3] * g[2] + 0.5773502691896257f * v[4] * g[3];
+      s[1] = t0;
+      const float w = th[7] * 0.5773502691896258f;
+      vo[0] += w * t0;
+    }
+    { // path 9: (1, -1) x (1,-1) -> (2, 1)
+      const float t0 = -0.7071067811865475f * v[2] * g[3] + -0.7071067811865475f * v[4] * g[1];
+      const float t1 = -0.7071067811865476f * v[2] * g[2] + -0.7071067811865476f * v[3] * g[1];
+      const float t2 = 0.4082482904638631f * v[2] * g[1] + -0.8164965809277261f * v[3] * g[2] + 0.4082482904638631f * v[4] * g[3];
+      const float t3 = -0.7071067811865476f * v[3] * g[3] + -0.7071067811865476f * v[4] * g[2];
+      const float t4 = 0.7071067811865475f * v[2] * g[1] + -0.7071067811865475f * v[4] * g[3];
+      const float w = th[9] * 0.4082482904638631f;
+      vo[4] += w * t0;
+      vo[5] += w * t1;
+      vo[6] += w * t2;
+      vo[7] += w * t3;
+      vo[8] += w * t4;
+    }
+    { // path 10: (1, -1) x (2,1) -> (1, -1)
+      const float t0 = -0.3162277660168379f * v[2] * g[6] + -0.547722557505166f * v[2] * g[8] + 0.547722557505166f * v[3] * g[5] + 0.547722557505166f * v[4] * g[4];
+      const float t1 = 0.547722557505166f * v[2] * g[5] + 0.632455532033676f * v[3] * g[6] + 0.547722557505166f * v[4] * g[7];
+      const float t2 = 0.547722557505166f * v[2] * g[4] + 0.547722557505166f * v[3] * g[7] + -0.3162277660168379f * v[4] * g[6] + 0.547722557505166f * v[4] * g[8];
+      const float w = th[10] * 0.4082482904638631f;
+      vo[1] += w * t0;
+      vo[2] += w * t1;
+      vo[3] += w * t2;
+    }
+    { // path 14: (1, 1) x (1,-1) -> (1, -1)
+      const float t0 = 0.7071067811865476f * v[6] * g[3] + -0.7071067811865476f * v[7] * g[2];
+      const float t1 = -0.7071067811865476f * v[5] * g[3] + 0.7071067811865476f * v[7] * g[1];
+      const float t2 = 0.7071067811865476f * v[5] * g[2] + -0.7071067811865476f * v[6] * g[1];
+      const float w = th[14] * 0.4082482904638631f;
+      vo[1] += w * t0;
+      vo[2] += w * t1;
+      vo[3] += w * t2;
+    }
+    { // path 17: (1, 1) x (2,1) -> (2, 1)
+      const float t0 = -0.408248290463863f * v[5] * g[5] + -0.816496580927726f * v[6] * g[8] + 0.408248290463863f * v[7] * g[7];
+      const float t1 = 0.408248290463863f * v[5] * g[4] + -0.408248290463863f * v[6] * g[7] + 0.7071067811865477f * v[7] * g[6] + 0.408248290463863f * v[7] * g[8];
+      const float t2 = 0.7071067811865477f * v[5] * g[7] + -0.7071067811865477f * v[7] * g[5];
+      const float t3 = -0.7071067811865477f * v[5] * g[6] + 0.408248290463863f * v[5] * g[8] + 0.408248290463863f * v[6] * g[5] + -0.408248290463863f * v[7] * g[4];
+      const float t4 = -0.408248290463863f * v[5] * g[7] + 0.816496580927726f * v[6] * g[4] + -0.408248290463863f * v[7] * g[5];
+      const float w = th[17] * 0.4082482904638631f;
+      vo[4] += w * t0;
+      vo[5] += w * t1;
+      vo[6] += w * t2;
+      vo[7] += w * t3;
+      vo[8] += w * t4;
+    }
+    { // path 18: (2, 1) x (0,1) -> (2, 1)
+      const float t0 = 1.0f * v[8] * g[0];
+      const float t1 = 1.0f * v[9] * g[0];
+      const float t2 = 1.0000000000000002f * v[10] * g[0];
+      const float t3 = 1.0f * v[11] * g[0];
+      const float t4 = 1.0f * v[12] * g[0];
+      const float w = th[18] * 0.4082482904638631f;
+      vo[4] += w * t0;
+      vo[5] += w * t1;
+      vo[6] += w * t2;
+      vo[7] += w * t3;
+      vo[8] += w * t4;
+    }
+    { // path 19: (2, 1) x (1,-1) -> (1, -1)
+      const float t0 = 0.547722557505166f * v[8] * g[3] + 0.547722557505166f * v[9] * g[2] + -0.3162277660168379f * v[10] * g[1] + -0.547722557505166f * v[12] * g[1];
+      const float t1 = 0.547722557505166f * v[9] * g[1] + 0.632455532033676f * v[10] * g[2] + 0.547722557505166f * v[11] * g[3];
+      const float t2 = 0.547722557505166f * v[8] * g[1] + -0.3162277660168379f * v[10] * g[3] + 0.547722557505166f * v[11] * g[2] + 0.547722557505166f * v[12] * g[3];
+      const float w = th[19] * 0.4082482904638631f;
+      vo[1] += w * t0;
+      vo[2] += w * t1;
+      vo[3] += w * t2;
+    }
+    { // path 21: (2, 1) x (2,1) -> (0, 1)
+      const float t0 = 0.4472135954999579f * v[8] * g[4] + 0.4472135954999579f * v[9] * g[5] + 0.44721359549995804f * v[10] * g[6] + 0.4472135954999579f * v[11] * g[7] + 0.4472135954999579f * v[12] * g[8];
+      s[2] = t0;
+      const float w = th[21] * 0.5773502691896258f;
+      vo[0] += w * t0;
+    }
+    { // path 23: (2, 1) x (2,1) -> (2, 1)
+      const float t0 = 0.5345224838248488f * v[8] * g[6] + -0.4629100498862757f * v[9] * g[7] + 0.5345224838248488f * v[10] * g[4] + -0.4629100498862757f * v[11] * g[5];
+      const float t1 = -0.4629100498862757f * v[8] * g[7] + -0.2672612419124244f * v[9] * g[6] + 0.4629100498862757f * v[9] * g[8] + -0.2672612419124244f * v[10] * g[5] + -0.4629100498862757f * v[11] * g[4] + 0.4629100498862757f * v[12] * g[5];
+      const float t2 = 0.5345224838248488f * v[8] * g[4] + -0.2672612419124244f * v[9] * g[5] + -0.5345224838248489f * v[10] * g[6] + -0.2672612419124244f * v[11] * g[7] + 0.5345224838248488f * v[12] * g[8];
+      const float t3 = -0.4629100498862757f * v[8] * g[5] + -0.4629100498862757f * v[9] * g[4] + -0.2672612419124244f * v[10] * g[7] + -0.2672612419124244f * v[11] * g[6] + -0.4629100498862757f * v[11] * g[8] + -0.4629100498862757f * v[12] * g[7];
+      const float t4 = 0.4629100498862757f * v[9] * g[5] + 0.5345224838248488f * v[10] * g[8] + -0.4629100498862757f * v[11] * g[7] + 0.5345224838248488f * v[12] * g[6];
+      const float w = th[23] * 0.4082482904638631f;
+      vo[4] += w * t0;
+      vo[5] += w * t1;
+      vo[6] += w * t2;
+      vo[7] += w * t3;
+      vo[8] += w * t4;
+    }
+    { // path 26: (2, -1) x (1,-1) -> (2, 1)
+      const float t0 = -0.408248290463863f * v[14] * g[1] + 0.408248290463863f * v[16] * g[3] + -0.816496580927726f * v[17] * g[2];
+      const float t1 = 0.408248290463863f * v[13] * g[1] + 0.7071067811865477f * v[15] * g[3] + -0.408248290463863f * v[16] * g[2] + 0.408248290463863f * v[17] * g[3];
+      const float t2 = -0.7071067811865477f * v[14] * g[3] + 0.7071067811865477f * v[16] * g[1];
+      const float t3 = -0.408248290463863f * v[13] * g[3] + 0.408248290463863f * v[14] * g[2] + -0.7071067811865477f * v[15] * g[1] + 0.408248290463863f * v[17] * g[1];
+      const float t4 = 0.816496580927726f * v[13] * g[2] + -0.408248290463863f * v[14] * g[3] + -0.408248290463863f * v[16] * g[1];
+      const float w = th[26] * 0.4082482904638631f;
+      vo[4] += w * t0;
+      vo[5] += w * t1;
+      vo[6] += w * t2;
+      vo[7] += w * t3;
+      vo[8] += w * t4;
+    }
+    { // path 28: (2, -1) x (2,1) -> (1, -1)
+      const float t0 = 0.3162277660168379f * v[13] * g[5] + -0.3162277660168379f * v[14] * g[4] + -0.5477225575051661f * v[15] * g[7] + 0.5477225575051661f * v[16] * g[6] + -0.3162277660168379f * v[16] * g[8] + 0.3162277660168379f * v[17] * g[7];
+      const float t1 = 0.6324555320336758f * v[13] * g[8] + 0.3162277660168379f * v[14] * g[7] + -0.3162277660168379f * v[16] * g[5] + -0.6324555320336758f * v[17] * g[4];
+      const float t2 = -0.3162277660168379f * v[13] * g[7] + -0.5477225575051661f * v[14] * g[6] + -0.3162277660168379f * v[14] * g[8] + 0.5477225575051661f * v[15] * g[5] + 0.3162277660168379f * v[16] * g[4] + 0.3162277660168379f * v[17] * g[5];
+      const float w = th[28] * 0.4082482904638631f;
+      vo[1] += w * t0;
+      vo[2] += w * t1;
+      vo[3] += w * t2;
+    }
+  }
+  static __device__ __forceinline__ void bwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, const float* __restrict__ gs, const float* __restrict__ gvo, float* gv, float* gg) {
+    { // path 0
+      const float w = th[0] * 0.5773502691896258f;
+      const float gt0 = gs[0] + w * gvo[0];
+      gv[0] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[0];
+    }
+    { // path 1
+      const float w = th[1] * 0.4082482904638631f;
+      const float gt0 = w * gvo[1];
+      const float gt1 = w * gvo[2];
+      const float gt2 = w * gvo[3];
+      gv[0] += 0.9999999999999999f * gt0 * g[1]; gg[1] += 0.9999999999999999f * gt0 * v[0];
+      gv[0] += 1.0000000000000002f * gt1 * g[2]; gg[2] += 1.0000000000000002f * gt1 * v[0];
+      gv[0] += 0.9999999999999999f * gt2 * g[3]; gg[3] += 0.9999999999999999f * gt2 * v[0];
+    }
+    { // path 2
+      const float w = th[2] * 0.4082482904638631f;
+      const float gt0 = w * gvo[4];
+      const float gt1 = w * gvo[5];
+      const float gt2 = w * gvo[6];
+      const float gt3 = w * gvo[7];
+      const float gt4 = w * gvo[8];
+      gv[0] += 1.0f * gt0 * g[4]; gg[4] += 1.0f * gt0 * v[0];
+      gv[0] += 1.0f * gt1 * g[5]; gg[5] += 1.0f * gt1 * v[0];
+      gv[0] += 1.0000000000000002f * gt2 * g[6]; gg[6] += 1.0000000000000002f * gt2 * v[0];
+      gv[0] += 1.0f * gt3 * g[7]; gg[7] += 1.0f * gt3 * v[0];
+      gv[0] += 1.0f * gt4 * g[8]; gg[8] += 1.0f * gt4 * v[0];
+    }
+    { // path 6
+      const float w = th[6] * 0.4082482904638631f;
+      const float gt0 = w * gvo[1];
+      const float gt1 = w * gvo[2];
+      const float gt2 = w * gvo[3];
       gv[2] += 0.9999999999999999f * gt0 * g[0]; gg[0] += 0.9999999999999999f * gt0 * v[2];
       gv[3] += 1.0000000000000002f * gt1 * g[0]; gg[0] += 1.0000000000000002f * gt1 * v[3];
       gv[4] += 0.9999999999999999f * gt2 * g[0]; gg[0] += 0.9999999999999999f * gt2 * v[4];
@@ -2087,25 +2570,13 @@ template <> struct TP<2, 2, 0> {
       gv[3] += 0.5773502691896258f * gt0 * g[2]; gg[2] += 0.5773502691896258f * gt0 * v[3];
       gv[4] += 0.5773502691896257f * gt0 * g[3]; gg[3] += 0.5773502691896257f * gt0 * v[4];
     }
-    { // path 8
-      const float w = th[8] * 0.4082482904638631f;
-      const float gt0 = w * gvo[5];
-      const float gt1 = w * gvo[6];
-      const float gt2 = w * gvo[7];
-      gv[2] += 0.7071067811865476f * gt2 * g[2]; gg[2] += 0.7071067811865476f * gt2 * v[2];
-      gv[2] += -0.7071067811865476f * gt1 * g[3]; gg[3] += -0.7071067811865476f * gt1 * v[2];
-      gv[3] += -0.7071067811865476f * gt2 * g[1]; gg[1] += -0.7071067811865476f * gt2 * v[3];
-      gv[3] += 0.7071067811865476f * gt0 * g[3]; gg[3] += 0.7071067811865476f * gt0 * v[3];
-      gv[4] += 0.7071067811865476f * gt1 * g[1]; gg[1] += 0.7071067811865476f * gt1 * v[4];
-      gv[4] += -0.7071067811865476f * gt0 * g[2]; gg[2] += -0.7071067811865476f * gt0 * v[4];
-    }
     { // path 9
       const float w = th[9] * 0.4082482904638631f;
-      const float gt0 = w * gvo[8];
-      const float gt1 = w * gvo[9];
-      const float gt2 = w * gvo[10];
-      const float gt3 = w * gvo[11];
-      const float gt4 = w * gvo[12];
+      const float gt0 = w * gvo[4];
+      const float gt1 = w * gvo[5];
+      const float gt2 = w * gvo[6];
+      const float gt3 = w * gvo[7];
+      const float gt4 = w * gvo[8];
       gv[2] += 0.4082482904638631f * gt2 * g[1]; gg[1] += 0.4082482904638631f * gt2 * v[2];
       gv[2] += 0.7071067811865475f * gt4 * g[1]; gg[1] += 0.7071067811865475f * gt4 * v[2];
       gv[2] += -0.7071067811865476f * gt1 * g[2]; gg[2] += -0.7071067811865476f * gt1 * v[2];
@@ -2120,9 +2591,9 @@ template <> struct TP<2, 2, 0> {
     }
     { // path 10
       const float w = th[10] * 0.4082482904638631f;
-      const float gt0 = w * gvo[2];
-      const float gt1 = w * gvo[3];
-      const float gt2 = w * gvo[4];
+      const float gt0 = w * gvo[1];
+      const float gt1 = w * gvo[2];
+      const float gt2 = w * gvo[3];
       gv[2] += 0.547722557505166f * gt2 * g[4]; gg[4] += 0.547722557505166f * gt2 * v[2];
       gv[2] += 0.547722557505166f * gt1 * g[5]; gg[5] += 0.547722557505166f * gt1 * v[2];
       gv[2] += -0.3162277660168379f * gt0 * g[6]; gg[6] += -0.3162277660168379f * gt0 * v[2];
@@ -2135,51 +2606,11 @@ template <> struct TP<2, 2, 0> {
       gv[4] += 0.547722557505166f * gt1 * g[7]; gg[7] += 0.547722557505166f * gt1 * v[4];
       gv[4] += 0.547722557505166f * gt2 * g[8]; gg[8] += 0.547722557505166f * gt2 * v[4];
     }
-    { // path 11
-      const float w = th[11] * 0.4082482904638631f;
-      const float gt0 = w * gvo[13];
-      const float gt1 = w * gvo[14];
-      const float gt2 = w * gvo[15];
-      const float gt3 = w * gvo[16];
-      const float gt4 = w * gvo[17];
-      gv[2] += 0.408248290463863f * gt1 * g[4]; gg[4] += 0.408248290463863f * gt1 * v[2];
-      gv[2] += -0.408248290463863f * gt0 * g[5]; gg[5] += -0.408248290463863f * gt0 * v[2];
-      gv[2] += -0.7071067811865477f * gt3 * g[6]; gg[6] += -0.7071067811865477f * gt3 * v[2];
-      gv[2] += 0.7071067811865477f * gt2 * g[7]; gg[7] += 0.7071067811865477f * gt2 * v[2];
-      gv[2] += -0.408248290463863f * gt4 * g[7]; gg[7] += -0.408248290463863f * gt4 * v[2];
-      gv[2] += 0.408248290463863f * gt3 * g[8]; gg[8] += 0.408248290463863f * gt3 * v[2];
-      gv[3] += 0.816496580927726f * gt4 * g[4]; gg[4] += 0.816496580927726f * gt4 * v[3];
-      gv[3] += 0.408248290463863f * gt3 * g[5]; gg[5] += 0.408248290463863f * gt3 * v[3];
-      gv[3] += -0.408248290463863f * gt1 * g[7]; gg[7] += -0.408248290463863f * gt1 * v[3];
-      gv[3] += -0.816496580927726f * gt0 * g[8]; gg[8] += -0.816496580927726f * gt0 * v[3];
-      gv[4] += -0.408248290463863f * gt3 * g[4]; gg[4] += -0.408248290463863f * gt3 * v[4];
-      gv[4] += -0.7071067811865477f * gt2 * g[5]; gg[5] += -0.7071067811865477f * gt2 * v[4];
-      gv[4] += -0.408248290463863f * gt4 * g[5]; gg[5] += -0.408248290463863f * gt4 * v[4];
-      gv[4] += 0.7071067811865477f * gt1 * g[6]; gg[6] += 0.7071067811865477f * gt1 * v[4];
-      gv[4] += 0.408248290463863f * gt0 * g[7]; gg[7] += 0.408248290463863f * gt0 * v[4];
-      gv[4] += 0.408248290463863f * gt1 * g[8]; gg[8] += 0.408248290463863f * gt1 * v[4];
-    }
-    { // path 12
-      const float w = th[12] * 0.4082482904638631f;
-      const float gt0 = w * gvo[5];
-      const float gt1 = w * gvo[6];
-      const float gt2 = w * gvo[7];
-      gv[5] += 0.9999999999999999f * gt0 * g[0]; gg[0] += 0.9999999999999999f * gt0 * v[5];
-      gv[6] += 1.0000000000000002f * gt1 * g[0]; gg[0] += 1.0000000000000002f * gt1 * v[6];
-      gv[7] += 0.9999999999999999f * gt2 * g[0]; gg[0] += 0.9999999999999999f * gt2 * v[7];
-    }
-    { // path 13
-      const float w = th[13] * 0.5773502691896258f;
-      const float gt0 = w * gvo[1];
-      gv[5] += 0.5773502691896257f * gt0 * g[1]; gg[1] += 0.5773502691896257f * gt0 * v[5];
-      gv[6] += 0.5773502691896258f * gt0 * g[2]; gg[2] += 0.5773502691896258f * gt0 * v[6];
-      gv[7] += 0.5773502691896257f * gt0 * g[3]; gg[3] += 0.5773502691896257f * gt0 * v[7];
-    }
     { // path 14
       const float w = th[14] * 0.4082482904638631f;
-      const float gt0 = w * gvo[2];
-      const float gt1 = w * gvo[3];
-      const float gt2 = w * gvo[4];
+      const float gt0 = w * gvo[1];
+      const float gt1 = w * gvo[2];
+      const float gt2 = w * gvo[3];
       gv[5] += 0.7071067811865476f * gt2 * g[2]; gg[2] += 0.7071067811865476f * gt2 * v[5];
       gv[5] += -0.7071067811865476f * gt1 * g[3]; gg[3] += -0.7071067811865476f * gt1 * v[5];
       gv[6] += -0.7071067811865476f * gt2 * g[1]; gg[1] += -0.7071067811865476f * gt2 * v[6];
@@ -2187,49 +2618,13 @@ template <> struct TP<2, 2, 0> {
       gv[7] += 0.7071067811865476f * gt1 * g[1]; gg[1] += 0.7071067811865476f * gt1 * v[7];
       gv[7] += -0.7071067811865476f * gt0 * g[2]; gg[2] += -0.7071067811865476f * gt0 * v[7];
     }
-    { // path 15
-      const float w = th[15] * 0.4082482904638631f;
-      const float gt0 = w * gvo[13];
-      const float gt1 = w * gvo[14];
-      const float gt2 = w * gvo[15];
-      const float gt3 = w * gvo[16];
-      const float gt4 = w * gvo[17];
-      gv[5] += 0.4082482904638631f * gt2 * g[1]; gg[1] += 0.4082482904638631f * gt2 * v[5];
-      gv[5] += 0.7071067811865475f * gt4 * g[1]; gg[1] += 0.7071067811865475f * gt4 * v[5];
-      gv[5] += -0.7071067811865476f * gt1 * g[2]; gg[2] += -0.7071067811865476f * gt1 * v[5];
-      gv[5] += -0.7071067811865475f * gt0 * g[3]; gg[3] += -0.7071067811865475f * gt0 * v[5];
-      gv[6] += -0.7071067811865476f * gt1 * g[1]; gg[1] += -0.7071067811865476f * gt1 * v[6];
-      gv[6] += -0.8164965809277261f * gt2 * g[2]; gg[2] += -0.8164965809277261f * gt2 * v[6];
-      gv[6] += -0.7071067811865476f * gt3 * g[3]; gg[3] += -0.7071067811865476f * gt3 * v[6];
-      gv[7] += -0.7071067811865475f * gt0 * g[1]; gg[1] += -0.7071067811865475f * gt0 * v[7];
-      gv[7] += -0.7071067811865476f * gt3 * g[2]; gg[2] += -0.7071067811865476f * gt3 * v[7];
-      gv[7] += 0.4082482904638631f * gt2 * g[3]; gg[3] += 0.4082482904638631f * gt2 * v[7];
-      gv[7] += -0.7071067811865475f * gt4 * g[3]; gg[3] += -0.7071067811865475f * gt4 * v[7];
-    }
-    { // path 16
-      const float w = th[16] * 0.4082482904638631f;
-      const float gt0 = w * gvo[5];
-      const float gt1 = w * gvo[6];
-      const float gt2 = w * gvo[7];
-      gv[5] += 0.547722557505166f * gt2 * g[4]; gg[4] += 0.547722557505166f * gt2 * v[5];
-      gv[5] += 0.547722557505166f * gt1 * g[5]; gg[5] += 0.547722557505166f * gt1 * v[5];
-      gv[5] += -0.3162277660168379f * gt0 * g[6]; gg[6] += -0.3162277660168379f * gt0 * v[5];
-      gv[5] += -0.547722557505166f * gt0 * g[8]; gg[8] += -0.547722557505166f * gt0 * v[5];
-      gv[6] += 0.547722557505166f * gt0 * g[5]; gg[5] += 0.547722557505166f * gt0 * v[6];
-      gv[6] += 0.632455532033676f * gt1 * g[6]; gg[6] += 0.632455532033676f * gt1 * v[6];
-      gv[6] += 0.547722557505166f * gt2 * g[7]; gg[7] += 0.547722557505166f * gt2 * v[6];
-      gv[7] += 0.547722557505166f * gt0 * g[4]; gg[4] += 0.547722557505166f * gt0 * v[7];
-      gv[7] += -0.3162277660168379f * gt2 * g[6]; gg[6] += -0.3162277660168379f * gt2 * v[7];
-      gv[7] += 0.547722557505166f * gt1 * g[7]; gg[7] += 0.547722557505166f * gt1 * v[7];
-      gv[7] += 0.547722557505166f * gt2 * g[8]; gg[8] += 0.547722557505166f * gt2 * v[7];
-    }
     { // path 17
       const float w = th[17] * 0.4082482904638631f;
-      const float gt0 = w * gvo[8];
-      const float gt1 = w * gvo[9];
-      const float gt2 = w * gvo[10];
-      const float gt3 = w * gvo[11];
-      const float gt4 = w * gvo[12];
+      const float gt0 = w * gvo[4];
+      const float gt1 = w * gvo[5];
+      const float gt2 = w * gvo[6];
+      const float gt3 = w * gvo[7];
+      const float gt4 = w * gvo[8];
       gv[5] += 0.408248290463863f * gt1 * g[4]; gg[4] += 0.408248290463863f * gt1 * v[5];
       gv[5] += -0.408248290463863f * gt0 * g[5]; gg[5] += -0.408248290463863f * gt0 * v[5];
       gv[5] += -0.7071067811865477f * gt3 * g[6]; gg[6] += -0.7071067811865477f * gt3 * v[5];
@@ -2249,11 +2644,11 @@ template <> struct TP<2, 2, 0> {
     }
     { // path 18
       const float w = th[18] * 0.4082482904638631f;
-      const float gt0 = w * gvo[8];
-      const float gt1 = w * gvo[9];
-      const float gt2 = w * gvo[10];
-      const float gt3 = w * gvo[11];
-      const float gt4 = w * gvo[12];
+      const float gt0 = w * gvo[4];
+      const float gt1 = w * gvo[5];
+      const float gt2 = w * gvo[6];
+      const float gt3 = w * gvo[7];
+      const float gt4 = w * gvo[8];
       gv[8] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[8];
       gv[9] += 1.0f * gt1 * g[0]; gg[0] += 1.0f * gt1 * v[9];
       gv[10] += 1.0000000000000002f * gt2 * g[0]; gg[0] += 1.0000000000000002f * gt2 * v[10];
@@ -2262,9 +2657,9 @@ template <> struct TP<2, 2, 0> {
     }
     { // path 19
       const float w = th[19] * 0.4082482904638631f;
-      const float gt0 = w * gvo[2];
-      const float gt1 = w * gvo[3];
-      const float gt2 = w * gvo[4];
+      const float gt0 = w * gvo[1];
+      const float gt1 = w * gvo[2];
+      const float gt2 = w * gvo[3];
       gv[8] += 0.547722557505166f * gt2 * g[1]; gg[1] += 0.547722557505166f * gt2 * v[8];
       gv[8] += 0.547722557505166f * gt0 * g[3]; gg[3] += 0.547722557505166f * gt0 * v[8];
       gv[9] += 0.547722557505166f * gt1 * g[1]; gg[1] += 0.547722557505166f * gt1 * v[9];
@@ -2277,30 +2672,6 @@ template <> struct TP<2, 2, 0> {
       gv[12] += -0.547722557505166f * gt0 * g[1]; gg[1] += -0.547722557505166f * gt0 * v[12];
       gv[12] += 0.547722557505166f * gt2 * g[3]; gg[3] += 0.547722557505166f * gt2 * v[12];
     }
-    { // path 20
-      const float w = th[20] * 0.4082482904638631f;
-      const float gt0 = w * gvo[13];
-      const float gt1 = w * gvo[14];
-      const float gt2 = w * gvo[15];
-      const float gt3 = w * gvo[16];
-      const float gt4 = w * gvo[17];
-      gv[8] += 0.408248290463863f * gt1 * g[1]; gg[1] += 0.408248290463863f * gt1 * v[8];
-      gv[8] += 0.816496580927726f * gt4 * g[2]; gg[2] += 0.816496580927726f * gt4 * v[8];
-      gv[8] += -0.408248290463863f * gt3 * g[3]; gg[3] += -0.408248290463863f * gt3 * v[8];
-      gv[9] += -0.408248290463863f * gt0 * g[1]; gg[1] += -0.408248290463863f * gt0 * v[9];
-      gv[9] += 0.408248290463863f * gt3 * g[2]; gg[2] += 0.408248290463863f * gt3 * v[9];
-      gv[9] += -0.7071067811865477f * gt2 * g[3]; gg[3] += -0.7071067811865477f * gt2 * v[9];
-      gv[9] += -0.408248290463863f * gt4 * g[3]; gg[3] += -0.408248290463863f * gt4 * v[9];
-      gv[10] += -0.7071067811865477f * gt3 * g[1]; gg[1] += -0.7071067811865477f * gt3 * v[10];
-      gv[10] += 0.7071067811865477f * gt1 * g[3]; gg[3] += 0.7071067811865477f * gt1 * v[10];
-      gv[11] += 0.7071067811865477f * gt2 * g[1]; gg[1] += 0.7071067811865477f * gt2 * v[11];
-      gv[11] += -0.408248290463863f * gt4 * g[1]; gg[1] += -0.408248290463863f * gt4 * v[11];
-      gv[11] += -0.408248290463863f * gt1 * g[2]; gg[2] += -0.408248290463863f * gt1 * v[11];
-      gv[11] += 0.408248290463863f * gt0 * g[3]; gg[3] += 0.408248290463863f * gt0 * v[11];
-      gv[12] += 0.408248290463863f * gt3 * g[1]; gg[1] += 0.408248290463863f * gt3 * v[12];
-      gv[12] += -0.816496580927726f * gt0 * g[2]; gg[2] += -0.816496580927726f * gt0 * v[12];
-      gv[12] += 0.408248290463863f * gt1 * g[3]; gg[3] += 0.408248290463863f * gt1 * v[12];
-    }
     { // path 21
       const float w = th[21] * 0.5773502691896258f;
       const float gt0 = gs[2] + w * gvo[0];
@@ -2310,35 +2681,13 @@ template <> struct TP<2, 2, 0> {
       gv[11] += 0.4472135954999579f * gt0 * g[7]; gg[7] += 0.4472135954999579f * gt0 * v[11];
       gv[12] += 0.4472135954999579f * gt0 * g[8]; gg[8] += 0.4472135954999579f * gt0 * v[12];
     }
-    { // path 22
-      const float w = th[22] * 0.4082482904638631f;
-      const float gt0 = w * gvo[5];
-      const float gt1 = w * gvo[6];
-      const float gt2 = w * gvo[7];
-      gv[8] += 0.3162277660168379f * gt0 * g[5]; gg[5] += 0.3162277660168379f * gt0 * v[8];
-      gv[8] += -0.3162277660168379f * gt2 * g[7]; gg[7] += -0.3162277660168379f * gt2 * v[8];
-      gv[8] += 0.6324555320336758f * gt1 * g[8]; gg[8] += 0.6324555320336758f * gt1 * v[8];
-      gv[9] += -0.3162277660168379f * gt0 * g[4]; gg[4] += -0.3162277660168379f * gt0 * v[9];
-      gv[9] += -0.5477225575051661f * gt2 * g[6]; gg[6] += -0.5477225575051661f * gt2 * v[9];
-      gv[9] += 0.3162277660168379f * gt1 * g[7]; gg[7] += 0.3162277660168379f * gt1 * v[9];
-      gv[9] += -0.3162277660168379f * gt2 * g[8]; gg[8] += -0.3162277660168379f * gt2 * v[9];
-      gv[10] += 0.5477225575051661f * gt2 * g[5]; gg[5] += 0.5477225575051661f * gt2 * v[10];
-      gv[10] += -0.5477225575051661f * gt0 * g[7]; gg[7] += -0.5477225575051661f * gt0 * v[10];
-      gv[11] += 0.3162277660168379f * gt2 * g[4]; gg[4] += 0.3162277660168379f * gt2 * v[11];
-      gv[11] += -0.3162277660168379f * gt1 * g[5]; gg[5] += -0.3162277660168379f * gt1 * v[11];
-      gv[11] += 0.5477225575051661f * gt0 * g[6]; gg[6] += 0.5477225575051661f * gt0 * v[11];
-      gv[11] += -0.3162277660168379f * gt0 * g[8]; gg[8] += -0.3162277660168379f * gt0 * v[11];
-      gv[12] += -0.6324555320336758f * gt1 * g[4]; gg[4] += -0.6324555320336758f * gt1 * v[12];
-      gv[12] += 0.3162277660168379f * gt2 * g[5]; gg[5] += 0.3162277660168379f * gt2 * v[12];
-      gv[12] += 0.3162277660168379f * gt0 * g[7]; gg[7] += 0.3162277660168379f * gt0 * v[12];
-    }
     { // path 23
       const float w = th[23] * 0.4082482904638631f;
-      const float gt0 = w * gvo[8];
-      const float gt1 = w * gvo[9];
-      const float gt2 = w * gvo[10];
-      const float gt3 = w * gvo[11];
-      const float gt4 = w * gvo[12];
+      const float gt0 = w * gvo[4];
+      const float gt1 = w * gvo[5];
+      const float gt2 = w * gvo[6];
+      const float gt3 = w * gvo[7];
+      const float gt4 = w * gvo[8];
       gv[8] += 0.5345224838248488f * gt2 * g[4]; gg[4] += 0.5345224838248488f * gt2 * v[8];
       gv[8] += -0.4629100498862757f * gt3 * g[5]; gg[5] += -0.4629100498862757f * gt3 * v[8];
       gv[8] += 0.5345224838248488f * gt0 * g[6]; gg[6] += 0.5345224838248488f * gt0 * v[8];
@@ -2365,43 +2714,13 @@ template <> struct TP<2, 2, 0> {
       gv[12] += -0.4629100498862757f * gt3 * g[7]; gg[7] += -0.4629100498862757f * gt3 * v[12];
       gv[12] += 0.5345224838248488f * gt2 * g[8]; gg[8] += 0.5345224838248488f * gt2 * v[12];
     }
-    { // path 24
-      const float w = th[24] * 0.4082482904638631f;
-      const float gt0 = w * gvo[13];
-      const float gt1 = w * gvo[14];
-      const float gt2 = w * gvo[15];
-      const float gt3 = w * gvo[16];
-      const float gt4 = w * gvo[17];
-      gv[13] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[13];
-      gv[14] += 1.0f * gt1 * g[0]; gg[0] += 1.0f * gt1 * v[14];
-      gv[15] += 1.0000000000000002f * gt2 * g[0]; gg[0] += 1.0000000000000002f * gt2 * v[15];
-      gv[16] += 1.0f * gt3 * g[0]; gg[0] += 1.0f * gt3 * v[16];
-      gv[17] += 1.0f * gt4 * g[0]; gg[0] += 1.0f * gt4 * v[17];
-    }
-    { // path 25
-      const float w = th[25] * 0.4082482904638631f;
-      const float gt0 = w * gvo[5];
-      const float gt1 = w * gvo[6];
-      const float gt2 = w * gvo[7];
-      gv[13] += 0.547722557505166f * gt2 * g[1]; gg[1] += 0.547722557505166f * gt2 * v[13];
-      gv[13] += 0.547722557505166f * gt0 * g[3]; gg[3] += 0.547722557505166f * gt0 * v[13];
-      gv[14] += 0.547722557505166f * gt1 * g[1]; gg[1] += 0.547722557505166f * gt1 * v[14];
-      gv[14] += 0.547722557505166f * gt0 * g[2]; gg[2] += 0.547722557505166f * gt0 * v[14];
-      gv[15] += -0.3162277660168379f * gt0 * g[1]; gg[1] += -0.3162277660168379f * gt0 * v[15];
-      gv[15] += 0.632455532033676f * gt1 * g[2]; gg[2] += 0.632455532033676f * gt1 * v[15];
-      gv[15] += -0.3162277660168379f * gt2 * g[3]; gg[3] += -0.3162277660168379f * gt2 * v[15];
-      gv[16] += 0.547722557505166f * gt2 * g[2]; gg[2] += 0.547722557505166f * gt2 * v[16];
-      gv[16] += 0.547722557505166f * gt1 * g[3]; gg[3] += 0.547722557505166f * gt1 * v[16];
-      gv[17] += -0.547722557505166f * gt0 * g[1]; gg[1] += -0.547722557505166f * gt0 * v[17];
-      gv[17] += 0.547722557505166f * gt2 * g[3]; gg[3] += 0.547722557505166f * gt2 * v[17];
-    }
     { // path 26
       const float w = th[26] * 0.4082482904638631f;
-      const float gt0 = w * gvo[8];
-      const float gt1 = w * gvo[9];
-      const float gt2 = w * gvo[10];
-      const float gt3 = w * gvo[11];
-      const float gt4 = w * gvo[12];
+      const float gt0 = w * gvo[4];
+      const float gt1 = w * gvo[5];
+      const float gt2 = w * gvo[6];
+      const float gt3 = w * gvo[7];
+      const float gt4 = w * gvo[8];
       gv[13] += 0.408248290463863f * gt1 * g[1]; gg[1] += 0.408248290463863f * gt1 * v[13];
       gv[13] += 0.816496580927726f * gt4 * g[2]; gg[2] += 0.816496580927726f * gt4 * v[13];
       gv[13] += -0.408248290463863f * gt3 * g[3]; gg[3] += -0.408248290463863f * gt3 * v[13];
@@ -2419,20 +2738,11 @@ template <> struct TP<2, 2, 0> {
       gv[17] += -0.816496580927726f * gt0 * g[2]; gg[2] += -0.816496580927726f * gt0 * v[17];
       gv[17] += 0.408248290463863f * gt1 * g[3]; gg[3] += 0.408248290463863f * gt1 * v[17];
     }
-    { // path 27
-      const float w = th[27] * 0.5773502691896258f;
-      const float gt0 = w * gvo[1];
-      gv[13] += 0.4472135954999579f * gt0 * g[4]; gg[4] += 0.4472135954999579f * gt0 * v[13];
-      gv[14] += 0.4472135954999579f * gt0 * g[5]; gg[5] += 0.4472135954999579f * gt0 * v[14];
-      gv[15] += 0.44721359549995804f * gt0 * g[6]; gg[6] += 0.44721359549995804f * gt0 * v[15];
-      gv[16] += 0.4472135954999579f * gt0 * g[7]; gg[7] += 0.4472135954999579f * gt0 * v[16];
-      gv[17] += 0.4472135954999579f * gt0 * g[8]; gg[8] += 0.4472135954999579f * gt0 * v[17];
-    }
     { // path 28
       const float w = th[28] * 0.4082482904638631f;
-      const float gt0 = w * gvo[2];
-      const float gt1 = w * gvo[3];
-      const float gt2 = w * gvo[4];
+      const float gt0 = w * gvo[1];
+      const float gt1 = w * gvo[2];
+      const float gt2 = w * gvo[3];
       gv[13] += 0.3162277660168379f * gt0 * g[5]; gg[5] += 0.3162277660168379f * gt0 * v[13];
       gv[13] += -0.3162277660168379f * gt2 * g[7]; gg[7] += -0.3162277660168379f * gt2 * v[13];
       gv[13] += 0.6324555320336758f * gt1 * g[8]; gg[8] += 0.6324555320336758f * gt1 * v[13];
@@ -2450,80 +2760,7 @@ template <> struct TP<2, 2, 0> {
       gv[17] += 0.3162277660168379f * gt2 * g[5]; gg[5] += 0.3162277660168379f * gt2 * v[17];
       gv[17] += 0.3162277660168379f * gt0 * g[7]; gg[7] += 0.3162277660168379f * gt0 * v[17];
     }
-    { // path 29
-      const float w = th[29] * 0.4082482904638631f;
-      const float gt0 = w * gvo[13];
-      const float gt1 = w * gvo[14];
-      const float gt2 = w * gvo[15];
-      const float gt3 = w * gvo[16];
-      const float gt4 = w * gvo[17];
-      gv[13] += 0.5345224838248488f * gt2 * g[4]; gg[4] += 0.5345224838248488f * gt2 * v[13];
-      gv[13] += -0.4629100498862757f * gt3 * g[5]; gg[5] += -0.4629100498862757f * gt3 * v[13];
-      gv[13] += 0.5345224838248488f * gt0 * g[6]; gg[6] += 0.5345224838248488f * gt0 * v[13];
-      gv[13] += -0.4629100498862757f * gt1 * g[7]; gg[7] += -0.4629100498862757f * gt1 * v[13];
-      gv[14] += -0.4629100498862757f * gt3 * g[4]; gg[4] += -0.4629100498862757f * gt3 * v[14];
-      gv[14] += -0.2672612419124244f * gt2 * g[5]; gg[5] += -0.2672612419124244f * gt2 * v[14];
-      gv[14] += 0.4629100498862757f * gt4 * g[5]; gg[5] += 0.4629100498862757f * gt4 * v[14];
-      gv[14] += -0.2672612419124244f * gt1 * g[6]; gg[6] += -0.2672612419124244f * gt1 * v[14];
-      gv[14] += -0.4629100498862757f * gt0 * g[7]; gg[7] += -0.4629100498862757f * gt0 * v[14];
-      gv[14] += 0.4629100498862757f * gt1 * g[8]; gg[8] += 0.4629100498862757f * gt1 * v[14];
-      gv[15] += 0.5345224838248488f * gt0 * g[4]; gg[4] += 0.5345224838248488f * gt0 * v[15];
-      gv[15] += -0.2672612419124244f * gt1 * g[5]; gg[5] += -0.2672612419124244f * gt1 * v[15];
-      gv[15] += -0.5345224838248489f * gt2 * g[6]; gg[6] += -0.5345224838248489f * gt2 * v[15];
-      gv[15] += -0.2672612419124244f * gt3 * g[7]; gg[7] += -0.2672612419124244f * gt3 * v[15];
-      gv[15] += 0.5345224838248488f * gt4 * g[8]; gg[8] += 0.5345224838248488f * gt4 * v[15];
-      gv[16] += -0.4629100498862757f * gt1 * g[4]; gg[4] += -0.4629100498862757f * gt1 * v[16];
-      gv[16] += -0.4629100498862757f * gt0 * g[5]; gg[5] += -0.4629100498862757f * gt0 * v[16];
-      gv[16] += -0.2672612419124244f * gt3 * g[6]; gg[6] += -0.2672612419124244f * gt3 * v[16];
-      gv[16] += -0.2672612419124244f * gt2 * g[7]; gg[7] += -0.2672612419124244f * gt2 * v[16];
-      gv[16] += -0.4629100498862757f * gt4 * g[7]; gg[7] += -0.4629100498862757f * gt4 * v[16];
-      gv[16] += -0.4629100498862757f * gt3 * g[8]; gg[8] += -0.4629100498862757f * gt3 * v[16];
-      gv[17] += 0.4629100498862757f * gt1 * g[5]; gg[5] += 0.4629100498862757f * gt1 * v[17];
-      gv[17] += 0.5345224838248488f * gt4 * g[6]; gg[6] += 0.5345224838248488f * gt4 * v[17];
-      gv[17] += -0.4629100498862757f * gt3 * g[7]; gg[7] += -0.4629100498862757f * gt3 * v[17];
-      gv[17] += 0.5345224838248488f * gt2 * g[8]; gg[8] += 0.5345224838248488f * gt2 * v[17];
-    }
   }
-  static constexpr int NNZ = 274;
-};
-
-template <> struct TP<2, 2, 1> {
-  // in irreps [(0, 1), (0, -1), (1, -1), (1, 1), (2, 1), (2, -1)]; out irreps [(0, 1)]
-  static constexpr int NP = 3, DIN = 18, DOUT = 1, NS = 3, NPW = 0;
-  static __device__ __forceinline__ void fwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, float* s, float* vo) {
-    { // path 0: (0, 1) x (0,1) -> (0, 1)
-      const float t0 = 1.0f * v[0] * g[0];
-      s[0] = t0;
-    }
-    { // path 1: (1, -1) x (1,-1) -> (0, 1)
-      const float t0 = 0.5773502691896257f * v[2] * g[1] + 0.5773502691896258f * v[3] * g[2] + 0.5773502691896257f * v[4] * g[3];
-      s[1] = t0;
-    }
-    { // path 2: (2, 1) x (2,1) -> (0, 1)
-      const float t0 = 0.4472135954999579f * v[8] * g[4] + 0.4472135954999579f * v[9] * g[5] + 0.44721359549995804f * v[10] * g[6] + 0.4472135954999579f * v[11] * g[7] + 0.4472135954999579f * v[12] * g[8];
-      s[2] = t0;
-    }
-  }
-  static __device__ __forceinline__ void bwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, const float* __restrict__ gs, const float* __restrict__ gvo, float* gv, float* gg) {
-    { // path 0
-      const float gt0 = gs[0];
-      gv[0] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[0];
-    }
-    { // path 1
-      const float gt0 = gs[1];
-      gv[2] += 0.5773502691896257f * gt0 * g[1]; gg[1] += 0.5773502691896257f * gt0 * v[2];
-      gv[3] += 0.5773502691896258f * gt0 * g[2]; gg[2] += 0.5773502691896258f * gt0 * v[3];
-      gv[4] += 0.5773502691896257f * gt0 * g[3]; gg[3] += 0.5773502691896257f * gt0 * v[4];
-    }
-    { // path 2
-      const float gt0 = gs[2];
-      gv[8] += 0.4472135954999579f * gt0 * g[4]; gg[4] += 0.4472135954999579f * gt0 * v[8];
-      gv[9] += 0.4472135954999579f * gt0 * g[5]; gg[5] += 0.4472135954999579f * gt0 * v[9];
-      gv[10] += 0.44721359549995804f * gt0 * g[6]; gg[6] += 0.44721359549995804f * gt0 * v[10];
-      gv[11] += 0.4472135954999579f * gt0 * g[7]; gg[7] += 0.4472135954999579f * gt0 * v[11];
-      gv[12] += 0.4472135954999579f * gt0 * g[8]; gg[8] += 0.4472135954999579f * gt0 * v[12];
-    }
-  }
-  static constexpr int NNZ = 9;
+  static constexpr int NNZ = 137;
 };
 

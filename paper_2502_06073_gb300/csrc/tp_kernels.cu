@@ -38,7 +38,8 @@ __device__ __forceinline__ void cp_async16(float* smem, const float* gmem) {
                : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Copy `rows` rows of CT floats (16-byte aligned; source rows `stride` floats apart) into a
 // dense [rows][CT] shared buffer with the CT lanes of a team.
@@ -52,70 +53,204 @@ __device__ __forceinline__ void stage(float* dst, const float* src, int rows, in
   }
 }
 
-// The per-edge rows [dim][C] of V (and of its gradient) are contiguous per edge and
-// consecutive edges of an atom are adjacent, so the team streams them through a
-// shared-memory double buffer with cp.async: edge e+1 is in flight while edge e is used.
-template <int LMAX, int INK, int LAST, int CT>
-__global__ void __launch_bounds__(128)
+// Sum of 16 per-lane values over the CT lanes of a team by recursive halving: each round
+// a lane keeps half of its values and sends the other half to its partner, so the team
+// needs 15 (CT = 16) or 16 (CT = 32) shuffles instead of 16 butterfly reductions.  On
+// return the lane holds the team total of value index (lane >> 1) for CT = 32 and
+// (lane & 15) for CT = 16.
+template <int CT>
+__device__ __forceinline__ float team_reduce_scatter16(const float (&p)[16], int lane) {
+  const unsigned mask = team_mask<CT>();
+  float a8[8], a4[4], a2[2];
+  {
+    constexpr int o = CT / 2;
+    const bool hi = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float keep = hi ? p[8 + i] : p[i], send = hi ? p[i] : p[8 + i];
+      a8[i] = keep + __shfl_xor_sync(mask, send, o, CT);
+    }
+  }
+  {
+    constexpr int o = CT / 4;
+    const bool hi = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float keep = hi ? a8[4 + i] : a8[i], send = hi ? a8[i] : a8[4 + i];
+      a4[i] = keep + __shfl_xor_sync(mask, send, o, CT);
+    }
+  }
+  {
+    constexpr int o = CT / 8;
+    const bool hi = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const float keep = hi ? a4[2 + i] : a4[i], send = hi ? a4[i] : a4[2 + i];
+      a2[i] = keep + __shfl_xor_sync(mask, send, o, CT);
+    }
+  }
+  constexpr int o = CT / 16;
+  const bool hi = (lane & o) != 0;
+  float r = (hi ? a2[1] : a2[0]) + __shfl_xor_sync(mask, hi ? a2[0] : a2[1], o, CT);
+  if (CT == 32) r += __shfl_xor_sync(mask, r, 1, CT);
+  return r;
+}
+
+// Which of the 9 harmonic components a lane holds after team_reduce_scatter16 (-1: none).
+template <int CT>
+__device__ __forceinline__ int rs_index(int lane) {
+  if (CT == 32) return (lane & 1) ? -1 : ((lane >> 1) < 9 ? (lane >> 1) : -1);
+  return (lane & 15) < 9 ? (lane & 15) : -1;
+}
+
+// Per-edge shared-memory record of a team: the edge-feature row (24 floats: the harmonics
+// sit at FF_EF_Y), the team's slice of the env weights [(lmax+1)][CT], and, as the kernel
+// needs them, the input features V [DIN][CT], the scalar gradients [NS][CT] and the output
+// feature gradients [DOUT][CT].  Edges stream through a ring of NSTG such records with
+// cp.async, NSTG - 1 edges ahead of the one in use, so no global load of the edge loop is
+// waited for in the iteration that uses it.
+// Layer kinds.  INK: 0 = V^0 = w (x) Y formed in the kernel (first layer), 1 = outputs of
+// the first layer, 2 = outputs of a later layer, 3 = natural-parity irreps read from the
+// previous layer (the last layer after a layer of output kind 1).  OUTK: 0 = all reachable
+// irreps, 1 = natural-parity irreps only (the layer before the last: no other output
+// reaches the energy), 2 = the 0e scalars only (last layer).
+template <int LMAX, int INK, int OUTK>
+using TPK = TP<LMAX, INK == 3 ? 0 : INK, OUTK>;
+
+template <int LMAX, int INK, int OUTK, int CT, bool BWD>
+struct EdgeRec {
+  using K = TPK<LMAX, INK, OUTK>;
+  static constexpr bool LAST = OUTK == 2;
+  static constexpr int TEAMS = 128 / CT;
+  static constexpr int OFF_W = FF_EF_STRIDE;
+  static constexpr int OFF_V = OFF_W + (LMAX + 1) * CT;
+  static constexpr int OFF_GS = OFF_V + (INK > 0 ? K::DIN * CT : 0);
+  static constexpr int OFF_GVO = OFF_GS + (BWD ? K::NS * CT : 0);
+  static constexpr int SST = OFF_GVO + ((BWD && !LAST) ? K::DOUT * CT : 0);
+  // ring depth: up to 4 records within ~40 KB (adjoint) or ~24 KB (forward, which keeps
+  // more blocks resident) of shared memory per block, at least double buffering
+  static constexpr int BUDGET = (BWD ? 40 : 24) * 1024;
+  static constexpr int NSTG_FIT = BUDGET / (TEAMS * SST * 4);
+  static constexpr int NSTG = NSTG_FIT < 2 ? 2 : (NSTG_FIT > 4 ? 4 : NSTG_FIT);
+  // the passes that read only the edge-feature row and the env weights use the same
+  // buffer as a deeper ring of smaller records
+  static constexpr int SR = FF_EF_STRIDE + (LMAX + 1) * CT;
+  static constexpr int NSR_FIT = NSTG * SST / SR;
+  static constexpr int NSR = NSR_FIT > 8 ? 8 : NSR_FIT;
+  static_assert(NSR >= 2, "ring of edge-feature / env-weight records");
+  static_assert(FF_EF_STRIDE % 4 == 0, "edge-feature rows must be 16-byte multiples");
+  static_assert(TEAMS * SST * NSTG * 4 <= 48 * 1024, "static shared memory");
+};
+
+template <int LMAX, int CT>
+__device__ __forceinline__ void stage_ef_w(float* rec, int e, int lane, int C, int grp,
+                                           const float* ef, const float* W, int ldw) {
+  if (lane < FF_EF_STRIDE / 4)
+    cp_async16(rec + 4 * lane, ef + (size_t)e * FF_EF_STRIDE + 4 * lane);
+  stage<CT>(rec + FF_EF_STRIDE, W + (size_t)e * ldw + grp * CT, LMAX + 1, C, lane);
+}
+
+template <int LMAX, int INK, int OUTK, int CT, bool BWD>
+__device__ __forceinline__ void stage_edge(float* rec, int e, int lane, int C, int grp,
+                                           const float* ef, const float* W, int ldw,
+                                           const float* vin, const float* GX, int ldx, int D,
+                                           const float* gvout) {
+  using R = EdgeRec<LMAX, INK, OUTK, CT, BWD>;
+  using K = TPK<LMAX, INK, OUTK>;
+  if (lane < FF_EF_STRIDE / 4)
+    cp_async16(rec + 4 * lane, ef + (size_t)e * FF_EF_STRIDE + 4 * lane);
+  stage<CT>(rec + R::OFF_W, W + (size_t)e * ldw + grp * CT, LMAX + 1, C, lane);
+  if (INK > 0) stage<CT>(rec + R::OFF_V, vin + (size_t)e * K::DIN * C, K::DIN, C, lane);
+  if (BWD) {
+    stage<CT>(rec + R::OFF_GS, GX + (size_t)e * ldx + D + grp * CT, K::NS, C, lane);
+    if (!R::LAST) stage<CT>(rec + R::OFF_GVO, gvout + (size_t)e * K::DOUT * C, K::DOUT, C, lane);
+  }
+}
+
+template <int LMAX, int INK, int OUTK, int CT>
+__global__ void __launch_bounds__(128, 8)
 k_env_tp_fwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
              const float* __restrict__ ef, const float* __restrict__ W, int ldw,
              const float* __restrict__ Vin, const float* __restrict__ thetaT,
              float* __restrict__ X, __nv_bfloat16* __restrict__ Xb, int ldx, int D,
              float* __restrict__ Vout, float* __restrict__ Gam, float inv_sqrt_nu) {
-  using K = TP<LMAX, INK, LAST>;
+  using K = TPK<LMAX, INK, OUTK>;
+  using R = EdgeRec<LMAX, INK, OUTK, CT, false>;
+  constexpr bool LAST = R::LAST;
   constexpr int NY = (LMAX + 1) * (LMAX + 1);
-  constexpr int TEAMS = 128 / CT;
-  constexpr int SIN = INK > 0 ? K::DIN * CT : 4;
-  __shared__ __align__(16) float s_in[TEAMS * 2 * SIN];
+  constexpr int NSTG = R::NSTG, SST = R::SST;
+  __shared__ __align__(16) float s_rec[R::TEAMS * NSTG * SST];
   const int G = C / CT;
   const int team = threadIdx.x / CT, lane = threadIdx.x % CT;
-  const long long tg = (long long)blockIdx.x * TEAMS + team;
+  const long long tg = (long long)blockIdx.x * R::TEAMS + team;
   const int a = (int)(tg / G), grp = (int)(tg - (long long)a * G);
   if (a >= n_atoms) return;
   const int c = grp * CT + lane;
   const int eb = row_ptr[a] - e0, ee = row_ptr[a + 1] - e0;
-  float* buf = s_in + team * 2 * SIN;
+  float* buf = s_rec + team * NSTG * SST;
   const float* vin = Vin + grp * CT;
-  if (INK > 0 && eb < ee) stage<CT>(buf, vin + (size_t)eb * K::DIN * C, K::DIN, C, lane);
-  cp_commit();
-
+  auto fetch = [&](int e, int slot) {
+    stage_edge<LMAX, INK, OUTK, CT, false>(buf + slot * SST, e, lane, C, grp, ef, W, ldw, vin,
+                                           nullptr, 0, 0, nullptr);
+  };
+  // environment sum over a ring of (edge-feature row, env-weight slice) records
+  constexpr int SR = R::SR, NSR = R::NSR;
+  auto fetch1 = [&](int e, int slot) {
+    stage_ef_w<LMAX, CT>(buf + slot * SR, e, lane, C, grp, ef, W, ldw);
+  };
+#pragma unroll
+  for (int p = 0; p < NSR - 1; ++p) {
+    if (eb + p < ee) fetch1(eb + p, p);
+    cp_commit();
+  }
   float G_[NY];
 #pragma unroll
   for (int k = 0; k < NY; ++k) G_[k] = 0.f;
   for (int e = eb; e < ee; ++e) {
-    const float* y = ef + (size_t)e * FF_EF_STRIDE + FF_EF_Y;
+    const int i = e - eb;
+    if (e + NSR - 1 < ee) fetch1(e + NSR - 1, (i + NSR - 1) % NSR);
+    cp_commit();
+    cp_wait<NSR - 1>();
+    __syncwarp(team_mask<CT>());
+    const float* rec = buf + (i % NSR) * SR;
 #pragma unroll
     for (int l = 0; l <= LMAX; ++l) {
-      const float w = W[(size_t)e * ldw + l * C + c];
+      const float w = rec[FF_EF_STRIDE + l * CT + lane];
 #pragma unroll
-      for (int m = 0; m < 2 * l + 1; ++m) G_[l * l + m] += w * y[l * l + m];
+      for (int m = 0; m < 2 * l + 1; ++m) G_[l * l + m] += w * rec[FF_EF_Y + l * l + m];
     }
+    __syncwarp(team_mask<CT>());
   }
 #pragma unroll
   for (int k = 0; k < NY; ++k) {
     G_[k] *= inv_sqrt_nu;
     Gam[((size_t)a * NY + k) * C + c] = G_[k];
   }
+  // tensor products over the ring of full records
+#pragma unroll
+  for (int p = 0; p < NSTG - 1; ++p) {
+    if (eb + p < ee) fetch(eb + p, p);
+    cp_commit();
+  }
   const float* th = thetaT + (size_t)c * K::NP;
   for (int e = eb; e < ee; ++e) {
-    const int cur = (e - eb) & 1;
-    if (INK > 0 && e + 1 < ee)
-      stage<CT>(buf + (cur ^ 1) * SIN, vin + (size_t)(e + 1) * K::DIN * C, K::DIN, C, lane);
+    const int i = e - eb;
+    if (e + NSTG - 1 < ee) fetch(e + NSTG - 1, (i + NSTG - 1) % NSTG);
     cp_commit();
-    cp_wait1();
+    cp_wait<NSTG - 1>();
     __syncwarp(team_mask<CT>());
+    const float* rec = buf + (i % NSTG) * SST;
     float v[K::DIN];
     if (INK == 0) {
-      const float* y = ef + (size_t)e * FF_EF_STRIDE + FF_EF_Y;
 #pragma unroll
       for (int l = 0; l <= LMAX; ++l) {
-        const float w = W[(size_t)e * ldw + l * C + c];
+        const float w = rec[R::OFF_W + l * CT + lane];
 #pragma unroll
-        for (int m = 0; m < 2 * l + 1; ++m) v[l * l + m] = w * y[l * l + m];
+        for (int m = 0; m < 2 * l + 1; ++m) v[l * l + m] = w * rec[FF_EF_Y + l * l + m];
       }
     } else {
 #pragma unroll
-      for (int k = 0; k < K::DIN; ++k) v[k] = buf[cur * SIN + k * CT + lane];
+      for (int k = 0; k < K::DIN; ++k) v[k] = rec[R::OFF_V + k * CT + lane];
     }
     float s[K::NS], vo[K::DOUT];
     K::fwd(v, G_, th, s, vo);
@@ -133,38 +268,46 @@ k_env_tp_fwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
   }
 }
 
-template <int LMAX, int INK, int LAST, int CT>
+// Adjoint.  First pass over the atom's edges: the tensor-product adjoint per edge (input
+// feature gradients, the layer-1 weight/harmonic terms of V^0 = w (x) Y) and the gradient
+// of the environment embedding, accumulated in registers.  Second pass: that gradient fanned
+// back to every edge's env weights and harmonics.  The harmonic gradients of each (pass,
+// channel group) go to their own slice of gY (written once, no read-modify-write); the
+// geometric adjoint sums the slices in a fixed order.
+template <int LMAX, int INK, int OUTK, int CT>
 __global__ void __launch_bounds__(128)
 k_env_tp_bwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
              const float* __restrict__ ef, const float* __restrict__ W, int ldw,
              const float* __restrict__ Vin, const float* __restrict__ thetaT,
              const float* __restrict__ GX, int ldx, int D, const float* __restrict__ gVout,
              float* __restrict__ gVin, float* __restrict__ GW, __nv_bfloat16* __restrict__ GWb,
-             float* __restrict__ gY, const float* __restrict__ Gam, float inv_sqrt_nu) {
-  using K = TP<LMAX, INK, LAST>;
+             float* __restrict__ gY_v0, float* __restrict__ gY_env, int gy_stride,
+             const float* __restrict__ Gam, float inv_sqrt_nu) {
+  using K = TPK<LMAX, INK, OUTK>;
+  using R = EdgeRec<LMAX, INK, OUTK, CT, true>;
+  constexpr bool LAST = R::LAST;
   constexpr int NY = (LMAX + 1) * (LMAX + 1);
-  constexpr int TEAMS = 128 / CT;
-  constexpr int SIN = INK > 0 ? K::DIN * CT : 0;
-  constexpr int SOUT = LAST ? 0 : K::DOUT * CT;
-  constexpr int SST = (SIN + SOUT) > 0 ? SIN + SOUT : 4;   // floats staged per edge
-  __shared__ __align__(16) float s_in[TEAMS * 2 * SST];
+  constexpr int NSTG = R::NSTG, SST = R::SST;
+  __shared__ __align__(16) float s_rec[R::TEAMS * NSTG * SST];
   const int G = C / CT;
   const int team = threadIdx.x / CT, lane = threadIdx.x % CT;
-  const long long tg = (long long)blockIdx.x * TEAMS + team;
+  const long long tg = (long long)blockIdx.x * R::TEAMS + team;
   const int a = (int)(tg / G), grp = (int)(tg - (long long)a * G);
   if (a >= n_atoms) return;
   const int c = grp * CT + lane;
   const int eb = row_ptr[a] - e0, ee = row_ptr[a + 1] - e0;
-  float* buf = s_in + team * 2 * SST;
+  float* buf = s_rec + team * NSTG * SST;
   const float* vin = Vin + grp * CT;
   const float* gvout = gVout + grp * CT;
-  auto prefetch = [&](int e, int slot) {
-    if (SIN > 0) stage<CT>(buf + slot * SST, vin + (size_t)e * K::DIN * C, K::DIN, C, lane);
-    if (SOUT > 0)
-      stage<CT>(buf + slot * SST + SIN, gvout + (size_t)e * K::DOUT * C, K::DOUT, C, lane);
+  auto fetch = [&](int e, int slot) {
+    stage_edge<LMAX, INK, OUTK, CT, true>(buf + slot * SST, e, lane, C, grp, ef, W, ldw, vin, GX,
+                                          ldx, D, gvout);
   };
-  if (eb < ee) prefetch(eb, 0);
-  cp_commit();
+#pragma unroll
+  for (int p = 0; p < NSTG - 1; ++p) {
+    if (eb + p < ee) fetch(eb + p, p);
+    cp_commit();
+  }
   float G_[NY], gG[NY];
 #pragma unroll
   for (int k = 0; k < NY; ++k) {
@@ -172,140 +315,174 @@ k_env_tp_bwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
     gG[k] = 0.f;
   }
   const float* th = thetaT + (size_t)c * K::NP;
-  // harmonic gradients: one partial per channel group, summed later in a fixed order
-  float* gYg = gY + (size_t)grp * 9;
-  const int gstride = 9 * G;
+  const int ridx = rs_index<CT>(lane);
   for (int e = eb; e < ee; ++e) {
-    const int cur = (e - eb) & 1;
-    if (e + 1 < ee) prefetch(e + 1, cur ^ 1);
+    const int i = e - eb;
+    if (e + NSTG - 1 < ee) fetch(e + NSTG - 1, (i + NSTG - 1) % NSTG);
     cp_commit();
-    cp_wait1();
+    cp_wait<NSTG - 1>();
     __syncwarp(team_mask<CT>());
-    const float* y = ef + (size_t)e * FF_EF_STRIDE + FF_EF_Y;
+    const float* rec = buf + (i % NSTG) * SST;
     float v[K::DIN], gv[K::DIN];
     float wl[LMAX + 1];
 #pragma unroll
-    for (int l = 0; l <= LMAX; ++l) wl[l] = W[(size_t)e * ldw + l * C + c];
+    for (int l = 0; l <= LMAX; ++l) wl[l] = rec[R::OFF_W + l * CT + lane];
     if (INK == 0) {
 #pragma unroll
       for (int l = 0; l <= LMAX; ++l)
 #pragma unroll
-        for (int m = 0; m < 2 * l + 1; ++m) v[l * l + m] = wl[l] * y[l * l + m];
+        for (int m = 0; m < 2 * l + 1; ++m) v[l * l + m] = wl[l] * rec[FF_EF_Y + l * l + m];
     } else {
 #pragma unroll
-      for (int k = 0; k < K::DIN; ++k) v[k] = buf[cur * SST + k * CT + lane];
+      for (int k = 0; k < K::DIN; ++k) v[k] = rec[R::OFF_V + k * CT + lane];
     }
 #pragma unroll
     for (int k = 0; k < K::DIN; ++k) gv[k] = 0.f;
     float gs[K::NS], gvo[K::DOUT];
 #pragma unroll
-    for (int q = 0; q < K::NS; ++q) gs[q] = GX[(size_t)e * ldx + D + q * C + c];
+    for (int q = 0; q < K::NS; ++q) gs[q] = rec[R::OFF_GS + q * CT + lane];
 #pragma unroll
-    for (int k = 0; k < K::DOUT; ++k) gvo[k] = LAST ? 0.f : buf[cur * SST + SIN + k * CT + lane];
+    for (int k = 0; k < K::DOUT; ++k) gvo[k] = LAST ? 0.f : rec[R::OFF_GVO + k * CT + lane];
     K::bwd(v, G_, th, gs, gvo, gv, gG);
     if (INK == 0) {
       // V^0 = w (x) Y: gradient to the env weights and to the harmonics
+      float p[16];
 #pragma unroll
       for (int l = 0; l <= LMAX; ++l) {
         float gw = 0.f;
 #pragma unroll
-        for (int m = 0; m < 2 * l + 1; ++m) gw += gv[l * l + m] * y[l * l + m];
+        for (int m = 0; m < 2 * l + 1; ++m) {
+          gw += gv[l * l + m] * rec[FF_EF_Y + l * l + m];
+          p[l * l + m] = gv[l * l + m] * wl[l];
+        }
         GW[(size_t)e * ldw + l * C + c] = gw;
       }
 #pragma unroll
-      for (int l = 0; l <= LMAX; ++l)
-#pragma unroll
-        for (int m = 0; m < 2 * l + 1; ++m) {
-          const float tt = team_sum<CT>(gv[l * l + m] * wl[l]);
-          if (lane == l * l + m) gYg[(size_t)e * gstride + l * l + m] += tt;
-        }
+      for (int k = NY; k < 16; ++k) p[k] = 0.f;
+      const float t = team_reduce_scatter16<CT>(p, lane);
+      if (ridx >= 0) gY_v0[(size_t)e * gy_stride + grp * 9 + ridx] = t;
     } else {
 #pragma unroll
       for (int k = 0; k < K::DIN; ++k) gVin[((size_t)e * K::DIN + k) * C + c] = gv[k];
     }
     __syncwarp(team_mask<CT>());
   }
-  // adjoint of the environment sum, fanned back out to every edge of the atom
+  // adjoint of the environment sum, fanned back out to every edge of the atom, over a ring
+  // of (edge-feature row, env-weight slice) records; the layer-1 weight gradients of the
+  // first pass (this lane's own stores) are read one edge ahead
 #pragma unroll
   for (int k = 0; k < NY; ++k) gG[k] *= inv_sqrt_nu;
+  constexpr int SR = R::SR, NSR = R::NSR;
+  auto fetch1 = [&](int e, int slot) {
+    stage_ef_w<LMAX, CT>(buf + slot * SR, e, lane, C, grp, ef, W, ldw);
+  };
+#pragma unroll
+  for (int p = 0; p < NSR - 1; ++p) {
+    if (eb + p < ee) fetch1(eb + p, p);
+    cp_commit();
+  }
+  float gw_next[LMAX + 1];
+#pragma unroll
+  for (int l = 0; l <= LMAX; ++l)
+    gw_next[l] = (INK == 0 && eb < ee) ? GW[(size_t)eb * ldw + l * C + c] : 0.f;
   for (int e = eb; e < ee; ++e) {
-    const float* y = ef + (size_t)e * FF_EF_STRIDE + FF_EF_Y;
+    const int i = e - eb;
+    if (e + NSR - 1 < ee) fetch1(e + NSR - 1, (i + NSR - 1) % NSR);
+    cp_commit();
+    float gw0[LMAX + 1];
 #pragma unroll
     for (int l = 0; l <= LMAX; ++l) {
-      const size_t wi = (size_t)e * ldw + l * C + c;
-      const float wl = W[wi];
+      gw0[l] = gw_next[l];
+      if (INK == 0 && e + 1 < ee) gw_next[l] = GW[(size_t)(e + 1) * ldw + l * C + c];
+    }
+    cp_wait<NSR - 1>();
+    __syncwarp(team_mask<CT>());
+    const float* rec = buf + (i % NSR) * SR;
+    float p[16];
+#pragma unroll
+    for (int l = 0; l <= LMAX; ++l) {
+      const float wl = rec[FF_EF_STRIDE + l * CT + lane];
       float gw = 0.f;
 #pragma unroll
-      for (int m = 0; m < 2 * l + 1; ++m) gw += gG[l * l + m] * y[l * l + m];
-      const float tot = (INK == 0 ? GW[wi] : 0.f) + gw;
+      for (int m = 0; m < 2 * l + 1; ++m) {
+        gw += gG[l * l + m] * rec[FF_EF_Y + l * l + m];
+        p[l * l + m] = gG[l * l + m] * wl;
+      }
+      const float tot = gw0[l] + gw;
+      const size_t wi = (size_t)e * ldw + l * C + c;
       if (GWb) GWb[wi] = __float2bfloat16_rn(tot);
       else GW[wi] = tot;
-#pragma unroll
-      for (int m = 0; m < 2 * l + 1; ++m) {
-        const float tt = team_sum<CT>(gG[l * l + m] * wl);
-        if (lane == l * l + m) gYg[(size_t)e * gstride + l * l + m] += tt;
-      }
     }
+#pragma unroll
+    for (int k = NY; k < 16; ++k) p[k] = 0.f;
+    const float t = team_reduce_scatter16<CT>(p, lane);
+    if (ridx >= 0) gY_env[(size_t)e * gy_stride + grp * 9 + ridx] = t;
+    __syncwarp(team_mask<CT>());
   }
 }
 
-template <int LMAX, int INK, int LAST, int CT>
+template <int LMAX, int INK, int OUTK, int CT>
 void fwd_one(int n_atoms, int C, const int* row_ptr, int e0, const float* ef, const float* W,
              int ldw, const float* Vin, const float* thetaT, float* X, __nv_bfloat16* Xb,
              int ldx, int D, float* Vout, float* Gam, float inv_sqrt_nu, cudaStream_t s) {
   const long long teams = (long long)n_atoms * (C / CT);
-  k_env_tp_fwd<LMAX, INK, LAST, CT><<<ff_cdiv(teams * CT, 128), 128, 0, s>>>(
+  k_env_tp_fwd<LMAX, INK, OUTK, CT><<<ff_cdiv(teams * CT, 128), 128, 0, s>>>(
       n_atoms, C, row_ptr, e0, ef, W, ldw, Vin, thetaT, X, Xb, ldx, D, Vout, Gam, inv_sqrt_nu);
 }
 
-template <int LMAX, int INK, int LAST, int CT>
+template <int LMAX, int INK, int OUTK, int CT>
 void bwd_one(int n_atoms, int C, const int* row_ptr, int e0, const float* ef, const float* W,
              int ldw, const float* Vin, const float* thetaT, const float* GX, int ldx, int D,
-             const float* gVout, float* gVin, float* GW, __nv_bfloat16* GWb, float* gY,
-             const float* Gam, float inv_sqrt_nu, cudaStream_t s) {
+             const float* gVout, float* gVin, float* GW, __nv_bfloat16* GWb, float* gY_v0,
+             float* gY_env, int gy_stride, const float* Gam, float inv_sqrt_nu, cudaStream_t s) {
   const long long teams = (long long)n_atoms * (C / CT);
-  k_env_tp_bwd<LMAX, INK, LAST, CT><<<ff_cdiv(teams * CT, 128), 128, 0, s>>>(
-      n_atoms, C, row_ptr, e0, ef, W, ldw, Vin, thetaT, GX, ldx, D, gVout, gVin, GW, GWb, gY,
-      Gam, inv_sqrt_nu);
+  k_env_tp_bwd<LMAX, INK, OUTK, CT><<<ff_cdiv(teams * CT, 128), 128, 0, s>>>(
+      n_atoms, C, row_ptr, e0, ef, W, ldw, Vin, thetaT, GX, ldx, D, gVout, gVin, GW, GWb, gY_v0,
+      gY_env, gy_stride, Gam, inv_sqrt_nu);
 }
 
+// (input kind, output kind) of every layer of a 1- to 4-layer model; see TPK above.
 #define FF_TP_DISPATCH(FN, ...)                                                             \
   do {                                                                                      \
-    const int key = ((lmax * 3 + in_kind) * 2 + last) * 2 + (C == 16 ? 0 : 1);              \
+    const int key = ((lmax * 4 + in_kind) * 3 + out_kind) * 2 + (C == 16 ? 0 : 1);          \
     switch (key) {                                                                          \
-      case ((1 * 3 + 0) * 2 + 0) * 2 + 0: FN<1, 0, 0, 16>(__VA_ARGS__); break;             \
-      case ((1 * 3 + 0) * 2 + 0) * 2 + 1: FN<1, 0, 0, 32>(__VA_ARGS__); break;             \
-      case ((1 * 3 + 0) * 2 + 1) * 2 + 0: FN<1, 0, 1, 16>(__VA_ARGS__); break;             \
-      case ((1 * 3 + 0) * 2 + 1) * 2 + 1: FN<1, 0, 1, 32>(__VA_ARGS__); break;             \
-      case ((1 * 3 + 1) * 2 + 0) * 2 + 0: FN<1, 1, 0, 16>(__VA_ARGS__); break;             \
-      case ((1 * 3 + 1) * 2 + 0) * 2 + 1: FN<1, 1, 0, 32>(__VA_ARGS__); break;             \
-      case ((1 * 3 + 1) * 2 + 1) * 2 + 0: FN<1, 1, 1, 16>(__VA_ARGS__); break;             \
-      case ((1 * 3 + 1) * 2 + 1) * 2 + 1: FN<1, 1, 1, 32>(__VA_ARGS__); break;             \
-      case ((1 * 3 + 2) * 2 + 0) * 2 + 0: FN<1, 2, 0, 16>(__VA_ARGS__); break;             \
-      case ((1 * 3 + 2) * 2 + 0) * 2 + 1: FN<1, 2, 0, 32>(__VA_ARGS__); break;             \
-      case ((1 * 3 + 2) * 2 + 1) * 2 + 0: FN<1, 2, 1, 16>(__VA_ARGS__); break;             \
-      case ((1 * 3 + 2) * 2 + 1) * 2 + 1: FN<1, 2, 1, 32>(__VA_ARGS__); break;             \
-      case ((2 * 3 + 0) * 2 + 0) * 2 + 0: FN<2, 0, 0, 16>(__VA_ARGS__); break;             \
-      case ((2 * 3 + 0) * 2 + 0) * 2 + 1: FN<2, 0, 0, 32>(__VA_ARGS__); break;             \
-      case ((2 * 3 + 0) * 2 + 1) * 2 + 0: FN<2, 0, 1, 16>(__VA_ARGS__); break;             \
-      case ((2 * 3 + 0) * 2 + 1) * 2 + 1: FN<2, 0, 1, 32>(__VA_ARGS__); break;             \
-      case ((2 * 3 + 1) * 2 + 0) * 2 + 0: FN<2, 1, 0, 16>(__VA_ARGS__); break;             \
-      case ((2 * 3 + 1) * 2 + 0) * 2 + 1: FN<2, 1, 0, 32>(__VA_ARGS__); break;             \
-      case ((2 * 3 + 1) * 2 + 1) * 2 + 0: FN<2, 1, 1, 16>(__VA_ARGS__); break;             \
-      case ((2 * 3 + 1) * 2 + 1) * 2 + 1: FN<2, 1, 1, 32>(__VA_ARGS__); break;             \
-      case ((2 * 3 + 2) * 2 + 0) * 2 + 0: FN<2, 2, 0, 16>(__VA_ARGS__); break;             \
-      case ((2 * 3 + 2) * 2 + 0) * 2 + 1: FN<2, 2, 0, 32>(__VA_ARGS__); break;             \
-      case ((2 * 3 + 2) * 2 + 1) * 2 + 0: FN<2, 2, 1, 16>(__VA_ARGS__); break;             \
-      case ((2 * 3 + 2) * 2 + 1) * 2 + 1: FN<2, 2, 1, 32>(__VA_ARGS__); break;             \
-      default: break;                                                                       \
+      case 24: FN<1, 0, 0, 16>(__VA_ARGS__); break;                                         \
+      case 25: FN<1, 0, 0, 32>(__VA_ARGS__); break;                                         \
+      case 26: FN<1, 0, 1, 16>(__VA_ARGS__); break;                                         \
+      case 27: FN<1, 0, 1, 32>(__VA_ARGS__); break;                                         \
+      case 28: FN<1, 0, 2, 16>(__VA_ARGS__); break;                                         \
+      case 29: FN<1, 0, 2, 32>(__VA_ARGS__); break;                                         \
+      case 30: FN<1, 1, 0, 16>(__VA_ARGS__); break;                                         \
+      case 31: FN<1, 1, 0, 32>(__VA_ARGS__); break;                                         \
+      case 32: FN<1, 1, 1, 16>(__VA_ARGS__); break;                                         \
+      case 33: FN<1, 1, 1, 32>(__VA_ARGS__); break;                                         \
+      case 38: FN<1, 2, 1, 16>(__VA_ARGS__); break;                                         \
+      case 39: FN<1, 2, 1, 32>(__VA_ARGS__); break;                                         \
+      case 46: FN<1, 3, 2, 16>(__VA_ARGS__); break;                                         \
+      case 47: FN<1, 3, 2, 32>(__VA_ARGS__); break;                                         \
+      case 48: FN<2, 0, 0, 16>(__VA_ARGS__); break;                                         \
+      case 49: FN<2, 0, 0, 32>(__VA_ARGS__); break;                                         \
+      case 50: FN<2, 0, 1, 16>(__VA_ARGS__); break;                                         \
+      case 51: FN<2, 0, 1, 32>(__VA_ARGS__); break;                                         \
+      case 52: FN<2, 0, 2, 16>(__VA_ARGS__); break;                                         \
+      case 53: FN<2, 0, 2, 32>(__VA_ARGS__); break;                                         \
+      case 54: FN<2, 1, 0, 16>(__VA_ARGS__); break;                                         \
+      case 55: FN<2, 1, 0, 32>(__VA_ARGS__); break;                                         \
+      case 56: FN<2, 1, 1, 16>(__VA_ARGS__); break;                                         \
+      case 57: FN<2, 1, 1, 32>(__VA_ARGS__); break;                                         \
+      case 62: FN<2, 2, 1, 16>(__VA_ARGS__); break;                                         \
+      case 63: FN<2, 2, 1, 32>(__VA_ARGS__); break;                                         \
+      case 70: FN<2, 3, 2, 16>(__VA_ARGS__); break;                                         \
+      case 71: FN<2, 3, 2, 32>(__VA_ARGS__); break;                                         \
+      default: break; /* unreachable: ff_create admits only these kinds */                   \
     }                                                                                       \
   } while (0)
 
 }  // namespace
 
 
-void launch_env_tp_fwd(int lmax, int in_kind, int last, int C, int n_atoms, const int* row_ptr,
-                       int e0, const float* ef, const float* W, int ldw, const float* Vin,
+void launch_env_tp_fwd(int lmax, int in_kind, int out_kind, int C, int n_atoms,
+                       const int* row_ptr, int e0, const float* ef, const float* W, int ldw, const float* Vin,
                        const float* theta, float* X, __nv_bfloat16* Xb, int ldx, int D,
                        float* Vout, float* Gam, float inv_sqrt_nu, cudaStream_t s) {
   ProfScope ps_(PC_TP_FWD, s);
@@ -315,14 +492,14 @@ void launch_env_tp_fwd(int lmax, int in_kind, int last, int C, int n_atoms, cons
   ff_count_launch(1);
 }
 
-void launch_env_tp_bwd(int lmax, int in_kind, int last, int C, int n_atoms, const int* row_ptr,
-                       int e0, const float* ef, const float* W, int ldw, const float* Vin,
+void launch_env_tp_bwd(int lmax, int in_kind, int out_kind, int C, int n_atoms,
+                       const int* row_ptr, int e0, const float* ef, const float* W, int ldw, const float* Vin,
                        const float* theta, const float* GX, int ldx, int D, const float* gVout,
-                       float* gVin, float* GW, __nv_bfloat16* GWb, float* gY, const float* Gam,
-                       float inv_sqrt_nu, cudaStream_t s) {
+                       float* gVin, float* GW, __nv_bfloat16* GWb, float* gY_v0, float* gY_env,
+                       int gy_stride, const float* Gam, float inv_sqrt_nu, cudaStream_t s) {
   ProfScope ps_(PC_TP_BWD, s);
   if (n_atoms <= 0) return;
   FF_TP_DISPATCH(bwd_one, n_atoms, C, row_ptr, e0, ef, W, ldw, Vin, theta, GX, ldx, D, gVout,
-                 gVin, GW, GWb, gY, Gam, inv_sqrt_nu, s);
+                 gVin, GW, GWb, gY_v0, gY_env, gy_stride, Gam, inv_sqrt_nu, s);
   ff_count_launch(1);
 }

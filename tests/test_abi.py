@@ -83,6 +83,41 @@ def test_generated_paths_match_oracle_paths():
                 assert irr == irr_in and gp == paths and gouts == outs
 
 
+def test_pruned_layer_before_last_keeps_everything_the_energy_sees():
+    """The layer before the last computes only natural-parity outputs (output kind 1) and
+    the last layer reads only those: check against the oracle's full path lists that every
+    path into a 0e output of the last layer starts from a natural-parity irrep, that the
+    pruned kind keeps exactly the paths into natural outputs with their full-list indices
+    (path weights and the 1/sqrt(n) mixing are those of the full layer), and that every
+    layer of a 1- to 4-layer model maps to a generated kind."""
+    from oracle import so3
+    gen = _gen_module()
+    for lmax in (1, 2):
+        for n_layers in (1, 2, 3, 4):
+            layers = so3.model_paths(lmax, n_layers)
+            irr_last, paths_last, _ = layers[-1]
+            for (i_in, _l2, out) in paths_last:
+                assert out == (0, 1) and gen.natural(irr_last[i_in])
+            for L in range(1, n_layers + 1):
+                ink, outk = gen.layer_kinds(L, n_layers)
+                irr = 0 if ink == 3 else ink
+                assert (irr, outk) in gen.KINDS
+                _, _, info = gen.gen_kind(lmax, irr, outk)
+                irr_in, paths, outs = layers[L - 1]
+                if ink == 3:
+                    assert info["irr_in"] == [ir for ir in irr_in if gen.natural(ir)]
+                else:
+                    assert info["irr_in"] == irr_in
+                if outk == 1:
+                    assert info["np"] == len(paths)
+                    assert info["kept"] == sum(gen.natural(p[2]) for p in paths)
+                    assert info["outs"] == [o for o in outs if gen.natural(o)]
+                elif outk == 2:
+                    assert info["outs"] == [(0, 1)] and info["kept"] == info["np"]
+                else:
+                    assert info["outs"] == outs and info["kept"] == len(paths)
+
+
 def test_committed_tp_header_is_current(tmp_path):
     gen = _gen_module()
     out = tmp_path / "tp_gen.cuh"

@@ -123,6 +123,18 @@ def test_energy_forces_full(ff, key, wl):
     _check_ef(Es, Ea, F, E_ref, Ea_ref, F_ref, key, s.sys_ptr)
 
 
+@pytest.mark.parametrize("n_layers,lmax", [(1, 2), (4, 2), (1, 1), (4, 1)])
+def test_layer_counts_full(ff, n_layers, lmax):
+    """1- and 4-layer models: every tensor-product layer kind (a single last layer; the
+    first, middle and pruned layer before the last, and a last layer reading it)."""
+    s = synth.config1_system()
+    hp = _hp("small", "cubic96", n_layers=n_layers, lmax=lmax)
+    m, pos = _bind(ff, hp, s)
+    Es, Ea, F = m.energy_forces(pos)
+    E_ref, Ea_ref, F_ref = pool.evaluate(hp, 42, s.pos, s.Z, s.box, s.pbc, s.sys_ptr)
+    _check_ef(Es, Ea, F, E_ref, Ea_ref, F_ref, f"L{n_layers} lmax{lmax}", s.sys_ptr)
+
+
 def test_water4095_energy_and_sampled_forces(ff):
     make, name, _ = SYSTEMS["water4095"]
     s = make()
