@@ -197,6 +197,11 @@ struct ff_ctx {
   __nv_bfloat16* Xb[FF_MAX_LAYERS + 1] = {nullptr};
   __nv_bfloat16* GZb[2] = {nullptr};
   __nv_bfloat16* GWb = nullptr;
+  // fused readout of the tensor-core path (last latent GEMM + edge-energy head): dE_e/dz
+  // of the last latent layer, per-edge energies and the envelope-gradient seed
+  bool head = false;
+  __nv_bfloat16* GZL = nullptr;
+  float* E_edge = nullptr; float* gfL = nullptr;
   // state of the last evaluation
   bool state_valid = false;
   int state_chunks = 0;
@@ -305,6 +310,7 @@ void build_structure(ff_ctx* c) {
   c->ldx = c->D + c->ns * c->C;
   c->ldw = (hp.lmax + 1) * c->C;
   c->cgroups = c->C > 32 ? c->C / 32 : 1;
+  c->head = hp.precision == 1 && c->D <= 256 && hp.latent[hp.n_latent - 1] == c->D;
   c->maxw = c->ldx;
   for (int k = 0; k < hp.n_two_body; ++k) c->maxw = std::max(c->maxw, hp.two_body[k]);
   for (int k = 0; k < hp.n_latent; ++k) c->maxw = std::max(c->maxw, hp.latent[k]);
@@ -460,11 +466,11 @@ void free_workspace(ff_ctx* c) {
   c->acap = 0;
 }
 
-// Carve every per-chunk buffer from one allocation sized for `ecap` edges / `acap` atoms.
 // Harmonic-gradient slices per edge: one per (layer, channel group) for the fan-out of the
 // environment adjoint, plus one per channel group for the layer-1 term of V^0 = w (x) Y.
 int gy_slices(const ff_ctx* c) { return (c->NL + 1) * c->cgroups; }
 
+// Carve every per-chunk buffer from one allocation sized for `ecap` edges / `acap` atoms.
 int ensure_workspace(ff_ctx* c, long long ecap, int acap, long long budget_edges) {
   if (ecap <= c->wcap && acap <= c->acap) return FF_OK;
   // grow with headroom (edge counts drift from step to step in MD, and every regrowth is
@@ -517,6 +523,11 @@ int ensure_workspace(ff_ctx* c, long long ecap, int acap, long long budget_edges
     b16(&c->GZb[1], ecap * c->maxw);
     b16(&c->GWb, ecap * c->ldw);
   }
+  if (c->head) {
+    b16(&c->GZL, ecap * c->D);
+    f32(&c->E_edge, ecap);
+    f32(&c->gfL, ecap);
+  }
   size_t total = 0;
   for (auto& p : plan) total += (p.second + 255) & ~(size_t)255;
   void* base = nullptr;
@@ -552,6 +563,7 @@ size_t bytes_per_edge(const ff_ctx* c) {
   b += (size_t)c->ldw * 4 + 9 * 4 * (size_t)gy_slices(c) + 4;
   if (hp.precision == 1)   // bf16 operands (the fp32 hidden activations are not kept)
     b += (size_t)(c->NL + 1) * c->ldx * 2 + 2 * (size_t)c->maxw * 2 + (size_t)c->ldw * 2;
+  if (c->head) b += (size_t)c->D * 2 + 8;
   return b;
 }
 
@@ -792,6 +804,20 @@ void forward_chunk(ff_ctx* c, const double* pos, int a0, int a1, float* E_atom, 
       EpiParams el{};
       el.alpha = (float)(1.0 / sqrt((double)fan));
       el.pre = c->zlat[L][k]; el.ldp = wout;
+      if (lastk && c->head && L == c->NL) {
+        // last latent layer + edge-energy head in one epilogue: per-edge energies, the
+        // envelope-gradient seed and dE/dz of this layer; x^N itself is never stored
+        el.pre = nullptr;
+        el.res = c->X[L - 1]; el.ldr = c->ldx;
+        el.f = fptr; el.ldf = FF_EF_STRIDE;
+        el.beta = (float)(1.0 / sqrt(2.0));
+        el.wv = c->w_eff;
+        el.outb = c->GZL; el.ldob = c->D;
+        el.eout = c->E_edge; el.gfo = c->gfL;
+        mlp_gemm(c, EPI_HEAD, Ec, wout, fan, A32, Ab, lda, c->Wlat[L][k], c->WlatT_b[L][k], el,
+                 s);
+        break;
+      }
       if (lastk) {
         el.out = c->X[L]; el.ldo = c->ldx;
         el.res = c->X[L - 1]; el.ldr = c->ldx;
@@ -810,7 +836,8 @@ void forward_chunk(ff_ctx* c, const double* pos, int a0, int a1, float* E_atom, 
       fan = lda = wout;
     }
   }
-  launch_energy(na, rp, e0, c->X[c->NL], c->ldx, c->D, c->w_eff, E_atom + a0, s);
+  if (c->head) launch_energy_sum(na, rp, e0, c->E_edge, E_atom + a0, s);
+  else launch_energy(na, rp, e0, c->X[c->NL], c->ldx, c->D, c->w_eff, E_atom + a0, s);
 }
 
 void backward_chunk(ff_ctx* c, int a0, int a1, const double* seed, cudaStream_t s) {
@@ -821,7 +848,10 @@ void backward_chunk(ff_ctx* c, int a0, int a1, const double* seed, cudaStream_t 
   if (Ec <= 0) return;
   const int* rp = c->row_ptr + a0;
   const int na = a1 - a0;
-  cudaMemsetAsync(c->gf, 0, (size_t)Ec * sizeof(float), s);
+  if (c->head)   // the forward readout seeded the envelope gradient of the last layer
+    cudaMemcpyAsync(c->gf, c->gfL, (size_t)Ec * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  else
+    cudaMemsetAsync(c->gf, 0, (size_t)Ec * sizeof(float), s);
   const float* gx = c->w_eff;
   int ldgx = 0;
   int cur = 0, gvb = 0;
@@ -829,26 +859,30 @@ void backward_chunk(ff_ctx* c, int a0, int a1, const double* seed, cudaStream_t 
   const float r2 = (float)(1.0 / sqrt(2.0));
   for (int L = c->NL; L >= 1; --L) {
     const int kl = c->nlat - 1;
-    launch_rowred_bwd(Ec, hp.latent[kl], gx, ldgx, c->zlat[L][kl], hp.latent[kl], c->ef, r2,
-                      tc ? nullptr : c->GZ[0], hp.latent[kl], tc ? c->GZb[0] : nullptr, c->gf,
-                      s);
+    const bool fused = c->head && L == c->NL;   // dE/dz of this layer came from the readout
+    if (!fused)
+      launch_rowred_bwd(Ec, hp.latent[kl], gx, ldgx, c->zlat[L][kl], hp.latent[kl], c->ef, r2,
+                        tc ? nullptr : c->GZ[0], hp.latent[kl], tc ? c->GZb[0] : nullptr,
+                        c->gf, s);
     int gzb = 0;
+    const __nv_bfloat16* gzA = fused ? c->GZL : c->GZb[0];
     for (int k = kl; k >= 1; --k) {
       EpiParams ep{};
       ep.alpha = (float)(1.0 / sqrt((double)hp.latent[k - 1]));
       if (tc) { ep.outb = c->GZb[gzb ^ 1]; ep.ldob = hp.latent[k - 1]; }
       else { ep.out = c->GZ[gzb ^ 1]; ep.ldo = hp.latent[k - 1]; }
       ep.z = c->zlat[L][k - 1]; ep.ldz = hp.latent[k - 1];
-      mlp_gemm(c, EPI_DSILU, Ec, hp.latent[k - 1], hp.latent[k], c->GZ[gzb], c->GZb[gzb],
+      mlp_gemm(c, EPI_DSILU, Ec, hp.latent[k - 1], hp.latent[k], c->GZ[gzb], gzA,
                hp.latent[k], c->WlatT[L][k], c->Wlat_b[L][k], ep, s);
       gzb ^= 1;
+      gzA = c->GZb[gzb];
     }
     {
       EpiParams ep{};
       ep.alpha = (float)(1.0 / sqrt((double)c->ldx));
       ep.out = c->GX[cur]; ep.ldo = c->ldx;
       ep.res = gx; ep.ldr = ldgx; ep.beta = r2; ep.split = c->D;
-      mlp_gemm(c, EPI_RES, Ec, c->ldx, hp.latent[0], c->GZ[gzb], c->GZb[gzb], hp.latent[0],
+      mlp_gemm(c, EPI_RES, Ec, c->ldx, hp.latent[0], c->GZ[gzb], gzA, hp.latent[0],
                c->WlatT[L][0], c->Wlat_b[L][0], ep, s);
     }
     const int last = L == c->NL ? 1 : 0;

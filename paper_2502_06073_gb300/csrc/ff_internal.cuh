@@ -54,7 +54,11 @@ enum EpiMode {
   EPI_SILU_RES = 3,  // pre = alpha acc; out = beta (res[row, col] + f[row] silu(pre))
   EPI_DSILU = 4,     // out = alpha acc silu'(z[row, col])
   EPI_RES = 5,       // out = alpha acc + (col < split ? beta res[row * ldr + col] : 0)
-  EPI_ACC = 6        // out += alpha acc
+  EPI_ACC = 6,       // out += alpha acc
+  // last latent layer with the edge-energy head (tensor-core GEMM, whole rows per CTA):
+  // z = alpha acc, s = silu(z), x = beta (res + f s);  eout[row] = sum_col wv x,
+  // gfo[row] = beta sum_col wv s,  outb = beta f silu'(z) wv  (dE_ij/dz, bf16)
+  EPI_HEAD = 7
 };
 
 struct EpiParams {
@@ -66,6 +70,8 @@ struct EpiParams {
   const float* z; int ldz;       // pre-activation source (DSILU)
   int split;
   __nv_bfloat16* outb; int ldob;  // optional bf16 copy of out (tensor-core GEMM only)
+  const float* wv;                // EPI_HEAD: readout vector [N]
+  float* eout; float* gfo;        // EPI_HEAD: per-row energy and envelope gradient
 };
 
 void launch_gemm_f32(int mode, int M, int N, int K, const float* A, int lda, const float* B,
@@ -135,6 +141,8 @@ void launch_env_tp_bwd(int lmax, int in_kind, int out_kind, int C, int n_atoms,
                        float inv_sqrt_nu, cudaStream_t s);
 void launch_energy(int n_atoms, const int* row_ptr, int e0, const float* X, int ldx, int D,
                    const float* w_eff, float* E_atom, cudaStream_t s);
+void launch_energy_sum(int n_atoms, const int* row_ptr, int e0, const float* E_edge,
+                       float* E_atom, cudaStream_t s);
 void launch_rowred_bwd(long long E, int N, const float* gx, int ldgx, const float* z, int ldz,
                        const float* ef, float alpha, float* gz, int ldgz, __nv_bfloat16* gzb,
                        float* gf, cudaStream_t s);

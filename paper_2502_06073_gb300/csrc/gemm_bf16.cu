@@ -137,7 +137,8 @@ __device__ __forceinline__ float dsilu_f(float z) {
 // rows r0 + 4i + (l >> 3), i = 0..7.  All loads of the batch are issued before any store.
 template <int MODE>
 __device__ __forceinline__ void epi_batch(const EpiParams& ep, const float4 (&acc)[8],
-                                          const int (&row)[8], int col, bool colok) {
+                                          const int (&row)[8], int col, bool colok,
+                                          float (&racc)[8][2]) {
   float4 aux[8];
   float fr[8];
 #pragma unroll
@@ -147,41 +148,74 @@ __device__ __forceinline__ void epi_batch(const EpiParams& ep, const float4 (&ac
     fr[i] = 0.f;
     if (!ok) continue;
     const size_t r = (size_t)row[i];
-    if (MODE == EPI_SILU_RES || (MODE == EPI_RES && col < ep.split))
+    if (MODE == EPI_SILU_RES || MODE == EPI_HEAD || (MODE == EPI_RES && col < ep.split))
       aux[i] = *reinterpret_cast<const float4*>(ep.res + r * ep.ldr + col);
     if (MODE == EPI_DSILU) aux[i] = *reinterpret_cast<const float4*>(ep.z + r * ep.ldz + col);
     if (MODE == EPI_ACC) aux[i] = *reinterpret_cast<const float4*>(ep.out + r * ep.ldo + col);
-    if (MODE == EPI_SILU_F || MODE == EPI_SILU_RES) fr[i] = ep.f[r * ep.ldf];
+    if (MODE == EPI_SILU_F || MODE == EPI_SILU_RES || MODE == EPI_HEAD)
+      fr[i] = ep.f[r * ep.ldf];
   }
+  if constexpr (MODE == EPI_HEAD) {
+    // readout: partial dot products of this lane's 4 columns, summed over rows later
+    if (!colok) return;
+    const float4 w4 = *reinterpret_cast<const float4*>(ep.wv + col);
+    const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    if (!colok || row[i] < 0) continue;
-    const size_t r = (size_t)row[i];
-    float v[4] = {ep.alpha * acc[i].x, ep.alpha * acc[i].y, ep.alpha * acc[i].z,
-                  ep.alpha * acc[i].w};
-    const float a4[4] = {aux[i].x, aux[i].y, aux[i].z, aux[i].w};
-    float o[4];
+    for (int i = 0; i < 8; ++i) {
+      if (row[i] < 0) continue;
+      const size_t r = (size_t)row[i];
+      const float a4[4] = {aux[i].x, aux[i].y, aux[i].z, aux[i].w};
+      const float v[4] = {ep.alpha * acc[i].x, ep.alpha * acc[i].y, ep.alpha * acc[i].z,
+                          ep.alpha * acc[i].w};
+      float g[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (MODE == EPI_STORE) o[j] = v[j];
-      else if (MODE == EPI_SILU) o[j] = silu_f(v[j]);
-      else if (MODE == EPI_SILU_F) o[j] = fr[i] * silu_f(v[j]);
-      else if (MODE == EPI_SILU_RES) o[j] = ep.beta * (a4[j] + fr[i] * silu_f(v[j]));
-      else if (MODE == EPI_DSILU) o[j] = v[j] * dsilu_f(a4[j]);
-      else if (MODE == EPI_RES) o[j] = v[j] + (col < ep.split ? ep.beta * a4[j] : 0.f);
-      else o[j] = a4[j] + v[j];
-    }
-    if (MODE == EPI_SILU || MODE == EPI_SILU_F || MODE == EPI_SILU_RES)
-      *reinterpret_cast<float4*>(ep.pre + r * ep.ldp + col) = make_float4(v[0], v[1], v[2], v[3]);
-    if (ep.out)
-      *reinterpret_cast<float4*>(ep.out + r * ep.ldo + col) = make_float4(o[0], o[1], o[2], o[3]);
-    if (ep.outb) {
-      __nv_bfloat162 lo = __floats2bfloat162_rn(o[0], o[1]);
-      __nv_bfloat162 hi = __floats2bfloat162_rn(o[2], o[3]);
+      for (int j = 0; j < 4; ++j) {
+        const float sg = 1.f / (1.f + expf(-v[j]));
+        const float sv = v[j] * sg;
+        racc[i][0] += wv[j] * (ep.beta * (a4[j] + fr[i] * sv));
+        racc[i][1] += wv[j] * sv;
+        g[j] = ep.beta * fr[i] * (sg * (1.f + v[j] * (1.f - sg))) * wv[j];
+      }
+      __nv_bfloat162 lo = __floats2bfloat162_rn(g[0], g[1]);
+      __nv_bfloat162 hi = __floats2bfloat162_rn(g[2], g[3]);
       uint2 pk;
       pk.x = *reinterpret_cast<uint32_t*>(&lo);
       pk.y = *reinterpret_cast<uint32_t*>(&hi);
       *reinterpret_cast<uint2*>(ep.outb + r * ep.ldob + col) = pk;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (!colok || row[i] < 0) continue;
+      const size_t r = (size_t)row[i];
+      float v[4] = {ep.alpha * acc[i].x, ep.alpha * acc[i].y, ep.alpha * acc[i].z,
+                    ep.alpha * acc[i].w};
+      const float a4[4] = {aux[i].x, aux[i].y, aux[i].z, aux[i].w};
+      float o[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (MODE == EPI_STORE) o[j] = v[j];
+        else if (MODE == EPI_SILU) o[j] = silu_f(v[j]);
+        else if (MODE == EPI_SILU_F) o[j] = fr[i] * silu_f(v[j]);
+        else if (MODE == EPI_SILU_RES) o[j] = ep.beta * (a4[j] + fr[i] * silu_f(v[j]));
+        else if (MODE == EPI_DSILU) o[j] = v[j] * dsilu_f(a4[j]);
+        else if (MODE == EPI_RES) o[j] = v[j] + (col < ep.split ? ep.beta * a4[j] : 0.f);
+        else o[j] = a4[j] + v[j];
+      }
+      if (MODE == EPI_SILU || MODE == EPI_SILU_F || MODE == EPI_SILU_RES)
+        *reinterpret_cast<float4*>(ep.pre + r * ep.ldp + col) =
+            make_float4(v[0], v[1], v[2], v[3]);
+      if (ep.out)
+        *reinterpret_cast<float4*>(ep.out + r * ep.ldo + col) =
+            make_float4(o[0], o[1], o[2], o[3]);
+      if (ep.outb) {
+        __nv_bfloat162 lo = __floats2bfloat162_rn(o[0], o[1]);
+        __nv_bfloat162 hi = __floats2bfloat162_rn(o[2], o[3]);
+        uint2 pk;
+        pk.x = *reinterpret_cast<uint32_t*>(&lo);
+        pk.y = *reinterpret_cast<uint32_t*>(&hi);
+        *reinterpret_cast<uint2*>(ep.outb + r * ep.ldob + col) = pk;
+      }
     }
   }
 }
@@ -279,6 +313,9 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   const int quad = warp & 3, half = warp >> 2;
   float* tile = reinterpret_cast<float*>(smem) + warp * 32 * 32;
   const int nchunks = (nbw + 31) / 32;
+  float racc[8][2];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) racc[i][0] = racc[i][1] = 0.f;
   for (int ci = half; ci < nchunks; ci += 2) {
     const int c0 = ci * 32;
     float v[32];
@@ -300,8 +337,46 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       const int row = m0 + quad * 32 + rl;
       rows[i] = (ok && row < M) ? row : -1;
     }
-    epi_batch<MODE>(ep, acc, rows, col, cl < nbw && col < N);
+    epi_batch<MODE>(ep, acc, rows, col, cl < nbw && col < N, racc);
     __syncwarp();
+  }
+  if (MODE == EPI_HEAD) {
+    // row sums: the 8 lanes sharing a row (lane & 7) by shuffles, then the two warps of
+    // a row quadrant (column parities) through shared memory after the tiles
+    float* red = reinterpret_cast<float*>(smem) + 8 * 32 * 32;
+    const int rsub = lane >> 3;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        float t = racc[i][q];
+        t += __shfl_xor_sync(0xffffffffu, t, 1);
+        t += __shfl_xor_sync(0xffffffffu, t, 2);
+        t += __shfl_xor_sync(0xffffffffu, t, 4);
+        racc[i][q] = t;
+      }
+    if (half == 1 && (lane & 7) == 0) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int rl = quad * 32 + 4 * i + rsub;
+        red[2 * rl] = racc[i][0];
+        red[2 * rl + 1] = racc[i][1];
+      }
+    }
+    __syncthreads();
+    if (half == 0 && (lane & 7) == 0) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int rl = quad * 32 + 4 * i + rsub;
+        const int row = m0 + rl;
+        if (ok && row < M) {
+          const float e_ = racc[i][0] + red[2 * rl];
+          const float g_ = racc[i][1] + red[2 * rl + 1];
+          ep.eout[row] = e_;
+          ep.gfo[row] = ep.beta * g_;
+        }
+      }
+    }
   }
   if (!ok && threadIdx.x == 0) s_fail = 1;
   fence_before();
@@ -374,6 +449,10 @@ bool launch_gemm_bf16(int mode, int M, int N, int K, const __nv_bfloat16* A, int
   if (M <= 0) return true;
   if (N % 16 != 0 || K % 8 != 0 || lda % 8 != 0 || ldb % 8 != 0) return false;
   if (slice != 128 && slice != 256) slice = 256;
+  if (mode == EPI_HEAD) {   // row sums need whole rows in one CTA
+    if (N > 256) return false;
+    slice = 256;
+  }
   for (int n0 = 0; n0 < N; n0 += slice) {
     const int nbw = N - n0 < slice ? N - n0 : slice;
     CUtensorMap ta, tb;
@@ -390,6 +469,7 @@ bool launch_gemm_bf16(int mode, int M, int N, int K, const __nv_bfloat16* A, int
       case EPI_DSILU: ok = launch_mode<EPI_DSILU>(ta, tb, M, N, K, n0, nbw, stages, smem, ep, err, s); break;
       case EPI_RES: ok = launch_mode<EPI_RES>(ta, tb, M, N, K, n0, nbw, stages, smem, ep, err, s); break;
       case EPI_ACC: ok = launch_mode<EPI_ACC>(ta, tb, M, N, K, n0, nbw, stages, smem, ep, err, s); break;
+      case EPI_HEAD: ok = launch_mode<EPI_HEAD>(ta, tb, M, N, K, n0, nbw, stages, smem, ep, err, s); break;
       default: return false;
     }
     if (!ok) return false;

@@ -119,6 +119,20 @@ __global__ void k_energy(int n_atoms, const int* __restrict__ row_ptr, int e0,
   if (lane == 0) E_atom[a] = acc;
 }
 
+// E_i = sum_{e in seg(i)} E_e for per-edge energies from the fused readout; one warp per
+// atom, lanes stride the segment, fixed-order warp sum.
+__global__ void k_energy_sum(int n_atoms, const int* __restrict__ row_ptr, int e0,
+                             const float* __restrict__ E_edge, float* __restrict__ E_atom) {
+  const int a = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (a >= n_atoms) return;
+  const int eb = row_ptr[a] - e0, ee = row_ptr[a + 1] - e0;
+  float acc = 0.f;
+  for (int e = eb + lane; e < ee; e += 32) acc += E_edge[e];
+  acc = warp_sum(acc);
+  if (lane == 0) E_atom[a] = acc;
+}
+
 // Adjoint of out = f * silu(z) (scaled by alpha):  gz = alpha f silu'(z) gx,
 // gf += alpha sum_d gx silu(z).  One warp per edge; lane l owns the float4 column groups
 // l, l + 32, ... (N % 4 == 0, N <= 512); all loads of the row are issued first.
@@ -449,6 +463,14 @@ void launch_energy(int n_atoms, const int* row_ptr, int e0, const float* X, int 
   ProfScope ps_(PC_ENERGY, s);
   if (n_atoms <= 0) return;
   k_energy<<<ff_cdiv(n_atoms, 8), 256, 0, s>>>(n_atoms, row_ptr, e0, X, ldx, D, w_eff, E_atom);
+  ff_count_launch(1);
+}
+
+void launch_energy_sum(int n_atoms, const int* row_ptr, int e0, const float* E_edge,
+                       float* E_atom, cudaStream_t s) {
+  ProfScope ps_(PC_ENERGY, s);
+  if (n_atoms <= 0) return;
+  k_energy_sum<<<ff_cdiv(n_atoms, 8), 256, 0, s>>>(n_atoms, row_ptr, e0, E_edge, E_atom);
   ff_count_launch(1);
 }
 
