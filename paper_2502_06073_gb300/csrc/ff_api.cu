@@ -146,6 +146,8 @@ struct ff_ctx {
   __nv_bfloat16* wbuf_b = nullptr;
   __nv_bfloat16* W2b_b[4] = {nullptr}; __nv_bfloat16* W2bT_b[4] = {nullptr};
   __nv_bfloat16* Wenv_b[FF_MAX_LAYERS + 1] = {nullptr};
+  __nv_bfloat16* Bcat_b[FF_MAX_LAYERS + 1] = {nullptr};
+  int bcat_k1p = 0, bcat_ld = 0;
   __nv_bfloat16* WenvT_b[FF_MAX_LAYERS + 1] = {nullptr};
   __nv_bfloat16* Wlat_b[FF_MAX_LAYERS + 1][4] = {{nullptr}};
   __nv_bfloat16* WlatT_b[FF_MAX_LAYERS + 1][4] = {{nullptr}};
@@ -450,6 +452,28 @@ int upload_weights(ff_ctx* c) {
       putb(&c->Wlat_b[L][k], tl, false);
       putb(&c->WlatT_b[L][k], tl, true);
     }
+  }
+  // adjoint of the latent input and the env weights in one GEMM over [GZ | GW]: per layer
+  // Bcat [D][K1p + K2p] = [Wlat[:D] | 0 | (a_env / a_lat) Wenv | 0] with a_lat = ldx^-1/2,
+  // a_env = D^-1/2 (the two fan-in scales), K parts padded to multiples of 64
+  c->bcat_k1p = (c->hp.latent[0] + 63) / 64 * 64;
+  c->bcat_ld = c->bcat_k1p + (c->ldw + 63) / 64 * 64;
+  for (int L = 1; L <= c->NL; ++L) {
+    const Tensor* tl = find_tensor(c, "Wlat." + std::to_string(L) + ".0");   // [ldx][latent0]
+    const Tensor* te = find_tensor(c, "Wenv." + std::to_string(L));          // [D][ldw]
+    const double ratio = sqrt((double)c->ldx) / sqrt((double)c->D);
+    const size_t base = hb.size();
+    const size_t n = (size_t)c->D * c->bcat_ld;
+    hb.resize(base + ((n + 127) / 128) * 128, __float2bfloat16_rn(0.f));
+    for (int r = 0; r < c->D; ++r) {
+      __nv_bfloat16* row = hb.data() + base + (size_t)r * c->bcat_ld;
+      for (int q = 0; q < tl->cols; ++q)
+        row[q] = __float2bfloat16_rn((float)c->params[tl->off + (size_t)r * tl->cols + q]);
+      for (int q = 0; q < te->cols; ++q)
+        row[c->bcat_k1p + q] =
+            __float2bfloat16_rn((float)(ratio * c->params[te->off + (size_t)r * te->cols + q]));
+    }
+    fixb.push_back({&c->Bcat_b[L], base});
   }
   FF_TRY(dalloc(c, &c->wbuf_b, hb.size()));
   FF_CK(c, cudaMemcpy(c->wbuf_b, hb.data(), hb.size() * sizeof(__nv_bfloat16),
@@ -792,9 +816,9 @@ void forward_chunk(ff_ctx* c, const double* pos, int a0, int a1, float* E_atom, 
              c->WenvT_b[L], ep, s);
     const int last = L == c->NL ? 1 : 0;
     launch_env_tp_fwd(c->lmax, c->layer_ink[L], c->layer_outk[L], c->C, na, rp, e0, c->ef,
-                      c->Wv[L], c->ldw, L >= 2 ? c->V[L - 1] : nullptr, last ? nullptr : c->theta[L],
-                      c->X[L - 1], tc ? c->Xb[L - 1] : nullptr, c->ldx, c->D,
-                      last ? nullptr : c->V[L], c->Gam[L], inv_sqrt_nu, s);
+                      c->Wv[L], c->ldw, L >= 2 ? c->V[L - 1] : nullptr,
+                      last ? nullptr : c->theta[L], c->X[L - 1], tc ? c->Xb[L - 1] : nullptr,
+                      c->ldx, c->D, last ? nullptr : c->V[L], c->Gam[L], inv_sqrt_nu, s);
     const float* A32 = c->X[L - 1];
     const __nv_bfloat16* Ab = c->Xb[L - 1];
     int fan = c->ldx, lda = c->ldx;
@@ -877,7 +901,15 @@ void backward_chunk(ff_ctx* c, int a0, int a1, const double* seed, cudaStream_t 
       gzb ^= 1;
       gzA = c->GZb[gzb];
     }
-    {
+    if (tc) {
+      // gradients of the tensor-product scalars only (GX columns D..): the TP adjoint needs
+      // them; the first D columns come after it, together with the env-weight term
+      EpiParams ep{};
+      ep.alpha = (float)(1.0 / sqrt((double)c->ldx));
+      ep.out = c->GX[cur] + c->D; ep.ldo = c->ldx;
+      mlp_gemm(c, EPI_STORE, Ec, c->ldx - c->D, hp.latent[0], nullptr, gzA, hp.latent[0],
+               nullptr, c->Wlat_b[L][0] + (size_t)c->D * hp.latent[0], ep, s);
+    } else {
       EpiParams ep{};
       ep.alpha = (float)(1.0 / sqrt((double)c->ldx));
       ep.out = c->GX[cur]; ep.ldo = c->ldx;
@@ -887,13 +919,25 @@ void backward_chunk(ff_ctx* c, int a0, int a1, const double* seed, cudaStream_t 
     }
     const int last = L == c->NL ? 1 : 0;
     launch_env_tp_bwd(c->lmax, c->layer_ink[L], c->layer_outk[L], c->C, na, rp, e0, c->ef,
-                      c->Wv[L], c->ldw, L >= 2 ? c->V[L - 1] : nullptr, last ? nullptr : c->theta[L],
-                      c->GX[cur], c->ldx, c->D, last ? nullptr : c->gV[gvb],
+                      c->Wv[L], c->ldw, L >= 2 ? c->V[L - 1] : nullptr,
+                      last ? nullptr : c->theta[L], c->GX[cur], c->ldx, c->D,
+                      last ? nullptr : c->gV[gvb],
                       L >= 2 ? c->gV[gvb ^ 1] : nullptr, c->GW, tc ? c->GWb : nullptr,
                       c->gY + (size_t)c->NL * c->cgroups * 9,
                       c->gY + (size_t)(L - 1) * c->cgroups * 9, 9 * gy_slices(c), c->Gam[L],
                       inv_sqrt_nu, s);
-    {
+    if (tc) {
+      // dE/dx^(L-1) = a_lat GZ Wlat[:D]^T + a_env GW Wenv^T + gx / sqrt(2): one GEMM over the
+      // concatenated K of [GZ | GW] (the env part of Bcat carries a_env / a_lat)
+      EpiParams ep{};
+      ep.alpha = (float)(1.0 / sqrt((double)c->ldx));
+      ep.out = c->GX[cur]; ep.ldo = c->ldx;
+      ep.res = gx; ep.ldr = ldgx; ep.beta = r2; ep.split = c->D;
+      if (!launch_gemm_bf16(EPI_RES, (int)Ec, c->D, hp.latent[0], gzA, hp.latent[0],
+                            c->Bcat_b[L], c->bcat_ld, ep, c->flags, s, c->tune_slice,
+                            c->tune_stages, c->GWb, c->ldw, c->ldw))
+        c->gemm_fail = true;
+    } else {
       EpiParams ep{};
       ep.alpha = (float)(1.0 / sqrt((double)c->D));
       ep.out = c->GX[cur]; ep.ldo = c->ldx;

@@ -82,10 +82,14 @@ void launch_gemm_f32(int mode, int M, int N, int K, const float* A, int lda, con
 // the launch could not be set up; a device-side timeout sets bit 64 of *err.
 bool gemm_bf16_available();
 // slice: output columns per CTA (128 or 256); stages_req: 2..4 pipeline stages, or 0
-// for the default (2 for 256-wide slices, 3 otherwise).
+// for the default (2 for 256-wide slices, 3 otherwise).  With A2 (bf16 [M][K2], row stride
+// lda2) the product is [A | A2] Bt^T over a concatenated K: A's K columns rounded up to a
+// multiple of 64 (zero-filled), then A2's; Bt then has ldb >= that padded total and zeros
+// in the padding.
 bool launch_gemm_bf16(int mode, int M, int N, int K, const __nv_bfloat16* A, int lda,
                       const __nv_bfloat16* Bt, int ldb, const EpiParams& ep, int* err,
-                      cudaStream_t s, int slice = 256, int stages_req = 0);
+                      cudaStream_t s, int slice = 256, int stages_req = 0,
+                      const __nv_bfloat16* A2 = nullptr, int K2 = 0, int lda2 = 0);
 
 // ----------------------------------------------------------------------------- neighbours
 struct NbrGrid {

@@ -222,8 +222,9 @@ __device__ __forceinline__ void epi_batch(const EpiParams& ep, const float4 (&ac
 
 template <int MODE>
 __global__ void __launch_bounds__(256, 2)
-k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M,
-          int N, int K, int n0, int nbw, int stages, EpiParams ep, int* __restrict__ err) {
+k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
+          const __grid_constant__ CUtensorMap tmB, int M, int N, int K, int k1c, int n0, int nbw,
+          int stages, EpiParams ep, int* __restrict__ err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t a_bytes = TM * TK * 2;
@@ -273,7 +274,9 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       }
       uint8_t* sa = smem + (size_t)s * st_bytes;
       mbar_expect_tx(smem_u32(&full[s]), st_bytes);
-      tma_load_2d(smem_u32(sa), &tmA, kc * TK, m0, smem_u32(&full[s]));
+      // K-chunks beyond k1c come from the second operand (A2 columns from 0)
+      if (kc < k1c) tma_load_2d(smem_u32(sa), &tmA, kc * TK, m0, smem_u32(&full[s]));
+      else tma_load_2d(smem_u32(sa), &tmA2, (kc - k1c) * TK, m0, smem_u32(&full[s]));
       tma_load_2d(smem_u32(sa + a_bytes), &tmB, kc * TK, n0, smem_u32(&full[s]));
       ++issued;
     }
@@ -424,9 +427,9 @@ bool make_map(CUtensorMap* m, const void* base, long long rows, int cols, int ld
 }
 
 template <int MODE>
-bool launch_mode(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K, int n0,
-                 int nbw, int stages, size_t smem, const EpiParams& ep, int* err,
-                 cudaStream_t s) {
+bool launch_mode(const CUtensorMap& ta, const CUtensorMap& ta2, const CUtensorMap& tb, int M,
+                 int N, int K, int k1c, int n0, int nbw, int stages, size_t smem,
+                 const EpiParams& ep, int* err, cudaStream_t s) {
   static bool attr_set = false;
   if (!attr_set) {
     if (cudaFuncSetAttribute(k_gemm_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -434,9 +437,18 @@ bool launch_mode(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int
       return false;
     attr_set = true;
   }
-  k_gemm_tc<MODE><<<ff_cdiv(M, TM), 256, smem, s>>>(ta, tb, M, N, K, n0, nbw, stages, ep, err);
+  k_gemm_tc<MODE><<<ff_cdiv(M, TM), 256, smem, s>>>(ta, ta2, tb, M, N, K, k1c, n0, nbw, stages,
+                                                     ep, err);
   return true;
 }
+
+using LaunchFn = bool (*)(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, int, int,
+                          int, int, int, int, int, size_t, const EpiParams&, int*, cudaStream_t);
+// indexed by epilogue mode
+const LaunchFn kLaunch[] = {launch_mode<EPI_STORE>, launch_mode<EPI_SILU>,
+                            launch_mode<EPI_SILU_F>, launch_mode<EPI_SILU_RES>,
+                            launch_mode<EPI_DSILU>, launch_mode<EPI_RES>,
+                            launch_mode<EPI_ACC>, launch_mode<EPI_HEAD>};
 
 }  // namespace
 
@@ -444,10 +456,17 @@ bool gemm_bf16_available() { return encoder() != nullptr; }
 
 bool launch_gemm_bf16(int mode, int M, int N, int K, const __nv_bfloat16* A, int lda,
                       const __nv_bfloat16* Bt, int ldb, const EpiParams& ep, int* err,
-                      cudaStream_t s, int slice, int stages_req) {
+                      cudaStream_t s, int slice, int stages_req, const __nv_bfloat16* A2,
+                      int K2, int lda2) {
   ProfScope ps_(PC_GEMM_BF16, s);
   if (M <= 0) return true;
   if (N % 16 != 0 || K % 8 != 0 || lda % 8 != 0 || ldb % 8 != 0) return false;
+  if (mode < EPI_STORE || mode > EPI_HEAD) return false;
+  if (A2 && (K2 <= 0 || K2 % 8 != 0 || lda2 % 8 != 0)) return false;
+  // concatenated K: A's columns padded to a whole chunk, then A2's; Bt holds both parts
+  const int k1c = A2 ? (K + TK - 1) / TK : (K + TK - 1) / TK + 1;
+  const int Ktot = A2 ? k1c * TK + K2 : K;
+  if (A2 && ldb < ((K2 + TK - 1) / TK + k1c) * TK) return false;
   if (slice != 128 && slice != 256) slice = 256;
   if (mode == EPI_HEAD) {   // row sums need whole rows in one CTA
     if (N > 256) return false;
@@ -455,24 +474,18 @@ bool launch_gemm_bf16(int mode, int M, int N, int K, const __nv_bfloat16* A, int
   }
   for (int n0 = 0; n0 < N; n0 += slice) {
     const int nbw = N - n0 < slice ? N - n0 : slice;
-    CUtensorMap ta, tb;
-    if (!make_map(&ta, A, M, K, lda, TM) || !make_map(&tb, Bt, N, K, ldb, nbw)) return false;
+    CUtensorMap ta, ta2, tb;
+    if (!make_map(&ta, A, M, K, lda, TM) || !make_map(&tb, Bt, N, Ktot, ldb, nbw)) return false;
+    if (A2) {
+      if (!make_map(&ta2, A2, M, K2, lda2, TM)) return false;
+    } else {
+      ta2 = ta;
+    }
     // default: <= 98 KB of stages, two CTAs per SM; the autotuner may ask for 2..4
     const int stages = (stages_req >= 2 && stages_req <= 4) ? stages_req : (nbw > 128 ? 2 : 3);
     const size_t smem = (size_t)stages * (TM * TK * 2 + (size_t)nbw * TK * 2) + 1024 + 256;
-    bool ok = false;
-    switch (mode) {
-      case EPI_STORE: ok = launch_mode<EPI_STORE>(ta, tb, M, N, K, n0, nbw, stages, smem, ep, err, s); break;
-      case EPI_SILU: ok = launch_mode<EPI_SILU>(ta, tb, M, N, K, n0, nbw, stages, smem, ep, err, s); break;
-      case EPI_SILU_F: ok = launch_mode<EPI_SILU_F>(ta, tb, M, N, K, n0, nbw, stages, smem, ep, err, s); break;
-      case EPI_SILU_RES: ok = launch_mode<EPI_SILU_RES>(ta, tb, M, N, K, n0, nbw, stages, smem, ep, err, s); break;
-      case EPI_DSILU: ok = launch_mode<EPI_DSILU>(ta, tb, M, N, K, n0, nbw, stages, smem, ep, err, s); break;
-      case EPI_RES: ok = launch_mode<EPI_RES>(ta, tb, M, N, K, n0, nbw, stages, smem, ep, err, s); break;
-      case EPI_ACC: ok = launch_mode<EPI_ACC>(ta, tb, M, N, K, n0, nbw, stages, smem, ep, err, s); break;
-      case EPI_HEAD: ok = launch_mode<EPI_HEAD>(ta, tb, M, N, K, n0, nbw, stages, smem, ep, err, s); break;
-      default: return false;
-    }
-    if (!ok) return false;
+    if (!kLaunch[mode](ta, ta2, tb, M, N, Ktot, k1c, n0, nbw, stages, smem, ep, err, s))
+      return false;
     ff_count_launch(1);
   }
   return true;
