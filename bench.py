@@ -85,33 +85,50 @@ def gemm_flops_per_edge(hp):
 def gemm_bytes_per_edge(hp, precision):
     """Compulsory HBM bytes per edge of all MLP GEMM launches of one E+F evaluation: each
     operand read once, each epilogue input read once, each output written once, in the
-    storage types of the path (FP32 everywhere for precision 0; BF16 GEMM operands plus
-    the FP32 pre-activations, residual stream and gradients for precision 1)."""
+    storage types of the path.  Precision 0: FP32 everywhere; the adjoint's latent-input
+    and env-weight products are two GEMMs.  Precision 1: BF16 GEMM operands and stored
+    pre-activations, FP32 residual stream and gradients; the last latent GEMM carries the
+    edge-energy readout (per-edge energy, envelope seed and bf16 dE/dz out, no latent
+    stored) when D <= 256; the adjoint computes the scalar gradients first and then one
+    GEMM over the concatenated [dE/dz | dE/dw]."""
     tb, lat = hp["two_body"], hp["latent"]
     D = tb[-1]
     C, lmax, NL = hp["channels"], hp["lmax"], hp["n_layers"]
     ldw = (lmax + 1) * C
     ldx = D + (lmax + 1) * C
-    sa = 2 if precision == 1 else 4          # bytes of a GEMM operand element
-    cp = 2 if precision == 1 else 0          # extra bf16 copy of the residual stream
+    tc = precision == 1
+    head = tc and D <= 256
+    sa = 2 if tc else 4                      # bytes of a GEMM operand element
+    sz = 2 if tc else 4                      # bytes of a stored pre-activation
+    cp = 2 if tc else 0                      # extra bf16 copy of the residual stream
     b = 0
     for k in range(1, len(tb)):              # two-body hidden layers
-        b += tb[k - 1] * sa + tb[k] * 4
+        b += tb[k - 1] * sa + tb[k] * sz
         b += (tb[k] * 4 + tb[k] * cp + 4) if k == len(tb) - 1 else tb[k] * sa
-    for _ in range(NL):
+    for L in range(1, NL + 1):
         b += D * sa + ldw * 4                # environment projection
         fan = ldx
         for k, w in enumerate(lat):
-            b += fan * sa + w * 4
-            b += (2 * D * 4 + D * cp + 4) if k == len(lat) - 1 else w * sa
+            b += fan * sa
+            if k < len(lat) - 1:
+                b += w * sz + w * sa
+            elif head and L == NL:
+                b += D * 4 + 4 + D * 2 + 4 + 4   # residual, f; dE/dz, E_e, envelope seed
+            else:
+                b += w * sz + 2 * D * 4 + D * cp + 4
             fan = w
     for L in range(NL, 0, -1):               # adjoint
         for k in range(len(lat) - 1, 0, -1):
-            b += lat[k] * sa + lat[k - 1] * 4 + lat[k - 1] * sa
-        b += lat[0] * sa + (0 if L == NL else D * 4) + ldx * 4
-        b += ldw * sa + 2 * D * 4
+            b += lat[k] * sa + lat[k - 1] * sz + lat[k - 1] * sa
+        res = 0 if L == NL else D * 4
+        if tc:
+            b += lat[0] * sa + (ldx - D) * 4                 # scalar gradients
+            b += lat[0] * sa + ldw * sa + res + D * 4        # [dE/dz | dE/dw] product
+        else:
+            b += lat[0] * sa + res + ldx * 4
+            b += ldw * sa + 2 * D * 4
     for k in range(len(tb) - 1, 0, -1):
-        b += tb[k] * sa + tb[k - 1] * 4 + tb[k - 1] * (sa if k > 1 else 4)
+        b += tb[k] * sa + tb[k - 1] * sz + tb[k - 1] * (sa if k > 1 else 4)
     return b
 
 

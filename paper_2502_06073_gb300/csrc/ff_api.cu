@@ -186,6 +186,9 @@ struct ff_ctx {
   size_t wsp_bytes = 0;
   float* ef = nullptr; int* zz = nullptr;
   float* z2b[4] = {nullptr}; float* h2b[4] = {nullptr};
+  // pre-activations of the tensor-core path, kept in bf16 for the adjoint's SiLU'
+  __nv_bfloat16* z2bb[4] = {nullptr};
+  __nv_bfloat16* zlatb[FF_MAX_LAYERS + 1][4] = {{nullptr}};
   float* X[FF_MAX_LAYERS + 1] = {nullptr};
   float* zlat[FF_MAX_LAYERS + 1][4] = {{nullptr}}; float* hlat[FF_MAX_LAYERS + 1][4] = {{nullptr}};
   float* Wv[FF_MAX_LAYERS + 1] = {nullptr};
@@ -512,7 +515,8 @@ int ensure_workspace(ff_ctx* c, long long ecap, int acap, long long budget_edges
   f32(&c->ef, ecap * FF_EF_STRIDE);
   plan.push_back({(void**)&c->zz, (size_t)ecap * 8});
   for (int k = 0; k < c->n2b; ++k) {
-    f32(&c->z2b[k], ecap * hp.two_body[k]);
+    if (tc) b16(&c->z2bb[k], ecap * hp.two_body[k]);
+    else f32(&c->z2b[k], ecap * hp.two_body[k]);
     if (k < c->n2b - 1) {
       if (tc) b16(&c->h2bb[k], ecap * hp.two_body[k]);
       else f32(&c->h2b[k], ecap * hp.two_body[k]);
@@ -524,7 +528,8 @@ int ensure_workspace(ff_ctx* c, long long ecap, int acap, long long budget_edges
   }
   for (int L = 1; L <= c->NL; ++L) {
     for (int k = 0; k < c->nlat; ++k) {
-      f32(&c->zlat[L][k], ecap * hp.latent[k]);
+      if (tc) b16(&c->zlatb[L][k], ecap * hp.latent[k]);
+      else f32(&c->zlat[L][k], ecap * hp.latent[k]);
       if (k < c->nlat - 1) {
         if (tc) b16(&c->hlatb[L][k], ecap * hp.latent[k]);
         else f32(&c->hlat[L][k], ecap * hp.latent[k]);
@@ -784,17 +789,17 @@ void forward_chunk(ff_ctx* c, const double* pos, int a0, int a1, float* E_atom, 
   const int w0 = hp.two_body[0];
   const float a0f = (float)(1.0 / sqrt((double)(2 * FF_N_SPECIES + hp.n_basis)));
   if (c->n2b == 1) {
-    launch_twobody_in(Ec, w0, hp.n_basis, c->ef, c->zz, c->W2b[0], a0f, c->z2b[0], c->X[0],
-                      c->ldx, tc ? c->Xb[0] : nullptr, c->ldx, 1, s);
+    launch_twobody_in(Ec, w0, hp.n_basis, c->ef, c->zz, c->W2b[0], a0f, c->z2b[0], c->z2bb[0],
+                      c->X[0], c->ldx, tc ? c->Xb[0] : nullptr, c->ldx, 1, s);
   } else {
-    launch_twobody_in(Ec, w0, hp.n_basis, c->ef, c->zz, c->W2b[0], a0f, c->z2b[0],
+    launch_twobody_in(Ec, w0, hp.n_basis, c->ef, c->zz, c->W2b[0], a0f, c->z2b[0], c->z2bb[0],
                       tc ? nullptr : c->h2b[0], w0, tc ? c->h2bb[0] : nullptr, w0, 0, s);
     for (int k = 1; k < c->n2b; ++k) {
       const int win = hp.two_body[k - 1], wout = hp.two_body[k];
       const bool last = k == c->n2b - 1;
       EpiParams ep{};
       ep.alpha = (float)(1.0 / sqrt((double)win));
-      ep.pre = c->z2b[k]; ep.ldp = wout;
+      ep.pre = c->z2b[k]; ep.preb = c->z2bb[k]; ep.ldp = wout;
       if (last) {
         ep.out = c->X[0]; ep.ldo = c->ldx; ep.f = fptr; ep.ldf = FF_EF_STRIDE;
         if (tc) { ep.outb = c->Xb[0]; ep.ldob = c->ldx; }
@@ -827,11 +832,11 @@ void forward_chunk(ff_ctx* c, const double* pos, int a0, int a1, float* E_atom, 
       const bool lastk = k == c->nlat - 1;
       EpiParams el{};
       el.alpha = (float)(1.0 / sqrt((double)fan));
-      el.pre = c->zlat[L][k]; el.ldp = wout;
+      el.pre = c->zlat[L][k]; el.preb = c->zlatb[L][k]; el.ldp = wout;
       if (lastk && c->head && L == c->NL) {
         // last latent layer + edge-energy head in one epilogue: per-edge energies, the
         // envelope-gradient seed and dE/dz of this layer; x^N itself is never stored
-        el.pre = nullptr;
+        el.pre = nullptr; el.preb = nullptr;
         el.res = c->X[L - 1]; el.ldr = c->ldx;
         el.f = fptr; el.ldf = FF_EF_STRIDE;
         el.beta = (float)(1.0 / sqrt(2.0));
@@ -885,9 +890,9 @@ void backward_chunk(ff_ctx* c, int a0, int a1, const double* seed, cudaStream_t 
     const int kl = c->nlat - 1;
     const bool fused = c->head && L == c->NL;   // dE/dz of this layer came from the readout
     if (!fused)
-      launch_rowred_bwd(Ec, hp.latent[kl], gx, ldgx, c->zlat[L][kl], hp.latent[kl], c->ef, r2,
-                        tc ? nullptr : c->GZ[0], hp.latent[kl], tc ? c->GZb[0] : nullptr,
-                        c->gf, s);
+      launch_rowred_bwd(Ec, hp.latent[kl], gx, ldgx, c->zlat[L][kl], c->zlatb[L][kl],
+                        hp.latent[kl], c->ef, r2, tc ? nullptr : c->GZ[0], hp.latent[kl],
+                        tc ? c->GZb[0] : nullptr, c->gf, s);
     int gzb = 0;
     const __nv_bfloat16* gzA = fused ? c->GZL : c->GZb[0];
     for (int k = kl; k >= 1; --k) {
@@ -895,7 +900,7 @@ void backward_chunk(ff_ctx* c, int a0, int a1, const double* seed, cudaStream_t 
       ep.alpha = (float)(1.0 / sqrt((double)hp.latent[k - 1]));
       if (tc) { ep.outb = c->GZb[gzb ^ 1]; ep.ldob = hp.latent[k - 1]; }
       else { ep.out = c->GZ[gzb ^ 1]; ep.ldo = hp.latent[k - 1]; }
-      ep.z = c->zlat[L][k - 1]; ep.ldz = hp.latent[k - 1];
+      ep.z = c->zlat[L][k - 1]; ep.zb = c->zlatb[L][k - 1]; ep.ldz = hp.latent[k - 1];
       mlp_gemm(c, EPI_DSILU, Ec, hp.latent[k - 1], hp.latent[k], c->GZ[gzb], gzA,
                hp.latent[k], c->WlatT[L][k], c->Wlat_b[L][k], ep, s);
       gzb ^= 1;
@@ -952,7 +957,8 @@ void backward_chunk(ff_ctx* c, int a0, int a1, const double* seed, cudaStream_t 
   // two-body MLP: x^0 = f * silu(z_last); the last gradient (dE/dz_0) stays FP32
   const int kb = c->n2b - 1;
   const bool b16_first = tc && kb >= 1;
-  launch_rowred_bwd(Ec, hp.two_body[kb], gx, ldgx, c->z2b[kb], hp.two_body[kb], c->ef, 1.f,
+  launch_rowred_bwd(Ec, hp.two_body[kb], gx, ldgx, c->z2b[kb], c->z2bb[kb], hp.two_body[kb],
+                    c->ef, 1.f,
                     b16_first ? nullptr : c->GZ[0], hp.two_body[kb],
                     b16_first ? c->GZb[0] : nullptr, c->gf, s);
   int gzb = 0;
@@ -961,7 +967,7 @@ void backward_chunk(ff_ctx* c, int a0, int a1, const double* seed, cudaStream_t 
     ep.alpha = (float)(1.0 / sqrt((double)hp.two_body[k - 1]));
     if (tc && k > 1) { ep.outb = c->GZb[gzb ^ 1]; ep.ldob = hp.two_body[k - 1]; }
     else { ep.out = c->GZ[gzb ^ 1]; ep.ldo = hp.two_body[k - 1]; }
-    ep.z = c->z2b[k - 1]; ep.ldz = hp.two_body[k - 1];
+    ep.z = c->z2b[k - 1]; ep.zb = c->z2bb[k - 1]; ep.ldz = hp.two_body[k - 1];
     mlp_gemm(c, EPI_DSILU, Ec, hp.two_body[k - 1], hp.two_body[k], c->GZ[gzb], c->GZb[gzb],
              hp.two_body[k], c->W2bT[k], c->W2b_b[k], ep, s);
     gzb ^= 1;

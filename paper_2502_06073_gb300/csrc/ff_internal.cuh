@@ -65,9 +65,11 @@ struct EpiParams {
   float alpha, beta;
   float* out; int ldo;
   float* pre; int ldp;           // pre-activation store (SILU modes)
+  __nv_bfloat16* preb;           // ... or its bf16 store (tensor-core GEMM; same ldp)
   const float* f; int ldf;       // per-row envelope: f[row * ldf]
   const float* res; int ldr;     // residual source (ldr == 0: one row broadcast)
   const float* z; int ldz;       // pre-activation source (DSILU)
+  const __nv_bfloat16* zb;       // ... or its bf16 source (tensor-core GEMM; same ldz)
   int split;
   __nv_bfloat16* outb; int ldob;  // optional bf16 copy of out (tensor-core GEMM only)
   const float* wv;                // EPI_HEAD: readout vector [N]
@@ -130,8 +132,9 @@ void launch_edge_features(long long E, const int* src, const int* col, const int
                           float rc, int n_basis, int p, int lmax, float* ef, int* zz,
                           cudaStream_t s);
 void launch_twobody_in(long long E, int width, int n_basis, const float* ef, const int* zz,
-                       const float* W0, float alpha, float* pre, float* out, int ldo,
-                       __nv_bfloat16* outb, int ldob, int final_layer, cudaStream_t s);
+                       const float* W0, float alpha, float* pre, __nv_bfloat16* preb,
+                       float* out, int ldo, __nv_bfloat16* outb, int ldob, int final_layer,
+                       cudaStream_t s);
 void launch_env_tp_fwd(int lmax, int in_kind, int out_kind, int C, int n_atoms,
                        const int* row_ptr, int e0, const float* ef, const float* W, int ldw,
                        const float* Vin, const float* theta, float* X, __nv_bfloat16* Xb,
@@ -147,9 +150,9 @@ void launch_energy(int n_atoms, const int* row_ptr, int e0, const float* X, int 
                    const float* w_eff, float* E_atom, cudaStream_t s);
 void launch_energy_sum(int n_atoms, const int* row_ptr, int e0, const float* E_edge,
                        float* E_atom, cudaStream_t s);
-void launch_rowred_bwd(long long E, int N, const float* gx, int ldgx, const float* z, int ldz,
-                       const float* ef, float alpha, float* gz, int ldgz, __nv_bfloat16* gzb,
-                       float* gf, cudaStream_t s);
+void launch_rowred_bwd(long long E, int N, const float* gx, int ldgx, const float* z,
+                       const __nv_bfloat16* zb, int ldz, const float* ef, float alpha,
+                       float* gz, int ldgz, __nv_bfloat16* gzb, float* gf, cudaStream_t s);
 void launch_cvt_bf16(const float* src, int lds, __nv_bfloat16* dst, int ldd, long long rows,
                      int col0, int ncols, cudaStream_t s);
 void launch_edge_grad(long long E, int w0, int n_basis, float rc, int p, int lmax,

@@ -1,7 +1,8 @@
 // BF16 tensor-core GEMM (tcgen05 + TMA) for the per-edge MLPs of precision mode 1:
 // C[M][N] = alpha * A[M][K] * B[K][N] with A (activations, one row per edge) and
 // Bt = B^T [N][K] both bf16 and K-contiguous, FP32 accumulation in tensor memory, and the
-// same fused element-wise epilogues as the FP32 path (SiLU, envelope, residual, SiLU').
+// same fused element-wise epilogues as the FP32 path (SiLU, envelope, residual, SiLU');
+// pre-activations are stored (SiLU modes) and read back (SiLU') in bf16.
 //
 // One CTA (4 warps) owns a 128-row tile and one slice of at most 256 output columns:
 //   warp 0 / lane 0   TMA producer: A and B K-chunks of 64 elements (128 B rows,
@@ -150,7 +151,12 @@ __device__ __forceinline__ void epi_batch(const EpiParams& ep, const float4 (&ac
     const size_t r = (size_t)row[i];
     if (MODE == EPI_SILU_RES || MODE == EPI_HEAD || (MODE == EPI_RES && col < ep.split))
       aux[i] = *reinterpret_cast<const float4*>(ep.res + r * ep.ldr + col);
-    if (MODE == EPI_DSILU) aux[i] = *reinterpret_cast<const float4*>(ep.z + r * ep.ldz + col);
+    if (MODE == EPI_DSILU) {   // pre-activations of this path are stored in bf16
+      const uint2 pk = *reinterpret_cast<const uint2*>(ep.zb + r * ep.ldz + col);
+      const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk.x));
+      const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk.y));
+      aux[i] = make_float4(lo.x, lo.y, hi.x, hi.y);
+    }
     if (MODE == EPI_ACC) aux[i] = *reinterpret_cast<const float4*>(ep.out + r * ep.ldo + col);
     if (MODE == EPI_SILU_F || MODE == EPI_SILU_RES || MODE == EPI_HEAD)
       fr[i] = ep.f[r * ep.ldf];
@@ -202,9 +208,14 @@ __device__ __forceinline__ void epi_batch(const EpiParams& ep, const float4 (&ac
         else if (MODE == EPI_RES) o[j] = v[j] + (col < ep.split ? ep.beta * a4[j] : 0.f);
         else o[j] = a4[j] + v[j];
       }
-      if (MODE == EPI_SILU || MODE == EPI_SILU_F || MODE == EPI_SILU_RES)
-        *reinterpret_cast<float4*>(ep.pre + r * ep.ldp + col) =
-            make_float4(v[0], v[1], v[2], v[3]);
+      if (MODE == EPI_SILU || MODE == EPI_SILU_F || MODE == EPI_SILU_RES) {
+        __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]);
+        __nv_bfloat162 hi = __floats2bfloat162_rn(v[2], v[3]);
+        uint2 pk;
+        pk.x = *reinterpret_cast<uint32_t*>(&lo);
+        pk.y = *reinterpret_cast<uint32_t*>(&hi);
+        *reinterpret_cast<uint2*>(ep.preb + r * ep.ldp + col) = pk;
+      }
       if (ep.out)
         *reinterpret_cast<float4*>(ep.out + r * ep.ldo + col) =
             make_float4(o[0], o[1], o[2], o[3]);

@@ -84,7 +84,8 @@ __global__ void k_edge_features(long long E, const int* __restrict__ src,
 // the radial part.  final_layer: out = f * silu(z) (x^0), otherwise out = silu(z).
 __global__ void k_twobody_in(long long E, int width, int n_basis, const float* __restrict__ ef,
                              const int* __restrict__ zz, const float* __restrict__ W0,
-                             float alpha, float* __restrict__ pre, float* __restrict__ out,
+                             float alpha, float* __restrict__ pre,
+                             __nv_bfloat16* __restrict__ preb, float* __restrict__ out,
                              int ldo, __nv_bfloat16* __restrict__ outb, int ldob,
                              int final_layer) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -96,7 +97,8 @@ __global__ void k_twobody_in(long long E, int width, int n_basis, const float* _
   const float* b = ef + e * FF_EF_STRIDE + FF_EF_B;
   for (int n = 0; n < n_basis; ++n) acc += b[n] * W0[(size_t)(2 * FF_N_SPECIES + n) * width + o];
   const float z = alpha * acc;
-  pre[e * width + o] = z;
+  if (preb) preb[e * width + o] = __float2bfloat16_rn(z);
+  else pre[e * width + o] = z;
   const float h = silu_f(z);
   const float v = final_layer ? ef[e * FF_EF_STRIDE + FF_EF_F] * h : h;
   if (out) out[e * ldo + o] = v;
@@ -134,54 +136,82 @@ __global__ void k_energy_sum(int n_atoms, const int* __restrict__ row_ptr, int e
 }
 
 // Adjoint of out = f * silu(z) (scaled by alpha):  gz = alpha f silu'(z) gx,
-// gf += alpha sum_d gx silu(z).  One warp per edge; lane l owns the float4 column groups
-// l, l + 32, ... (N % 4 == 0, N <= 512); all loads of the row are issued first.
-// ldgx == 0: gx is one broadcast row.  gz (FP32) and/or gzb (BF16) receive the result.
+// gf += alpha sum_d gx silu(z).  One warp per EPW edges; lane l owns the float4 column
+// groups l, l + 32, ... (NGL of them: N <= 128 NGL) of each row; all loads of the rows are
+// issued first.  ldgx == 0: gx is one broadcast row.  gz (FP32) and/or gzb (BF16) receive
+// the result.  ZB: the pre-activations are bf16 (tensor-core path).
+template <bool ZB, int NGL, int EPW>
 __global__ void k_rowred_bwd(long long E, int N, const float* __restrict__ gx, int ldgx,
-                             const float* __restrict__ z, int ldz, const float* __restrict__ ef,
-                             float alpha, float* __restrict__ gz, int ldgz,
-                             __nv_bfloat16* __restrict__ gzb, float* __restrict__ gf) {
-  const long long e = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+                             const float* __restrict__ z, const __nv_bfloat16* __restrict__ zb,
+                             int ldz, const float* __restrict__ ef, float alpha,
+                             float* __restrict__ gz, int ldgz, __nv_bfloat16* __restrict__ gzb,
+                             float* __restrict__ gf) {
+  const long long eb = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * EPW;
   const int lane = threadIdx.x & 31;
-  if (e >= E) return;
-  const float f = ef[e * FF_EF_STRIDE + FF_EF_F];
+  if (eb >= E) return;
   const int ng = N >> 2;
-  float4 g4[4], z4[4];
+  float4 g4[EPW][NGL], z4[EPW][NGL];
+  float f[EPW];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int gi = lane + 32 * k;
-    if (gi < ng) {
-      g4[k] = *reinterpret_cast<const float4*>(gx + (size_t)e * ldgx + 4 * gi);
-      z4[k] = *reinterpret_cast<const float4*>(z + (size_t)e * ldz + 4 * gi);
+  for (int u = 0; u < EPW; ++u) {
+    const long long e = eb + u;
+    f[u] = e < E ? ef[e * FF_EF_STRIDE + FF_EF_F] : 0.f;
+#pragma unroll
+    for (int k = 0; k < NGL; ++k) {
+      const int gi = lane + 32 * k;
+      if (e < E && gi < ng) {
+        g4[u][k] = *reinterpret_cast<const float4*>(gx + (size_t)e * ldgx + 4 * gi);
+        if (ZB) {
+          const uint2 pk = *reinterpret_cast<const uint2*>(zb + (size_t)e * ldz + 4 * gi);
+          const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk.x));
+          const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk.y));
+          z4[u][k] = make_float4(lo.x, lo.y, hi.x, hi.y);
+        } else {
+          z4[u][k] = *reinterpret_cast<const float4*>(z + (size_t)e * ldz + 4 * gi);
+        }
+      }
     }
   }
-  float acc = 0.f;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int gi = lane + 32 * k;
-    if (gi >= ng) continue;
-    const float gv[4] = {g4[k].x, g4[k].y, g4[k].z, g4[k].w};
-    const float zv[4] = {z4[k].x, z4[k].y, z4[k].z, z4[k].w};
-    float o[4];
+  for (int u = 0; u < EPW; ++u) {
+    const long long e = eb + u;
+    if (e >= E) break;
+    float acc = 0.f;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float sg = sigm_f(zv[j]);
-      o[j] = alpha * f * gv[j] * (sg * (1.f + zv[j] * (1.f - sg)));
-      acc += gv[j] * zv[j] * sg;
+    for (int k = 0; k < NGL; ++k) {
+      const int gi = lane + 32 * k;
+      if (gi >= ng) continue;
+      const float gv[4] = {g4[u][k].x, g4[u][k].y, g4[u][k].z, g4[u][k].w};
+      const float zv[4] = {z4[u][k].x, z4[u][k].y, z4[u][k].z, z4[u][k].w};
+      float o[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float sg = sigm_f(zv[j]);
+        o[j] = alpha * f[u] * gv[j] * (sg * (1.f + zv[j] * (1.f - sg)));
+        acc += gv[j] * zv[j] * sg;
+      }
+      const size_t oi = (size_t)e * ldgz + 4 * gi;
+      if (gz) *reinterpret_cast<float4*>(gz + oi) = make_float4(o[0], o[1], o[2], o[3]);
+      if (gzb) {
+        __nv_bfloat162 lo = __floats2bfloat162_rn(o[0], o[1]);
+        __nv_bfloat162 hi = __floats2bfloat162_rn(o[2], o[3]);
+        uint2 pk;
+        pk.x = *reinterpret_cast<uint32_t*>(&lo);
+        pk.y = *reinterpret_cast<uint32_t*>(&hi);
+        *reinterpret_cast<uint2*>(gzb + oi) = pk;
+      }
     }
-    const size_t oi = (size_t)e * ldgz + 4 * gi;
-    if (gz) *reinterpret_cast<float4*>(gz + oi) = make_float4(o[0], o[1], o[2], o[3]);
-    if (gzb) {
-      __nv_bfloat162 lo = __floats2bfloat162_rn(o[0], o[1]);
-      __nv_bfloat162 hi = __floats2bfloat162_rn(o[2], o[3]);
-      uint2 pk;
-      pk.x = *reinterpret_cast<uint32_t*>(&lo);
-      pk.y = *reinterpret_cast<uint32_t*>(&hi);
-      *reinterpret_cast<uint2*>(gzb + oi) = pk;
-    }
+    acc = warp_sum(acc);
+    if (lane == 0) gf[e] += alpha * acc;
   }
-  acc = warp_sum(acc);
-  if (lane == 0) gf[e] += alpha * acc;
+}
+
+template <bool ZB, int NGL, int EPW>
+void rowred_one(long long E, int N, const float* gx, int ldgx, const float* z,
+                const __nv_bfloat16* zb, int ldz, const float* ef, float alpha, float* gz,
+                int ldgz, __nv_bfloat16* gzb, float* gf, cudaStream_t s) {
+  k_rowred_bwd<ZB, NGL, EPW><<<ff_cdiv(E, 8 * EPW), 256, 0, s>>>(E, N, gx, ldgx, z, zb, ldz, ef,
+                                                               alpha, gz, ldgz, gzb, gf);
 }
 
 // dE/dr_e from the radial-basis gradient (via the first two-body layer), the envelope
@@ -449,12 +479,13 @@ void launch_edge_features(long long E, const int* src, const int* col, const int
 }
 
 void launch_twobody_in(long long E, int width, int n_basis, const float* ef, const int* zz,
-                       const float* W0, float alpha, float* pre, float* out, int ldo,
-                       __nv_bfloat16* outb, int ldob, int final_layer, cudaStream_t s) {
+                       const float* W0, float alpha, float* pre, __nv_bfloat16* preb,
+                       float* out, int ldo, __nv_bfloat16* outb, int ldob, int final_layer,
+                       cudaStream_t s) {
   ProfScope ps_(PC_TWOBODY_IN, s);
   if (E <= 0) return;
   k_twobody_in<<<ff_cdiv(E * width, 256), 256, 0, s>>>(E, width, n_basis, ef, zz, W0, alpha, pre,
-                                                      out, ldo, outb, ldob, final_layer);
+                                                      preb, out, ldo, outb, ldob, final_layer);
   ff_count_launch(1);
 }
 
@@ -474,13 +505,22 @@ void launch_energy_sum(int n_atoms, const int* row_ptr, int e0, const float* E_e
   ff_count_launch(1);
 }
 
-void launch_rowred_bwd(long long E, int N, const float* gx, int ldgx, const float* z, int ldz,
-                       const float* ef, float alpha, float* gz, int ldgz, __nv_bfloat16* gzb,
-                       float* gf, cudaStream_t s) {
+void launch_rowred_bwd(long long E, int N, const float* gx, int ldgx, const float* z,
+                       const __nv_bfloat16* zb, int ldz, const float* ef, float alpha,
+                       float* gz, int ldgz, __nv_bfloat16* gzb, float* gf, cudaStream_t s) {
   ProfScope ps_(PC_ROWRED, s);
   if (E <= 0) return;
-  k_rowred_bwd<<<ff_cdiv(E, 8), 256, 0, s>>>(E, N, gx, ldgx, z, ldz, ef, alpha, gz, ldgz, gzb,
-                                            gf);
+  // registers sized to the row: NGL float4 groups per lane, two rows per warp up to N = 256
+  if (N <= 128) {
+    if (zb) rowred_one<true, 1, 2>(E, N, gx, ldgx, z, zb, ldz, ef, alpha, gz, ldgz, gzb, gf, s);
+    else rowred_one<false, 1, 2>(E, N, gx, ldgx, z, zb, ldz, ef, alpha, gz, ldgz, gzb, gf, s);
+  } else if (N <= 256) {
+    if (zb) rowred_one<true, 2, 2>(E, N, gx, ldgx, z, zb, ldz, ef, alpha, gz, ldgz, gzb, gf, s);
+    else rowred_one<false, 2, 2>(E, N, gx, ldgx, z, zb, ldz, ef, alpha, gz, ldgz, gzb, gf, s);
+  } else {
+    if (zb) rowred_one<true, 4, 1>(E, N, gx, ldgx, z, zb, ldz, ef, alpha, gz, ldgz, gzb, gf, s);
+    else rowred_one<false, 4, 1>(E, N, gx, ldgx, z, zb, ldz, ef, alpha, gz, ldgz, gzb, gf, s);
+  }
   ff_count_launch(1);
 }
 
