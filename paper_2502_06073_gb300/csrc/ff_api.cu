@@ -522,8 +522,10 @@ int ensure_workspace(ff_ctx* c, long long ecap, int acap, long long budget_edges
       else f32(&c->h2b[k], ecap * hp.two_body[k]);
     }
   }
+  // the tensor-core path keeps the residual stream in bf16 (its GEMM operand) and needs
+  // an FP32 copy only of x^N when the readout is not fused
   for (int L = 0; L <= c->NL; ++L) {
-    f32(&c->X[L], ecap * c->ldx);
+    if (!tc || (L == c->NL && !c->head)) f32(&c->X[L], ecap * c->ldx);
     if (tc) b16(&c->Xb[L], ecap * c->ldx);
   }
   for (int L = 1; L <= c->NL; ++L) {
@@ -790,7 +792,7 @@ void forward_chunk(ff_ctx* c, const double* pos, int a0, int a1, float* E_atom, 
   const float a0f = (float)(1.0 / sqrt((double)(2 * FF_N_SPECIES + hp.n_basis)));
   if (c->n2b == 1) {
     launch_twobody_in(Ec, w0, hp.n_basis, c->ef, c->zz, c->W2b[0], a0f, c->z2b[0], c->z2bb[0],
-                      c->X[0], c->ldx, tc ? c->Xb[0] : nullptr, c->ldx, 1, s);
+                      tc ? nullptr : c->X[0], c->ldx, tc ? c->Xb[0] : nullptr, c->ldx, 1, s);
   } else {
     launch_twobody_in(Ec, w0, hp.n_basis, c->ef, c->zz, c->W2b[0], a0f, c->z2b[0], c->z2bb[0],
                       tc ? nullptr : c->h2b[0], w0, tc ? c->h2bb[0] : nullptr, w0, 0, s);
@@ -801,8 +803,9 @@ void forward_chunk(ff_ctx* c, const double* pos, int a0, int a1, float* E_atom, 
       ep.alpha = (float)(1.0 / sqrt((double)win));
       ep.pre = c->z2b[k]; ep.preb = c->z2bb[k]; ep.ldp = wout;
       if (last) {
-        ep.out = c->X[0]; ep.ldo = c->ldx; ep.f = fptr; ep.ldf = FF_EF_STRIDE;
+        ep.f = fptr; ep.ldf = FF_EF_STRIDE;
         if (tc) { ep.outb = c->Xb[0]; ep.ldob = c->ldx; }
+        else { ep.out = c->X[0]; ep.ldo = c->ldx; }
       } else if (tc) {
         ep.outb = c->h2bb[k]; ep.ldob = wout;
       } else {
@@ -822,7 +825,8 @@ void forward_chunk(ff_ctx* c, const double* pos, int a0, int a1, float* E_atom, 
     const int last = L == c->NL ? 1 : 0;
     launch_env_tp_fwd(c->lmax, c->layer_ink[L], c->layer_outk[L], c->C, na, rp, e0, c->ef,
                       c->Wv[L], c->ldw, L >= 2 ? c->V[L - 1] : nullptr,
-                      last ? nullptr : c->theta[L], c->X[L - 1], tc ? c->Xb[L - 1] : nullptr,
+                      last ? nullptr : c->theta[L], tc ? nullptr : c->X[L - 1],
+                      tc ? c->Xb[L - 1] : nullptr,
                       c->ldx, c->D, last ? nullptr : c->V[L], c->Gam[L], inv_sqrt_nu, s);
     const float* A32 = c->X[L - 1];
     const __nv_bfloat16* Ab = c->Xb[L - 1];
@@ -837,7 +841,7 @@ void forward_chunk(ff_ctx* c, const double* pos, int a0, int a1, float* E_atom, 
         // last latent layer + edge-energy head in one epilogue: per-edge energies, the
         // envelope-gradient seed and dE/dz of this layer; x^N itself is never stored
         el.pre = nullptr; el.preb = nullptr;
-        el.res = c->X[L - 1]; el.ldr = c->ldx;
+        el.resb = c->Xb[L - 1]; el.ldr = c->ldx;
         el.f = fptr; el.ldf = FF_EF_STRIDE;
         el.beta = (float)(1.0 / sqrt(2.0));
         el.wv = c->w_eff;
@@ -848,11 +852,16 @@ void forward_chunk(ff_ctx* c, const double* pos, int a0, int a1, float* E_atom, 
         break;
       }
       if (lastk) {
-        el.out = c->X[L]; el.ldo = c->ldx;
-        el.res = c->X[L - 1]; el.ldr = c->ldx;
+        el.out = c->X[L]; el.ldo = c->ldx;   // null in the tensor-core path but for x^N
         el.f = fptr; el.ldf = FF_EF_STRIDE;
         el.beta = (float)(1.0 / sqrt(2.0));
-        if (tc) { el.outb = c->Xb[L]; el.ldob = c->ldx; }
+        el.ldr = c->ldx;
+        if (tc) {
+          el.resb = c->Xb[L - 1];
+          el.outb = c->Xb[L]; el.ldob = c->ldx;
+        } else {
+          el.res = c->X[L - 1];
+        }
       } else if (tc) {
         el.outb = c->hlatb[L][k]; el.ldob = wout;
       } else {

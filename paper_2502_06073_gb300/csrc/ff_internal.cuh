@@ -68,6 +68,7 @@ struct EpiParams {
   __nv_bfloat16* preb;           // ... or its bf16 store (tensor-core GEMM; same ldp)
   const float* f; int ldf;       // per-row envelope: f[row * ldf]
   const float* res; int ldr;     // residual source (ldr == 0: one row broadcast)
+  const __nv_bfloat16* resb;     // bf16 residual stream (tensor-core SILU_RES / HEAD; ldr)
   const float* z; int ldz;       // pre-activation source (DSILU)
   const __nv_bfloat16* zb;       // ... or its bf16 source (tensor-core GEMM; same ldz)
   int split;

@@ -2,7 +2,8 @@
 // C[M][N] = alpha * A[M][K] * B[K][N] with A (activations, one row per edge) and
 // Bt = B^T [N][K] both bf16 and K-contiguous, FP32 accumulation in tensor memory, and the
 // same fused element-wise epilogues as the FP32 path (SiLU, envelope, residual, SiLU');
-// pre-activations are stored (SiLU modes) and read back (SiLU') in bf16.
+// pre-activations are stored (SiLU modes) and read back (SiLU') in bf16, and the residual
+// stream x^L is read in bf16 (the copy that is also the next GEMM's operand).
 //
 // One CTA (4 warps) owns a 128-row tile and one slice of at most 256 output columns:
 //   warp 0 / lane 0   TMA producer: A and B K-chunks of 64 elements (128 B rows,
@@ -128,9 +129,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-__device__ __forceinline__ float silu_f(float z) { return z / (1.f + expf(-z)); }
+// Logistic sigmoid from the hardware exponential and fast division (a few ulp; the error
+// budget of this path is set by its bf16 operands, 2^-9 relative).  exp(-z) = inf for
+// z < -88 gives 0, the correct limit.
+__device__ __forceinline__ float sigm_fast(float z) { return __fdividef(1.f, 1.f + __expf(-z)); }
+__device__ __forceinline__ float silu_f(float z) { return z * sigm_fast(z); }
 __device__ __forceinline__ float dsilu_f(float z) {
-  const float sg = 1.f / (1.f + expf(-z));
+  const float sg = sigm_fast(z);
   return sg * (1.f + z * (1.f - sg));
 }
 
@@ -149,7 +154,13 @@ __device__ __forceinline__ void epi_batch(const EpiParams& ep, const float4 (&ac
     fr[i] = 0.f;
     if (!ok) continue;
     const size_t r = (size_t)row[i];
-    if (MODE == EPI_SILU_RES || MODE == EPI_HEAD || (MODE == EPI_RES && col < ep.split))
+    if (MODE == EPI_SILU_RES || MODE == EPI_HEAD) {   // residual stream kept in bf16
+      const uint2 pk = *reinterpret_cast<const uint2*>(ep.resb + r * ep.ldr + col);
+      const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk.x));
+      const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk.y));
+      aux[i] = make_float4(lo.x, lo.y, hi.x, hi.y);
+    }
+    if (MODE == EPI_RES && col < ep.split)
       aux[i] = *reinterpret_cast<const float4*>(ep.res + r * ep.ldr + col);
     if (MODE == EPI_DSILU) {   // pre-activations of this path are stored in bf16
       const uint2 pk = *reinterpret_cast<const uint2*>(ep.zb + r * ep.ldz + col);
@@ -176,7 +187,7 @@ __device__ __forceinline__ void epi_batch(const EpiParams& ep, const float4 (&ac
       float g[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const float sg = 1.f / (1.f + expf(-v[j]));
+        const float sg = sigm_fast(v[j]);
         const float sv = v[j] * sg;
         racc[i][0] += wv[j] * (ep.beta * (a4[j] + fr[i] * sv));
         racc[i][1] += wv[j] * sv;

@@ -82,27 +82,57 @@ __global__ void k_edge_features(long long E, const int* __restrict__ src,
 
 // First two-body layer: one-hot(Z_i) || one-hot(Z_j) || B(r) times W0 = two table rows plus
 // the radial part.  final_layer: out = f * silu(z) (x^0), otherwise out = silu(z).
+// One thread per (edge, 4 consecutive output columns), width % 4 == 0: float4 rows of W0
+// (read through L1; the table is ~48 KB at width 64) and 4-wide stores.
+__device__ __forceinline__ void store4(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store4(__nv_bfloat16* p, const float (&v)[4]) {
+  __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]);
+  __nv_bfloat162 hi = __floats2bfloat162_rn(v[2], v[3]);
+  uint2 pk;
+  pk.x = *reinterpret_cast<uint32_t*>(&lo);
+  pk.y = *reinterpret_cast<uint32_t*>(&hi);
+  *reinterpret_cast<uint2*>(p) = pk;
+}
+
 __global__ void k_twobody_in(long long E, int width, int n_basis, const float* __restrict__ ef,
                              const int* __restrict__ zz, const float* __restrict__ W0,
                              float alpha, float* __restrict__ pre,
                              __nv_bfloat16* __restrict__ preb, float* __restrict__ out,
                              int ldo, __nv_bfloat16* __restrict__ outb, int ldob,
                              int final_layer) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= E * width) return;
-  const long long e = t / width;
-  const int o = (int)(t - e * width);
+  const int tpe = width >> 2;                 // threads per edge
+  const int epb = blockDim.x / tpe;
+  const int slot = threadIdx.x / tpe, o = 4 * (threadIdx.x - slot * tpe);
+  const long long e = (long long)blockIdx.x * epb + slot;
+  if (slot >= epb || e >= E) return;
   const int zi = zz[2 * e], zj = zz[2 * e + 1];
-  float acc = W0[(size_t)(zi - 1) * width + o] + W0[(size_t)(FF_N_SPECIES + zj - 1) * width + o];
-  const float* b = ef + e * FF_EF_STRIDE + FF_EF_B;
-  for (int n = 0; n < n_basis; ++n) acc += b[n] * W0[(size_t)(2 * FF_N_SPECIES + n) * width + o];
-  const float z = alpha * acc;
-  if (preb) preb[e * width + o] = __float2bfloat16_rn(z);
-  else pre[e * width + o] = z;
-  const float h = silu_f(z);
-  const float v = final_layer ? ef[e * FF_EF_STRIDE + FF_EF_F] * h : h;
-  if (out) out[e * ldo + o] = v;
-  if (outb) outb[e * ldob + o] = __float2bfloat16_rn(v);
+  const float* bb = ef + e * FF_EF_STRIDE + FF_EF_B;
+  float b[10];
+#pragma unroll
+  for (int n = 0; n < 10; ++n) b[n] = n < n_basis ? bb[n] : 0.f;
+  const float4 ri = *reinterpret_cast<const float4*>(W0 + (zi - 1) * width + o);
+  const float4 rj = *reinterpret_cast<const float4*>(W0 + (FF_N_SPECIES + zj - 1) * width + o);
+  float acc[4] = {ri.x + rj.x, ri.y + rj.y, ri.z + rj.z, ri.w + rj.w};
+  const float* wr = W0 + 2 * FF_N_SPECIES * width + o;
+#pragma unroll
+  for (int n = 0; n < 10; ++n) {
+    if (n >= n_basis) break;
+    const float4 w = *reinterpret_cast<const float4*>(wr + n * width);
+    acc[0] += b[n] * w.x; acc[1] += b[n] * w.y; acc[2] += b[n] * w.z; acc[3] += b[n] * w.w;
+  }
+  const float f = final_layer ? ef[e * FF_EF_STRIDE + FF_EF_F] : 1.f;
+  float z[4], v[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    z[j] = alpha * acc[j];
+    v[j] = final_layer ? f * silu_f(z[j]) : silu_f(z[j]);
+  }
+  if (preb) store4(preb + e * width + o, z);
+  else store4(pre + e * width + o, z);
+  if (out) store4(out + e * ldo + o, v);
+  if (outb) store4(outb + e * ldob + o, v);
 }
 
 // E_i = sum over the edges of i of x^N_ij . w_eff (the linear edge-energy MLP folded into
@@ -186,7 +216,8 @@ __global__ void k_rowred_bwd(long long E, int N, const float* __restrict__ gx, i
       float o[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const float sg = sigm_f(zv[j]);
+        // the bf16 path takes the hardware exponential and fast division, as its GEMMs do
+        const float sg = ZB ? __fdividef(1.f, 1.f + __expf(-zv[j])) : sigm_f(zv[j]);
         o[j] = alpha * f[u] * gv[j] * (sg * (1.f + zv[j] * (1.f - sg)));
         acc += gv[j] * zv[j] * sg;
       }
@@ -484,8 +515,9 @@ void launch_twobody_in(long long E, int width, int n_basis, const float* ef, con
                        cudaStream_t s) {
   ProfScope ps_(PC_TWOBODY_IN, s);
   if (E <= 0) return;
-  k_twobody_in<<<ff_cdiv(E * width, 256), 256, 0, s>>>(E, width, n_basis, ef, zz, W0, alpha, pre,
-                                                      preb, out, ldo, outb, ldob, final_layer);
+  const int epb = 256 / (width / 4);
+  k_twobody_in<<<ff_cdiv(E, epb), 256, 0, s>>>(E, width, n_basis, ef, zz, W0, alpha, pre, preb,
+                                               out, ldo, outb, ldob, final_layer);
   ff_count_launch(1);
 }
 
