@@ -181,11 +181,12 @@ __global__ void k_rowred_bwd(long long E, int N, const float* __restrict__ gx, i
   if (eb >= E) return;
   const int ng = N >> 2;
   float4 g4[EPW][NGL], z4[EPW][NGL];
-  float f[EPW];
+  float f[EPW], gf0[EPW];
 #pragma unroll
   for (int u = 0; u < EPW; ++u) {
     const long long e = eb + u;
     f[u] = e < E ? ef[e * FF_EF_STRIDE + FF_EF_F] : 0.f;
+    gf0[u] = (e < E && lane == 0) ? gf[e] : 0.f;   // read with the rows, not after the sum
 #pragma unroll
     for (int k = 0; k < NGL; ++k) {
       const int gi = lane + 32 * k;
@@ -233,7 +234,7 @@ __global__ void k_rowred_bwd(long long E, int N, const float* __restrict__ gx, i
       }
     }
     acc = warp_sum(acc);
-    if (lane == 0) gf[e] += alpha * acc;
+    if (lane == 0) gf[e] = gf0[u] + alpha * acc;
   }
 }
 
