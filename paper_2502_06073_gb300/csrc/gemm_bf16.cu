@@ -242,8 +242,19 @@ __device__ __forceinline__ void epi_batch(const EpiParams& ep, const float4 (&ac
   }
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(256, 2)
+// Shared memory before the barriers: the stage ring, or the epilogue tiles (32x32 floats
+// per warp) plus the readout's row sums (2 x 128 floats), whichever is larger.
+__host__ __device__ inline size_t gemm_pipe_bytes(int mode, int nw, int stages, int nbw) {
+  const size_t ring = (size_t)stages * (TM * TK * 2 + (size_t)nbw * TK * 2);
+  const size_t epi = (size_t)nw * 32 * 32 * 4 + (mode == EPI_HEAD ? 2 * TM * 4 : 0);
+  return ring > epi ? ring : epi;
+}
+
+// NW = 8 warps (two CTAs per SM; slices of up to 256 columns) or NW = 4 (slices of up to
+// 128 columns: up to four CTAs per SM share the tensor memory, so more epilogue warps run
+// per SM on the narrow products).
+template <int MODE, int NW>
+__global__ void __launch_bounds__(32 * NW, 8 / NW * 2)
 k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
           const __grid_constant__ CUtensorMap tmB, int M, int N, int K, int k1c, int n0, int nbw,
           int stages, EpiParams ep, int* __restrict__ err) {
@@ -252,7 +263,9 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   const uint32_t a_bytes = TM * TK * 2;
   const uint32_t b_bytes = (uint32_t)nbw * TK * 2;
   const uint32_t st_bytes = a_bytes + b_bytes;
-  uint64_t* bars = (uint64_t*)(smem + (size_t)stages * st_bytes);
+  // the epilogue's shared tiles (and the readout's row sums) reuse the stage memory; the
+  // barriers sit after whichever of the two is larger
+  uint64_t* bars = (uint64_t*)(smem + gemm_pipe_bytes(MODE, NW, stages, nbw));
   uint64_t* full = bars;
   uint64_t* empty = bars + stages;
   uint64_t* accf = bars + 2 * stages;
@@ -328,8 +341,8 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   }
   __syncwarp();
 
-  // ---- epilogue: 8 warps; warp w drains TMEM lane quadrant (w & 3) (tile rows
-  // 32(w&3)..+31) for every other 32-column chunk (w >> 2 picks the parity).  Each 32x32
+  // ---- epilogue: NW warps; warp w drains TMEM lane quadrant (w & 3) (tile rows
+  // 32(w&3)..+31) for every (NW/4)-th 32-column chunk (w >> 2 picks which).  Each 32x32
   // block goes through a shared tile (float4 groups XOR-swizzled by row, conflict-free
   // both ways; it reuses the pipeline stages, free once the accumulator is complete) and
   // leaves as float4 row segments, so one warp instruction covers 4 rows x 32 columns.
@@ -341,7 +354,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   float racc[8][2];
 #pragma unroll
   for (int i = 0; i < 8; ++i) racc[i][0] = racc[i][1] = 0.f;
-  for (int ci = half; ci < nchunks; ci += 2) {
+  for (int ci = half; ci < nchunks; ci += NW / 4) {
     const int c0 = ci * 32;
     float v[32];
     tmem_ld32(tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
@@ -368,7 +381,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   if (MODE == EPI_HEAD) {
     // row sums: the 8 lanes sharing a row (lane & 7) by shuffles, then the two warps of
     // a row quadrant (column parities) through shared memory after the tiles
-    float* red = reinterpret_cast<float*>(smem) + 8 * 32 * 32;
+    float* red = reinterpret_cast<float*>(smem) + NW * 32 * 32;
     const int rsub = lane >> 3;
 #pragma unroll
     for (int i = 0; i < 8; ++i)
@@ -448,24 +461,37 @@ bool make_map(CUtensorMap* m, const void* base, long long rows, int cols, int ld
          CUDA_SUCCESS;
 }
 
-template <int MODE>
-bool launch_mode(const CUtensorMap& ta, const CUtensorMap& ta2, const CUtensorMap& tb, int M,
-                 int N, int K, int k1c, int n0, int nbw, int stages, size_t smem,
-                 const EpiParams& ep, int* err, cudaStream_t s) {
+template <int MODE, int NW>
+bool launch_nw(const CUtensorMap& ta, const CUtensorMap& ta2, const CUtensorMap& tb, int M, int N,
+               int K, int k1c, int n0, int nbw, int stages, const EpiParams& ep, int* err,
+               cudaStream_t s) {
   static bool attr_set = false;
   if (!attr_set) {
-    if (cudaFuncSetAttribute(k_gemm_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_gemm_tc<MODE, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 * 1024) != cudaSuccess)
       return false;
     attr_set = true;
   }
-  k_gemm_tc<MODE><<<ff_cdiv(M, TM), 256, smem, s>>>(ta, ta2, tb, M, N, K, k1c, n0, nbw, stages,
-                                                     ep, err);
+  const size_t bytes = gemm_pipe_bytes(MODE, NW, stages, nbw) + 1024 + 256;   // align + bars
+  if (bytes > 200 * 1024) return false;
+  k_gemm_tc<MODE, NW><<<ff_cdiv(M, TM), 32 * NW, bytes, s>>>(ta, ta2, tb, M, N, K, k1c, n0, nbw,
+                                                              stages, ep, err);
   return true;
 }
 
+template <int MODE>
+bool launch_mode(const CUtensorMap& ta, const CUtensorMap& ta2, const CUtensorMap& tb, int M,
+                 int N, int K, int k1c, int n0, int nbw, int stages, const EpiParams& ep,
+                 int* err, cudaStream_t s) {
+  if constexpr (MODE != EPI_HEAD) {   // the readout needs the 8-warp row reduction
+    if (nbw <= 128)
+      return launch_nw<MODE, 4>(ta, ta2, tb, M, N, K, k1c, n0, nbw, stages, ep, err, s);
+  }
+  return launch_nw<MODE, 8>(ta, ta2, tb, M, N, K, k1c, n0, nbw, stages, ep, err, s);
+}
+
 using LaunchFn = bool (*)(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, int, int,
-                          int, int, int, int, int, size_t, const EpiParams&, int*, cudaStream_t);
+                          int, int, int, int, int, const EpiParams&, int*, cudaStream_t);
 // indexed by epilogue mode
 const LaunchFn kLaunch[] = {launch_mode<EPI_STORE>, launch_mode<EPI_SILU>,
                             launch_mode<EPI_SILU_F>, launch_mode<EPI_SILU_RES>,
@@ -503,10 +529,11 @@ bool launch_gemm_bf16(int mode, int M, int N, int K, const __nv_bfloat16* A, int
     } else {
       ta2 = ta;
     }
-    // default: <= 98 KB of stages, two CTAs per SM; the autotuner may ask for 2..4
-    const int stages = (stages_req >= 2 && stages_req <= 4) ? stages_req : (nbw > 128 ? 2 : 3);
-    const size_t smem = (size_t)stages * (TM * TK * 2 + (size_t)nbw * TK * 2) + 1024 + 256;
-    if (!kLaunch[mode](ta, ta2, tb, M, N, Ktot, k1c, n0, nbw, stages, smem, ep, err, s))
+    // default: 2 stages for 256-column slices (<= 96 KB: two CTAs per SM), 1 for the 4-warp
+    // CTAs of narrower slices (<= 32 KB: four per SM, which overlap each other's loads);
+    // the autotuner may ask for 2..4
+    const int stages = (stages_req >= 2 && stages_req <= 4) ? stages_req : (nbw > 128 ? 2 : 1);
+    if (!kLaunch[mode](ta, ta2, tb, M, N, Ktot, k1c, n0, nbw, stages, ep, err, s))
       return false;
     ff_count_launch(1);
   }
