@@ -156,8 +156,9 @@ int ff_energy_forces_graph(ff_ctx* ctx, const double* pos, double* E_sys, float*
 
 /* Autotuner of the tensor-core MLP GEMMs (precision 1): times complete E+F evaluations of
  * the bound system at `pos` (device) for each edge-tile configuration -- output-column
- * slice of 128 or 256 per CTA and 2, 3 or 4 shared-memory pipeline stages (which sets how
- * many CTAs share an SM) -- keeps the fastest for this context and reports it
+ * slice of 128 or 256 per CTA and the default (0: 2 stages for 256-column slices, 1 for
+ * narrower) or 2, 3 or 4 shared-memory pipeline stages (which sets how many CTAs share an
+ * SM) -- keeps the fastest for this context and reports it
  * (*slice, *stages; *ms_best = its mean evaluation time; any may be NULL).  For
  * precision 0 nothing is timed.  Synchronises `stream`.  Errors: as ff_energy_forces. */
 int ff_autotune(ff_ctx* ctx, const double* pos, int* slice, int* stages, double* ms_best,

@@ -1366,7 +1366,8 @@ int ff_autotune(ff_ctx* c, const double* pos, int* slice, int* stages, double* m
   if (!pos) return set_err(c, FF_ERR_ARG, "pos is null");
   cudaStream_t s = (cudaStream_t)stream;
   if (c->hp.precision == 1) {
-    static const int cand[][2] = {{256, 2}, {256, 3}, {256, 4}, {128, 2}, {128, 3}, {128, 4}};
+    // stages 0 = the launcher's default depth (2 for 256-column slices, 1 for narrower ones)
+    static const int cand[][2] = {{256, 0}, {256, 3}, {256, 4}, {128, 0}, {128, 2}, {128, 3}};
     cudaEvent_t e0, e1;
     FF_CK(c, cudaEventCreate(&e0));
     FF_CK(c, cudaEventCreate(&e1));

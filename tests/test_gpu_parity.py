@@ -367,7 +367,7 @@ def test_autotune_picks_a_valid_tile_and_keeps_results(ff):
     m, pos = _bind(ff, hp, s, precision=1)
     _, Ea0, F0 = m.energy_forces(pos)
     cfg = m.autotune(pos)
-    assert cfg["slice"] in (128, 256) and cfg["stages"] in (2, 3, 4)
+    assert cfg["slice"] in (128, 256) and cfg["stages"] in (0, 2, 3, 4)
     assert cfg["ms_per_evaluation"] > 0
     _, Ea1, F1 = m.energy_forces(pos)
     # the tile shape changes no arithmetic: the K loop and the accumulation are the same
