@@ -57,7 +57,11 @@ enum {
  *   latent[]          widths of the per-layer latent MLP (last must equal D)
  *   edge_eng[]        hidden widths of the linear edge-energy MLP (output width 1 implied)
  *   avg_num_neighbors nu, normalisation of the environment sum
- *   precision         0 = FP32 everywhere; 1 = BF16 latent MLPs with FP32 accumulation
+ *   precision         0 = FP32 everywhere; 1 = BF16 latent MLPs on the tensor cores with
+ *                     FP32 accumulation: GEMM operands, the residual stream x^L and the
+ *                     stored pre-activations are bf16; harmonics, edge features, CG
+ *                     products, tensor-product features and every gradient accumulator
+ *                     stay FP32, energy/virial/MD reductions FP64
  *   Every width must be a multiple of 16 and at most 512. */
 typedef struct {
   float rc, skin;
