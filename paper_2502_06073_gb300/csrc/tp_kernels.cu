@@ -275,7 +275,7 @@ k_env_tp_fwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
 // channel group) go to their own slice of gY (written once, no read-modify-write); the
 // geometric adjoint sums the slices in a fixed order.
 template <int LMAX, int INK, int OUTK, int CT>
-__global__ void __launch_bounds__(128, 6)
+__global__ void __launch_bounds__(128)
 k_env_tp_bwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
              const float* __restrict__ ef, const float* __restrict__ W, int ldw,
              const float* __restrict__ Vin, const float* __restrict__ thetaT,
