@@ -351,6 +351,34 @@ class Allegro64:
             out[i] = (Ei[a], cols[a], shs[a], g[off[a]:off[a + 1]])
         return out
 
+    def readout_scale(self, pos, Z, box, pbc, atoms, sys_ptr=None):
+        """Per atom i: sum over its edges and latent columns of |x^N_ijd w_d|, where
+        w = We.0 We.1 ... / prod sqrt(fan_in) is the linear edge-energy readout composed into
+        one vector (Table 1: no non-linearity), so E_ij = sum_d x^N_ijd w_d.  A relative
+        perturbation of at most u in every x^N component moves E_i by at most u times this
+        scale; it sets the scale of reduced-precision per-atom energy errors (the per-atom
+        energies themselves can be far smaller through cancellation)."""
+        pos = np.asarray(pos, dtype=np.float64)
+        nl = neighbors.neighbor_list(pos, box, pbc, self.hp["rc"], 0.0, sys_ptr,
+                                     centres=atoms)
+        ids = sorted(nl)
+        cnt = np.array([nl[i][0].shape[0] for i in ids])
+        if cnt.sum() == 0:
+            return {i: 0.0 for i in ids}
+        i_e = np.repeat(np.array(ids), cnt)
+        seg = np.repeat(np.arange(len(ids)), cnt)
+        j_e = np.concatenate([nl[i][0] for i in ids])
+        s_e = np.concatenate([nl[i][1] for i in ids])
+        rvec = self.edge_vectors(pos, box, i_e, j_e, s_e)
+        _, t = self._forward(rvec, np.asarray(Z)[i_e], np.asarray(Z)[j_e], seg, len(ids))
+        w = np.eye(self.D)
+        for k in range(len(self.hp["edge_eng"]) + 1):
+            W = self.params[f"We.{k}"]
+            w = w @ W / math.sqrt(W.shape[0])
+        sc = np.bincount(seg, np.abs(t["x"][-1] * w[:, 0][None, :]).sum(axis=1),
+                         minlength=len(ids))
+        return {i: float(sc[a]) for a, i in enumerate(ids)}
+
     def sampled_forces(self, pos, Z, box, pbc, atoms, sys_ptr=None):
         """Forces on a few atoms m, from the edges out of m and the edges into m."""
         pos = np.asarray(pos, dtype=np.float64)

@@ -289,6 +289,50 @@ def test_csh131072_adjoint_vs_oracle_gradient_on_32_atoms(ff, precision, fbar):
         assert np.abs(de).max() <= 4e-3 * emax
 
 
+BENCH_SIZES = {
+    "water12288": (lambda: synth.water_system(4096, L=49.67, seed=1001), "water12288"),
+    "molecules1024": (lambda: synth.molecules_system(1024, 1003), "molecules1024"),
+    "sio2_4194304": (lambda: synth.sio2_system(162, 4194304, 1004), "sio2_4194304"),
+}
+
+
+@pytest.mark.parametrize("key,precision", [("water12288", 0), ("water12288", 1),
+                                           ("molecules1024", 1), ("sio2_4194304", 0),
+                                           ("sio2_4194304", 1)])
+def test_bench_sizes_sampled_forces(ff, key, precision):
+    """The benchmark's workloads at full size, in the launch configuration it times
+    (per-step filtered list, default GEMM tiles, the chunk plan of the default budget):
+    forces and per-atom energies of 16 random atoms against the oracle.  FP32 bars for
+    precision 0; for precision 1 the stated force bar (RMSE and max <= 5 meV/A) and a
+    per-atom energy bar of 8 u S_i, u = 2^-8 the bf16 unit roundoff, S_i the oracle's
+    readout scale sum_j sum_d |x_ijd w_d| (first order, each bf16 rounding of a quantity
+    on the residual path moves E_i by at most u S_i; about 8 such roundings: the two-body
+    output and, per layer, the residual stream and the GEMM operand)."""
+    make, wl = BENCH_SIZES[key]
+    s = make()
+    hp = _hp("fm_water", wl)
+    m, pos = _bind(ff, hp, s, precision=precision)
+    _, Ea, F = m.energy_forces(pos)
+    atoms = np.random.default_rng(16).choice(s.n, 16, replace=False).tolist()
+    multi = s.sys_ptr.shape[0] > 2
+    Fr, Er = pool.sampled_forces(hp, 42, s.pos, s.Z, s.box, s.pbc, atoms,
+                                 s.sys_ptr if multi else None)
+    Fg = F.double().cpu().numpy()
+    Eg = Ea.double().cpu().numpy()
+    d = np.array([Fg[a] - Fr[a] for a in atoms])
+    de = np.array([Eg[a] - Er[a] for a in atoms])
+    emax = max(abs(Er[a]) for a in atoms)
+    if precision == 0:
+        assert np.abs(d).max() <= F_ABS, np.abs(d).max()
+        assert np.abs(de).max() <= EA_REL * emax
+    else:
+        assert np.sqrt((d ** 2).mean()) <= 5e-3 and np.abs(d).max() <= 5e-3
+        scale = Allegro64(hp, 42).readout_scale(s.pos, s.Z, s.box, s.pbc, atoms,
+                                                s.sys_ptr if multi else None)
+        for a, err in zip(atoms, de):
+            assert abs(err) <= 8 * 2.0 ** -8 * scale[a], (a, err, scale[a])
+
+
 def test_autograd_adjoint_with_several_chunks(ff):
     """With a small workspace budget the adjoint recomputes each chunk's forward; the
     gradient must equal the one-pass forces bit for bit."""

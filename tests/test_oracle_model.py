@@ -265,3 +265,22 @@ def test_nvt_drives_temperature_towards_target(small):
     v1 = synth.maxwell_boltzmann(m, 6000.0, seed=2)
     *_, ek, H, xi, _ = md.run_nvt(small, s.pos, v1, s.Z, s.box, s.pbc, m, 1.0, 30, 300.0, 10.0)
     assert ek.min() < 0.5 * md.kinetic(v1, m)
+
+
+def test_readout_scale_bounds_the_edge_energies():
+    """The readout scale sum_j sum_d |x_ijd w_d| bounds sum_j |E_ij| (triangle inequality,
+    E_ij = sum_d x_ijd w_d for the linear readout) and hence |E_i|; it is positive for an
+    atom with edges and zero for an isolated one."""
+    hp = synth.preset("small")
+    s = synth.config1_system()
+    model = Allegro64(hp, 42)
+    atoms = [0, 5, 17, 42]
+    sc = model.readout_scale(s.pos, s.Z, s.box, s.pbc, atoms)
+    terms = model.centre_terms(s.pos, s.Z, s.box, s.pbc, atoms)
+    for a in atoms:
+        assert sc[a] > 0 and abs(terms[a][0]) <= sc[a]
+    iso = np.array([[0.0, 0.0, 0.0], [20.0, 20.0, 20.0]])
+    sc2 = model.readout_scale(iso, np.array([1, 8]), np.array([40.0, 40.0, 40.0]),
+                              np.array([False, False, False]), [0, 1])
+    assert sc2[0] == 0.0 and sc2[1] == 0.0
+
