@@ -130,7 +130,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 }
 
 // Logistic sigmoid from the hardware exponential and fast division (a few ulp; the error
-// budget of this path is set by its bf16 operands, 2^-9 relative).  exp(-z) = inf for
+// budget of this path is set by its bf16 operands, unit roundoff 2^-8).  exp(-z) = inf for
 // z < -88 gives 0, the correct limit.
 __device__ __forceinline__ float sigm_fast(float z) { return __fdividef(1.f, 1.f + __expf(-z)); }
 __device__ __forceinline__ float silu_f(float z) { return z * sigm_fast(z); }
