@@ -262,7 +262,8 @@ int dalloc(ff_ctx* c, T** p, size_t count) {
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
-    return set_err(c, FF_ERR_OOM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) +
+    return set_err(c, FF_ERR_OOM,
+                   std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) +
                                       " bytes failed: " + cudaGetErrorString(e));
   }
   return FF_OK;
@@ -282,7 +283,10 @@ int validate(const ff_hparams& hp, std::string& why) {
   if (hp.poly_p < 2) { why = "poly_p must be >= 2"; return 0; }
   if (hp.lmax < 1 || hp.lmax > 2) { why = "lmax must be 1 or 2"; return 0; }
   if (hp.parity != 1) { why = "only parity = 1 (full O(3)) is supported"; return 0; }
-  if (hp.n_layers < 1 || hp.n_layers > FF_MAX_LAYERS) { why = "n_layers must be in 1..4"; return 0; }
+  if (hp.n_layers < 1 || hp.n_layers > FF_MAX_LAYERS) {
+    why = "n_layers must be in 1..4";
+    return 0;
+  }
   if (hp.channels != 16 && hp.channels != 32 && hp.channels != 64 && hp.channels != 128) {
     why = "channels must be 16, 32, 64 or 128"; return 0;
   }
@@ -290,9 +294,15 @@ int validate(const ff_hparams& hp, std::string& why) {
   if (hp.n_latent < 1 || hp.n_latent > 4) { why = "n_latent must be in 1..4"; return 0; }
   if (hp.n_edge_eng < 0 || hp.n_edge_eng > 2) { why = "n_edge_eng must be in 0..2"; return 0; }
   for (int k = 0; k < hp.n_two_body; ++k)
-    if (!width_ok(hp.two_body[k])) { why = "two_body widths must be multiples of 16 in 16..512"; return 0; }
+    if (!width_ok(hp.two_body[k])) {
+      why = "two_body widths must be multiples of 16 in 16..512";
+      return 0;
+    }
   for (int k = 0; k < hp.n_latent; ++k)
-    if (!width_ok(hp.latent[k])) { why = "latent widths must be multiples of 16 in 16..512"; return 0; }
+    if (!width_ok(hp.latent[k])) {
+      why = "latent widths must be multiples of 16 in 16..512";
+      return 0;
+    }
   for (int k = 0; k < hp.n_edge_eng; ++k)
     if (hp.edge_eng[k] < 1) { why = "edge_eng widths must be positive"; return 0; }
   if (hp.latent[hp.n_latent - 1] != hp.two_body[hp.n_two_body - 1]) {
@@ -1091,7 +1101,8 @@ int graph_eval(ff_ctx* c, const double* pos, double* E_sys, float* E_atom, float
       return r;
     }
     if (ec != cudaSuccess || !g)
-      return set_err(c, FF_ERR_CUDA, std::string("graph capture failed: ") + cudaGetErrorString(ec));
+      return set_err(c, FF_ERR_CUDA,
+                     std::string("graph capture failed: ") + cudaGetErrorString(ec));
     const cudaError_t ei = cudaGraphInstantiate(&c->gexec, g, 0);
     cudaGraphDestroy(g);
     if (ei != cudaSuccess) {
@@ -1134,7 +1145,8 @@ int ff_create(ff_ctx** out, const ff_hparams* hp, uint64_t seed) {
   std::string why;
   if (!validate(*hp, why)) return set_err(nullptr, FF_ERR_ARG, why);
   if (hp->precision == 1 && !gemm_bf16_available())
-    return set_err(nullptr, FF_ERR_ARG, "BF16 tensor-core path unavailable (no tensor-map encoder)");
+    return set_err(nullptr, FF_ERR_ARG,
+                   "BF16 tensor-core path unavailable (no tensor-map encoder)");
   ff_ctx* c = new ff_ctx();
   c->hp = *hp;
   c->seed = seed;
@@ -1169,7 +1181,8 @@ void ff_destroy(ff_ctx* c) {
   if (c->ev_a) cudaEventDestroy(c->ev_a);
   if (c->ev_b) cudaEventDestroy(c->ev_b);
   free_workspace(c);
-  dfree(c->wbuf); dfree(c->wbuf_b); dfree(c->Z); dfree(c->sys_ptr); dfree(c->sys_of); dfree(c->L_d); dfree(c->Lf_d);
+  dfree(c->wbuf); dfree(c->wbuf_b); dfree(c->Z); dfree(c->sys_ptr); dfree(c->sys_of);
+  dfree(c->L_d); dfree(c->Lf_d);
   dfree(c->vl_j); dfree(c->vl_s); dfree(c->vl_cnt); dfree(c->cell_of); dfree(c->img); dfree(c->xf);
   dfree(c->cell_count); dfree(c->cell_start); dfree(c->cell_fill); dfree(c->cell_atoms);
   dfree(c->xref); dfree(c->cnt); dfree(c->row_ptr); dfree(c->col); dfree(c->shift); dfree(c->src);
@@ -1246,8 +1259,10 @@ int ff_neighbors(ff_ctx* c, const double* pos, const int32_t* Z, int n_atoms, co
   for (int k = 0; k < n_sys; ++k)
     for (int i = sp[k]; i < sp[k + 1]; ++i) sof[i] = k;
   FF_CK(c, cudaMemcpyAsync(c->Z, Z, (size_t)n_atoms * sizeof(int), cudaMemcpyDeviceToDevice, s));
-  FF_CK(c, cudaMemcpy(c->sys_of, sof.data(), (size_t)n_atoms * sizeof(int), cudaMemcpyHostToDevice));
-  FF_CK(c, cudaMemcpy(c->sys_ptr, sp.data(), (size_t)(n_sys + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  FF_CK(c, cudaMemcpy(c->sys_of, sof.data(), (size_t)n_atoms * sizeof(int),
+                      cudaMemcpyHostToDevice));
+  FF_CK(c, cudaMemcpy(c->sys_ptr, sp.data(), (size_t)(n_sys + 1) * sizeof(int),
+                      cudaMemcpyHostToDevice));
   const float Lf[3] = {(float)box[0], (float)box[1], (float)box[2]};
   FF_CK(c, cudaMemcpy(c->L_d, box, 3 * sizeof(double), cudaMemcpyHostToDevice));
   FF_CK(c, cudaMemcpy(c->Lf_d, Lf, 3 * sizeof(float), cudaMemcpyHostToDevice));
@@ -1443,7 +1458,8 @@ int ff_md_nvt(ff_ctx* c, double* x, double* v, const double* mass, int n_steps, 
       FF_CK(c, cudaMemcpyAsync(E_pot + o, c->esys_tmp, c->n_sys * sizeof(double),
                                cudaMemcpyDeviceToDevice, s));
     if (E_kin)
-      FF_CK(c, cudaMemcpyAsync(E_kin + o, ke, c->n_sys * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      FF_CK(c, cudaMemcpyAsync(E_kin + o, ke, c->n_sys * sizeof(double),
+                               cudaMemcpyDeviceToDevice, s));
     if (H) launch_nh_energy(c->n_sys, c->sys_ptr, c->esys_tmp, ke, thermo, kT, tau_fs, H + o, s);
   }
   FF_CK(c, cudaGetLastError());
@@ -1484,7 +1500,8 @@ int ff_get_edges(ff_ctx* c, int64_t* n_edges, int32_t* row_ptr, int32_t* col, in
   }
   FF_CK(c, cudaStreamSynchronize(s));
   if (shift)
-    for (long long e = 0; e < c->E; ++e) ff_unpack_shift(packed[e], shift[3 * e], shift[3 * e + 1], shift[3 * e + 2]);
+    for (long long e = 0; e < c->E; ++e)
+      ff_unpack_shift(packed[e], shift[3 * e], shift[3 * e + 1], shift[3 * e + 2]);
   return FF_OK;
 }
 
@@ -1505,7 +1522,8 @@ int ff_profile_read(int64_t* launches, double* ms, int cap, int* n_classes) {
   std::lock_guard<std::mutex> g(p.mu);
   for (auto& pr : p.pending) {
     float t = 0.f;
-    if (cudaEventElapsedTime(&t, p.pool[pr.second].first, p.pool[pr.second].second) == cudaSuccess) {
+    if (cudaEventElapsedTime(&t, p.pool[pr.second].first, p.pool[pr.second].second) ==
+        cudaSuccess) {
       p.ms[pr.first] += t;
       p.launches[pr.first] += 1;
     } else {

@@ -134,7 +134,9 @@ void launch_gemm_f32(int mode, int M, int N, int K, const float* A, int lda, con
     case EPI_STORE: k_sgemm<EPI_STORE><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, ep); break;
     case EPI_SILU: k_sgemm<EPI_SILU><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, ep); break;
     case EPI_SILU_F: k_sgemm<EPI_SILU_F><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, ep); break;
-    case EPI_SILU_RES: k_sgemm<EPI_SILU_RES><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, ep); break;
+    case EPI_SILU_RES:
+      k_sgemm<EPI_SILU_RES><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, ep);
+      break;
     case EPI_DSILU: k_sgemm<EPI_DSILU><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, ep); break;
     case EPI_RES: k_sgemm<EPI_RES><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, ep); break;
     case EPI_ACC: k_sgemm<EPI_ACC><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, ep); break;

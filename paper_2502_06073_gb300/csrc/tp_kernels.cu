@@ -3,8 +3,8 @@
 // l = 2, full O(3); the layer structure follows the Allegro architecture the paper uses).
 //
 // One team of CT threads (16 or 32) owns one centre atom i and one group of CT channels
-// (C = 16: one team of 16; C = 32, 64, 128: C/32 teams of 32); thread owns channel c.  Because every edge of i is contiguous in the sorted edge list, the
-// environment sum
+// (C = 16: one team of 16; C = 32, 64, 128: C/32 teams of 32); thread owns channel c.
+// Because every edge of i is contiguous in the sorted edge list, the environment sum
 //     G_i[c, lm] = nu^(-1/2) sum_{k in N(i)} w_ik[l, c] Y_lm(u_ik)
 // is a register accumulation over the atom's segment (no atomics, fixed order), and the
 // tensor product of every edge of i with G_i follows in the same kernel:
@@ -39,7 +39,9 @@ __device__ __forceinline__ void cp_async16(float* smem, const float* gmem) {
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // Copy `rows` rows of CT floats (16-byte aligned; source rows `stride` floats apart) into a
 // dense [rows][CT] shared buffer with the CT lanes of a team.
@@ -482,9 +484,10 @@ void bwd_one(int n_atoms, int C, const int* row_ptr, int e0, const float* ef, co
 
 
 void launch_env_tp_fwd(int lmax, int in_kind, int out_kind, int C, int n_atoms,
-                       const int* row_ptr, int e0, const float* ef, const float* W, int ldw, const float* Vin,
-                       const float* theta, float* X, __nv_bfloat16* Xb, int ldx, int D,
-                       float* Vout, float* Gam, float inv_sqrt_nu, cudaStream_t s) {
+                       const int* row_ptr, int e0, const float* ef, const float* W, int ldw,
+                       const float* Vin, const float* theta, float* X, __nv_bfloat16* Xb,
+                       int ldx, int D, float* Vout, float* Gam, float inv_sqrt_nu,
+                       cudaStream_t s) {
   ProfScope ps_(PC_TP_FWD, s);
   if (n_atoms <= 0) return;
   FF_TP_DISPATCH(fwd_one, n_atoms, C, row_ptr, e0, ef, W, ldw, Vin, theta, X, Xb, ldx, D, Vout,
@@ -493,9 +496,9 @@ void launch_env_tp_fwd(int lmax, int in_kind, int out_kind, int C, int n_atoms,
 }
 
 void launch_env_tp_bwd(int lmax, int in_kind, int out_kind, int C, int n_atoms,
-                       const int* row_ptr, int e0, const float* ef, const float* W, int ldw, const float* Vin,
-                       const float* theta, const float* GX, int ldx, int D, const float* gVout,
-                       float* gVin, float* GW, __nv_bfloat16* GWb, float* gY_v0, float* gY_env,
+                       const int* row_ptr, int e0, const float* ef, const float* W, int ldw,
+                       const float* Vin, const float* theta, const float* GX, int ldx, int D,
+                       const float* gVout, float* gVin, float* GW, __nv_bfloat16* GWb, float* gY_v0, float* gY_env,
                        int gy_stride, const float* Gam, float inv_sqrt_nu, cudaStream_t s) {
   ProfScope ps_(PC_TP_BWD, s);
   if (n_atoms <= 0) return;
