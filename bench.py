@@ -484,8 +484,8 @@ def run_ours(args):
                        "dt_fs": dt_fs, "parallelism": f"replicas x{world}",
                        "path": "CUDA graph on the frozen Verlet list" if args.graph
                                else "per-step filtered list",
-                       "gemm_tiles": tuned or "default (256-column slices: 8-warp CTAs, 2 stages; "
-                                             "narrower: 4-warp CTAs, 1 stage)",
+                       "gemm_tiles": tuned or "default (128-column slices: 4-warp CTAs, 1 stage; "
+                                             "readout 256 columns: 8-warp CTAs, 2 stages)",
                        "l2": "flushed between timed steps (512 MiB write)"},
             "roofline": roof,
             "cpu_baseline": cpu,

@@ -227,7 +227,7 @@ struct ff_ctx {
   double* vir_part = nullptr;
   double* nh_buf = nullptr;     // NVT scratch: kinetic energy and scale factor per system
   // tensor-core GEMM tile configuration (set by ff_autotune)
-  int tune_slice = 256, tune_stages = 0;
+  int tune_slice = 128, tune_stages = 0;   // the autotuner's pick for 12,288-atom water
   const double* state_pos = nullptr;
   const double* md_force_pos = nullptr;
   long long md_force_gen = -1;

@@ -256,8 +256,8 @@ __host__ __device__ inline size_t gemm_pipe_bytes(int mode, int nw, int stages, 
 template <int MODE, int NW>
 __global__ void __launch_bounds__(32 * NW, 8 / NW * 2)
 k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
-          const __grid_constant__ CUtensorMap tmB, int M, int N, int K, int k1c, int n0, int nbw,
-          int stages, EpiParams ep, int* __restrict__ err) {
+          const __grid_constant__ CUtensorMap tmB, int M, int N, int K, int k1c, int nslices,
+          int nbw, int stages, EpiParams ep, int* __restrict__ err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t a_bytes = TM * TK * 2;
@@ -273,7 +273,8 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   __shared__ int s_fail;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * TM;
+  const int m0 = (blockIdx.x / nslices) * TM;
+  const int n0 = (blockIdx.x % nslices) * nbw;
   const uint32_t ncols = nbw <= 32 ? 32u : nbw <= 64 ? 64u : nbw <= 128 ? 128u : 256u;
 
   if (threadIdx.x == 0) {
@@ -463,7 +464,7 @@ bool make_map(CUtensorMap* m, const void* base, long long rows, int cols, int ld
 
 template <int MODE, int NW>
 bool launch_nw(const CUtensorMap& ta, const CUtensorMap& ta2, const CUtensorMap& tb, int M, int N,
-               int K, int k1c, int n0, int nbw, int stages, const EpiParams& ep, int* err,
+               int K, int k1c, int nslices, int nbw, int stages, const EpiParams& ep, int* err,
                cudaStream_t s) {
   static bool attr_set = false;
   if (!attr_set) {
@@ -474,20 +475,23 @@ bool launch_nw(const CUtensorMap& ta, const CUtensorMap& ta2, const CUtensorMap&
   }
   const size_t bytes = gemm_pipe_bytes(MODE, NW, stages, nbw) + 1024 + 256;   // align + bars
   if (bytes > 200 * 1024) return false;
-  k_gemm_tc<MODE, NW><<<ff_cdiv(M, TM), 32 * NW, bytes, s>>>(ta, ta2, tb, M, N, K, k1c, n0, nbw,
+  // one CTA per (row tile, column slice), the slices of a row tile adjacent so the second
+  // reads the A tile from L2
+  k_gemm_tc<MODE, NW><<<ff_cdiv(M, TM) * nslices, 32 * NW, bytes, s>>>(ta, ta2, tb, M, N, K, k1c,
+                                                                       nslices, nbw,
                                                               stages, ep, err);
   return true;
 }
 
 template <int MODE>
 bool launch_mode(const CUtensorMap& ta, const CUtensorMap& ta2, const CUtensorMap& tb, int M,
-                 int N, int K, int k1c, int n0, int nbw, int stages, const EpiParams& ep,
+                 int N, int K, int k1c, int nslices, int nbw, int stages, const EpiParams& ep,
                  int* err, cudaStream_t s) {
   if constexpr (MODE != EPI_HEAD) {   // the readout needs the 8-warp row reduction
     if (nbw <= 128)
-      return launch_nw<MODE, 4>(ta, ta2, tb, M, N, K, k1c, n0, nbw, stages, ep, err, s);
+      return launch_nw<MODE, 4>(ta, ta2, tb, M, N, K, k1c, nslices, nbw, stages, ep, err, s);
   }
-  return launch_nw<MODE, 8>(ta, ta2, tb, M, N, K, k1c, n0, nbw, stages, ep, err, s);
+  return launch_nw<MODE, 8>(ta, ta2, tb, M, N, K, k1c, nslices, nbw, stages, ep, err, s);
 }
 
 using LaunchFn = bool (*)(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, int, int,
@@ -520,22 +524,23 @@ bool launch_gemm_bf16(int mode, int M, int N, int K, const __nv_bfloat16* A, int
     if (N > 256) return false;
     slice = 256;
   }
-  for (int n0 = 0; n0 < N; n0 += slice) {
-    const int nbw = N - n0 < slice ? N - n0 : slice;
-    CUtensorMap ta, ta2, tb;
-    if (!make_map(&ta, A, M, K, lda, TM) || !make_map(&tb, Bt, N, Ktot, ldb, nbw)) return false;
-    if (A2) {
-      if (!make_map(&ta2, A2, M, K2, lda2, TM)) return false;
-    } else {
-      ta2 = ta;
-    }
-    // default: 2 stages for 256-column slices (<= 96 KB: two CTAs per SM), 1 for the 4-warp
-    // CTAs of narrower slices (<= 32 KB: four per SM, which overlap each other's loads);
-    // the autotuner may ask for 2..4
-    const int stages = (stages_req >= 2 && stages_req <= 4) ? stages_req : (nbw > 128 ? 2 : 1);
-    if (!kLaunch[mode](ta, ta2, tb, M, N, Ktot, k1c, n0, nbw, stages, ep, err, s))
-      return false;
-    ff_count_launch(1);
+  // all column slices in one launch; a partial last slice reads zero-filled B rows and
+  // masks its columns >= N
+  const int nbw = N < slice ? N : slice;
+  const int nslices = (N + nbw - 1) / nbw;
+  CUtensorMap ta, ta2, tb;
+  if (!make_map(&ta, A, M, K, lda, TM) || !make_map(&tb, Bt, N, Ktot, ldb, nbw)) return false;
+  if (A2) {
+    if (!make_map(&ta2, A2, M, K2, lda2, TM)) return false;
+  } else {
+    ta2 = ta;
   }
+  // default: 2 stages for 256-column slices (<= 96 KB: two CTAs per SM), 1 for the 4-warp
+  // CTAs of narrower slices (<= 32 KB: four per SM, which overlap each other's loads);
+  // the autotuner may ask for 2..4
+  const int stages = (stages_req >= 2 && stages_req <= 4) ? stages_req : (nbw > 128 ? 2 : 1);
+  if (!kLaunch[mode](ta, ta2, tb, M, N, Ktot, k1c, nslices, nbw, stages, ep, err, s))
+    return false;
+  ff_count_launch(1);
   return true;
 }
