@@ -3,8 +3,9 @@
 // residual update, SiLU' of the adjoint).
 //
 // C[M][N] = alpha * A[M][K] B[K][N]; A is edge-major (one row per edge), B the weight
-// matrix.  Tile 128 x 64 x 16, 256 threads, 8 x 4 outputs per thread, register
-// double-buffered global loads.  Requires K % 16 == 0, N % 4 == 0, lda/ldb % 4 == 0 and
+// matrix.  Tile 128 x 64 x 16, 256 threads, 8 x 4 outputs per thread (packed two-wide
+// FP32 FMAs over row pairs), register double-buffered global loads, three blocks per SM
+// (80 registers, no spills).  Requires K % 16 == 0, N % 4 == 0, lda/ldb % 4 == 0 and
 // 16-byte aligned A and B.
 #include "ff_internal.cuh"
 
@@ -44,7 +45,7 @@ __device__ __forceinline__ void epilogue(const EpiParams& ep, int row, int col, 
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 k_sgemm(int M, int N, int K, const float* __restrict__ A, int lda, const float* __restrict__ B,
         int ldb, EpiParams ep) {
   __shared__ __align__(16) float As[2][BK][BM + 4];
@@ -80,11 +81,13 @@ k_sgemm(int M, int N, int K, const float* __restrict__ A, int lda, const float* 
     *reinterpret_cast<float4*>(&Bs[buf][b_k][b_c]) = rb;
   };
 
-  float acc[8][4];
+  // acc[p][j] holds rows 2p and 2p+1 of column j: packed FP32 FMAs (two per instruction,
+  // each rounded as a scalar FMA) over the row pairs that one float4 of A delivers
+  float2 acc[4][4];
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
 
   const int nk = K / BK;
   load(0);
@@ -98,12 +101,14 @@ k_sgemm(int M, int N, int K, const float* __restrict__ A, int lda, const float* 
       const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 8]);
       const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 8 + 4]);
       const float4 b = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
-      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      const float bb[4] = {b.x, b.y, b.z, b.w};
+      const float2 a[4] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w),
+                           make_float2(a1.x, a1.y), make_float2(a1.z, a1.w)};
+      const float2 bb[4] = {make_float2(b.x, b.x), make_float2(b.y, b.y),
+                            make_float2(b.z, b.z), make_float2(b.w, b.w)};
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
+        for (int j = 0; j < 4; ++j) acc[i][j] = __ffma2_rn(a[i], bb[j], acc[i][j]);
     }
     if (kt + 1 < nk) {
       store(buf ^ 1);
@@ -117,7 +122,7 @@ k_sgemm(int M, int N, int K, const float* __restrict__ A, int lda, const float* 
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int c = col0 + tx * 4 + j;
-      if (c < N) epilogue<MODE>(ep, (int)r, c, acc[i][j]);
+      if (c < N) epilogue<MODE>(ep, (int)r, c, (i & 1) ? acc[i >> 1][j].y : acc[i >> 1][j].x);
     }
   }
 }
