@@ -40,7 +40,7 @@ enum {
   FF_ERR_OOM = -3,       /* device allocation failed */
   FF_ERR_CUDA = -4,      /* a CUDA runtime call failed (message has the CUDA error) */
   FF_ERR_CAPACITY = -5,  /* a neighbour count exceeded the per-atom limit FF_MAX_NEIGHBORS */
-  FF_ERR_NONFINITE = -6, /* non-finite energy or force */
+  FF_ERR_NONFINITE = -6, /* non-finite position, energy or force */
   FF_ERR_STATE = -7,     /* call order violated (e.g. forces before any energy call) */
   FF_ERR_BOX = -8        /* image shift out of range (|s| > 100 box lengths) */
 };

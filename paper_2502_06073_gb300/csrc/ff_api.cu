@@ -635,6 +635,7 @@ int read_flags(ff_ctx* c, cudaStream_t s) {
     if (e & 8) return set_err(c, FF_ERR_STATE, "reverse edge missing (asymmetric list)");
     if (e & 32) return set_err(c, FF_ERR_NONFINITE, "non-finite force");
     if (e & 64) return set_err(c, FF_ERR_CUDA, "tensor-core GEMM pipeline wait timed out");
+    if (e & 128) return set_err(c, FF_ERR_NONFINITE, "non-finite position");
   }
   return FF_OK;
 }
@@ -671,6 +672,9 @@ void setup_grid(ff_ctx* c) {
 }
 
 int build_verlet(ff_ctx* c, const double* pos, cudaStream_t s) {
+  // positions are binned only once they are known to be finite
+  launch_check_pos(pos, c->n, c->flags, s);
+  FF_TRY(read_flags(c, s));
   for (int attempt = 0; attempt < 3; ++attempt) {
     if (c->allpairs) {
       launch_pos_to_f32(pos, c->n, c->xf, s);

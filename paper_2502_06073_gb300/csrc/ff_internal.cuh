@@ -116,6 +116,8 @@ void launch_verlet_allpairs(int n, const int* sys_of, const int* sys_ptr, const 
                             float rl2, int vmax, int* vl_j, int* vl_s, int* vl_cnt,
                             int* err, cudaStream_t s);
 void launch_pos_to_f32(const double* pos, int n, float4* xf, cudaStream_t s);
+// sets bit 128 of *err if any coordinate is not finite
+void launch_check_pos(const double* pos, int n, int* err, cudaStream_t s);
 void launch_filter(int pass, int n, const float4* xf, const float* Lf, float rc2, int vmax,
                    const int* vl_j, const int* vl_s, const int* vl_cnt, int* cnt,
                    const int* row_ptr, int* col, int* shift, int* src, cudaStream_t s);

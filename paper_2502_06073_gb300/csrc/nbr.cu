@@ -318,7 +318,13 @@ __global__ void k_disp_check(const double* __restrict__ x, const double* __restr
   const double dx = x[3 * (long long)i] - xref[3 * (long long)i];
   const double dy = x[3 * (long long)i + 1] - xref[3 * (long long)i + 1];
   const double dz = x[3 * (long long)i + 2] - xref[3 * (long long)i + 2];
-  if (dx * dx + dy * dy + dz * dz > lim2) atomicOr(flag, 1);
+  // a non-finite position also asks for a rebuild, which reports it
+  if (!(dx * dx + dy * dy + dz * dz <= lim2)) atomicOr(flag, 1);
+}
+
+__global__ void k_check_pos(const double* __restrict__ x, long long n3, int* __restrict__ err) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n3 && !isfinite(x[t])) atomicOr(err, 128);
 }
 
 __global__ void k_check_species(const int* __restrict__ Z, int n, int* __restrict__ err) {
@@ -354,6 +360,13 @@ void launch_pos_to_f32(const double* pos, int n, float4* xf, cudaStream_t s) {
   ProfScope ps_(PC_NEIGHBOR, s);
   if (n <= 0) return;
   k_pos_to_f32<<<ff_cdiv(n, 256), 256, 0, s>>>(pos, n, xf);
+  ff_count_launch(1);
+}
+
+void launch_check_pos(const double* pos, int n, int* err, cudaStream_t s) {
+  ProfScope ps_(PC_NEIGHBOR, s);
+  if (n <= 0) return;
+  k_check_pos<<<ff_cdiv(3LL * n, 256), 256, 0, s>>>(pos, 3LL * n, err);
   ff_count_launch(1);
 }
 

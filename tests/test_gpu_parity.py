@@ -226,6 +226,35 @@ def test_errors_are_reported(ff):
         m.bind(_dev(s.pos, torch.float64), _dev(bad, torch.int32), s.box, s.pbc)
 
 
+def test_capacity_and_nonfinite_errors(ff):
+    """An atom with more than FF_MAX_NEIGHBORS (1024) neighbours within rc + skin is
+    reported (the list kernels only count past the capacity), a non-finite position is
+    reported before it is binned, and a non-finite velocity is reported at the rebuild the
+    displacement check then asks for."""
+    rng = np.random.default_rng(7)
+    pts = rng.uniform(-1.0, 1.0, size=(6000, 3))
+    pts = pts[np.linalg.norm(pts, axis=1) <= 1.0][:1100] * 4.5 + 20.0   # 1,100 atoms, r 4.5 A
+    s = synth.System("dense", np.asarray(pts, np.float32).astype(np.float64),
+                     np.full(pts.shape[0], 1, np.int32), np.array([40.0, 40.0, 40.0]),
+                     np.array([False, False, False]), np.array([0, pts.shape[0]], np.int32))
+    m = ff.FFModel(synth.preset("small"), seed=1)
+    with pytest.raises(ff.FFError, match="FF_ERR_CAPACITY"):
+        m.bind(_dev(s.pos, torch.float64), _dev(s.Z, torch.int32), s.box, s.pbc)
+    c = synth.config1_system()
+    bad = c.pos.copy()
+    bad[5, 1] = np.nan
+    m2 = ff.FFModel(synth.preset("small"), seed=1)
+    with pytest.raises(ff.FFError, match="FF_ERR_NONFINITE"):
+        m2.bind(_dev(bad, torch.float64), _dev(c.Z, torch.int32), c.box, c.pbc)
+    hp = synth.preset("small", skin=0.5)
+    m3, x = _bind(ff, hp, c)
+    v = torch.zeros_like(x)
+    v[3, 0] = float("nan")
+    mass = _dev(c.masses, torch.float64)
+    with pytest.raises(ff.FFError, match="FF_ERR_NONFINITE"):
+        m3.md(x, v, mass, 2, 0.5)
+
+
 def test_md_matches_oracle_trajectory(ff):
     s = synth.config1_system()
     hp = synth.preset("small", skin=0.5)
