@@ -5,12 +5,13 @@
 // pre-activations are stored (SiLU modes) and read back (SiLU') in bf16, and the residual
 // stream x^L is read in bf16 (the copy that is also the next GEMM's operand).
 //
-// One CTA (4 warps) owns a 128-row tile and one slice of at most 256 output columns:
+// One CTA (4 or 8 warps) owns a 128-row tile and one slice of at most 256 output columns;
+// the slices of a row tile are adjacent CTAs of one launch:
 //   warp 0 / lane 0   TMA producer: A and B K-chunks of 64 elements (128 B rows,
 //                     128-byte swizzle) into a ring of `stages` shared-memory stages;
 //   warp 1 / lane 0   MMA issuer: 4 x tcgen05.mma (M=128, N=slice, K=16) per chunk,
 //                     tcgen05.commit releases the stage, a final commit the accumulator;
-//   all 4 warps       epilogue: tcgen05.ld of their 32 TMEM lanes (= tile rows), 32
+//   all warps         epilogue: tcgen05.ld of their 32 TMEM lanes (= tile rows), 32
 //                     columns at a time, fused element-wise op, stores.
 // Every mbarrier wait is bounded; a timeout sets bit 64 of the error word and the CTA
 // drains what it issued, frees its tensor memory and returns.
