@@ -123,16 +123,26 @@ def test_energy_forces_full(ff, key, wl):
     _check_ef(Es, Ea, F, E_ref, Ea_ref, F_ref, key, s.sys_ptr)
 
 
-@pytest.mark.parametrize("n_layers,lmax", [(1, 2), (4, 2), (1, 1), (4, 1)])
-def test_layer_counts_full(ff, n_layers, lmax):
+@pytest.mark.parametrize("n_layers,lmax,two_body,precision",
+                         [(1, 2, [32, 32], 0), (4, 2, [32, 32], 0), (1, 1, [32, 32], 0),
+                          (4, 1, [32, 32], 0), (2, 2, [32], 0), (2, 2, [32], 1)])
+def test_layer_counts_full(ff, n_layers, lmax, two_body, precision):
     """1- and 4-layer models: every tensor-product layer kind (a single last layer; the
-    first, middle and pruned layer before the last, and a last layer reading it)."""
+    first, middle and pruned layer before the last, and a last layer reading it); and a
+    two-body MLP of a single layer (the embedding layer is also the output) in both
+    precisions."""
     s = synth.config1_system()
-    hp = _hp("small", "cubic96", n_layers=n_layers, lmax=lmax)
-    m, pos = _bind(ff, hp, s)
+    hp = _hp("small", "cubic96", n_layers=n_layers, lmax=lmax, two_body=two_body)
+    m, pos = _bind(ff, hp, s, precision=precision)
     Es, Ea, F = m.energy_forces(pos)
     E_ref, Ea_ref, F_ref = pool.evaluate(hp, 42, s.pos, s.Z, s.box, s.pbc, s.sys_ptr)
-    _check_ef(Es, Ea, F, E_ref, Ea_ref, F_ref, f"L{n_layers} lmax{lmax}", s.sys_ptr)
+    if precision == 0:
+        _check_ef(Es, Ea, F, E_ref, Ea_ref, F_ref, f"L{n_layers} lmax{lmax}", s.sys_ptr)
+    else:
+        d = F.double().cpu().numpy() - F_ref
+        assert np.sqrt((d ** 2).mean()) <= 5e-3 and np.abs(d).max() <= 5e-3
+        Ea = Ea.double().cpu().numpy()
+        assert np.abs(Ea - Ea_ref).max() <= 4e-3 * np.abs(Ea_ref).max()
 
 
 def test_water4095_energy_and_sampled_forces(ff):
