@@ -105,12 +105,14 @@ __device__ __forceinline__ int rs_index(int lane) {
   return (lane & 15) < 9 ? (lane & 15) : -1;
 }
 
-// Per-edge shared-memory record of a team: the edge-feature row (24 floats: the harmonics
-// sit at FF_EF_Y), the team's slice of the env weights [(lmax+1)][CT], and, as the kernel
-// needs them, the input features V [DIN][CT], the scalar gradients [NS][CT] and the output
-// feature gradients [DOUT][CT].  Edges stream through a ring of NSTG such records with
-// cp.async, NSTG - 1 edges ahead of the one in use, so no global load of the edge loop is
-// waited for in the iteration that uses it.
+// Per-edge shared-memory record of a team: for the first layer (V^0 = w (x) Y formed in
+// the kernel) the edge-feature row (24 floats: the harmonics sit at FF_EF_Y) and the team's
+// slice of the env weights [(lmax+1)][CT]; for later layers the input features V [DIN][CT]
+// instead (the tensor product of a later layer reads neither the harmonics nor its env
+// weights); and, in the adjoint, the scalar gradients [NS][CT] and the output feature
+// gradients [DOUT][CT].  Edges stream through a ring of NSTG such records with cp.async,
+// NSTG - 1 edges ahead of the one in use, so no global load of the edge loop is waited for
+// in the iteration that uses it.
 // Layer kinds.  INK: 0 = V^0 = w (x) Y formed in the kernel (first layer), 1 = outputs of
 // the first layer, 2 = outputs of a later layer, 3 = natural-parity irreps read from the
 // previous layer (the last layer after a layer of output kind 1).  OUTK: 0 = all reachable
@@ -124,8 +126,8 @@ struct EdgeRec {
   using K = TPK<LMAX, INK, OUTK>;
   static constexpr bool LAST = OUTK == 2;
   static constexpr int TEAMS = 128 / CT;
-  static constexpr int OFF_W = FF_EF_STRIDE;
-  static constexpr int OFF_V = OFF_W + (LMAX + 1) * CT;
+  static constexpr int OFF_W = INK == 0 ? FF_EF_STRIDE : 0;
+  static constexpr int OFF_V = INK == 0 ? OFF_W + (LMAX + 1) * CT : 0;
   static constexpr int OFF_GS = OFF_V + (INK > 0 ? K::DIN * CT : 0);
   static constexpr int OFF_GVO = OFF_GS + (BWD ? K::NS * CT : 0);
   static constexpr int SST = OFF_GVO + ((BWD && !LAST) ? K::DOUT * CT : 0);
@@ -135,13 +137,14 @@ struct EdgeRec {
   static constexpr int NSTG_FIT = BUDGET / (TEAMS * SST * 4);
   static constexpr int NSTG = NSTG_FIT < 2 ? 2 : (NSTG_FIT > 4 ? 4 : NSTG_FIT);
   // the passes that read only the edge-feature row and the env weights use the same
-  // buffer as a deeper ring of smaller records
+  // buffer as a deeper ring of smaller records (2 to 8 of them)
   static constexpr int SR = FF_EF_STRIDE + (LMAX + 1) * CT;
   static constexpr int NSR_FIT = NSTG * SST / SR;
-  static constexpr int NSR = NSR_FIT > 8 ? 8 : NSR_FIT;
-  static_assert(NSR >= 2, "ring of edge-feature / env-weight records");
-  static_assert(FF_EF_STRIDE % 4 == 0, "edge-feature rows must be 16-byte multiples");
-  static_assert(TEAMS * SST * NSTG * 4 <= 48 * 1024, "static shared memory");
+  static constexpr int NSR = NSR_FIT < 2 ? 2 : (NSR_FIT > 8 ? 8 : NSR_FIT);
+  static constexpr int BUF = NSTG * SST > NSR * SR ? NSTG * SST : NSR * SR;
+  static_assert(FF_EF_STRIDE % 4 == 0 && SST % 4 == 0 && SR % 4 == 0,
+                "records must be 16-byte multiples");
+  static_assert(TEAMS * BUF * 4 <= 48 * 1024, "static shared memory");
 };
 
 template <int LMAX, int CT>
@@ -159,10 +162,13 @@ __device__ __forceinline__ void stage_edge(float* rec, int e, int lane, int C, i
                                            const float* gvout) {
   using R = EdgeRec<LMAX, INK, OUTK, CT, BWD>;
   using K = TPK<LMAX, INK, OUTK>;
-  if (lane < FF_EF_STRIDE / 4)
-    cp_async16(rec + 4 * lane, ef + (size_t)e * FF_EF_STRIDE + 4 * lane);
-  stage<CT>(rec + R::OFF_W, W + (size_t)e * ldw + grp * CT, LMAX + 1, C, lane);
-  if (INK > 0) stage<CT>(rec + R::OFF_V, vin + (size_t)e * K::DIN * C, K::DIN, C, lane);
+  if (INK == 0) {
+    if (lane < FF_EF_STRIDE / 4)
+      cp_async16(rec + 4 * lane, ef + (size_t)e * FF_EF_STRIDE + 4 * lane);
+    stage<CT>(rec + R::OFF_W, W + (size_t)e * ldw + grp * CT, LMAX + 1, C, lane);
+  } else {
+    stage<CT>(rec + R::OFF_V, vin + (size_t)e * K::DIN * C, K::DIN, C, lane);
+  }
   if (BWD) {
     stage<CT>(rec + R::OFF_GS, GX + (size_t)e * ldx + D + grp * CT, K::NS, C, lane);
     if (!R::LAST) stage<CT>(rec + R::OFF_GVO, gvout + (size_t)e * K::DOUT * C, K::DOUT, C, lane);
@@ -181,7 +187,7 @@ k_env_tp_fwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
   constexpr bool LAST = R::LAST;
   constexpr int NY = (LMAX + 1) * (LMAX + 1);
   constexpr int NSTG = R::NSTG, SST = R::SST;
-  __shared__ __align__(16) float s_rec[R::TEAMS * NSTG * SST];
+  __shared__ __align__(16) float s_rec[R::TEAMS * R::BUF];
   const int G = C / CT;
   const int team = threadIdx.x / CT, lane = threadIdx.x % CT;
   const long long tg = (long long)blockIdx.x * R::TEAMS + team;
@@ -189,7 +195,7 @@ k_env_tp_fwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
   if (a >= n_atoms) return;
   const int c = grp * CT + lane;
   const int eb = row_ptr[a] - e0, ee = row_ptr[a + 1] - e0;
-  float* buf = s_rec + team * NSTG * SST;
+  float* buf = s_rec + team * R::BUF;
   const float* vin = Vin + grp * CT;
   auto fetch = [&](int e, int slot) {
     stage_edge<LMAX, INK, OUTK, CT, false>(buf + slot * SST, e, lane, C, grp, ef, W, ldw, vin,
@@ -290,7 +296,7 @@ k_env_tp_bwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
   constexpr bool LAST = R::LAST;
   constexpr int NY = (LMAX + 1) * (LMAX + 1);
   constexpr int NSTG = R::NSTG, SST = R::SST;
-  __shared__ __align__(16) float s_rec[R::TEAMS * NSTG * SST];
+  __shared__ __align__(16) float s_rec[R::TEAMS * R::BUF];
   const int G = C / CT;
   const int team = threadIdx.x / CT, lane = threadIdx.x % CT;
   const long long tg = (long long)blockIdx.x * R::TEAMS + team;
@@ -298,7 +304,7 @@ k_env_tp_bwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
   if (a >= n_atoms) return;
   const int c = grp * CT + lane;
   const int eb = row_ptr[a] - e0, ee = row_ptr[a + 1] - e0;
-  float* buf = s_rec + team * NSTG * SST;
+  float* buf = s_rec + team * R::BUF;
   const float* vin = Vin + grp * CT;
   const float* gvout = gVout + grp * CT;
   auto fetch = [&](int e, int slot) {
@@ -328,7 +334,7 @@ k_env_tp_bwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
     float v[K::DIN], gv[K::DIN];
     float wl[LMAX + 1];
 #pragma unroll
-    for (int l = 0; l <= LMAX; ++l) wl[l] = rec[R::OFF_W + l * CT + lane];
+    for (int l = 0; l <= LMAX; ++l) wl[l] = INK == 0 ? rec[R::OFF_W + l * CT + lane] : 0.f;
     if (INK == 0) {
 #pragma unroll
       for (int l = 0; l <= LMAX; ++l)
