@@ -31,6 +31,9 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
+# the headline metric; both arms print it on the same workload, unit and direction
+METRIC = "MD atom-steps/s (E+F, 1 GB300) at stated force error vs FP64 oracle; % roofline"
+UNIT = "atom-steps/s"
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.070 GHz (maximum SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
@@ -241,7 +244,7 @@ def oracle_leg(wl, pos, F_gpu, n_atoms=24, workers=None):
             Fm = Fm - g[col == m].sum(axis=0)
         d.append(F_gpu[m] - Fm)
     d = np.array(d)
-    cpu = {"value": len(centres) / dt, "unit": "atom-steps/s", "cores": workers,
+    cpu = {"value": len(centres) / dt, "unit": UNIT, "cores": workers,
            "kind": "oracle",
            "sample": f"E+F of {len(centres)} centres of {wl} (the neighbourhoods of {n_atoms} "
                      f"atoms), {dt:.1f} s on a spawn pool of {workers} processes"}
@@ -276,17 +279,19 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     value = n * args.steps / dt
     line = {
-        "impl": "reference", "metric": "MD atom-steps/s (E+F)", "value": value,
-        "unit": "atom-steps/s", "n_gpus": args.gpus, "steps": args.steps,
+        "impl": "reference", "metric": METRIC, "value": value,
+        "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded), random-init weights",
         "config": {"workload": wl, "desc": WORKLOADS[wl]["desc"], "model": WORKLOADS[wl]["model"],
+                   "atoms": s.n, "dt_fs": WORKLOADS[wl].get("dt_fs", 0.5),
+                   "parallelism": f"{workers} host processes (rank 0)",
                    "sample_atoms_per_step": n},
-        "cpu_baseline": {"value": value, "unit": "atom-steps/s", "cores": workers,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers,
                          "kind": "oracle",
                          "sample": f"E+F of centres 0..{n - 1} of {wl} per step"},
-        "e2e": {"value": value, "unit": "atom-steps/s", "h2d_bytes_per_step": 0,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -481,8 +486,8 @@ def run_ours(args):
 
     if rank == 0:
         line = {
-            "metric": "MD atom-steps/s (E+F, velocity Verlet)", "value": value,
-            "unit": "atom-steps/s", "n_gpus": world, "steps": args.steps,
+            "metric": METRIC, "value": value,
+            "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == 0 else "bf16-mlp/f32",
@@ -497,7 +502,7 @@ def run_ours(args):
                        "l2": "flushed between timed steps (512 MiB write)"},
             "roofline": roof,
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e, "unit": "atom-steps/s", "h2d_bytes_per_step": h2d,
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "clocks": clk,
