@@ -1,6 +1,6 @@
 """Host-side checks of the library: it builds for sm_103a, loads without a GPU, exports
-every entry point declared in include/ff.h, validates hyperparameters before touching the
-device, and its generated tensor-product tables agree with the oracle's coupling tensors
+every entry point declared in include/ff.h, validates hyperparameters and null or
+out-of-range arguments before touching the device, and its generated tensor-product tables agree with the oracle's coupling tensors
 (two independent constructions: Racah formula vs Wigner-matrix null space)."""
 import ctypes
 import importlib.util
@@ -123,3 +123,57 @@ def test_committed_tp_header_is_current(tmp_path):
     out = tmp_path / "tp_gen.cuh"
     gen.main(str(out))
     assert out.read_text() == open(os.path.join(CSRC, "tp_gen.cuh")).read()
+
+
+def test_null_context_and_argument_errors(lib):
+    """Every entry point that takes a context rejects a null one with FF_ERR_ARG before any
+    device work; the argument checks that need no device answer the same way on a host
+    without a GPU."""
+    import synth
+    import paper_2502_06073_gb300 as ff
+    ERR_ARG = -1
+    zeros = {ctypes.c_void_p: None, ctypes.c_int: 0, ctypes.c_int64: 0, ctypes.c_double: 0.0,
+             ctypes.c_float: 0.0, ctypes.c_size_t: 0, ctypes.c_uint64: 0,
+             ctypes.c_char_p: None}
+    takes_ctx = ("ff_neighbors", "ff_energy_forces", "ff_forces", "ff_md_step",
+                 "ff_export_params", "ff_get_edges", "ff_energy_forces_graph", "ff_set_graph",
+                 "ff_autotune", "ff_virial", "ff_md_nvt")
+    for name in takes_ctx:
+        fn = getattr(lib, name)
+        args = [zeros.get(t) for t in fn.argtypes]
+        assert fn(*args) == ERR_ARG, name
+    lib.ff_destroy(None)
+    assert isinstance(lib.ff_last_error(None), bytes)
+    # ff_create: null output or hyperparameters
+    h = ctypes.c_void_p()
+    st = ff.hparams_struct(synth.preset("small"))
+    assert lib.ff_create(None, ctypes.byref(st), 1) == ERR_ARG
+    assert lib.ff_create(ctypes.byref(h), None, 1) == ERR_ARG and not h.value
+    # profiler: the class table and a too-small read buffer
+    n = ctypes.c_int()
+    one = (ctypes.c_int64 * 1)()
+    onef = (ctypes.c_double * 1)()
+    assert lib.ff_profile_read(one, onef, 1, ctypes.byref(n)) == ERR_ARG
+    assert n.value >= 2
+    names = [lib.ff_profile_class(k).decode() for k in range(n.value)]
+    assert all(names) and len(set(names)) == n.value
+    assert lib.ff_profile_class(-1) == b"" and lib.ff_profile_class(n.value) == b""
+    # ff_neighbors_noalloc validates its arguments before it asks for a device
+    dummy = ctypes.c_void_p(16)           # never dereferenced on these paths
+    ne = ctypes.c_int64()
+    msg = ctypes.create_string_buffer(256)
+    box = (ctypes.c_double * 3)(20.0, 20.0, 20.0)
+    pbc = (ctypes.c_int * 3)(1, 1, 1)
+
+    def noalloc(pos=dummy, n_atoms=10, box_=box, pbc_=pbc, rc=5.0, row_ptr=dummy):
+        msg.value = b""
+        return lib.ff_neighbors_noalloc(pos, n_atoms, box_, pbc_, rc, row_ptr, None, None, 0,
+                                        ctypes.byref(ne), msg, 256, None)
+
+    assert noalloc(pos=None) == ERR_ARG and msg.value
+    assert noalloc(row_ptr=None) == ERR_ARG and msg.value
+    assert noalloc(n_atoms=0) == ERR_ARG
+    assert noalloc(n_atoms=4097) == ERR_ARG and b"FF_NOALLOC_MAX_ATOMS" in msg.value
+    assert noalloc(rc=0.0) == ERR_ARG and b"rc" in msg.value
+    assert noalloc(box_=(ctypes.c_double * 3)(20.0, -1.0, 20.0)) == ERR_ARG
+    assert noalloc(pbc_=(ctypes.c_int * 3)(1, 2, 1)) == ERR_ARG
