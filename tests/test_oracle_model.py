@@ -6,7 +6,7 @@ force, invariance of E and covariance of F under rotations, inversion, translati
 permutations, extensivity under periodic replication, strict locality, the isolated
 atom, the dimer (forces along the bond, smooth decay at the cutoff), the pair-potential
 special case with the environment switched off, and NVE energy conservation with
-fluctuations that scale as dt^2.
+fluctuations that scale as dt^2 and no secular drift over a long run.
 """
 import itertools
 
@@ -203,6 +203,26 @@ def test_nve_energy_fluctuation_scales_dt2(small):
         et = ep + ek
         fl.append(et.max() - et.min())
     assert 3.0 < fl[0] / fl[1] < 5.0, fl
+
+
+@pytest.mark.slow
+def test_nve_no_secular_drift(small):
+    """Velocity Verlet is symplectic: over many steps the total energy fluctuates about a
+    constant without a trend.  Eight atoms in a periodic 6.5 A box (they keep
+    interacting through the images), 800 steps of 1 fs from 300 K: the fitted linear drift
+    over the run is far below the fluctuation, and the fluctuation is small next to the
+    potential-energy excursions it is made of."""
+    s = synth.lattice_system("box8", (2, 2, 2), 3.25, 8, [1, 6, 8, 14], 21)
+    m = s.masses
+    v0 = synth.maxwell_boltzmann(m, 300.0, seed=3)
+    n = 800
+    _, _, ep, ek = md.run_nve(small, s.pos, v0, s.Z, s.box, s.pbc, m, 1.0, n)
+    et = ep + ek
+    slope = np.polyfit(np.arange(n, dtype=np.float64), et, 1)[0]
+    assert abs(slope * n) < 0.25 * et.std(), (slope * n, et.std())
+    assert et.max() - et.min() < 5e-3 * (ep.max() - ep.min())
+    # the two halves of the run have the same mean energy within the fluctuation
+    assert abs(et[: n // 2].mean() - et[n // 2:].mean()) < 0.25 * et.std()
 
 
 def test_virial_matches_strain_derivative_cluster(small):
