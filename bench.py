@@ -1,13 +1,17 @@
 #!/usr/bin/env python3
 """MD throughput of the Allegro-FM energy/force path on GB300 (one JSON line on stdout).
 
-Workload (default): water-like fluid, 4,096 H2O = 12,288 atoms in a periodic cube of
-49.67 A (1.0 g/cm^3), l<=2 / 3-layer / 32-channel model, rc 6 A, skin 1 A, seeded
-random-init weights; velocity Verlet at 0.5 fs from 300 K.  One step = kick, drift,
-neighbour maintenance, energies + forces (forward + hand-written adjoint), kick.
+Workload (default): the large NVE MD system, a 4,194,304-atom SiO2-like amorphous solid
+(1,398,101 Si + 2,796,203 O on a jittered 162^3 lattice, 2.2 g/cm^3, periodic cube of
+398.75 A), l<=2 / 3-layer / 32-channel model (rc 6 A, skin 1 A, seeded random-init
+weights) with BF16 tensor-core MLPs and the FP32 adjoint; velocity Verlet at 1 fs from
+300 K.  One step = kick, drift, neighbour maintenance, energies (per atom and per system)
++ forces (forward + hand-written adjoint), kick.  After the BF16 timing the same
+workload is timed on the plain FP32 path (a few steps) and both force fields are
+compared with the FP64 oracle on sampled atoms.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload NAME] [--precision 0|1]
+                    [--workload NAME] [--precision 0|1] [--fp32-steps K32]
 
 Under torchrun (N > 1) every rank runs an independent replica (weak scaling); rank 0
 prints the line with the max-over-ranks time.  --impl reference times the FP64 CPU
@@ -82,6 +86,34 @@ def gemm_flops_per_edge(hp):
     mac = sum(tb[k - 1] * tb[k] for k in range(1, len(tb)))
     per_layer = D * ldw + ldx * lat[0] + sum(lat[k - 1] * lat[k] for k in range(1, len(lat)))
     mac += hp["n_layers"] * per_layer
+    return 2 * 2 * mac
+
+
+def method_flops_per_edge(hp):
+    """Algorithmic FLOPs per edge of one E+F evaluation on the matrix units: every dense
+    layer of the method counted as the model defines it -- the radial input layer of the
+    two-body MLP (n_basis -> first width; the species one-hot rows are lookups), its hidden
+    layers, per interaction layer the environment projection and the latent MLP over
+    [x | scalars], and the edge-energy MLP (hidden widths -> 1) -- forward plus the
+    adjoint's input gradients of the same shapes (2 FLOP per multiply-add, x2 for the
+    adjoint).  Recomputation and the folding of the linear readout into one vector are
+    implementation choices and are not counted."""
+    tb, lat, ee = hp["two_body"], hp["latent"], list(hp["edge_eng"])
+    D = tb[-1]
+    C, lmax = hp["channels"], hp["lmax"]
+    ldw = (lmax + 1) * C
+    mac = hp["n_basis"] * tb[0]
+    mac += sum(tb[k - 1] * tb[k] for k in range(1, len(tb)))
+    fan = D + ldw
+    per_layer = D * ldw
+    for w in lat:
+        per_layer += fan * w
+        fan = w
+    mac += hp["n_layers"] * per_layer
+    fan = D
+    for w in ee + [1]:
+        mac += fan * w
+        fan = w
     return 2 * 2 * mac
 
 
@@ -219,9 +251,10 @@ def traffic_per_edge(kernel):
 
 
 # ------------------------------------------------------------------------- oracle arm
-def oracle_leg(wl, pos, F_gpu, n_atoms=24, workers=None):
+def oracle_leg(wl, pos, F_paths, n_atoms=24, workers=None):
     """Time the FP64 oracle (spawn pool over all host cores) on the centres that the
-    forces of `n_atoms` sampled atoms need, and compare those forces with F_gpu."""
+    forces of `n_atoms` sampled atoms need, and compare those oracle forces with each
+    force field in F_paths ({name: F [n, 3]}, all at positions `pos`)."""
     from oracle import neighbors, pool
     s = WORKLOADS[wl]["make"]()
     hp = model_hp(wl)
@@ -236,22 +269,25 @@ def oracle_leg(wl, pos, F_gpu, n_atoms=24, workers=None):
     terms = pool.centre_terms(hp, 42, pos, s.Z, s.box, s.pbc, centres, s.sys_ptr,
                               workers=workers)
     dt = time.perf_counter() - t0
-    d = []
+    F_ref = {}
     for m in atoms:
         Fm = terms[m][3].sum(axis=0)
         for i in sorted(set(int(j) for j in nl[m][0])):
             col, g = terms[i][1], terms[i][3]
             Fm = Fm - g[col == m].sum(axis=0)
-        d.append(F_gpu[m] - Fm)
-    d = np.array(d)
+        F_ref[m] = Fm
     cpu = {"value": len(centres) / dt, "unit": UNIT, "cores": workers,
            "kind": "oracle",
            "sample": f"E+F of {len(centres)} centres of {wl} (the neighbourhoods of {n_atoms} "
                      f"atoms), {dt:.1f} s on a spawn pool of {workers} processes"}
-    ferr = {"rmse_meV_per_A": float(np.sqrt((d ** 2).mean()) * 1e3),
-            "max_meV_per_A": float(np.abs(d).max() * 1e3),
-            "sample": f"forces on {n_atoms} atoms at the final positions vs the FP64 oracle"}
-    return cpu, ferr
+    ferrs = {}
+    for name, F in F_paths.items():
+        d = np.array([F[m] - F_ref[m] for m in atoms])
+        ferrs[name] = {"rmse_meV_per_A": float(np.sqrt((d ** 2).mean()) * 1e3),
+                       "max_meV_per_A": float(np.abs(d).max() * 1e3),
+                       "sample": f"forces on {n_atoms} atoms at the final positions vs the "
+                                 "FP64 oracle"}
+    return cpu, ferrs
 
 
 def run_reference(args):
@@ -319,10 +355,11 @@ def run_ours(args):
     x = torch.tensor(s.pos, dtype=torch.float64, device=dev)
     Z = torch.tensor(s.Z, dtype=torch.int32, device=dev)
     mass = torch.tensor(s.masses, dtype=torch.float64, device=dev)
-    v = torch.tensor(synth.maxwell_boltzmann(s.masses, 300.0, seed=7), dtype=torch.float64,
-                     device=dev)
+    v0 = synth.maxwell_boltzmann(s.masses, 300.0, seed=7)
+    v = torch.tensor(v0, dtype=torch.float64, device=dev)
     multi = s.sys_ptr.shape[0] > 2
-    model.bind(x, Z, s.box, s.pbc, s.sys_ptr if multi else None)
+    sys_ptr = s.sys_ptr if multi else None
+    model.bind(x, Z, s.box, s.pbc, sys_ptr)
     tuned = None
     if args.autotune and args.precision == 1:
         tuned = model.autotune(x)
@@ -338,21 +375,22 @@ def run_ours(args):
     clocks.start()
     time.sleep(1.0)
     for _ in range(args.warmup):
-        model.md(x, v, mass, 1, dt_fs, energies=False)
+        model.md(x, v, mass, 1, dt_fs, energies=True)
     torch.cuda.synchronize()
     E_edges = model.edges()[1].shape[0]
 
-    # ---- timed region: K MD steps, device-timed per step, L2 flushed between steps
-    def timed_steps(profile):
+    # ---- timed region: K MD steps (energies per atom and per system + forces each step),
+    # device-timed per step, L2 flushed between steps
+    def timed_steps(nsteps, profile):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
+              for _ in range(nsteps)]
         if profile:
             ff.profile_enable(True)
             ff.profile_read()
-        for k in range(args.steps):
+        for k in range(nsteps):
             flush.zero_()
             ev[k][0].record(stream)
-            model.md(x, v, mass, 1, dt_fs, energies=False)
+            model.md(x, v, mass, 1, dt_fs, energies=True)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         prof = None
@@ -366,18 +404,19 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks.mark("t0")
     l0 = model.launches()
-    step_ms, _ = timed_steps(False)
+    step_ms, _ = timed_steps(args.steps, False)
     launches = model.launches() - l0
     clocks.mark("t1")
     clk = clocks.stop()
-    # the same number of steps again with every launch bracketed by events (per-kernel
-    # durations for the roofline; kept out of the headline timing).  A graph replay carries
-    # no per-launch events, so with --graph this pass launches the same kernels eagerly (one
-    # untimed step first, which evaluates the forces at the current positions)
+    # a few steps again with every launch bracketed by events (per-kernel durations for the
+    # roofline; kept out of the headline timing).  A graph replay carries no per-launch
+    # events, so with --graph this pass launches the same kernels eagerly (one untimed step
+    # first, which evaluates the forces at the current positions)
     if args.graph:
         model.set_graph(False)
-        model.md(x, v, mass, 1, dt_fs, energies=False)
-    prof_ms, prof = timed_steps(True)
+        model.md(x, v, mass, 1, dt_fs, energies=True)
+    n_prof = min(args.steps, args.profile_steps)
+    prof_ms, prof = timed_steps(n_prof, True)
     E_prof = model.edges()[1].shape[0] if args.graph else E_edges
     if args.graph:
         model.set_graph(True)
@@ -418,49 +457,47 @@ def run_ours(args):
     h2d = 2 * s.n * 3 * 8
     d2h = 2 * s.n * 3 * 8 + 8
 
-    # ---- roofline of the dominant kernel class
+    # ---- roofline of the dominant kernel class (per-kernel CUDA events of the profiled
+    # pass); the contraction classes are measured against the matrix-unit work the method
+    # defines (method_flops_per_edge), not against what this implementation stores
     pk, pk_kind = peaks()
     dom = max(prof.items(), key=lambda kv: kv[1][1])
     dom_name, (dom_launch, dom_ms) = dom
-    n_eval = args.steps
+    method_flop = method_flops_per_edge(hp) * E_prof * n_prof
     if dom_name == "gemm_f32":
-        flops = gemm_flops_per_edge(hp) * E_prof * n_eval
-        achieved = flops / (dom_ms / 1e3) / 1e12
+        achieved = method_flop / (dom_ms / 1e3) / 1e12
         peak = FP32_PEAK_TFLOPS
         roof = {"kernel": "gemm_f32 (all FP32 MLP GEMM launches)", "bound": "alu",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 FLOP x 2.070 GHz",
+                "flop_per_edge": method_flops_per_edge(hp),
                 "launches": dom_launch, "avg_launch_us": 1e3 * dom_ms / max(dom_launch, 1)}
         tpe = traffic_per_edge("gemm_f32")
-        roof["traffic"] = (tpe * E_prof * n_eval / max(dom_launch, 1)) if tpe else None
+        roof["traffic"] = (tpe * E_prof * n_prof / max(dom_launch, 1)) if tpe else None
     elif dom_name == "gemm_bf16":
-        # tensor-core GEMMs with FP32 epilogue streams: the HBM ceiling is the lower one
-        flops = gemm_flops_per_edge(hp) * E_prof * n_eval
-        byts = gemm_bytes_per_edge(hp, 1) * E_prof * n_eval
         t_s = dom_ms / 1e3
-        t_tensor = flops / (pk["bf16_tflops_sustained"] * 1e12)
-        t_hbm = byts / (pk["hbm_gbs"] * 1e9)
-        if t_hbm >= t_tensor:
-            achieved, peak = byts / t_s / 1e9, pk["hbm_gbs"]
-            roof = {"kernel": "gemm_bf16 (tcgen05, all MLP GEMM launches)", "bound": "hbm",
-                    "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "peak_source": f"hbm_gbs ({pk_kind})"}
-        else:
-            achieved, peak = flops / t_s / 1e12, pk["bf16_tflops_sustained"]
-            roof = {"kernel": "gemm_bf16 (tcgen05, all MLP GEMM launches)", "bound": "tensor",
-                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak,
-                    "peak_source": f"bf16_tflops_sustained ({pk_kind})"}
-        roof.update({"tensor_tflops": flops / t_s / 1e12,
-                     "tensor_frac": flops / t_s / 1e12 / pk["bf16_tflops_sustained"],
-                     "algorithmic_bytes_per_edge": gemm_bytes_per_edge(hp, 1),
-                     "launches": dom_launch, "avg_launch_us": 1e3 * dom_ms / max(dom_launch, 1)})
+        achieved = method_flop / t_s / 1e12
+        byts = gemm_bytes_per_edge(hp, 1) * E_prof * n_prof
+        roof = {"kernel": "gemm_bf16 (tcgen05, all MLP GEMM launches)", "bound": "tensor",
+                "achieved": achieved, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                "frac": achieved / pk["bf16_tflops"],
+                "peak_source": f"bf16_tflops burst ({pk_kind})",
+                "frac_of_sustained": achieved / pk["bf16_tflops_sustained"],
+                "flop_per_edge": method_flops_per_edge(hp),
+                "unfused_gemm_bytes_per_edge": gemm_bytes_per_edge(hp, 1),
+                "unfused_bytes_hbm_frac": byts / t_s / 1e9 / pk["hbm_gbs"],
+                "launches": dom_launch, "avg_launch_us": 1e3 * dom_ms / max(dom_launch, 1)}
         tpe = traffic_per_edge("gemm_bf16")
-        roof["traffic"] = (tpe * E_prof * n_eval / max(dom_launch, 1)) if tpe else None
+        roof["traffic"] = (tpe * E_prof * n_prof / max(dom_launch, 1)) if tpe else None
     else:
-        roof = {"kernel": dom_name, "bound": "alu", "achieved": None, "peak": None,
-                "unit": None, "frac": None, "traffic": None}
+        roof = {"kernel": dom_name, "bound": "hbm", "achieved": None, "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": None, "traffic": None}
+    # the whole step against the same matrix-unit work (what the fused design is bound by)
+    step_flop = method_flops_per_edge(hp) * E_edges * args.steps
+    tensor_peak = pk["bf16_tflops"] if args.precision == 1 else FP32_PEAK_TFLOPS
+    roof["step_tensor_tflops"] = step_flop / t_total / 1e12
+    roof["step_tensor_frac"] = step_flop / t_total / 1e12 / tensor_peak
 
     # ---- NVE energy drift (optional): linear fit of E_pot + E_kin per atom over a run
     drift = None
@@ -476,13 +513,55 @@ def run_ours(args):
         except ff.FFError as exc:      # e.g. the random-weight system collapsing
             drift = {"error": str(exc), "steps": args.drift_steps}
 
+    # forces of this path at the final positions (compared with the oracle below)
+    x_end = x.clone()
+    _, _, F_main = model.energy_forces(x_end, E_atom=False)
+    F_main = F_main.double().cpu().numpy()
+    model.close()
+    del model
+    torch.cuda.empty_cache()
+
+    # ---- the plain FP32 path on the same workload (a few steps from the same state)
+    fp32 = None
+    F_32 = None
+    if args.precision == 1 and args.fp32_steps > 0:
+        m32 = ff.FFModel(hp, seed=42, precision=0)
+        m32.bind(x_end, Z, s.box, s.pbc, sys_ptr)
+        _, _, F32 = m32.energy_forces(x_end, E_atom=False)
+        F_32 = F32.double().cpu().numpy()
+        x32, v32 = x_end.clone(), v.clone()
+        m32.md(x32, v32, mass, 1, dt_fs, energies=True)               # untimed warm-up step
+        torch.cuda.synchronize()
+        ev32 = []
+        for _ in range(args.fp32_steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            a.record(stream)
+            m32.md(x32, v32, mass, 1, dt_fs, energies=True)
+            b.record(stream)
+            ev32.append((a, b))
+        torch.cuda.synchronize()
+        ms32 = [a.elapsed_time(b) for a, b in ev32]
+        fp32 = {"value": s.n * len(ms32) / (sum(ms32) / 1e3), "unit": UNIT,
+                "ms_per_step": sum(ms32) / len(ms32), "steps": len(ms32), "warmup": 2,
+                "dtype": "f32", "bf16_speedup": (sum(ms32) / len(ms32)) /
+                                                 (1e3 * t_total / args.steps)}
+        m32.close()
+        del m32
+        torch.cuda.empty_cache()
+
     # ---- CPU-baseline leg: the FP64 oracle on a bounded sample of this workload (the
     # neighbourhoods of a few atoms at the final positions), timed; the same oracle
-    # results give the force error of this run's path on those atoms
+    # results give the force error of each path on those atoms
     cpu = ferr = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        _, _, F = model.energy_forces(x, E_atom=False)
-        cpu, ferr = oracle_leg(wl, x.cpu().numpy(), F.double().cpu().numpy())
+        Fs = {"main": F_main}
+        if F_32 is not None:
+            Fs["fp32"] = F_32
+        cpu, ferrs = oracle_leg(wl, x_end.cpu().numpy(), Fs)
+        ferr = ferrs["main"]
+        if fp32 is not None:
+            fp32["force_error"] = ferrs["fp32"]
 
     if rank == 0:
         line = {
@@ -497,20 +576,22 @@ def run_ours(args):
                        "dt_fs": dt_fs, "parallelism": f"replicas x{world}",
                        "path": "CUDA graph on the frozen Verlet list" if args.graph
                                else "per-step filtered list",
-                       "gemm_tiles": tuned or "default (128-column slices: 4-warp CTAs, 1 stage; "
-                                             "readout 256 columns: 8-warp CTAs, 2 stages)",
-                       "l2": "flushed between timed steps (512 MiB write)"},
+                       "gemm_tiles": tuned or "default",
+                       "l2": "flushed between timed steps (512 MiB write); per-step inputs "
+                             "far larger than L2"},
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "clocks": clk,
-            "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof.items()
+            "kernel_ms_per_step": {k: round(v[1] / n_prof, 4) for k, v in prof.items()
                                    if v[0]},
-            "profiled_ms_per_step": sum(prof_ms) / args.steps,
+            "profiled_steps": n_prof,
+            "profiled_ms_per_step": sum(prof_ms) / n_prof,
             "step_ms": [round(t, 3) for t in step_ms],
             "force_error": ferr,
+            "fp32": fp32,
             "nve_drift": drift,
         }
         print(json.dumps(line), flush=True)
@@ -521,13 +602,18 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="water12288", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="sio2_4194304", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1],
                     help="1: BF16 tensor-core MLPs (default); 0: plain FP32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp32-steps", type=int, default=2,
+                    help="with --precision 1: time this many steps of the plain FP32 path on "
+                         "the same workload after the main timing (0: skip)")
+    ap.add_argument("--profile-steps", type=int, default=3,
+                    help="steps of the per-kernel event pass that feeds the roofline")
     ap.add_argument("--drift-steps", type=int, default=0,
                     help="after timing, run this many NVE steps and fit the energy drift")
     ap.add_argument("--autotune", action="store_true",

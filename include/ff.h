@@ -42,7 +42,11 @@ enum {
   FF_ERR_CAPACITY = -5,  /* a neighbour count exceeded the per-atom limit FF_MAX_NEIGHBORS */
   FF_ERR_NONFINITE = -6, /* non-finite position, energy or force */
   FF_ERR_STATE = -7,     /* call order violated (e.g. forces before any energy call) */
-  FF_ERR_BOX = -8        /* image shift out of range (|s| > 100 box lengths) */
+  FF_ERR_BOX = -8,       /* image shift out of range (|s| > 100 box lengths) */
+  FF_ERR_TIMEOUT = -9    /* a bounded device-side wait (the tensor-core GEMM pipeline's
+                            barrier waits, about two seconds each) ran out: the kernel
+                            released its resources and returned early, so the outputs of
+                            that call are invalid; the context stays usable */
 };
 
 /* Largest number of neighbours within rc + skin of one atom. */
@@ -113,7 +117,8 @@ int ff_neighbors(ff_ctx* ctx, const double* pos, const int32_t* Z, int n_atoms,
  *                                            intermediates are kept for ff_forces)
  * Re-filters the Verlet list at rc for `pos` and rebuilds it first when an atom moved
  * more than skin/2 since the last build.  Synchronises `stream` (edge count).
- * Errors: FF_ERR_STATE (no ff_neighbors yet), FF_ERR_CAPACITY, FF_ERR_OOM, FF_ERR_CUDA. */
+ * Errors: FF_ERR_STATE (no ff_neighbors yet), FF_ERR_CAPACITY, FF_ERR_NONFINITE, FF_ERR_OOM,
+ * FF_ERR_CUDA, FF_ERR_TIMEOUT (precision 1: a tensor-core pipeline wait ran out). */
 int ff_energy_forces(ff_ctx* ctx, const double* pos, double* E_sys, float* E_atom, float* F,
                      void* stream);
 
@@ -122,7 +127,7 @@ int ff_energy_forces(ff_ctx* ctx, const double* pos, double* E_sys, float* E_ato
  *   F       device float[n_atoms][3]
  * Requires the previous ff_energy_forces to have been called with F == NULL and the
  * same positions (the stored intermediates are used).  Errors: FF_ERR_STATE,
- * FF_ERR_CUDA. */
+ * FF_ERR_CUDA, FF_ERR_TIMEOUT. */
 int ff_forces(ff_ctx* ctx, const double* grad_E, float* F, void* stream);
 
 /* Virial of each system from the edge gradients of the last force evaluation (a
@@ -221,8 +226,7 @@ const char* ff_profile_class(int k);
 /* The neighbour-list build of ff_neighbors (same float32 membership test, same sorted
  * (i, j, s) order, same list at rc) for one small system, without allocating anything.
  * It exists for callers that cannot allocate device memory: an MD engine that only hands
- * out memory from a pool it reserved up front, code running while a CUDA graph is being
- * captured (cudaMalloc is not permitted there), or a host that forbids allocation inside
+ * out memory from a pool it reserved up front, or a host that forbids allocation inside
  * its time-step loop.  It needs no context.  The paper has no counterpart of this call.
  *   pos      device double[n_atoms][3]; n_atoms <= FF_NOALLOC_MAX_ATOMS (4096)
  *   box, pbc host double[3], host int[3] as in ff_neighbors; rc: cutoff (A)
@@ -236,14 +240,18 @@ const char* ff_profile_class(int k);
  * Working memory is a single file-scope __device__ array of about 13 MB that every GPU
  * loading the library holds until the process exits; no cudaMalloc, cudaFree or other
  * allocating call is made.  The first call on each device looks up that array's device
- * address (cudaGetSymbolAddress) with the device current; make that first call before
- * any stream capture.  Every call shares the array and it keeps the previous call's
- * contents (what must start at zero is cleared on every call), so calls that overlap on
- * the GPU -- on different streams or host threads -- race and must not be issued.
- * Kernel profiling (ff_profile_enable) must be off, as it creates CUDA events.
- * Synchronises `stream` (edge count).  Errors: FF_ERR_ARG (n_atoms above the limit, or
- * cap below the edge count), FF_ERR_CAPACITY (an atom with more than
- * FF_NOALLOC_MAX_NEIGHBORS neighbours), FF_ERR_BOX, FF_ERR_CUDA. */
+ * address (cudaGetSymbolAddress) with the device current.  Every call shares the array and
+ * it keeps the previous call's contents (what must start at zero is cleared on every
+ * call), so calls that overlap on the GPU -- on different streams or host threads -- race
+ * and must not be issued.  The cell grid is capped at 4096 cells: in a large box with a
+ * small rc the cells are coarsened (never below rc wide), so each atom then scans more
+ * candidates than ff_neighbors does, with the same result.
+ * The call copies a few words from host memory and synchronises `stream` (it reads the
+ * error word and the edge count back), so it must not be issued while the stream is being
+ * captured into a CUDA graph.  Kernel profiling (ff_profile_enable) must be off, as it
+ * creates CUDA events.  Errors: FF_ERR_ARG (n_atoms above the limit, or cap below the edge
+ * count), FF_ERR_NONFINITE (a non-finite coordinate), FF_ERR_CAPACITY (an atom with more
+ * than FF_NOALLOC_MAX_NEIGHBORS neighbours), FF_ERR_BOX, FF_ERR_CUDA. */
 int ff_neighbors_noalloc(const double* pos, int n_atoms, const double box[3], const int pbc[3],
                          float rc, int32_t* row_ptr, int32_t* col, int32_t* shift, int64_t cap,
                          int64_t* n_edges, char* msg, size_t msg_cap, void* stream);

@@ -22,7 +22,8 @@ LIB_PATH = _build.LIB
 
 FF_OK = 0
 ERRORS = {-1: "FF_ERR_ARG", -2: "FF_ERR_SPECIES", -3: "FF_ERR_OOM", -4: "FF_ERR_CUDA",
-          -5: "FF_ERR_CAPACITY", -6: "FF_ERR_NONFINITE", -7: "FF_ERR_STATE", -8: "FF_ERR_BOX"}
+          -5: "FF_ERR_CAPACITY", -6: "FF_ERR_NONFINITE", -7: "FF_ERR_STATE", -8: "FF_ERR_BOX",
+          -9: "FF_ERR_TIMEOUT"}
 
 # Every function the C ABI exports (include/ff.h).
 ABI = ("ff_create", "ff_destroy", "ff_neighbors", "ff_energy_forces", "ff_forces",

@@ -629,13 +629,9 @@ int read_flags(ff_ctx* c, cudaStream_t s) {
   const int e = c->flags_h[0];
   if (e) {
     FF_CK(c, cudaMemsetAsync(c->flags, 0, sizeof(int), s));
-    if (e & 16) return set_err(c, FF_ERR_SPECIES, "atomic number outside 1..89");
-    if (e & 4) return set_err(c, FF_ERR_BOX, "periodic image shift beyond 100 box lengths");
-    if (e & 1) return set_err(c, FF_ERR_CAPACITY, "neighbour count above the per-atom limit");
-    if (e & 8) return set_err(c, FF_ERR_STATE, "reverse edge missing (asymmetric list)");
-    if (e & 32) return set_err(c, FF_ERR_NONFINITE, "non-finite force");
-    if (e & 64) return set_err(c, FF_ERR_CUDA, "tensor-core GEMM pipeline wait timed out");
-    if (e & 128) return set_err(c, FF_ERR_NONFINITE, "non-finite position");
+    const char* what = nullptr;
+    const int st = ff_flags_status(e, &what);
+    if (st != FF_OK) return set_err(c, st, what);
   }
   return FF_OK;
 }

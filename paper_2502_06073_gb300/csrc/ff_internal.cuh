@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/ff.h"
+#include "ff_flags.h"
 
 #define FF_MAX_LAYERS 4
 #define FF_EF_STRIDE 24      // floats per edge in the edge-feature record
@@ -82,7 +83,7 @@ void launch_gemm_f32(int mode, int M, int N, int K, const float* A, int lda, con
 
 // BF16 tensor-core GEMM (tcgen05 + TMA): A bf16 [M][K] row-major, Bt = B^T bf16 [N][K]
 // row-major; N % 16 == 0, K, lda, ldb % 8 == 0, 16-byte aligned bases.  Returns false if
-// the launch could not be set up; a device-side timeout sets bit 64 of *err.
+// the launch could not be set up; a device-side timeout sets FF_FLAG_TIMEOUT in *err.
 bool gemm_bf16_available();
 // slice: output columns per CTA (128 or 256); stages_req: 2..4 pipeline stages, or 0
 // for the default (2 for 256-wide slices, 3 otherwise).  With A2 (bf16 [M][K2], row stride
@@ -116,7 +117,7 @@ void launch_verlet_allpairs(int n, const int* sys_of, const int* sys_ptr, const 
                             float rl2, int vmax, int* vl_j, int* vl_s, int* vl_cnt,
                             int* err, cudaStream_t s);
 void launch_pos_to_f32(const double* pos, int n, float4* xf, cudaStream_t s);
-// sets bit 128 of *err if any coordinate is not finite
+// sets FF_FLAG_NONFINITE_POS in *err if any coordinate is not finite
 void launch_check_pos(const double* pos, int n, int* err, cudaStream_t s);
 void launch_filter(int pass, int n, const float4* xf, const float* Lf, float rc2, int vmax,
                    const int* vl_j, const int* vl_s, const int* vl_cnt, int* cnt,

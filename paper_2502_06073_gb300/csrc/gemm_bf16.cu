@@ -13,8 +13,8 @@
 //                     tcgen05.commit releases the stage, a final commit the accumulator;
 //   all warps         epilogue: tcgen05.ld of their 32 TMEM lanes (= tile rows), 32
 //                     columns at a time, fused element-wise op, stores.
-// Every mbarrier wait is bounded; a timeout sets bit 64 of the error word and the CTA
-// drains what it issued, frees its tensor memory and returns.
+// Every mbarrier wait is bounded; a timeout sets FF_FLAG_TIMEOUT in the error word and the
+// CTA drains what it issued, frees its tensor memory and returns.
 #include <cuda.h>   // CUtensorMap (types only; the encoder is fetched at run time)
 
 #include <mutex>
@@ -421,7 +421,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   if (!ok && threadIdx.x == 0) s_fail = 1;
   fence_before();
   __syncthreads();
-  if (threadIdx.x == 0 && s_fail) atomicOr(err, 64);
+  if (threadIdx.x == 0 && s_fail) atomicOr(err, FF_FLAG_TIMEOUT);
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(ncols)
                  : "memory");

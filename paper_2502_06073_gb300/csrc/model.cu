@@ -493,7 +493,7 @@ __global__ void k_fill_f32(float* __restrict__ p, long long n, float v) {
 
 __global__ void k_check_finite(const float* __restrict__ F, long long n, int* __restrict__ err) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n && !isfinite(F[t])) atomicOr(err, 32);
+  if (t < n && !isfinite(F[t])) atomicOr(err, FF_FLAG_NONFINITE_F);
 }
 
 }  // namespace

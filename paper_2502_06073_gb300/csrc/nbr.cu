@@ -213,8 +213,8 @@ k_verlet_cells(int n, NbrGrid g, const int* __restrict__ cell_of, const int4* __
       }
     }
   }
-  if (__any_sync(kFull, bad_shift) && lane == 0) atomicOr(err, 4);
-  if (cnt > vmax && lane == 0) atomicOr(err, 1);
+  if (__any_sync(kFull, bad_shift) && lane == 0) atomicOr(err, FF_FLAG_BOX);
+  if (cnt > vmax && lane == 0) atomicOr(err, FF_FLAG_CAPACITY);
   __syncwarp();
   const int cw = cnt < vmax ? cnt : vmax;
   warp_rank_store(keys, cw, lane, vl_j + (size_t)i * vmax, vl_s + (size_t)i * vmax);
@@ -245,7 +245,7 @@ __global__ void k_verlet_allpairs(int n, const int* __restrict__ sys_of,
     }
     cnt += __popc(b);
   }
-  if (cnt > vmax && lane == 0) atomicOr(err, 1);
+  if (cnt > vmax && lane == 0) atomicOr(err, FF_FLAG_CAPACITY);
   if (lane == 0) vl_cnt[i] = cnt;
 }
 
@@ -307,7 +307,7 @@ __global__ void k_rev_index(long long E, const int* __restrict__ row_ptr,
     if (k == want) { found = mid; break; }
     if (k < want) lo = mid + 1; else hi = mid - 1;
   }
-  if (found < 0) { atomicOr(err, 8); found = (int)e; }
+  if (found < 0) { atomicOr(err, FF_FLAG_REVERSE); found = (int)e; }
   rev[e] = found;
 }
 
@@ -324,13 +324,13 @@ __global__ void k_disp_check(const double* __restrict__ x, const double* __restr
 
 __global__ void k_check_pos(const double* __restrict__ x, long long n3, int* __restrict__ err) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n3 && !isfinite(x[t])) atomicOr(err, 128);
+  if (t < n3 && !isfinite(x[t])) atomicOr(err, FF_FLAG_NONFINITE_POS);
 }
 
 __global__ void k_check_species(const int* __restrict__ Z, int n, int* __restrict__ err) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  if (Z[i] < 1 || Z[i] > FF_N_SPECIES) atomicOr(err, 16);
+  if (Z[i] < 1 || Z[i] > FF_N_SPECIES) atomicOr(err, FF_FLAG_SPECIES);
 }
 
 }  // namespace

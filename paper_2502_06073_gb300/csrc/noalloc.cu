@@ -1,9 +1,10 @@
 // ff_neighbors_noalloc: the neighbour-list build of ff_neighbors for one small system,
 // for callers that cannot allocate device memory -- e.g. an MD engine that hands out
-// only pre-reserved memory from its own pool, code running while a CUDA graph is being
-// captured (where cudaMalloc is not allowed), or a plug-in host that forbids allocation
+// only pre-reserved memory from its own pool, or a plug-in host that forbids allocation
 // inside its step loop.  No context is needed and nothing is allocated: the working
-// memory is one file-scope device array of fixed size, shared by every call.
+// memory is one file-scope device array of fixed size, shared by every call.  The call
+// reads its error word and edge count back (a host copy and a stream synchronisation), so
+// it cannot be recorded into a CUDA graph.
 #include <mutex>
 #include <string.h>
 
@@ -144,6 +145,9 @@ extern "C" int ff_neighbors_noalloc(const double* pos, int n_atoms, const double
     cudaGetLastError();
     return fail(msg, msg_cap, FF_ERR_CUDA, "clearing the scratch failed");
   }
+  // positions are checked like ff_neighbors checks them; a non-finite coordinate is binned
+  // (clamped into a valid cell) but the call then reports it instead of a list
+  launch_check_pos(pos, n_atoms, flags, s);
   launch_bin_atoms(pos, n_atoms, g, cell_of, img, xf, cell_count, s);
   launch_scan_i32(cell_count, cell_start, ncells, scan_tmp, s);
   launch_cell_scatter(cell_of, n_atoms, cell_start, cell_fill, cell_atoms, s);
@@ -160,11 +164,13 @@ extern "C" int ff_neighbors_noalloc(const double* pos, int n_atoms, const double
     cudaGetLastError();
     return fail(msg, msg_cap, FF_ERR_CUDA, "reading the edge count failed");
   }
-  if (host[0] & 1)
-    return fail(msg, msg_cap, FF_ERR_CAPACITY,
-                "an atom has more than FF_NOALLOC_MAX_NEIGHBORS (256) neighbours");
-  if (host[0] & 4)
-    return fail(msg, msg_cap, FF_ERR_BOX, "periodic image shift beyond 100 box lengths");
+  if (host[0]) {
+    const char* what = nullptr;
+    const int st = ff_flags_status(host[0], &what);
+    if (st == FF_ERR_CAPACITY)
+      what = "an atom has more than FF_NOALLOC_MAX_NEIGHBORS (256) neighbours";
+    return fail(msg, msg_cap, st, what);
+  }
   *n_edges = host[1];
   if (!col || !shift) return FF_OK;
   if ((int64_t)host[1] > cap)

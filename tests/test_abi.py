@@ -177,3 +177,26 @@ def test_null_context_and_argument_errors(lib):
     assert noalloc(rc=0.0) == ERR_ARG and b"rc" in msg.value
     assert noalloc(box_=(ctypes.c_double * 3)(20.0, -1.0, 20.0)) == ERR_ARG
     assert noalloc(pbc_=(ctypes.c_int * 3)(1, 2, 1)) == ERR_ARG
+
+
+def test_error_word_decoding(tmp_path):
+    """The mapping from the device error word to status codes (csrc/ff_flags.h), compiled
+    on the host with gcc: each bit gives its code, a bad input wins over what it causes,
+    a pipeline timeout is FF_ERR_TIMEOUT, an unknown bit FF_ERR_CUDA."""
+    import subprocess
+    shim = tmp_path / "shim.c"
+    shim.write_text('#include "ff_flags.h"\n'
+                    'int decode(int w) { const char* m = 0; int s = ff_flags_status(w, &m);'
+                    ' return (w && !(m && m[0])) ? 99 : s; }\n')
+    so = tmp_path / "libshim.so"
+    subprocess.run(["gcc", "-shared", "-fPIC", "-std=c99", "-Wall", "-Werror", "-I", CSRC,
+                    str(shim), "-o", str(so)], check=True)
+    dec = ctypes.CDLL(str(so)).decode
+    expect = {0: 0, 1: -5, 4: -8, 8: -7, 16: -2, 32: -6, 64: -9, 128: -6, 256: -4,
+              16 | 64: -2, 128 | 1: -6, 4 | 1: -8, 64 | 32: -9, 1 | 64: -5}
+    for word, code in expect.items():
+        assert dec(word) == code, (word, dec(word), code)
+    import paper_2502_06073_gb300 as ff
+    assert ff.ERRORS[-9] == "FF_ERR_TIMEOUT"
+    hdr = open(os.path.join(ROOT, "include", "ff.h")).read()
+    assert "FF_ERR_TIMEOUT = -9" in hdr

@@ -90,3 +90,19 @@ def test_water_model_figures():
     # compulsory bytes of the two paths' GEMM classes, as the roofline uses them
     assert bench.gemm_bytes_per_edge(hp, 1) == 22_424
     assert bench.gemm_bytes_per_edge(hp, 0) == 41_232
+
+
+def test_method_flops_per_edge_matches_the_model_definition():
+    """Matrix-unit work of one E+F per edge as the method defines it, for the config-2
+    model: radial input 8x64, two-body 64x128 + 128x256, 3 x (env 256x96 + latent
+    352x256), edge-energy 256x128 + 128x1 = 418,432 multiply-adds forward; x2 FLOP, x2
+    for the adjoint's input gradients."""
+    import bench
+    import synth
+    hp = synth.preset("fm_water")
+    mac = 8 * 64 + 64 * 128 + 128 * 256 + 3 * (256 * 96 + 352 * 256) + 256 * 128 + 128
+    assert mac == 418_432
+    assert bench.method_flops_per_edge(hp) == 4 * mac == 1_673_728
+    # the readout and radial layers are the only difference from the GEMM-shaped work
+    assert bench.method_flops_per_edge(hp) - bench.gemm_flops_per_edge(hp) == \
+        4 * (8 * 64 + 256 * 128 + 128)

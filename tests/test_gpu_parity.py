@@ -426,6 +426,50 @@ def test_graph_path_matches_plain_path_and_replays(ff, key, wl, prec):
     check(pos.clone())
 
 
+def test_graph_path_bf16_molecules1024_vs_oracle(ff):
+    """The batching path as it runs (1,024 molecules, BF16 MLPs, frozen Verlet list replayed
+    from a CUDA graph by ff_energy_forces_graph) against the FP64 oracle: at the capturing
+    call and at a replay after every atom moved by up to 0.1 A (inside skin/2), the energies
+    of 12 whole molecules and the forces and per-atom energies of all their atoms.  Bars:
+    force RMSE and max <= 5 meV/A; per-atom energy 8 u S_i and per-molecule energy
+    sum_i 8 u S_i (u = 2^-8, S_i the oracle's readout scale; see
+    test_bench_sizes_sampled_forces)."""
+    s = synth.molecules_system(1024, 1003)
+    hp = _hp("fm_water", "molecules1024")
+    m, pos = _bind(ff, hp, s, precision=1)
+    Es = torch.empty(m.n_sys, dtype=torch.float64, device="cuda")
+    Ea = torch.empty(s.n, dtype=torch.float32, device="cuda")
+    F = torch.empty(s.n, 3, dtype=torch.float32, device="cuda")
+    mols = np.random.default_rng(12).choice(1024, 12, replace=False).tolist()
+    atoms = [a for k in mols for a in range(int(s.sys_ptr[k]), int(s.sys_ptr[k + 1]))]
+    u = 2.0 ** -8
+
+    def check(p):
+        Fr, Er = pool.sampled_forces(hp, 42, p, s.Z, s.box, s.pbc, atoms, s.sys_ptr)
+        scale = Allegro64(hp, 42).readout_scale(p, s.Z, s.box, s.pbc, atoms, s.sys_ptr)
+        Fg = F.double().cpu().numpy()
+        Eg = Ea.double().cpu().numpy()
+        Esg = Es.cpu().numpy()
+        d = np.array([Fg[a] - Fr[a] for a in atoms])
+        assert np.sqrt((d ** 2).mean()) <= 5e-3 and np.abs(d).max() <= 5e-3, np.abs(d).max()
+        for a in atoms:
+            assert abs(Eg[a] - Er[a]) <= 8 * u * scale[a], (a, Eg[a], Er[a], scale[a])
+        for k in mols:
+            own = range(int(s.sys_ptr[k]), int(s.sys_ptr[k + 1]))
+            ref = sum(Er[a] for a in own)
+            bar = sum(8 * u * scale[a] for a in own)
+            assert abs(Esg[k] - ref) <= bar, (k, Esg[k], ref, bar)
+
+    m.energy_forces_graph(pos, Es, Ea, F)          # evaluates and captures
+    torch.cuda.synchronize()
+    check(s.pos)
+    delta = np.random.default_rng(5).uniform(-0.057, 0.057, size=(s.n, 3))
+    pos.add_(torch.tensor(delta, dtype=torch.float64, device="cuda"))
+    m.energy_forces_graph(pos, Es, Ea, F)          # replays the graph
+    torch.cuda.synchronize()
+    check(pos.cpu().numpy())
+
+
 def test_graph_md_matches_oracle_trajectory(ff):
     s = synth.config1_system()
     hp = synth.preset("small", skin=0.3)
