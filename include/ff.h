@@ -165,9 +165,11 @@ int ff_energy_forces_graph(ff_ctx* ctx, const double* pos, double* E_sys, float*
 
 /* Autotuner of the tensor-core MLP GEMMs (precision 1): times complete E+F evaluations of
  * the bound system at `pos` (device) for each edge-tile configuration -- output-column
- * slice of 128 or 256 per CTA and the default (0: 2 stages for 256-column slices, 1 for
- * narrower) or 2, 3 or 4 shared-memory pipeline stages (which sets how many CTAs share an
- * SM) -- keeps the fastest for this context and reports it
+ * slice of 128 or 256 per CTA; stages 0 (the default: for 128-column slices the persistent
+ * kernel, one CTA per SM with a producer warp, an MMA warp and three tensor-memory
+ * accumulators drained by their own epilogue warps; for 256-column slices 2 stages) or 1..4
+ * (the one-tile-per-CTA kernel with that many shared-memory pipeline stages, which sets how
+ * many CTAs share an SM) -- keeps the fastest for this context and reports it
  * (*slice, *stages; *ms_best = its mean evaluation time; any may be NULL).  For
  * precision 0 nothing is timed.  Synchronises `stream`.  Errors: as ff_energy_forces. */
 int ff_autotune(ff_ctx* ctx, const double* pos, int* slice, int* stages, double* ms_best,

@@ -1381,14 +1381,17 @@ int ff_autotune(ff_ctx* c, const double* pos, int* slice, int* stages, double* m
   if (!pos) return set_err(c, FF_ERR_ARG, "pos is null");
   cudaStream_t s = (cudaStream_t)stream;
   if (c->hp.precision == 1) {
-    // stages 0 = the launcher's default depth (2 for 256-column slices, 1 for narrower ones)
-    static const int cand[][2] = {{256, 0}, {256, 3}, {256, 4}, {128, 0}, {128, 2}, {128, 3}};
+    // stages 0 = the launcher's default (2 stages for 256-column slices; the persistent
+    // kernel for narrower ones), 1..4 = the non-persistent kernel with that ring depth
+    static const int cand[][2] = {{256, 0}, {256, 3}, {256, 4}, {128, 0},
+                                  {128, 1}, {128, 2}, {128, 3}};
+    constexpr int ncand = (int)(sizeof(cand) / sizeof(cand[0]));
     cudaEvent_t e0, e1;
     FF_CK(c, cudaEventCreate(&e0));
     FF_CK(c, cudaEventCreate(&e1));
     float best = 1e30f;
     int bi = 0;
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < ncand; ++k) {
       c->tune_slice = cand[k][0];
       c->tune_stages = cand[k][1];
       FF_TRY(evaluate(c, pos, nullptr, nullptr, c->F_int, nullptr, true, s));   // warm-up

@@ -140,46 +140,44 @@ __device__ __forceinline__ float dsilu_f(float z) {
   return sg * (1.f + z * (1.f - sg));
 }
 
-// Vectorised epilogue of 8 row-groups: lane l of a warp owns 4 consecutive columns of
-// rows r0 + 4i + (l >> 3), i = 0..7.  All loads of the batch are issued before any store.
+// Element type of the epilogue input a mode reads per output element (0: none, 1: bf16,
+// 2: fp32): the bf16 residual stream (SILU_RES, HEAD), the bf16 pre-activations (DSILU),
+// the FP32 residual (RES) or the FP32 output it accumulates into (ACC).
 template <int MODE>
-__device__ __forceinline__ void epi_batch(const EpiParams& ep, const float4 (&acc)[8],
-                                          const int (&row)[8], int col, bool colok,
-                                          float (&racc)[8][2]) {
-  float4 aux[8];
-  float fr[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const bool ok = colok && row[i] >= 0;
-    aux[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    fr[i] = 0.f;
-    if (!ok) continue;
-    const size_t r = (size_t)row[i];
-    if (MODE == EPI_SILU_RES || MODE == EPI_HEAD) {   // residual stream kept in bf16
-      const uint2 pk = *reinterpret_cast<const uint2*>(ep.resb + r * ep.ldr + col);
-      const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk.x));
-      const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk.y));
-      aux[i] = make_float4(lo.x, lo.y, hi.x, hi.y);
-    }
-    if (MODE == EPI_RES && col < ep.split)
-      aux[i] = *reinterpret_cast<const float4*>(ep.res + r * ep.ldr + col);
-    if (MODE == EPI_DSILU) {   // pre-activations of this path are stored in bf16
-      const uint2 pk = *reinterpret_cast<const uint2*>(ep.zb + r * ep.ldz + col);
-      const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk.x));
-      const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk.y));
-      aux[i] = make_float4(lo.x, lo.y, hi.x, hi.y);
-    }
-    if (MODE == EPI_ACC) aux[i] = *reinterpret_cast<const float4*>(ep.out + r * ep.ldo + col);
-    if (MODE == EPI_SILU_F || MODE == EPI_SILU_RES || MODE == EPI_HEAD)
-      fr[i] = ep.f[r * ep.ldf];
-  }
+__host__ __device__ constexpr int aux_kind() {
+  return (MODE == EPI_SILU_RES || MODE == EPI_HEAD || MODE == EPI_DSILU) ? 1
+         : (MODE == EPI_RES || MODE == EPI_ACC)                          ? 2
+                                                                         : 0;
+}
+// Bytes of one warp's epilogue-input tile (32 rows x 32 columns).
+template <int MODE>
+__host__ __device__ constexpr int aux_tile_bytes() {
+  return aux_kind<MODE>() == 2 ? 32 * 32 * 4 : aux_kind<MODE>() == 1 ? 32 * 32 * 2 : 0;
+}
+// The readout's 8-warp CTAs keep two per SM only if their input tiles reuse the stage ring
+// (behind the epilogue tiles and row sums), so there the first tile is loaded once the
+// accumulator is complete; the other modes give them their own region and load the first
+// one while the main loop runs.
+template <int MODE>
+__host__ __device__ constexpr bool aux_in_ring() {
+  return MODE == EPI_HEAD;
+}
+
+// Vectorised epilogue of 8 row-groups: lane l of a warp owns 4 consecutive columns of
+// rows r0 + 4i + (l >> 3), i = 0..7.  The epilogue inputs (aux) and the per-row envelope
+// (fr) arrive already loaded.
+template <int MODE, int RG>
+__device__ __forceinline__ void epi_batch(const EpiParams& ep, const float4 (&acc)[RG],
+                                          const float4 (&aux)[RG], const float* fr,
+                                          const int* row, int col, bool colok,
+                                          float (*racc)[2]) {
   if constexpr (MODE == EPI_HEAD) {
     // readout: partial dot products of this lane's 4 columns, summed over rows later
     if (!colok) return;
     const float4 w4 = *reinterpret_cast<const float4*>(ep.wv + col);
     const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < RG; ++i) {
       if (row[i] < 0) continue;
       const size_t r = (size_t)row[i];
       const float a4[4] = {aux[i].x, aux[i].y, aux[i].z, aux[i].w};
@@ -203,7 +201,7 @@ __device__ __forceinline__ void epi_batch(const EpiParams& ep, const float4 (&ac
     }
   } else {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < RG; ++i) {
       if (!colok || row[i] < 0) continue;
       const size_t r = (size_t)row[i];
       float v[4] = {ep.alpha * acc[i].x, ep.alpha * acc[i].y, ep.alpha * acc[i].z,
@@ -243,11 +241,118 @@ __device__ __forceinline__ void epi_batch(const EpiParams& ep, const float4 (&ac
   }
 }
 
+// Rows and envelope values of the 8 row groups a lane handles in a warp's 32 tile rows
+// starting at tile row r0 (row -1: outside the matrix or the accumulator is invalid).
+template <int MODE>
+__device__ __forceinline__ void epi_rows(const EpiParams& ep, int r0, int M, bool ok, int lane,
+                                         int (&rows)[8], float (&fr)[8]) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int row = r0 + 4 * i + (lane >> 3);
+    rows[i] = (ok && row < M) ? row : -1;
+    fr[i] = 0.f;
+    if ((MODE == EPI_SILU_F || MODE == EPI_SILU_RES || MODE == EPI_HEAD) && rows[i] >= 0)
+      fr[i] = ep.f[(size_t)rows[i] * ep.ldf];
+  }
+}
+
+// One 32-column chunk of a warp's 32 tile rows: the accumulator block (TMEM address taddr)
+// goes through the warp's shared tile (float4 groups XOR-swizzled by row, conflict-free
+// both ways) and leaves as float4 row segments, so one warp instruction covers 4 rows x 32
+// columns.  The chunk's epilogue inputs come from the warp's TMA-filled input tile (use_aux:
+// waited for on `auxbar` with parity aux_par; once every lane has read it, lane 0 starts
+// the load of the next tile at (nx, ny) unless nx < 0) or, without a tensor map, from
+// global memory.  Returns false if the wait for the input tile timed out.
+template <int MODE, int RG = 8>
+__device__ __forceinline__ bool epi_chunk(const EpiParams& ep, uint32_t taddr, float* tile,
+                                          const uint8_t* my_aux, bool use_aux,
+                                          uint32_t auxbar, uint32_t aux_par,
+                                          const CUtensorMap* tmX, int nx, int ny,
+                                          const int (&rows)[8], const float (&fr)[8], int col,
+                                          bool colok, float (&racc)[8][2]) {
+  constexpr int AUXB = aux_tile_bytes<MODE>();
+  const int lane = threadIdx.x & 31;
+  const int gq = lane & 7, rsub = lane >> 3;
+  {
+    float v[32];
+    tmem_ld32(taddr, v);
+#pragma unroll
+    for (int g4 = 0; g4 < 8; ++g4)
+      *reinterpret_cast<float4*>(&tile[lane * 32 + 4 * (g4 ^ (lane & 7))]) =
+          make_float4(v[4 * g4], v[4 * g4 + 1], v[4 * g4 + 2], v[4 * g4 + 3]);
+  }
+  __syncwarp();
+  bool okw = true;
+  if (use_aux) okw = __all_sync(0xffffffffu, mbar_wait(auxbar, aux_par));   // one answer
+  // row groups in passes of RG (fewer live registers for RG < 8)
+#pragma unroll
+  for (int p = 0; p < 8 / RG; ++p) {
+    float4 acc[RG], aux[RG];
+#pragma unroll
+    for (int ii = 0; ii < RG; ++ii) {
+      const int rl = 4 * (p * RG + ii) + rsub;
+      acc[ii] = *reinterpret_cast<const float4*>(&tile[rl * 32 + 4 * (gq ^ (rl & 7))]);
+      aux[ii] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (use_aux) {
+#pragma unroll
+      for (int ii = 0; ii < RG; ++ii) {
+        const int rl = 4 * (p * RG + ii) + rsub;
+        if (aux_kind<MODE>() == 2) {
+          aux[ii] = *reinterpret_cast<const float4*>(my_aux + (rl * 32 + 4 * gq) * 4);
+        } else {
+          const uint2 pk = *reinterpret_cast<const uint2*>(my_aux + (rl * 32 + 4 * gq) * 2);
+          const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk.x));
+          const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk.y));
+          aux[ii] = make_float4(lo.x, lo.y, hi.x, hi.y);
+        }
+      }
+    } else if (MODE == EPI_RES && ep.ldr == 0 && colok) {
+      // broadcast residual row (the readout vector): one load for every row of the chunk
+      const float4 b = col < ep.split ? *reinterpret_cast<const float4*>(ep.res + col)
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int ii = 0; ii < RG; ++ii) aux[ii] = b;
+    } else if (AUXB > 0 && colok) {
+      // no tensor map for this input: plain loads
+#pragma unroll
+      for (int ii = 0; ii < RG; ++ii) {
+        const int i = p * RG + ii;
+        if (rows[i] < 0) continue;
+        const size_t r = (size_t)rows[i];
+        if (MODE == EPI_RES && col < ep.split)
+          aux[ii] = *reinterpret_cast<const float4*>(ep.res + r * ep.ldr + col);
+        if (MODE == EPI_ACC)
+          aux[ii] = *reinterpret_cast<const float4*>(ep.out + r * ep.ldo + col);
+        if (MODE == EPI_SILU_RES || MODE == EPI_HEAD || MODE == EPI_DSILU) {
+          const __nv_bfloat16* src =
+              (MODE == EPI_DSILU) ? ep.zb + r * ep.ldz + col : ep.resb + r * ep.ldr + col;
+          const uint2 pk = *reinterpret_cast<const uint2*>(src);
+          const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk.x));
+          const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk.y));
+          aux[ii] = make_float4(lo.x, lo.y, hi.x, hi.y);
+        }
+      }
+    }
+    if (p == 8 / RG - 1) {
+      __syncwarp();   // every lane has read the shared tile and the input tile
+      if (use_aux && okw && lane == 0 && nx >= 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(auxbar, AUXB);
+        tma_load_2d(smem_u32(my_aux), tmX, nx, ny, auxbar);
+      }
+    }
+    epi_batch<MODE, RG>(ep, acc, aux, fr + p * RG, rows + p * RG, col, colok, racc + p * RG);
+  }
+  return okw;
+}
+
 // Shared memory before the barriers: the stage ring, or the epilogue tiles (32x32 floats
 // per warp) plus the readout's row sums (2 x 128 floats), whichever is larger.
 __host__ __device__ inline size_t gemm_pipe_bytes(int mode, int nw, int stages, int nbw) {
   const size_t ring = (size_t)stages * (TM * TK * 2 + (size_t)nbw * TK * 2);
-  const size_t epi = (size_t)nw * 32 * 32 * 4 + (mode == EPI_HEAD ? 2 * TM * 4 : 0);
+  const size_t epi = (size_t)nw * 32 * 32 * 4 +
+                     (mode == EPI_HEAD ? 2 * TM * 4 + (size_t)nw * 32 * 32 * 2 : 0);
   return ring > epi ? ring : epi;
 }
 
@@ -257,8 +362,9 @@ __host__ __device__ inline size_t gemm_pipe_bytes(int mode, int nw, int stages, 
 template <int MODE, int NW>
 __global__ void __launch_bounds__(32 * NW, 8 / NW * 2)
 k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
-          const __grid_constant__ CUtensorMap tmB, int M, int N, int K, int k1c, int nslices,
-          int nbw, int stages, EpiParams ep, int* __restrict__ err) {
+          const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmX,
+          int M, int N, int K, int k1c, int nslices, int nbw, int stages, int aux_tma,
+          EpiParams ep, int* __restrict__ err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t a_bytes = TM * TK * 2;
@@ -266,11 +372,18 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   const uint32_t st_bytes = a_bytes + b_bytes;
   // the epilogue's shared tiles (and the readout's row sums) reuse the stage memory; the
   // barriers sit after whichever of the two is larger
-  uint64_t* bars = (uint64_t*)(smem + gemm_pipe_bytes(MODE, NW, stages, nbw));
+  // each warp's epilogue-input tile (filled by TMA, one chunk ahead) follows them, then the
+  // barriers
+  constexpr int AUXB = aux_tile_bytes<MODE>();
+  constexpr bool IN_RING = aux_in_ring<MODE>();
+  const size_t pipe = gemm_pipe_bytes(MODE, NW, stages, nbw);
+  uint8_t* auxbuf = IN_RING ? smem + NW * 32 * 32 * 4 + 2 * TM * 4 : smem + pipe;
+  uint64_t* bars = (uint64_t*)(smem + pipe + ((IN_RING || !aux_tma) ? 0 : (size_t)NW * AUXB));
   uint64_t* full = bars;
   uint64_t* empty = bars + stages;
   uint64_t* accf = bars + 2 * stages;
-  uint32_t* tslot = (uint32_t*)(accf + 1);
+  uint64_t* auxf = accf + 1;   // one per warp
+  uint32_t* tslot = (uint32_t*)(auxf + NW);
   __shared__ int s_fail;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -285,6 +398,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       mbar_init(smem_u32(&empty[s]), 1);
     }
     mbar_init(smem_u32(accf), 1);
+    for (int w = 0; w < NW; ++w) mbar_init(smem_u32(&auxf[w]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -299,6 +413,16 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   fence_after();
   const uint32_t tbase = *tslot;
   const int nk = (K + TK - 1) / TK;
+  const int quad = warp & 3, half = warp >> 2;
+  const int nchunks = (nbw + 31) / 32;
+  // epilogue inputs of this warp's first chunk: rows 32*quad.. of the tile, columns of
+  // chunk `half`; the load runs while the main loop does
+  const bool use_aux = AUXB > 0 && aux_tma != 0;
+  uint8_t* my_aux = auxbuf + (size_t)warp * AUXB;
+  if (!IN_RING && use_aux && lane == 0 && half < nchunks) {
+    mbar_expect_tx(smem_u32(&auxf[warp]), AUXB);
+    tma_load_2d(smem_u32(my_aux), &tmX, n0 + half * 32, m0 + quad * 32, smem_u32(&auxf[warp]));
+  }
 
   if (warp == 0 && lane == 0) {
     // ---- TMA producer
@@ -344,41 +468,43 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   __syncwarp();
 
   // ---- epilogue: NW warps; warp w drains TMEM lane quadrant (w & 3) (tile rows
-  // 32(w&3)..+31) for every (NW/4)-th 32-column chunk (w >> 2 picks which).  Each 32x32
-  // block goes through a shared tile (float4 groups XOR-swizzled by row, conflict-free
-  // both ways; it reuses the pipeline stages, free once the accumulator is complete) and
-  // leaves as float4 row segments, so one warp instruction covers 4 rows x 32 columns.
+  // 32(w&3)..+31) for every (NW/4)-th 32-column chunk (w >> 2 picks which); its shared
+  // tile reuses the pipeline stages, free once the accumulator is complete
   const bool ok = mbar_wait(smem_u32(accf), 0);
   fence_after();
-  const int quad = warp & 3, half = warp >> 2;
+  if (IN_RING && use_aux && lane == 0 && half < nchunks) {
+    // the stages are free: every MMA that read them has completed
+    mbar_expect_tx(smem_u32(&auxf[warp]), AUXB);
+    tma_load_2d(smem_u32(my_aux), &tmX, n0 + half * 32, m0 + quad * 32, smem_u32(&auxf[warp]));
+  }
   float* tile = reinterpret_cast<float*>(smem) + warp * 32 * 32;
-  const int nchunks = (nbw + 31) / 32;
+  int rows[8];
+  float fr[8];
+  epi_rows<MODE>(ep, m0 + quad * 32, M, ok, lane, rows, fr);
+  bool aux_ok = true;
+  int aux_fail_k = 0;
   float racc[8][2];
 #pragma unroll
   for (int i = 0; i < 8; ++i) racc[i][0] = racc[i][1] = 0.f;
-  for (int ci = half; ci < nchunks; ci += NW / 4) {
+  int k = 0;
+  for (int ci = half; ci < nchunks; ci += NW / 4, ++k) {
     const int c0 = ci * 32;
-    float v[32];
-    tmem_ld32(tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
-#pragma unroll
-    for (int g4 = 0; g4 < 8; ++g4)
-      *reinterpret_cast<float4*>(&tile[lane * 32 + 4 * (g4 ^ (lane & 7))]) =
-          make_float4(v[4 * g4], v[4 * g4 + 1], v[4 * g4 + 2], v[4 * g4 + 3]);
-    __syncwarp();
-    const int gq = lane & 7, rsub = lane >> 3;
-    const int cl = c0 + 4 * gq;
+    const int cl = c0 + 4 * (lane & 7);
     const int col = n0 + cl;
-    float4 acc[8];
-    int rows[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int rl = 4 * i + rsub;
-      acc[i] = *reinterpret_cast<const float4*>(&tile[rl * 32 + 4 * (gq ^ (rl & 7))]);
-      const int row = m0 + quad * 32 + rl;
-      rows[i] = (ok && row < M) ? row : -1;
+    const int nci = ci + NW / 4;
+    const bool wok = epi_chunk<MODE>(
+        ep, tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, tile, my_aux,
+        use_aux && aux_ok, smem_u32(&auxf[warp]), k & 1, &tmX,
+        nci < nchunks ? n0 + nci * 32 : -1, m0 + quad * 32, rows, fr, col,
+        cl < nbw && col < N, racc);
+    if (!wok && aux_ok) {
+      aux_ok = false;   // that load is still owed: waited for again before exit
+      aux_fail_k = k;
     }
-    epi_batch<MODE>(ep, acc, rows, col, cl < nbw && col < N, racc);
-    __syncwarp();
+  }
+  if (!aux_ok) {
+    mbar_wait(smem_u32(&auxf[warp]), aux_fail_k & 1);
+    s_fail = 1;
   }
   if (MODE == EPI_HEAD) {
     // row sums: the 8 lanes sharing a row (lane & 7) by shuffles, then the two warps of
@@ -427,6 +553,270 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                  : "memory");
 }
 
+// ---------------------------------------------------------------------------------------
+// Persistent variant for output slices of at most 128 columns (every mode but the readout):
+// one CTA per SM walks the (row tile, column slice) tiles blockIdx.x, + gridDim.x, ... with
+//   warp PP_EW      TMA producer: A/B K-chunks of all its tiles through a ring of `stages`
+//                   stages, running ahead of the MMAs across tile boundaries;
+//   warp PP_EW + 1  MMA issuer: tile j accumulates into TMEM buffer j % PP_NA (128 columns
+//                   each) once the epilogue group of that buffer has drained it;
+//   warps 0..PP_EW-1  PP_NA epilogue groups of 4 warps; group g drains the tiles j = g mod
+//                   PP_NA, so the loads and MMAs of the next tiles overlap its epilogue.
+// Every wait is bounded; a timeout sets FF_FLAG_TIMEOUT, and s_abort makes the other roles
+// leave their loops at their next wait.
+// Accumulator buffers (epilogue groups) per mode: four, with the epilogue in passes of 4 row
+// groups so that 18 warps fit the register file (96 registers a thread); the residual update
+// and the readout (sixteen row sums per lane) need more registers and get three (14 warps,
+// 128 registers).
+template <int MODE>
+__host__ __device__ constexpr int pp_na() {
+  return (MODE == EPI_HEAD || MODE == EPI_SILU_RES) ? 3 : 4;
+}
+template <int MODE>
+__host__ __device__ constexpr int pp_threads() {
+  return 32 * (4 * pp_na<MODE>() + 2);
+}
+
+// Bounded wait that also gives up once another role has aborted.
+__device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity,
+                                             const volatile int* abort_flag) {
+  for (long it = 0; it < kWaitLimit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (it > 32) __nanosleep(128);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__host__ __device__ inline size_t pp_ring_bytes(int stages, int nbw) {
+  return (size_t)stages * (TM * TK * 2 + (size_t)nbw * TK * 2);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(pp_threads<MODE>(), 1)
+k_gemm_pp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
+          const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmX,
+          int M, int N, int K, int k1c, int nslices, int nbw, int stages, int aux_tma,
+          EpiParams ep, int* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr int PP_NA = pp_na<MODE>();
+  constexpr int PP_EW = 4 * PP_NA;
+  constexpr int RG = 4;
+  constexpr int AUXB = aux_tile_bytes<MODE>();
+  const uint32_t a_bytes = TM * TK * 2;
+  const uint32_t st_bytes = a_bytes + (uint32_t)nbw * TK * 2;
+  const size_t ring = pp_ring_bytes(stages, nbw);
+  float* tiles = reinterpret_cast<float*>(smem + ring);                  // PP_EW x 4 KB
+  uint8_t* auxbuf = smem + ring + (size_t)PP_EW * 32 * 32 * 4;           // PP_EW x AUXB
+  uint64_t* bars = (uint64_t*)(auxbuf + (size_t)PP_EW * AUXB);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + stages;
+  uint64_t* accf = bars + 2 * stages;     // PP_NA: accumulator complete
+  uint64_t* acce = accf + PP_NA;          // PP_NA: accumulator drained (4 arrivals)
+  uint64_t* auxf = acce + PP_NA;          // PP_EW: epilogue input tile landed
+  uint64_t* fin = auxf + PP_EW;           // the MMA issuer's last commit
+  uint32_t* tslot = (uint32_t*)(fin + 1);
+  __shared__ int s_fail;
+  __shared__ volatile int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntiles = ff_cdiv(M, TM) * nslices;
+  const int nk = (K + TK - 1) / TK;
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    s_abort = 0;
+    for (int q = 0; q < stages; ++q) {
+      mbar_init(smem_u32(&full[q]), 1);
+      mbar_init(smem_u32(&empty[q]), 1);
+    }
+    for (int a = 0; a < PP_NA; ++a) {
+      mbar_init(smem_u32(&accf[a]), 1);
+      mbar_init(smem_u32(&acce[a]), 4);
+    }
+    for (int w = 0; w < PP_EW; ++w) mbar_init(smem_u32(&auxf[w]), 1);
+    mbar_init(smem_u32(fin), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == PP_EW + 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tbase = *tslot;
+
+  if (warp == PP_EW) {
+    // ---- TMA producer
+    if (lane == 0) {
+      long q = 0;   // K-chunks issued so far (ring position)
+      bool good = true;
+      for (int t = blockIdx.x; t < ntiles && good; t += gridDim.x) {
+        const int m0 = (t / nslices) * TM, n0 = (t % nslices) * nbw;
+        for (int kc = 0; kc < nk; ++kc, ++q) {
+          const int st = (int)(q % stages);
+          if (q >= stages &&
+              !mbar_wait_ab(smem_u32(&empty[st]), (uint32_t)(((q / stages) - 1) & 1), &s_abort)) {
+            good = false;
+            break;
+          }
+          uint8_t* sa = smem + (size_t)st * st_bytes;
+          mbar_expect_tx(smem_u32(&full[st]), st_bytes);
+          if (kc < k1c) tma_load_2d(smem_u32(sa), &tmA, kc * TK, m0, smem_u32(&full[st]));
+          else tma_load_2d(smem_u32(sa), &tmA2, (kc - k1c) * TK, m0, smem_u32(&full[st]));
+          tma_load_2d(smem_u32(sa + a_bytes), &tmB, kc * TK, n0, smem_u32(&full[st]));
+        }
+      }
+      if (!good) {
+        s_fail = 1;
+        s_abort = 1;
+      }
+      // the loads issued last land before the CTA may exit
+      for (long p = q - 1; p >= 0 && p >= q - stages; --p)
+        mbar_wait(smem_u32(&full[p % stages]), (uint32_t)((p / stages) & 1));
+    }
+  } else if (warp == PP_EW + 1) {
+    // ---- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = instr_desc(TM, nbw);
+      long q = 0;
+      bool good = true;
+      int j = 0;
+      for (int t = blockIdx.x; t < ntiles && good; t += gridDim.x, ++j) {
+        const int a = j % PP_NA;
+        if (j >= PP_NA &&
+            !mbar_wait_ab(smem_u32(&acce[a]), (uint32_t)(((j / PP_NA) - 1) & 1), &s_abort)) {
+          good = false;
+          break;
+        }
+        fence_after();
+        const uint32_t dacc = tbase + (uint32_t)(a * 128);
+        for (int kc = 0; kc < nk; ++kc, ++q) {
+          const int st = (int)(q % stages);
+          if (!mbar_wait_ab(smem_u32(&full[st]), (uint32_t)((q / stages) & 1), &s_abort)) {
+            good = false;
+            break;
+          }
+          fence_after();
+          const uint8_t* sa = smem + (size_t)st * st_bytes;
+          const uint64_t da = smem_desc(smem_u32(sa));
+          const uint64_t db = smem_desc(smem_u32(sa + a_bytes));
+#pragma unroll
+          for (int kk = 0; kk < TK / 16; ++kk)
+            mma_bf16(dacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
+                     (kc > 0 || kk > 0) ? 1u : 0u);
+          mma_commit(smem_u32(&empty[st]));
+        }
+        if (good) mma_commit(smem_u32(&accf[a]));
+      }
+      if (!good) {
+        s_fail = 1;
+        s_abort = 1;
+      }
+      // every MMA issued above has completed before the tensor memory is released
+      mma_commit(smem_u32(fin));
+      mbar_wait(smem_u32(fin), 0);
+    }
+  } else {
+    // ---- epilogue group g = warp / 4, lane quadrant warp & 3
+    const int g = warp >> 2, quad = warp & 3;
+    const bool use_aux = AUXB > 0 && aux_tma != 0;
+    uint8_t* my_aux = auxbuf + (size_t)warp * AUXB;
+    float* tile = tiles + warp * 32 * 32;
+    const int nchunks = (nbw + 31) / 32;
+    uint32_t aux_n = 0;   // input tiles loaded by this warp so far (barrier phase)
+    bool good = true;
+    int j = g;
+    for (int t = blockIdx.x + g * gridDim.x; t < ntiles && good; t += PP_NA * gridDim.x,
+             j += PP_NA) {
+      const int m0 = (t / nslices) * TM, n0 = (t % nslices) * nbw;
+      if (use_aux && lane == 0) {   // first chunk's inputs, while the accumulator fills
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(smem_u32(&auxf[warp]), AUXB);
+        tma_load_2d(smem_u32(my_aux), &tmX, n0, m0 + quad * 32, smem_u32(&auxf[warp]));
+      }
+      int rows[8];
+      float fr[8];
+      epi_rows<MODE>(ep, m0 + quad * 32, M, true, lane, rows, fr);
+      const bool okacc = __all_sync(
+          0xffffffffu, mbar_wait_ab(smem_u32(&accf[g]), (uint32_t)((j / PP_NA) & 1), &s_abort));
+      fence_after();
+      if (!okacc) {
+        good = false;
+        if (use_aux) mbar_wait(smem_u32(&auxf[warp]), aux_n & 1);   // the load still owed
+        break;
+      }
+      float racc[8][2];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) racc[i][0] = racc[i][1] = 0.f;
+      for (int ci = 0; ci < nchunks; ++ci) {
+        const int c0 = ci * 32;
+        const int cl = c0 + 4 * (lane & 7);
+        const int col = n0 + cl;
+        const bool wok = epi_chunk<MODE, RG>(
+            ep, tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)(g * 128 + c0), tile, my_aux,
+            use_aux, smem_u32(&auxf[warp]), aux_n & 1, &tmX,
+            ci + 1 < nchunks ? n0 + c0 + 32 : -1, m0 + quad * 32, rows, fr, col,
+            cl < nbw && col < N, racc);
+        if (use_aux) ++aux_n;
+        if (!wok) {
+          good = false;   // no further load was started; the timed-out one is owed
+          mbar_wait(smem_u32(&auxf[warp]), (aux_n - 1) & 1);
+          break;
+        }
+      }
+      if (MODE == EPI_HEAD && good) {
+        // readout of this 128-column slice: the 8 lanes sharing a row sum their columns,
+        // then one lane adds the row's partial energy and envelope-gradient sums into the
+        // zeroed outputs (two slices per 256-wide row: 0 + a + b is the same in any order)
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            float t = racc[i][q];
+            t += __shfl_xor_sync(0xffffffffu, t, 1);
+            t += __shfl_xor_sync(0xffffffffu, t, 2);
+            t += __shfl_xor_sync(0xffffffffu, t, 4);
+            racc[i][q] = t;
+          }
+        if ((lane & 7) == 0) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int row = m0 + quad * 32 + 4 * i + (lane >> 3);
+            if (row < M) {
+              atomicAdd(&ep.eout[row], racc[i][0]);
+              atomicAdd(&ep.gfo[row], ep.beta * racc[i][1]);
+            }
+          }
+        }
+      }
+      // the accumulator buffer is free again
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&acce[g]));
+    }
+    if (!good && lane == 0) {
+      s_fail = 1;
+      s_abort = 1;
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && s_fail) atomicOr(err, FF_FLAG_TIMEOUT);
+  if (warp == PP_EW + 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512)
+                 : "memory");
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -463,6 +853,42 @@ bool make_map(CUtensorMap* m, const void* base, long long rows, int cols, int ld
          CUDA_SUCCESS;
 }
 
+// 2-D tensor map of an epilogue input: rows x cols elements of `es` bytes (bf16 or fp32),
+// row stride ld_bytes, box 32 x 32, no swizzle, zero fill out of bounds.  False if the
+// layout does not meet the tensor-map rules (the kernel then reads the input directly).
+bool make_aux_map(CUtensorMap* m, const void* base, long long rows, int cols, size_t ld_bytes,
+                  int es) {
+  EncodeTiledFn enc = encoder();
+  if (!enc || !base || rows <= 0 || cols <= 0) return false;
+  if (((uintptr_t)base & 15) || (ld_bytes & 15) || ld_bytes == 0) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld_bytes};
+  const cuuint32_t box[2] = {32, 32};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(m, es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+             const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The epilogue input of a mode as a tensor map (1), or 0 when it has none or it is read
+// directly (a broadcast row or a layout the tensor-map rules do not admit).
+template <int MODE>
+int aux_map(CUtensorMap* tx, const EpiParams& ep, int M, int N) {
+  if constexpr (aux_kind<MODE>() == 1) {
+    const bool dz = MODE == EPI_DSILU;
+    const __nv_bfloat16* src = dz ? ep.zb : ep.resb;
+    const int ld = dz ? ep.ldz : ep.ldr;
+    return ld > 0 && make_aux_map(tx, src, M, N, (size_t)ld * 2, 2);
+  } else if constexpr (MODE == EPI_RES) {
+    return ep.ldr > 0 && ep.split > 0 &&
+           make_aux_map(tx, ep.res, M, ep.split < N ? ep.split : N, (size_t)ep.ldr * 4, 4);
+  } else if constexpr (MODE == EPI_ACC) {
+    return make_aux_map(tx, ep.out, M, N, (size_t)ep.ldo * 4, 4);
+  }
+  return 0;
+}
+
 template <int MODE, int NW>
 bool launch_nw(const CUtensorMap& ta, const CUtensorMap& ta2, const CUtensorMap& tb, int M, int N,
                int K, int k1c, int nslices, int nbw, int stages, const EpiParams& ep, int* err,
@@ -474,13 +900,61 @@ bool launch_nw(const CUtensorMap& ta, const CUtensorMap& ta2, const CUtensorMap&
       return false;
     attr_set = true;
   }
-  const size_t bytes = gemm_pipe_bytes(MODE, NW, stages, nbw) + 1024 + 256;   // align + bars
+  CUtensorMap tx = ta;
+  int aux_tma = aux_map<MODE>(&tx, ep, M, N);
+  const size_t base_bytes = gemm_pipe_bytes(MODE, NW, stages, nbw) + 1024 + 256;  // align + bars
+  size_t bytes = base_bytes;
+  if (aux_tma && !aux_in_ring<MODE>()) bytes += (size_t)NW * aux_tile_bytes<MODE>();
+  if (bytes > 200 * 1024) {   // a deep ring leaves no room: the inputs are read directly
+    aux_tma = 0;
+    bytes = base_bytes;
+  }
   if (bytes > 200 * 1024) return false;
   // one CTA per (row tile, column slice), the slices of a row tile adjacent so the second
   // reads the A tile from L2
-  k_gemm_tc<MODE, NW><<<ff_cdiv(M, TM) * nslices, 32 * NW, bytes, s>>>(ta, ta2, tb, M, N, K, k1c,
-                                                                       nslices, nbw,
-                                                              stages, ep, err);
+  k_gemm_tc<MODE, NW><<<ff_cdiv(M, TM) * nslices, 32 * NW, bytes, s>>>(
+      ta, ta2, tb, tx, M, N, K, k1c, nslices, nbw, stages, aux_tma, ep, err);
+  return true;
+}
+
+// Persistent launch: one CTA per SM (at most one per tile), the deepest ring that fits.
+template <int MODE>
+bool launch_pp(const CUtensorMap& ta, const CUtensorMap& ta2, const CUtensorMap& tb, int M,
+               int N, int K, int k1c, int nslices, int nbw, const EpiParams& ep, int* err,
+               cudaStream_t s) {
+  static int n_sm = 0;
+  static size_t kMaxSmem = 0;   // the opt-in per-block limit less the static shared memory
+  if (!kMaxSmem) {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa{};
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess ||
+        cudaFuncGetAttributes(&fa, k_gemm_pp<MODE>) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    const size_t lim = (size_t)optin - fa.sharedSizeBytes;
+    if (cudaFuncSetAttribute(k_gemm_pp<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)lim) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    kMaxSmem = lim;
+  }
+  CUtensorMap tx = ta;
+  int aux_tma = aux_map<MODE>(&tx, ep, M, N);
+  constexpr int PP_EW = 4 * pp_na<MODE>();
+  const size_t fixed = (size_t)PP_EW * 32 * 32 * 4 + (size_t)PP_EW * aux_tile_bytes<MODE>() +
+                       1024 + 512;   // epilogue tiles, input tiles, alignment, barriers
+  int stages = 4;
+  while (stages > 1 && pp_ring_bytes(stages, nbw) + fixed > kMaxSmem) --stages;
+  if (pp_ring_bytes(stages, nbw) + fixed > kMaxSmem) return false;
+  const int ntiles = ff_cdiv(M, TM) * nslices;
+  const int grid = ntiles < n_sm ? ntiles : n_sm;
+  k_gemm_pp<MODE><<<grid, pp_threads<MODE>(), pp_ring_bytes(stages, nbw) + fixed, s>>>(
+      ta, ta2, tb, tx, M, N, K, k1c, nslices, nbw, stages, aux_tma, ep, err);
   return true;
 }
 
@@ -488,11 +962,15 @@ template <int MODE>
 bool launch_mode(const CUtensorMap& ta, const CUtensorMap& ta2, const CUtensorMap& tb, int M,
                  int N, int K, int k1c, int nslices, int nbw, int stages, const EpiParams& ep,
                  int* err, cudaStream_t s) {
-  if constexpr (MODE != EPI_HEAD) {   // the readout needs the 8-warp row reduction
+  if (nbw <= 128 && stages == 0)
+    return launch_pp<MODE>(ta, ta2, tb, M, N, K, k1c, nslices, nbw, ep, err, s);
+  if constexpr (MODE != EPI_HEAD) {   // the one-tile readout needs the 8-warp row sums
     if (nbw <= 128)
-      return launch_nw<MODE, 4>(ta, ta2, tb, M, N, K, k1c, nslices, nbw, stages, ep, err, s);
+      return launch_nw<MODE, 4>(ta, ta2, tb, M, N, K, k1c, nslices, nbw, stages < 1 ? 1 : stages,
+                                ep, err, s);
   }
-  return launch_nw<MODE, 8>(ta, ta2, tb, M, N, K, k1c, nslices, nbw, stages, ep, err, s);
+  return launch_nw<MODE, 8>(ta, ta2, tb, M, N, K, k1c, nslices, nbw, stages < 1 ? 2 : stages,
+                            ep, err, s);
 }
 
 using LaunchFn = bool (*)(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, int, int,
@@ -521,9 +999,11 @@ bool launch_gemm_bf16(int mode, int M, int N, int K, const __nv_bfloat16* A, int
   const int Ktot = A2 ? k1c * TK + K2 : K;
   if (A2 && ldb < ((K2 + TK - 1) / TK + k1c) * TK) return false;
   if (slice != 128 && slice != 256) slice = 256;
-  if (mode == EPI_HEAD) {   // row sums need whole rows in one CTA
+  if (mode == EPI_HEAD) {
     if (N > 256) return false;
-    slice = 256;
+    // the persistent kernel adds the row sums of 128-column slices into zeroed outputs;
+    // the one-tile kernel needs whole rows in one CTA
+    if (!(slice == 128 && stages_req == 0)) slice = 256;
   }
   // all column slices in one launch; a partial last slice reads zero-filled B rows and
   // masks its columns >= N
@@ -539,7 +1019,14 @@ bool launch_gemm_bf16(int mode, int M, int N, int K, const __nv_bfloat16* A, int
   // default: 2 stages for 256-column slices (<= 96 KB: two CTAs per SM), 1 for the 4-warp
   // CTAs of narrower slices (<= 32 KB: four per SM, which overlap each other's loads);
   // the autotuner may ask for 2..4
-  const int stages = (stages_req >= 2 && stages_req <= 4) ? stages_req : (nbw > 128 ? 2 : 1);
+  // default: slices of up to 128 columns run the persistent kernel (stages 0: it picks the
+  // deepest ring that fits), 256-column slices two stages (<= 96 KB: two CTAs per SM); the
+  // autotuner may ask for the non-persistent kernel with 1..4 stages
+  const int stages = (stages_req >= 1 && stages_req <= 4) ? stages_req : (nbw > 128 ? 2 : 0);
+  if (mode == EPI_HEAD && nbw <= 128 && stages == 0 &&
+      (cudaMemsetAsync(ep.eout, 0, (size_t)M * sizeof(float), s) != cudaSuccess ||
+       cudaMemsetAsync(ep.gfo, 0, (size_t)M * sizeof(float), s) != cudaSuccess))
+    return false;
   if (!kLaunch[mode](ta, ta2, tb, M, N, Ktot, k1c, nslices, nbw, stages, ep, err, s))
     return false;
   ff_count_launch(1);

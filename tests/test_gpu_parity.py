@@ -494,11 +494,17 @@ def test_autotune_picks_a_valid_tile_and_keeps_results(ff):
     m, pos = _bind(ff, hp, s, precision=1)
     _, Ea0, F0 = m.energy_forces(pos)
     cfg = m.autotune(pos)
-    assert cfg["slice"] in (128, 256) and cfg["stages"] in (0, 2, 3, 4)
+    assert cfg["slice"] in (128, 256) and cfg["stages"] in (0, 1, 2, 3, 4)
     assert cfg["ms_per_evaluation"] > 0
     _, Ea1, F1 = m.energy_forces(pos)
-    # the tile shape changes no arithmetic: the K loop and the accumulation are the same
-    assert torch.equal(Ea0, Ea1) and torch.equal(F0, F1)
+    # the tile shape changes no element-wise arithmetic (same K loop and accumulation); only
+    # the readout's row sums over the 256 latent columns are added in a different order
+    # (two 128-column halves in the persistent kernel, whole rows in the other), an FP32
+    # reordering of 256 terms
+    _, Ea2, F2 = m.energy_forces(pos)
+    assert torch.equal(Ea1, Ea2) and torch.equal(F1, F2)     # deterministic per tile shape
+    assert (Ea1 - Ea0).abs().max().item() <= 1e-5 * Ea0.abs().max().item()
+    assert (F1 - F0).abs().max().item() <= 1e-5 * F0.abs().max().item()
 
 
 @pytest.mark.parametrize("model", ["fm64", "fm256", "fm512"])
