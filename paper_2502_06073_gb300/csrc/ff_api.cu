@@ -207,6 +207,9 @@ struct ff_ctx {
   bool head = false;
   __nv_bfloat16* GZL = nullptr;
   float* E_edge = nullptr; float* gfL = nullptr;
+  // envelope-gradient partials written by the fused RES + SiLU-adjoint GEMMs: one slot per
+  // (fused launch, 128-column slice), ecap floats each
+  float* gfp = nullptr; int gfp_slots = 0;
   // state of the last evaluation
   bool state_valid = false;
   int state_chunks = 0;
@@ -569,6 +572,10 @@ int ensure_workspace(ff_ctx* c, long long ecap, int acap, long long budget_edges
     f32(&c->E_edge, ecap);
     f32(&c->gfL, ecap);
   }
+  if (tc) {
+    c->gfp_slots = c->NL * ((c->D + 127) / 128);
+    f32(&c->gfp, ecap * c->gfp_slots);
+  }
   size_t total = 0;
   for (auto& p : plan) total += (p.second + 255) & ~(size_t)255;
   void* base = nullptr;
@@ -905,15 +912,30 @@ void backward_chunk(ff_ctx* c, int a0, int a1, const double* seed, cudaStream_t 
   int cur = 0, gvb = 0;
   const float inv_sqrt_nu = (float)(1.0 / sqrt((double)hp.avg_num_neighbors));
   const float r2 = (float)(1.0 / sqrt(2.0));
+  // with the persistent tensor-core GEMM, each layer's dE/dx GEMM also applies the SiLU
+  // adjoint of the layer below (its row reduction): bf16 dE/dz out, envelope-gradient
+  // partials per 128-column slice into their own slots (summed in order by the geometric
+  // adjoint)
+  const int kb = c->n2b - 1;
+  const bool rr_fuse = tc && c->tune_stages == 0 && c->tune_slice == 128;
+  const int nsl = (c->D + 127) / 128;
+  int n_gfp = 0;
+  bool rr_done = false;   // dE/dz of the next layer down was produced by the last GEMM
+  int zb0 = 0;            // which of the ping-pong dE/dz buffers holds this layer's
   for (int L = c->NL; L >= 1; --L) {
     const int kl = c->nlat - 1;
-    const bool fused = c->head && L == c->NL;   // dE/dz of this layer came from the readout
-    if (!fused)
+    // dE/dz of this layer came from the readout or from the previous layer's GEMM
+    const bool from_head = c->head && L == c->NL;
+    const bool fused = from_head || rr_done;
+    rr_done = false;
+    if (!fused) {
+      zb0 = 0;
       launch_rowred_bwd(Ec, hp.latent[kl], gx, ldgx, c->zlat[L][kl], c->zlatb[L][kl],
                         hp.latent[kl], c->ef, r2, tc ? nullptr : c->GZ[0], hp.latent[kl],
                         tc ? c->GZb[0] : nullptr, c->gf, s);
-    int gzb = 0;
-    const __nv_bfloat16* gzA = fused ? c->GZL : c->GZb[0];
+    }
+    int gzb = from_head ? 0 : zb0;
+    const __nv_bfloat16* gzA = from_head ? c->GZL : c->GZb[gzb];
     for (int k = kl; k >= 1; --k) {
       EpiParams ep{};
       ep.alpha = (float)(1.0 / sqrt((double)hp.latent[k - 1]));
@@ -957,7 +979,25 @@ void backward_chunk(ff_ctx* c, int a0, int a1, const double* seed, cudaStream_t 
       ep.alpha = (float)(1.0 / sqrt((double)c->ldx));
       ep.out = c->GX[cur]; ep.ldo = c->ldx;
       ep.res = gx; ep.ldr = ldgx; ep.beta = r2; ep.split = c->D;
-      if (!launch_gemm_bf16(EPI_RES, (int)Ec, c->D, hp.latent[0], gzA, hp.latent[0],
+      // the layer below: latent layer L-1 (scale 1/sqrt2) or the two-body MLP (scale 1; its
+      // dE/dz must be bf16, i.e. it has a hidden layer before the last)
+      const bool below_2b = L == 1;
+      const bool fuse_here = rr_fuse && (!below_2b || kb >= 1) &&
+                             (below_2b ? hp.two_body[kb] : hp.latent[kl]) == c->D;
+      int mode = EPI_RES;
+      if (fuse_here) {
+        mode = EPI_RES_DS;
+        ep.zs = below_2b ? c->z2bb[kb] : c->zlatb[L - 1][kl];
+        ep.ldzs = c->D;
+        ep.alpha2 = below_2b ? 1.f : r2;
+        ep.gzo = c->GZb[gzb ^ 1]; ep.ldgzo = c->D;   // not this GEMM's own operand
+        zb0 = gzb ^ 1;
+        ep.f = c->ef + FF_EF_F; ep.ldf = FF_EF_STRIDE;
+        ep.gfp = c->gfp + (size_t)n_gfp * c->wcap; ep.gfp_ld = c->wcap;
+        n_gfp += nsl;
+        rr_done = true;
+      }
+      if (!launch_gemm_bf16(mode, (int)Ec, c->D, hp.latent[0], gzA, hp.latent[0],
                             c->Bcat_b[L], c->bcat_ld, ep, c->flags, s, c->tune_slice,
                             c->tune_stages, c->GWb, c->ldw, c->ldw))
         c->gemm_fail = true;
@@ -974,13 +1014,12 @@ void backward_chunk(ff_ctx* c, int a0, int a1, const double* seed, cudaStream_t 
     gvb ^= 1;
   }
   // two-body MLP: x^0 = f * silu(z_last); the last gradient (dE/dz_0) stays FP32
-  const int kb = c->n2b - 1;
   const bool b16_first = tc && kb >= 1;
-  launch_rowred_bwd(Ec, hp.two_body[kb], gx, ldgx, c->z2b[kb], c->z2bb[kb], hp.two_body[kb],
-                    c->ef, 1.f,
-                    b16_first ? nullptr : c->GZ[0], hp.two_body[kb],
-                    b16_first ? c->GZb[0] : nullptr, c->gf, s);
-  int gzb = 0;
+  if (!rr_done)
+    launch_rowred_bwd(Ec, hp.two_body[kb], gx, ldgx, c->z2b[kb], c->z2bb[kb],
+                      hp.two_body[kb], c->ef, 1.f, b16_first ? nullptr : c->GZ[0],
+                      hp.two_body[kb], b16_first ? c->GZb[0] : nullptr, c->gf, s);
+  int gzb = rr_done ? zb0 : 0;
   for (int k = kb; k >= 1; --k) {
     EpiParams ep{};
     ep.alpha = (float)(1.0 / sqrt((double)hp.two_body[k - 1]));
@@ -994,8 +1033,8 @@ void backward_chunk(ff_ctx* c, int a0, int a1, const double* seed, cudaStream_t 
   const int w0 = hp.two_body[0];
   const float a0f = (float)(1.0 / sqrt((double)(2 * FF_N_SPECIES + hp.n_basis)));
   launch_edge_grad(Ec, w0, hp.n_basis, hp.rc, hp.poly_p, c->lmax, c->ef, c->GZ[gzb], w0,
-                   c->W2b[0] + (size_t)2 * FF_N_SPECIES * w0, a0f, c->gf, c->gY, gy_slices(c),
-                   c->src + e0, c->sys_of, seed, c->g + e0, s);
+                   c->W2b[0] + (size_t)2 * FF_N_SPECIES * w0, a0f, c->gf, c->gfp, n_gfp,
+                   c->wcap, c->gY, gy_slices(c), c->src + e0, c->sys_of, seed, c->g + e0, s);
 }
 
 // chunk plan for the current model list, workspace sized for it

@@ -59,7 +59,12 @@ enum EpiMode {
   // last latent layer with the edge-energy head (tensor-core GEMM, whole rows per CTA):
   // z = alpha acc, s = silu(z), x = beta (res + f s);  eout[row] = sum_col wv x,
   // gfo[row] = beta sum_col wv s,  outb = beta f silu'(z) wv  (dE_ij/dz, bf16)
-  EPI_HEAD = 7
+  EPI_HEAD = 7,
+  // tensor-core GEMM, persistent kernel only: EPI_RES, fused with the SiLU adjoint of the
+  // layer below that the row reduction would otherwise do: with o the RES output and z the
+  // layer's stored pre-activation (zs), gzo = alpha2 f o silu'(z) (bf16) and, per column
+  // slice, gfp[slice * gfp_ld + row] = alpha2 sum_col o silu(z) (the envelope gradient)
+  EPI_RES_DS = 8
 };
 
 struct EpiParams {
@@ -76,6 +81,10 @@ struct EpiParams {
   __nv_bfloat16* outb; int ldob;  // optional bf16 copy of out (tensor-core GEMM only)
   const float* wv;                // EPI_HEAD: readout vector [N]
   float* eout; float* gfo;        // EPI_HEAD: per-row energy and envelope gradient
+  const __nv_bfloat16* zs; int ldzs;   // EPI_RES_DS: pre-activations of the layer below
+  float alpha2;                        // EPI_RES_DS: that layer's residual scale
+  __nv_bfloat16* gzo; int ldgzo;       // EPI_RES_DS: dE/dz out (bf16)
+  float* gfp; long long gfp_ld;        // EPI_RES_DS: envelope-gradient partial per slice
 };
 
 void launch_gemm_f32(int mode, int M, int N, int K, const float* A, int lda, const float* B,
@@ -159,11 +168,13 @@ void launch_rowred_bwd(long long E, int N, const float* gx, int ldgx, const floa
                        float* gz, int ldgz, __nv_bfloat16* gzb, float* gf, cudaStream_t s);
 void launch_cvt_bf16(const float* src, int lds, __nv_bfloat16* dst, int ldd, long long rows,
                      int col0, int ncols, cudaStream_t s);
+// gf: envelope gradient per edge; gfp: n_gfp further partial sums per edge (rows gfp_ld
+// apart), added to gf in order
 void launch_edge_grad(long long E, int w0, int n_basis, float rc, int p, int lmax,
                       const float* ef, const float* gz0, int ldg, const float* WB,
-                      float alpha0, const float* gf, const float* gY, int gy_groups,
-                      const int* src, const int* sys_of, const double* seed, float4* g,
-                      cudaStream_t s);
+                      float alpha0, const float* gf, const float* gfp, int n_gfp,
+                      long long gfp_ld, const float* gY, int gy_groups, const int* src,
+                      const int* sys_of, const double* seed, float4* g, cudaStream_t s);
 void launch_force_gather(int n, const int* row_ptr, const int* rev, const float4* g,
                          float* F, cudaStream_t s);
 void launch_esys(const float* E_atom, const int* sys_ptr, int n_sys, double* E_sys,

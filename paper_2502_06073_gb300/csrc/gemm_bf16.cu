@@ -145,15 +145,18 @@ __device__ __forceinline__ float dsilu_f(float z) {
 // the FP32 residual (RES) or the FP32 output it accumulates into (ACC).
 template <int MODE>
 __host__ __device__ constexpr int aux_kind() {
-  return (MODE == EPI_SILU_RES || MODE == EPI_HEAD || MODE == EPI_DSILU) ? 1
-         : (MODE == EPI_RES || MODE == EPI_ACC)                          ? 2
-                                                                         : 0;
+  return (MODE == EPI_SILU_RES || MODE == EPI_HEAD || MODE == EPI_DSILU)  ? 1
+         : (MODE == EPI_RES || MODE == EPI_ACC || MODE == EPI_RES_DS) ? 2
+                                                                        : 0;
 }
-// Bytes of one warp's epilogue-input tile (32 rows x 32 columns).
+// Bytes of one warp's epilogue-input tile (32 rows x 32 columns); EPI_RES_DS adds the bf16
+// pre-activation tile of the layer below behind its FP32 residual tile.
 template <int MODE>
 __host__ __device__ constexpr int aux_tile_bytes() {
-  return aux_kind<MODE>() == 2 ? 32 * 32 * 4 : aux_kind<MODE>() == 1 ? 32 * 32 * 2 : 0;
+  return (aux_kind<MODE>() == 2 ? 32 * 32 * 4 : aux_kind<MODE>() == 1 ? 32 * 32 * 2 : 0) +
+         (MODE == EPI_RES_DS ? 32 * 32 * 2 : 0);
 }
+constexpr int kZsOff = 32 * 32 * 4;   // EPI_RES_DS: offset of the pre-activation tile
 // The readout's 8-warp CTAs keep two per SM only if their input tiles reuse the stage ring
 // (behind the epilogue tiles and row sums), so there the first tile is loaded once the
 // accumulator is complete; the other modes give them their own region and load the first
@@ -168,9 +171,9 @@ __host__ __device__ constexpr bool aux_in_ring() {
 // (fr) arrive already loaded.
 template <int MODE, int RG>
 __device__ __forceinline__ void epi_batch(const EpiParams& ep, const float4 (&acc)[RG],
-                                          const float4 (&aux)[RG], const float* fr,
-                                          const int* row, int col, bool colok,
-                                          float (*racc)[2]) {
+                                          const float4 (&aux)[RG], const float4 (&zz)[RG],
+                                          const float* fr, const int* row, int col,
+                                          bool colok, float (*racc)[2]) {
   if constexpr (MODE == EPI_HEAD) {
     // readout: partial dot products of this lane's 4 columns, summed over rows later
     if (!colok) return;
@@ -215,8 +218,26 @@ __device__ __forceinline__ void epi_batch(const EpiParams& ep, const float4 (&ac
         else if (MODE == EPI_SILU_F) o[j] = fr[i] * silu_f(v[j]);
         else if (MODE == EPI_SILU_RES) o[j] = ep.beta * (a4[j] + fr[i] * silu_f(v[j]));
         else if (MODE == EPI_DSILU) o[j] = v[j] * dsilu_f(a4[j]);
-        else if (MODE == EPI_RES) o[j] = v[j] + (col < ep.split ? ep.beta * a4[j] : 0.f);
+        else if (MODE == EPI_RES || MODE == EPI_RES_DS)
+          o[j] = v[j] + (col < ep.split ? ep.beta * a4[j] : 0.f);
         else o[j] = a4[j] + v[j];
+      }
+      if (MODE == EPI_RES_DS) {
+        // SiLU adjoint of the layer below (as its row reduction computes it)
+        const float z4[4] = {zz[i].x, zz[i].y, zz[i].z, zz[i].w};
+        float gz[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float sg = sigm_fast(z4[j]);
+          gz[j] = ep.alpha2 * fr[i] * o[j] * (sg * (1.f + z4[j] * (1.f - sg)));
+          racc[i][0] += o[j] * z4[j] * sg;
+        }
+        __nv_bfloat162 lo = __floats2bfloat162_rn(gz[0], gz[1]);
+        __nv_bfloat162 hi = __floats2bfloat162_rn(gz[2], gz[3]);
+        uint2 pk;
+        pk.x = *reinterpret_cast<uint32_t*>(&lo);
+        pk.y = *reinterpret_cast<uint32_t*>(&hi);
+        *reinterpret_cast<uint2*>(ep.gzo + r * ep.ldgzo + col) = pk;
       }
       if (MODE == EPI_SILU || MODE == EPI_SILU_F || MODE == EPI_SILU_RES) {
         __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]);
@@ -251,7 +272,9 @@ __device__ __forceinline__ void epi_rows(const EpiParams& ep, int r0, int M, boo
     const int row = r0 + 4 * i + (lane >> 3);
     rows[i] = (ok && row < M) ? row : -1;
     fr[i] = 0.f;
-    if ((MODE == EPI_SILU_F || MODE == EPI_SILU_RES || MODE == EPI_HEAD) && rows[i] >= 0)
+    if ((MODE == EPI_SILU_F || MODE == EPI_SILU_RES || MODE == EPI_HEAD ||
+         MODE == EPI_RES_DS) &&
+        rows[i] >= 0)
       fr[i] = ep.f[(size_t)rows[i] * ep.ldf];
   }
 }
@@ -267,9 +290,11 @@ template <int MODE, int RG = 8>
 __device__ __forceinline__ bool epi_chunk(const EpiParams& ep, uint32_t taddr, float* tile,
                                           const uint8_t* my_aux, bool use_aux,
                                           uint32_t auxbar, uint32_t aux_par,
-                                          const CUtensorMap* tmX, int nx, int ny,
-                                          const int (&rows)[8], const float (&fr)[8], int col,
-                                          bool colok, float (&racc)[8][2]) {
+                                          const CUtensorMap* tmX, const CUtensorMap* tmX2,
+                                          int nx, int ny, const int (&rows)[8],
+                                          const float (&fr)[8], int col, bool colok,
+                                          float (&racc)[8][2]) {
+  constexpr bool DS = MODE == EPI_RES_DS;   // its pre-activation tile always comes by TMA
   constexpr int AUXB = aux_tile_bytes<MODE>();
   const int lane = threadIdx.x & 31;
   const int gq = lane & 7, rsub = lane >> 3;
@@ -283,16 +308,24 @@ __device__ __forceinline__ bool epi_chunk(const EpiParams& ep, uint32_t taddr, f
   }
   __syncwarp();
   bool okw = true;
-  if (use_aux) okw = __all_sync(0xffffffffu, mbar_wait(auxbar, aux_par));   // one answer
+  if (use_aux || DS) okw = __all_sync(0xffffffffu, mbar_wait(auxbar, aux_par));   // one answer
   // row groups in passes of RG (fewer live registers for RG < 8)
 #pragma unroll
   for (int p = 0; p < 8 / RG; ++p) {
-    float4 acc[RG], aux[RG];
+    float4 acc[RG], aux[RG], zz[RG];
 #pragma unroll
     for (int ii = 0; ii < RG; ++ii) {
       const int rl = 4 * (p * RG + ii) + rsub;
       acc[ii] = *reinterpret_cast<const float4*>(&tile[rl * 32 + 4 * (gq ^ (rl & 7))]);
       aux[ii] = make_float4(0.f, 0.f, 0.f, 0.f);
+      zz[ii] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (DS) {
+        const uint2 pk =
+            *reinterpret_cast<const uint2*>(my_aux + kZsOff + (rl * 32 + 4 * gq) * 2);
+        const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk.x));
+        const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk.y));
+        zz[ii] = make_float4(lo.x, lo.y, hi.x, hi.y);
+      }
     }
     if (use_aux) {
 #pragma unroll
@@ -307,7 +340,7 @@ __device__ __forceinline__ bool epi_chunk(const EpiParams& ep, uint32_t taddr, f
           aux[ii] = make_float4(lo.x, lo.y, hi.x, hi.y);
         }
       }
-    } else if (MODE == EPI_RES && ep.ldr == 0 && colok) {
+    } else if ((MODE == EPI_RES || MODE == EPI_RES_DS) && ep.ldr == 0 && colok) {
       // broadcast residual row (the readout vector): one load for every row of the chunk
       const float4 b = col < ep.split ? *reinterpret_cast<const float4*>(ep.res + col)
                                       : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -336,13 +369,16 @@ __device__ __forceinline__ bool epi_chunk(const EpiParams& ep, uint32_t taddr, f
     }
     if (p == 8 / RG - 1) {
       __syncwarp();   // every lane has read the shared tile and the input tile
-      if (use_aux && okw && lane == 0 && nx >= 0) {
+      if ((use_aux || DS) && okw && lane == 0 && nx >= 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(auxbar, AUXB);
-        tma_load_2d(smem_u32(my_aux), tmX, nx, ny, auxbar);
+        mbar_expect_tx(auxbar, (use_aux ? AUXB - (DS ? 32 * 32 * 2 : 0) : 0) +
+                                   (DS ? 32 * 32 * 2 : 0));
+        if (use_aux) tma_load_2d(smem_u32(my_aux), tmX, nx, ny, auxbar);
+        if (DS) tma_load_2d(smem_u32(my_aux + kZsOff), tmX2, nx, ny, auxbar);
       }
     }
-    epi_batch<MODE, RG>(ep, acc, aux, fr + p * RG, rows + p * RG, col, colok, racc + p * RG);
+    epi_batch<MODE, RG>(ep, acc, aux, zz, fr + p * RG, rows + p * RG, col, colok,
+                        racc + p * RG);
   }
   return okw;
 }
@@ -494,7 +530,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     const int nci = ci + NW / 4;
     const bool wok = epi_chunk<MODE>(
         ep, tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, tile, my_aux,
-        use_aux && aux_ok, smem_u32(&auxf[warp]), k & 1, &tmX,
+        use_aux && aux_ok, smem_u32(&auxf[warp]), k & 1, &tmX, &tmX,
         nci < nchunks ? n0 + nci * 32 : -1, m0 + quad * 32, rows, fr, col,
         cl < nbw && col < N, racc);
     if (!wok && aux_ok) {
@@ -570,7 +606,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 // 128 registers).
 template <int MODE>
 __host__ __device__ constexpr int pp_na() {
-  return (MODE == EPI_HEAD || MODE == EPI_SILU_RES) ? 3 : 4;
+  return (MODE == EPI_HEAD || MODE == EPI_SILU_RES || MODE == EPI_RES_DS) ? 3 : 4;
 }
 template <int MODE>
 __host__ __device__ constexpr int pp_threads() {
@@ -600,8 +636,8 @@ template <int MODE>
 __global__ void __launch_bounds__(pp_threads<MODE>(), 1)
 k_gemm_pp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
           const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmX,
-          int M, int N, int K, int k1c, int nslices, int nbw, int stages, int aux_tma,
-          EpiParams ep, int* __restrict__ err) {
+          const __grid_constant__ CUtensorMap tmX2, int M, int N, int K, int k1c, int nslices,
+          int nbw, int stages, int aux_tma, EpiParams ep, int* __restrict__ err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   constexpr int PP_NA = pp_na<MODE>();
@@ -729,7 +765,11 @@ k_gemm_pp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   } else {
     // ---- epilogue group g = warp / 4, lane quadrant warp & 3
     const int g = warp >> 2, quad = warp & 3;
-    const bool use_aux = AUXB > 0 && aux_tma != 0;
+    constexpr bool DS = MODE == EPI_RES_DS;
+    const bool use_aux = AUXB > 0 && aux_tma != 0;   // the main epilogue input by TMA
+    const bool any_aux = use_aux || DS;              // (DS: its z tile always is)
+    const uint32_t aux_bytes =
+        (use_aux ? AUXB - (DS ? 32 * 32 * 2 : 0) : 0) + (DS ? 32 * 32 * 2 : 0);
     uint8_t* my_aux = auxbuf + (size_t)warp * AUXB;
     float* tile = tiles + warp * 32 * 32;
     const int nchunks = (nbw + 31) / 32;
@@ -739,10 +779,14 @@ k_gemm_pp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     for (int t = blockIdx.x + g * gridDim.x; t < ntiles && good; t += PP_NA * gridDim.x,
              j += PP_NA) {
       const int m0 = (t / nslices) * TM, n0 = (t % nslices) * nbw;
-      if (use_aux && lane == 0) {   // first chunk's inputs, while the accumulator fills
+      if (any_aux && lane == 0) {   // first chunk's inputs, while the accumulator fills
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(smem_u32(&auxf[warp]), AUXB);
-        tma_load_2d(smem_u32(my_aux), &tmX, n0, m0 + quad * 32, smem_u32(&auxf[warp]));
+        mbar_expect_tx(smem_u32(&auxf[warp]), aux_bytes);
+        if (use_aux)
+          tma_load_2d(smem_u32(my_aux), &tmX, n0, m0 + quad * 32, smem_u32(&auxf[warp]));
+        if (DS)
+          tma_load_2d(smem_u32(my_aux + kZsOff), &tmX2, n0, m0 + quad * 32,
+                      smem_u32(&auxf[warp]));
       }
       int rows[8];
       float fr[8];
@@ -752,7 +796,7 @@ k_gemm_pp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       fence_after();
       if (!okacc) {
         good = false;
-        if (use_aux) mbar_wait(smem_u32(&auxf[warp]), aux_n & 1);   // the load still owed
+        if (any_aux) mbar_wait(smem_u32(&auxf[warp]), aux_n & 1);   // the load still owed
         break;
       }
       float racc[8][2];
@@ -764,14 +808,34 @@ k_gemm_pp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         const int col = n0 + cl;
         const bool wok = epi_chunk<MODE, RG>(
             ep, tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)(g * 128 + c0), tile, my_aux,
-            use_aux, smem_u32(&auxf[warp]), aux_n & 1, &tmX,
+            use_aux, smem_u32(&auxf[warp]), aux_n & 1, &tmX, &tmX2,
             ci + 1 < nchunks ? n0 + c0 + 32 : -1, m0 + quad * 32, rows, fr, col,
             cl < nbw && col < N, racc);
-        if (use_aux) ++aux_n;
+        if (any_aux) ++aux_n;
         if (!wok) {
           good = false;   // no further load was started; the timed-out one is owed
           mbar_wait(smem_u32(&auxf[warp]), (aux_n - 1) & 1);
           break;
+        }
+      }
+      if (MODE == EPI_RES_DS && good) {
+        // envelope-gradient partial of this slice: the 8 lanes sharing a row sum their
+        // columns; one lane writes the row's value into the slice's own slot
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          float t = racc[i][0];
+          t += __shfl_xor_sync(0xffffffffu, t, 1);
+          t += __shfl_xor_sync(0xffffffffu, t, 2);
+          t += __shfl_xor_sync(0xffffffffu, t, 4);
+          racc[i][0] = t;
+        }
+        if ((lane & 7) == 0) {
+          float* dst = ep.gfp + (size_t)(n0 / nbw) * ep.gfp_ld;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int row = m0 + quad * 32 + 4 * i + (lane >> 3);
+            if (row < M) dst[row] = ep.alpha2 * racc[i][0];
+          }
         }
       }
       if (MODE == EPI_HEAD && good) {
@@ -880,7 +944,7 @@ int aux_map(CUtensorMap* tx, const EpiParams& ep, int M, int N) {
     const __nv_bfloat16* src = dz ? ep.zb : ep.resb;
     const int ld = dz ? ep.ldz : ep.ldr;
     return ld > 0 && make_aux_map(tx, src, M, N, (size_t)ld * 2, 2);
-  } else if constexpr (MODE == EPI_RES) {
+  } else if constexpr (MODE == EPI_RES || MODE == EPI_RES_DS) {
     return ep.ldr > 0 && ep.split > 0 &&
            make_aux_map(tx, ep.res, M, ep.split < N ? ep.split : N, (size_t)ep.ldr * 4, 4);
   } else if constexpr (MODE == EPI_ACC) {
@@ -943,8 +1007,11 @@ bool launch_pp(const CUtensorMap& ta, const CUtensorMap& ta2, const CUtensorMap&
     }
     kMaxSmem = lim;
   }
-  CUtensorMap tx = ta;
+  CUtensorMap tx = ta, tx2 = ta;
   int aux_tma = aux_map<MODE>(&tx, ep, M, N);
+  if constexpr (MODE == EPI_RES_DS) {
+    if (ep.ldzs <= 0 || !make_aux_map(&tx2, ep.zs, M, N, (size_t)ep.ldzs * 2, 2)) return false;
+  }
   constexpr int PP_EW = 4 * pp_na<MODE>();
   const size_t fixed = (size_t)PP_EW * 32 * 32 * 4 + (size_t)PP_EW * aux_tile_bytes<MODE>() +
                        1024 + 512;   // epilogue tiles, input tiles, alignment, barriers
@@ -954,7 +1021,7 @@ bool launch_pp(const CUtensorMap& ta, const CUtensorMap& ta2, const CUtensorMap&
   const int ntiles = ff_cdiv(M, TM) * nslices;
   const int grid = ntiles < n_sm ? ntiles : n_sm;
   k_gemm_pp<MODE><<<grid, pp_threads<MODE>(), pp_ring_bytes(stages, nbw) + fixed, s>>>(
-      ta, ta2, tb, tx, M, N, K, k1c, nslices, nbw, stages, aux_tma, ep, err);
+      ta, ta2, tb, tx, tx2, M, N, K, k1c, nslices, nbw, stages, aux_tma, ep, err);
   return true;
 }
 
@@ -964,13 +1031,17 @@ bool launch_mode(const CUtensorMap& ta, const CUtensorMap& ta2, const CUtensorMa
                  int* err, cudaStream_t s) {
   if (nbw <= 128 && stages == 0)
     return launch_pp<MODE>(ta, ta2, tb, M, N, K, k1c, nslices, nbw, ep, err, s);
-  if constexpr (MODE != EPI_HEAD) {   // the one-tile readout needs the 8-warp row sums
-    if (nbw <= 128)
-      return launch_nw<MODE, 4>(ta, ta2, tb, M, N, K, k1c, nslices, nbw, stages < 1 ? 1 : stages,
-                                ep, err, s);
+  if constexpr (MODE == EPI_RES_DS) {
+    return false;   // the fused SiLU adjoint exists only in the persistent kernel
+  } else {
+    if constexpr (MODE != EPI_HEAD) {   // the one-tile readout needs the 8-warp row sums
+      if (nbw <= 128)
+        return launch_nw<MODE, 4>(ta, ta2, tb, M, N, K, k1c, nslices, nbw,
+                                  stages < 1 ? 1 : stages, ep, err, s);
+    }
+    return launch_nw<MODE, 8>(ta, ta2, tb, M, N, K, k1c, nslices, nbw, stages < 1 ? 2 : stages,
+                              ep, err, s);
   }
-  return launch_nw<MODE, 8>(ta, ta2, tb, M, N, K, k1c, nslices, nbw, stages < 1 ? 2 : stages,
-                            ep, err, s);
 }
 
 using LaunchFn = bool (*)(const CUtensorMap&, const CUtensorMap&, const CUtensorMap&, int, int,
@@ -979,7 +1050,8 @@ using LaunchFn = bool (*)(const CUtensorMap&, const CUtensorMap&, const CUtensor
 const LaunchFn kLaunch[] = {launch_mode<EPI_STORE>, launch_mode<EPI_SILU>,
                             launch_mode<EPI_SILU_F>, launch_mode<EPI_SILU_RES>,
                             launch_mode<EPI_DSILU>, launch_mode<EPI_RES>,
-                            launch_mode<EPI_ACC>, launch_mode<EPI_HEAD>};
+                            launch_mode<EPI_ACC>, launch_mode<EPI_HEAD>,
+                            launch_mode<EPI_RES_DS>};
 
 }  // namespace
 
@@ -992,7 +1064,7 @@ bool launch_gemm_bf16(int mode, int M, int N, int K, const __nv_bfloat16* A, int
   ProfScope ps_(PC_GEMM_BF16, s);
   if (M <= 0) return true;
   if (N % 16 != 0 || K % 8 != 0 || lda % 8 != 0 || ldb % 8 != 0) return false;
-  if (mode < EPI_STORE || mode > EPI_HEAD) return false;
+  if (mode < EPI_STORE || mode > EPI_RES_DS) return false;
   if (A2 && (K2 <= 0 || K2 % 8 != 0 || lda2 % 8 != 0)) return false;
   // concatenated K: A's columns padded to a whole chunk, then A2's; Bt holds both parts
   const int k1c = A2 ? (K + TK - 1) / TK : (K + TK - 1) / TK + 1;

@@ -252,7 +252,8 @@ void rowred_one(long long E, int N, const float* gx, int ldgx, const float* z,
 __global__ void k_edge_grad(long long E, int w0, int n_basis, float rc, int p, int lmax,
                             const float* __restrict__ ef, const float* __restrict__ gz0, int ldg,
                             const float* __restrict__ WB, float alpha0,
-                            const float* __restrict__ gf, const float* __restrict__ gY,
+                            const float* __restrict__ gf, const float* __restrict__ gfp,
+                            int n_gfp, long long gfp_ld, const float* __restrict__ gY,
                             int gy_groups, const int* __restrict__ src,
                             const int* __restrict__ sys_of, const double* __restrict__ seed,
                             float4* __restrict__ g) {
@@ -285,7 +286,9 @@ __global__ void k_edge_grad(long long E, int w0, int n_basis, float rc, int p, i
     sincosf(a * r, &sn, &cs);
     gr += alpha0 * gB[n - 1] * pref * (a * cs * r - sn) / (r * r);
   }
-  gr += gf[e] * envelope_df(r / rc, p, rc);
+  float gfe = gf[e];
+  for (int k = 0; k < n_gfp; ++k) gfe += gfp[(size_t)k * gfp_ld + e];
+  gr += gfe * envelope_df(r / rc, p, rc);
   // harmonic gradients: partial sums of the channel groups, added in a fixed order
   float gy[9];
 #pragma unroll
@@ -559,13 +562,14 @@ void launch_rowred_bwd(long long E, int N, const float* gx, int ldgx, const floa
 
 void launch_edge_grad(long long E, int w0, int n_basis, float rc, int p, int lmax,
                       const float* ef, const float* gz0, int ldg, const float* WB, float alpha0,
-                      const float* gf, const float* gY, int gy_groups, const int* src,
-                      const int* sys_of, const double* seed, float4* g, cudaStream_t s) {
+                      const float* gf, const float* gfp, int n_gfp, long long gfp_ld,
+                      const float* gY, int gy_groups, const int* src, const int* sys_of,
+                      const double* seed, float4* g, cudaStream_t s) {
   ProfScope ps_(PC_EDGE_GRAD, s);
   if (E <= 0) return;
   k_edge_grad<<<ff_cdiv(E, 256), 256, (size_t)n_basis * w0 * sizeof(float), s>>>(
-      E, w0, n_basis, rc, p, lmax, ef, gz0, ldg, WB, alpha0, gf, gY, gy_groups, src, sys_of,
-      seed, g);
+      E, w0, n_basis, rc, p, lmax, ef, gz0, ldg, WB, alpha0, gf, gfp, n_gfp, gfp_ld, gY,
+      gy_groups, src, sys_of, seed, g);
   ff_count_launch(1);
 }
 
