@@ -214,6 +214,39 @@ def test_forces_fd_of_gpu_energy(ff):
         assert abs(fd - F[a, k].item()) < 2e-3 * max(1.0, abs(fd)), (a, k, fd, F[a, k].item())
 
 
+def test_fd_of_gpu_energy_on_32_random_atoms_csh512(ff):
+    """Finite differences of the GPU's own energy on the periodic 512-atom C-S-H box (FP32,
+    32 random atoms, all three components) against the hand-written adjoint.  Central
+    differences at h = 2e-3 and 1e-3 A, Richardson-extrapolated (error O(h^4)); the energy
+    is the FP64 sum of FP32 per-atom energies, whose rounding (about 1e-8 eV per atom near
+    the displaced one) gives about 1e-4 eV/A of noise in the extrapolated difference, so the
+    bar is 3e-4 eV/A + 1e-5 |F|."""
+    make, name, _ = SYSTEMS["csh512"]
+    s = make()
+    hp = _hp(name, "csh512")
+    m, pos = _bind(ff, hp, s)
+    _, _, F = m.energy_forces(pos)
+    F = F.double().cpu().numpy()
+    atoms = np.random.default_rng(33).choice(s.n, 32, replace=False).tolist()
+
+    def fd(a, k, h):
+        p1, p2 = pos.clone(), pos.clone()
+        p1[a, k] += h
+        p2[a, k] -= h
+        e1 = m.energy_forces(p1, forces=False)[0].item()
+        e2 = m.energy_forces(p2, forces=False)[0].item()
+        return -(e1 - e2) / (2 * h)
+
+    worst = 0.0
+    for a in atoms:
+        for k in range(3):
+            r = (4 * fd(a, k, 1e-3) - fd(a, k, 2e-3)) / 3
+            err = abs(r - F[a, k])
+            assert err <= 3e-4 + 1e-5 * abs(F[a, k]), (a, k, r, F[a, k])
+            worst = max(worst, err)
+    assert worst > 0.0     # the comparison ran on real differences
+
+
 def test_isolated_atom_and_empty_list(ff):
     pos = np.array([[5.0, 5.0, 5.0], [15.0, 15.0, 15.0]])
     s = synth.System("two-far", pos, np.array([8, 1], np.int32), np.array([20.0, 20.0, 20.0]),
