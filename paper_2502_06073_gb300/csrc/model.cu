@@ -10,8 +10,6 @@
 //   f(x)   = 1 - (p+1)(p+2)/2 x^p + p(p+2) x^(p+1) - p(p+1)/2 x^(p+2)  (x = r/rc < 1)
 //   Y_1 = sqrt3 (y, z, x); Y_2 = (sqrt15 xy, sqrt15 yz, sqrt5/2 (3z^2-1), sqrt15 xz,
 //         sqrt15/2 (x^2-y^2))                      (real, component-normalised harmonics)
-#include <algorithm>
-
 #include "ff_internal.cuh"
 
 namespace {
@@ -104,49 +102,37 @@ __global__ void k_twobody_in(long long E, int width, int n_basis, const float* _
                              __nv_bfloat16* __restrict__ preb, float* __restrict__ out,
                              int ldo, __nv_bfloat16* __restrict__ outb, int ldob,
                              int final_layer) {
-  // tpe threads own one edge (4 output columns each) and walk the edges group, group + G,
-  // ...; the thread's slice of the radial weights stays in registers across its edges
-  const int tpe = width >> 2;
+  const int tpe = width >> 2;                 // threads per edge
   const int epb = blockDim.x / tpe;
   const int slot = threadIdx.x / tpe, o = 4 * (threadIdx.x - slot * tpe);
-  if (slot >= epb) return;
-  const long long G = (long long)gridDim.x * epb;
+  const long long e = (long long)blockIdx.x * epb + slot;
+  if (slot >= epb || e >= E) return;
+  const int zi = zz[2 * e], zj = zz[2 * e + 1];
+  const float* bb = ef + e * FF_EF_STRIDE + FF_EF_B;
+  float b[10];
+#pragma unroll
+  for (int n = 0; n < 10; ++n) b[n] = n < n_basis ? bb[n] : 0.f;
+  const float4 ri = *reinterpret_cast<const float4*>(W0 + (zi - 1) * width + o);
+  const float4 rj = *reinterpret_cast<const float4*>(W0 + (FF_N_SPECIES + zj - 1) * width + o);
+  float acc[4] = {ri.x + rj.x, ri.y + rj.y, ri.z + rj.z, ri.w + rj.w};
   const float* wr = W0 + 2 * FF_N_SPECIES * width + o;
-  float4 wb[10];
 #pragma unroll
-  for (int n = 0; n < 10; ++n)
-    wb[n] = n < n_basis ? *reinterpret_cast<const float4*>(wr + n * width)
-                        : make_float4(0.f, 0.f, 0.f, 0.f);
-  for (long long e = (long long)blockIdx.x * epb + slot; e < E; e += G) {
-    const int2 zp = *reinterpret_cast<const int2*>(zz + 2 * e);
-    // the radial basis sits at floats 4..13 of the 16-byte-aligned edge record
-    const float* rec = ef + e * FF_EF_STRIDE;
-    const float4 b0 = *reinterpret_cast<const float4*>(rec + FF_EF_B);
-    const float4 b1 = *reinterpret_cast<const float4*>(rec + FF_EF_B + 4);
-    const float2 b2 = *reinterpret_cast<const float2*>(rec + FF_EF_B + 8);
-    const float b[10] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w, b2.x, b2.y};
-    const float4 ri = *reinterpret_cast<const float4*>(W0 + (zp.x - 1) * width + o);
-    const float4 rj =
-        *reinterpret_cast<const float4*>(W0 + (FF_N_SPECIES + zp.y - 1) * width + o);
-    float acc[4] = {ri.x + rj.x, ri.y + rj.y, ri.z + rj.z, ri.w + rj.w};
-#pragma unroll
-    for (int n = 0; n < 10; ++n) {
-      if (n >= n_basis) break;
-      acc[0] += b[n] * wb[n].x; acc[1] += b[n] * wb[n].y;
-      acc[2] += b[n] * wb[n].z; acc[3] += b[n] * wb[n].w;
-    }
-    const float f = final_layer ? rec[FF_EF_F] : 1.f;
-    float z[4], v[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      z[j] = alpha * acc[j];
-      v[j] = final_layer ? f * silu_f(z[j]) : silu_f(z[j]);
-    }
-    if (preb) store4(preb + e * width + o, z);
-    else store4(pre + e * width + o, z);
-    if (out) store4(out + e * ldo + o, v);
-    if (outb) store4(outb + e * ldob + o, v);
+  for (int n = 0; n < 10; ++n) {
+    if (n >= n_basis) break;
+    const float4 w = *reinterpret_cast<const float4*>(wr + n * width);
+    acc[0] += b[n] * w.x; acc[1] += b[n] * w.y; acc[2] += b[n] * w.z; acc[3] += b[n] * w.w;
   }
+  const float f = final_layer ? ef[e * FF_EF_STRIDE + FF_EF_F] : 1.f;
+  float z[4], v[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    z[j] = alpha * acc[j];
+    v[j] = final_layer ? f * silu_f(z[j]) : silu_f(z[j]);
+  }
+  if (preb) store4(preb + e * width + o, z);
+  else store4(pre + e * width + o, z);
+  if (out) store4(out + e * ldo + o, v);
+  if (outb) store4(outb + e * ldob + o, v);
 }
 
 // E_i = sum over the edges of i of x^N_ij . w_eff (the linear edge-energy MLP folded into
@@ -534,21 +520,8 @@ void launch_twobody_in(long long E, int width, int n_basis, const float* ef, con
   ProfScope ps_(PC_TWOBODY_IN, s);
   if (E <= 0) return;
   const int epb = 256 / (width / 4);
-  // a few edges per thread group (the radial weights load once per thread), the grid a
-  // multiple of the SM count
-  static int n_sm = 0;
-  if (!n_sm) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-      cudaGetLastError();
-      n_sm = 132;
-    }
-  }
-  const long long want = ff_cdiv(E, (long long)epb * 4);
-  const int grid = (int)std::min<long long>(want, (long long)n_sm * 16);
-  k_twobody_in<<<grid, 256, 0, s>>>(E, width, n_basis, ef, zz, W0, alpha, pre, preb, out, ldo,
-                                    outb, ldob, final_layer);
+  k_twobody_in<<<ff_cdiv(E, epb), 256, 0, s>>>(E, width, n_basis, ef, zz, W0, alpha, pre, preb,
+                                               out, ldo, outb, ldob, final_layer);
   ff_count_launch(1);
 }
 
