@@ -82,7 +82,11 @@ typedef struct ff_ctx ff_ctx;
 /* Create a context: validates `hp`, draws every weight from SplitMix64(seed) as
  * U(-sqrt3, sqrt3) (the paper's unit-variance uniform initialisation; Methodology,
  * Model Training) in the documented tensor order, uploads them to the current device.
- * *out receives the handle (NULL on failure).  Errors: FF_ERR_ARG, FF_ERR_OOM,
+ * *out receives the handle (NULL on failure).  Environment read here: FF_WORKSPACE_MB
+ * (per-chunk workspace budget in MiB; default 120 GB or 60 % of the free device memory)
+ * and FF_TEST_STALL_ONCE (tests of the timeout path only: with precision 1 the context's
+ * first tensor-core GEMM withholds a completion signal, so a bounded device wait runs out
+ * and that evaluation returns FF_ERR_TIMEOUT).  Errors: FF_ERR_ARG, FF_ERR_OOM,
  * FF_ERR_CUDA. */
 int ff_create(ff_ctx** out, const ff_hparams* hp, uint64_t seed);
 
@@ -116,7 +120,8 @@ int ff_neighbors(ff_ctx* ctx, const double* pos, const int32_t* Z, int n_atoms,
  *   F       device float[n_atoms][3] or NULL forces -dE/dx (NULL: energy only; the
  *                                            intermediates are kept for ff_forces)
  * Re-filters the Verlet list at rc for `pos` and rebuilds it first when an atom moved
- * more than skin/2 since the last build.  Synchronises `stream` (edge count).
+ * more than skin/2 since the last build.  Synchronises `stream` (edge count, and the
+ * device error word after the evaluation).
  * Errors: FF_ERR_STATE (no ff_neighbors yet), FF_ERR_CAPACITY, FF_ERR_NONFINITE, FF_ERR_OOM,
  * FF_ERR_CUDA, FF_ERR_TIMEOUT (precision 1: a tensor-core pipeline wait ran out). */
 int ff_energy_forces(ff_ctx* ctx, const double* pos, double* E_sys, float* E_atom, float* F,
@@ -126,8 +131,8 @@ int ff_energy_forces(ff_ctx* ctx, const double* pos, double* E_sys, float* E_ato
  *   grad_E  device double[n_sys] or NULL (NULL = all ones)
  *   F       device float[n_atoms][3]
  * Requires the previous ff_energy_forces to have been called with F == NULL and the
- * same positions (the stored intermediates are used).  Errors: FF_ERR_STATE,
- * FF_ERR_CUDA, FF_ERR_TIMEOUT. */
+ * same positions (the stored intermediates are used).  Synchronises `stream` (device error
+ * word).  Errors: FF_ERR_STATE, FF_ERR_CUDA, FF_ERR_TIMEOUT. */
 int ff_forces(ff_ctx* ctx, const double* grad_E, float* F, void* stream);
 
 /* Virial of each system from the edge gradients of the last force evaluation (a
@@ -159,7 +164,9 @@ int ff_md_step(ff_ctx* ctx, double* x, double* v, const double* mass, int n_step
  * on an internal stream ordered after and before `stream`.  Arguments as in
  * ff_energy_forces.  Valid while every atom stays within skin/2 of its position at the
  * last list build (the caller's responsibility; ff_neighbors rebuilds).  ff_forces does
- * not apply to this call.  Errors: FF_ERR_STATE, FF_ERR_OOM, FF_ERR_CUDA. */
+ * not apply to this call.  A replay does not synchronise: a device error of a replay
+ * (FF_ERR_TIMEOUT) is reported by the next call that reads the error word (any other
+ * entry point that synchronises).  Errors: FF_ERR_STATE, FF_ERR_OOM, FF_ERR_CUDA. */
 int ff_energy_forces_graph(ff_ctx* ctx, const double* pos, double* E_sys, float* E_atom,
                            float* F, void* stream);
 

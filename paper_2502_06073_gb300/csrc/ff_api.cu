@@ -210,6 +210,9 @@ struct ff_ctx {
   // envelope-gradient partials written by the fused RES + SiLU-adjoint GEMMs: one slot per
   // (fused launch, 128-column slice), ecap floats each
   float* gfp = nullptr; int gfp_slots = 0;
+  // FF_TEST_STALL_ONCE set at creation: the next tensor-core GEMM launch withholds a
+  // completion signal so that a bounded device wait runs out (tests of the timeout path)
+  bool test_stall_pending = false;
   // state of the last evaluation
   bool state_valid = false;
   int state_chunks = 0;
@@ -788,10 +791,16 @@ void mlp_gemm(ff_ctx* c, int mode, long long M, int N, int K, const float* A32,
               const EpiParams& ep, cudaStream_t s) {
   if (c->hp.precision == 0) {
     launch_gemm_f32(mode, (int)M, N, K, A32, lda, W32, N, ep, s);
-  } else if (!launch_gemm_bf16(mode, (int)M, N, K, Ab, lda, Wt_b, K, ep, c->flags, s,
-                               c->tune_slice, c->tune_stages)) {
-    c->gemm_fail = true;
+    return;
   }
+  EpiParams e2 = ep;
+  if (c->test_stall_pending) {
+    e2.test_stall = 1;
+    c->test_stall_pending = false;
+  }
+  if (!launch_gemm_bf16(mode, (int)M, N, K, Ab, lda, Wt_b, K, e2, c->flags, s, c->tune_slice,
+                        c->tune_stages))
+    c->gemm_fail = true;
 }
 
 void forward_chunk(ff_ctx* c, const double* pos, int a0, int a1, float* E_atom, cudaStream_t s) {
@@ -1078,6 +1087,8 @@ int evaluate(ff_ctx* c, const double* pos, double* E_sys, float* E_atom, float* 
   std::vector<int> starts;
   FF_TRY(plan_and_reserve(c, starts));
   FF_TRY(run_model(c, pos, E_sys, E_atom, F, seed, forces, starts, s));
+  // the error word of this evaluation (a tensor-core pipeline timeout) is reported by it
+  FF_TRY(read_flags(c, s));
   c->g_pos = (forces && !seed) ? pos : nullptr;
   c->state_valid = true;
   c->state_chunks = (int)starts.size() - 1;
@@ -1164,8 +1175,9 @@ int graph_eval(ff_ctx* c, const double* pos, double* E_sys, float* E_atom, float
 int check_rebuild(ff_ctx* c, const double* x, cudaStream_t s) {
   const double lim = 0.5 * (double)c->hp.skin;
   launch_disp_check(x, c->xref, c->n, lim * lim, c->flags + 1, s);
-  FF_CK(c, cudaMemcpyAsync(c->flags_h + 1, c->flags + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
-  FF_CK(c, cudaStreamSynchronize(s));
+  // one read of both words: the displacement flag and the error word of the graph replays
+  // enqueued before it (a tensor-core pipeline timeout)
+  FF_TRY(read_flags(c, s));
   if (c->flags_h[1] || !c->built) {
     FF_CK(c, cudaMemsetAsync(c->flags + 1, 0, sizeof(int), s));
     FF_TRY(build_verlet(c, x, s));
@@ -1189,6 +1201,7 @@ int ff_create(ff_ctx** out, const ff_hparams* hp, uint64_t seed) {
   ff_ctx* c = new ff_ctx();
   c->hp = *hp;
   c->seed = seed;
+  c->test_stall_pending = hp->precision == 1 && getenv("FF_TEST_STALL_ONCE") != nullptr;
   build_structure(c);
   int r = upload_weights(c);
   if (r == FF_OK) r = dalloc(c, &c->flags, 4);
@@ -1343,6 +1356,11 @@ int ff_forces(ff_ctx* c, const double* grad_E, float* F, void* stream) {
   }
   launch_force_gather(c->n, c->row_ptr, c->rev, c->g, F, s);
   FF_CK(c, cudaGetLastError());
+  if (c->gemm_fail) {
+    c->gemm_fail = false;
+    return set_err(c, FF_ERR_CUDA, "tensor-core GEMM launch could not be set up");
+  }
+  FF_TRY(read_flags(c, s));
   c->g_pos = grad_E ? nullptr : c->state_pos;
   return FF_OK;
 }

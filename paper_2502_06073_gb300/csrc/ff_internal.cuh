@@ -85,6 +85,9 @@ struct EpiParams {
   float alpha2;                        // EPI_RES_DS: that layer's residual scale
   __nv_bfloat16* gzo; int ldgzo;       // EPI_RES_DS: dE/dz out (bf16)
   float* gfp; long long gfp_ld;        // EPI_RES_DS: envelope-gradient partial per slice
+  // test hook of the persistent tensor-core GEMM (0 normally): withhold the accumulator
+  // signal of each CTA's first tile so that a bounded wait runs out (FF_FLAG_TIMEOUT)
+  int test_stall;
 };
 
 void launch_gemm_f32(int mode, int M, int N, int K, const float* A, int lda, const float* B,

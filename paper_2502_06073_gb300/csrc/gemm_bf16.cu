@@ -26,6 +26,7 @@ namespace {
 constexpr int TM = 128;
 constexpr int TK = 64;
 constexpr long kWaitLimit = 1L << 24;
+constexpr long kTestWaitLimit = 1L << 16;   // the accumulator wait under the stall test hook
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -615,8 +616,9 @@ __host__ __device__ constexpr int pp_threads() {
 
 // Bounded wait that also gives up once another role has aborted.
 __device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity,
-                                             const volatile int* abort_flag) {
-  for (long it = 0; it < kWaitLimit; ++it) {
+                                             const volatile int* abort_flag,
+                                             long limit = kWaitLimit) {
+  for (long it = 0; it < limit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
     if (it > 32) __nanosleep(128);
@@ -752,7 +754,9 @@ k_gemm_pp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                      (kc > 0 || kk > 0) ? 1u : 0u);
           mma_commit(smem_u32(&empty[st]));
         }
-        if (good) mma_commit(smem_u32(&accf[a]));
+        // (test hook: the accumulator of this CTA's first tile is never signalled, so its
+        // epilogue group's bounded wait runs out and every role leaves through the abort path)
+        if (good && !(ep.test_stall && j == 0)) mma_commit(smem_u32(&accf[a]));
       }
       if (!good) {
         s_fail = 1;
@@ -792,7 +796,8 @@ k_gemm_pp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       float fr[8];
       epi_rows<MODE>(ep, m0 + quad * 32, M, true, lane, rows, fr);
       const bool okacc = __all_sync(
-          0xffffffffu, mbar_wait_ab(smem_u32(&accf[g]), (uint32_t)((j / PP_NA) & 1), &s_abort));
+          0xffffffffu, mbar_wait_ab(smem_u32(&accf[g]), (uint32_t)((j / PP_NA) & 1), &s_abort,
+                                    ep.test_stall ? kTestWaitLimit : kWaitLimit));
       fence_after();
       if (!okacc) {
         good = false;
