@@ -150,7 +150,10 @@ int ff_virial(ff_ctx* ctx, double* W, void* stream);
  *   mass    device double[n_atoms] (amu)
  *   E_pot, E_kin  device double[n_steps * n_sys] or NULL: energies after each step
  * Forces at the starting positions are computed first unless the previous call left
- * them for exactly these positions.  Synchronises `stream` once per step.
+ * them for exactly these positions.  Synchronises `stream` in every step (neighbour
+ * maintenance, which also reads the device error word of the previous step) and once
+ * after the last step (its error word), so a device error is reported by the call in
+ * which it happened.
  * Errors: as ff_energy_forces. */
 int ff_md_step(ff_ctx* ctx, double* x, double* v, const double* mass, int n_steps,
                double dt_fs, double* E_pot, double* E_kin, void* stream);
@@ -181,6 +184,14 @@ int ff_energy_forces_graph(ff_ctx* ctx, const double* pos, double* E_sys, float*
  * precision 0 nothing is timed.  Synchronises `stream`.  Errors: as ff_energy_forces. */
 int ff_autotune(ff_ctx* ctx, const double* pos, int* slice, int* stages, double* ms_best,
                 void* stream);
+
+/* Set the tensor-core GEMM tile configuration explicitly (precision 1; the values
+ * ff_autotune chooses among): slice 128 or 256 output columns per CTA; stages 0 (the
+ * default: persistent kernel for 128-column slices, 2 stages for 256) or 1..4 (the
+ * one-tile kernel with that many pipeline stages).  With any configuration but
+ * (128, 0) the adjoint keeps the separate SiLU row reductions.  Cheap: no device work.
+ * Errors: FF_ERR_ARG. */
+int ff_set_tiles(ff_ctx* ctx, int slice, int stages);
 
 /* enable != 0: ff_md_step uses the frozen-list graph path: per step kick, drift, a
  * displacement check (one flag read; rebuild + recapture when an atom moved more than

@@ -29,7 +29,8 @@ ERRORS = {-1: "FF_ERR_ARG", -2: "FF_ERR_SPECIES", -3: "FF_ERR_OOM", -4: "FF_ERR_
 ABI = ("ff_create", "ff_destroy", "ff_neighbors", "ff_energy_forces", "ff_forces",
        "ff_md_step", "ff_export_params", "ff_get_edges", "ff_kernel_launches", "ff_last_error",
        "ff_profile_enable", "ff_profile_read", "ff_profile_class", "ff_neighbors_noalloc",
-       "ff_energy_forces_graph", "ff_set_graph", "ff_autotune", "ff_virial", "ff_md_nvt")
+       "ff_energy_forces_graph", "ff_set_graph", "ff_autotune", "ff_virial", "ff_md_nvt",
+       "ff_set_tiles")
 
 
 class HParams(ctypes.Structure):
@@ -67,6 +68,7 @@ def load_library(path: str | None = None):
     lib.ff_energy_forces.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.ff_energy_forces_graph.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.ff_set_graph.argtypes = [vp, i32]
+    lib.ff_set_tiles.argtypes = [vp, i32, i32]
     lib.ff_virial.argtypes = [vp, vp, vp]
     lib.ff_md_nvt.argtypes = [vp, vp, vp, vp, i32, ctypes.c_double, ctypes.c_double,
                               ctypes.c_double, vp, vp, vp, vp, vp]
@@ -222,6 +224,10 @@ class FFModel:
         W = torch.empty(self.n_sys, 3, 3, dtype=torch.float64, device="cuda")
         self._check(self.lib.ff_virial(self._h, _ptr(W), _stream(torch)))
         return W
+
+    def set_tiles(self, slice: int, stages: int):
+        """Select the tensor-core GEMM tile configuration (see ff_set_tiles)."""
+        self._check(self.lib.ff_set_tiles(self._h, int(slice), int(stages)))
 
     def set_graph(self, enable: bool = True):
         """Make md() replay a captured CUDA graph on a frozen Verlet list."""

@@ -753,8 +753,9 @@ int update_neighbors(ff_ctx* c, const double* pos, cudaStream_t s) {
   if (!rebuild) {
     const double lim = 0.5 * (double)c->hp.skin;
     launch_disp_check(pos, c->xref, c->n, lim * lim, c->flags + 1, s);
-    FF_CK(c, cudaMemcpyAsync(c->flags_h + 1, c->flags + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
-    FF_CK(c, cudaStreamSynchronize(s));
+    // one read of both words: the displacement flag and the error word of the work
+    // enqueued before it
+    FF_TRY(read_flags(c, s));
     if (c->flags_h[1]) {
       rebuild = true;
       FF_CK(c, cudaMemsetAsync(c->flags + 1, 0, sizeof(int), s));
@@ -1081,14 +1082,16 @@ int run_model(ff_ctx* c, const double* pos, double* E_sys, float* E_atom, float*
   return FF_OK;
 }
 
+// check_err: read the device error word back before returning (an MD loop instead reads
+// it with each step's displacement check and once after its last step).
 int evaluate(ff_ctx* c, const double* pos, double* E_sys, float* E_atom, float* F,
-             const double* seed, bool forces, cudaStream_t s) {
+             const double* seed, bool forces, cudaStream_t s, bool check_err = true) {
   FF_TRY(update_neighbors(c, pos, s));
   std::vector<int> starts;
   FF_TRY(plan_and_reserve(c, starts));
   FF_TRY(run_model(c, pos, E_sys, E_atom, F, seed, forces, starts, s));
   // the error word of this evaluation (a tensor-core pipeline timeout) is reported by it
-  FF_TRY(read_flags(c, s));
+  if (check_err) FF_TRY(read_flags(c, s));
   c->g_pos = (forces && !seed) ? pos : nullptr;
   c->state_valid = true;
   c->state_chunks = (int)starts.size() - 1;
@@ -1402,6 +1405,7 @@ int ff_md_step(ff_ctx* c, double* x, double* v, const double* mass, int n_steps,
       if (E_kin) launch_kinetic(v, mass, c->sys_ptr, c->n_sys, E_kin + (size_t)it * c->n_sys, s);
     }
     FF_CK(c, cudaGetLastError());
+    FF_TRY(read_flags(c, s));   // the last replay (earlier ones: the next step's check)
     c->md_force_pos = x;
     c->md_force_gen = c->eval_gen;
     return FF_OK;
@@ -1412,11 +1416,12 @@ int ff_md_step(ff_ctx* c, double* x, double* v, const double* mass, int n_steps,
     launch_kick(c->n, v, c->F_int, mass, 0.5 * dt_fs, s);
     launch_drift(c->n, x, v, dt_fs, s);
     FF_TRY(evaluate(c, x, E_pot ? E_pot + (size_t)it * c->n_sys : nullptr, nullptr, c->F_int,
-                    nullptr, true, s));
+                    nullptr, true, s, false));
     launch_kick(c->n, v, c->F_int, mass, 0.5 * dt_fs, s);
     if (E_kin) launch_kinetic(v, mass, c->sys_ptr, c->n_sys, E_kin + (size_t)it * c->n_sys, s);
   }
   FF_CK(c, cudaGetLastError());
+  FF_TRY(read_flags(c, s));   // the last step's evaluation (earlier ones: the next step's check)
   c->md_force_pos = x;
   c->md_force_gen = c->eval_gen;
   return FF_OK;
@@ -1482,6 +1487,18 @@ int ff_autotune(ff_ctx* c, const double* pos, int* slice, int* stages, double* m
   return FF_OK;
 }
 
+int ff_set_tiles(ff_ctx* c, int slice, int stages) {
+  if (!c) return FF_ERR_ARG;
+  if ((slice != 128 && slice != 256) || stages < 0 || stages > 4)
+    return set_err(c, FF_ERR_ARG, "slice must be 128 or 256 and stages 0..4");
+  c->tune_slice = slice;
+  c->tune_stages = stages;
+  graph_reset(c);
+  c->state_valid = false;
+  c->md_force_pos = nullptr;
+  return FF_OK;
+}
+
 int ff_set_graph(ff_ctx* c, int enable) {
   if (!c) return FF_ERR_ARG;
   c->graph_md = enable != 0;
@@ -1508,7 +1525,7 @@ int ff_md_nvt(ff_ctx* c, double* x, double* v, const double* mass, int n_steps, 
                    tau_fs, s);
     launch_kick(c->n, v, c->F_int, mass, 0.5 * dt_fs, s);
     launch_drift(c->n, x, v, dt_fs, s);
-    FF_TRY(evaluate(c, x, c->esys_tmp, nullptr, c->F_int, nullptr, true, s));
+    FF_TRY(evaluate(c, x, c->esys_tmp, nullptr, c->F_int, nullptr, true, s, false));
     launch_kick(c->n, v, c->F_int, mass, 0.5 * dt_fs, s);
     launch_nh_half(c->n, c->n_sys, c->sys_ptr, c->sys_of, v, mass, ke, scale, thermo, dt_fs, kT,
                    tau_fs, s);
@@ -1523,6 +1540,7 @@ int ff_md_nvt(ff_ctx* c, double* x, double* v, const double* mass, int n_steps, 
     if (H) launch_nh_energy(c->n_sys, c->sys_ptr, c->esys_tmp, ke, thermo, kT, tau_fs, H + o, s);
   }
   FF_CK(c, cudaGetLastError());
+  FF_TRY(read_flags(c, s));   // the last step's evaluation (earlier ones: the next step's check)
   c->md_force_pos = x;
   c->md_force_gen = c->eval_gen;
   return FF_OK;

@@ -542,6 +542,37 @@ def test_autotune_picks_a_valid_tile_and_keeps_results(ff):
     assert (F1 - F0).abs().max().item() <= 1e-5 * F0.abs().max().item()
 
 
+@pytest.mark.parametrize("slice_,stages", [(128, 0), (128, 1), (128, 3), (256, 0), (256, 4)])
+def test_every_gemm_tile_configuration_vs_oracle(ff, slice_, stages):
+    """Each tile configuration the autotuner may pick -- the persistent kernel (128, 0),
+    whose adjoint fuses the SiLU row reductions into the dE/dx GEMMs, and the one-tile
+    kernel with 128- or 256-column slices and 1-4 stages, whose adjoint runs them
+    separately -- against the FP64 oracle on the 512-atom C-S-H box at the BF16 bars, and
+    deterministic per configuration."""
+    make, name, _ = SYSTEMS["csh512"]
+    s = make()
+    hp = _hp(name, "csh512")
+    m, pos = _bind(ff, hp, s, precision=1)
+    m.set_tiles(slice_, stages)
+    Es, Ea, F = m.energy_forces(pos)
+    _, Ea2, F2 = m.energy_forces(pos)
+    assert torch.equal(Ea, Ea2) and torch.equal(F, F2)
+    E_ref, Ea_ref, F_ref = pool.evaluate(hp, 42, s.pos, s.Z, s.box, s.pbc)
+    d = F.double().cpu().numpy() - F_ref
+    assert np.sqrt((d ** 2).mean()) <= 5e-3 and np.abs(d).max() <= 5e-3
+    Ea = Ea.double().cpu().numpy()
+    assert np.abs(Ea - Ea_ref).max() <= 4e-3 * np.abs(Ea_ref).max()
+    assert abs(Es.item() - E_ref[0]) <= 4e-3 * np.abs(Ea_ref).sum()
+
+
+def test_set_tiles_rejects_bad_values(ff):
+    make, name, _ = SYSTEMS["cubic96"]
+    m = ff.FFModel(_hp(name), seed=1, precision=1)
+    for bad in [(64, 0), (128, 5), (256, -1)]:
+        with pytest.raises(ff.FFError, match="FF_ERR_ARG"):
+            m.set_tiles(*bad)
+
+
 @pytest.mark.parametrize("model", ["fm64", "fm256", "fm512"])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_table1_model_sizes(ff, model, precision):
