@@ -167,13 +167,24 @@ __host__ __device__ constexpr bool aux_in_ring() {
   return MODE == EPI_HEAD;
 }
 
+// Row index of row group i of a lane (rows base + 4i), or -1 outside the matrix: computed
+// on use rather than held in registers.
+struct Rows {
+  int base, lim;   // lim = M, or 0 when the accumulator is invalid
+  __device__ __forceinline__ int operator[](int i) const {
+    const int r = base + 4 * i;
+    return r < lim ? r : -1;
+  }
+  __device__ __forceinline__ Rows shift(int groups) const { return Rows{base + 4 * groups, lim}; }
+};
+
 // Vectorised epilogue of 8 row-groups: lane l of a warp owns 4 consecutive columns of
 // rows r0 + 4i + (l >> 3), i = 0..7.  The epilogue inputs (aux) and the per-row envelope
 // (fr) arrive already loaded.
 template <int MODE, int RG>
 __device__ __forceinline__ void epi_batch(const EpiParams& ep, const float4 (&acc)[RG],
                                           const float4 (&aux)[RG], const float4 (&zz)[RG],
-                                          const float* fr, const int* row, int col,
+                                          const float* fr, Rows row, int col,
                                           bool colok, float (*racc)[2]) {
   if constexpr (MODE == EPI_HEAD) {
     // readout: partial dot products of this lane's 4 columns, summed over rows later
@@ -264,20 +275,20 @@ __device__ __forceinline__ void epi_batch(const EpiParams& ep, const float4 (&ac
 }
 
 // Rows and envelope values of the 8 row groups a lane handles in a warp's 32 tile rows
-// starting at tile row r0 (row -1: outside the matrix or the accumulator is invalid).
+// starting at tile row r0 (invalid rows: outside the matrix, or all when !ok).
 template <int MODE>
-__device__ __forceinline__ void epi_rows(const EpiParams& ep, int r0, int M, bool ok, int lane,
-                                         int (&rows)[8], float (&fr)[8]) {
+__device__ __forceinline__ Rows epi_rows(const EpiParams& ep, int r0, int M, bool ok, int lane,
+                                         float (&fr)[8]) {
+  const Rows rows{r0 + (lane >> 3), ok ? M : 0};
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    const int row = r0 + 4 * i + (lane >> 3);
-    rows[i] = (ok && row < M) ? row : -1;
     fr[i] = 0.f;
     if ((MODE == EPI_SILU_F || MODE == EPI_SILU_RES || MODE == EPI_HEAD ||
          MODE == EPI_RES_DS) &&
         rows[i] >= 0)
       fr[i] = ep.f[(size_t)rows[i] * ep.ldf];
   }
+  return rows;
 }
 
 // One 32-column chunk of a warp's 32 tile rows: the accumulator block (TMEM address taddr)
@@ -292,7 +303,7 @@ __device__ __forceinline__ bool epi_chunk(const EpiParams& ep, uint32_t taddr, f
                                           const uint8_t* my_aux, bool use_aux,
                                           uint32_t auxbar, uint32_t aux_par,
                                           const CUtensorMap* tmX, const CUtensorMap* tmX2,
-                                          int nx, int ny, const int (&rows)[8],
+                                          int nx, int ny, Rows rows,
                                           const float (&fr)[8], int col, bool colok,
                                           float (&racc)[8][2]) {
   constexpr bool DS = MODE == EPI_RES_DS;   // its pre-activation tile always comes by TMA
@@ -378,7 +389,7 @@ __device__ __forceinline__ bool epi_chunk(const EpiParams& ep, uint32_t taddr, f
         if (DS) tma_load_2d(smem_u32(my_aux + kZsOff), tmX2, nx, ny, auxbar);
       }
     }
-    epi_batch<MODE, RG>(ep, acc, aux, zz, fr + p * RG, rows + p * RG, col, colok,
+    epi_batch<MODE, RG>(ep, acc, aux, zz, fr + p * RG, rows.shift(p * RG), col, colok,
                         racc + p * RG);
   }
   return okw;
@@ -515,9 +526,8 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     tma_load_2d(smem_u32(my_aux), &tmX, n0 + half * 32, m0 + quad * 32, smem_u32(&auxf[warp]));
   }
   float* tile = reinterpret_cast<float*>(smem) + warp * 32 * 32;
-  int rows[8];
   float fr[8];
-  epi_rows<MODE>(ep, m0 + quad * 32, M, ok, lane, rows, fr);
+  const Rows rows = epi_rows<MODE>(ep, m0 + quad * 32, M, ok, lane, fr);
   bool aux_ok = true;
   int aux_fail_k = 0;
   float racc[8][2];
@@ -602,9 +612,9 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 // Every wait is bounded; a timeout sets FF_FLAG_TIMEOUT, and s_abort makes the other roles
 // leave their loops at their next wait.
 // Accumulator buffers (epilogue groups) per mode: four, with the epilogue in passes of 4 row
-// groups so that 18 warps fit the register file (96 registers a thread); the residual update
-// and the readout (sixteen row sums per lane) need more registers and get three (14 warps,
-// 128 registers).
+// groups so that 18 warps fit the register file (96 registers a thread); the readout
+// (sixteen row sums per lane), the residual update and RES_DS (two input tiles, dE/dz out)
+// need more registers and get three (14 warps, 128 registers).
 template <int MODE>
 __host__ __device__ constexpr int pp_na() {
   return (MODE == EPI_HEAD || MODE == EPI_SILU_RES || MODE == EPI_RES_DS) ? 3 : 4;
@@ -792,9 +802,8 @@ k_gemm_pp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
           tma_load_2d(smem_u32(my_aux + kZsOff), &tmX2, n0, m0 + quad * 32,
                       smem_u32(&auxf[warp]));
       }
-      int rows[8];
       float fr[8];
-      epi_rows<MODE>(ep, m0 + quad * 32, M, true, lane, rows, fr);
+      const Rows rows = epi_rows<MODE>(ep, m0 + quad * 32, M, true, lane, fr);
       const bool okacc = __all_sync(
           0xffffffffu, mbar_wait_ab(smem_u32(&accf[g]), (uint32_t)((j / PP_NA) & 1), &s_abort,
                                     ep.test_stall ? kTestWaitLimit : kWaitLimit));
