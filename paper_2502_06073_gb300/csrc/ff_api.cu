@@ -410,8 +410,20 @@ int upload_weights(ff_ctx* c) {
     const Tensor* t = find_tensor(c, "Wenv." + std::to_string(L));
     put(&c->Wenv[L], t, false);
     put(&c->WenvT[L], t, true);
-    // path weights transposed to [channel][path]: each thread reads its own row
-    if (L < c->NL) put(&c->theta[L], find_tensor(c, "theta." + std::to_string(L)), true);
+    // path weights transposed to [channel][path] (each thread reads its own row) and
+    // multiplied by 1/sqrt(paths into the output irrep) in FP32, the product the tensor
+    // product applies to every edge
+    if (L < c->NL) {
+      const size_t base = host.size();
+      put(&c->theta[L], find_tensor(c, "theta." + std::to_string(L)), true);
+      const TPKindInfo* k = tp_kind(c->lmax, c->layer_ink[L], c->layer_outk[L]);
+      const float* sc = kTPPathScale[k - kTPKinds];
+      for (int ch = 0; ch < c->C; ++ch)
+        for (int q = 0; q < k->n_paths; ++q) {
+          float& t = host[base + (size_t)ch * k->n_paths + q];
+          t = t * sc[q];
+        }
+    }
     for (int k = 0; k < c->nlat; ++k) {
       const Tensor* tl = find_tensor(c, "Wlat." + std::to_string(L) + "." + std::to_string(k));
       put(&c->Wlat[L][k], tl, false);

@@ -28,6 +28,7 @@ from __future__ import annotations
 
 import math
 import os
+import struct
 import sys
 from fractions import Fraction
 
@@ -177,6 +178,11 @@ def offsets(irreps):
     return off, o
 
 
+def f32(x):
+    """x rounded to float32 (the value of the literal fl(x) in CUDA)."""
+    return struct.unpack("f", struct.pack("f", x))[0]
+
+
 def fl(x):
     s = repr(float(x))
     if "e" not in s and "." not in s:
@@ -203,6 +209,7 @@ def gen_kind(lmax, in_kind, out_kind):
     lines.append(f"  static constexpr int NP = {len(full)}, DIN = {din}, "
                  f"DOUT = {max(dout, 1)}, NS = {len(scal)}, NPW = {0 if last else len(full)};")
     # forward
+    lines.append("  template <int TS>")
     lines.append("  static __device__ __forceinline__ void fwd(const float* __restrict__ v, "
                  "const float* __restrict__ g, const float* __restrict__ th, float* s, float* vo) {")
     if not last:
@@ -222,14 +229,14 @@ def gen_kind(lmax, in_kind, out_kind):
         if out == (0, 1):
             lines.append(f"      s[{scal.index(q)}] = t0;")
         if not last:
-            k = 1.0 / math.sqrt(n_into[out])
             oo = off_out[outs.index(out)]
-            lines.append(f"      const float w = th[{q}] * {fl(k)};")
+            lines.append(f"      const float w = th[{q} * TS];")
             for c in range(2 * l3 + 1):
                 lines.append(f"      vo[{oo + c}] += w * t{c};")
         lines.append("    }")
     lines.append("  }")
     # backward
+    lines.append("  template <int TS>")
     lines.append("  static __device__ __forceinline__ void bwd(const float* __restrict__ v, "
                  "const float* __restrict__ g, const float* __restrict__ th, "
                  "const float* __restrict__ gs, const float* __restrict__ gvo, "
@@ -240,9 +247,8 @@ def gen_kind(lmax, in_kind, out_kind):
         C = coupling_real(l1, l2, l3)
         lines.append(f"    {{ // path {q}")
         if not last:
-            k = 1.0 / math.sqrt(n_into[out])
             oo = off_out[outs.index(out)]
-            lines.append(f"      const float w = th[{q}] * {fl(k)};")
+            lines.append(f"      const float w = th[{q} * TS];")
         for c in range(2 * l3 + 1):
             parts = []
             if out == (0, 1) and c == 0:
@@ -251,15 +257,27 @@ def gen_kind(lmax, in_kind, out_kind):
                 parts.append(f"w * gvo[{oo + c}]")
             lines.append(f"      const float gt{c} = " + (" + ".join(parts) if parts else "0.f")
                          + ";")
+        # one product |C| gt_c per (output component, float32 magnitude), shared by the
+        # entries of either sign: fma(-s, x, y) equals y + (C gt_c) x exactly for C < 0
+        prods = {}
         for (a, b, c), val in sorted(C.items()):
-            lines.append(f"      gv[{off_in[i_in] + a}] += {fl(val)} * gt{c} * g[{goff[l2] + b}];"
-                         f" gg[{goff[l2] + b}] += {fl(val)} * gt{c} * v[{off_in[i_in] + a}];")
+            mag = f32(abs(val))
+            if (c, mag) not in prods:
+                name = f"s{c}_{len([k for k in prods if k[0] == c])}"
+                prods[(c, mag)] = name
+                rhs = f"gt{c}" if mag == 1.0 else f"{fl(abs(val))} * gt{c}"
+                lines.append(f"      const float {name} = {rhs};")
+            sv = ("" if val > 0 else "-") + prods[(c, mag)]
+            ia, ib = off_in[i_in] + a, goff[l2] + b
+            lines.append(f"      gv[{ia}] = fmaf({sv}, g[{ib}], gv[{ia}]);"
+                         f" gg[{ib}] = fmaf({sv}, v[{ia}], gg[{ib}]);")
         lines.append("    }")
     lines.append("  }")
     lines.append(f"  static constexpr int NNZ = {nnz_total};")
     lines.append("};")
+    scale = [1.0 / math.sqrt(n_into[p[2]]) for p in full]
     return name, lines, dict(np=len(full), kept=len(kept), din=din, dout=dout, ns=len(scal),
-                             nnz=nnz_total, irr_in=irr_in, outs=outs)
+                             nnz=nnz_total, irr_in=irr_in, outs=outs, scale=scale)
 
 
 def main(out_path):
@@ -291,6 +309,13 @@ def main(out_path):
                    f"{info['dout']}, {info['ns']}, {info['nnz']}}},")
     hdr.append("};")
     hdr.append(f"static const int kNumTPKinds = {len(table)};")
+    maxp = max(info["np"] for (_, _, _, info) in table)
+    hdr.append("// 1/sqrt(paths into the output irrep) of every path, per kind (rows as above): the")
+    hdr.append("// weights are stored as theta_path times this, and fwd/bwd read them at th[q * TS].")
+    hdr.append(f"static const float kTPPathScale[][{maxp}] = {{")
+    for (_, _, _, info) in table:
+        hdr.append("  {" + ", ".join(fl(x) for x in info["scale"]) + "},")
+    hdr.append("};")
     hdr.append("")
     with open(out_path, "w") as f:
         f.write("\n".join(hdr + body) + "\n")

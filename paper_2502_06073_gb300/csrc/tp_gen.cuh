@@ -25,24 +25,41 @@ static const TPKindInfo kTPKinds[] = {
   {2, 2, 1, 30, 15, 18, 9, 3, 137},
 };
 static const int kNumTPKinds = 12;
+// 1/sqrt(paths into the output irrep) of every path, per kind (rows as above): the
+// weights are stored as theta_path times this, and fwd/bwd read them at th[q * TS].
+static const float kTPPathScale[][30] = {
+  {0.7071067811865475f, 0.7071067811865475f, 0.7071067811865475f, 0.7071067811865475f, 1.0f},
+  {0.7071067811865475f, 0.7071067811865475f, 0.7071067811865475f, 0.7071067811865475f, 1.0f},
+  {0.7071067811865475f, 0.7071067811865475f},
+  {0.7071067811865475f, 0.5773502691896258f, 0.5773502691896258f, 0.7071067811865475f, 0.7071067811865475f, 0.7071067811865475f, 1.0f, 0.5773502691896258f},
+  {0.7071067811865475f, 0.5773502691896258f, 0.5773502691896258f, 0.7071067811865475f, 0.7071067811865475f, 0.7071067811865475f, 1.0f, 0.5773502691896258f},
+  {0.7071067811865475f, 0.5773502691896258f, 0.7071067811865475f, 0.5773502691896258f, 0.5773502691896258f, 0.7071067811865475f, 0.5773502691896258f, 0.5773502691896258f, 0.7071067811865475f, 0.5773502691896258f},
+  {0.5773502691896258f, 0.5f, 0.5f, 0.5f, 0.5773502691896258f, 0.7071067811865475f, 0.5f, 0.5f, 0.7071067811865475f, 0.5f, 0.5f, 0.7071067811865475f, 0.5773502691896258f, 0.7071067811865475f, 0.5f},
+  {0.5773502691896258f, 0.5f, 0.5f, 0.5f, 0.5773502691896258f, 0.7071067811865475f, 0.5f, 0.5f, 0.7071067811865475f, 0.5f, 0.5f, 0.7071067811865475f, 0.5773502691896258f, 0.7071067811865475f, 0.5f},
+  {0.5773502691896258f, 0.5773502691896258f, 0.5773502691896258f},
+  {0.5773502691896258f, 0.4082482904638631f, 0.4082482904638631f, 0.4082482904638631f, 0.5773502691896258f, 0.4472135954999579f, 0.4082482904638631f, 0.4082482904638631f, 0.4472135954999579f, 0.4472135954999579f, 0.7071067811865475f, 0.4082482904638631f, 0.4472135954999579f, 0.4472135954999579f, 0.4082482904638631f, 0.4082482904638631f, 0.4082482904638631f, 0.4472135954999579f, 0.5773502691896258f, 0.4472135954999579f, 0.4082482904638631f, 0.4472135954999579f, 0.4472135954999579f, 0.4082482904638631f, 0.7071067811865475f, 0.4082482904638631f, 0.4472135954999579f},
+  {0.5773502691896258f, 0.4082482904638631f, 0.4082482904638631f, 0.4082482904638631f, 0.5773502691896258f, 0.4472135954999579f, 0.4082482904638631f, 0.4082482904638631f, 0.4472135954999579f, 0.4472135954999579f, 0.7071067811865475f, 0.4082482904638631f, 0.4472135954999579f, 0.4472135954999579f, 0.4082482904638631f, 0.4082482904638631f, 0.4082482904638631f, 0.4472135954999579f, 0.5773502691896258f, 0.4472135954999579f, 0.4082482904638631f, 0.4472135954999579f, 0.4472135954999579f, 0.4082482904638631f, 0.7071067811865475f, 0.4082482904638631f, 0.4472135954999579f},
+  {0.5773502691896258f, 0.4082482904638631f, 0.4082482904638631f, 0.5773502691896258f, 0.4082482904638631f, 0.4082482904638631f, 0.4082482904638631f, 0.5773502691896258f, 0.4082482904638631f, 0.4082482904638631f, 0.4082482904638631f, 0.4082482904638631f, 0.4082482904638631f, 0.5773502691896258f, 0.4082482904638631f, 0.4082482904638631f, 0.4082482904638631f, 0.4082482904638631f, 0.4082482904638631f, 0.4082482904638631f, 0.4082482904638631f, 0.5773502691896258f, 0.4082482904638631f, 0.4082482904638631f, 0.4082482904638631f, 0.4082482904638631f, 0.4082482904638631f, 0.5773502691896258f, 0.4082482904638631f, 0.4082482904638631f},
+};
 
 template <> struct TP<1, 0, 0> {
   // in irreps [(0, 1), (1, -1)]; out irreps [(0, 1), (1, -1), (1, 1)]
   static constexpr int NP = 5, DIN = 4, DOUT = 7, NS = 2, NPW = 5;
+  template <int TS>
   static __device__ __forceinline__ void fwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, float* s, float* vo) {
     #pragma unroll
     for (int k = 0; k < 7; ++k) vo[k] = 0.f;
     { // path 0: (0, 1) x (0,1) -> (0, 1)
       const float t0 = 1.0f * v[0] * g[0];
       s[0] = t0;
-      const float w = th[0] * 0.7071067811865475f;
+      const float w = th[0 * TS];
       vo[0] += w * t0;
     }
     { // path 1: (0, 1) x (1,-1) -> (1, -1)
       const float t0 = 0.9999999999999999f * v[0] * g[1];
       const float t1 = 1.0000000000000002f * v[0] * g[2];
       const float t2 = 0.9999999999999999f * v[0] * g[3];
-      const float w = th[1] * 0.7071067811865475f;
+      const float w = th[1 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
@@ -51,7 +68,7 @@ template <> struct TP<1, 0, 0> {
       const float t0 = 0.9999999999999999f * v[1] * g[0];
       const float t1 = 1.0000000000000002f * v[2] * g[0];
       const float t2 = 0.9999999999999999f * v[3] * g[0];
-      const float w = th[2] * 0.7071067811865475f;
+      const float w = th[2 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
@@ -59,61 +76,73 @@ template <> struct TP<1, 0, 0> {
     { // path 3: (1, -1) x (1,-1) -> (0, 1)
       const float t0 = 0.5773502691896257f * v[1] * g[1] + 0.5773502691896258f * v[2] * g[2] + 0.5773502691896257f * v[3] * g[3];
       s[1] = t0;
-      const float w = th[3] * 0.7071067811865475f;
+      const float w = th[3 * TS];
       vo[0] += w * t0;
     }
     { // path 4: (1, -1) x (1,-1) -> (1, 1)
       const float t0 = 0.7071067811865476f * v[2] * g[3] + -0.7071067811865476f * v[3] * g[2];
       const float t1 = -0.7071067811865476f * v[1] * g[3] + 0.7071067811865476f * v[3] * g[1];
       const float t2 = 0.7071067811865476f * v[1] * g[2] + -0.7071067811865476f * v[2] * g[1];
-      const float w = th[4] * 1.0f;
+      const float w = th[4 * TS];
       vo[4] += w * t0;
       vo[5] += w * t1;
       vo[6] += w * t2;
     }
   }
+  template <int TS>
   static __device__ __forceinline__ void bwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, const float* __restrict__ gs, const float* __restrict__ gvo, float* gv, float* gg) {
     { // path 0
-      const float w = th[0] * 0.7071067811865475f;
+      const float w = th[0 * TS];
       const float gt0 = gs[0] + w * gvo[0];
-      gv[0] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[0];
+      const float s0_0 = gt0;
+      gv[0] = fmaf(s0_0, g[0], gv[0]); gg[0] = fmaf(s0_0, v[0], gg[0]);
     }
     { // path 1
-      const float w = th[1] * 0.7071067811865475f;
+      const float w = th[1 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[0] += 0.9999999999999999f * gt0 * g[1]; gg[1] += 0.9999999999999999f * gt0 * v[0];
-      gv[0] += 1.0000000000000002f * gt1 * g[2]; gg[2] += 1.0000000000000002f * gt1 * v[0];
-      gv[0] += 0.9999999999999999f * gt2 * g[3]; gg[3] += 0.9999999999999999f * gt2 * v[0];
+      const float s0_0 = gt0;
+      gv[0] = fmaf(s0_0, g[1], gv[0]); gg[1] = fmaf(s0_0, v[0], gg[1]);
+      const float s1_0 = gt1;
+      gv[0] = fmaf(s1_0, g[2], gv[0]); gg[2] = fmaf(s1_0, v[0], gg[2]);
+      const float s2_0 = gt2;
+      gv[0] = fmaf(s2_0, g[3], gv[0]); gg[3] = fmaf(s2_0, v[0], gg[3]);
     }
     { // path 2
-      const float w = th[2] * 0.7071067811865475f;
+      const float w = th[2 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[1] += 0.9999999999999999f * gt0 * g[0]; gg[0] += 0.9999999999999999f * gt0 * v[1];
-      gv[2] += 1.0000000000000002f * gt1 * g[0]; gg[0] += 1.0000000000000002f * gt1 * v[2];
-      gv[3] += 0.9999999999999999f * gt2 * g[0]; gg[0] += 0.9999999999999999f * gt2 * v[3];
+      const float s0_0 = gt0;
+      gv[1] = fmaf(s0_0, g[0], gv[1]); gg[0] = fmaf(s0_0, v[1], gg[0]);
+      const float s1_0 = gt1;
+      gv[2] = fmaf(s1_0, g[0], gv[2]); gg[0] = fmaf(s1_0, v[2], gg[0]);
+      const float s2_0 = gt2;
+      gv[3] = fmaf(s2_0, g[0], gv[3]); gg[0] = fmaf(s2_0, v[3], gg[0]);
     }
     { // path 3
-      const float w = th[3] * 0.7071067811865475f;
+      const float w = th[3 * TS];
       const float gt0 = gs[1] + w * gvo[0];
-      gv[1] += 0.5773502691896257f * gt0 * g[1]; gg[1] += 0.5773502691896257f * gt0 * v[1];
-      gv[2] += 0.5773502691896258f * gt0 * g[2]; gg[2] += 0.5773502691896258f * gt0 * v[2];
-      gv[3] += 0.5773502691896257f * gt0 * g[3]; gg[3] += 0.5773502691896257f * gt0 * v[3];
+      const float s0_0 = 0.5773502691896257f * gt0;
+      gv[1] = fmaf(s0_0, g[1], gv[1]); gg[1] = fmaf(s0_0, v[1], gg[1]);
+      gv[2] = fmaf(s0_0, g[2], gv[2]); gg[2] = fmaf(s0_0, v[2], gg[2]);
+      gv[3] = fmaf(s0_0, g[3], gv[3]); gg[3] = fmaf(s0_0, v[3], gg[3]);
     }
     { // path 4
-      const float w = th[4] * 1.0f;
+      const float w = th[4 * TS];
       const float gt0 = w * gvo[4];
       const float gt1 = w * gvo[5];
       const float gt2 = w * gvo[6];
-      gv[1] += 0.7071067811865476f * gt2 * g[2]; gg[2] += 0.7071067811865476f * gt2 * v[1];
-      gv[1] += -0.7071067811865476f * gt1 * g[3]; gg[3] += -0.7071067811865476f * gt1 * v[1];
-      gv[2] += -0.7071067811865476f * gt2 * g[1]; gg[1] += -0.7071067811865476f * gt2 * v[2];
-      gv[2] += 0.7071067811865476f * gt0 * g[3]; gg[3] += 0.7071067811865476f * gt0 * v[2];
-      gv[3] += 0.7071067811865476f * gt1 * g[1]; gg[1] += 0.7071067811865476f * gt1 * v[3];
-      gv[3] += -0.7071067811865476f * gt0 * g[2]; gg[2] += -0.7071067811865476f * gt0 * v[3];
+      const float s2_0 = 0.7071067811865476f * gt2;
+      gv[1] = fmaf(s2_0, g[2], gv[1]); gg[2] = fmaf(s2_0, v[1], gg[2]);
+      const float s1_0 = 0.7071067811865476f * gt1;
+      gv[1] = fmaf(-s1_0, g[3], gv[1]); gg[3] = fmaf(-s1_0, v[1], gg[3]);
+      gv[2] = fmaf(-s2_0, g[1], gv[2]); gg[1] = fmaf(-s2_0, v[2], gg[1]);
+      const float s0_0 = 0.7071067811865476f * gt0;
+      gv[2] = fmaf(s0_0, g[3], gv[2]); gg[3] = fmaf(s0_0, v[2], gg[3]);
+      gv[3] = fmaf(s1_0, g[1], gv[3]); gg[1] = fmaf(s1_0, v[3], gg[1]);
+      gv[3] = fmaf(-s0_0, g[2], gv[3]); gg[2] = fmaf(-s0_0, v[3], gg[2]);
     }
   }
   static constexpr int NNZ = 16;
@@ -122,20 +151,21 @@ template <> struct TP<1, 0, 0> {
 template <> struct TP<1, 0, 1> {
   // in irreps [(0, 1), (1, -1)]; out irreps [(0, 1), (1, -1)]
   static constexpr int NP = 5, DIN = 4, DOUT = 4, NS = 2, NPW = 5;
+  template <int TS>
   static __device__ __forceinline__ void fwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, float* s, float* vo) {
     #pragma unroll
     for (int k = 0; k < 4; ++k) vo[k] = 0.f;
     { // path 0: (0, 1) x (0,1) -> (0, 1)
       const float t0 = 1.0f * v[0] * g[0];
       s[0] = t0;
-      const float w = th[0] * 0.7071067811865475f;
+      const float w = th[0 * TS];
       vo[0] += w * t0;
     }
     { // path 1: (0, 1) x (1,-1) -> (1, -1)
       const float t0 = 0.9999999999999999f * v[0] * g[1];
       const float t1 = 1.0000000000000002f * v[0] * g[2];
       const float t2 = 0.9999999999999999f * v[0] * g[3];
-      const float w = th[1] * 0.7071067811865475f;
+      const float w = th[1 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
@@ -144,7 +174,7 @@ template <> struct TP<1, 0, 1> {
       const float t0 = 0.9999999999999999f * v[1] * g[0];
       const float t1 = 1.0000000000000002f * v[2] * g[0];
       const float t2 = 0.9999999999999999f * v[3] * g[0];
-      const float w = th[2] * 0.7071067811865475f;
+      const float w = th[2 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
@@ -152,40 +182,49 @@ template <> struct TP<1, 0, 1> {
     { // path 3: (1, -1) x (1,-1) -> (0, 1)
       const float t0 = 0.5773502691896257f * v[1] * g[1] + 0.5773502691896258f * v[2] * g[2] + 0.5773502691896257f * v[3] * g[3];
       s[1] = t0;
-      const float w = th[3] * 0.7071067811865475f;
+      const float w = th[3 * TS];
       vo[0] += w * t0;
     }
   }
+  template <int TS>
   static __device__ __forceinline__ void bwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, const float* __restrict__ gs, const float* __restrict__ gvo, float* gv, float* gg) {
     { // path 0
-      const float w = th[0] * 0.7071067811865475f;
+      const float w = th[0 * TS];
       const float gt0 = gs[0] + w * gvo[0];
-      gv[0] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[0];
+      const float s0_0 = gt0;
+      gv[0] = fmaf(s0_0, g[0], gv[0]); gg[0] = fmaf(s0_0, v[0], gg[0]);
     }
     { // path 1
-      const float w = th[1] * 0.7071067811865475f;
+      const float w = th[1 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[0] += 0.9999999999999999f * gt0 * g[1]; gg[1] += 0.9999999999999999f * gt0 * v[0];
-      gv[0] += 1.0000000000000002f * gt1 * g[2]; gg[2] += 1.0000000000000002f * gt1 * v[0];
-      gv[0] += 0.9999999999999999f * gt2 * g[3]; gg[3] += 0.9999999999999999f * gt2 * v[0];
+      const float s0_0 = gt0;
+      gv[0] = fmaf(s0_0, g[1], gv[0]); gg[1] = fmaf(s0_0, v[0], gg[1]);
+      const float s1_0 = gt1;
+      gv[0] = fmaf(s1_0, g[2], gv[0]); gg[2] = fmaf(s1_0, v[0], gg[2]);
+      const float s2_0 = gt2;
+      gv[0] = fmaf(s2_0, g[3], gv[0]); gg[3] = fmaf(s2_0, v[0], gg[3]);
     }
     { // path 2
-      const float w = th[2] * 0.7071067811865475f;
+      const float w = th[2 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[1] += 0.9999999999999999f * gt0 * g[0]; gg[0] += 0.9999999999999999f * gt0 * v[1];
-      gv[2] += 1.0000000000000002f * gt1 * g[0]; gg[0] += 1.0000000000000002f * gt1 * v[2];
-      gv[3] += 0.9999999999999999f * gt2 * g[0]; gg[0] += 0.9999999999999999f * gt2 * v[3];
+      const float s0_0 = gt0;
+      gv[1] = fmaf(s0_0, g[0], gv[1]); gg[0] = fmaf(s0_0, v[1], gg[0]);
+      const float s1_0 = gt1;
+      gv[2] = fmaf(s1_0, g[0], gv[2]); gg[0] = fmaf(s1_0, v[2], gg[0]);
+      const float s2_0 = gt2;
+      gv[3] = fmaf(s2_0, g[0], gv[3]); gg[0] = fmaf(s2_0, v[3], gg[0]);
     }
     { // path 3
-      const float w = th[3] * 0.7071067811865475f;
+      const float w = th[3 * TS];
       const float gt0 = gs[1] + w * gvo[0];
-      gv[1] += 0.5773502691896257f * gt0 * g[1]; gg[1] += 0.5773502691896257f * gt0 * v[1];
-      gv[2] += 0.5773502691896258f * gt0 * g[2]; gg[2] += 0.5773502691896258f * gt0 * v[2];
-      gv[3] += 0.5773502691896257f * gt0 * g[3]; gg[3] += 0.5773502691896257f * gt0 * v[3];
+      const float s0_0 = 0.5773502691896257f * gt0;
+      gv[1] = fmaf(s0_0, g[1], gv[1]); gg[1] = fmaf(s0_0, v[1], gg[1]);
+      gv[2] = fmaf(s0_0, g[2], gv[2]); gg[2] = fmaf(s0_0, v[2], gg[2]);
+      gv[3] = fmaf(s0_0, g[3], gv[3]); gg[3] = fmaf(s0_0, v[3], gg[3]);
     }
   }
   static constexpr int NNZ = 10;
@@ -194,6 +233,7 @@ template <> struct TP<1, 0, 1> {
 template <> struct TP<1, 0, 2> {
   // in irreps [(0, 1), (1, -1)]; out irreps [(0, 1)]
   static constexpr int NP = 2, DIN = 4, DOUT = 1, NS = 2, NPW = 0;
+  template <int TS>
   static __device__ __forceinline__ void fwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, float* s, float* vo) {
     { // path 0: (0, 1) x (0,1) -> (0, 1)
       const float t0 = 1.0f * v[0] * g[0];
@@ -204,16 +244,19 @@ template <> struct TP<1, 0, 2> {
       s[1] = t0;
     }
   }
+  template <int TS>
   static __device__ __forceinline__ void bwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, const float* __restrict__ gs, const float* __restrict__ gvo, float* gv, float* gg) {
     { // path 0
       const float gt0 = gs[0];
-      gv[0] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[0];
+      const float s0_0 = gt0;
+      gv[0] = fmaf(s0_0, g[0], gv[0]); gg[0] = fmaf(s0_0, v[0], gg[0]);
     }
     { // path 1
       const float gt0 = gs[1];
-      gv[1] += 0.5773502691896257f * gt0 * g[1]; gg[1] += 0.5773502691896257f * gt0 * v[1];
-      gv[2] += 0.5773502691896258f * gt0 * g[2]; gg[2] += 0.5773502691896258f * gt0 * v[2];
-      gv[3] += 0.5773502691896257f * gt0 * g[3]; gg[3] += 0.5773502691896257f * gt0 * v[3];
+      const float s0_0 = 0.5773502691896257f * gt0;
+      gv[1] = fmaf(s0_0, g[1], gv[1]); gg[1] = fmaf(s0_0, v[1], gg[1]);
+      gv[2] = fmaf(s0_0, g[2], gv[2]); gg[2] = fmaf(s0_0, v[2], gg[2]);
+      gv[3] = fmaf(s0_0, g[3], gv[3]); gg[3] = fmaf(s0_0, v[3], gg[3]);
     }
   }
   static constexpr int NNZ = 4;
@@ -222,20 +265,21 @@ template <> struct TP<1, 0, 2> {
 template <> struct TP<1, 1, 0> {
   // in irreps [(0, 1), (1, -1), (1, 1)]; out irreps [(0, 1), (0, -1), (1, -1), (1, 1)]
   static constexpr int NP = 8, DIN = 7, DOUT = 8, NS = 2, NPW = 8;
+  template <int TS>
   static __device__ __forceinline__ void fwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, float* s, float* vo) {
     #pragma unroll
     for (int k = 0; k < 8; ++k) vo[k] = 0.f;
     { // path 0: (0, 1) x (0,1) -> (0, 1)
       const float t0 = 1.0f * v[0] * g[0];
       s[0] = t0;
-      const float w = th[0] * 0.7071067811865475f;
+      const float w = th[0 * TS];
       vo[0] += w * t0;
     }
     { // path 1: (0, 1) x (1,-1) -> (1, -1)
       const float t0 = 0.9999999999999999f * v[0] * g[1];
       const float t1 = 1.0000000000000002f * v[0] * g[2];
       const float t2 = 0.9999999999999999f * v[0] * g[3];
-      const float w = th[1] * 0.5773502691896258f;
+      const float w = th[1 * TS];
       vo[2] += w * t0;
       vo[3] += w * t1;
       vo[4] += w * t2;
@@ -244,7 +288,7 @@ template <> struct TP<1, 1, 0> {
       const float t0 = 0.9999999999999999f * v[1] * g[0];
       const float t1 = 1.0000000000000002f * v[2] * g[0];
       const float t2 = 0.9999999999999999f * v[3] * g[0];
-      const float w = th[2] * 0.5773502691896258f;
+      const float w = th[2 * TS];
       vo[2] += w * t0;
       vo[3] += w * t1;
       vo[4] += w * t2;
@@ -252,14 +296,14 @@ template <> struct TP<1, 1, 0> {
     { // path 3: (1, -1) x (1,-1) -> (0, 1)
       const float t0 = 0.5773502691896257f * v[1] * g[1] + 0.5773502691896258f * v[2] * g[2] + 0.5773502691896257f * v[3] * g[3];
       s[1] = t0;
-      const float w = th[3] * 0.7071067811865475f;
+      const float w = th[3 * TS];
       vo[0] += w * t0;
     }
     { // path 4: (1, -1) x (1,-1) -> (1, 1)
       const float t0 = 0.7071067811865476f * v[2] * g[3] + -0.7071067811865476f * v[3] * g[2];
       const float t1 = -0.7071067811865476f * v[1] * g[3] + 0.7071067811865476f * v[3] * g[1];
       const float t2 = 0.7071067811865476f * v[1] * g[2] + -0.7071067811865476f * v[2] * g[1];
-      const float w = th[4] * 0.7071067811865475f;
+      const float w = th[4 * TS];
       vo[5] += w * t0;
       vo[6] += w * t1;
       vo[7] += w * t2;
@@ -268,96 +312,115 @@ template <> struct TP<1, 1, 0> {
       const float t0 = 0.9999999999999999f * v[4] * g[0];
       const float t1 = 1.0000000000000002f * v[5] * g[0];
       const float t2 = 0.9999999999999999f * v[6] * g[0];
-      const float w = th[5] * 0.7071067811865475f;
+      const float w = th[5 * TS];
       vo[5] += w * t0;
       vo[6] += w * t1;
       vo[7] += w * t2;
     }
     { // path 6: (1, 1) x (1,-1) -> (0, -1)
       const float t0 = 0.5773502691896257f * v[4] * g[1] + 0.5773502691896258f * v[5] * g[2] + 0.5773502691896257f * v[6] * g[3];
-      const float w = th[6] * 1.0f;
+      const float w = th[6 * TS];
       vo[1] += w * t0;
     }
     { // path 7: (1, 1) x (1,-1) -> (1, -1)
       const float t0 = 0.7071067811865476f * v[5] * g[3] + -0.7071067811865476f * v[6] * g[2];
       const float t1 = -0.7071067811865476f * v[4] * g[3] + 0.7071067811865476f * v[6] * g[1];
       const float t2 = 0.7071067811865476f * v[4] * g[2] + -0.7071067811865476f * v[5] * g[1];
-      const float w = th[7] * 0.5773502691896258f;
+      const float w = th[7 * TS];
       vo[2] += w * t0;
       vo[3] += w * t1;
       vo[4] += w * t2;
     }
   }
+  template <int TS>
   static __device__ __forceinline__ void bwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, const float* __restrict__ gs, const float* __restrict__ gvo, float* gv, float* gg) {
     { // path 0
-      const float w = th[0] * 0.7071067811865475f;
+      const float w = th[0 * TS];
       const float gt0 = gs[0] + w * gvo[0];
-      gv[0] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[0];
+      const float s0_0 = gt0;
+      gv[0] = fmaf(s0_0, g[0], gv[0]); gg[0] = fmaf(s0_0, v[0], gg[0]);
     }
     { // path 1
-      const float w = th[1] * 0.5773502691896258f;
+      const float w = th[1 * TS];
       const float gt0 = w * gvo[2];
       const float gt1 = w * gvo[3];
       const float gt2 = w * gvo[4];
-      gv[0] += 0.9999999999999999f * gt0 * g[1]; gg[1] += 0.9999999999999999f * gt0 * v[0];
-      gv[0] += 1.0000000000000002f * gt1 * g[2]; gg[2] += 1.0000000000000002f * gt1 * v[0];
-      gv[0] += 0.9999999999999999f * gt2 * g[3]; gg[3] += 0.9999999999999999f * gt2 * v[0];
+      const float s0_0 = gt0;
+      gv[0] = fmaf(s0_0, g[1], gv[0]); gg[1] = fmaf(s0_0, v[0], gg[1]);
+      const float s1_0 = gt1;
+      gv[0] = fmaf(s1_0, g[2], gv[0]); gg[2] = fmaf(s1_0, v[0], gg[2]);
+      const float s2_0 = gt2;
+      gv[0] = fmaf(s2_0, g[3], gv[0]); gg[3] = fmaf(s2_0, v[0], gg[3]);
     }
     { // path 2
-      const float w = th[2] * 0.5773502691896258f;
+      const float w = th[2 * TS];
       const float gt0 = w * gvo[2];
       const float gt1 = w * gvo[3];
       const float gt2 = w * gvo[4];
-      gv[1] += 0.9999999999999999f * gt0 * g[0]; gg[0] += 0.9999999999999999f * gt0 * v[1];
-      gv[2] += 1.0000000000000002f * gt1 * g[0]; gg[0] += 1.0000000000000002f * gt1 * v[2];
-      gv[3] += 0.9999999999999999f * gt2 * g[0]; gg[0] += 0.9999999999999999f * gt2 * v[3];
+      const float s0_0 = gt0;
+      gv[1] = fmaf(s0_0, g[0], gv[1]); gg[0] = fmaf(s0_0, v[1], gg[0]);
+      const float s1_0 = gt1;
+      gv[2] = fmaf(s1_0, g[0], gv[2]); gg[0] = fmaf(s1_0, v[2], gg[0]);
+      const float s2_0 = gt2;
+      gv[3] = fmaf(s2_0, g[0], gv[3]); gg[0] = fmaf(s2_0, v[3], gg[0]);
     }
     { // path 3
-      const float w = th[3] * 0.7071067811865475f;
+      const float w = th[3 * TS];
       const float gt0 = gs[1] + w * gvo[0];
-      gv[1] += 0.5773502691896257f * gt0 * g[1]; gg[1] += 0.5773502691896257f * gt0 * v[1];
-      gv[2] += 0.5773502691896258f * gt0 * g[2]; gg[2] += 0.5773502691896258f * gt0 * v[2];
-      gv[3] += 0.5773502691896257f * gt0 * g[3]; gg[3] += 0.5773502691896257f * gt0 * v[3];
+      const float s0_0 = 0.5773502691896257f * gt0;
+      gv[1] = fmaf(s0_0, g[1], gv[1]); gg[1] = fmaf(s0_0, v[1], gg[1]);
+      gv[2] = fmaf(s0_0, g[2], gv[2]); gg[2] = fmaf(s0_0, v[2], gg[2]);
+      gv[3] = fmaf(s0_0, g[3], gv[3]); gg[3] = fmaf(s0_0, v[3], gg[3]);
     }
     { // path 4
-      const float w = th[4] * 0.7071067811865475f;
+      const float w = th[4 * TS];
       const float gt0 = w * gvo[5];
       const float gt1 = w * gvo[6];
       const float gt2 = w * gvo[7];
-      gv[1] += 0.7071067811865476f * gt2 * g[2]; gg[2] += 0.7071067811865476f * gt2 * v[1];
-      gv[1] += -0.7071067811865476f * gt1 * g[3]; gg[3] += -0.7071067811865476f * gt1 * v[1];
-      gv[2] += -0.7071067811865476f * gt2 * g[1]; gg[1] += -0.7071067811865476f * gt2 * v[2];
-      gv[2] += 0.7071067811865476f * gt0 * g[3]; gg[3] += 0.7071067811865476f * gt0 * v[2];
-      gv[3] += 0.7071067811865476f * gt1 * g[1]; gg[1] += 0.7071067811865476f * gt1 * v[3];
-      gv[3] += -0.7071067811865476f * gt0 * g[2]; gg[2] += -0.7071067811865476f * gt0 * v[3];
+      const float s2_0 = 0.7071067811865476f * gt2;
+      gv[1] = fmaf(s2_0, g[2], gv[1]); gg[2] = fmaf(s2_0, v[1], gg[2]);
+      const float s1_0 = 0.7071067811865476f * gt1;
+      gv[1] = fmaf(-s1_0, g[3], gv[1]); gg[3] = fmaf(-s1_0, v[1], gg[3]);
+      gv[2] = fmaf(-s2_0, g[1], gv[2]); gg[1] = fmaf(-s2_0, v[2], gg[1]);
+      const float s0_0 = 0.7071067811865476f * gt0;
+      gv[2] = fmaf(s0_0, g[3], gv[2]); gg[3] = fmaf(s0_0, v[2], gg[3]);
+      gv[3] = fmaf(s1_0, g[1], gv[3]); gg[1] = fmaf(s1_0, v[3], gg[1]);
+      gv[3] = fmaf(-s0_0, g[2], gv[3]); gg[2] = fmaf(-s0_0, v[3], gg[2]);
     }
     { // path 5
-      const float w = th[5] * 0.7071067811865475f;
+      const float w = th[5 * TS];
       const float gt0 = w * gvo[5];
       const float gt1 = w * gvo[6];
       const float gt2 = w * gvo[7];
-      gv[4] += 0.9999999999999999f * gt0 * g[0]; gg[0] += 0.9999999999999999f * gt0 * v[4];
-      gv[5] += 1.0000000000000002f * gt1 * g[0]; gg[0] += 1.0000000000000002f * gt1 * v[5];
-      gv[6] += 0.9999999999999999f * gt2 * g[0]; gg[0] += 0.9999999999999999f * gt2 * v[6];
+      const float s0_0 = gt0;
+      gv[4] = fmaf(s0_0, g[0], gv[4]); gg[0] = fmaf(s0_0, v[4], gg[0]);
+      const float s1_0 = gt1;
+      gv[5] = fmaf(s1_0, g[0], gv[5]); gg[0] = fmaf(s1_0, v[5], gg[0]);
+      const float s2_0 = gt2;
+      gv[6] = fmaf(s2_0, g[0], gv[6]); gg[0] = fmaf(s2_0, v[6], gg[0]);
     }
     { // path 6
-      const float w = th[6] * 1.0f;
+      const float w = th[6 * TS];
       const float gt0 = w * gvo[1];
-      gv[4] += 0.5773502691896257f * gt0 * g[1]; gg[1] += 0.5773502691896257f * gt0 * v[4];
-      gv[5] += 0.5773502691896258f * gt0 * g[2]; gg[2] += 0.5773502691896258f * gt0 * v[5];
-      gv[6] += 0.5773502691896257f * gt0 * g[3]; gg[3] += 0.5773502691896257f * gt0 * v[6];
+      const float s0_0 = 0.5773502691896257f * gt0;
+      gv[4] = fmaf(s0_0, g[1], gv[4]); gg[1] = fmaf(s0_0, v[4], gg[1]);
+      gv[5] = fmaf(s0_0, g[2], gv[5]); gg[2] = fmaf(s0_0, v[5], gg[2]);
+      gv[6] = fmaf(s0_0, g[3], gv[6]); gg[3] = fmaf(s0_0, v[6], gg[3]);
     }
     { // path 7
-      const float w = th[7] * 0.5773502691896258f;
+      const float w = th[7 * TS];
       const float gt0 = w * gvo[2];
       const float gt1 = w * gvo[3];
       const float gt2 = w * gvo[4];
-      gv[4] += 0.7071067811865476f * gt2 * g[2]; gg[2] += 0.7071067811865476f * gt2 * v[4];
-      gv[4] += -0.7071067811865476f * gt1 * g[3]; gg[3] += -0.7071067811865476f * gt1 * v[4];
-      gv[5] += -0.7071067811865476f * gt2 * g[1]; gg[1] += -0.7071067811865476f * gt2 * v[5];
-      gv[5] += 0.7071067811865476f * gt0 * g[3]; gg[3] += 0.7071067811865476f * gt0 * v[5];
-      gv[6] += 0.7071067811865476f * gt1 * g[1]; gg[1] += 0.7071067811865476f * gt1 * v[6];
-      gv[6] += -0.7071067811865476f * gt0 * g[2]; gg[2] += -0.7071067811865476f * gt0 * v[6];
+      const float s2_0 = 0.7071067811865476f * gt2;
+      gv[4] = fmaf(s2_0, g[2], gv[4]); gg[2] = fmaf(s2_0, v[4], gg[2]);
+      const float s1_0 = 0.7071067811865476f * gt1;
+      gv[4] = fmaf(-s1_0, g[3], gv[4]); gg[3] = fmaf(-s1_0, v[4], gg[3]);
+      gv[5] = fmaf(-s2_0, g[1], gv[5]); gg[1] = fmaf(-s2_0, v[5], gg[1]);
+      const float s0_0 = 0.7071067811865476f * gt0;
+      gv[5] = fmaf(s0_0, g[3], gv[5]); gg[3] = fmaf(s0_0, v[5], gg[3]);
+      gv[6] = fmaf(s1_0, g[1], gv[6]); gg[1] = fmaf(s1_0, v[6], gg[1]);
+      gv[6] = fmaf(-s0_0, g[2], gv[6]); gg[2] = fmaf(-s0_0, v[6], gg[2]);
     }
   }
   static constexpr int NNZ = 28;
@@ -366,20 +429,21 @@ template <> struct TP<1, 1, 0> {
 template <> struct TP<1, 1, 1> {
   // in irreps [(0, 1), (1, -1), (1, 1)]; out irreps [(0, 1), (1, -1)]
   static constexpr int NP = 8, DIN = 7, DOUT = 4, NS = 2, NPW = 8;
+  template <int TS>
   static __device__ __forceinline__ void fwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, float* s, float* vo) {
     #pragma unroll
     for (int k = 0; k < 4; ++k) vo[k] = 0.f;
     { // path 0: (0, 1) x (0,1) -> (0, 1)
       const float t0 = 1.0f * v[0] * g[0];
       s[0] = t0;
-      const float w = th[0] * 0.7071067811865475f;
+      const float w = th[0 * TS];
       vo[0] += w * t0;
     }
     { // path 1: (0, 1) x (1,-1) -> (1, -1)
       const float t0 = 0.9999999999999999f * v[0] * g[1];
       const float t1 = 1.0000000000000002f * v[0] * g[2];
       const float t2 = 0.9999999999999999f * v[0] * g[3];
-      const float w = th[1] * 0.5773502691896258f;
+      const float w = th[1 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
@@ -388,7 +452,7 @@ template <> struct TP<1, 1, 1> {
       const float t0 = 0.9999999999999999f * v[1] * g[0];
       const float t1 = 1.0000000000000002f * v[2] * g[0];
       const float t2 = 0.9999999999999999f * v[3] * g[0];
-      const float w = th[2] * 0.5773502691896258f;
+      const float w = th[2 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
@@ -396,61 +460,73 @@ template <> struct TP<1, 1, 1> {
     { // path 3: (1, -1) x (1,-1) -> (0, 1)
       const float t0 = 0.5773502691896257f * v[1] * g[1] + 0.5773502691896258f * v[2] * g[2] + 0.5773502691896257f * v[3] * g[3];
       s[1] = t0;
-      const float w = th[3] * 0.7071067811865475f;
+      const float w = th[3 * TS];
       vo[0] += w * t0;
     }
     { // path 7: (1, 1) x (1,-1) -> (1, -1)
       const float t0 = 0.7071067811865476f * v[5] * g[3] + -0.7071067811865476f * v[6] * g[2];
       const float t1 = -0.7071067811865476f * v[4] * g[3] + 0.7071067811865476f * v[6] * g[1];
       const float t2 = 0.7071067811865476f * v[4] * g[2] + -0.7071067811865476f * v[5] * g[1];
-      const float w = th[7] * 0.5773502691896258f;
+      const float w = th[7 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
     }
   }
+  template <int TS>
   static __device__ __forceinline__ void bwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, const float* __restrict__ gs, const float* __restrict__ gvo, float* gv, float* gg) {
     { // path 0
-      const float w = th[0] * 0.7071067811865475f;
+      const float w = th[0 * TS];
       const float gt0 = gs[0] + w * gvo[0];
-      gv[0] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[0];
+      const float s0_0 = gt0;
+      gv[0] = fmaf(s0_0, g[0], gv[0]); gg[0] = fmaf(s0_0, v[0], gg[0]);
     }
     { // path 1
-      const float w = th[1] * 0.5773502691896258f;
+      const float w = th[1 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[0] += 0.9999999999999999f * gt0 * g[1]; gg[1] += 0.9999999999999999f * gt0 * v[0];
-      gv[0] += 1.0000000000000002f * gt1 * g[2]; gg[2] += 1.0000000000000002f * gt1 * v[0];
-      gv[0] += 0.9999999999999999f * gt2 * g[3]; gg[3] += 0.9999999999999999f * gt2 * v[0];
+      const float s0_0 = gt0;
+      gv[0] = fmaf(s0_0, g[1], gv[0]); gg[1] = fmaf(s0_0, v[0], gg[1]);
+      const float s1_0 = gt1;
+      gv[0] = fmaf(s1_0, g[2], gv[0]); gg[2] = fmaf(s1_0, v[0], gg[2]);
+      const float s2_0 = gt2;
+      gv[0] = fmaf(s2_0, g[3], gv[0]); gg[3] = fmaf(s2_0, v[0], gg[3]);
     }
     { // path 2
-      const float w = th[2] * 0.5773502691896258f;
+      const float w = th[2 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[1] += 0.9999999999999999f * gt0 * g[0]; gg[0] += 0.9999999999999999f * gt0 * v[1];
-      gv[2] += 1.0000000000000002f * gt1 * g[0]; gg[0] += 1.0000000000000002f * gt1 * v[2];
-      gv[3] += 0.9999999999999999f * gt2 * g[0]; gg[0] += 0.9999999999999999f * gt2 * v[3];
+      const float s0_0 = gt0;
+      gv[1] = fmaf(s0_0, g[0], gv[1]); gg[0] = fmaf(s0_0, v[1], gg[0]);
+      const float s1_0 = gt1;
+      gv[2] = fmaf(s1_0, g[0], gv[2]); gg[0] = fmaf(s1_0, v[2], gg[0]);
+      const float s2_0 = gt2;
+      gv[3] = fmaf(s2_0, g[0], gv[3]); gg[0] = fmaf(s2_0, v[3], gg[0]);
     }
     { // path 3
-      const float w = th[3] * 0.7071067811865475f;
+      const float w = th[3 * TS];
       const float gt0 = gs[1] + w * gvo[0];
-      gv[1] += 0.5773502691896257f * gt0 * g[1]; gg[1] += 0.5773502691896257f * gt0 * v[1];
-      gv[2] += 0.5773502691896258f * gt0 * g[2]; gg[2] += 0.5773502691896258f * gt0 * v[2];
-      gv[3] += 0.5773502691896257f * gt0 * g[3]; gg[3] += 0.5773502691896257f * gt0 * v[3];
+      const float s0_0 = 0.5773502691896257f * gt0;
+      gv[1] = fmaf(s0_0, g[1], gv[1]); gg[1] = fmaf(s0_0, v[1], gg[1]);
+      gv[2] = fmaf(s0_0, g[2], gv[2]); gg[2] = fmaf(s0_0, v[2], gg[2]);
+      gv[3] = fmaf(s0_0, g[3], gv[3]); gg[3] = fmaf(s0_0, v[3], gg[3]);
     }
     { // path 7
-      const float w = th[7] * 0.5773502691896258f;
+      const float w = th[7 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[4] += 0.7071067811865476f * gt2 * g[2]; gg[2] += 0.7071067811865476f * gt2 * v[4];
-      gv[4] += -0.7071067811865476f * gt1 * g[3]; gg[3] += -0.7071067811865476f * gt1 * v[4];
-      gv[5] += -0.7071067811865476f * gt2 * g[1]; gg[1] += -0.7071067811865476f * gt2 * v[5];
-      gv[5] += 0.7071067811865476f * gt0 * g[3]; gg[3] += 0.7071067811865476f * gt0 * v[5];
-      gv[6] += 0.7071067811865476f * gt1 * g[1]; gg[1] += 0.7071067811865476f * gt1 * v[6];
-      gv[6] += -0.7071067811865476f * gt0 * g[2]; gg[2] += -0.7071067811865476f * gt0 * v[6];
+      const float s2_0 = 0.7071067811865476f * gt2;
+      gv[4] = fmaf(s2_0, g[2], gv[4]); gg[2] = fmaf(s2_0, v[4], gg[2]);
+      const float s1_0 = 0.7071067811865476f * gt1;
+      gv[4] = fmaf(-s1_0, g[3], gv[4]); gg[3] = fmaf(-s1_0, v[4], gg[3]);
+      gv[5] = fmaf(-s2_0, g[1], gv[5]); gg[1] = fmaf(-s2_0, v[5], gg[1]);
+      const float s0_0 = 0.7071067811865476f * gt0;
+      gv[5] = fmaf(s0_0, g[3], gv[5]); gg[3] = fmaf(s0_0, v[5], gg[3]);
+      gv[6] = fmaf(s1_0, g[1], gv[6]); gg[1] = fmaf(s1_0, v[6], gg[1]);
+      gv[6] = fmaf(-s0_0, g[2], gv[6]); gg[2] = fmaf(-s0_0, v[6], gg[2]);
     }
   }
   static constexpr int NNZ = 16;
@@ -459,20 +535,21 @@ template <> struct TP<1, 1, 1> {
 template <> struct TP<1, 2, 1> {
   // in irreps [(0, 1), (0, -1), (1, -1), (1, 1)]; out irreps [(0, 1), (1, -1)]
   static constexpr int NP = 10, DIN = 8, DOUT = 4, NS = 2, NPW = 10;
+  template <int TS>
   static __device__ __forceinline__ void fwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, float* s, float* vo) {
     #pragma unroll
     for (int k = 0; k < 4; ++k) vo[k] = 0.f;
     { // path 0: (0, 1) x (0,1) -> (0, 1)
       const float t0 = 1.0f * v[0] * g[0];
       s[0] = t0;
-      const float w = th[0] * 0.7071067811865475f;
+      const float w = th[0 * TS];
       vo[0] += w * t0;
     }
     { // path 1: (0, 1) x (1,-1) -> (1, -1)
       const float t0 = 0.9999999999999999f * v[0] * g[1];
       const float t1 = 1.0000000000000002f * v[0] * g[2];
       const float t2 = 0.9999999999999999f * v[0] * g[3];
-      const float w = th[1] * 0.5773502691896258f;
+      const float w = th[1 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
@@ -481,7 +558,7 @@ template <> struct TP<1, 2, 1> {
       const float t0 = 0.9999999999999999f * v[2] * g[0];
       const float t1 = 1.0000000000000002f * v[3] * g[0];
       const float t2 = 0.9999999999999999f * v[4] * g[0];
-      const float w = th[4] * 0.5773502691896258f;
+      const float w = th[4 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
@@ -489,61 +566,73 @@ template <> struct TP<1, 2, 1> {
     { // path 5: (1, -1) x (1,-1) -> (0, 1)
       const float t0 = 0.5773502691896257f * v[2] * g[1] + 0.5773502691896258f * v[3] * g[2] + 0.5773502691896257f * v[4] * g[3];
       s[1] = t0;
-      const float w = th[5] * 0.7071067811865475f;
+      const float w = th[5 * TS];
       vo[0] += w * t0;
     }
     { // path 9: (1, 1) x (1,-1) -> (1, -1)
       const float t0 = 0.7071067811865476f * v[6] * g[3] + -0.7071067811865476f * v[7] * g[2];
       const float t1 = -0.7071067811865476f * v[5] * g[3] + 0.7071067811865476f * v[7] * g[1];
       const float t2 = 0.7071067811865476f * v[5] * g[2] + -0.7071067811865476f * v[6] * g[1];
-      const float w = th[9] * 0.5773502691896258f;
+      const float w = th[9 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
     }
   }
+  template <int TS>
   static __device__ __forceinline__ void bwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, const float* __restrict__ gs, const float* __restrict__ gvo, float* gv, float* gg) {
     { // path 0
-      const float w = th[0] * 0.7071067811865475f;
+      const float w = th[0 * TS];
       const float gt0 = gs[0] + w * gvo[0];
-      gv[0] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[0];
+      const float s0_0 = gt0;
+      gv[0] = fmaf(s0_0, g[0], gv[0]); gg[0] = fmaf(s0_0, v[0], gg[0]);
     }
     { // path 1
-      const float w = th[1] * 0.5773502691896258f;
+      const float w = th[1 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[0] += 0.9999999999999999f * gt0 * g[1]; gg[1] += 0.9999999999999999f * gt0 * v[0];
-      gv[0] += 1.0000000000000002f * gt1 * g[2]; gg[2] += 1.0000000000000002f * gt1 * v[0];
-      gv[0] += 0.9999999999999999f * gt2 * g[3]; gg[3] += 0.9999999999999999f * gt2 * v[0];
+      const float s0_0 = gt0;
+      gv[0] = fmaf(s0_0, g[1], gv[0]); gg[1] = fmaf(s0_0, v[0], gg[1]);
+      const float s1_0 = gt1;
+      gv[0] = fmaf(s1_0, g[2], gv[0]); gg[2] = fmaf(s1_0, v[0], gg[2]);
+      const float s2_0 = gt2;
+      gv[0] = fmaf(s2_0, g[3], gv[0]); gg[3] = fmaf(s2_0, v[0], gg[3]);
     }
     { // path 4
-      const float w = th[4] * 0.5773502691896258f;
+      const float w = th[4 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[2] += 0.9999999999999999f * gt0 * g[0]; gg[0] += 0.9999999999999999f * gt0 * v[2];
-      gv[3] += 1.0000000000000002f * gt1 * g[0]; gg[0] += 1.0000000000000002f * gt1 * v[3];
-      gv[4] += 0.9999999999999999f * gt2 * g[0]; gg[0] += 0.9999999999999999f * gt2 * v[4];
+      const float s0_0 = gt0;
+      gv[2] = fmaf(s0_0, g[0], gv[2]); gg[0] = fmaf(s0_0, v[2], gg[0]);
+      const float s1_0 = gt1;
+      gv[3] = fmaf(s1_0, g[0], gv[3]); gg[0] = fmaf(s1_0, v[3], gg[0]);
+      const float s2_0 = gt2;
+      gv[4] = fmaf(s2_0, g[0], gv[4]); gg[0] = fmaf(s2_0, v[4], gg[0]);
     }
     { // path 5
-      const float w = th[5] * 0.7071067811865475f;
+      const float w = th[5 * TS];
       const float gt0 = gs[1] + w * gvo[0];
-      gv[2] += 0.5773502691896257f * gt0 * g[1]; gg[1] += 0.5773502691896257f * gt0 * v[2];
-      gv[3] += 0.5773502691896258f * gt0 * g[2]; gg[2] += 0.5773502691896258f * gt0 * v[3];
-      gv[4] += 0.5773502691896257f * gt0 * g[3]; gg[3] += 0.5773502691896257f * gt0 * v[4];
+      const float s0_0 = 0.5773502691896257f * gt0;
+      gv[2] = fmaf(s0_0, g[1], gv[2]); gg[1] = fmaf(s0_0, v[2], gg[1]);
+      gv[3] = fmaf(s0_0, g[2], gv[3]); gg[2] = fmaf(s0_0, v[3], gg[2]);
+      gv[4] = fmaf(s0_0, g[3], gv[4]); gg[3] = fmaf(s0_0, v[4], gg[3]);
     }
     { // path 9
-      const float w = th[9] * 0.5773502691896258f;
+      const float w = th[9 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[5] += 0.7071067811865476f * gt2 * g[2]; gg[2] += 0.7071067811865476f * gt2 * v[5];
-      gv[5] += -0.7071067811865476f * gt1 * g[3]; gg[3] += -0.7071067811865476f * gt1 * v[5];
-      gv[6] += -0.7071067811865476f * gt2 * g[1]; gg[1] += -0.7071067811865476f * gt2 * v[6];
-      gv[6] += 0.7071067811865476f * gt0 * g[3]; gg[3] += 0.7071067811865476f * gt0 * v[6];
-      gv[7] += 0.7071067811865476f * gt1 * g[1]; gg[1] += 0.7071067811865476f * gt1 * v[7];
-      gv[7] += -0.7071067811865476f * gt0 * g[2]; gg[2] += -0.7071067811865476f * gt0 * v[7];
+      const float s2_0 = 0.7071067811865476f * gt2;
+      gv[5] = fmaf(s2_0, g[2], gv[5]); gg[2] = fmaf(s2_0, v[5], gg[2]);
+      const float s1_0 = 0.7071067811865476f * gt1;
+      gv[5] = fmaf(-s1_0, g[3], gv[5]); gg[3] = fmaf(-s1_0, v[5], gg[3]);
+      gv[6] = fmaf(-s2_0, g[1], gv[6]); gg[1] = fmaf(-s2_0, v[6], gg[1]);
+      const float s0_0 = 0.7071067811865476f * gt0;
+      gv[6] = fmaf(s0_0, g[3], gv[6]); gg[3] = fmaf(s0_0, v[6], gg[3]);
+      gv[7] = fmaf(s1_0, g[1], gv[7]); gg[1] = fmaf(s1_0, v[7], gg[1]);
+      gv[7] = fmaf(-s0_0, g[2], gv[7]); gg[2] = fmaf(-s0_0, v[7], gg[2]);
     }
   }
   static constexpr int NNZ = 16;
@@ -552,20 +641,21 @@ template <> struct TP<1, 2, 1> {
 template <> struct TP<2, 0, 0> {
   // in irreps [(0, 1), (1, -1), (2, 1)]; out irreps [(0, 1), (1, -1), (1, 1), (2, 1), (2, -1)]
   static constexpr int NP = 15, DIN = 9, DOUT = 17, NS = 3, NPW = 15;
+  template <int TS>
   static __device__ __forceinline__ void fwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, float* s, float* vo) {
     #pragma unroll
     for (int k = 0; k < 17; ++k) vo[k] = 0.f;
     { // path 0: (0, 1) x (0,1) -> (0, 1)
       const float t0 = 1.0f * v[0] * g[0];
       s[0] = t0;
-      const float w = th[0] * 0.5773502691896258f;
+      const float w = th[0 * TS];
       vo[0] += w * t0;
     }
     { // path 1: (0, 1) x (1,-1) -> (1, -1)
       const float t0 = 0.9999999999999999f * v[0] * g[1];
       const float t1 = 1.0000000000000002f * v[0] * g[2];
       const float t2 = 0.9999999999999999f * v[0] * g[3];
-      const float w = th[1] * 0.5f;
+      const float w = th[1 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
@@ -576,7 +666,7 @@ template <> struct TP<2, 0, 0> {
       const float t2 = 1.0000000000000002f * v[0] * g[6];
       const float t3 = 1.0f * v[0] * g[7];
       const float t4 = 1.0f * v[0] * g[8];
-      const float w = th[2] * 0.5f;
+      const float w = th[2 * TS];
       vo[7] += w * t0;
       vo[8] += w * t1;
       vo[9] += w * t2;
@@ -587,7 +677,7 @@ template <> struct TP<2, 0, 0> {
       const float t0 = 0.9999999999999999f * v[1] * g[0];
       const float t1 = 1.0000000000000002f * v[2] * g[0];
       const float t2 = 0.9999999999999999f * v[3] * g[0];
-      const float w = th[3] * 0.5f;
+      const float w = th[3 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
@@ -595,14 +685,14 @@ template <> struct TP<2, 0, 0> {
     { // path 4: (1, -1) x (1,-1) -> (0, 1)
       const float t0 = 0.5773502691896257f * v[1] * g[1] + 0.5773502691896258f * v[2] * g[2] + 0.5773502691896257f * v[3] * g[3];
       s[1] = t0;
-      const float w = th[4] * 0.5773502691896258f;
+      const float w = th[4 * TS];
       vo[0] += w * t0;
     }
     { // path 5: (1, -1) x (1,-1) -> (1, 1)
       const float t0 = 0.7071067811865476f * v[2] * g[3] + -0.7071067811865476f * v[3] * g[2];
       const float t1 = -0.7071067811865476f * v[1] * g[3] + 0.7071067811865476f * v[3] * g[1];
       const float t2 = 0.7071067811865476f * v[1] * g[2] + -0.7071067811865476f * v[2] * g[1];
-      const float w = th[5] * 0.7071067811865475f;
+      const float w = th[5 * TS];
       vo[4] += w * t0;
       vo[5] += w * t1;
       vo[6] += w * t2;
@@ -613,7 +703,7 @@ template <> struct TP<2, 0, 0> {
       const float t2 = 0.4082482904638631f * v[1] * g[1] + -0.8164965809277261f * v[2] * g[2] + 0.4082482904638631f * v[3] * g[3];
       const float t3 = -0.7071067811865476f * v[2] * g[3] + -0.7071067811865476f * v[3] * g[2];
       const float t4 = 0.7071067811865475f * v[1] * g[1] + -0.7071067811865475f * v[3] * g[3];
-      const float w = th[6] * 0.5f;
+      const float w = th[6 * TS];
       vo[7] += w * t0;
       vo[8] += w * t1;
       vo[9] += w * t2;
@@ -624,7 +714,7 @@ template <> struct TP<2, 0, 0> {
       const float t0 = -0.3162277660168379f * v[1] * g[6] + -0.547722557505166f * v[1] * g[8] + 0.547722557505166f * v[2] * g[5] + 0.547722557505166f * v[3] * g[4];
       const float t1 = 0.547722557505166f * v[1] * g[5] + 0.632455532033676f * v[2] * g[6] + 0.547722557505166f * v[3] * g[7];
       const float t2 = 0.547722557505166f * v[1] * g[4] + 0.547722557505166f * v[2] * g[7] + -0.3162277660168379f * v[3] * g[6] + 0.547722557505166f * v[3] * g[8];
-      const float w = th[7] * 0.5f;
+      const float w = th[7 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
@@ -635,7 +725,7 @@ template <> struct TP<2, 0, 0> {
       const float t2 = 0.7071067811865477f * v[1] * g[7] + -0.7071067811865477f * v[3] * g[5];
       const float t3 = -0.7071067811865477f * v[1] * g[6] + 0.408248290463863f * v[1] * g[8] + 0.408248290463863f * v[2] * g[5] + -0.408248290463863f * v[3] * g[4];
       const float t4 = -0.408248290463863f * v[1] * g[7] + 0.816496580927726f * v[2] * g[4] + -0.408248290463863f * v[3] * g[5];
-      const float w = th[8] * 0.7071067811865475f;
+      const float w = th[8 * TS];
       vo[12] += w * t0;
       vo[13] += w * t1;
       vo[14] += w * t2;
@@ -648,7 +738,7 @@ template <> struct TP<2, 0, 0> {
       const float t2 = 1.0000000000000002f * v[6] * g[0];
       const float t3 = 1.0f * v[7] * g[0];
       const float t4 = 1.0f * v[8] * g[0];
-      const float w = th[9] * 0.5f;
+      const float w = th[9 * TS];
       vo[7] += w * t0;
       vo[8] += w * t1;
       vo[9] += w * t2;
@@ -659,7 +749,7 @@ template <> struct TP<2, 0, 0> {
       const float t0 = 0.547722557505166f * v[4] * g[3] + 0.547722557505166f * v[5] * g[2] + -0.3162277660168379f * v[6] * g[1] + -0.547722557505166f * v[8] * g[1];
       const float t1 = 0.547722557505166f * v[5] * g[1] + 0.632455532033676f * v[6] * g[2] + 0.547722557505166f * v[7] * g[3];
       const float t2 = 0.547722557505166f * v[4] * g[1] + -0.3162277660168379f * v[6] * g[3] + 0.547722557505166f * v[7] * g[2] + 0.547722557505166f * v[8] * g[3];
-      const float w = th[10] * 0.5f;
+      const float w = th[10 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
@@ -670,7 +760,7 @@ template <> struct TP<2, 0, 0> {
       const float t2 = -0.7071067811865477f * v[5] * g[3] + 0.7071067811865477f * v[7] * g[1];
       const float t3 = -0.408248290463863f * v[4] * g[3] + 0.408248290463863f * v[5] * g[2] + -0.7071067811865477f * v[6] * g[1] + 0.408248290463863f * v[8] * g[1];
       const float t4 = 0.816496580927726f * v[4] * g[2] + -0.408248290463863f * v[5] * g[3] + -0.408248290463863f * v[7] * g[1];
-      const float w = th[11] * 0.7071067811865475f;
+      const float w = th[11 * TS];
       vo[12] += w * t0;
       vo[13] += w * t1;
       vo[14] += w * t2;
@@ -680,14 +770,14 @@ template <> struct TP<2, 0, 0> {
     { // path 12: (2, 1) x (2,1) -> (0, 1)
       const float t0 = 0.4472135954999579f * v[4] * g[4] + 0.4472135954999579f * v[5] * g[5] + 0.44721359549995804f * v[6] * g[6] + 0.4472135954999579f * v[7] * g[7] + 0.4472135954999579f * v[8] * g[8];
       s[2] = t0;
-      const float w = th[12] * 0.5773502691896258f;
+      const float w = th[12 * TS];
       vo[0] += w * t0;
     }
     { // path 13: (2, 1) x (2,1) -> (1, 1)
       const float t0 = 0.3162277660168379f * v[4] * g[5] + -0.3162277660168379f * v[5] * g[4] + -0.5477225575051661f * v[6] * g[7] + 0.5477225575051661f * v[7] * g[6] + -0.3162277660168379f * v[7] * g[8] + 0.3162277660168379f * v[8] * g[7];
       const float t1 = 0.6324555320336758f * v[4] * g[8] + 0.3162277660168379f * v[5] * g[7] + -0.3162277660168379f * v[7] * g[5] + -0.6324555320336758f * v[8] * g[4];
       const float t2 = -0.3162277660168379f * v[4] * g[7] + -0.5477225575051661f * v[5] * g[6] + -0.3162277660168379f * v[5] * g[8] + 0.5477225575051661f * v[6] * g[5] + 0.3162277660168379f * v[7] * g[4] + 0.3162277660168379f * v[8] * g[5];
-      const float w = th[13] * 0.7071067811865475f;
+      const float w = th[13 * TS];
       vo[4] += w * t0;
       vo[5] += w * t1;
       vo[6] += w * t2;
@@ -698,7 +788,7 @@ template <> struct TP<2, 0, 0> {
       const float t2 = 0.5345224838248488f * v[4] * g[4] + -0.2672612419124244f * v[5] * g[5] + -0.5345224838248489f * v[6] * g[6] + -0.2672612419124244f * v[7] * g[7] + 0.5345224838248488f * v[8] * g[8];
       const float t3 = -0.4629100498862757f * v[4] * g[5] + -0.4629100498862757f * v[5] * g[4] + -0.2672612419124244f * v[6] * g[7] + -0.2672612419124244f * v[7] * g[6] + -0.4629100498862757f * v[7] * g[8] + -0.4629100498862757f * v[8] * g[7];
       const float t4 = 0.4629100498862757f * v[5] * g[5] + 0.5345224838248488f * v[6] * g[8] + -0.4629100498862757f * v[7] * g[7] + 0.5345224838248488f * v[8] * g[6];
-      const float w = th[14] * 0.5f;
+      const float w = th[14 * TS];
       vo[7] += w * t0;
       vo[8] += w * t1;
       vo[9] += w * t2;
@@ -706,239 +796,314 @@ template <> struct TP<2, 0, 0> {
       vo[11] += w * t4;
     }
   }
+  template <int TS>
   static __device__ __forceinline__ void bwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, const float* __restrict__ gs, const float* __restrict__ gvo, float* gv, float* gg) {
     { // path 0
-      const float w = th[0] * 0.5773502691896258f;
+      const float w = th[0 * TS];
       const float gt0 = gs[0] + w * gvo[0];
-      gv[0] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[0];
+      const float s0_0 = gt0;
+      gv[0] = fmaf(s0_0, g[0], gv[0]); gg[0] = fmaf(s0_0, v[0], gg[0]);
     }
     { // path 1
-      const float w = th[1] * 0.5f;
+      const float w = th[1 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[0] += 0.9999999999999999f * gt0 * g[1]; gg[1] += 0.9999999999999999f * gt0 * v[0];
-      gv[0] += 1.0000000000000002f * gt1 * g[2]; gg[2] += 1.0000000000000002f * gt1 * v[0];
-      gv[0] += 0.9999999999999999f * gt2 * g[3]; gg[3] += 0.9999999999999999f * gt2 * v[0];
+      const float s0_0 = gt0;
+      gv[0] = fmaf(s0_0, g[1], gv[0]); gg[1] = fmaf(s0_0, v[0], gg[1]);
+      const float s1_0 = gt1;
+      gv[0] = fmaf(s1_0, g[2], gv[0]); gg[2] = fmaf(s1_0, v[0], gg[2]);
+      const float s2_0 = gt2;
+      gv[0] = fmaf(s2_0, g[3], gv[0]); gg[3] = fmaf(s2_0, v[0], gg[3]);
     }
     { // path 2
-      const float w = th[2] * 0.5f;
+      const float w = th[2 * TS];
       const float gt0 = w * gvo[7];
       const float gt1 = w * gvo[8];
       const float gt2 = w * gvo[9];
       const float gt3 = w * gvo[10];
       const float gt4 = w * gvo[11];
-      gv[0] += 1.0f * gt0 * g[4]; gg[4] += 1.0f * gt0 * v[0];
-      gv[0] += 1.0f * gt1 * g[5]; gg[5] += 1.0f * gt1 * v[0];
-      gv[0] += 1.0000000000000002f * gt2 * g[6]; gg[6] += 1.0000000000000002f * gt2 * v[0];
-      gv[0] += 1.0f * gt3 * g[7]; gg[7] += 1.0f * gt3 * v[0];
-      gv[0] += 1.0f * gt4 * g[8]; gg[8] += 1.0f * gt4 * v[0];
+      const float s0_0 = gt0;
+      gv[0] = fmaf(s0_0, g[4], gv[0]); gg[4] = fmaf(s0_0, v[0], gg[4]);
+      const float s1_0 = gt1;
+      gv[0] = fmaf(s1_0, g[5], gv[0]); gg[5] = fmaf(s1_0, v[0], gg[5]);
+      const float s2_0 = gt2;
+      gv[0] = fmaf(s2_0, g[6], gv[0]); gg[6] = fmaf(s2_0, v[0], gg[6]);
+      const float s3_0 = gt3;
+      gv[0] = fmaf(s3_0, g[7], gv[0]); gg[7] = fmaf(s3_0, v[0], gg[7]);
+      const float s4_0 = gt4;
+      gv[0] = fmaf(s4_0, g[8], gv[0]); gg[8] = fmaf(s4_0, v[0], gg[8]);
     }
     { // path 3
-      const float w = th[3] * 0.5f;
+      const float w = th[3 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[1] += 0.9999999999999999f * gt0 * g[0]; gg[0] += 0.9999999999999999f * gt0 * v[1];
-      gv[2] += 1.0000000000000002f * gt1 * g[0]; gg[0] += 1.0000000000000002f * gt1 * v[2];
-      gv[3] += 0.9999999999999999f * gt2 * g[0]; gg[0] += 0.9999999999999999f * gt2 * v[3];
+      const float s0_0 = gt0;
+      gv[1] = fmaf(s0_0, g[0], gv[1]); gg[0] = fmaf(s0_0, v[1], gg[0]);
+      const float s1_0 = gt1;
+      gv[2] = fmaf(s1_0, g[0], gv[2]); gg[0] = fmaf(s1_0, v[2], gg[0]);
+      const float s2_0 = gt2;
+      gv[3] = fmaf(s2_0, g[0], gv[3]); gg[0] = fmaf(s2_0, v[3], gg[0]);
     }
     { // path 4
-      const float w = th[4] * 0.5773502691896258f;
+      const float w = th[4 * TS];
       const float gt0 = gs[1] + w * gvo[0];
-      gv[1] += 0.5773502691896257f * gt0 * g[1]; gg[1] += 0.5773502691896257f * gt0 * v[1];
-      gv[2] += 0.5773502691896258f * gt0 * g[2]; gg[2] += 0.5773502691896258f * gt0 * v[2];
-      gv[3] += 0.5773502691896257f * gt0 * g[3]; gg[3] += 0.5773502691896257f * gt0 * v[3];
+      const float s0_0 = 0.5773502691896257f * gt0;
+      gv[1] = fmaf(s0_0, g[1], gv[1]); gg[1] = fmaf(s0_0, v[1], gg[1]);
+      gv[2] = fmaf(s0_0, g[2], gv[2]); gg[2] = fmaf(s0_0, v[2], gg[2]);
+      gv[3] = fmaf(s0_0, g[3], gv[3]); gg[3] = fmaf(s0_0, v[3], gg[3]);
     }
     { // path 5
-      const float w = th[5] * 0.7071067811865475f;
+      const float w = th[5 * TS];
       const float gt0 = w * gvo[4];
       const float gt1 = w * gvo[5];
       const float gt2 = w * gvo[6];
-      gv[1] += 0.7071067811865476f * gt2 * g[2]; gg[2] += 0.7071067811865476f * gt2 * v[1];
-      gv[1] += -0.7071067811865476f * gt1 * g[3]; gg[3] += -0.7071067811865476f * gt1 * v[1];
-      gv[2] += -0.7071067811865476f * gt2 * g[1]; gg[1] += -0.7071067811865476f * gt2 * v[2];
-      gv[2] += 0.7071067811865476f * gt0 * g[3]; gg[3] += 0.7071067811865476f * gt0 * v[2];
-      gv[3] += 0.7071067811865476f * gt1 * g[1]; gg[1] += 0.7071067811865476f * gt1 * v[3];
-      gv[3] += -0.7071067811865476f * gt0 * g[2]; gg[2] += -0.7071067811865476f * gt0 * v[3];
+      const float s2_0 = 0.7071067811865476f * gt2;
+      gv[1] = fmaf(s2_0, g[2], gv[1]); gg[2] = fmaf(s2_0, v[1], gg[2]);
+      const float s1_0 = 0.7071067811865476f * gt1;
+      gv[1] = fmaf(-s1_0, g[3], gv[1]); gg[3] = fmaf(-s1_0, v[1], gg[3]);
+      gv[2] = fmaf(-s2_0, g[1], gv[2]); gg[1] = fmaf(-s2_0, v[2], gg[1]);
+      const float s0_0 = 0.7071067811865476f * gt0;
+      gv[2] = fmaf(s0_0, g[3], gv[2]); gg[3] = fmaf(s0_0, v[2], gg[3]);
+      gv[3] = fmaf(s1_0, g[1], gv[3]); gg[1] = fmaf(s1_0, v[3], gg[1]);
+      gv[3] = fmaf(-s0_0, g[2], gv[3]); gg[2] = fmaf(-s0_0, v[3], gg[2]);
     }
     { // path 6
-      const float w = th[6] * 0.5f;
+      const float w = th[6 * TS];
       const float gt0 = w * gvo[7];
       const float gt1 = w * gvo[8];
       const float gt2 = w * gvo[9];
       const float gt3 = w * gvo[10];
       const float gt4 = w * gvo[11];
-      gv[1] += 0.4082482904638631f * gt2 * g[1]; gg[1] += 0.4082482904638631f * gt2 * v[1];
-      gv[1] += 0.7071067811865475f * gt4 * g[1]; gg[1] += 0.7071067811865475f * gt4 * v[1];
-      gv[1] += -0.7071067811865476f * gt1 * g[2]; gg[2] += -0.7071067811865476f * gt1 * v[1];
-      gv[1] += -0.7071067811865475f * gt0 * g[3]; gg[3] += -0.7071067811865475f * gt0 * v[1];
-      gv[2] += -0.7071067811865476f * gt1 * g[1]; gg[1] += -0.7071067811865476f * gt1 * v[2];
-      gv[2] += -0.8164965809277261f * gt2 * g[2]; gg[2] += -0.8164965809277261f * gt2 * v[2];
-      gv[2] += -0.7071067811865476f * gt3 * g[3]; gg[3] += -0.7071067811865476f * gt3 * v[2];
-      gv[3] += -0.7071067811865475f * gt0 * g[1]; gg[1] += -0.7071067811865475f * gt0 * v[3];
-      gv[3] += -0.7071067811865476f * gt3 * g[2]; gg[2] += -0.7071067811865476f * gt3 * v[3];
-      gv[3] += 0.4082482904638631f * gt2 * g[3]; gg[3] += 0.4082482904638631f * gt2 * v[3];
-      gv[3] += -0.7071067811865475f * gt4 * g[3]; gg[3] += -0.7071067811865475f * gt4 * v[3];
+      const float s2_0 = 0.4082482904638631f * gt2;
+      gv[1] = fmaf(s2_0, g[1], gv[1]); gg[1] = fmaf(s2_0, v[1], gg[1]);
+      const float s4_0 = 0.7071067811865475f * gt4;
+      gv[1] = fmaf(s4_0, g[1], gv[1]); gg[1] = fmaf(s4_0, v[1], gg[1]);
+      const float s1_0 = 0.7071067811865476f * gt1;
+      gv[1] = fmaf(-s1_0, g[2], gv[1]); gg[2] = fmaf(-s1_0, v[1], gg[2]);
+      const float s0_0 = 0.7071067811865475f * gt0;
+      gv[1] = fmaf(-s0_0, g[3], gv[1]); gg[3] = fmaf(-s0_0, v[1], gg[3]);
+      gv[2] = fmaf(-s1_0, g[1], gv[2]); gg[1] = fmaf(-s1_0, v[2], gg[1]);
+      const float s2_1 = 0.8164965809277261f * gt2;
+      gv[2] = fmaf(-s2_1, g[2], gv[2]); gg[2] = fmaf(-s2_1, v[2], gg[2]);
+      const float s3_0 = 0.7071067811865476f * gt3;
+      gv[2] = fmaf(-s3_0, g[3], gv[2]); gg[3] = fmaf(-s3_0, v[2], gg[3]);
+      gv[3] = fmaf(-s0_0, g[1], gv[3]); gg[1] = fmaf(-s0_0, v[3], gg[1]);
+      gv[3] = fmaf(-s3_0, g[2], gv[3]); gg[2] = fmaf(-s3_0, v[3], gg[2]);
+      gv[3] = fmaf(s2_0, g[3], gv[3]); gg[3] = fmaf(s2_0, v[3], gg[3]);
+      gv[3] = fmaf(-s4_0, g[3], gv[3]); gg[3] = fmaf(-s4_0, v[3], gg[3]);
     }
     { // path 7
-      const float w = th[7] * 0.5f;
+      const float w = th[7 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[1] += 0.547722557505166f * gt2 * g[4]; gg[4] += 0.547722557505166f * gt2 * v[1];
-      gv[1] += 0.547722557505166f * gt1 * g[5]; gg[5] += 0.547722557505166f * gt1 * v[1];
-      gv[1] += -0.3162277660168379f * gt0 * g[6]; gg[6] += -0.3162277660168379f * gt0 * v[1];
-      gv[1] += -0.547722557505166f * gt0 * g[8]; gg[8] += -0.547722557505166f * gt0 * v[1];
-      gv[2] += 0.547722557505166f * gt0 * g[5]; gg[5] += 0.547722557505166f * gt0 * v[2];
-      gv[2] += 0.632455532033676f * gt1 * g[6]; gg[6] += 0.632455532033676f * gt1 * v[2];
-      gv[2] += 0.547722557505166f * gt2 * g[7]; gg[7] += 0.547722557505166f * gt2 * v[2];
-      gv[3] += 0.547722557505166f * gt0 * g[4]; gg[4] += 0.547722557505166f * gt0 * v[3];
-      gv[3] += -0.3162277660168379f * gt2 * g[6]; gg[6] += -0.3162277660168379f * gt2 * v[3];
-      gv[3] += 0.547722557505166f * gt1 * g[7]; gg[7] += 0.547722557505166f * gt1 * v[3];
-      gv[3] += 0.547722557505166f * gt2 * g[8]; gg[8] += 0.547722557505166f * gt2 * v[3];
+      const float s2_0 = 0.547722557505166f * gt2;
+      gv[1] = fmaf(s2_0, g[4], gv[1]); gg[4] = fmaf(s2_0, v[1], gg[4]);
+      const float s1_0 = 0.547722557505166f * gt1;
+      gv[1] = fmaf(s1_0, g[5], gv[1]); gg[5] = fmaf(s1_0, v[1], gg[5]);
+      const float s0_0 = 0.3162277660168379f * gt0;
+      gv[1] = fmaf(-s0_0, g[6], gv[1]); gg[6] = fmaf(-s0_0, v[1], gg[6]);
+      const float s0_1 = 0.547722557505166f * gt0;
+      gv[1] = fmaf(-s0_1, g[8], gv[1]); gg[8] = fmaf(-s0_1, v[1], gg[8]);
+      gv[2] = fmaf(s0_1, g[5], gv[2]); gg[5] = fmaf(s0_1, v[2], gg[5]);
+      const float s1_1 = 0.632455532033676f * gt1;
+      gv[2] = fmaf(s1_1, g[6], gv[2]); gg[6] = fmaf(s1_1, v[2], gg[6]);
+      gv[2] = fmaf(s2_0, g[7], gv[2]); gg[7] = fmaf(s2_0, v[2], gg[7]);
+      gv[3] = fmaf(s0_1, g[4], gv[3]); gg[4] = fmaf(s0_1, v[3], gg[4]);
+      const float s2_1 = 0.3162277660168379f * gt2;
+      gv[3] = fmaf(-s2_1, g[6], gv[3]); gg[6] = fmaf(-s2_1, v[3], gg[6]);
+      gv[3] = fmaf(s1_0, g[7], gv[3]); gg[7] = fmaf(s1_0, v[3], gg[7]);
+      gv[3] = fmaf(s2_0, g[8], gv[3]); gg[8] = fmaf(s2_0, v[3], gg[8]);
     }
     { // path 8
-      const float w = th[8] * 0.7071067811865475f;
+      const float w = th[8 * TS];
       const float gt0 = w * gvo[12];
       const float gt1 = w * gvo[13];
       const float gt2 = w * gvo[14];
       const float gt3 = w * gvo[15];
       const float gt4 = w * gvo[16];
-      gv[1] += 0.408248290463863f * gt1 * g[4]; gg[4] += 0.408248290463863f * gt1 * v[1];
-      gv[1] += -0.408248290463863f * gt0 * g[5]; gg[5] += -0.408248290463863f * gt0 * v[1];
-      gv[1] += -0.7071067811865477f * gt3 * g[6]; gg[6] += -0.7071067811865477f * gt3 * v[1];
-      gv[1] += 0.7071067811865477f * gt2 * g[7]; gg[7] += 0.7071067811865477f * gt2 * v[1];
-      gv[1] += -0.408248290463863f * gt4 * g[7]; gg[7] += -0.408248290463863f * gt4 * v[1];
-      gv[1] += 0.408248290463863f * gt3 * g[8]; gg[8] += 0.408248290463863f * gt3 * v[1];
-      gv[2] += 0.816496580927726f * gt4 * g[4]; gg[4] += 0.816496580927726f * gt4 * v[2];
-      gv[2] += 0.408248290463863f * gt3 * g[5]; gg[5] += 0.408248290463863f * gt3 * v[2];
-      gv[2] += -0.408248290463863f * gt1 * g[7]; gg[7] += -0.408248290463863f * gt1 * v[2];
-      gv[2] += -0.816496580927726f * gt0 * g[8]; gg[8] += -0.816496580927726f * gt0 * v[2];
-      gv[3] += -0.408248290463863f * gt3 * g[4]; gg[4] += -0.408248290463863f * gt3 * v[3];
-      gv[3] += -0.7071067811865477f * gt2 * g[5]; gg[5] += -0.7071067811865477f * gt2 * v[3];
-      gv[3] += -0.408248290463863f * gt4 * g[5]; gg[5] += -0.408248290463863f * gt4 * v[3];
-      gv[3] += 0.7071067811865477f * gt1 * g[6]; gg[6] += 0.7071067811865477f * gt1 * v[3];
-      gv[3] += 0.408248290463863f * gt0 * g[7]; gg[7] += 0.408248290463863f * gt0 * v[3];
-      gv[3] += 0.408248290463863f * gt1 * g[8]; gg[8] += 0.408248290463863f * gt1 * v[3];
+      const float s1_0 = 0.408248290463863f * gt1;
+      gv[1] = fmaf(s1_0, g[4], gv[1]); gg[4] = fmaf(s1_0, v[1], gg[4]);
+      const float s0_0 = 0.408248290463863f * gt0;
+      gv[1] = fmaf(-s0_0, g[5], gv[1]); gg[5] = fmaf(-s0_0, v[1], gg[5]);
+      const float s3_0 = 0.7071067811865477f * gt3;
+      gv[1] = fmaf(-s3_0, g[6], gv[1]); gg[6] = fmaf(-s3_0, v[1], gg[6]);
+      const float s2_0 = 0.7071067811865477f * gt2;
+      gv[1] = fmaf(s2_0, g[7], gv[1]); gg[7] = fmaf(s2_0, v[1], gg[7]);
+      const float s4_0 = 0.408248290463863f * gt4;
+      gv[1] = fmaf(-s4_0, g[7], gv[1]); gg[7] = fmaf(-s4_0, v[1], gg[7]);
+      const float s3_1 = 0.408248290463863f * gt3;
+      gv[1] = fmaf(s3_1, g[8], gv[1]); gg[8] = fmaf(s3_1, v[1], gg[8]);
+      const float s4_1 = 0.816496580927726f * gt4;
+      gv[2] = fmaf(s4_1, g[4], gv[2]); gg[4] = fmaf(s4_1, v[2], gg[4]);
+      gv[2] = fmaf(s3_1, g[5], gv[2]); gg[5] = fmaf(s3_1, v[2], gg[5]);
+      gv[2] = fmaf(-s1_0, g[7], gv[2]); gg[7] = fmaf(-s1_0, v[2], gg[7]);
+      const float s0_1 = 0.816496580927726f * gt0;
+      gv[2] = fmaf(-s0_1, g[8], gv[2]); gg[8] = fmaf(-s0_1, v[2], gg[8]);
+      gv[3] = fmaf(-s3_1, g[4], gv[3]); gg[4] = fmaf(-s3_1, v[3], gg[4]);
+      gv[3] = fmaf(-s2_0, g[5], gv[3]); gg[5] = fmaf(-s2_0, v[3], gg[5]);
+      gv[3] = fmaf(-s4_0, g[5], gv[3]); gg[5] = fmaf(-s4_0, v[3], gg[5]);
+      const float s1_1 = 0.7071067811865477f * gt1;
+      gv[3] = fmaf(s1_1, g[6], gv[3]); gg[6] = fmaf(s1_1, v[3], gg[6]);
+      gv[3] = fmaf(s0_0, g[7], gv[3]); gg[7] = fmaf(s0_0, v[3], gg[7]);
+      gv[3] = fmaf(s1_0, g[8], gv[3]); gg[8] = fmaf(s1_0, v[3], gg[8]);
     }
     { // path 9
-      const float w = th[9] * 0.5f;
+      const float w = th[9 * TS];
       const float gt0 = w * gvo[7];
       const float gt1 = w * gvo[8];
       const float gt2 = w * gvo[9];
       const float gt3 = w * gvo[10];
       const float gt4 = w * gvo[11];
-      gv[4] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[4];
-      gv[5] += 1.0f * gt1 * g[0]; gg[0] += 1.0f * gt1 * v[5];
-      gv[6] += 1.0000000000000002f * gt2 * g[0]; gg[0] += 1.0000000000000002f * gt2 * v[6];
-      gv[7] += 1.0f * gt3 * g[0]; gg[0] += 1.0f * gt3 * v[7];
-      gv[8] += 1.0f * gt4 * g[0]; gg[0] += 1.0f * gt4 * v[8];
+      const float s0_0 = gt0;
+      gv[4] = fmaf(s0_0, g[0], gv[4]); gg[0] = fmaf(s0_0, v[4], gg[0]);
+      const float s1_0 = gt1;
+      gv[5] = fmaf(s1_0, g[0], gv[5]); gg[0] = fmaf(s1_0, v[5], gg[0]);
+      const float s2_0 = gt2;
+      gv[6] = fmaf(s2_0, g[0], gv[6]); gg[0] = fmaf(s2_0, v[6], gg[0]);
+      const float s3_0 = gt3;
+      gv[7] = fmaf(s3_0, g[0], gv[7]); gg[0] = fmaf(s3_0, v[7], gg[0]);
+      const float s4_0 = gt4;
+      gv[8] = fmaf(s4_0, g[0], gv[8]); gg[0] = fmaf(s4_0, v[8], gg[0]);
     }
     { // path 10
-      const float w = th[10] * 0.5f;
+      const float w = th[10 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[4] += 0.547722557505166f * gt2 * g[1]; gg[1] += 0.547722557505166f * gt2 * v[4];
-      gv[4] += 0.547722557505166f * gt0 * g[3]; gg[3] += 0.547722557505166f * gt0 * v[4];
-      gv[5] += 0.547722557505166f * gt1 * g[1]; gg[1] += 0.547722557505166f * gt1 * v[5];
-      gv[5] += 0.547722557505166f * gt0 * g[2]; gg[2] += 0.547722557505166f * gt0 * v[5];
-      gv[6] += -0.3162277660168379f * gt0 * g[1]; gg[1] += -0.3162277660168379f * gt0 * v[6];
-      gv[6] += 0.632455532033676f * gt1 * g[2]; gg[2] += 0.632455532033676f * gt1 * v[6];
-      gv[6] += -0.3162277660168379f * gt2 * g[3]; gg[3] += -0.3162277660168379f * gt2 * v[6];
-      gv[7] += 0.547722557505166f * gt2 * g[2]; gg[2] += 0.547722557505166f * gt2 * v[7];
-      gv[7] += 0.547722557505166f * gt1 * g[3]; gg[3] += 0.547722557505166f * gt1 * v[7];
-      gv[8] += -0.547722557505166f * gt0 * g[1]; gg[1] += -0.547722557505166f * gt0 * v[8];
-      gv[8] += 0.547722557505166f * gt2 * g[3]; gg[3] += 0.547722557505166f * gt2 * v[8];
+      const float s2_0 = 0.547722557505166f * gt2;
+      gv[4] = fmaf(s2_0, g[1], gv[4]); gg[1] = fmaf(s2_0, v[4], gg[1]);
+      const float s0_0 = 0.547722557505166f * gt0;
+      gv[4] = fmaf(s0_0, g[3], gv[4]); gg[3] = fmaf(s0_0, v[4], gg[3]);
+      const float s1_0 = 0.547722557505166f * gt1;
+      gv[5] = fmaf(s1_0, g[1], gv[5]); gg[1] = fmaf(s1_0, v[5], gg[1]);
+      gv[5] = fmaf(s0_0, g[2], gv[5]); gg[2] = fmaf(s0_0, v[5], gg[2]);
+      const float s0_1 = 0.3162277660168379f * gt0;
+      gv[6] = fmaf(-s0_1, g[1], gv[6]); gg[1] = fmaf(-s0_1, v[6], gg[1]);
+      const float s1_1 = 0.632455532033676f * gt1;
+      gv[6] = fmaf(s1_1, g[2], gv[6]); gg[2] = fmaf(s1_1, v[6], gg[2]);
+      const float s2_1 = 0.3162277660168379f * gt2;
+      gv[6] = fmaf(-s2_1, g[3], gv[6]); gg[3] = fmaf(-s2_1, v[6], gg[3]);
+      gv[7] = fmaf(s2_0, g[2], gv[7]); gg[2] = fmaf(s2_0, v[7], gg[2]);
+      gv[7] = fmaf(s1_0, g[3], gv[7]); gg[3] = fmaf(s1_0, v[7], gg[3]);
+      gv[8] = fmaf(-s0_0, g[1], gv[8]); gg[1] = fmaf(-s0_0, v[8], gg[1]);
+      gv[8] = fmaf(s2_0, g[3], gv[8]); gg[3] = fmaf(s2_0, v[8], gg[3]);
     }
     { // path 11
-      const float w = th[11] * 0.7071067811865475f;
+      const float w = th[11 * TS];
       const float gt0 = w * gvo[12];
       const float gt1 = w * gvo[13];
       const float gt2 = w * gvo[14];
       const float gt3 = w * gvo[15];
       const float gt4 = w * gvo[16];
-      gv[4] += 0.408248290463863f * gt1 * g[1]; gg[1] += 0.408248290463863f * gt1 * v[4];
-      gv[4] += 0.816496580927726f * gt4 * g[2]; gg[2] += 0.816496580927726f * gt4 * v[4];
-      gv[4] += -0.408248290463863f * gt3 * g[3]; gg[3] += -0.408248290463863f * gt3 * v[4];
-      gv[5] += -0.408248290463863f * gt0 * g[1]; gg[1] += -0.408248290463863f * gt0 * v[5];
-      gv[5] += 0.408248290463863f * gt3 * g[2]; gg[2] += 0.408248290463863f * gt3 * v[5];
-      gv[5] += -0.7071067811865477f * gt2 * g[3]; gg[3] += -0.7071067811865477f * gt2 * v[5];
-      gv[5] += -0.408248290463863f * gt4 * g[3]; gg[3] += -0.408248290463863f * gt4 * v[5];
-      gv[6] += -0.7071067811865477f * gt3 * g[1]; gg[1] += -0.7071067811865477f * gt3 * v[6];
-      gv[6] += 0.7071067811865477f * gt1 * g[3]; gg[3] += 0.7071067811865477f * gt1 * v[6];
-      gv[7] += 0.7071067811865477f * gt2 * g[1]; gg[1] += 0.7071067811865477f * gt2 * v[7];
-      gv[7] += -0.408248290463863f * gt4 * g[1]; gg[1] += -0.408248290463863f * gt4 * v[7];
-      gv[7] += -0.408248290463863f * gt1 * g[2]; gg[2] += -0.408248290463863f * gt1 * v[7];
-      gv[7] += 0.408248290463863f * gt0 * g[3]; gg[3] += 0.408248290463863f * gt0 * v[7];
-      gv[8] += 0.408248290463863f * gt3 * g[1]; gg[1] += 0.408248290463863f * gt3 * v[8];
-      gv[8] += -0.816496580927726f * gt0 * g[2]; gg[2] += -0.816496580927726f * gt0 * v[8];
-      gv[8] += 0.408248290463863f * gt1 * g[3]; gg[3] += 0.408248290463863f * gt1 * v[8];
+      const float s1_0 = 0.408248290463863f * gt1;
+      gv[4] = fmaf(s1_0, g[1], gv[4]); gg[1] = fmaf(s1_0, v[4], gg[1]);
+      const float s4_0 = 0.816496580927726f * gt4;
+      gv[4] = fmaf(s4_0, g[2], gv[4]); gg[2] = fmaf(s4_0, v[4], gg[2]);
+      const float s3_0 = 0.408248290463863f * gt3;
+      gv[4] = fmaf(-s3_0, g[3], gv[4]); gg[3] = fmaf(-s3_0, v[4], gg[3]);
+      const float s0_0 = 0.408248290463863f * gt0;
+      gv[5] = fmaf(-s0_0, g[1], gv[5]); gg[1] = fmaf(-s0_0, v[5], gg[1]);
+      gv[5] = fmaf(s3_0, g[2], gv[5]); gg[2] = fmaf(s3_0, v[5], gg[2]);
+      const float s2_0 = 0.7071067811865477f * gt2;
+      gv[5] = fmaf(-s2_0, g[3], gv[5]); gg[3] = fmaf(-s2_0, v[5], gg[3]);
+      const float s4_1 = 0.408248290463863f * gt4;
+      gv[5] = fmaf(-s4_1, g[3], gv[5]); gg[3] = fmaf(-s4_1, v[5], gg[3]);
+      const float s3_1 = 0.7071067811865477f * gt3;
+      gv[6] = fmaf(-s3_1, g[1], gv[6]); gg[1] = fmaf(-s3_1, v[6], gg[1]);
+      const float s1_1 = 0.7071067811865477f * gt1;
+      gv[6] = fmaf(s1_1, g[3], gv[6]); gg[3] = fmaf(s1_1, v[6], gg[3]);
+      gv[7] = fmaf(s2_0, g[1], gv[7]); gg[1] = fmaf(s2_0, v[7], gg[1]);
+      gv[7] = fmaf(-s4_1, g[1], gv[7]); gg[1] = fmaf(-s4_1, v[7], gg[1]);
+      gv[7] = fmaf(-s1_0, g[2], gv[7]); gg[2] = fmaf(-s1_0, v[7], gg[2]);
+      gv[7] = fmaf(s0_0, g[3], gv[7]); gg[3] = fmaf(s0_0, v[7], gg[3]);
+      gv[8] = fmaf(s3_0, g[1], gv[8]); gg[1] = fmaf(s3_0, v[8], gg[1]);
+      const float s0_1 = 0.816496580927726f * gt0;
+      gv[8] = fmaf(-s0_1, g[2], gv[8]); gg[2] = fmaf(-s0_1, v[8], gg[2]);
+      gv[8] = fmaf(s1_0, g[3], gv[8]); gg[3] = fmaf(s1_0, v[8], gg[3]);
     }
     { // path 12
-      const float w = th[12] * 0.5773502691896258f;
+      const float w = th[12 * TS];
       const float gt0 = gs[2] + w * gvo[0];
-      gv[4] += 0.4472135954999579f * gt0 * g[4]; gg[4] += 0.4472135954999579f * gt0 * v[4];
-      gv[5] += 0.4472135954999579f * gt0 * g[5]; gg[5] += 0.4472135954999579f * gt0 * v[5];
-      gv[6] += 0.44721359549995804f * gt0 * g[6]; gg[6] += 0.44721359549995804f * gt0 * v[6];
-      gv[7] += 0.4472135954999579f * gt0 * g[7]; gg[7] += 0.4472135954999579f * gt0 * v[7];
-      gv[8] += 0.4472135954999579f * gt0 * g[8]; gg[8] += 0.4472135954999579f * gt0 * v[8];
+      const float s0_0 = 0.4472135954999579f * gt0;
+      gv[4] = fmaf(s0_0, g[4], gv[4]); gg[4] = fmaf(s0_0, v[4], gg[4]);
+      gv[5] = fmaf(s0_0, g[5], gv[5]); gg[5] = fmaf(s0_0, v[5], gg[5]);
+      gv[6] = fmaf(s0_0, g[6], gv[6]); gg[6] = fmaf(s0_0, v[6], gg[6]);
+      gv[7] = fmaf(s0_0, g[7], gv[7]); gg[7] = fmaf(s0_0, v[7], gg[7]);
+      gv[8] = fmaf(s0_0, g[8], gv[8]); gg[8] = fmaf(s0_0, v[8], gg[8]);
     }
     { // path 13
-      const float w = th[13] * 0.7071067811865475f;
+      const float w = th[13 * TS];
       const float gt0 = w * gvo[4];
       const float gt1 = w * gvo[5];
       const float gt2 = w * gvo[6];
-      gv[4] += 0.3162277660168379f * gt0 * g[5]; gg[5] += 0.3162277660168379f * gt0 * v[4];
-      gv[4] += -0.3162277660168379f * gt2 * g[7]; gg[7] += -0.3162277660168379f * gt2 * v[4];
-      gv[4] += 0.6324555320336758f * gt1 * g[8]; gg[8] += 0.6324555320336758f * gt1 * v[4];
-      gv[5] += -0.3162277660168379f * gt0 * g[4]; gg[4] += -0.3162277660168379f * gt0 * v[5];
-      gv[5] += -0.5477225575051661f * gt2 * g[6]; gg[6] += -0.5477225575051661f * gt2 * v[5];
-      gv[5] += 0.3162277660168379f * gt1 * g[7]; gg[7] += 0.3162277660168379f * gt1 * v[5];
-      gv[5] += -0.3162277660168379f * gt2 * g[8]; gg[8] += -0.3162277660168379f * gt2 * v[5];
-      gv[6] += 0.5477225575051661f * gt2 * g[5]; gg[5] += 0.5477225575051661f * gt2 * v[6];
-      gv[6] += -0.5477225575051661f * gt0 * g[7]; gg[7] += -0.5477225575051661f * gt0 * v[6];
-      gv[7] += 0.3162277660168379f * gt2 * g[4]; gg[4] += 0.3162277660168379f * gt2 * v[7];
-      gv[7] += -0.3162277660168379f * gt1 * g[5]; gg[5] += -0.3162277660168379f * gt1 * v[7];
-      gv[7] += 0.5477225575051661f * gt0 * g[6]; gg[6] += 0.5477225575051661f * gt0 * v[7];
-      gv[7] += -0.3162277660168379f * gt0 * g[8]; gg[8] += -0.3162277660168379f * gt0 * v[7];
-      gv[8] += -0.6324555320336758f * gt1 * g[4]; gg[4] += -0.6324555320336758f * gt1 * v[8];
-      gv[8] += 0.3162277660168379f * gt2 * g[5]; gg[5] += 0.3162277660168379f * gt2 * v[8];
-      gv[8] += 0.3162277660168379f * gt0 * g[7]; gg[7] += 0.3162277660168379f * gt0 * v[8];
+      const float s0_0 = 0.3162277660168379f * gt0;
+      gv[4] = fmaf(s0_0, g[5], gv[4]); gg[5] = fmaf(s0_0, v[4], gg[5]);
+      const float s2_0 = 0.3162277660168379f * gt2;
+      gv[4] = fmaf(-s2_0, g[7], gv[4]); gg[7] = fmaf(-s2_0, v[4], gg[7]);
+      const float s1_0 = 0.6324555320336758f * gt1;
+      gv[4] = fmaf(s1_0, g[8], gv[4]); gg[8] = fmaf(s1_0, v[4], gg[8]);
+      gv[5] = fmaf(-s0_0, g[4], gv[5]); gg[4] = fmaf(-s0_0, v[5], gg[4]);
+      const float s2_1 = 0.5477225575051661f * gt2;
+      gv[5] = fmaf(-s2_1, g[6], gv[5]); gg[6] = fmaf(-s2_1, v[5], gg[6]);
+      const float s1_1 = 0.3162277660168379f * gt1;
+      gv[5] = fmaf(s1_1, g[7], gv[5]); gg[7] = fmaf(s1_1, v[5], gg[7]);
+      gv[5] = fmaf(-s2_0, g[8], gv[5]); gg[8] = fmaf(-s2_0, v[5], gg[8]);
+      gv[6] = fmaf(s2_1, g[5], gv[6]); gg[5] = fmaf(s2_1, v[6], gg[5]);
+      const float s0_1 = 0.5477225575051661f * gt0;
+      gv[6] = fmaf(-s0_1, g[7], gv[6]); gg[7] = fmaf(-s0_1, v[6], gg[7]);
+      gv[7] = fmaf(s2_0, g[4], gv[7]); gg[4] = fmaf(s2_0, v[7], gg[4]);
+      gv[7] = fmaf(-s1_1, g[5], gv[7]); gg[5] = fmaf(-s1_1, v[7], gg[5]);
+      gv[7] = fmaf(s0_1, g[6], gv[7]); gg[6] = fmaf(s0_1, v[7], gg[6]);
+      gv[7] = fmaf(-s0_0, g[8], gv[7]); gg[8] = fmaf(-s0_0, v[7], gg[8]);
+      gv[8] = fmaf(-s1_0, g[4], gv[8]); gg[4] = fmaf(-s1_0, v[8], gg[4]);
+      gv[8] = fmaf(s2_0, g[5], gv[8]); gg[5] = fmaf(s2_0, v[8], gg[5]);
+      gv[8] = fmaf(s0_0, g[7], gv[8]); gg[7] = fmaf(s0_0, v[8], gg[7]);
     }
     { // path 14
-      const float w = th[14] * 0.5f;
+      const float w = th[14 * TS];
       const float gt0 = w * gvo[7];
       const float gt1 = w * gvo[8];
       const float gt2 = w * gvo[9];
       const float gt3 = w * gvo[10];
       const float gt4 = w * gvo[11];
-      gv[4] += 0.5345224838248488f * gt2 * g[4]; gg[4] += 0.5345224838248488f * gt2 * v[4];
-      gv[4] += -0.4629100498862757f * gt3 * g[5]; gg[5] += -0.4629100498862757f * gt3 * v[4];
-      gv[4] += 0.5345224838248488f * gt0 * g[6]; gg[6] += 0.5345224838248488f * gt0 * v[4];
-      gv[4] += -0.4629100498862757f * gt1 * g[7]; gg[7] += -0.4629100498862757f * gt1 * v[4];
-      gv[5] += -0.4629100498862757f * gt3 * g[4]; gg[4] += -0.4629100498862757f * gt3 * v[5];
-      gv[5] += -0.2672612419124244f * gt2 * g[5]; gg[5] += -0.2672612419124244f * gt2 * v[5];
-      gv[5] += 0.4629100498862757f * gt4 * g[5]; gg[5] += 0.4629100498862757f * gt4 * v[5];
-      gv[5] += -0.2672612419124244f * gt1 * g[6]; gg[6] += -0.2672612419124244f * gt1 * v[5];
-      gv[5] += -0.4629100498862757f * gt0 * g[7]; gg[7] += -0.4629100498862757f * gt0 * v[5];
-      gv[5] += 0.4629100498862757f * gt1 * g[8]; gg[8] += 0.4629100498862757f * gt1 * v[5];
-      gv[6] += 0.5345224838248488f * gt0 * g[4]; gg[4] += 0.5345224838248488f * gt0 * v[6];
-      gv[6] += -0.2672612419124244f * gt1 * g[5]; gg[5] += -0.2672612419124244f * gt1 * v[6];
-      gv[6] += -0.5345224838248489f * gt2 * g[6]; gg[6] += -0.5345224838248489f * gt2 * v[6];
-      gv[6] += -0.2672612419124244f * gt3 * g[7]; gg[7] += -0.2672612419124244f * gt3 * v[6];
-      gv[6] += 0.5345224838248488f * gt4 * g[8]; gg[8] += 0.5345224838248488f * gt4 * v[6];
-      gv[7] += -0.4629100498862757f * gt1 * g[4]; gg[4] += -0.4629100498862757f * gt1 * v[7];
-      gv[7] += -0.4629100498862757f * gt0 * g[5]; gg[5] += -0.4629100498862757f * gt0 * v[7];
-      gv[7] += -0.2672612419124244f * gt3 * g[6]; gg[6] += -0.2672612419124244f * gt3 * v[7];
-      gv[7] += -0.2672612419124244f * gt2 * g[7]; gg[7] += -0.2672612419124244f * gt2 * v[7];
-      gv[7] += -0.4629100498862757f * gt4 * g[7]; gg[7] += -0.4629100498862757f * gt4 * v[7];
-      gv[7] += -0.4629100498862757f * gt3 * g[8]; gg[8] += -0.4629100498862757f * gt3 * v[7];
-      gv[8] += 0.4629100498862757f * gt1 * g[5]; gg[5] += 0.4629100498862757f * gt1 * v[8];
-      gv[8] += 0.5345224838248488f * gt4 * g[6]; gg[6] += 0.5345224838248488f * gt4 * v[8];
-      gv[8] += -0.4629100498862757f * gt3 * g[7]; gg[7] += -0.4629100498862757f * gt3 * v[8];
-      gv[8] += 0.5345224838248488f * gt2 * g[8]; gg[8] += 0.5345224838248488f * gt2 * v[8];
+      const float s2_0 = 0.5345224838248488f * gt2;
+      gv[4] = fmaf(s2_0, g[4], gv[4]); gg[4] = fmaf(s2_0, v[4], gg[4]);
+      const float s3_0 = 0.4629100498862757f * gt3;
+      gv[4] = fmaf(-s3_0, g[5], gv[4]); gg[5] = fmaf(-s3_0, v[4], gg[5]);
+      const float s0_0 = 0.5345224838248488f * gt0;
+      gv[4] = fmaf(s0_0, g[6], gv[4]); gg[6] = fmaf(s0_0, v[4], gg[6]);
+      const float s1_0 = 0.4629100498862757f * gt1;
+      gv[4] = fmaf(-s1_0, g[7], gv[4]); gg[7] = fmaf(-s1_0, v[4], gg[7]);
+      gv[5] = fmaf(-s3_0, g[4], gv[5]); gg[4] = fmaf(-s3_0, v[5], gg[4]);
+      const float s2_1 = 0.2672612419124244f * gt2;
+      gv[5] = fmaf(-s2_1, g[5], gv[5]); gg[5] = fmaf(-s2_1, v[5], gg[5]);
+      const float s4_0 = 0.4629100498862757f * gt4;
+      gv[5] = fmaf(s4_0, g[5], gv[5]); gg[5] = fmaf(s4_0, v[5], gg[5]);
+      const float s1_1 = 0.2672612419124244f * gt1;
+      gv[5] = fmaf(-s1_1, g[6], gv[5]); gg[6] = fmaf(-s1_1, v[5], gg[6]);
+      const float s0_1 = 0.4629100498862757f * gt0;
+      gv[5] = fmaf(-s0_1, g[7], gv[5]); gg[7] = fmaf(-s0_1, v[5], gg[7]);
+      gv[5] = fmaf(s1_0, g[8], gv[5]); gg[8] = fmaf(s1_0, v[5], gg[8]);
+      gv[6] = fmaf(s0_0, g[4], gv[6]); gg[4] = fmaf(s0_0, v[6], gg[4]);
+      gv[6] = fmaf(-s1_1, g[5], gv[6]); gg[5] = fmaf(-s1_1, v[6], gg[5]);
+      gv[6] = fmaf(-s2_0, g[6], gv[6]); gg[6] = fmaf(-s2_0, v[6], gg[6]);
+      const float s3_1 = 0.2672612419124244f * gt3;
+      gv[6] = fmaf(-s3_1, g[7], gv[6]); gg[7] = fmaf(-s3_1, v[6], gg[7]);
+      const float s4_1 = 0.5345224838248488f * gt4;
+      gv[6] = fmaf(s4_1, g[8], gv[6]); gg[8] = fmaf(s4_1, v[6], gg[8]);
+      gv[7] = fmaf(-s1_0, g[4], gv[7]); gg[4] = fmaf(-s1_0, v[7], gg[4]);
+      gv[7] = fmaf(-s0_1, g[5], gv[7]); gg[5] = fmaf(-s0_1, v[7], gg[5]);
+      gv[7] = fmaf(-s3_1, g[6], gv[7]); gg[6] = fmaf(-s3_1, v[7], gg[6]);
+      gv[7] = fmaf(-s2_1, g[7], gv[7]); gg[7] = fmaf(-s2_1, v[7], gg[7]);
+      gv[7] = fmaf(-s4_0, g[7], gv[7]); gg[7] = fmaf(-s4_0, v[7], gg[7]);
+      gv[7] = fmaf(-s3_0, g[8], gv[7]); gg[8] = fmaf(-s3_0, v[7], gg[8]);
+      gv[8] = fmaf(s1_0, g[5], gv[8]); gg[5] = fmaf(s1_0, v[8], gg[5]);
+      gv[8] = fmaf(s4_1, g[6], gv[8]); gg[6] = fmaf(s4_1, v[8], gg[6]);
+      gv[8] = fmaf(-s3_0, g[7], gv[8]); gg[7] = fmaf(-s3_0, v[8], gg[7]);
+      gv[8] = fmaf(s2_0, g[8], gv[8]); gg[8] = fmaf(s2_0, v[8], gg[8]);
     }
   }
   static constexpr int NNZ = 137;
@@ -947,20 +1112,21 @@ template <> struct TP<2, 0, 0> {
 template <> struct TP<2, 0, 1> {
   // in irreps [(0, 1), (1, -1), (2, 1)]; out irreps [(0, 1), (1, -1), (2, 1)]
   static constexpr int NP = 15, DIN = 9, DOUT = 9, NS = 3, NPW = 15;
+  template <int TS>
   static __device__ __forceinline__ void fwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, float* s, float* vo) {
     #pragma unroll
     for (int k = 0; k < 9; ++k) vo[k] = 0.f;
     { // path 0: (0, 1) x (0,1) -> (0, 1)
       const float t0 = 1.0f * v[0] * g[0];
       s[0] = t0;
-      const float w = th[0] * 0.5773502691896258f;
+      const float w = th[0 * TS];
       vo[0] += w * t0;
     }
     { // path 1: (0, 1) x (1,-1) -> (1, -1)
       const float t0 = 0.9999999999999999f * v[0] * g[1];
       const float t1 = 1.0000000000000002f * v[0] * g[2];
       const float t2 = 0.9999999999999999f * v[0] * g[3];
-      const float w = th[1] * 0.5f;
+      const float w = th[1 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
@@ -971,7 +1137,7 @@ template <> struct TP<2, 0, 1> {
       const float t2 = 1.0000000000000002f * v[0] * g[6];
       const float t3 = 1.0f * v[0] * g[7];
       const float t4 = 1.0f * v[0] * g[8];
-      const float w = th[2] * 0.5f;
+      const float w = th[2 * TS];
       vo[4] += w * t0;
       vo[5] += w * t1;
       vo[6] += w * t2;
@@ -982,7 +1148,7 @@ template <> struct TP<2, 0, 1> {
       const float t0 = 0.9999999999999999f * v[1] * g[0];
       const float t1 = 1.0000000000000002f * v[2] * g[0];
       const float t2 = 0.9999999999999999f * v[3] * g[0];
-      const float w = th[3] * 0.5f;
+      const float w = th[3 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
@@ -990,7 +1156,7 @@ template <> struct TP<2, 0, 1> {
     { // path 4: (1, -1) x (1,-1) -> (0, 1)
       const float t0 = 0.5773502691896257f * v[1] * g[1] + 0.5773502691896258f * v[2] * g[2] + 0.5773502691896257f * v[3] * g[3];
       s[1] = t0;
-      const float w = th[4] * 0.5773502691896258f;
+      const float w = th[4 * TS];
       vo[0] += w * t0;
     }
     { // path 6: (1, -1) x (1,-1) -> (2, 1)
@@ -999,7 +1165,7 @@ template <> struct TP<2, 0, 1> {
       const float t2 = 0.4082482904638631f * v[1] * g[1] + -0.8164965809277261f * v[2] * g[2] + 0.4082482904638631f * v[3] * g[3];
       const float t3 = -0.7071067811865476f * v[2] * g[3] + -0.7071067811865476f * v[3] * g[2];
       const float t4 = 0.7071067811865475f * v[1] * g[1] + -0.7071067811865475f * v[3] * g[3];
-      const float w = th[6] * 0.5f;
+      const float w = th[6 * TS];
       vo[4] += w * t0;
       vo[5] += w * t1;
       vo[6] += w * t2;
@@ -1010,7 +1176,7 @@ template <> struct TP<2, 0, 1> {
       const float t0 = -0.3162277660168379f * v[1] * g[6] + -0.547722557505166f * v[1] * g[8] + 0.547722557505166f * v[2] * g[5] + 0.547722557505166f * v[3] * g[4];
       const float t1 = 0.547722557505166f * v[1] * g[5] + 0.632455532033676f * v[2] * g[6] + 0.547722557505166f * v[3] * g[7];
       const float t2 = 0.547722557505166f * v[1] * g[4] + 0.547722557505166f * v[2] * g[7] + -0.3162277660168379f * v[3] * g[6] + 0.547722557505166f * v[3] * g[8];
-      const float w = th[7] * 0.5f;
+      const float w = th[7 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
@@ -1021,7 +1187,7 @@ template <> struct TP<2, 0, 1> {
       const float t2 = 1.0000000000000002f * v[6] * g[0];
       const float t3 = 1.0f * v[7] * g[0];
       const float t4 = 1.0f * v[8] * g[0];
-      const float w = th[9] * 0.5f;
+      const float w = th[9 * TS];
       vo[4] += w * t0;
       vo[5] += w * t1;
       vo[6] += w * t2;
@@ -1032,7 +1198,7 @@ template <> struct TP<2, 0, 1> {
       const float t0 = 0.547722557505166f * v[4] * g[3] + 0.547722557505166f * v[5] * g[2] + -0.3162277660168379f * v[6] * g[1] + -0.547722557505166f * v[8] * g[1];
       const float t1 = 0.547722557505166f * v[5] * g[1] + 0.632455532033676f * v[6] * g[2] + 0.547722557505166f * v[7] * g[3];
       const float t2 = 0.547722557505166f * v[4] * g[1] + -0.3162277660168379f * v[6] * g[3] + 0.547722557505166f * v[7] * g[2] + 0.547722557505166f * v[8] * g[3];
-      const float w = th[10] * 0.5f;
+      const float w = th[10 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
@@ -1040,7 +1206,7 @@ template <> struct TP<2, 0, 1> {
     { // path 12: (2, 1) x (2,1) -> (0, 1)
       const float t0 = 0.4472135954999579f * v[4] * g[4] + 0.4472135954999579f * v[5] * g[5] + 0.44721359549995804f * v[6] * g[6] + 0.4472135954999579f * v[7] * g[7] + 0.4472135954999579f * v[8] * g[8];
       s[2] = t0;
-      const float w = th[12] * 0.5773502691896258f;
+      const float w = th[12 * TS];
       vo[0] += w * t0;
     }
     { // path 14: (2, 1) x (2,1) -> (2, 1)
@@ -1049,7 +1215,7 @@ template <> struct TP<2, 0, 1> {
       const float t2 = 0.5345224838248488f * v[4] * g[4] + -0.2672612419124244f * v[5] * g[5] + -0.5345224838248489f * v[6] * g[6] + -0.2672612419124244f * v[7] * g[7] + 0.5345224838248488f * v[8] * g[8];
       const float t3 = -0.4629100498862757f * v[4] * g[5] + -0.4629100498862757f * v[5] * g[4] + -0.2672612419124244f * v[6] * g[7] + -0.2672612419124244f * v[7] * g[6] + -0.4629100498862757f * v[7] * g[8] + -0.4629100498862757f * v[8] * g[7];
       const float t4 = 0.4629100498862757f * v[5] * g[5] + 0.5345224838248488f * v[6] * g[8] + -0.4629100498862757f * v[7] * g[7] + 0.5345224838248488f * v[8] * g[6];
-      const float w = th[14] * 0.5f;
+      const float w = th[14 * TS];
       vo[4] += w * t0;
       vo[5] += w * t1;
       vo[6] += w * t2;
@@ -1057,157 +1223,205 @@ template <> struct TP<2, 0, 1> {
       vo[8] += w * t4;
     }
   }
+  template <int TS>
   static __device__ __forceinline__ void bwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, const float* __restrict__ gs, const float* __restrict__ gvo, float* gv, float* gg) {
     { // path 0
-      const float w = th[0] * 0.5773502691896258f;
+      const float w = th[0 * TS];
       const float gt0 = gs[0] + w * gvo[0];
-      gv[0] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[0];
+      const float s0_0 = gt0;
+      gv[0] = fmaf(s0_0, g[0], gv[0]); gg[0] = fmaf(s0_0, v[0], gg[0]);
     }
     { // path 1
-      const float w = th[1] * 0.5f;
+      const float w = th[1 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[0] += 0.9999999999999999f * gt0 * g[1]; gg[1] += 0.9999999999999999f * gt0 * v[0];
-      gv[0] += 1.0000000000000002f * gt1 * g[2]; gg[2] += 1.0000000000000002f * gt1 * v[0];
-      gv[0] += 0.9999999999999999f * gt2 * g[3]; gg[3] += 0.9999999999999999f * gt2 * v[0];
+      const float s0_0 = gt0;
+      gv[0] = fmaf(s0_0, g[1], gv[0]); gg[1] = fmaf(s0_0, v[0], gg[1]);
+      const float s1_0 = gt1;
+      gv[0] = fmaf(s1_0, g[2], gv[0]); gg[2] = fmaf(s1_0, v[0], gg[2]);
+      const float s2_0 = gt2;
+      gv[0] = fmaf(s2_0, g[3], gv[0]); gg[3] = fmaf(s2_0, v[0], gg[3]);
     }
     { // path 2
-      const float w = th[2] * 0.5f;
+      const float w = th[2 * TS];
       const float gt0 = w * gvo[4];
       const float gt1 = w * gvo[5];
       const float gt2 = w * gvo[6];
       const float gt3 = w * gvo[7];
       const float gt4 = w * gvo[8];
-      gv[0] += 1.0f * gt0 * g[4]; gg[4] += 1.0f * gt0 * v[0];
-      gv[0] += 1.0f * gt1 * g[5]; gg[5] += 1.0f * gt1 * v[0];
-      gv[0] += 1.0000000000000002f * gt2 * g[6]; gg[6] += 1.0000000000000002f * gt2 * v[0];
-      gv[0] += 1.0f * gt3 * g[7]; gg[7] += 1.0f * gt3 * v[0];
-      gv[0] += 1.0f * gt4 * g[8]; gg[8] += 1.0f * gt4 * v[0];
+      const float s0_0 = gt0;
+      gv[0] = fmaf(s0_0, g[4], gv[0]); gg[4] = fmaf(s0_0, v[0], gg[4]);
+      const float s1_0 = gt1;
+      gv[0] = fmaf(s1_0, g[5], gv[0]); gg[5] = fmaf(s1_0, v[0], gg[5]);
+      const float s2_0 = gt2;
+      gv[0] = fmaf(s2_0, g[6], gv[0]); gg[6] = fmaf(s2_0, v[0], gg[6]);
+      const float s3_0 = gt3;
+      gv[0] = fmaf(s3_0, g[7], gv[0]); gg[7] = fmaf(s3_0, v[0], gg[7]);
+      const float s4_0 = gt4;
+      gv[0] = fmaf(s4_0, g[8], gv[0]); gg[8] = fmaf(s4_0, v[0], gg[8]);
     }
     { // path 3
-      const float w = th[3] * 0.5f;
+      const float w = th[3 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[1] += 0.9999999999999999f * gt0 * g[0]; gg[0] += 0.9999999999999999f * gt0 * v[1];
-      gv[2] += 1.0000000000000002f * gt1 * g[0]; gg[0] += 1.0000000000000002f * gt1 * v[2];
-      gv[3] += 0.9999999999999999f * gt2 * g[0]; gg[0] += 0.9999999999999999f * gt2 * v[3];
+      const float s0_0 = gt0;
+      gv[1] = fmaf(s0_0, g[0], gv[1]); gg[0] = fmaf(s0_0, v[1], gg[0]);
+      const float s1_0 = gt1;
+      gv[2] = fmaf(s1_0, g[0], gv[2]); gg[0] = fmaf(s1_0, v[2], gg[0]);
+      const float s2_0 = gt2;
+      gv[3] = fmaf(s2_0, g[0], gv[3]); gg[0] = fmaf(s2_0, v[3], gg[0]);
     }
     { // path 4
-      const float w = th[4] * 0.5773502691896258f;
+      const float w = th[4 * TS];
       const float gt0 = gs[1] + w * gvo[0];
-      gv[1] += 0.5773502691896257f * gt0 * g[1]; gg[1] += 0.5773502691896257f * gt0 * v[1];
-      gv[2] += 0.5773502691896258f * gt0 * g[2]; gg[2] += 0.5773502691896258f * gt0 * v[2];
-      gv[3] += 0.5773502691896257f * gt0 * g[3]; gg[3] += 0.5773502691896257f * gt0 * v[3];
+      const float s0_0 = 0.5773502691896257f * gt0;
+      gv[1] = fmaf(s0_0, g[1], gv[1]); gg[1] = fmaf(s0_0, v[1], gg[1]);
+      gv[2] = fmaf(s0_0, g[2], gv[2]); gg[2] = fmaf(s0_0, v[2], gg[2]);
+      gv[3] = fmaf(s0_0, g[3], gv[3]); gg[3] = fmaf(s0_0, v[3], gg[3]);
     }
     { // path 6
-      const float w = th[6] * 0.5f;
+      const float w = th[6 * TS];
       const float gt0 = w * gvo[4];
       const float gt1 = w * gvo[5];
       const float gt2 = w * gvo[6];
       const float gt3 = w * gvo[7];
       const float gt4 = w * gvo[8];
-      gv[1] += 0.4082482904638631f * gt2 * g[1]; gg[1] += 0.4082482904638631f * gt2 * v[1];
-      gv[1] += 0.7071067811865475f * gt4 * g[1]; gg[1] += 0.7071067811865475f * gt4 * v[1];
-      gv[1] += -0.7071067811865476f * gt1 * g[2]; gg[2] += -0.7071067811865476f * gt1 * v[1];
-      gv[1] += -0.7071067811865475f * gt0 * g[3]; gg[3] += -0.7071067811865475f * gt0 * v[1];
-      gv[2] += -0.7071067811865476f * gt1 * g[1]; gg[1] += -0.7071067811865476f * gt1 * v[2];
-      gv[2] += -0.8164965809277261f * gt2 * g[2]; gg[2] += -0.8164965809277261f * gt2 * v[2];
-      gv[2] += -0.7071067811865476f * gt3 * g[3]; gg[3] += -0.7071067811865476f * gt3 * v[2];
-      gv[3] += -0.7071067811865475f * gt0 * g[1]; gg[1] += -0.7071067811865475f * gt0 * v[3];
-      gv[3] += -0.7071067811865476f * gt3 * g[2]; gg[2] += -0.7071067811865476f * gt3 * v[3];
-      gv[3] += 0.4082482904638631f * gt2 * g[3]; gg[3] += 0.4082482904638631f * gt2 * v[3];
-      gv[3] += -0.7071067811865475f * gt4 * g[3]; gg[3] += -0.7071067811865475f * gt4 * v[3];
+      const float s2_0 = 0.4082482904638631f * gt2;
+      gv[1] = fmaf(s2_0, g[1], gv[1]); gg[1] = fmaf(s2_0, v[1], gg[1]);
+      const float s4_0 = 0.7071067811865475f * gt4;
+      gv[1] = fmaf(s4_0, g[1], gv[1]); gg[1] = fmaf(s4_0, v[1], gg[1]);
+      const float s1_0 = 0.7071067811865476f * gt1;
+      gv[1] = fmaf(-s1_0, g[2], gv[1]); gg[2] = fmaf(-s1_0, v[1], gg[2]);
+      const float s0_0 = 0.7071067811865475f * gt0;
+      gv[1] = fmaf(-s0_0, g[3], gv[1]); gg[3] = fmaf(-s0_0, v[1], gg[3]);
+      gv[2] = fmaf(-s1_0, g[1], gv[2]); gg[1] = fmaf(-s1_0, v[2], gg[1]);
+      const float s2_1 = 0.8164965809277261f * gt2;
+      gv[2] = fmaf(-s2_1, g[2], gv[2]); gg[2] = fmaf(-s2_1, v[2], gg[2]);
+      const float s3_0 = 0.7071067811865476f * gt3;
+      gv[2] = fmaf(-s3_0, g[3], gv[2]); gg[3] = fmaf(-s3_0, v[2], gg[3]);
+      gv[3] = fmaf(-s0_0, g[1], gv[3]); gg[1] = fmaf(-s0_0, v[3], gg[1]);
+      gv[3] = fmaf(-s3_0, g[2], gv[3]); gg[2] = fmaf(-s3_0, v[3], gg[2]);
+      gv[3] = fmaf(s2_0, g[3], gv[3]); gg[3] = fmaf(s2_0, v[3], gg[3]);
+      gv[3] = fmaf(-s4_0, g[3], gv[3]); gg[3] = fmaf(-s4_0, v[3], gg[3]);
     }
     { // path 7
-      const float w = th[7] * 0.5f;
+      const float w = th[7 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[1] += 0.547722557505166f * gt2 * g[4]; gg[4] += 0.547722557505166f * gt2 * v[1];
-      gv[1] += 0.547722557505166f * gt1 * g[5]; gg[5] += 0.547722557505166f * gt1 * v[1];
-      gv[1] += -0.3162277660168379f * gt0 * g[6]; gg[6] += -0.3162277660168379f * gt0 * v[1];
-      gv[1] += -0.547722557505166f * gt0 * g[8]; gg[8] += -0.547722557505166f * gt0 * v[1];
-      gv[2] += 0.547722557505166f * gt0 * g[5]; gg[5] += 0.547722557505166f * gt0 * v[2];
-      gv[2] += 0.632455532033676f * gt1 * g[6]; gg[6] += 0.632455532033676f * gt1 * v[2];
-      gv[2] += 0.547722557505166f * gt2 * g[7]; gg[7] += 0.547722557505166f * gt2 * v[2];
-      gv[3] += 0.547722557505166f * gt0 * g[4]; gg[4] += 0.547722557505166f * gt0 * v[3];
-      gv[3] += -0.3162277660168379f * gt2 * g[6]; gg[6] += -0.3162277660168379f * gt2 * v[3];
-      gv[3] += 0.547722557505166f * gt1 * g[7]; gg[7] += 0.547722557505166f * gt1 * v[3];
-      gv[3] += 0.547722557505166f * gt2 * g[8]; gg[8] += 0.547722557505166f * gt2 * v[3];
+      const float s2_0 = 0.547722557505166f * gt2;
+      gv[1] = fmaf(s2_0, g[4], gv[1]); gg[4] = fmaf(s2_0, v[1], gg[4]);
+      const float s1_0 = 0.547722557505166f * gt1;
+      gv[1] = fmaf(s1_0, g[5], gv[1]); gg[5] = fmaf(s1_0, v[1], gg[5]);
+      const float s0_0 = 0.3162277660168379f * gt0;
+      gv[1] = fmaf(-s0_0, g[6], gv[1]); gg[6] = fmaf(-s0_0, v[1], gg[6]);
+      const float s0_1 = 0.547722557505166f * gt0;
+      gv[1] = fmaf(-s0_1, g[8], gv[1]); gg[8] = fmaf(-s0_1, v[1], gg[8]);
+      gv[2] = fmaf(s0_1, g[5], gv[2]); gg[5] = fmaf(s0_1, v[2], gg[5]);
+      const float s1_1 = 0.632455532033676f * gt1;
+      gv[2] = fmaf(s1_1, g[6], gv[2]); gg[6] = fmaf(s1_1, v[2], gg[6]);
+      gv[2] = fmaf(s2_0, g[7], gv[2]); gg[7] = fmaf(s2_0, v[2], gg[7]);
+      gv[3] = fmaf(s0_1, g[4], gv[3]); gg[4] = fmaf(s0_1, v[3], gg[4]);
+      const float s2_1 = 0.3162277660168379f * gt2;
+      gv[3] = fmaf(-s2_1, g[6], gv[3]); gg[6] = fmaf(-s2_1, v[3], gg[6]);
+      gv[3] = fmaf(s1_0, g[7], gv[3]); gg[7] = fmaf(s1_0, v[3], gg[7]);
+      gv[3] = fmaf(s2_0, g[8], gv[3]); gg[8] = fmaf(s2_0, v[3], gg[8]);
     }
     { // path 9
-      const float w = th[9] * 0.5f;
+      const float w = th[9 * TS];
       const float gt0 = w * gvo[4];
       const float gt1 = w * gvo[5];
       const float gt2 = w * gvo[6];
       const float gt3 = w * gvo[7];
       const float gt4 = w * gvo[8];
-      gv[4] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[4];
-      gv[5] += 1.0f * gt1 * g[0]; gg[0] += 1.0f * gt1 * v[5];
-      gv[6] += 1.0000000000000002f * gt2 * g[0]; gg[0] += 1.0000000000000002f * gt2 * v[6];
-      gv[7] += 1.0f * gt3 * g[0]; gg[0] += 1.0f * gt3 * v[7];
-      gv[8] += 1.0f * gt4 * g[0]; gg[0] += 1.0f * gt4 * v[8];
+      const float s0_0 = gt0;
+      gv[4] = fmaf(s0_0, g[0], gv[4]); gg[0] = fmaf(s0_0, v[4], gg[0]);
+      const float s1_0 = gt1;
+      gv[5] = fmaf(s1_0, g[0], gv[5]); gg[0] = fmaf(s1_0, v[5], gg[0]);
+      const float s2_0 = gt2;
+      gv[6] = fmaf(s2_0, g[0], gv[6]); gg[0] = fmaf(s2_0, v[6], gg[0]);
+      const float s3_0 = gt3;
+      gv[7] = fmaf(s3_0, g[0], gv[7]); gg[0] = fmaf(s3_0, v[7], gg[0]);
+      const float s4_0 = gt4;
+      gv[8] = fmaf(s4_0, g[0], gv[8]); gg[0] = fmaf(s4_0, v[8], gg[0]);
     }
     { // path 10
-      const float w = th[10] * 0.5f;
+      const float w = th[10 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[4] += 0.547722557505166f * gt2 * g[1]; gg[1] += 0.547722557505166f * gt2 * v[4];
-      gv[4] += 0.547722557505166f * gt0 * g[3]; gg[3] += 0.547722557505166f * gt0 * v[4];
-      gv[5] += 0.547722557505166f * gt1 * g[1]; gg[1] += 0.547722557505166f * gt1 * v[5];
-      gv[5] += 0.547722557505166f * gt0 * g[2]; gg[2] += 0.547722557505166f * gt0 * v[5];
-      gv[6] += -0.3162277660168379f * gt0 * g[1]; gg[1] += -0.3162277660168379f * gt0 * v[6];
-      gv[6] += 0.632455532033676f * gt1 * g[2]; gg[2] += 0.632455532033676f * gt1 * v[6];
-      gv[6] += -0.3162277660168379f * gt2 * g[3]; gg[3] += -0.3162277660168379f * gt2 * v[6];
-      gv[7] += 0.547722557505166f * gt2 * g[2]; gg[2] += 0.547722557505166f * gt2 * v[7];
-      gv[7] += 0.547722557505166f * gt1 * g[3]; gg[3] += 0.547722557505166f * gt1 * v[7];
-      gv[8] += -0.547722557505166f * gt0 * g[1]; gg[1] += -0.547722557505166f * gt0 * v[8];
-      gv[8] += 0.547722557505166f * gt2 * g[3]; gg[3] += 0.547722557505166f * gt2 * v[8];
+      const float s2_0 = 0.547722557505166f * gt2;
+      gv[4] = fmaf(s2_0, g[1], gv[4]); gg[1] = fmaf(s2_0, v[4], gg[1]);
+      const float s0_0 = 0.547722557505166f * gt0;
+      gv[4] = fmaf(s0_0, g[3], gv[4]); gg[3] = fmaf(s0_0, v[4], gg[3]);
+      const float s1_0 = 0.547722557505166f * gt1;
+      gv[5] = fmaf(s1_0, g[1], gv[5]); gg[1] = fmaf(s1_0, v[5], gg[1]);
+      gv[5] = fmaf(s0_0, g[2], gv[5]); gg[2] = fmaf(s0_0, v[5], gg[2]);
+      const float s0_1 = 0.3162277660168379f * gt0;
+      gv[6] = fmaf(-s0_1, g[1], gv[6]); gg[1] = fmaf(-s0_1, v[6], gg[1]);
+      const float s1_1 = 0.632455532033676f * gt1;
+      gv[6] = fmaf(s1_1, g[2], gv[6]); gg[2] = fmaf(s1_1, v[6], gg[2]);
+      const float s2_1 = 0.3162277660168379f * gt2;
+      gv[6] = fmaf(-s2_1, g[3], gv[6]); gg[3] = fmaf(-s2_1, v[6], gg[3]);
+      gv[7] = fmaf(s2_0, g[2], gv[7]); gg[2] = fmaf(s2_0, v[7], gg[2]);
+      gv[7] = fmaf(s1_0, g[3], gv[7]); gg[3] = fmaf(s1_0, v[7], gg[3]);
+      gv[8] = fmaf(-s0_0, g[1], gv[8]); gg[1] = fmaf(-s0_0, v[8], gg[1]);
+      gv[8] = fmaf(s2_0, g[3], gv[8]); gg[3] = fmaf(s2_0, v[8], gg[3]);
     }
     { // path 12
-      const float w = th[12] * 0.5773502691896258f;
+      const float w = th[12 * TS];
       const float gt0 = gs[2] + w * gvo[0];
-      gv[4] += 0.4472135954999579f * gt0 * g[4]; gg[4] += 0.4472135954999579f * gt0 * v[4];
-      gv[5] += 0.4472135954999579f * gt0 * g[5]; gg[5] += 0.4472135954999579f * gt0 * v[5];
-      gv[6] += 0.44721359549995804f * gt0 * g[6]; gg[6] += 0.44721359549995804f * gt0 * v[6];
-      gv[7] += 0.4472135954999579f * gt0 * g[7]; gg[7] += 0.4472135954999579f * gt0 * v[7];
-      gv[8] += 0.4472135954999579f * gt0 * g[8]; gg[8] += 0.4472135954999579f * gt0 * v[8];
+      const float s0_0 = 0.4472135954999579f * gt0;
+      gv[4] = fmaf(s0_0, g[4], gv[4]); gg[4] = fmaf(s0_0, v[4], gg[4]);
+      gv[5] = fmaf(s0_0, g[5], gv[5]); gg[5] = fmaf(s0_0, v[5], gg[5]);
+      gv[6] = fmaf(s0_0, g[6], gv[6]); gg[6] = fmaf(s0_0, v[6], gg[6]);
+      gv[7] = fmaf(s0_0, g[7], gv[7]); gg[7] = fmaf(s0_0, v[7], gg[7]);
+      gv[8] = fmaf(s0_0, g[8], gv[8]); gg[8] = fmaf(s0_0, v[8], gg[8]);
     }
     { // path 14
-      const float w = th[14] * 0.5f;
+      const float w = th[14 * TS];
       const float gt0 = w * gvo[4];
       const float gt1 = w * gvo[5];
       const float gt2 = w * gvo[6];
       const float gt3 = w * gvo[7];
       const float gt4 = w * gvo[8];
-      gv[4] += 0.5345224838248488f * gt2 * g[4]; gg[4] += 0.5345224838248488f * gt2 * v[4];
-      gv[4] += -0.4629100498862757f * gt3 * g[5]; gg[5] += -0.4629100498862757f * gt3 * v[4];
-      gv[4] += 0.5345224838248488f * gt0 * g[6]; gg[6] += 0.5345224838248488f * gt0 * v[4];
-      gv[4] += -0.4629100498862757f * gt1 * g[7]; gg[7] += -0.4629100498862757f * gt1 * v[4];
-      gv[5] += -0.4629100498862757f * gt3 * g[4]; gg[4] += -0.4629100498862757f * gt3 * v[5];
-      gv[5] += -0.2672612419124244f * gt2 * g[5]; gg[5] += -0.2672612419124244f * gt2 * v[5];
-      gv[5] += 0.4629100498862757f * gt4 * g[5]; gg[5] += 0.4629100498862757f * gt4 * v[5];
-      gv[5] += -0.2672612419124244f * gt1 * g[6]; gg[6] += -0.2672612419124244f * gt1 * v[5];
-      gv[5] += -0.4629100498862757f * gt0 * g[7]; gg[7] += -0.4629100498862757f * gt0 * v[5];
-      gv[5] += 0.4629100498862757f * gt1 * g[8]; gg[8] += 0.4629100498862757f * gt1 * v[5];
-      gv[6] += 0.5345224838248488f * gt0 * g[4]; gg[4] += 0.5345224838248488f * gt0 * v[6];
-      gv[6] += -0.2672612419124244f * gt1 * g[5]; gg[5] += -0.2672612419124244f * gt1 * v[6];
-      gv[6] += -0.5345224838248489f * gt2 * g[6]; gg[6] += -0.5345224838248489f * gt2 * v[6];
-      gv[6] += -0.2672612419124244f * gt3 * g[7]; gg[7] += -0.2672612419124244f * gt3 * v[6];
-      gv[6] += 0.5345224838248488f * gt4 * g[8]; gg[8] += 0.5345224838248488f * gt4 * v[6];
-      gv[7] += -0.4629100498862757f * gt1 * g[4]; gg[4] += -0.4629100498862757f * gt1 * v[7];
-      gv[7] += -0.4629100498862757f * gt0 * g[5]; gg[5] += -0.4629100498862757f * gt0 * v[7];
-      gv[7] += -0.2672612419124244f * gt3 * g[6]; gg[6] += -0.2672612419124244f * gt3 * v[7];
-      gv[7] += -0.2672612419124244f * gt2 * g[7]; gg[7] += -0.2672612419124244f * gt2 * v[7];
-      gv[7] += -0.4629100498862757f * gt4 * g[7]; gg[7] += -0.4629100498862757f * gt4 * v[7];
-      gv[7] += -0.4629100498862757f * gt3 * g[8]; gg[8] += -0.4629100498862757f * gt3 * v[7];
-      gv[8] += 0.4629100498862757f * gt1 * g[5]; gg[5] += 0.4629100498862757f * gt1 * v[8];
-      gv[8] += 0.5345224838248488f * gt4 * g[6]; gg[6] += 0.5345224838248488f * gt4 * v[8];
-      gv[8] += -0.4629100498862757f * gt3 * g[7]; gg[7] += -0.4629100498862757f * gt3 * v[8];
-      gv[8] += 0.5345224838248488f * gt2 * g[8]; gg[8] += 0.5345224838248488f * gt2 * v[8];
+      const float s2_0 = 0.5345224838248488f * gt2;
+      gv[4] = fmaf(s2_0, g[4], gv[4]); gg[4] = fmaf(s2_0, v[4], gg[4]);
+      const float s3_0 = 0.4629100498862757f * gt3;
+      gv[4] = fmaf(-s3_0, g[5], gv[4]); gg[5] = fmaf(-s3_0, v[4], gg[5]);
+      const float s0_0 = 0.5345224838248488f * gt0;
+      gv[4] = fmaf(s0_0, g[6], gv[4]); gg[6] = fmaf(s0_0, v[4], gg[6]);
+      const float s1_0 = 0.4629100498862757f * gt1;
+      gv[4] = fmaf(-s1_0, g[7], gv[4]); gg[7] = fmaf(-s1_0, v[4], gg[7]);
+      gv[5] = fmaf(-s3_0, g[4], gv[5]); gg[4] = fmaf(-s3_0, v[5], gg[4]);
+      const float s2_1 = 0.2672612419124244f * gt2;
+      gv[5] = fmaf(-s2_1, g[5], gv[5]); gg[5] = fmaf(-s2_1, v[5], gg[5]);
+      const float s4_0 = 0.4629100498862757f * gt4;
+      gv[5] = fmaf(s4_0, g[5], gv[5]); gg[5] = fmaf(s4_0, v[5], gg[5]);
+      const float s1_1 = 0.2672612419124244f * gt1;
+      gv[5] = fmaf(-s1_1, g[6], gv[5]); gg[6] = fmaf(-s1_1, v[5], gg[6]);
+      const float s0_1 = 0.4629100498862757f * gt0;
+      gv[5] = fmaf(-s0_1, g[7], gv[5]); gg[7] = fmaf(-s0_1, v[5], gg[7]);
+      gv[5] = fmaf(s1_0, g[8], gv[5]); gg[8] = fmaf(s1_0, v[5], gg[8]);
+      gv[6] = fmaf(s0_0, g[4], gv[6]); gg[4] = fmaf(s0_0, v[6], gg[4]);
+      gv[6] = fmaf(-s1_1, g[5], gv[6]); gg[5] = fmaf(-s1_1, v[6], gg[5]);
+      gv[6] = fmaf(-s2_0, g[6], gv[6]); gg[6] = fmaf(-s2_0, v[6], gg[6]);
+      const float s3_1 = 0.2672612419124244f * gt3;
+      gv[6] = fmaf(-s3_1, g[7], gv[6]); gg[7] = fmaf(-s3_1, v[6], gg[7]);
+      const float s4_1 = 0.5345224838248488f * gt4;
+      gv[6] = fmaf(s4_1, g[8], gv[6]); gg[8] = fmaf(s4_1, v[6], gg[8]);
+      gv[7] = fmaf(-s1_0, g[4], gv[7]); gg[4] = fmaf(-s1_0, v[7], gg[4]);
+      gv[7] = fmaf(-s0_1, g[5], gv[7]); gg[5] = fmaf(-s0_1, v[7], gg[5]);
+      gv[7] = fmaf(-s3_1, g[6], gv[7]); gg[6] = fmaf(-s3_1, v[7], gg[6]);
+      gv[7] = fmaf(-s2_1, g[7], gv[7]); gg[7] = fmaf(-s2_1, v[7], gg[7]);
+      gv[7] = fmaf(-s4_0, g[7], gv[7]); gg[7] = fmaf(-s4_0, v[7], gg[7]);
+      gv[7] = fmaf(-s3_0, g[8], gv[7]); gg[8] = fmaf(-s3_0, v[7], gg[8]);
+      gv[8] = fmaf(s1_0, g[5], gv[8]); gg[5] = fmaf(s1_0, v[8], gg[5]);
+      gv[8] = fmaf(s4_1, g[6], gv[8]); gg[6] = fmaf(s4_1, v[8], gg[6]);
+      gv[8] = fmaf(-s3_0, g[7], gv[8]); gg[7] = fmaf(-s3_0, v[8], gg[7]);
+      gv[8] = fmaf(s2_0, g[8], gv[8]); gg[8] = fmaf(s2_0, v[8], gg[8]);
     }
   }
   static constexpr int NNZ = 83;
@@ -1216,6 +1430,7 @@ template <> struct TP<2, 0, 1> {
 template <> struct TP<2, 0, 2> {
   // in irreps [(0, 1), (1, -1), (2, 1)]; out irreps [(0, 1)]
   static constexpr int NP = 3, DIN = 9, DOUT = 1, NS = 3, NPW = 0;
+  template <int TS>
   static __device__ __forceinline__ void fwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, float* s, float* vo) {
     { // path 0: (0, 1) x (0,1) -> (0, 1)
       const float t0 = 1.0f * v[0] * g[0];
@@ -1230,24 +1445,28 @@ template <> struct TP<2, 0, 2> {
       s[2] = t0;
     }
   }
+  template <int TS>
   static __device__ __forceinline__ void bwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, const float* __restrict__ gs, const float* __restrict__ gvo, float* gv, float* gg) {
     { // path 0
       const float gt0 = gs[0];
-      gv[0] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[0];
+      const float s0_0 = gt0;
+      gv[0] = fmaf(s0_0, g[0], gv[0]); gg[0] = fmaf(s0_0, v[0], gg[0]);
     }
     { // path 1
       const float gt0 = gs[1];
-      gv[1] += 0.5773502691896257f * gt0 * g[1]; gg[1] += 0.5773502691896257f * gt0 * v[1];
-      gv[2] += 0.5773502691896258f * gt0 * g[2]; gg[2] += 0.5773502691896258f * gt0 * v[2];
-      gv[3] += 0.5773502691896257f * gt0 * g[3]; gg[3] += 0.5773502691896257f * gt0 * v[3];
+      const float s0_0 = 0.5773502691896257f * gt0;
+      gv[1] = fmaf(s0_0, g[1], gv[1]); gg[1] = fmaf(s0_0, v[1], gg[1]);
+      gv[2] = fmaf(s0_0, g[2], gv[2]); gg[2] = fmaf(s0_0, v[2], gg[2]);
+      gv[3] = fmaf(s0_0, g[3], gv[3]); gg[3] = fmaf(s0_0, v[3], gg[3]);
     }
     { // path 2
       const float gt0 = gs[2];
-      gv[4] += 0.4472135954999579f * gt0 * g[4]; gg[4] += 0.4472135954999579f * gt0 * v[4];
-      gv[5] += 0.4472135954999579f * gt0 * g[5]; gg[5] += 0.4472135954999579f * gt0 * v[5];
-      gv[6] += 0.44721359549995804f * gt0 * g[6]; gg[6] += 0.44721359549995804f * gt0 * v[6];
-      gv[7] += 0.4472135954999579f * gt0 * g[7]; gg[7] += 0.4472135954999579f * gt0 * v[7];
-      gv[8] += 0.4472135954999579f * gt0 * g[8]; gg[8] += 0.4472135954999579f * gt0 * v[8];
+      const float s0_0 = 0.4472135954999579f * gt0;
+      gv[4] = fmaf(s0_0, g[4], gv[4]); gg[4] = fmaf(s0_0, v[4], gg[4]);
+      gv[5] = fmaf(s0_0, g[5], gv[5]); gg[5] = fmaf(s0_0, v[5], gg[5]);
+      gv[6] = fmaf(s0_0, g[6], gv[6]); gg[6] = fmaf(s0_0, v[6], gg[6]);
+      gv[7] = fmaf(s0_0, g[7], gv[7]); gg[7] = fmaf(s0_0, v[7], gg[7]);
+      gv[8] = fmaf(s0_0, g[8], gv[8]); gg[8] = fmaf(s0_0, v[8], gg[8]);
     }
   }
   static constexpr int NNZ = 9;
@@ -1256,20 +1475,21 @@ template <> struct TP<2, 0, 2> {
 template <> struct TP<2, 1, 0> {
   // in irreps [(0, 1), (1, -1), (1, 1), (2, 1), (2, -1)]; out irreps [(0, 1), (0, -1), (1, -1), (1, 1), (2, 1), (2, -1)]
   static constexpr int NP = 27, DIN = 17, DOUT = 18, NS = 3, NPW = 27;
+  template <int TS>
   static __device__ __forceinline__ void fwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, float* s, float* vo) {
     #pragma unroll
     for (int k = 0; k < 18; ++k) vo[k] = 0.f;
     { // path 0: (0, 1) x (0,1) -> (0, 1)
       const float t0 = 1.0f * v[0] * g[0];
       s[0] = t0;
-      const float w = th[0] * 0.5773502691896258f;
+      const float w = th[0 * TS];
       vo[0] += w * t0;
     }
     { // path 1: (0, 1) x (1,-1) -> (1, -1)
       const float t0 = 0.9999999999999999f * v[0] * g[1];
       const float t1 = 1.0000000000000002f * v[0] * g[2];
       const float t2 = 0.9999999999999999f * v[0] * g[3];
-      const float w = th[1] * 0.4082482904638631f;
+      const float w = th[1 * TS];
       vo[2] += w * t0;
       vo[3] += w * t1;
       vo[4] += w * t2;
@@ -1280,7 +1500,7 @@ template <> struct TP<2, 1, 0> {
       const float t2 = 1.0000000000000002f * v[0] * g[6];
       const float t3 = 1.0f * v[0] * g[7];
       const float t4 = 1.0f * v[0] * g[8];
-      const float w = th[2] * 0.4082482904638631f;
+      const float w = th[2 * TS];
       vo[8] += w * t0;
       vo[9] += w * t1;
       vo[10] += w * t2;
@@ -1291,7 +1511,7 @@ template <> struct TP<2, 1, 0> {
       const float t0 = 0.9999999999999999f * v[1] * g[0];
       const float t1 = 1.0000000000000002f * v[2] * g[0];
       const float t2 = 0.9999999999999999f * v[3] * g[0];
-      const float w = th[3] * 0.4082482904638631f;
+      const float w = th[3 * TS];
       vo[2] += w * t0;
       vo[3] += w * t1;
       vo[4] += w * t2;
@@ -1299,14 +1519,14 @@ template <> struct TP<2, 1, 0> {
     { // path 4: (1, -1) x (1,-1) -> (0, 1)
       const float t0 = 0.5773502691896257f * v[1] * g[1] + 0.5773502691896258f * v[2] * g[2] + 0.5773502691896257f * v[3] * g[3];
       s[1] = t0;
-      const float w = th[4] * 0.5773502691896258f;
+      const float w = th[4 * TS];
       vo[0] += w * t0;
     }
     { // path 5: (1, -1) x (1,-1) -> (1, 1)
       const float t0 = 0.7071067811865476f * v[2] * g[3] + -0.7071067811865476f * v[3] * g[2];
       const float t1 = -0.7071067811865476f * v[1] * g[3] + 0.7071067811865476f * v[3] * g[1];
       const float t2 = 0.7071067811865476f * v[1] * g[2] + -0.7071067811865476f * v[2] * g[1];
-      const float w = th[5] * 0.4472135954999579f;
+      const float w = th[5 * TS];
       vo[5] += w * t0;
       vo[6] += w * t1;
       vo[7] += w * t2;
@@ -1317,7 +1537,7 @@ template <> struct TP<2, 1, 0> {
       const float t2 = 0.4082482904638631f * v[1] * g[1] + -0.8164965809277261f * v[2] * g[2] + 0.4082482904638631f * v[3] * g[3];
       const float t3 = -0.7071067811865476f * v[2] * g[3] + -0.7071067811865476f * v[3] * g[2];
       const float t4 = 0.7071067811865475f * v[1] * g[1] + -0.7071067811865475f * v[3] * g[3];
-      const float w = th[6] * 0.4082482904638631f;
+      const float w = th[6 * TS];
       vo[8] += w * t0;
       vo[9] += w * t1;
       vo[10] += w * t2;
@@ -1328,7 +1548,7 @@ template <> struct TP<2, 1, 0> {
       const float t0 = -0.3162277660168379f * v[1] * g[6] + -0.547722557505166f * v[1] * g[8] + 0.547722557505166f * v[2] * g[5] + 0.547722557505166f * v[3] * g[4];
       const float t1 = 0.547722557505166f * v[1] * g[5] + 0.632455532033676f * v[2] * g[6] + 0.547722557505166f * v[3] * g[7];
       const float t2 = 0.547722557505166f * v[1] * g[4] + 0.547722557505166f * v[2] * g[7] + -0.3162277660168379f * v[3] * g[6] + 0.547722557505166f * v[3] * g[8];
-      const float w = th[7] * 0.4082482904638631f;
+      const float w = th[7 * TS];
       vo[2] += w * t0;
       vo[3] += w * t1;
       vo[4] += w * t2;
@@ -1339,7 +1559,7 @@ template <> struct TP<2, 1, 0> {
       const float t2 = 0.7071067811865477f * v[1] * g[7] + -0.7071067811865477f * v[3] * g[5];
       const float t3 = -0.7071067811865477f * v[1] * g[6] + 0.408248290463863f * v[1] * g[8] + 0.408248290463863f * v[2] * g[5] + -0.408248290463863f * v[3] * g[4];
       const float t4 = -0.408248290463863f * v[1] * g[7] + 0.816496580927726f * v[2] * g[4] + -0.408248290463863f * v[3] * g[5];
-      const float w = th[8] * 0.4472135954999579f;
+      const float w = th[8 * TS];
       vo[13] += w * t0;
       vo[14] += w * t1;
       vo[15] += w * t2;
@@ -1350,21 +1570,21 @@ template <> struct TP<2, 1, 0> {
       const float t0 = 0.9999999999999999f * v[4] * g[0];
       const float t1 = 1.0000000000000002f * v[5] * g[0];
       const float t2 = 0.9999999999999999f * v[6] * g[0];
-      const float w = th[9] * 0.4472135954999579f;
+      const float w = th[9 * TS];
       vo[5] += w * t0;
       vo[6] += w * t1;
       vo[7] += w * t2;
     }
     { // path 10: (1, 1) x (1,-1) -> (0, -1)
       const float t0 = 0.5773502691896257f * v[4] * g[1] + 0.5773502691896258f * v[5] * g[2] + 0.5773502691896257f * v[6] * g[3];
-      const float w = th[10] * 0.7071067811865475f;
+      const float w = th[10 * TS];
       vo[1] += w * t0;
     }
     { // path 11: (1, 1) x (1,-1) -> (1, -1)
       const float t0 = 0.7071067811865476f * v[5] * g[3] + -0.7071067811865476f * v[6] * g[2];
       const float t1 = -0.7071067811865476f * v[4] * g[3] + 0.7071067811865476f * v[6] * g[1];
       const float t2 = 0.7071067811865476f * v[4] * g[2] + -0.7071067811865476f * v[5] * g[1];
-      const float w = th[11] * 0.4082482904638631f;
+      const float w = th[11 * TS];
       vo[2] += w * t0;
       vo[3] += w * t1;
       vo[4] += w * t2;
@@ -1375,7 +1595,7 @@ template <> struct TP<2, 1, 0> {
       const float t2 = 0.4082482904638631f * v[4] * g[1] + -0.8164965809277261f * v[5] * g[2] + 0.4082482904638631f * v[6] * g[3];
       const float t3 = -0.7071067811865476f * v[5] * g[3] + -0.7071067811865476f * v[6] * g[2];
       const float t4 = 0.7071067811865475f * v[4] * g[1] + -0.7071067811865475f * v[6] * g[3];
-      const float w = th[12] * 0.4472135954999579f;
+      const float w = th[12 * TS];
       vo[13] += w * t0;
       vo[14] += w * t1;
       vo[15] += w * t2;
@@ -1386,7 +1606,7 @@ template <> struct TP<2, 1, 0> {
       const float t0 = -0.3162277660168379f * v[4] * g[6] + -0.547722557505166f * v[4] * g[8] + 0.547722557505166f * v[5] * g[5] + 0.547722557505166f * v[6] * g[4];
       const float t1 = 0.547722557505166f * v[4] * g[5] + 0.632455532033676f * v[5] * g[6] + 0.547722557505166f * v[6] * g[7];
       const float t2 = 0.547722557505166f * v[4] * g[4] + 0.547722557505166f * v[5] * g[7] + -0.3162277660168379f * v[6] * g[6] + 0.547722557505166f * v[6] * g[8];
-      const float w = th[13] * 0.4472135954999579f;
+      const float w = th[13 * TS];
       vo[5] += w * t0;
       vo[6] += w * t1;
       vo[7] += w * t2;
@@ -1397,7 +1617,7 @@ template <> struct TP<2, 1, 0> {
       const float t2 = 0.7071067811865477f * v[4] * g[7] + -0.7071067811865477f * v[6] * g[5];
       const float t3 = -0.7071067811865477f * v[4] * g[6] + 0.408248290463863f * v[4] * g[8] + 0.408248290463863f * v[5] * g[5] + -0.408248290463863f * v[6] * g[4];
       const float t4 = -0.408248290463863f * v[4] * g[7] + 0.816496580927726f * v[5] * g[4] + -0.408248290463863f * v[6] * g[5];
-      const float w = th[14] * 0.4082482904638631f;
+      const float w = th[14 * TS];
       vo[8] += w * t0;
       vo[9] += w * t1;
       vo[10] += w * t2;
@@ -1410,7 +1630,7 @@ template <> struct TP<2, 1, 0> {
       const float t2 = 1.0000000000000002f * v[9] * g[0];
       const float t3 = 1.0f * v[10] * g[0];
       const float t4 = 1.0f * v[11] * g[0];
-      const float w = th[15] * 0.4082482904638631f;
+      const float w = th[15 * TS];
       vo[8] += w * t0;
       vo[9] += w * t1;
       vo[10] += w * t2;
@@ -1421,7 +1641,7 @@ template <> struct TP<2, 1, 0> {
       const float t0 = 0.547722557505166f * v[7] * g[3] + 0.547722557505166f * v[8] * g[2] + -0.3162277660168379f * v[9] * g[1] + -0.547722557505166f * v[11] * g[1];
       const float t1 = 0.547722557505166f * v[8] * g[1] + 0.632455532033676f * v[9] * g[2] + 0.547722557505166f * v[10] * g[3];
       const float t2 = 0.547722557505166f * v[7] * g[1] + -0.3162277660168379f * v[9] * g[3] + 0.547722557505166f * v[10] * g[2] + 0.547722557505166f * v[11] * g[3];
-      const float w = th[16] * 0.4082482904638631f;
+      const float w = th[16 * TS];
       vo[2] += w * t0;
       vo[3] += w * t1;
       vo[4] += w * t2;
@@ -1432,7 +1652,7 @@ template <> struct TP<2, 1, 0> {
       const float t2 = -0.7071067811865477f * v[8] * g[3] + 0.7071067811865477f * v[10] * g[1];
       const float t3 = -0.408248290463863f * v[7] * g[3] + 0.408248290463863f * v[8] * g[2] + -0.7071067811865477f * v[9] * g[1] + 0.408248290463863f * v[11] * g[1];
       const float t4 = 0.816496580927726f * v[7] * g[2] + -0.408248290463863f * v[8] * g[3] + -0.408248290463863f * v[10] * g[1];
-      const float w = th[17] * 0.4472135954999579f;
+      const float w = th[17 * TS];
       vo[13] += w * t0;
       vo[14] += w * t1;
       vo[15] += w * t2;
@@ -1442,14 +1662,14 @@ template <> struct TP<2, 1, 0> {
     { // path 18: (2, 1) x (2,1) -> (0, 1)
       const float t0 = 0.4472135954999579f * v[7] * g[4] + 0.4472135954999579f * v[8] * g[5] + 0.44721359549995804f * v[9] * g[6] + 0.4472135954999579f * v[10] * g[7] + 0.4472135954999579f * v[11] * g[8];
       s[2] = t0;
-      const float w = th[18] * 0.5773502691896258f;
+      const float w = th[18 * TS];
       vo[0] += w * t0;
     }
     { // path 19: (2, 1) x (2,1) -> (1, 1)
       const float t0 = 0.3162277660168379f * v[7] * g[5] + -0.3162277660168379f * v[8] * g[4] + -0.5477225575051661f * v[9] * g[7] + 0.5477225575051661f * v[10] * g[6] + -0.3162277660168379f * v[10] * g[8] + 0.3162277660168379f * v[11] * g[7];
       const float t1 = 0.6324555320336758f * v[7] * g[8] + 0.3162277660168379f * v[8] * g[7] + -0.3162277660168379f * v[10] * g[5] + -0.6324555320336758f * v[11] * g[4];
       const float t2 = -0.3162277660168379f * v[7] * g[7] + -0.5477225575051661f * v[8] * g[6] + -0.3162277660168379f * v[8] * g[8] + 0.5477225575051661f * v[9] * g[5] + 0.3162277660168379f * v[10] * g[4] + 0.3162277660168379f * v[11] * g[5];
-      const float w = th[19] * 0.4472135954999579f;
+      const float w = th[19 * TS];
       vo[5] += w * t0;
       vo[6] += w * t1;
       vo[7] += w * t2;
@@ -1460,7 +1680,7 @@ template <> struct TP<2, 1, 0> {
       const float t2 = 0.5345224838248488f * v[7] * g[4] + -0.2672612419124244f * v[8] * g[5] + -0.5345224838248489f * v[9] * g[6] + -0.2672612419124244f * v[10] * g[7] + 0.5345224838248488f * v[11] * g[8];
       const float t3 = -0.4629100498862757f * v[7] * g[5] + -0.4629100498862757f * v[8] * g[4] + -0.2672612419124244f * v[9] * g[7] + -0.2672612419124244f * v[10] * g[6] + -0.4629100498862757f * v[10] * g[8] + -0.4629100498862757f * v[11] * g[7];
       const float t4 = 0.4629100498862757f * v[8] * g[5] + 0.5345224838248488f * v[9] * g[8] + -0.4629100498862757f * v[10] * g[7] + 0.5345224838248488f * v[11] * g[6];
-      const float w = th[20] * 0.4082482904638631f;
+      const float w = th[20 * TS];
       vo[8] += w * t0;
       vo[9] += w * t1;
       vo[10] += w * t2;
@@ -1473,7 +1693,7 @@ template <> struct TP<2, 1, 0> {
       const float t2 = 1.0000000000000002f * v[14] * g[0];
       const float t3 = 1.0f * v[15] * g[0];
       const float t4 = 1.0f * v[16] * g[0];
-      const float w = th[21] * 0.4472135954999579f;
+      const float w = th[21 * TS];
       vo[13] += w * t0;
       vo[14] += w * t1;
       vo[15] += w * t2;
@@ -1484,7 +1704,7 @@ template <> struct TP<2, 1, 0> {
       const float t0 = 0.547722557505166f * v[12] * g[3] + 0.547722557505166f * v[13] * g[2] + -0.3162277660168379f * v[14] * g[1] + -0.547722557505166f * v[16] * g[1];
       const float t1 = 0.547722557505166f * v[13] * g[1] + 0.632455532033676f * v[14] * g[2] + 0.547722557505166f * v[15] * g[3];
       const float t2 = 0.547722557505166f * v[12] * g[1] + -0.3162277660168379f * v[14] * g[3] + 0.547722557505166f * v[15] * g[2] + 0.547722557505166f * v[16] * g[3];
-      const float w = th[22] * 0.4472135954999579f;
+      const float w = th[22 * TS];
       vo[5] += w * t0;
       vo[6] += w * t1;
       vo[7] += w * t2;
@@ -1495,7 +1715,7 @@ template <> struct TP<2, 1, 0> {
       const float t2 = -0.7071067811865477f * v[13] * g[3] + 0.7071067811865477f * v[15] * g[1];
       const float t3 = -0.408248290463863f * v[12] * g[3] + 0.408248290463863f * v[13] * g[2] + -0.7071067811865477f * v[14] * g[1] + 0.408248290463863f * v[16] * g[1];
       const float t4 = 0.816496580927726f * v[12] * g[2] + -0.408248290463863f * v[13] * g[3] + -0.408248290463863f * v[15] * g[1];
-      const float w = th[23] * 0.4082482904638631f;
+      const float w = th[23 * TS];
       vo[8] += w * t0;
       vo[9] += w * t1;
       vo[10] += w * t2;
@@ -1504,14 +1724,14 @@ template <> struct TP<2, 1, 0> {
     }
     { // path 24: (2, -1) x (2,1) -> (0, -1)
       const float t0 = 0.4472135954999579f * v[12] * g[4] + 0.4472135954999579f * v[13] * g[5] + 0.44721359549995804f * v[14] * g[6] + 0.4472135954999579f * v[15] * g[7] + 0.4472135954999579f * v[16] * g[8];
-      const float w = th[24] * 0.7071067811865475f;
+      const float w = th[24 * TS];
       vo[1] += w * t0;
     }
     { // path 25: (2, -1) x (2,1) -> (1, -1)
       const float t0 = 0.3162277660168379f * v[12] * g[5] + -0.3162277660168379f * v[13] * g[4] + -0.5477225575051661f * v[14] * g[7] + 0.5477225575051661f * v[15] * g[6] + -0.3162277660168379f * v[15] * g[8] + 0.3162277660168379f * v[16] * g[7];
       const float t1 = 0.6324555320336758f * v[12] * g[8] + 0.3162277660168379f * v[13] * g[7] + -0.3162277660168379f * v[15] * g[5] + -0.6324555320336758f * v[16] * g[4];
       const float t2 = -0.3162277660168379f * v[12] * g[7] + -0.5477225575051661f * v[13] * g[6] + -0.3162277660168379f * v[13] * g[8] + 0.5477225575051661f * v[14] * g[5] + 0.3162277660168379f * v[15] * g[4] + 0.3162277660168379f * v[16] * g[5];
-      const float w = th[25] * 0.4082482904638631f;
+      const float w = th[25 * TS];
       vo[2] += w * t0;
       vo[3] += w * t1;
       vo[4] += w * t2;
@@ -1522,7 +1742,7 @@ template <> struct TP<2, 1, 0> {
       const float t2 = 0.5345224838248488f * v[12] * g[4] + -0.2672612419124244f * v[13] * g[5] + -0.5345224838248489f * v[14] * g[6] + -0.2672612419124244f * v[15] * g[7] + 0.5345224838248488f * v[16] * g[8];
       const float t3 = -0.4629100498862757f * v[12] * g[5] + -0.4629100498862757f * v[13] * g[4] + -0.2672612419124244f * v[14] * g[7] + -0.2672612419124244f * v[15] * g[6] + -0.4629100498862757f * v[15] * g[8] + -0.4629100498862757f * v[16] * g[7];
       const float t4 = 0.4629100498862757f * v[13] * g[5] + 0.5345224838248488f * v[14] * g[8] + -0.4629100498862757f * v[15] * g[7] + 0.5345224838248488f * v[16] * g[6];
-      const float w = th[26] * 0.4472135954999579f;
+      const float w = th[26 * TS];
       vo[13] += w * t0;
       vo[14] += w * t1;
       vo[15] += w * t2;
@@ -1530,445 +1750,585 @@ template <> struct TP<2, 1, 0> {
       vo[17] += w * t4;
     }
   }
+  template <int TS>
   static __device__ __forceinline__ void bwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, const float* __restrict__ gs, const float* __restrict__ gvo, float* gv, float* gg) {
     { // path 0
-      const float w = th[0] * 0.5773502691896258f;
+      const float w = th[0 * TS];
       const float gt0 = gs[0] + w * gvo[0];
-      gv[0] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[0];
+      const float s0_0 = gt0;
+      gv[0] = fmaf(s0_0, g[0], gv[0]); gg[0] = fmaf(s0_0, v[0], gg[0]);
     }
     { // path 1
-      const float w = th[1] * 0.4082482904638631f;
+      const float w = th[1 * TS];
       const float gt0 = w * gvo[2];
       const float gt1 = w * gvo[3];
       const float gt2 = w * gvo[4];
-      gv[0] += 0.9999999999999999f * gt0 * g[1]; gg[1] += 0.9999999999999999f * gt0 * v[0];
-      gv[0] += 1.0000000000000002f * gt1 * g[2]; gg[2] += 1.0000000000000002f * gt1 * v[0];
-      gv[0] += 0.9999999999999999f * gt2 * g[3]; gg[3] += 0.9999999999999999f * gt2 * v[0];
+      const float s0_0 = gt0;
+      gv[0] = fmaf(s0_0, g[1], gv[0]); gg[1] = fmaf(s0_0, v[0], gg[1]);
+      const float s1_0 = gt1;
+      gv[0] = fmaf(s1_0, g[2], gv[0]); gg[2] = fmaf(s1_0, v[0], gg[2]);
+      const float s2_0 = gt2;
+      gv[0] = fmaf(s2_0, g[3], gv[0]); gg[3] = fmaf(s2_0, v[0], gg[3]);
     }
     { // path 2
-      const float w = th[2] * 0.4082482904638631f;
+      const float w = th[2 * TS];
       const float gt0 = w * gvo[8];
       const float gt1 = w * gvo[9];
       const float gt2 = w * gvo[10];
       const float gt3 = w * gvo[11];
       const float gt4 = w * gvo[12];
-      gv[0] += 1.0f * gt0 * g[4]; gg[4] += 1.0f * gt0 * v[0];
-      gv[0] += 1.0f * gt1 * g[5]; gg[5] += 1.0f * gt1 * v[0];
-      gv[0] += 1.0000000000000002f * gt2 * g[6]; gg[6] += 1.0000000000000002f * gt2 * v[0];
-      gv[0] += 1.0f * gt3 * g[7]; gg[7] += 1.0f * gt3 * v[0];
-      gv[0] += 1.0f * gt4 * g[8]; gg[8] += 1.0f * gt4 * v[0];
+      const float s0_0 = gt0;
+      gv[0] = fmaf(s0_0, g[4], gv[0]); gg[4] = fmaf(s0_0, v[0], gg[4]);
+      const float s1_0 = gt1;
+      gv[0] = fmaf(s1_0, g[5], gv[0]); gg[5] = fmaf(s1_0, v[0], gg[5]);
+      const float s2_0 = gt2;
+      gv[0] = fmaf(s2_0, g[6], gv[0]); gg[6] = fmaf(s2_0, v[0], gg[6]);
+      const float s3_0 = gt3;
+      gv[0] = fmaf(s3_0, g[7], gv[0]); gg[7] = fmaf(s3_0, v[0], gg[7]);
+      const float s4_0 = gt4;
+      gv[0] = fmaf(s4_0, g[8], gv[0]); gg[8] = fmaf(s4_0, v[0], gg[8]);
     }
     { // path 3
-      const float w = th[3] * 0.4082482904638631f;
+      const float w = th[3 * TS];
       const float gt0 = w * gvo[2];
       const float gt1 = w * gvo[3];
       const float gt2 = w * gvo[4];
-      gv[1] += 0.9999999999999999f * gt0 * g[0]; gg[0] += 0.9999999999999999f * gt0 * v[1];
-      gv[2] += 1.0000000000000002f * gt1 * g[0]; gg[0] += 1.0000000000000002f * gt1 * v[2];
-      gv[3] += 0.9999999999999999f * gt2 * g[0]; gg[0] += 0.9999999999999999f * gt2 * v[3];
+      const float s0_0 = gt0;
+      gv[1] = fmaf(s0_0, g[0], gv[1]); gg[0] = fmaf(s0_0, v[1], gg[0]);
+      const float s1_0 = gt1;
+      gv[2] = fmaf(s1_0, g[0], gv[2]); gg[0] = fmaf(s1_0, v[2], gg[0]);
+      const float s2_0 = gt2;
+      gv[3] = fmaf(s2_0, g[0], gv[3]); gg[0] = fmaf(s2_0, v[3], gg[0]);
     }
     { // path 4
-      const float w = th[4] * 0.5773502691896258f;
+      const float w = th[4 * TS];
       const float gt0 = gs[1] + w * gvo[0];
-      gv[1] += 0.5773502691896257f * gt0 * g[1]; gg[1] += 0.5773502691896257f * gt0 * v[1];
-      gv[2] += 0.5773502691896258f * gt0 * g[2]; gg[2] += 0.5773502691896258f * gt0 * v[2];
-      gv[3] += 0.5773502691896257f * gt0 * g[3]; gg[3] += 0.5773502691896257f * gt0 * v[3];
+      const float s0_0 = 0.5773502691896257f * gt0;
+      gv[1] = fmaf(s0_0, g[1], gv[1]); gg[1] = fmaf(s0_0, v[1], gg[1]);
+      gv[2] = fmaf(s0_0, g[2], gv[2]); gg[2] = fmaf(s0_0, v[2], gg[2]);
+      gv[3] = fmaf(s0_0, g[3], gv[3]); gg[3] = fmaf(s0_0, v[3], gg[3]);
     }
     { // path 5
-      const float w = th[5] * 0.4472135954999579f;
+      const float w = th[5 * TS];
       const float gt0 = w * gvo[5];
       const float gt1 = w * gvo[6];
       const float gt2 = w * gvo[7];
-      gv[1] += 0.7071067811865476f * gt2 * g[2]; gg[2] += 0.7071067811865476f * gt2 * v[1];
-      gv[1] += -0.7071067811865476f * gt1 * g[3]; gg[3] += -0.7071067811865476f * gt1 * v[1];
-      gv[2] += -0.7071067811865476f * gt2 * g[1]; gg[1] += -0.7071067811865476f * gt2 * v[2];
-      gv[2] += 0.7071067811865476f * gt0 * g[3]; gg[3] += 0.7071067811865476f * gt0 * v[2];
-      gv[3] += 0.7071067811865476f * gt1 * g[1]; gg[1] += 0.7071067811865476f * gt1 * v[3];
-      gv[3] += -0.7071067811865476f * gt0 * g[2]; gg[2] += -0.7071067811865476f * gt0 * v[3];
+      const float s2_0 = 0.7071067811865476f * gt2;
+      gv[1] = fmaf(s2_0, g[2], gv[1]); gg[2] = fmaf(s2_0, v[1], gg[2]);
+      const float s1_0 = 0.7071067811865476f * gt1;
+      gv[1] = fmaf(-s1_0, g[3], gv[1]); gg[3] = fmaf(-s1_0, v[1], gg[3]);
+      gv[2] = fmaf(-s2_0, g[1], gv[2]); gg[1] = fmaf(-s2_0, v[2], gg[1]);
+      const float s0_0 = 0.7071067811865476f * gt0;
+      gv[2] = fmaf(s0_0, g[3], gv[2]); gg[3] = fmaf(s0_0, v[2], gg[3]);
+      gv[3] = fmaf(s1_0, g[1], gv[3]); gg[1] = fmaf(s1_0, v[3], gg[1]);
+      gv[3] = fmaf(-s0_0, g[2], gv[3]); gg[2] = fmaf(-s0_0, v[3], gg[2]);
     }
     { // path 6
-      const float w = th[6] * 0.4082482904638631f;
+      const float w = th[6 * TS];
       const float gt0 = w * gvo[8];
       const float gt1 = w * gvo[9];
       const float gt2 = w * gvo[10];
       const float gt3 = w * gvo[11];
       const float gt4 = w * gvo[12];
-      gv[1] += 0.4082482904638631f * gt2 * g[1]; gg[1] += 0.4082482904638631f * gt2 * v[1];
-      gv[1] += 0.7071067811865475f * gt4 * g[1]; gg[1] += 0.7071067811865475f * gt4 * v[1];
-      gv[1] += -0.7071067811865476f * gt1 * g[2]; gg[2] += -0.7071067811865476f * gt1 * v[1];
-      gv[1] += -0.7071067811865475f * gt0 * g[3]; gg[3] += -0.7071067811865475f * gt0 * v[1];
-      gv[2] += -0.7071067811865476f * gt1 * g[1]; gg[1] += -0.7071067811865476f * gt1 * v[2];
-      gv[2] += -0.8164965809277261f * gt2 * g[2]; gg[2] += -0.8164965809277261f * gt2 * v[2];
-      gv[2] += -0.7071067811865476f * gt3 * g[3]; gg[3] += -0.7071067811865476f * gt3 * v[2];
-      gv[3] += -0.7071067811865475f * gt0 * g[1]; gg[1] += -0.7071067811865475f * gt0 * v[3];
-      gv[3] += -0.7071067811865476f * gt3 * g[2]; gg[2] += -0.7071067811865476f * gt3 * v[3];
-      gv[3] += 0.4082482904638631f * gt2 * g[3]; gg[3] += 0.4082482904638631f * gt2 * v[3];
-      gv[3] += -0.7071067811865475f * gt4 * g[3]; gg[3] += -0.7071067811865475f * gt4 * v[3];
+      const float s2_0 = 0.4082482904638631f * gt2;
+      gv[1] = fmaf(s2_0, g[1], gv[1]); gg[1] = fmaf(s2_0, v[1], gg[1]);
+      const float s4_0 = 0.7071067811865475f * gt4;
+      gv[1] = fmaf(s4_0, g[1], gv[1]); gg[1] = fmaf(s4_0, v[1], gg[1]);
+      const float s1_0 = 0.7071067811865476f * gt1;
+      gv[1] = fmaf(-s1_0, g[2], gv[1]); gg[2] = fmaf(-s1_0, v[1], gg[2]);
+      const float s0_0 = 0.7071067811865475f * gt0;
+      gv[1] = fmaf(-s0_0, g[3], gv[1]); gg[3] = fmaf(-s0_0, v[1], gg[3]);
+      gv[2] = fmaf(-s1_0, g[1], gv[2]); gg[1] = fmaf(-s1_0, v[2], gg[1]);
+      const float s2_1 = 0.8164965809277261f * gt2;
+      gv[2] = fmaf(-s2_1, g[2], gv[2]); gg[2] = fmaf(-s2_1, v[2], gg[2]);
+      const float s3_0 = 0.7071067811865476f * gt3;
+      gv[2] = fmaf(-s3_0, g[3], gv[2]); gg[3] = fmaf(-s3_0, v[2], gg[3]);
+      gv[3] = fmaf(-s0_0, g[1], gv[3]); gg[1] = fmaf(-s0_0, v[3], gg[1]);
+      gv[3] = fmaf(-s3_0, g[2], gv[3]); gg[2] = fmaf(-s3_0, v[3], gg[2]);
+      gv[3] = fmaf(s2_0, g[3], gv[3]); gg[3] = fmaf(s2_0, v[3], gg[3]);
+      gv[3] = fmaf(-s4_0, g[3], gv[3]); gg[3] = fmaf(-s4_0, v[3], gg[3]);
     }
     { // path 7
-      const float w = th[7] * 0.4082482904638631f;
+      const float w = th[7 * TS];
       const float gt0 = w * gvo[2];
       const float gt1 = w * gvo[3];
       const float gt2 = w * gvo[4];
-      gv[1] += 0.547722557505166f * gt2 * g[4]; gg[4] += 0.547722557505166f * gt2 * v[1];
-      gv[1] += 0.547722557505166f * gt1 * g[5]; gg[5] += 0.547722557505166f * gt1 * v[1];
-      gv[1] += -0.3162277660168379f * gt0 * g[6]; gg[6] += -0.3162277660168379f * gt0 * v[1];
-      gv[1] += -0.547722557505166f * gt0 * g[8]; gg[8] += -0.547722557505166f * gt0 * v[1];
-      gv[2] += 0.547722557505166f * gt0 * g[5]; gg[5] += 0.547722557505166f * gt0 * v[2];
-      gv[2] += 0.632455532033676f * gt1 * g[6]; gg[6] += 0.632455532033676f * gt1 * v[2];
-      gv[2] += 0.547722557505166f * gt2 * g[7]; gg[7] += 0.547722557505166f * gt2 * v[2];
-      gv[3] += 0.547722557505166f * gt0 * g[4]; gg[4] += 0.547722557505166f * gt0 * v[3];
-      gv[3] += -0.3162277660168379f * gt2 * g[6]; gg[6] += -0.3162277660168379f * gt2 * v[3];
-      gv[3] += 0.547722557505166f * gt1 * g[7]; gg[7] += 0.547722557505166f * gt1 * v[3];
-      gv[3] += 0.547722557505166f * gt2 * g[8]; gg[8] += 0.547722557505166f * gt2 * v[3];
+      const float s2_0 = 0.547722557505166f * gt2;
+      gv[1] = fmaf(s2_0, g[4], gv[1]); gg[4] = fmaf(s2_0, v[1], gg[4]);
+      const float s1_0 = 0.547722557505166f * gt1;
+      gv[1] = fmaf(s1_0, g[5], gv[1]); gg[5] = fmaf(s1_0, v[1], gg[5]);
+      const float s0_0 = 0.3162277660168379f * gt0;
+      gv[1] = fmaf(-s0_0, g[6], gv[1]); gg[6] = fmaf(-s0_0, v[1], gg[6]);
+      const float s0_1 = 0.547722557505166f * gt0;
+      gv[1] = fmaf(-s0_1, g[8], gv[1]); gg[8] = fmaf(-s0_1, v[1], gg[8]);
+      gv[2] = fmaf(s0_1, g[5], gv[2]); gg[5] = fmaf(s0_1, v[2], gg[5]);
+      const float s1_1 = 0.632455532033676f * gt1;
+      gv[2] = fmaf(s1_1, g[6], gv[2]); gg[6] = fmaf(s1_1, v[2], gg[6]);
+      gv[2] = fmaf(s2_0, g[7], gv[2]); gg[7] = fmaf(s2_0, v[2], gg[7]);
+      gv[3] = fmaf(s0_1, g[4], gv[3]); gg[4] = fmaf(s0_1, v[3], gg[4]);
+      const float s2_1 = 0.3162277660168379f * gt2;
+      gv[3] = fmaf(-s2_1, g[6], gv[3]); gg[6] = fmaf(-s2_1, v[3], gg[6]);
+      gv[3] = fmaf(s1_0, g[7], gv[3]); gg[7] = fmaf(s1_0, v[3], gg[7]);
+      gv[3] = fmaf(s2_0, g[8], gv[3]); gg[8] = fmaf(s2_0, v[3], gg[8]);
     }
     { // path 8
-      const float w = th[8] * 0.4472135954999579f;
+      const float w = th[8 * TS];
       const float gt0 = w * gvo[13];
       const float gt1 = w * gvo[14];
       const float gt2 = w * gvo[15];
       const float gt3 = w * gvo[16];
       const float gt4 = w * gvo[17];
-      gv[1] += 0.408248290463863f * gt1 * g[4]; gg[4] += 0.408248290463863f * gt1 * v[1];
-      gv[1] += -0.408248290463863f * gt0 * g[5]; gg[5] += -0.408248290463863f * gt0 * v[1];
-      gv[1] += -0.7071067811865477f * gt3 * g[6]; gg[6] += -0.7071067811865477f * gt3 * v[1];
-      gv[1] += 0.7071067811865477f * gt2 * g[7]; gg[7] += 0.7071067811865477f * gt2 * v[1];
-      gv[1] += -0.408248290463863f * gt4 * g[7]; gg[7] += -0.408248290463863f * gt4 * v[1];
-      gv[1] += 0.408248290463863f * gt3 * g[8]; gg[8] += 0.408248290463863f * gt3 * v[1];
-      gv[2] += 0.816496580927726f * gt4 * g[4]; gg[4] += 0.816496580927726f * gt4 * v[2];
-      gv[2] += 0.408248290463863f * gt3 * g[5]; gg[5] += 0.408248290463863f * gt3 * v[2];
-      gv[2] += -0.408248290463863f * gt1 * g[7]; gg[7] += -0.408248290463863f * gt1 * v[2];
-      gv[2] += -0.816496580927726f * gt0 * g[8]; gg[8] += -0.816496580927726f * gt0 * v[2];
-      gv[3] += -0.408248290463863f * gt3 * g[4]; gg[4] += -0.408248290463863f * gt3 * v[3];
-      gv[3] += -0.7071067811865477f * gt2 * g[5]; gg[5] += -0.7071067811865477f * gt2 * v[3];
-      gv[3] += -0.408248290463863f * gt4 * g[5]; gg[5] += -0.408248290463863f * gt4 * v[3];
-      gv[3] += 0.7071067811865477f * gt1 * g[6]; gg[6] += 0.7071067811865477f * gt1 * v[3];
-      gv[3] += 0.408248290463863f * gt0 * g[7]; gg[7] += 0.408248290463863f * gt0 * v[3];
-      gv[3] += 0.408248290463863f * gt1 * g[8]; gg[8] += 0.408248290463863f * gt1 * v[3];
+      const float s1_0 = 0.408248290463863f * gt1;
+      gv[1] = fmaf(s1_0, g[4], gv[1]); gg[4] = fmaf(s1_0, v[1], gg[4]);
+      const float s0_0 = 0.408248290463863f * gt0;
+      gv[1] = fmaf(-s0_0, g[5], gv[1]); gg[5] = fmaf(-s0_0, v[1], gg[5]);
+      const float s3_0 = 0.7071067811865477f * gt3;
+      gv[1] = fmaf(-s3_0, g[6], gv[1]); gg[6] = fmaf(-s3_0, v[1], gg[6]);
+      const float s2_0 = 0.7071067811865477f * gt2;
+      gv[1] = fmaf(s2_0, g[7], gv[1]); gg[7] = fmaf(s2_0, v[1], gg[7]);
+      const float s4_0 = 0.408248290463863f * gt4;
+      gv[1] = fmaf(-s4_0, g[7], gv[1]); gg[7] = fmaf(-s4_0, v[1], gg[7]);
+      const float s3_1 = 0.408248290463863f * gt3;
+      gv[1] = fmaf(s3_1, g[8], gv[1]); gg[8] = fmaf(s3_1, v[1], gg[8]);
+      const float s4_1 = 0.816496580927726f * gt4;
+      gv[2] = fmaf(s4_1, g[4], gv[2]); gg[4] = fmaf(s4_1, v[2], gg[4]);
+      gv[2] = fmaf(s3_1, g[5], gv[2]); gg[5] = fmaf(s3_1, v[2], gg[5]);
+      gv[2] = fmaf(-s1_0, g[7], gv[2]); gg[7] = fmaf(-s1_0, v[2], gg[7]);
+      const float s0_1 = 0.816496580927726f * gt0;
+      gv[2] = fmaf(-s0_1, g[8], gv[2]); gg[8] = fmaf(-s0_1, v[2], gg[8]);
+      gv[3] = fmaf(-s3_1, g[4], gv[3]); gg[4] = fmaf(-s3_1, v[3], gg[4]);
+      gv[3] = fmaf(-s2_0, g[5], gv[3]); gg[5] = fmaf(-s2_0, v[3], gg[5]);
+      gv[3] = fmaf(-s4_0, g[5], gv[3]); gg[5] = fmaf(-s4_0, v[3], gg[5]);
+      const float s1_1 = 0.7071067811865477f * gt1;
+      gv[3] = fmaf(s1_1, g[6], gv[3]); gg[6] = fmaf(s1_1, v[3], gg[6]);
+      gv[3] = fmaf(s0_0, g[7], gv[3]); gg[7] = fmaf(s0_0, v[3], gg[7]);
+      gv[3] = fmaf(s1_0, g[8], gv[3]); gg[8] = fmaf(s1_0, v[3], gg[8]);
     }
     { // path 9
-      const float w = th[9] * 0.4472135954999579f;
+      const float w = th[9 * TS];
       const float gt0 = w * gvo[5];
       const float gt1 = w * gvo[6];
       const float gt2 = w * gvo[7];
-      gv[4] += 0.9999999999999999f * gt0 * g[0]; gg[0] += 0.9999999999999999f * gt0 * v[4];
-      gv[5] += 1.0000000000000002f * gt1 * g[0]; gg[0] += 1.0000000000000002f * gt1 * v[5];
-      gv[6] += 0.9999999999999999f * gt2 * g[0]; gg[0] += 0.9999999999999999f * gt2 * v[6];
+      const float s0_0 = gt0;
+      gv[4] = fmaf(s0_0, g[0], gv[4]); gg[0] = fmaf(s0_0, v[4], gg[0]);
+      const float s1_0 = gt1;
+      gv[5] = fmaf(s1_0, g[0], gv[5]); gg[0] = fmaf(s1_0, v[5], gg[0]);
+      const float s2_0 = gt2;
+      gv[6] = fmaf(s2_0, g[0], gv[6]); gg[0] = fmaf(s2_0, v[6], gg[0]);
     }
     { // path 10
-      const float w = th[10] * 0.7071067811865475f;
+      const float w = th[10 * TS];
       const float gt0 = w * gvo[1];
-      gv[4] += 0.5773502691896257f * gt0 * g[1]; gg[1] += 0.5773502691896257f * gt0 * v[4];
-      gv[5] += 0.5773502691896258f * gt0 * g[2]; gg[2] += 0.5773502691896258f * gt0 * v[5];
-      gv[6] += 0.5773502691896257f * gt0 * g[3]; gg[3] += 0.5773502691896257f * gt0 * v[6];
+      const float s0_0 = 0.5773502691896257f * gt0;
+      gv[4] = fmaf(s0_0, g[1], gv[4]); gg[1] = fmaf(s0_0, v[4], gg[1]);
+      gv[5] = fmaf(s0_0, g[2], gv[5]); gg[2] = fmaf(s0_0, v[5], gg[2]);
+      gv[6] = fmaf(s0_0, g[3], gv[6]); gg[3] = fmaf(s0_0, v[6], gg[3]);
     }
     { // path 11
-      const float w = th[11] * 0.4082482904638631f;
+      const float w = th[11 * TS];
       const float gt0 = w * gvo[2];
       const float gt1 = w * gvo[3];
       const float gt2 = w * gvo[4];
-      gv[4] += 0.7071067811865476f * gt2 * g[2]; gg[2] += 0.7071067811865476f * gt2 * v[4];
-      gv[4] += -0.7071067811865476f * gt1 * g[3]; gg[3] += -0.7071067811865476f * gt1 * v[4];
-      gv[5] += -0.7071067811865476f * gt2 * g[1]; gg[1] += -0.7071067811865476f * gt2 * v[5];
-      gv[5] += 0.7071067811865476f * gt0 * g[3]; gg[3] += 0.7071067811865476f * gt0 * v[5];
-      gv[6] += 0.7071067811865476f * gt1 * g[1]; gg[1] += 0.7071067811865476f * gt1 * v[6];
-      gv[6] += -0.7071067811865476f * gt0 * g[2]; gg[2] += -0.7071067811865476f * gt0 * v[6];
+      const float s2_0 = 0.7071067811865476f * gt2;
+      gv[4] = fmaf(s2_0, g[2], gv[4]); gg[2] = fmaf(s2_0, v[4], gg[2]);
+      const float s1_0 = 0.7071067811865476f * gt1;
+      gv[4] = fmaf(-s1_0, g[3], gv[4]); gg[3] = fmaf(-s1_0, v[4], gg[3]);
+      gv[5] = fmaf(-s2_0, g[1], gv[5]); gg[1] = fmaf(-s2_0, v[5], gg[1]);
+      const float s0_0 = 0.7071067811865476f * gt0;
+      gv[5] = fmaf(s0_0, g[3], gv[5]); gg[3] = fmaf(s0_0, v[5], gg[3]);
+      gv[6] = fmaf(s1_0, g[1], gv[6]); gg[1] = fmaf(s1_0, v[6], gg[1]);
+      gv[6] = fmaf(-s0_0, g[2], gv[6]); gg[2] = fmaf(-s0_0, v[6], gg[2]);
     }
     { // path 12
-      const float w = th[12] * 0.4472135954999579f;
+      const float w = th[12 * TS];
       const float gt0 = w * gvo[13];
       const float gt1 = w * gvo[14];
       const float gt2 = w * gvo[15];
       const float gt3 = w * gvo[16];
       const float gt4 = w * gvo[17];
-      gv[4] += 0.4082482904638631f * gt2 * g[1]; gg[1] += 0.4082482904638631f * gt2 * v[4];
-      gv[4] += 0.7071067811865475f * gt4 * g[1]; gg[1] += 0.7071067811865475f * gt4 * v[4];
-      gv[4] += -0.7071067811865476f * gt1 * g[2]; gg[2] += -0.7071067811865476f * gt1 * v[4];
-      gv[4] += -0.7071067811865475f * gt0 * g[3]; gg[3] += -0.7071067811865475f * gt0 * v[4];
-      gv[5] += -0.7071067811865476f * gt1 * g[1]; gg[1] += -0.7071067811865476f * gt1 * v[5];
-      gv[5] += -0.8164965809277261f * gt2 * g[2]; gg[2] += -0.8164965809277261f * gt2 * v[5];
-      gv[5] += -0.7071067811865476f * gt3 * g[3]; gg[3] += -0.7071067811865476f * gt3 * v[5];
-      gv[6] += -0.7071067811865475f * gt0 * g[1]; gg[1] += -0.7071067811865475f * gt0 * v[6];
-      gv[6] += -0.7071067811865476f * gt3 * g[2]; gg[2] += -0.7071067811865476f * gt3 * v[6];
-      gv[6] += 0.4082482904638631f * gt2 * g[3]; gg[3] += 0.4082482904638631f * gt2 * v[6];
-      gv[6] += -0.7071067811865475f * gt4 * g[3]; gg[3] += -0.7071067811865475f * gt4 * v[6];
+      const float s2_0 = 0.4082482904638631f * gt2;
+      gv[4] = fmaf(s2_0, g[1], gv[4]); gg[1] = fmaf(s2_0, v[4], gg[1]);
+      const float s4_0 = 0.7071067811865475f * gt4;
+      gv[4] = fmaf(s4_0, g[1], gv[4]); gg[1] = fmaf(s4_0, v[4], gg[1]);
+      const float s1_0 = 0.7071067811865476f * gt1;
+      gv[4] = fmaf(-s1_0, g[2], gv[4]); gg[2] = fmaf(-s1_0, v[4], gg[2]);
+      const float s0_0 = 0.7071067811865475f * gt0;
+      gv[4] = fmaf(-s0_0, g[3], gv[4]); gg[3] = fmaf(-s0_0, v[4], gg[3]);
+      gv[5] = fmaf(-s1_0, g[1], gv[5]); gg[1] = fmaf(-s1_0, v[5], gg[1]);
+      const float s2_1 = 0.8164965809277261f * gt2;
+      gv[5] = fmaf(-s2_1, g[2], gv[5]); gg[2] = fmaf(-s2_1, v[5], gg[2]);
+      const float s3_0 = 0.7071067811865476f * gt3;
+      gv[5] = fmaf(-s3_0, g[3], gv[5]); gg[3] = fmaf(-s3_0, v[5], gg[3]);
+      gv[6] = fmaf(-s0_0, g[1], gv[6]); gg[1] = fmaf(-s0_0, v[6], gg[1]);
+      gv[6] = fmaf(-s3_0, g[2], gv[6]); gg[2] = fmaf(-s3_0, v[6], gg[2]);
+      gv[6] = fmaf(s2_0, g[3], gv[6]); gg[3] = fmaf(s2_0, v[6], gg[3]);
+      gv[6] = fmaf(-s4_0, g[3], gv[6]); gg[3] = fmaf(-s4_0, v[6], gg[3]);
     }
     { // path 13
-      const float w = th[13] * 0.4472135954999579f;
+      const float w = th[13 * TS];
       const float gt0 = w * gvo[5];
       const float gt1 = w * gvo[6];
       const float gt2 = w * gvo[7];
-      gv[4] += 0.547722557505166f * gt2 * g[4]; gg[4] += 0.547722557505166f * gt2 * v[4];
-      gv[4] += 0.547722557505166f * gt1 * g[5]; gg[5] += 0.547722557505166f * gt1 * v[4];
-      gv[4] += -0.3162277660168379f * gt0 * g[6]; gg[6] += -0.3162277660168379f * gt0 * v[4];
-      gv[4] += -0.547722557505166f * gt0 * g[8]; gg[8] += -0.547722557505166f * gt0 * v[4];
-      gv[5] += 0.547722557505166f * gt0 * g[5]; gg[5] += 0.547722557505166f * gt0 * v[5];
-      gv[5] += 0.632455532033676f * gt1 * g[6]; gg[6] += 0.632455532033676f * gt1 * v[5];
-      gv[5] += 0.547722557505166f * gt2 * g[7]; gg[7] += 0.547722557505166f * gt2 * v[5];
-      gv[6] += 0.547722557505166f * gt0 * g[4]; gg[4] += 0.547722557505166f * gt0 * v[6];
-      gv[6] += -0.3162277660168379f * gt2 * g[6]; gg[6] += -0.3162277660168379f * gt2 * v[6];
-      gv[6] += 0.547722557505166f * gt1 * g[7]; gg[7] += 0.547722557505166f * gt1 * v[6];
-      gv[6] += 0.547722557505166f * gt2 * g[8]; gg[8] += 0.547722557505166f * gt2 * v[6];
+      const float s2_0 = 0.547722557505166f * gt2;
+      gv[4] = fmaf(s2_0, g[4], gv[4]); gg[4] = fmaf(s2_0, v[4], gg[4]);
+      const float s1_0 = 0.547722557505166f * gt1;
+      gv[4] = fmaf(s1_0, g[5], gv[4]); gg[5] = fmaf(s1_0, v[4], gg[5]);
+      const float s0_0 = 0.3162277660168379f * gt0;
+      gv[4] = fmaf(-s0_0, g[6], gv[4]); gg[6] = fmaf(-s0_0, v[4], gg[6]);
+      const float s0_1 = 0.547722557505166f * gt0;
+      gv[4] = fmaf(-s0_1, g[8], gv[4]); gg[8] = fmaf(-s0_1, v[4], gg[8]);
+      gv[5] = fmaf(s0_1, g[5], gv[5]); gg[5] = fmaf(s0_1, v[5], gg[5]);
+      const float s1_1 = 0.632455532033676f * gt1;
+      gv[5] = fmaf(s1_1, g[6], gv[5]); gg[6] = fmaf(s1_1, v[5], gg[6]);
+      gv[5] = fmaf(s2_0, g[7], gv[5]); gg[7] = fmaf(s2_0, v[5], gg[7]);
+      gv[6] = fmaf(s0_1, g[4], gv[6]); gg[4] = fmaf(s0_1, v[6], gg[4]);
+      const float s2_1 = 0.3162277660168379f * gt2;
+      gv[6] = fmaf(-s2_1, g[6], gv[6]); gg[6] = fmaf(-s2_1, v[6], gg[6]);
+      gv[6] = fmaf(s1_0, g[7], gv[6]); gg[7] = fmaf(s1_0, v[6], gg[7]);
+      gv[6] = fmaf(s2_0, g[8], gv[6]); gg[8] = fmaf(s2_0, v[6], gg[8]);
     }
     { // path 14
-      const float w = th[14] * 0.4082482904638631f;
+      const float w = th[14 * TS];
       const float gt0 = w * gvo[8];
       const float gt1 = w * gvo[9];
       const float gt2 = w * gvo[10];
       const float gt3 = w * gvo[11];
       const float gt4 = w * gvo[12];
-      gv[4] += 0.408248290463863f * gt1 * g[4]; gg[4] += 0.408248290463863f * gt1 * v[4];
-      gv[4] += -0.408248290463863f * gt0 * g[5]; gg[5] += -0.408248290463863f * gt0 * v[4];
-      gv[4] += -0.7071067811865477f * gt3 * g[6]; gg[6] += -0.7071067811865477f * gt3 * v[4];
-      gv[4] += 0.7071067811865477f * gt2 * g[7]; gg[7] += 0.7071067811865477f * gt2 * v[4];
-      gv[4] += -0.408248290463863f * gt4 * g[7]; gg[7] += -0.408248290463863f * gt4 * v[4];
-      gv[4] += 0.408248290463863f * gt3 * g[8]; gg[8] += 0.408248290463863f * gt3 * v[4];
-      gv[5] += 0.816496580927726f * gt4 * g[4]; gg[4] += 0.816496580927726f * gt4 * v[5];
-      gv[5] += 0.408248290463863f * gt3 * g[5]; gg[5] += 0.408248290463863f * gt3 * v[5];
-      gv[5] += -0.408248290463863f * gt1 * g[7]; gg[7] += -0.408248290463863f * gt1 * v[5];
-      gv[5] += -0.816496580927726f * gt0 * g[8]; gg[8] += -0.816496580927726f * gt0 * v[5];
-      gv[6] += -0.408248290463863f * gt3 * g[4]; gg[4] += -0.408248290463863f * gt3 * v[6];
-      gv[6] += -0.7071067811865477f * gt2 * g[5]; gg[5] += -0.7071067811865477f * gt2 * v[6];
-      gv[6] += -0.408248290463863f * gt4 * g[5]; gg[5] += -0.408248290463863f * gt4 * v[6];
-      gv[6] += 0.7071067811865477f * gt1 * g[6]; gg[6] += 0.7071067811865477f * gt1 * v[6];
-      gv[6] += 0.408248290463863f * gt0 * g[7]; gg[7] += 0.408248290463863f * gt0 * v[6];
-      gv[6] += 0.408248290463863f * gt1 * g[8]; gg[8] += 0.408248290463863f * gt1 * v[6];
+      const float s1_0 = 0.408248290463863f * gt1;
+      gv[4] = fmaf(s1_0, g[4], gv[4]); gg[4] = fmaf(s1_0, v[4], gg[4]);
+      const float s0_0 = 0.408248290463863f * gt0;
+      gv[4] = fmaf(-s0_0, g[5], gv[4]); gg[5] = fmaf(-s0_0, v[4], gg[5]);
+      const float s3_0 = 0.7071067811865477f * gt3;
+      gv[4] = fmaf(-s3_0, g[6], gv[4]); gg[6] = fmaf(-s3_0, v[4], gg[6]);
+      const float s2_0 = 0.7071067811865477f * gt2;
+      gv[4] = fmaf(s2_0, g[7], gv[4]); gg[7] = fmaf(s2_0, v[4], gg[7]);
+      const float s4_0 = 0.408248290463863f * gt4;
+      gv[4] = fmaf(-s4_0, g[7], gv[4]); gg[7] = fmaf(-s4_0, v[4], gg[7]);
+      const float s3_1 = 0.408248290463863f * gt3;
+      gv[4] = fmaf(s3_1, g[8], gv[4]); gg[8] = fmaf(s3_1, v[4], gg[8]);
+      const float s4_1 = 0.816496580927726f * gt4;
+      gv[5] = fmaf(s4_1, g[4], gv[5]); gg[4] = fmaf(s4_1, v[5], gg[4]);
+      gv[5] = fmaf(s3_1, g[5], gv[5]); gg[5] = fmaf(s3_1, v[5], gg[5]);
+      gv[5] = fmaf(-s1_0, g[7], gv[5]); gg[7] = fmaf(-s1_0, v[5], gg[7]);
+      const float s0_1 = 0.816496580927726f * gt0;
+      gv[5] = fmaf(-s0_1, g[8], gv[5]); gg[8] = fmaf(-s0_1, v[5], gg[8]);
+      gv[6] = fmaf(-s3_1, g[4], gv[6]); gg[4] = fmaf(-s3_1, v[6], gg[4]);
+      gv[6] = fmaf(-s2_0, g[5], gv[6]); gg[5] = fmaf(-s2_0, v[6], gg[5]);
+      gv[6] = fmaf(-s4_0, g[5], gv[6]); gg[5] = fmaf(-s4_0, v[6], gg[5]);
+      const float s1_1 = 0.7071067811865477f * gt1;
+      gv[6] = fmaf(s1_1, g[6], gv[6]); gg[6] = fmaf(s1_1, v[6], gg[6]);
+      gv[6] = fmaf(s0_0, g[7], gv[6]); gg[7] = fmaf(s0_0, v[6], gg[7]);
+      gv[6] = fmaf(s1_0, g[8], gv[6]); gg[8] = fmaf(s1_0, v[6], gg[8]);
     }
     { // path 15
-      const float w = th[15] * 0.4082482904638631f;
+      const float w = th[15 * TS];
       const float gt0 = w * gvo[8];
       const float gt1 = w * gvo[9];
       const float gt2 = w * gvo[10];
       const float gt3 = w * gvo[11];
       const float gt4 = w * gvo[12];
-      gv[7] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[7];
-      gv[8] += 1.0f * gt1 * g[0]; gg[0] += 1.0f * gt1 * v[8];
-      gv[9] += 1.0000000000000002f * gt2 * g[0]; gg[0] += 1.0000000000000002f * gt2 * v[9];
-      gv[10] += 1.0f * gt3 * g[0]; gg[0] += 1.0f * gt3 * v[10];
-      gv[11] += 1.0f * gt4 * g[0]; gg[0] += 1.0f * gt4 * v[11];
+      const float s0_0 = gt0;
+      gv[7] = fmaf(s0_0, g[0], gv[7]); gg[0] = fmaf(s0_0, v[7], gg[0]);
+      const float s1_0 = gt1;
+      gv[8] = fmaf(s1_0, g[0], gv[8]); gg[0] = fmaf(s1_0, v[8], gg[0]);
+      const float s2_0 = gt2;
+      gv[9] = fmaf(s2_0, g[0], gv[9]); gg[0] = fmaf(s2_0, v[9], gg[0]);
+      const float s3_0 = gt3;
+      gv[10] = fmaf(s3_0, g[0], gv[10]); gg[0] = fmaf(s3_0, v[10], gg[0]);
+      const float s4_0 = gt4;
+      gv[11] = fmaf(s4_0, g[0], gv[11]); gg[0] = fmaf(s4_0, v[11], gg[0]);
     }
     { // path 16
-      const float w = th[16] * 0.4082482904638631f;
+      const float w = th[16 * TS];
       const float gt0 = w * gvo[2];
       const float gt1 = w * gvo[3];
       const float gt2 = w * gvo[4];
-      gv[7] += 0.547722557505166f * gt2 * g[1]; gg[1] += 0.547722557505166f * gt2 * v[7];
-      gv[7] += 0.547722557505166f * gt0 * g[3]; gg[3] += 0.547722557505166f * gt0 * v[7];
-      gv[8] += 0.547722557505166f * gt1 * g[1]; gg[1] += 0.547722557505166f * gt1 * v[8];
-      gv[8] += 0.547722557505166f * gt0 * g[2]; gg[2] += 0.547722557505166f * gt0 * v[8];
-      gv[9] += -0.3162277660168379f * gt0 * g[1]; gg[1] += -0.3162277660168379f * gt0 * v[9];
-      gv[9] += 0.632455532033676f * gt1 * g[2]; gg[2] += 0.632455532033676f * gt1 * v[9];
-      gv[9] += -0.3162277660168379f * gt2 * g[3]; gg[3] += -0.3162277660168379f * gt2 * v[9];
-      gv[10] += 0.547722557505166f * gt2 * g[2]; gg[2] += 0.547722557505166f * gt2 * v[10];
-      gv[10] += 0.547722557505166f * gt1 * g[3]; gg[3] += 0.547722557505166f * gt1 * v[10];
-      gv[11] += -0.547722557505166f * gt0 * g[1]; gg[1] += -0.547722557505166f * gt0 * v[11];
-      gv[11] += 0.547722557505166f * gt2 * g[3]; gg[3] += 0.547722557505166f * gt2 * v[11];
+      const float s2_0 = 0.547722557505166f * gt2;
+      gv[7] = fmaf(s2_0, g[1], gv[7]); gg[1] = fmaf(s2_0, v[7], gg[1]);
+      const float s0_0 = 0.547722557505166f * gt0;
+      gv[7] = fmaf(s0_0, g[3], gv[7]); gg[3] = fmaf(s0_0, v[7], gg[3]);
+      const float s1_0 = 0.547722557505166f * gt1;
+      gv[8] = fmaf(s1_0, g[1], gv[8]); gg[1] = fmaf(s1_0, v[8], gg[1]);
+      gv[8] = fmaf(s0_0, g[2], gv[8]); gg[2] = fmaf(s0_0, v[8], gg[2]);
+      const float s0_1 = 0.3162277660168379f * gt0;
+      gv[9] = fmaf(-s0_1, g[1], gv[9]); gg[1] = fmaf(-s0_1, v[9], gg[1]);
+      const float s1_1 = 0.632455532033676f * gt1;
+      gv[9] = fmaf(s1_1, g[2], gv[9]); gg[2] = fmaf(s1_1, v[9], gg[2]);
+      const float s2_1 = 0.3162277660168379f * gt2;
+      gv[9] = fmaf(-s2_1, g[3], gv[9]); gg[3] = fmaf(-s2_1, v[9], gg[3]);
+      gv[10] = fmaf(s2_0, g[2], gv[10]); gg[2] = fmaf(s2_0, v[10], gg[2]);
+      gv[10] = fmaf(s1_0, g[3], gv[10]); gg[3] = fmaf(s1_0, v[10], gg[3]);
+      gv[11] = fmaf(-s0_0, g[1], gv[11]); gg[1] = fmaf(-s0_0, v[11], gg[1]);
+      gv[11] = fmaf(s2_0, g[3], gv[11]); gg[3] = fmaf(s2_0, v[11], gg[3]);
     }
     { // path 17
-      const float w = th[17] * 0.4472135954999579f;
+      const float w = th[17 * TS];
       const float gt0 = w * gvo[13];
       const float gt1 = w * gvo[14];
       const float gt2 = w * gvo[15];
       const float gt3 = w * gvo[16];
       const float gt4 = w * gvo[17];
-      gv[7] += 0.408248290463863f * gt1 * g[1]; gg[1] += 0.408248290463863f * gt1 * v[7];
-      gv[7] += 0.816496580927726f * gt4 * g[2]; gg[2] += 0.816496580927726f * gt4 * v[7];
-      gv[7] += -0.408248290463863f * gt3 * g[3]; gg[3] += -0.408248290463863f * gt3 * v[7];
-      gv[8] += -0.408248290463863f * gt0 * g[1]; gg[1] += -0.408248290463863f * gt0 * v[8];
-      gv[8] += 0.408248290463863f * gt3 * g[2]; gg[2] += 0.408248290463863f * gt3 * v[8];
-      gv[8] += -0.7071067811865477f * gt2 * g[3]; gg[3] += -0.7071067811865477f * gt2 * v[8];
-      gv[8] += -0.408248290463863f * gt4 * g[3]; gg[3] += -0.408248290463863f * gt4 * v[8];
-      gv[9] += -0.7071067811865477f * gt3 * g[1]; gg[1] += -0.7071067811865477f * gt3 * v[9];
-      gv[9] += 0.7071067811865477f * gt1 * g[3]; gg[3] += 0.7071067811865477f * gt1 * v[9];
-      gv[10] += 0.7071067811865477f * gt2 * g[1]; gg[1] += 0.7071067811865477f * gt2 * v[10];
-      gv[10] += -0.408248290463863f * gt4 * g[1]; gg[1] += -0.408248290463863f * gt4 * v[10];
-      gv[10] += -0.408248290463863f * gt1 * g[2]; gg[2] += -0.408248290463863f * gt1 * v[10];
-      gv[10] += 0.408248290463863f * gt0 * g[3]; gg[3] += 0.408248290463863f * gt0 * v[10];
-      gv[11] += 0.408248290463863f * gt3 * g[1]; gg[1] += 0.408248290463863f * gt3 * v[11];
-      gv[11] += -0.816496580927726f * gt0 * g[2]; gg[2] += -0.816496580927726f * gt0 * v[11];
-      gv[11] += 0.408248290463863f * gt1 * g[3]; gg[3] += 0.408248290463863f * gt1 * v[11];
+      const float s1_0 = 0.408248290463863f * gt1;
+      gv[7] = fmaf(s1_0, g[1], gv[7]); gg[1] = fmaf(s1_0, v[7], gg[1]);
+      const float s4_0 = 0.816496580927726f * gt4;
+      gv[7] = fmaf(s4_0, g[2], gv[7]); gg[2] = fmaf(s4_0, v[7], gg[2]);
+      const float s3_0 = 0.408248290463863f * gt3;
+      gv[7] = fmaf(-s3_0, g[3], gv[7]); gg[3] = fmaf(-s3_0, v[7], gg[3]);
+      const float s0_0 = 0.408248290463863f * gt0;
+      gv[8] = fmaf(-s0_0, g[1], gv[8]); gg[1] = fmaf(-s0_0, v[8], gg[1]);
+      gv[8] = fmaf(s3_0, g[2], gv[8]); gg[2] = fmaf(s3_0, v[8], gg[2]);
+      const float s2_0 = 0.7071067811865477f * gt2;
+      gv[8] = fmaf(-s2_0, g[3], gv[8]); gg[3] = fmaf(-s2_0, v[8], gg[3]);
+      const float s4_1 = 0.408248290463863f * gt4;
+      gv[8] = fmaf(-s4_1, g[3], gv[8]); gg[3] = fmaf(-s4_1, v[8], gg[3]);
+      const float s3_1 = 0.7071067811865477f * gt3;
+      gv[9] = fmaf(-s3_1, g[1], gv[9]); gg[1] = fmaf(-s3_1, v[9], gg[1]);
+      const float s1_1 = 0.7071067811865477f * gt1;
+      gv[9] = fmaf(s1_1, g[3], gv[9]); gg[3] = fmaf(s1_1, v[9], gg[3]);
+      gv[10] = fmaf(s2_0, g[1], gv[10]); gg[1] = fmaf(s2_0, v[10], gg[1]);
+      gv[10] = fmaf(-s4_1, g[1], gv[10]); gg[1] = fmaf(-s4_1, v[10], gg[1]);
+      gv[10] = fmaf(-s1_0, g[2], gv[10]); gg[2] = fmaf(-s1_0, v[10], gg[2]);
+      gv[10] = fmaf(s0_0, g[3], gv[10]); gg[3] = fmaf(s0_0, v[10], gg[3]);
+      gv[11] = fmaf(s3_0, g[1], gv[11]); gg[1] = fmaf(s3_0, v[11], gg[1]);
+      const float s0_1 = 0.816496580927726f * gt0;
+      gv[11] = fmaf(-s0_1, g[2], gv[11]); gg[2] = fmaf(-s0_1, v[11], gg[2]);
+      gv[11] = fmaf(s1_0, g[3], gv[11]); gg[3] = fmaf(s1_0, v[11], gg[3]);
     }
     { // path 18
-      const float w = th[18] * 0.5773502691896258f;
+      const float w = th[18 * TS];
       const float gt0 = gs[2] + w * gvo[0];
-      gv[7] += 0.4472135954999579f * gt0 * g[4]; gg[4] += 0.4472135954999579f * gt0 * v[7];
-      gv[8] += 0.4472135954999579f * gt0 * g[5]; gg[5] += 0.4472135954999579f * gt0 * v[8];
-      gv[9] += 0.44721359549995804f * gt0 * g[6]; gg[6] += 0.44721359549995804f * gt0 * v[9];
-      gv[10] += 0.4472135954999579f * gt0 * g[7]; gg[7] += 0.4472135954999579f * gt0 * v[10];
-      gv[11] += 0.4472135954999579f * gt0 * g[8]; gg[8] += 0.4472135954999579f * gt0 * v[11];
+      const float s0_0 = 0.4472135954999579f * gt0;
+      gv[7] = fmaf(s0_0, g[4], gv[7]); gg[4] = fmaf(s0_0, v[7], gg[4]);
+      gv[8] = fmaf(s0_0, g[5], gv[8]); gg[5] = fmaf(s0_0, v[8], gg[5]);
+      gv[9] = fmaf(s0_0, g[6], gv[9]); gg[6] = fmaf(s0_0, v[9], gg[6]);
+      gv[10] = fmaf(s0_0, g[7], gv[10]); gg[7] = fmaf(s0_0, v[10], gg[7]);
+      gv[11] = fmaf(s0_0, g[8], gv[11]); gg[8] = fmaf(s0_0, v[11], gg[8]);
     }
     { // path 19
-      const float w = th[19] * 0.4472135954999579f;
+      const float w = th[19 * TS];
       const float gt0 = w * gvo[5];
       const float gt1 = w * gvo[6];
       const float gt2 = w * gvo[7];
-      gv[7] += 0.3162277660168379f * gt0 * g[5]; gg[5] += 0.3162277660168379f * gt0 * v[7];
-      gv[7] += -0.3162277660168379f * gt2 * g[7]; gg[7] += -0.3162277660168379f * gt2 * v[7];
-      gv[7] += 0.6324555320336758f * gt1 * g[8]; gg[8] += 0.6324555320336758f * gt1 * v[7];
-      gv[8] += -0.3162277660168379f * gt0 * g[4]; gg[4] += -0.3162277660168379f * gt0 * v[8];
-      gv[8] += -0.5477225575051661f * gt2 * g[6]; gg[6] += -0.5477225575051661f * gt2 * v[8];
-      gv[8] += 0.3162277660168379f * gt1 * g[7]; gg[7] += 0.3162277660168379f * gt1 * v[8];
-      gv[8] += -0.3162277660168379f * gt2 * g[8]; gg[8] += -0.3162277660168379f * gt2 * v[8];
-      gv[9] += 0.5477225575051661f * gt2 * g[5]; gg[5] += 0.5477225575051661f * gt2 * v[9];
-      gv[9] += -0.5477225575051661f * gt0 * g[7]; gg[7] += -0.5477225575051661f * gt0 * v[9];
-      gv[10] += 0.3162277660168379f * gt2 * g[4]; gg[4] += 0.3162277660168379f * gt2 * v[10];
-      gv[10] += -0.3162277660168379f * gt1 * g[5]; gg[5] += -0.3162277660168379f * gt1 * v[10];
-      gv[10] += 0.5477225575051661f * gt0 * g[6]; gg[6] += 0.5477225575051661f * gt0 * v[10];
-      gv[10] += -0.3162277660168379f * gt0 * g[8]; gg[8] += -0.3162277660168379f * gt0 * v[10];
-      gv[11] += -0.6324555320336758f * gt1 * g[4]; gg[4] += -0.6324555320336758f * gt1 * v[11];
-      gv[11] += 0.3162277660168379f * gt2 * g[5]; gg[5] += 0.3162277660168379f * gt2 * v[11];
-      gv[11] += 0.3162277660168379f * gt0 * g[7]; gg[7] += 0.3162277660168379f * gt0 * v[11];
+      const float s0_0 = 0.3162277660168379f * gt0;
+      gv[7] = fmaf(s0_0, g[5], gv[7]); gg[5] = fmaf(s0_0, v[7], gg[5]);
+      const float s2_0 = 0.3162277660168379f * gt2;
+      gv[7] = fmaf(-s2_0, g[7], gv[7]); gg[7] = fmaf(-s2_0, v[7], gg[7]);
+      const float s1_0 = 0.6324555320336758f * gt1;
+      gv[7] = fmaf(s1_0, g[8], gv[7]); gg[8] = fmaf(s1_0, v[7], gg[8]);
+      gv[8] = fmaf(-s0_0, g[4], gv[8]); gg[4] = fmaf(-s0_0, v[8], gg[4]);
+      const float s2_1 = 0.5477225575051661f * gt2;
+      gv[8] = fmaf(-s2_1, g[6], gv[8]); gg[6] = fmaf(-s2_1, v[8], gg[6]);
+      const float s1_1 = 0.3162277660168379f * gt1;
+      gv[8] = fmaf(s1_1, g[7], gv[8]); gg[7] = fmaf(s1_1, v[8], gg[7]);
+      gv[8] = fmaf(-s2_0, g[8], gv[8]); gg[8] = fmaf(-s2_0, v[8], gg[8]);
+      gv[9] = fmaf(s2_1, g[5], gv[9]); gg[5] = fmaf(s2_1, v[9], gg[5]);
+      const float s0_1 = 0.5477225575051661f * gt0;
+      gv[9] = fmaf(-s0_1, g[7], gv[9]); gg[7] = fmaf(-s0_1, v[9], gg[7]);
+      gv[10] = fmaf(s2_0, g[4], gv[10]); gg[4] = fmaf(s2_0, v[10], gg[4]);
+      gv[10] = fmaf(-s1_1, g[5], gv[10]); gg[5] = fmaf(-s1_1, v[10], gg[5]);
+      gv[10] = fmaf(s0_1, g[6], gv[10]); gg[6] = fmaf(s0_1, v[10], gg[6]);
+      gv[10] = fmaf(-s0_0, g[8], gv[10]); gg[8] = fmaf(-s0_0, v[10], gg[8]);
+      gv[11] = fmaf(-s1_0, g[4], gv[11]); gg[4] = fmaf(-s1_0, v[11], gg[4]);
+      gv[11] = fmaf(s2_0, g[5], gv[11]); gg[5] = fmaf(s2_0, v[11], gg[5]);
+      gv[11] = fmaf(s0_0, g[7], gv[11]); gg[7] = fmaf(s0_0, v[11], gg[7]);
     }
     { // path 20
-      const float w = th[20] * 0.4082482904638631f;
+      const float w = th[20 * TS];
       const float gt0 = w * gvo[8];
       const float gt1 = w * gvo[9];
       const float gt2 = w * gvo[10];
       const float gt3 = w * gvo[11];
       const float gt4 = w * gvo[12];
-      gv[7] += 0.5345224838248488f * gt2 * g[4]; gg[4] += 0.5345224838248488f * gt2 * v[7];
-      gv[7] += -0.4629100498862757f * gt3 * g[5]; gg[5] += -0.4629100498862757f * gt3 * v[7];
-      gv[7] += 0.5345224838248488f * gt0 * g[6]; gg[6] += 0.5345224838248488f * gt0 * v[7];
-      gv[7] += -0.4629100498862757f * gt1 * g[7]; gg[7] += -0.4629100498862757f * gt1 * v[7];
-      gv[8] += -0.4629100498862757f * gt3 * g[4]; gg[4] += -0.4629100498862757f * gt3 * v[8];
-      gv[8] += -0.2672612419124244f * gt2 * g[5]; gg[5] += -0.2672612419124244f * gt2 * v[8];
-      gv[8] += 0.4629100498862757f * gt4 * g[5]; gg[5] += 0.4629100498862757f * gt4 * v[8];
-      gv[8] += -0.2672612419124244f * gt1 * g[6]; gg[6] += -0.2672612419124244f * gt1 * v[8];
-      gv[8] += -0.4629100498862757f * gt0 * g[7]; gg[7] += -0.4629100498862757f * gt0 * v[8];
-      gv[8] += 0.4629100498862757f * gt1 * g[8]; gg[8] += 0.4629100498862757f * gt1 * v[8];
-      gv[9] += 0.5345224838248488f * gt0 * g[4]; gg[4] += 0.5345224838248488f * gt0 * v[9];
-      gv[9] += -0.2672612419124244f * gt1 * g[5]; gg[5] += -0.2672612419124244f * gt1 * v[9];
-      gv[9] += -0.5345224838248489f * gt2 * g[6]; gg[6] += -0.5345224838248489f * gt2 * v[9];
-      gv[9] += -0.2672612419124244f * gt3 * g[7]; gg[7] += -0.2672612419124244f * gt3 * v[9];
-      gv[9] += 0.5345224838248488f * gt4 * g[8]; gg[8] += 0.5345224838248488f * gt4 * v[9];
-      gv[10] += -0.4629100498862757f * gt1 * g[4]; gg[4] += -0.4629100498862757f * gt1 * v[10];
-      gv[10] += -0.4629100498862757f * gt0 * g[5]; gg[5] += -0.4629100498862757f * gt0 * v[10];
-      gv[10] += -0.2672612419124244f * gt3 * g[6]; gg[6] += -0.2672612419124244f * gt3 * v[10];
-      gv[10] += -0.2672612419124244f * gt2 * g[7]; gg[7] += -0.2672612419124244f * gt2 * v[10];
-      gv[10] += -0.4629100498862757f * gt4 * g[7]; gg[7] += -0.4629100498862757f * gt4 * v[10];
-      gv[10] += -0.4629100498862757f * gt3 * g[8]; gg[8] += -0.4629100498862757f * gt3 * v[10];
-      gv[11] += 0.4629100498862757f * gt1 * g[5]; gg[5] += 0.4629100498862757f * gt1 * v[11];
-      gv[11] += 0.5345224838248488f * gt4 * g[6]; gg[6] += 0.5345224838248488f * gt4 * v[11];
-      gv[11] += -0.4629100498862757f * gt3 * g[7]; gg[7] += -0.4629100498862757f * gt3 * v[11];
-      gv[11] += 0.5345224838248488f * gt2 * g[8]; gg[8] += 0.5345224838248488f * gt2 * v[11];
+      const float s2_0 = 0.5345224838248488f * gt2;
+      gv[7] = fmaf(s2_0, g[4], gv[7]); gg[4] = fmaf(s2_0, v[7], gg[4]);
+      const float s3_0 = 0.4629100498862757f * gt3;
+      gv[7] = fmaf(-s3_0, g[5], gv[7]); gg[5] = fmaf(-s3_0, v[7], gg[5]);
+      const float s0_0 = 0.5345224838248488f * gt0;
+      gv[7] = fmaf(s0_0, g[6], gv[7]); gg[6] = fmaf(s0_0, v[7], gg[6]);
+      const float s1_0 = 0.4629100498862757f * gt1;
+      gv[7] = fmaf(-s1_0, g[7], gv[7]); gg[7] = fmaf(-s1_0, v[7], gg[7]);
+      gv[8] = fmaf(-s3_0, g[4], gv[8]); gg[4] = fmaf(-s3_0, v[8], gg[4]);
+      const float s2_1 = 0.2672612419124244f * gt2;
+      gv[8] = fmaf(-s2_1, g[5], gv[8]); gg[5] = fmaf(-s2_1, v[8], gg[5]);
+      const float s4_0 = 0.4629100498862757f * gt4;
+      gv[8] = fmaf(s4_0, g[5], gv[8]); gg[5] = fmaf(s4_0, v[8], gg[5]);
+      const float s1_1 = 0.2672612419124244f * gt1;
+      gv[8] = fmaf(-s1_1, g[6], gv[8]); gg[6] = fmaf(-s1_1, v[8], gg[6]);
+      const float s0_1 = 0.4629100498862757f * gt0;
+      gv[8] = fmaf(-s0_1, g[7], gv[8]); gg[7] = fmaf(-s0_1, v[8], gg[7]);
+      gv[8] = fmaf(s1_0, g[8], gv[8]); gg[8] = fmaf(s1_0, v[8], gg[8]);
+      gv[9] = fmaf(s0_0, g[4], gv[9]); gg[4] = fmaf(s0_0, v[9], gg[4]);
+      gv[9] = fmaf(-s1_1, g[5], gv[9]); gg[5] = fmaf(-s1_1, v[9], gg[5]);
+      gv[9] = fmaf(-s2_0, g[6], gv[9]); gg[6] = fmaf(-s2_0, v[9], gg[6]);
+      const float s3_1 = 0.2672612419124244f * gt3;
+      gv[9] = fmaf(-s3_1, g[7], gv[9]); gg[7] = fmaf(-s3_1, v[9], gg[7]);
+      const float s4_1 = 0.5345224838248488f * gt4;
+      gv[9] = fmaf(s4_1, g[8], gv[9]); gg[8] = fmaf(s4_1, v[9], gg[8]);
+      gv[10] = fmaf(-s1_0, g[4], gv[10]); gg[4] = fmaf(-s1_0, v[10], gg[4]);
+      gv[10] = fmaf(-s0_1, g[5], gv[10]); gg[5] = fmaf(-s0_1, v[10], gg[5]);
+      gv[10] = fmaf(-s3_1, g[6], gv[10]); gg[6] = fmaf(-s3_1, v[10], gg[6]);
+      gv[10] = fmaf(-s2_1, g[7], gv[10]); gg[7] = fmaf(-s2_1, v[10], gg[7]);
+      gv[10] = fmaf(-s4_0, g[7], gv[10]); gg[7] = fmaf(-s4_0, v[10], gg[7]);
+      gv[10] = fmaf(-s3_0, g[8], gv[10]); gg[8] = fmaf(-s3_0, v[10], gg[8]);
+      gv[11] = fmaf(s1_0, g[5], gv[11]); gg[5] = fmaf(s1_0, v[11], gg[5]);
+      gv[11] = fmaf(s4_1, g[6], gv[11]); gg[6] = fmaf(s4_1, v[11], gg[6]);
+      gv[11] = fmaf(-s3_0, g[7], gv[11]); gg[7] = fmaf(-s3_0, v[11], gg[7]);
+      gv[11] = fmaf(s2_0, g[8], gv[11]); gg[8] = fmaf(s2_0, v[11], gg[8]);
     }
     { // path 21
-      const float w = th[21] * 0.4472135954999579f;
+      const float w = th[21 * TS];
       const float gt0 = w * gvo[13];
       const float gt1 = w * gvo[14];
       const float gt2 = w * gvo[15];
       const float gt3 = w * gvo[16];
       const float gt4 = w * gvo[17];
-      gv[12] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[12];
-      gv[13] += 1.0f * gt1 * g[0]; gg[0] += 1.0f * gt1 * v[13];
-      gv[14] += 1.0000000000000002f * gt2 * g[0]; gg[0] += 1.0000000000000002f * gt2 * v[14];
-      gv[15] += 1.0f * gt3 * g[0]; gg[0] += 1.0f * gt3 * v[15];
-      gv[16] += 1.0f * gt4 * g[0]; gg[0] += 1.0f * gt4 * v[16];
+      const float s0_0 = gt0;
+      gv[12] = fmaf(s0_0, g[0], gv[12]); gg[0] = fmaf(s0_0, v[12], gg[0]);
+      const float s1_0 = gt1;
+      gv[13] = fmaf(s1_0, g[0], gv[13]); gg[0] = fmaf(s1_0, v[13], gg[0]);
+      const float s2_0 = gt2;
+      gv[14] = fmaf(s2_0, g[0], gv[14]); gg[0] = fmaf(s2_0, v[14], gg[0]);
+      const float s3_0 = gt3;
+      gv[15] = fmaf(s3_0, g[0], gv[15]); gg[0] = fmaf(s3_0, v[15], gg[0]);
+      const float s4_0 = gt4;
+      gv[16] = fmaf(s4_0, g[0], gv[16]); gg[0] = fmaf(s4_0, v[16], gg[0]);
     }
     { // path 22
-      const float w = th[22] * 0.4472135954999579f;
+      const float w = th[22 * TS];
       const float gt0 = w * gvo[5];
       const float gt1 = w * gvo[6];
       const float gt2 = w * gvo[7];
-      gv[12] += 0.547722557505166f * gt2 * g[1]; gg[1] += 0.547722557505166f * gt2 * v[12];
-      gv[12] += 0.547722557505166f * gt0 * g[3]; gg[3] += 0.547722557505166f * gt0 * v[12];
-      gv[13] += 0.547722557505166f * gt1 * g[1]; gg[1] += 0.547722557505166f * gt1 * v[13];
-      gv[13] += 0.547722557505166f * gt0 * g[2]; gg[2] += 0.547722557505166f * gt0 * v[13];
-      gv[14] += -0.3162277660168379f * gt0 * g[1]; gg[1] += -0.3162277660168379f * gt0 * v[14];
-      gv[14] += 0.632455532033676f * gt1 * g[2]; gg[2] += 0.632455532033676f * gt1 * v[14];
-      gv[14] += -0.3162277660168379f * gt2 * g[3]; gg[3] += -0.3162277660168379f * gt2 * v[14];
-      gv[15] += 0.547722557505166f * gt2 * g[2]; gg[2] += 0.547722557505166f * gt2 * v[15];
-      gv[15] += 0.547722557505166f * gt1 * g[3]; gg[3] += 0.547722557505166f * gt1 * v[15];
-      gv[16] += -0.547722557505166f * gt0 * g[1]; gg[1] += -0.547722557505166f * gt0 * v[16];
-      gv[16] += 0.547722557505166f * gt2 * g[3]; gg[3] += 0.547722557505166f * gt2 * v[16];
+      const float s2_0 = 0.547722557505166f * gt2;
+      gv[12] = fmaf(s2_0, g[1], gv[12]); gg[1] = fmaf(s2_0, v[12], gg[1]);
+      const float s0_0 = 0.547722557505166f * gt0;
+      gv[12] = fmaf(s0_0, g[3], gv[12]); gg[3] = fmaf(s0_0, v[12], gg[3]);
+      const float s1_0 = 0.547722557505166f * gt1;
+      gv[13] = fmaf(s1_0, g[1], gv[13]); gg[1] = fmaf(s1_0, v[13], gg[1]);
+      gv[13] = fmaf(s0_0, g[2], gv[13]); gg[2] = fmaf(s0_0, v[13], gg[2]);
+      const float s0_1 = 0.3162277660168379f * gt0;
+      gv[14] = fmaf(-s0_1, g[1], gv[14]); gg[1] = fmaf(-s0_1, v[14], gg[1]);
+      const float s1_1 = 0.632455532033676f * gt1;
+      gv[14] = fmaf(s1_1, g[2], gv[14]); gg[2] = fmaf(s1_1, v[14], gg[2]);
+      const float s2_1 = 0.3162277660168379f * gt2;
+      gv[14] = fmaf(-s2_1, g[3], gv[14]); gg[3] = fmaf(-s2_1, v[14], gg[3]);
+      gv[15] = fmaf(s2_0, g[2], gv[15]); gg[2] = fmaf(s2_0, v[15], gg[2]);
+      gv[15] = fmaf(s1_0, g[3], gv[15]); gg[3] = fmaf(s1_0, v[15], gg[3]);
+      gv[16] = fmaf(-s0_0, g[1], gv[16]); gg[1] = fmaf(-s0_0, v[16], gg[1]);
+      gv[16] = fmaf(s2_0, g[3], gv[16]); gg[3] = fmaf(s2_0, v[16], gg[3]);
     }
     { // path 23
-      const float w = th[23] * 0.4082482904638631f;
+      const float w = th[23 * TS];
       const float gt0 = w * gvo[8];
       const float gt1 = w * gvo[9];
       const float gt2 = w * gvo[10];
       const float gt3 = w * gvo[11];
       const float gt4 = w * gvo[12];
-      gv[12] += 0.408248290463863f * gt1 * g[1]; gg[1] += 0.408248290463863f * gt1 * v[12];
-      gv[12] += 0.816496580927726f * gt4 * g[2]; gg[2] += 0.816496580927726f * gt4 * v[12];
-      gv[12] += -0.408248290463863f * gt3 * g[3]; gg[3] += -0.408248290463863f * gt3 * v[12];
-      gv[13] += -0.408248290463863f * gt0 * g[1]; gg[1] += -0.408248290463863f * gt0 * v[13];
-      gv[13] += 0.408248290463863f * gt3 * g[2]; gg[2] += 0.408248290463863f * gt3 * v[13];
-      gv[13] += -0.7071067811865477f * gt2 * g[3]; gg[3] += -0.7071067811865477f * gt2 * v[13];
-      gv[13] += -0.408248290463863f * gt4 * g[3]; gg[3] += -0.408248290463863f * gt4 * v[13];
-      gv[14] += -0.7071067811865477f * gt3 * g[1]; gg[1] += -0.7071067811865477f * gt3 * v[14];
-      gv[14] += 0.7071067811865477f * gt1 * g[3]; gg[3] += 0.7071067811865477f * gt1 * v[14];
-      gv[15] += 0.7071067811865477f * gt2 * g[1]; gg[1] += 0.7071067811865477f * gt2 * v[15];
-      gv[15] += -0.408248290463863f * gt4 * g[1]; gg[1] += -0.408248290463863f * gt4 * v[15];
-      gv[15] += -0.408248290463863f * gt1 * g[2]; gg[2] += -0.408248290463863f * gt1 * v[15];
-      gv[15] += 0.408248290463863f * gt0 * g[3]; gg[3] += 0.408248290463863f * gt0 * v[15];
-      gv[16] += 0.408248290463863f * gt3 * g[1]; gg[1] += 0.408248290463863f * gt3 * v[16];
-      gv[16] += -0.816496580927726f * gt0 * g[2]; gg[2] += -0.816496580927726f * gt0 * v[16];
-      gv[16] += 0.408248290463863f * gt1 * g[3]; gg[3] += 0.408248290463863f * gt1 * v[16];
+      const float s1_0 = 0.408248290463863f * gt1;
+      gv[12] = fmaf(s1_0, g[1], gv[12]); gg[1] = fmaf(s1_0, v[12], gg[1]);
+      const float s4_0 = 0.816496580927726f * gt4;
+      gv[12] = fmaf(s4_0, g[2], gv[12]); gg[2] = fmaf(s4_0, v[12], gg[2]);
+      const float s3_0 = 0.408248290463863f * gt3;
+      gv[12] = fmaf(-s3_0, g[3], gv[12]); gg[3] = fmaf(-s3_0, v[12], gg[3]);
+      const float s0_0 = 0.408248290463863f * gt0;
+      gv[13] = fmaf(-s0_0, g[1], gv[13]); gg[1] = fmaf(-s0_0, v[13], gg[1]);
+      gv[13] = fmaf(s3_0, g[2], gv[13]); gg[2] = fmaf(s3_0, v[13], gg[2]);
+      const float s2_0 = 0.7071067811865477f * gt2;
+      gv[13] = fmaf(-s2_0, g[3], gv[13]); gg[3] = fmaf(-s2_0, v[13], gg[3]);
+      const float s4_1 = 0.408248290463863f * gt4;
+      gv[13] = fmaf(-s4_1, g[3], gv[13]); gg[3] = fmaf(-s4_1, v[13], gg[3]);
+      const float s3_1 = 0.7071067811865477f * gt3;
+      gv[14] = fmaf(-s3_1, g[1], gv[14]); gg[1] = fmaf(-s3_1, v[14], gg[1]);
+      const float s1_1 = 0.7071067811865477f * gt1;
+      gv[14] = fmaf(s1_1, g[3], gv[14]); gg[3] = fmaf(s1_1, v[14], gg[3]);
+      gv[15] = fmaf(s2_0, g[1], gv[15]); gg[1] = fmaf(s2_0, v[15], gg[1]);
+      gv[15] = fmaf(-s4_1, g[1], gv[15]); gg[1] = fmaf(-s4_1, v[15], gg[1]);
+      gv[15] = fmaf(-s1_0, g[2], gv[15]); gg[2] = fmaf(-s1_0, v[15], gg[2]);
+      gv[15] = fmaf(s0_0, g[3], gv[15]); gg[3] = fmaf(s0_0, v[15], gg[3]);
+      gv[16] = fmaf(s3_0, g[1], gv[16]); gg[1] = fmaf(s3_0, v[16], gg[1]);
+      const float s0_1 = 0.816496580927726f * gt0;
+      gv[16] = fmaf(-s0_1, g[2], gv[16]); gg[2] = fmaf(-s0_1, v[16], gg[2]);
+      gv[16] = fmaf(s1_0, g[3], gv[16]); gg[3] = fmaf(s1_0, v[16], gg[3]);
     }
     { // path 24
-      const float w = th[24] * 0.7071067811865475f;
+      const float w = th[24 * TS];
       const float gt0 = w * gvo[1];
-      gv[12] += 0.4472135954999579f * gt0 * g[4]; gg[4] += 0.4472135954999579f * gt0 * v[12];
-      gv[13] += 0.4472135954999579f * gt0 * g[5]; gg[5] += 0.4472135954999579f * gt0 * v[13];
-      gv[14] += 0.44721359549995804f * gt0 * g[6]; gg[6] += 0.44721359549995804f * gt0 * v[14];
-      gv[15] += 0.4472135954999579f * gt0 * g[7]; gg[7] += 0.4472135954999579f * gt0 * v[15];
-      gv[16] += 0.4472135954999579f * gt0 * g[8]; gg[8] += 0.4472135954999579f * gt0 * v[16];
+      const float s0_0 = 0.4472135954999579f * gt0;
+      gv[12] = fmaf(s0_0, g[4], gv[12]); gg[4] = fmaf(s0_0, v[12], gg[4]);
+      gv[13] = fmaf(s0_0, g[5], gv[13]); gg[5] = fmaf(s0_0, v[13], gg[5]);
+      gv[14] = fmaf(s0_0, g[6], gv[14]); gg[6] = fmaf(s0_0, v[14], gg[6]);
+      gv[15] = fmaf(s0_0, g[7], gv[15]); gg[7] = fmaf(s0_0, v[15], gg[7]);
+      gv[16] = fmaf(s0_0, g[8], gv[16]); gg[8] = fmaf(s0_0, v[16], gg[8]);
     }
     { // path 25
-      const float w = th[25] * 0.4082482904638631f;
+      const float w = th[25 * TS];
       const float gt0 = w * gvo[2];
       const float gt1 = w * gvo[3];
       const float gt2 = w * gvo[4];
-      gv[12] += 0.3162277660168379f * gt0 * g[5]; gg[5] += 0.3162277660168379f * gt0 * v[12];
-      gv[12] += -0.3162277660168379f * gt2 * g[7]; gg[7] += -0.3162277660168379f * gt2 * v[12];
-      gv[12] += 0.6324555320336758f * gt1 * g[8]; gg[8] += 0.6324555320336758f * gt1 * v[12];
-      gv[13] += -0.3162277660168379f * gt0 * g[4]; gg[4] += -0.3162277660168379f * gt0 * v[13];
-      gv[13] += -0.5477225575051661f * gt2 * g[6]; gg[6] += -0.5477225575051661f * gt2 * v[13];
-      gv[13] += 0.3162277660168379f * gt1 * g[7]; gg[7] += 0.3162277660168379f * gt1 * v[13];
-      gv[13] += -0.3162277660168379f * gt2 * g[8]; gg[8] += -0.3162277660168379f * gt2 * v[13];
-      gv[14] += 0.5477225575051661f * gt2 * g[5]; gg[5] += 0.5477225575051661f * gt2 * v[14];
-      gv[14] += -0.5477225575051661f * gt0 * g[7]; gg[7] += -0.5477225575051661f * gt0 * v[14];
-      gv[15] += 0.3162277660168379f * gt2 * g[4]; gg[4] += 0.3162277660168379f * gt2 * v[15];
-      gv[15] += -0.3162277660168379f * gt1 * g[5]; gg[5] += -0.3162277660168379f * gt1 * v[15];
-      gv[15] += 0.5477225575051661f * gt0 * g[6]; gg[6] += 0.5477225575051661f * gt0 * v[15];
-      gv[15] += -0.3162277660168379f * gt0 * g[8]; gg[8] += -0.3162277660168379f * gt0 * v[15];
-      gv[16] += -0.6324555320336758f * gt1 * g[4]; gg[4] += -0.6324555320336758f * gt1 * v[16];
-      gv[16] += 0.3162277660168379f * gt2 * g[5]; gg[5] += 0.3162277660168379f * gt2 * v[16];
-      gv[16] += 0.3162277660168379f * gt0 * g[7]; gg[7] += 0.3162277660168379f * gt0 * v[16];
+      const float s0_0 = 0.3162277660168379f * gt0;
+      gv[12] = fmaf(s0_0, g[5], gv[12]); gg[5] = fmaf(s0_0, v[12], gg[5]);
+      const float s2_0 = 0.3162277660168379f * gt2;
+      gv[12] = fmaf(-s2_0, g[7], gv[12]); gg[7] = fmaf(-s2_0, v[12], gg[7]);
+      const float s1_0 = 0.6324555320336758f * gt1;
+      gv[12] = fmaf(s1_0, g[8], gv[12]); gg[8] = fmaf(s1_0, v[12], gg[8]);
+      gv[13] = fmaf(-s0_0, g[4], gv[13]); gg[4] = fmaf(-s0_0, v[13], gg[4]);
+      const float s2_1 = 0.5477225575051661f * gt2;
+      gv[13] = fmaf(-s2_1, g[6], gv[13]); gg[6] = fmaf(-s2_1, v[13], gg[6]);
+      const float s1_1 = 0.3162277660168379f * gt1;
+      gv[13] = fmaf(s1_1, g[7], gv[13]); gg[7] = fmaf(s1_1, v[13], gg[7]);
+      gv[13] = fmaf(-s2_0, g[8], gv[13]); gg[8] = fmaf(-s2_0, v[13], gg[8]);
+      gv[14] = fmaf(s2_1, g[5], gv[14]); gg[5] = fmaf(s2_1, v[14], gg[5]);
+      const float s0_1 = 0.5477225575051661f * gt0;
+      gv[14] = fmaf(-s0_1, g[7], gv[14]); gg[7] = fmaf(-s0_1, v[14], gg[7]);
+      gv[15] = fmaf(s2_0, g[4], gv[15]); gg[4] = fmaf(s2_0, v[15], gg[4]);
+      gv[15] = fmaf(-s1_1, g[5], gv[15]); gg[5] = fmaf(-s1_1, v[15], gg[5]);
+      gv[15] = fmaf(s0_1, g[6], gv[15]); gg[6] = fmaf(s0_1, v[15], gg[6]);
+      gv[15] = fmaf(-s0_0, g[8], gv[15]); gg[8] = fmaf(-s0_0, v[15], gg[8]);
+      gv[16] = fmaf(-s1_0, g[4], gv[16]); gg[4] = fmaf(-s1_0, v[16], gg[4]);
+      gv[16] = fmaf(s2_0, g[5], gv[16]); gg[5] = fmaf(s2_0, v[16], gg[5]);
+      gv[16] = fmaf(s0_0, g[7], gv[16]); gg[7] = fmaf(s0_0, v[16], gg[7]);
     }
     { // path 26
-      const float w = th[26] * 0.4472135954999579f;
+      const float w = th[26 * TS];
       const float gt0 = w * gvo[13];
       const float gt1 = w * gvo[14];
       const float gt2 = w * gvo[15];
       const float gt3 = w * gvo[16];
       const float gt4 = w * gvo[17];
-      gv[12] += 0.5345224838248488f * gt2 * g[4]; gg[4] += 0.5345224838248488f * gt2 * v[12];
-      gv[12] += -0.4629100498862757f * gt3 * g[5]; gg[5] += -0.4629100498862757f * gt3 * v[12];
-      gv[12] += 0.5345224838248488f * gt0 * g[6]; gg[6] += 0.5345224838248488f * gt0 * v[12];
-      gv[12] += -0.4629100498862757f * gt1 * g[7]; gg[7] += -0.4629100498862757f * gt1 * v[12];
-      gv[13] += -0.4629100498862757f * gt3 * g[4]; gg[4] += -0.4629100498862757f * gt3 * v[13];
-      gv[13] += -0.2672612419124244f * gt2 * g[5]; gg[5] += -0.2672612419124244f * gt2 * v[13];
-      gv[13] += 0.4629100498862757f * gt4 * g[5]; gg[5] += 0.4629100498862757f * gt4 * v[13];
-      gv[13] += -0.2672612419124244f * gt1 * g[6]; gg[6] += -0.2672612419124244f * gt1 * v[13];
-      gv[13] += -0.4629100498862757f * gt0 * g[7]; gg[7] += -0.4629100498862757f * gt0 * v[13];
-      gv[13] += 0.4629100498862757f * gt1 * g[8]; gg[8] += 0.4629100498862757f * gt1 * v[13];
-      gv[14] += 0.5345224838248488f * gt0 * g[4]; gg[4] += 0.5345224838248488f * gt0 * v[14];
-      gv[14] += -0.2672612419124244f * gt1 * g[5]; gg[5] += -0.2672612419124244f * gt1 * v[14];
-      gv[14] += -0.5345224838248489f * gt2 * g[6]; gg[6] += -0.5345224838248489f * gt2 * v[14];
-      gv[14] += -0.2672612419124244f * gt3 * g[7]; gg[7] += -0.2672612419124244f * gt3 * v[14];
-      gv[14] += 0.5345224838248488f * gt4 * g[8]; gg[8] += 0.5345224838248488f * gt4 * v[14];
-      gv[15] += -0.4629100498862757f * gt1 * g[4]; gg[4] += -0.4629100498862757f * gt1 * v[15];
-      gv[15] += -0.4629100498862757f * gt0 * g[5]; gg[5] += -0.4629100498862757f * gt0 * v[15];
-      gv[15] += -0.2672612419124244f * gt3 * g[6]; gg[6] += -0.2672612419124244f * gt3 * v[15];
-      gv[15] += -0.2672612419124244f * gt2 * g[7]; gg[7] += -0.2672612419124244f * gt2 * v[15];
-      gv[15] += -0.4629100498862757f * gt4 * g[7]; gg[7] += -0.4629100498862757f * gt4 * v[15];
-      gv[15] += -0.4629100498862757f * gt3 * g[8]; gg[8] += -0.4629100498862757f * gt3 * v[15];
-      gv[16] += 0.4629100498862757f * gt1 * g[5]; gg[5] += 0.4629100498862757f * gt1 * v[16];
-      gv[16] += 0.5345224838248488f * gt4 * g[6]; gg[6] += 0.5345224838248488f * gt4 * v[16];
-      gv[16] += -0.4629100498862757f * gt3 * g[7]; gg[7] += -0.4629100498862757f * gt3 * v[16];
-      gv[16] += 0.5345224838248488f * gt2 * g[8]; gg[8] += 0.5345224838248488f * gt2 * v[16];
+      const float s2_0 = 0.5345224838248488f * gt2;
+      gv[12] = fmaf(s2_0, g[4], gv[12]); gg[4] = fmaf(s2_0, v[12], gg[4]);
+      const float s3_0 = 0.4629100498862757f * gt3;
+      gv[12] = fmaf(-s3_0, g[5], gv[12]); gg[5] = fmaf(-s3_0, v[12], gg[5]);
+      const float s0_0 = 0.5345224838248488f * gt0;
+      gv[12] = fmaf(s0_0, g[6], gv[12]); gg[6] = fmaf(s0_0, v[12], gg[6]);
+      const float s1_0 = 0.4629100498862757f * gt1;
+      gv[12] = fmaf(-s1_0, g[7], gv[12]); gg[7] = fmaf(-s1_0, v[12], gg[7]);
+      gv[13] = fmaf(-s3_0, g[4], gv[13]); gg[4] = fmaf(-s3_0, v[13], gg[4]);
+      const float s2_1 = 0.2672612419124244f * gt2;
+      gv[13] = fmaf(-s2_1, g[5], gv[13]); gg[5] = fmaf(-s2_1, v[13], gg[5]);
+      const float s4_0 = 0.4629100498862757f * gt4;
+      gv[13] = fmaf(s4_0, g[5], gv[13]); gg[5] = fmaf(s4_0, v[13], gg[5]);
+      const float s1_1 = 0.2672612419124244f * gt1;
+      gv[13] = fmaf(-s1_1, g[6], gv[13]); gg[6] = fmaf(-s1_1, v[13], gg[6]);
+      const float s0_1 = 0.4629100498862757f * gt0;
+      gv[13] = fmaf(-s0_1, g[7], gv[13]); gg[7] = fmaf(-s0_1, v[13], gg[7]);
+      gv[13] = fmaf(s1_0, g[8], gv[13]); gg[8] = fmaf(s1_0, v[13], gg[8]);
+      gv[14] = fmaf(s0_0, g[4], gv[14]); gg[4] = fmaf(s0_0, v[14], gg[4]);
+      gv[14] = fmaf(-s1_1, g[5], gv[14]); gg[5] = fmaf(-s1_1, v[14], gg[5]);
+      gv[14] = fmaf(-s2_0, g[6], gv[14]); gg[6] = fmaf(-s2_0, v[14], gg[6]);
+      const float s3_1 = 0.2672612419124244f * gt3;
+      gv[14] = fmaf(-s3_1, g[7], gv[14]); gg[7] = fmaf(-s3_1, v[14], gg[7]);
+      const float s4_1 = 0.5345224838248488f * gt4;
+      gv[14] = fmaf(s4_1, g[8], gv[14]); gg[8] = fmaf(s4_1, v[14], gg[8]);
+      gv[15] = fmaf(-s1_0, g[4], gv[15]); gg[4] = fmaf(-s1_0, v[15], gg[4]);
+      gv[15] = fmaf(-s0_1, g[5], gv[15]); gg[5] = fmaf(-s0_1, v[15], gg[5]);
+      gv[15] = fmaf(-s3_1, g[6], gv[15]); gg[6] = fmaf(-s3_1, v[15], gg[6]);
+      gv[15] = fmaf(-s2_1, g[7], gv[15]); gg[7] = fmaf(-s2_1, v[15], gg[7]);
+      gv[15] = fmaf(-s4_0, g[7], gv[15]); gg[7] = fmaf(-s4_0, v[15], gg[7]);
+      gv[15] = fmaf(-s3_0, g[8], gv[15]); gg[8] = fmaf(-s3_0, v[15], gg[8]);
+      gv[16] = fmaf(s1_0, g[5], gv[16]); gg[5] = fmaf(s1_0, v[16], gg[5]);
+      gv[16] = fmaf(s4_1, g[6], gv[16]); gg[6] = fmaf(s4_1, v[16], gg[6]);
+      gv[16] = fmaf(-s3_0, g[7], gv[16]); gg[7] = fmaf(-s3_0, v[16], gg[7]);
+      gv[16] = fmaf(s2_0, g[8], gv[16]); gg[8] = fmaf(s2_0, v[16], gg[8]);
     }
   }
   static constexpr int NNZ = 265;
@@ -1977,20 +2337,21 @@ template <> struct TP<2, 1, 0> {
 template <> struct TP<2, 1, 1> {
   // in irreps [(0, 1), (1, -1), (1, 1), (2, 1), (2, -1)]; out irreps [(0, 1), (1, -1), (2, 1)]
   static constexpr int NP = 27, DIN = 17, DOUT = 9, NS = 3, NPW = 27;
+  template <int TS>
   static __device__ __forceinline__ void fwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, float* s, float* vo) {
     #pragma unroll
     for (int k = 0; k < 9; ++k) vo[k] = 0.f;
     { // path 0: (0, 1) x (0,1) -> (0, 1)
       const float t0 = 1.0f * v[0] * g[0];
       s[0] = t0;
-      const float w = th[0] * 0.5773502691896258f;
+      const float w = th[0 * TS];
       vo[0] += w * t0;
     }
     { // path 1: (0, 1) x (1,-1) -> (1, -1)
       const float t0 = 0.9999999999999999f * v[0] * g[1];
       const float t1 = 1.0000000000000002f * v[0] * g[2];
       const float t2 = 0.9999999999999999f * v[0] * g[3];
-      const float w = th[1] * 0.4082482904638631f;
+      const float w = th[1 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
@@ -2001,7 +2362,7 @@ template <> struct TP<2, 1, 1> {
       const float t2 = 1.0000000000000002f * v[0] * g[6];
       const float t3 = 1.0f * v[0] * g[7];
       const float t4 = 1.0f * v[0] * g[8];
-      const float w = th[2] * 0.4082482904638631f;
+      const float w = th[2 * TS];
       vo[4] += w * t0;
       vo[5] += w * t1;
       vo[6] += w * t2;
@@ -2012,7 +2373,7 @@ template <> struct TP<2, 1, 1> {
       const float t0 = 0.9999999999999999f * v[1] * g[0];
       const float t1 = 1.0000000000000002f * v[2] * g[0];
       const float t2 = 0.9999999999999999f * v[3] * g[0];
-      const float w = th[3] * 0.4082482904638631f;
+      const float w = th[3 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
@@ -2020,7 +2381,7 @@ template <> struct TP<2, 1, 1> {
     { // path 4: (1, -1) x (1,-1) -> (0, 1)
       const float t0 = 0.5773502691896257f * v[1] * g[1] + 0.5773502691896258f * v[2] * g[2] + 0.5773502691896257f * v[3] * g[3];
       s[1] = t0;
-      const float w = th[4] * 0.5773502691896258f;
+      const float w = th[4 * TS];
       vo[0] += w * t0;
     }
     { // path 6: (1, -1) x (1,-1) -> (2, 1)
@@ -2029,7 +2390,7 @@ template <> struct TP<2, 1, 1> {
       const float t2 = 0.4082482904638631f * v[1] * g[1] + -0.8164965809277261f * v[2] * g[2] + 0.4082482904638631f * v[3] * g[3];
       const float t3 = -0.7071067811865476f * v[2] * g[3] + -0.7071067811865476f * v[3] * g[2];
       const float t4 = 0.7071067811865475f * v[1] * g[1] + -0.7071067811865475f * v[3] * g[3];
-      const float w = th[6] * 0.4082482904638631f;
+      const float w = th[6 * TS];
       vo[4] += w * t0;
       vo[5] += w * t1;
       vo[6] += w * t2;
@@ -2040,7 +2401,7 @@ template <> struct TP<2, 1, 1> {
       const float t0 = -0.3162277660168379f * v[1] * g[6] + -0.547722557505166f * v[1] * g[8] + 0.547722557505166f * v[2] * g[5] + 0.547722557505166f * v[3] * g[4];
       const float t1 = 0.547722557505166f * v[1] * g[5] + 0.632455532033676f * v[2] * g[6] + 0.547722557505166f * v[3] * g[7];
       const float t2 = 0.547722557505166f * v[1] * g[4] + 0.547722557505166f * v[2] * g[7] + -0.3162277660168379f * v[3] * g[6] + 0.547722557505166f * v[3] * g[8];
-      const float w = th[7] * 0.4082482904638631f;
+      const float w = th[7 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
@@ -2049,7 +2410,7 @@ template <> struct TP<2, 1, 1> {
       const float t0 = 0.7071067811865476f * v[5] * g[3] + -0.7071067811865476f * v[6] * g[2];
       const float t1 = -0.7071067811865476f * v[4] * g[3] + 0.7071067811865476f * v[6] * g[1];
       const float t2 = 0.7071067811865476f * v[4] * g[2] + -0.7071067811865476f * v[5] * g[1];
-      const float w = th[11] * 0.4082482904638631f;
+      const float w = th[11 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
@@ -2060,7 +2421,7 @@ template <> struct TP<2, 1, 1> {
       const float t2 = 0.7071067811865477f * v[4] * g[7] + -0.7071067811865477f * v[6] * g[5];
       const float t3 = -0.7071067811865477f * v[4] * g[6] + 0.408248290463863f * v[4] * g[8] + 0.408248290463863f * v[5] * g[5] + -0.408248290463863f * v[6] * g[4];
       const float t4 = -0.408248290463863f * v[4] * g[7] + 0.816496580927726f * v[5] * g[4] + -0.408248290463863f * v[6] * g[5];
-      const float w = th[14] * 0.4082482904638631f;
+      const float w = th[14 * TS];
       vo[4] += w * t0;
       vo[5] += w * t1;
       vo[6] += w * t2;
@@ -2073,7 +2434,7 @@ template <> struct TP<2, 1, 1> {
       const float t2 = 1.0000000000000002f * v[9] * g[0];
       const float t3 = 1.0f * v[10] * g[0];
       const float t4 = 1.0f * v[11] * g[0];
-      const float w = th[15] * 0.4082482904638631f;
+      const float w = th[15 * TS];
       vo[4] += w * t0;
       vo[5] += w * t1;
       vo[6] += w * t2;
@@ -2084,7 +2445,7 @@ template <> struct TP<2, 1, 1> {
       const float t0 = 0.547722557505166f * v[7] * g[3] + 0.547722557505166f * v[8] * g[2] + -0.3162277660168379f * v[9] * g[1] + -0.547722557505166f * v[11] * g[1];
       const float t1 = 0.547722557505166f * v[8] * g[1] + 0.632455532033676f * v[9] * g[2] + 0.547722557505166f * v[10] * g[3];
       const float t2 = 0.547722557505166f * v[7] * g[1] + -0.3162277660168379f * v[9] * g[3] + 0.547722557505166f * v[10] * g[2] + 0.547722557505166f * v[11] * g[3];
-      const float w = th[16] * 0.4082482904638631f;
+      const float w = th[16 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
@@ -2092,7 +2453,7 @@ template <> struct TP<2, 1, 1> {
     { // path 18: (2, 1) x (2,1) -> (0, 1)
       const float t0 = 0.4472135954999579f * v[7] * g[4] + 0.4472135954999579f * v[8] * g[5] + 0.44721359549995804f * v[9] * g[6] + 0.4472135954999579f * v[10] * g[7] + 0.4472135954999579f * v[11] * g[8];
       s[2] = t0;
-      const float w = th[18] * 0.5773502691896258f;
+      const float w = th[18 * TS];
       vo[0] += w * t0;
     }
     { // path 20: (2, 1) x (2,1) -> (2, 1)
@@ -2101,7 +2462,7 @@ template <> struct TP<2, 1, 1> {
       const float t2 = 0.5345224838248488f * v[7] * g[4] + -0.2672612419124244f * v[8] * g[5] + -0.5345224838248489f * v[9] * g[6] + -0.2672612419124244f * v[10] * g[7] + 0.5345224838248488f * v[11] * g[8];
       const float t3 = -0.4629100498862757f * v[7] * g[5] + -0.4629100498862757f * v[8] * g[4] + -0.2672612419124244f * v[9] * g[7] + -0.2672612419124244f * v[10] * g[6] + -0.4629100498862757f * v[10] * g[8] + -0.4629100498862757f * v[11] * g[7];
       const float t4 = 0.4629100498862757f * v[8] * g[5] + 0.5345224838248488f * v[9] * g[8] + -0.4629100498862757f * v[10] * g[7] + 0.5345224838248488f * v[11] * g[6];
-      const float w = th[20] * 0.4082482904638631f;
+      const float w = th[20 * TS];
       vo[4] += w * t0;
       vo[5] += w * t1;
       vo[6] += w * t2;
@@ -2114,7 +2475,7 @@ template <> struct TP<2, 1, 1> {
       const float t2 = -0.7071067811865477f * v[13] * g[3] + 0.7071067811865477f * v[15] * g[1];
       const float t3 = -0.408248290463863f * v[12] * g[3] + 0.408248290463863f * v[13] * g[2] + -0.7071067811865477f * v[14] * g[1] + 0.408248290463863f * v[16] * g[1];
       const float t4 = 0.816496580927726f * v[12] * g[2] + -0.408248290463863f * v[13] * g[3] + -0.408248290463863f * v[15] * g[1];
-      const float w = th[23] * 0.4082482904638631f;
+      const float w = th[23 * TS];
       vo[4] += w * t0;
       vo[5] += w * t1;
       vo[6] += w * t2;
@@ -2125,245 +2486,320 @@ template <> struct TP<2, 1, 1> {
       const float t0 = 0.3162277660168379f * v[12] * g[5] + -0.3162277660168379f * v[13] * g[4] + -0.5477225575051661f * v[14] * g[7] + 0.5477225575051661f * v[15] * g[6] + -0.3162277660168379f * v[15] * g[8] + 0.3162277660168379f * v[16] * g[7];
       const float t1 = 0.6324555320336758f * v[12] * g[8] + 0.3162277660168379f * v[13] * g[7] + -0.3162277660168379f * v[15] * g[5] + -0.6324555320336758f * v[16] * g[4];
       const float t2 = -0.3162277660168379f * v[12] * g[7] + -0.5477225575051661f * v[13] * g[6] + -0.3162277660168379f * v[13] * g[8] + 0.5477225575051661f * v[14] * g[5] + 0.3162277660168379f * v[15] * g[4] + 0.3162277660168379f * v[16] * g[5];
-      const float w = th[25] * 0.4082482904638631f;
+      const float w = th[25 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
     }
   }
+  template <int TS>
   static __device__ __forceinline__ void bwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, const float* __restrict__ gs, const float* __restrict__ gvo, float* gv, float* gg) {
     { // path 0
-      const float w = th[0] * 0.5773502691896258f;
+      const float w = th[0 * TS];
       const float gt0 = gs[0] + w * gvo[0];
-      gv[0] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[0];
+      const float s0_0 = gt0;
+      gv[0] = fmaf(s0_0, g[0], gv[0]); gg[0] = fmaf(s0_0, v[0], gg[0]);
     }
     { // path 1
-      const float w = th[1] * 0.4082482904638631f;
+      const float w = th[1 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[0] += 0.9999999999999999f * gt0 * g[1]; gg[1] += 0.9999999999999999f * gt0 * v[0];
-      gv[0] += 1.0000000000000002f * gt1 * g[2]; gg[2] += 1.0000000000000002f * gt1 * v[0];
-      gv[0] += 0.9999999999999999f * gt2 * g[3]; gg[3] += 0.9999999999999999f * gt2 * v[0];
+      const float s0_0 = gt0;
+      gv[0] = fmaf(s0_0, g[1], gv[0]); gg[1] = fmaf(s0_0, v[0], gg[1]);
+      const float s1_0 = gt1;
+      gv[0] = fmaf(s1_0, g[2], gv[0]); gg[2] = fmaf(s1_0, v[0], gg[2]);
+      const float s2_0 = gt2;
+      gv[0] = fmaf(s2_0, g[3], gv[0]); gg[3] = fmaf(s2_0, v[0], gg[3]);
     }
     { // path 2
-      const float w = th[2] * 0.4082482904638631f;
+      const float w = th[2 * TS];
       const float gt0 = w * gvo[4];
       const float gt1 = w * gvo[5];
       const float gt2 = w * gvo[6];
       const float gt3 = w * gvo[7];
       const float gt4 = w * gvo[8];
-      gv[0] += 1.0f * gt0 * g[4]; gg[4] += 1.0f * gt0 * v[0];
-      gv[0] += 1.0f * gt1 * g[5]; gg[5] += 1.0f * gt1 * v[0];
-      gv[0] += 1.0000000000000002f * gt2 * g[6]; gg[6] += 1.0000000000000002f * gt2 * v[0];
-      gv[0] += 1.0f * gt3 * g[7]; gg[7] += 1.0f * gt3 * v[0];
-      gv[0] += 1.0f * gt4 * g[8]; gg[8] += 1.0f * gt4 * v[0];
+      const float s0_0 = gt0;
+      gv[0] = fmaf(s0_0, g[4], gv[0]); gg[4] = fmaf(s0_0, v[0], gg[4]);
+      const float s1_0 = gt1;
+      gv[0] = fmaf(s1_0, g[5], gv[0]); gg[5] = fmaf(s1_0, v[0], gg[5]);
+      const float s2_0 = gt2;
+      gv[0] = fmaf(s2_0, g[6], gv[0]); gg[6] = fmaf(s2_0, v[0], gg[6]);
+      const float s3_0 = gt3;
+      gv[0] = fmaf(s3_0, g[7], gv[0]); gg[7] = fmaf(s3_0, v[0], gg[7]);
+      const float s4_0 = gt4;
+      gv[0] = fmaf(s4_0, g[8], gv[0]); gg[8] = fmaf(s4_0, v[0], gg[8]);
     }
     { // path 3
-      const float w = th[3] * 0.4082482904638631f;
+      const float w = th[3 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[1] += 0.9999999999999999f * gt0 * g[0]; gg[0] += 0.9999999999999999f * gt0 * v[1];
-      gv[2] += 1.0000000000000002f * gt1 * g[0]; gg[0] += 1.0000000000000002f * gt1 * v[2];
-      gv[3] += 0.9999999999999999f * gt2 * g[0]; gg[0] += 0.9999999999999999f * gt2 * v[3];
+      const float s0_0 = gt0;
+      gv[1] = fmaf(s0_0, g[0], gv[1]); gg[0] = fmaf(s0_0, v[1], gg[0]);
+      const float s1_0 = gt1;
+      gv[2] = fmaf(s1_0, g[0], gv[2]); gg[0] = fmaf(s1_0, v[2], gg[0]);
+      const float s2_0 = gt2;
+      gv[3] = fmaf(s2_0, g[0], gv[3]); gg[0] = fmaf(s2_0, v[3], gg[0]);
     }
     { // path 4
-      const float w = th[4] * 0.5773502691896258f;
+      const float w = th[4 * TS];
       const float gt0 = gs[1] + w * gvo[0];
-      gv[1] += 0.5773502691896257f * gt0 * g[1]; gg[1] += 0.5773502691896257f * gt0 * v[1];
-      gv[2] += 0.5773502691896258f * gt0 * g[2]; gg[2] += 0.5773502691896258f * gt0 * v[2];
-      gv[3] += 0.5773502691896257f * gt0 * g[3]; gg[3] += 0.5773502691896257f * gt0 * v[3];
+      const float s0_0 = 0.5773502691896257f * gt0;
+      gv[1] = fmaf(s0_0, g[1], gv[1]); gg[1] = fmaf(s0_0, v[1], gg[1]);
+      gv[2] = fmaf(s0_0, g[2], gv[2]); gg[2] = fmaf(s0_0, v[2], gg[2]);
+      gv[3] = fmaf(s0_0, g[3], gv[3]); gg[3] = fmaf(s0_0, v[3], gg[3]);
     }
     { // path 6
-      const float w = th[6] * 0.4082482904638631f;
+      const float w = th[6 * TS];
       const float gt0 = w * gvo[4];
       const float gt1 = w * gvo[5];
       const float gt2 = w * gvo[6];
       const float gt3 = w * gvo[7];
       const float gt4 = w * gvo[8];
-      gv[1] += 0.4082482904638631f * gt2 * g[1]; gg[1] += 0.4082482904638631f * gt2 * v[1];
-      gv[1] += 0.7071067811865475f * gt4 * g[1]; gg[1] += 0.7071067811865475f * gt4 * v[1];
-      gv[1] += -0.7071067811865476f * gt1 * g[2]; gg[2] += -0.7071067811865476f * gt1 * v[1];
-      gv[1] += -0.7071067811865475f * gt0 * g[3]; gg[3] += -0.7071067811865475f * gt0 * v[1];
-      gv[2] += -0.7071067811865476f * gt1 * g[1]; gg[1] += -0.7071067811865476f * gt1 * v[2];
-      gv[2] += -0.8164965809277261f * gt2 * g[2]; gg[2] += -0.8164965809277261f * gt2 * v[2];
-      gv[2] += -0.7071067811865476f * gt3 * g[3]; gg[3] += -0.7071067811865476f * gt3 * v[2];
-      gv[3] += -0.7071067811865475f * gt0 * g[1]; gg[1] += -0.7071067811865475f * gt0 * v[3];
-      gv[3] += -0.7071067811865476f * gt3 * g[2]; gg[2] += -0.7071067811865476f * gt3 * v[3];
-      gv[3] += 0.4082482904638631f * gt2 * g[3]; gg[3] += 0.4082482904638631f * gt2 * v[3];
-      gv[3] += -0.7071067811865475f * gt4 * g[3]; gg[3] += -0.7071067811865475f * gt4 * v[3];
+      const float s2_0 = 0.4082482904638631f * gt2;
+      gv[1] = fmaf(s2_0, g[1], gv[1]); gg[1] = fmaf(s2_0, v[1], gg[1]);
+      const float s4_0 = 0.7071067811865475f * gt4;
+      gv[1] = fmaf(s4_0, g[1], gv[1]); gg[1] = fmaf(s4_0, v[1], gg[1]);
+      const float s1_0 = 0.7071067811865476f * gt1;
+      gv[1] = fmaf(-s1_0, g[2], gv[1]); gg[2] = fmaf(-s1_0, v[1], gg[2]);
+      const float s0_0 = 0.7071067811865475f * gt0;
+      gv[1] = fmaf(-s0_0, g[3], gv[1]); gg[3] = fmaf(-s0_0, v[1], gg[3]);
+      gv[2] = fmaf(-s1_0, g[1], gv[2]); gg[1] = fmaf(-s1_0, v[2], gg[1]);
+      const float s2_1 = 0.8164965809277261f * gt2;
+      gv[2] = fmaf(-s2_1, g[2], gv[2]); gg[2] = fmaf(-s2_1, v[2], gg[2]);
+      const float s3_0 = 0.7071067811865476f * gt3;
+      gv[2] = fmaf(-s3_0, g[3], gv[2]); gg[3] = fmaf(-s3_0, v[2], gg[3]);
+      gv[3] = fmaf(-s0_0, g[1], gv[3]); gg[1] = fmaf(-s0_0, v[3], gg[1]);
+      gv[3] = fmaf(-s3_0, g[2], gv[3]); gg[2] = fmaf(-s3_0, v[3], gg[2]);
+      gv[3] = fmaf(s2_0, g[3], gv[3]); gg[3] = fmaf(s2_0, v[3], gg[3]);
+      gv[3] = fmaf(-s4_0, g[3], gv[3]); gg[3] = fmaf(-s4_0, v[3], gg[3]);
     }
     { // path 7
-      const float w = th[7] * 0.4082482904638631f;
+      const float w = th[7 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[1] += 0.547722557505166f * gt2 * g[4]; gg[4] += 0.547722557505166f * gt2 * v[1];
-      gv[1] += 0.547722557505166f * gt1 * g[5]; gg[5] += 0.547722557505166f * gt1 * v[1];
-      gv[1] += -0.3162277660168379f * gt0 * g[6]; gg[6] += -0.3162277660168379f * gt0 * v[1];
-      gv[1] += -0.547722557505166f * gt0 * g[8]; gg[8] += -0.547722557505166f * gt0 * v[1];
-      gv[2] += 0.547722557505166f * gt0 * g[5]; gg[5] += 0.547722557505166f * gt0 * v[2];
-      gv[2] += 0.632455532033676f * gt1 * g[6]; gg[6] += 0.632455532033676f * gt1 * v[2];
-      gv[2] += 0.547722557505166f * gt2 * g[7]; gg[7] += 0.547722557505166f * gt2 * v[2];
-      gv[3] += 0.547722557505166f * gt0 * g[4]; gg[4] += 0.547722557505166f * gt0 * v[3];
-      gv[3] += -0.3162277660168379f * gt2 * g[6]; gg[6] += -0.3162277660168379f * gt2 * v[3];
-      gv[3] += 0.547722557505166f * gt1 * g[7]; gg[7] += 0.547722557505166f * gt1 * v[3];
-      gv[3] += 0.547722557505166f * gt2 * g[8]; gg[8] += 0.547722557505166f * gt2 * v[3];
+      const float s2_0 = 0.547722557505166f * gt2;
+      gv[1] = fmaf(s2_0, g[4], gv[1]); gg[4] = fmaf(s2_0, v[1], gg[4]);
+      const float s1_0 = 0.547722557505166f * gt1;
+      gv[1] = fmaf(s1_0, g[5], gv[1]); gg[5] = fmaf(s1_0, v[1], gg[5]);
+      const float s0_0 = 0.3162277660168379f * gt0;
+      gv[1] = fmaf(-s0_0, g[6], gv[1]); gg[6] = fmaf(-s0_0, v[1], gg[6]);
+      const float s0_1 = 0.547722557505166f * gt0;
+      gv[1] = fmaf(-s0_1, g[8], gv[1]); gg[8] = fmaf(-s0_1, v[1], gg[8]);
+      gv[2] = fmaf(s0_1, g[5], gv[2]); gg[5] = fmaf(s0_1, v[2], gg[5]);
+      const float s1_1 = 0.632455532033676f * gt1;
+      gv[2] = fmaf(s1_1, g[6], gv[2]); gg[6] = fmaf(s1_1, v[2], gg[6]);
+      gv[2] = fmaf(s2_0, g[7], gv[2]); gg[7] = fmaf(s2_0, v[2], gg[7]);
+      gv[3] = fmaf(s0_1, g[4], gv[3]); gg[4] = fmaf(s0_1, v[3], gg[4]);
+      const float s2_1 = 0.3162277660168379f * gt2;
+      gv[3] = fmaf(-s2_1, g[6], gv[3]); gg[6] = fmaf(-s2_1, v[3], gg[6]);
+      gv[3] = fmaf(s1_0, g[7], gv[3]); gg[7] = fmaf(s1_0, v[3], gg[7]);
+      gv[3] = fmaf(s2_0, g[8], gv[3]); gg[8] = fmaf(s2_0, v[3], gg[8]);
     }
     { // path 11
-      const float w = th[11] * 0.4082482904638631f;
+      const float w = th[11 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[4] += 0.7071067811865476f * gt2 * g[2]; gg[2] += 0.7071067811865476f * gt2 * v[4];
-      gv[4] += -0.7071067811865476f * gt1 * g[3]; gg[3] += -0.7071067811865476f * gt1 * v[4];
-      gv[5] += -0.7071067811865476f * gt2 * g[1]; gg[1] += -0.7071067811865476f * gt2 * v[5];
-      gv[5] += 0.7071067811865476f * gt0 * g[3]; gg[3] += 0.7071067811865476f * gt0 * v[5];
-      gv[6] += 0.7071067811865476f * gt1 * g[1]; gg[1] += 0.7071067811865476f * gt1 * v[6];
-      gv[6] += -0.7071067811865476f * gt0 * g[2]; gg[2] += -0.7071067811865476f * gt0 * v[6];
+      const float s2_0 = 0.7071067811865476f * gt2;
+      gv[4] = fmaf(s2_0, g[2], gv[4]); gg[2] = fmaf(s2_0, v[4], gg[2]);
+      const float s1_0 = 0.7071067811865476f * gt1;
+      gv[4] = fmaf(-s1_0, g[3], gv[4]); gg[3] = fmaf(-s1_0, v[4], gg[3]);
+      gv[5] = fmaf(-s2_0, g[1], gv[5]); gg[1] = fmaf(-s2_0, v[5], gg[1]);
+      const float s0_0 = 0.7071067811865476f * gt0;
+      gv[5] = fmaf(s0_0, g[3], gv[5]); gg[3] = fmaf(s0_0, v[5], gg[3]);
+      gv[6] = fmaf(s1_0, g[1], gv[6]); gg[1] = fmaf(s1_0, v[6], gg[1]);
+      gv[6] = fmaf(-s0_0, g[2], gv[6]); gg[2] = fmaf(-s0_0, v[6], gg[2]);
     }
     { // path 14
-      const float w = th[14] * 0.4082482904638631f;
+      const float w = th[14 * TS];
       const float gt0 = w * gvo[4];
       const float gt1 = w * gvo[5];
       const float gt2 = w * gvo[6];
       const float gt3 = w * gvo[7];
       const float gt4 = w * gvo[8];
-      gv[4] += 0.408248290463863f * gt1 * g[4]; gg[4] += 0.408248290463863f * gt1 * v[4];
-      gv[4] += -0.408248290463863f * gt0 * g[5]; gg[5] += -0.408248290463863f * gt0 * v[4];
-      gv[4] += -0.7071067811865477f * gt3 * g[6]; gg[6] += -0.7071067811865477f * gt3 * v[4];
-      gv[4] += 0.7071067811865477f * gt2 * g[7]; gg[7] += 0.7071067811865477f * gt2 * v[4];
-      gv[4] += -0.408248290463863f * gt4 * g[7]; gg[7] += -0.408248290463863f * gt4 * v[4];
-      gv[4] += 0.408248290463863f * gt3 * g[8]; gg[8] += 0.408248290463863f * gt3 * v[4];
-      gv[5] += 0.816496580927726f * gt4 * g[4]; gg[4] += 0.816496580927726f * gt4 * v[5];
-      gv[5] += 0.408248290463863f * gt3 * g[5]; gg[5] += 0.408248290463863f * gt3 * v[5];
-      gv[5] += -0.408248290463863f * gt1 * g[7]; gg[7] += -0.408248290463863f * gt1 * v[5];
-      gv[5] += -0.816496580927726f * gt0 * g[8]; gg[8] += -0.816496580927726f * gt0 * v[5];
-      gv[6] += -0.408248290463863f * gt3 * g[4]; gg[4] += -0.408248290463863f * gt3 * v[6];
-      gv[6] += -0.7071067811865477f * gt2 * g[5]; gg[5] += -0.7071067811865477f * gt2 * v[6];
-      gv[6] += -0.408248290463863f * gt4 * g[5]; gg[5] += -0.408248290463863f * gt4 * v[6];
-      gv[6] += 0.7071067811865477f * gt1 * g[6]; gg[6] += 0.7071067811865477f * gt1 * v[6];
-      gv[6] += 0.408248290463863f * gt0 * g[7]; gg[7] += 0.408248290463863f * gt0 * v[6];
-      gv[6] += 0.408248290463863f * gt1 * g[8]; gg[8] += 0.408248290463863f * gt1 * v[6];
+      const float s1_0 = 0.408248290463863f * gt1;
+      gv[4] = fmaf(s1_0, g[4], gv[4]); gg[4] = fmaf(s1_0, v[4], gg[4]);
+      const float s0_0 = 0.408248290463863f * gt0;
+      gv[4] = fmaf(-s0_0, g[5], gv[4]); gg[5] = fmaf(-s0_0, v[4], gg[5]);
+      const float s3_0 = 0.7071067811865477f * gt3;
+      gv[4] = fmaf(-s3_0, g[6], gv[4]); gg[6] = fmaf(-s3_0, v[4], gg[6]);
+      const float s2_0 = 0.7071067811865477f * gt2;
+      gv[4] = fmaf(s2_0, g[7], gv[4]); gg[7] = fmaf(s2_0, v[4], gg[7]);
+      const float s4_0 = 0.408248290463863f * gt4;
+      gv[4] = fmaf(-s4_0, g[7], gv[4]); gg[7] = fmaf(-s4_0, v[4], gg[7]);
+      const float s3_1 = 0.408248290463863f * gt3;
+      gv[4] = fmaf(s3_1, g[8], gv[4]); gg[8] = fmaf(s3_1, v[4], gg[8]);
+      const float s4_1 = 0.816496580927726f * gt4;
+      gv[5] = fmaf(s4_1, g[4], gv[5]); gg[4] = fmaf(s4_1, v[5], gg[4]);
+      gv[5] = fmaf(s3_1, g[5], gv[5]); gg[5] = fmaf(s3_1, v[5], gg[5]);
+      gv[5] = fmaf(-s1_0, g[7], gv[5]); gg[7] = fmaf(-s1_0, v[5], gg[7]);
+      const float s0_1 = 0.816496580927726f * gt0;
+      gv[5] = fmaf(-s0_1, g[8], gv[5]); gg[8] = fmaf(-s0_1, v[5], gg[8]);
+      gv[6] = fmaf(-s3_1, g[4], gv[6]); gg[4] = fmaf(-s3_1, v[6], gg[4]);
+      gv[6] = fmaf(-s2_0, g[5], gv[6]); gg[5] = fmaf(-s2_0, v[6], gg[5]);
+      gv[6] = fmaf(-s4_0, g[5], gv[6]); gg[5] = fmaf(-s4_0, v[6], gg[5]);
+      const float s1_1 = 0.7071067811865477f * gt1;
+      gv[6] = fmaf(s1_1, g[6], gv[6]); gg[6] = fmaf(s1_1, v[6], gg[6]);
+      gv[6] = fmaf(s0_0, g[7], gv[6]); gg[7] = fmaf(s0_0, v[6], gg[7]);
+      gv[6] = fmaf(s1_0, g[8], gv[6]); gg[8] = fmaf(s1_0, v[6], gg[8]);
     }
     { // path 15
-      const float w = th[15] * 0.4082482904638631f;
+      const float w = th[15 * TS];
       const float gt0 = w * gvo[4];
       const float gt1 = w * gvo[5];
       const float gt2 = w * gvo[6];
       const float gt3 = w * gvo[7];
       const float gt4 = w * gvo[8];
-      gv[7] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[7];
-      gv[8] += 1.0f * gt1 * g[0]; gg[0] += 1.0f * gt1 * v[8];
-      gv[9] += 1.0000000000000002f * gt2 * g[0]; gg[0] += 1.0000000000000002f * gt2 * v[9];
-      gv[10] += 1.0f * gt3 * g[0]; gg[0] += 1.0f * gt3 * v[10];
-      gv[11] += 1.0f * gt4 * g[0]; gg[0] += 1.0f * gt4 * v[11];
+      const float s0_0 = gt0;
+      gv[7] = fmaf(s0_0, g[0], gv[7]); gg[0] = fmaf(s0_0, v[7], gg[0]);
+      const float s1_0 = gt1;
+      gv[8] = fmaf(s1_0, g[0], gv[8]); gg[0] = fmaf(s1_0, v[8], gg[0]);
+      const float s2_0 = gt2;
+      gv[9] = fmaf(s2_0, g[0], gv[9]); gg[0] = fmaf(s2_0, v[9], gg[0]);
+      const float s3_0 = gt3;
+      gv[10] = fmaf(s3_0, g[0], gv[10]); gg[0] = fmaf(s3_0, v[10], gg[0]);
+      const float s4_0 = gt4;
+      gv[11] = fmaf(s4_0, g[0], gv[11]); gg[0] = fmaf(s4_0, v[11], gg[0]);
     }
     { // path 16
-      const float w = th[16] * 0.4082482904638631f;
+      const float w = th[16 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[7] += 0.547722557505166f * gt2 * g[1]; gg[1] += 0.547722557505166f * gt2 * v[7];
-      gv[7] += 0.547722557505166f * gt0 * g[3]; gg[3] += 0.547722557505166f * gt0 * v[7];
-      gv[8] += 0.547722557505166f * gt1 * g[1]; gg[1] += 0.547722557505166f * gt1 * v[8];
-      gv[8] += 0.547722557505166f * gt0 * g[2]; gg[2] += 0.547722557505166f * gt0 * v[8];
-      gv[9] += -0.3162277660168379f * gt0 * g[1]; gg[1] += -0.3162277660168379f * gt0 * v[9];
-      gv[9] += 0.632455532033676f * gt1 * g[2]; gg[2] += 0.632455532033676f * gt1 * v[9];
-      gv[9] += -0.3162277660168379f * gt2 * g[3]; gg[3] += -0.3162277660168379f * gt2 * v[9];
-      gv[10] += 0.547722557505166f * gt2 * g[2]; gg[2] += 0.547722557505166f * gt2 * v[10];
-      gv[10] += 0.547722557505166f * gt1 * g[3]; gg[3] += 0.547722557505166f * gt1 * v[10];
-      gv[11] += -0.547722557505166f * gt0 * g[1]; gg[1] += -0.547722557505166f * gt0 * v[11];
-      gv[11] += 0.547722557505166f * gt2 * g[3]; gg[3] += 0.547722557505166f * gt2 * v[11];
+      const float s2_0 = 0.547722557505166f * gt2;
+      gv[7] = fmaf(s2_0, g[1], gv[7]); gg[1] = fmaf(s2_0, v[7], gg[1]);
+      const float s0_0 = 0.547722557505166f * gt0;
+      gv[7] = fmaf(s0_0, g[3], gv[7]); gg[3] = fmaf(s0_0, v[7], gg[3]);
+      const float s1_0 = 0.547722557505166f * gt1;
+      gv[8] = fmaf(s1_0, g[1], gv[8]); gg[1] = fmaf(s1_0, v[8], gg[1]);
+      gv[8] = fmaf(s0_0, g[2], gv[8]); gg[2] = fmaf(s0_0, v[8], gg[2]);
+      const float s0_1 = 0.3162277660168379f * gt0;
+      gv[9] = fmaf(-s0_1, g[1], gv[9]); gg[1] = fmaf(-s0_1, v[9], gg[1]);
+      const float s1_1 = 0.632455532033676f * gt1;
+      gv[9] = fmaf(s1_1, g[2], gv[9]); gg[2] = fmaf(s1_1, v[9], gg[2]);
+      const float s2_1 = 0.3162277660168379f * gt2;
+      gv[9] = fmaf(-s2_1, g[3], gv[9]); gg[3] = fmaf(-s2_1, v[9], gg[3]);
+      gv[10] = fmaf(s2_0, g[2], gv[10]); gg[2] = fmaf(s2_0, v[10], gg[2]);
+      gv[10] = fmaf(s1_0, g[3], gv[10]); gg[3] = fmaf(s1_0, v[10], gg[3]);
+      gv[11] = fmaf(-s0_0, g[1], gv[11]); gg[1] = fmaf(-s0_0, v[11], gg[1]);
+      gv[11] = fmaf(s2_0, g[3], gv[11]); gg[3] = fmaf(s2_0, v[11], gg[3]);
     }
     { // path 18
-      const float w = th[18] * 0.5773502691896258f;
+      const float w = th[18 * TS];
       const float gt0 = gs[2] + w * gvo[0];
-      gv[7] += 0.4472135954999579f * gt0 * g[4]; gg[4] += 0.4472135954999579f * gt0 * v[7];
-      gv[8] += 0.4472135954999579f * gt0 * g[5]; gg[5] += 0.4472135954999579f * gt0 * v[8];
-      gv[9] += 0.44721359549995804f * gt0 * g[6]; gg[6] += 0.44721359549995804f * gt0 * v[9];
-      gv[10] += 0.4472135954999579f * gt0 * g[7]; gg[7] += 0.4472135954999579f * gt0 * v[10];
-      gv[11] += 0.4472135954999579f * gt0 * g[8]; gg[8] += 0.4472135954999579f * gt0 * v[11];
+      const float s0_0 = 0.4472135954999579f * gt0;
+      gv[7] = fmaf(s0_0, g[4], gv[7]); gg[4] = fmaf(s0_0, v[7], gg[4]);
+      gv[8] = fmaf(s0_0, g[5], gv[8]); gg[5] = fmaf(s0_0, v[8], gg[5]);
+      gv[9] = fmaf(s0_0, g[6], gv[9]); gg[6] = fmaf(s0_0, v[9], gg[6]);
+      gv[10] = fmaf(s0_0, g[7], gv[10]); gg[7] = fmaf(s0_0, v[10], gg[7]);
+      gv[11] = fmaf(s0_0, g[8], gv[11]); gg[8] = fmaf(s0_0, v[11], gg[8]);
     }
     { // path 20
-      const float w = th[20] * 0.4082482904638631f;
+      const float w = th[20 * TS];
       const float gt0 = w * gvo[4];
       const float gt1 = w * gvo[5];
       const float gt2 = w * gvo[6];
       const float gt3 = w * gvo[7];
       const float gt4 = w * gvo[8];
-      gv[7] += 0.5345224838248488f * gt2 * g[4]; gg[4] += 0.5345224838248488f * gt2 * v[7];
-      gv[7] += -0.4629100498862757f * gt3 * g[5]; gg[5] += -0.4629100498862757f * gt3 * v[7];
-      gv[7] += 0.5345224838248488f * gt0 * g[6]; gg[6] += 0.5345224838248488f * gt0 * v[7];
-      gv[7] += -0.4629100498862757f * gt1 * g[7]; gg[7] += -0.4629100498862757f * gt1 * v[7];
-      gv[8] += -0.4629100498862757f * gt3 * g[4]; gg[4] += -0.4629100498862757f * gt3 * v[8];
-      gv[8] += -0.2672612419124244f * gt2 * g[5]; gg[5] += -0.2672612419124244f * gt2 * v[8];
-      gv[8] += 0.4629100498862757f * gt4 * g[5]; gg[5] += 0.4629100498862757f * gt4 * v[8];
-      gv[8] += -0.2672612419124244f * gt1 * g[6]; gg[6] += -0.2672612419124244f * gt1 * v[8];
-      gv[8] += -0.4629100498862757f * gt0 * g[7]; gg[7] += -0.4629100498862757f * gt0 * v[8];
-      gv[8] += 0.4629100498862757f * gt1 * g[8]; gg[8] += 0.4629100498862757f * gt1 * v[8];
-      gv[9] += 0.5345224838248488f * gt0 * g[4]; gg[4] += 0.5345224838248488f * gt0 * v[9];
-      gv[9] += -0.2672612419124244f * gt1 * g[5]; gg[5] += -0.2672612419124244f * gt1 * v[9];
-      gv[9] += -0.5345224838248489f * gt2 * g[6]; gg[6] += -0.5345224838248489f * gt2 * v[9];
-      gv[9] += -0.2672612419124244f * gt3 * g[7]; gg[7] += -0.2672612419124244f * gt3 * v[9];
-      gv[9] += 0.5345224838248488f * gt4 * g[8]; gg[8] += 0.5345224838248488f * gt4 * v[9];
-      gv[10] += -0.4629100498862757f * gt1 * g[4]; gg[4] += -0.4629100498862757f * gt1 * v[10];
-      gv[10] += -0.4629100498862757f * gt0 * g[5]; gg[5] += -0.4629100498862757f * gt0 * v[10];
-      gv[10] += -0.2672612419124244f * gt3 * g[6]; gg[6] += -0.2672612419124244f * gt3 * v[10];
-      gv[10] += -0.2672612419124244f * gt2 * g[7]; gg[7] += -0.2672612419124244f * gt2 * v[10];
-      gv[10] += -0.4629100498862757f * gt4 * g[7]; gg[7] += -0.4629100498862757f * gt4 * v[10];
-      gv[10] += -0.4629100498862757f * gt3 * g[8]; gg[8] += -0.4629100498862757f * gt3 * v[10];
-      gv[11] += 0.4629100498862757f * gt1 * g[5]; gg[5] += 0.4629100498862757f * gt1 * v[11];
-      gv[11] += 0.5345224838248488f * gt4 * g[6]; gg[6] += 0.5345224838248488f * gt4 * v[11];
-      gv[11] += -0.4629100498862757f * gt3 * g[7]; gg[7] += -0.4629100498862757f * gt3 * v[11];
-      gv[11] += 0.5345224838248488f * gt2 * g[8]; gg[8] += 0.5345224838248488f * gt2 * v[11];
+      const float s2_0 = 0.5345224838248488f * gt2;
+      gv[7] = fmaf(s2_0, g[4], gv[7]); gg[4] = fmaf(s2_0, v[7], gg[4]);
+      const float s3_0 = 0.4629100498862757f * gt3;
+      gv[7] = fmaf(-s3_0, g[5], gv[7]); gg[5] = fmaf(-s3_0, v[7], gg[5]);
+      const float s0_0 = 0.5345224838248488f * gt0;
+      gv[7] = fmaf(s0_0, g[6], gv[7]); gg[6] = fmaf(s0_0, v[7], gg[6]);
+      const float s1_0 = 0.4629100498862757f * gt1;
+      gv[7] = fmaf(-s1_0, g[7], gv[7]); gg[7] = fmaf(-s1_0, v[7], gg[7]);
+      gv[8] = fmaf(-s3_0, g[4], gv[8]); gg[4] = fmaf(-s3_0, v[8], gg[4]);
+      const float s2_1 = 0.2672612419124244f * gt2;
+      gv[8] = fmaf(-s2_1, g[5], gv[8]); gg[5] = fmaf(-s2_1, v[8], gg[5]);
+      const float s4_0 = 0.4629100498862757f * gt4;
+      gv[8] = fmaf(s4_0, g[5], gv[8]); gg[5] = fmaf(s4_0, v[8], gg[5]);
+      const float s1_1 = 0.2672612419124244f * gt1;
+      gv[8] = fmaf(-s1_1, g[6], gv[8]); gg[6] = fmaf(-s1_1, v[8], gg[6]);
+      const float s0_1 = 0.4629100498862757f * gt0;
+      gv[8] = fmaf(-s0_1, g[7], gv[8]); gg[7] = fmaf(-s0_1, v[8], gg[7]);
+      gv[8] = fmaf(s1_0, g[8], gv[8]); gg[8] = fmaf(s1_0, v[8], gg[8]);
+      gv[9] = fmaf(s0_0, g[4], gv[9]); gg[4] = fmaf(s0_0, v[9], gg[4]);
+      gv[9] = fmaf(-s1_1, g[5], gv[9]); gg[5] = fmaf(-s1_1, v[9], gg[5]);
+      gv[9] = fmaf(-s2_0, g[6], gv[9]); gg[6] = fmaf(-s2_0, v[9], gg[6]);
+      const float s3_1 = 0.2672612419124244f * gt3;
+      gv[9] = fmaf(-s3_1, g[7], gv[9]); gg[7] = fmaf(-s3_1, v[9], gg[7]);
+      const float s4_1 = 0.5345224838248488f * gt4;
+      gv[9] = fmaf(s4_1, g[8], gv[9]); gg[8] = fmaf(s4_1, v[9], gg[8]);
+      gv[10] = fmaf(-s1_0, g[4], gv[10]); gg[4] = fmaf(-s1_0, v[10], gg[4]);
+      gv[10] = fmaf(-s0_1, g[5], gv[10]); gg[5] = fmaf(-s0_1, v[10], gg[5]);
+      gv[10] = fmaf(-s3_1, g[6], gv[10]); gg[6] = fmaf(-s3_1, v[10], gg[6]);
+      gv[10] = fmaf(-s2_1, g[7], gv[10]); gg[7] = fmaf(-s2_1, v[10], gg[7]);
+      gv[10] = fmaf(-s4_0, g[7], gv[10]); gg[7] = fmaf(-s4_0, v[10], gg[7]);
+      gv[10] = fmaf(-s3_0, g[8], gv[10]); gg[8] = fmaf(-s3_0, v[10], gg[8]);
+      gv[11] = fmaf(s1_0, g[5], gv[11]); gg[5] = fmaf(s1_0, v[11], gg[5]);
+      gv[11] = fmaf(s4_1, g[6], gv[11]); gg[6] = fmaf(s4_1, v[11], gg[6]);
+      gv[11] = fmaf(-s3_0, g[7], gv[11]); gg[7] = fmaf(-s3_0, v[11], gg[7]);
+      gv[11] = fmaf(s2_0, g[8], gv[11]); gg[8] = fmaf(s2_0, v[11], gg[8]);
     }
     { // path 23
-      const float w = th[23] * 0.4082482904638631f;
+      const float w = th[23 * TS];
       const float gt0 = w * gvo[4];
       const float gt1 = w * gvo[5];
       const float gt2 = w * gvo[6];
       const float gt3 = w * gvo[7];
       const float gt4 = w * gvo[8];
-      gv[12] += 0.408248290463863f * gt1 * g[1]; gg[1] += 0.408248290463863f * gt1 * v[12];
-      gv[12] += 0.816496580927726f * gt4 * g[2]; gg[2] += 0.816496580927726f * gt4 * v[12];
-      gv[12] += -0.408248290463863f * gt3 * g[3]; gg[3] += -0.408248290463863f * gt3 * v[12];
-      gv[13] += -0.408248290463863f * gt0 * g[1]; gg[1] += -0.408248290463863f * gt0 * v[13];
-      gv[13] += 0.408248290463863f * gt3 * g[2]; gg[2] += 0.408248290463863f * gt3 * v[13];
-      gv[13] += -0.7071067811865477f * gt2 * g[3]; gg[3] += -0.7071067811865477f * gt2 * v[13];
-      gv[13] += -0.408248290463863f * gt4 * g[3]; gg[3] += -0.408248290463863f * gt4 * v[13];
-      gv[14] += -0.7071067811865477f * gt3 * g[1]; gg[1] += -0.7071067811865477f * gt3 * v[14];
-      gv[14] += 0.7071067811865477f * gt1 * g[3]; gg[3] += 0.7071067811865477f * gt1 * v[14];
-      gv[15] += 0.7071067811865477f * gt2 * g[1]; gg[1] += 0.7071067811865477f * gt2 * v[15];
-      gv[15] += -0.408248290463863f * gt4 * g[1]; gg[1] += -0.408248290463863f * gt4 * v[15];
-      gv[15] += -0.408248290463863f * gt1 * g[2]; gg[2] += -0.408248290463863f * gt1 * v[15];
-      gv[15] += 0.408248290463863f * gt0 * g[3]; gg[3] += 0.408248290463863f * gt0 * v[15];
-      gv[16] += 0.408248290463863f * gt3 * g[1]; gg[1] += 0.408248290463863f * gt3 * v[16];
-      gv[16] += -0.816496580927726f * gt0 * g[2]; gg[2] += -0.816496580927726f * gt0 * v[16];
-      gv[16] += 0.408248290463863f * gt1 * g[3]; gg[3] += 0.408248290463863f * gt1 * v[16];
+      const float s1_0 = 0.408248290463863f * gt1;
+      gv[12] = fmaf(s1_0, g[1], gv[12]); gg[1] = fmaf(s1_0, v[12], gg[1]);
+      const float s4_0 = 0.816496580927726f * gt4;
+      gv[12] = fmaf(s4_0, g[2], gv[12]); gg[2] = fmaf(s4_0, v[12], gg[2]);
+      const float s3_0 = 0.408248290463863f * gt3;
+      gv[12] = fmaf(-s3_0, g[3], gv[12]); gg[3] = fmaf(-s3_0, v[12], gg[3]);
+      const float s0_0 = 0.408248290463863f * gt0;
+      gv[13] = fmaf(-s0_0, g[1], gv[13]); gg[1] = fmaf(-s0_0, v[13], gg[1]);
+      gv[13] = fmaf(s3_0, g[2], gv[13]); gg[2] = fmaf(s3_0, v[13], gg[2]);
+      const float s2_0 = 0.7071067811865477f * gt2;
+      gv[13] = fmaf(-s2_0, g[3], gv[13]); gg[3] = fmaf(-s2_0, v[13], gg[3]);
+      const float s4_1 = 0.408248290463863f * gt4;
+      gv[13] = fmaf(-s4_1, g[3], gv[13]); gg[3] = fmaf(-s4_1, v[13], gg[3]);
+      const float s3_1 = 0.7071067811865477f * gt3;
+      gv[14] = fmaf(-s3_1, g[1], gv[14]); gg[1] = fmaf(-s3_1, v[14], gg[1]);
+      const float s1_1 = 0.7071067811865477f * gt1;
+      gv[14] = fmaf(s1_1, g[3], gv[14]); gg[3] = fmaf(s1_1, v[14], gg[3]);
+      gv[15] = fmaf(s2_0, g[1], gv[15]); gg[1] = fmaf(s2_0, v[15], gg[1]);
+      gv[15] = fmaf(-s4_1, g[1], gv[15]); gg[1] = fmaf(-s4_1, v[15], gg[1]);
+      gv[15] = fmaf(-s1_0, g[2], gv[15]); gg[2] = fmaf(-s1_0, v[15], gg[2]);
+      gv[15] = fmaf(s0_0, g[3], gv[15]); gg[3] = fmaf(s0_0, v[15], gg[3]);
+      gv[16] = fmaf(s3_0, g[1], gv[16]); gg[1] = fmaf(s3_0, v[16], gg[1]);
+      const float s0_1 = 0.816496580927726f * gt0;
+      gv[16] = fmaf(-s0_1, g[2], gv[16]); gg[2] = fmaf(-s0_1, v[16], gg[2]);
+      gv[16] = fmaf(s1_0, g[3], gv[16]); gg[3] = fmaf(s1_0, v[16], gg[3]);
     }
     { // path 25
-      const float w = th[25] * 0.4082482904638631f;
+      const float w = th[25 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[12] += 0.3162277660168379f * gt0 * g[5]; gg[5] += 0.3162277660168379f * gt0 * v[12];
-      gv[12] += -0.3162277660168379f * gt2 * g[7]; gg[7] += -0.3162277660168379f * gt2 * v[12];
-      gv[12] += 0.6324555320336758f * gt1 * g[8]; gg[8] += 0.6324555320336758f * gt1 * v[12];
-      gv[13] += -0.3162277660168379f * gt0 * g[4]; gg[4] += -0.3162277660168379f * gt0 * v[13];
-      gv[13] += -0.5477225575051661f * gt2 * g[6]; gg[6] += -0.5477225575051661f * gt2 * v[13];
-      gv[13] += 0.3162277660168379f * gt1 * g[7]; gg[7] += 0.3162277660168379f * gt1 * v[13];
-      gv[13] += -0.3162277660168379f * gt2 * g[8]; gg[8] += -0.3162277660168379f * gt2 * v[13];
-      gv[14] += 0.5477225575051661f * gt2 * g[5]; gg[5] += 0.5477225575051661f * gt2 * v[14];
-      gv[14] += -0.5477225575051661f * gt0 * g[7]; gg[7] += -0.5477225575051661f * gt0 * v[14];
-      gv[15] += 0.3162277660168379f * gt2 * g[4]; gg[4] += 0.3162277660168379f * gt2 * v[15];
-      gv[15] += -0.3162277660168379f * gt1 * g[5]; gg[5] += -0.3162277660168379f * gt1 * v[15];
-      gv[15] += 0.5477225575051661f * gt0 * g[6]; gg[6] += 0.5477225575051661f * gt0 * v[15];
-      gv[15] += -0.3162277660168379f * gt0 * g[8]; gg[8] += -0.3162277660168379f * gt0 * v[15];
-      gv[16] += -0.6324555320336758f * gt1 * g[4]; gg[4] += -0.6324555320336758f * gt1 * v[16];
-      gv[16] += 0.3162277660168379f * gt2 * g[5]; gg[5] += 0.3162277660168379f * gt2 * v[16];
-      gv[16] += 0.3162277660168379f * gt0 * g[7]; gg[7] += 0.3162277660168379f * gt0 * v[16];
+      const float s0_0 = 0.3162277660168379f * gt0;
+      gv[12] = fmaf(s0_0, g[5], gv[12]); gg[5] = fmaf(s0_0, v[12], gg[5]);
+      const float s2_0 = 0.3162277660168379f * gt2;
+      gv[12] = fmaf(-s2_0, g[7], gv[12]); gg[7] = fmaf(-s2_0, v[12], gg[7]);
+      const float s1_0 = 0.6324555320336758f * gt1;
+      gv[12] = fmaf(s1_0, g[8], gv[12]); gg[8] = fmaf(s1_0, v[12], gg[8]);
+      gv[13] = fmaf(-s0_0, g[4], gv[13]); gg[4] = fmaf(-s0_0, v[13], gg[4]);
+      const float s2_1 = 0.5477225575051661f * gt2;
+      gv[13] = fmaf(-s2_1, g[6], gv[13]); gg[6] = fmaf(-s2_1, v[13], gg[6]);
+      const float s1_1 = 0.3162277660168379f * gt1;
+      gv[13] = fmaf(s1_1, g[7], gv[13]); gg[7] = fmaf(s1_1, v[13], gg[7]);
+      gv[13] = fmaf(-s2_0, g[8], gv[13]); gg[8] = fmaf(-s2_0, v[13], gg[8]);
+      gv[14] = fmaf(s2_1, g[5], gv[14]); gg[5] = fmaf(s2_1, v[14], gg[5]);
+      const float s0_1 = 0.5477225575051661f * gt0;
+      gv[14] = fmaf(-s0_1, g[7], gv[14]); gg[7] = fmaf(-s0_1, v[14], gg[7]);
+      gv[15] = fmaf(s2_0, g[4], gv[15]); gg[4] = fmaf(s2_0, v[15], gg[4]);
+      gv[15] = fmaf(-s1_1, g[5], gv[15]); gg[5] = fmaf(-s1_1, v[15], gg[5]);
+      gv[15] = fmaf(s0_1, g[6], gv[15]); gg[6] = fmaf(s0_1, v[15], gg[6]);
+      gv[15] = fmaf(-s0_0, g[8], gv[15]); gg[8] = fmaf(-s0_0, v[15], gg[8]);
+      gv[16] = fmaf(-s1_0, g[4], gv[16]); gg[4] = fmaf(-s1_0, v[16], gg[4]);
+      gv[16] = fmaf(s2_0, g[5], gv[16]); gg[5] = fmaf(s2_0, v[16], gg[5]);
+      gv[16] = fmaf(s0_0, g[7], gv[16]); gg[7] = fmaf(s0_0, v[16], gg[7]);
     }
   }
   static constexpr int NNZ = 137;
@@ -2372,20 +2808,21 @@ template <> struct TP<2, 1, 1> {
 template <> struct TP<2, 2, 1> {
   // in irreps [(0, 1), (0, -1), (1, -1), (1, 1), (2, 1), (2, -1)]; out irreps [(0, 1), (1, -1), (2, 1)]
   static constexpr int NP = 30, DIN = 18, DOUT = 9, NS = 3, NPW = 30;
+  template <int TS>
   static __device__ __forceinline__ void fwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, float* s, float* vo) {
     #pragma unroll
     for (int k = 0; k < 9; ++k) vo[k] = 0.f;
     { // path 0: (0, 1) x (0,1) -> (0, 1)
       const float t0 = 1.0f * v[0] * g[0];
       s[0] = t0;
-      const float w = th[0] * 0.5773502691896258f;
+      const float w = th[0 * TS];
       vo[0] += w * t0;
     }
     { // path 1: (0, 1) x (1,-1) -> (1, -1)
       const float t0 = 0.9999999999999999f * v[0] * g[1];
       const float t1 = 1.0000000000000002f * v[0] * g[2];
       const float t2 = 0.9999999999999999f * v[0] * g[3];
-      const float w = th[1] * 0.4082482904638631f;
+      const float w = th[1 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
@@ -2396,7 +2833,7 @@ template <> struct TP<2, 2, 1> {
       const float t2 = 1.0000000000000002f * v[0] * g[6];
       const float t3 = 1.0f * v[0] * g[7];
       const float t4 = 1.0f * v[0] * g[8];
-      const float w = th[2] * 0.4082482904638631f;
+      const float w = th[2 * TS];
       vo[4] += w * t0;
       vo[5] += w * t1;
       vo[6] += w * t2;
@@ -2407,7 +2844,7 @@ template <> struct TP<2, 2, 1> {
       const float t0 = 0.9999999999999999f * v[2] * g[0];
       const float t1 = 1.0000000000000002f * v[3] * g[0];
       const float t2 = 0.9999999999999999f * v[4] * g[0];
-      const float w = th[6] * 0.4082482904638631f;
+      const float w = th[6 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
@@ -2415,7 +2852,7 @@ template <> struct TP<2, 2, 1> {
     { // path 7: (1, -1) x (1,-1) -> (0, 1)
       const float t0 = 0.5773502691896257f * v[2] * g[1] + 0.5773502691896258f * v[3] * g[2] + 0.5773502691896257f * v[4] * g[3];
       s[1] = t0;
-      const float w = th[7] * 0.5773502691896258f;
+      const float w = th[7 * TS];
       vo[0] += w * t0;
     }
     { // path 9: (1, -1) x (1,-1) -> (2, 1)
@@ -2424,7 +2861,7 @@ template <> struct TP<2, 2, 1> {
       const float t2 = 0.4082482904638631f * v[2] * g[1] + -0.8164965809277261f * v[3] * g[2] + 0.4082482904638631f * v[4] * g[3];
       const float t3 = -0.7071067811865476f * v[3] * g[3] + -0.7071067811865476f * v[4] * g[2];
       const float t4 = 0.7071067811865475f * v[2] * g[1] + -0.7071067811865475f * v[4] * g[3];
-      const float w = th[9] * 0.4082482904638631f;
+      const float w = th[9 * TS];
       vo[4] += w * t0;
       vo[5] += w * t1;
       vo[6] += w * t2;
@@ -2435,7 +2872,7 @@ template <> struct TP<2, 2, 1> {
       const float t0 = -0.3162277660168379f * v[2] * g[6] + -0.547722557505166f * v[2] * g[8] + 0.547722557505166f * v[3] * g[5] + 0.547722557505166f * v[4] * g[4];
       const float t1 = 0.547722557505166f * v[2] * g[5] + 0.632455532033676f * v[3] * g[6] + 0.547722557505166f * v[4] * g[7];
       const float t2 = 0.547722557505166f * v[2] * g[4] + 0.547722557505166f * v[3] * g[7] + -0.3162277660168379f * v[4] * g[6] + 0.547722557505166f * v[4] * g[8];
-      const float w = th[10] * 0.4082482904638631f;
+      const float w = th[10 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
@@ -2444,7 +2881,7 @@ template <> struct TP<2, 2, 1> {
       const float t0 = 0.7071067811865476f * v[6] * g[3] + -0.7071067811865476f * v[7] * g[2];
       const float t1 = -0.7071067811865476f * v[5] * g[3] + 0.7071067811865476f * v[7] * g[1];
       const float t2 = 0.7071067811865476f * v[5] * g[2] + -0.7071067811865476f * v[6] * g[1];
-      const float w = th[14] * 0.4082482904638631f;
+      const float w = th[14 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
@@ -2455,7 +2892,7 @@ template <> struct TP<2, 2, 1> {
       const float t2 = 0.7071067811865477f * v[5] * g[7] + -0.7071067811865477f * v[7] * g[5];
       const float t3 = -0.7071067811865477f * v[5] * g[6] + 0.408248290463863f * v[5] * g[8] + 0.408248290463863f * v[6] * g[5] + -0.408248290463863f * v[7] * g[4];
       const float t4 = -0.408248290463863f * v[5] * g[7] + 0.816496580927726f * v[6] * g[4] + -0.408248290463863f * v[7] * g[5];
-      const float w = th[17] * 0.4082482904638631f;
+      const float w = th[17 * TS];
       vo[4] += w * t0;
       vo[5] += w * t1;
       vo[6] += w * t2;
@@ -2468,7 +2905,7 @@ template <> struct TP<2, 2, 1> {
       const float t2 = 1.0000000000000002f * v[10] * g[0];
       const float t3 = 1.0f * v[11] * g[0];
       const float t4 = 1.0f * v[12] * g[0];
-      const float w = th[18] * 0.4082482904638631f;
+      const float w = th[18 * TS];
       vo[4] += w * t0;
       vo[5] += w * t1;
       vo[6] += w * t2;
@@ -2479,7 +2916,7 @@ template <> struct TP<2, 2, 1> {
       const float t0 = 0.547722557505166f * v[8] * g[3] + 0.547722557505166f * v[9] * g[2] + -0.3162277660168379f * v[10] * g[1] + -0.547722557505166f * v[12] * g[1];
       const float t1 = 0.547722557505166f * v[9] * g[1] + 0.632455532033676f * v[10] * g[2] + 0.547722557505166f * v[11] * g[3];
       const float t2 = 0.547722557505166f * v[8] * g[1] + -0.3162277660168379f * v[10] * g[3] + 0.547722557505166f * v[11] * g[2] + 0.547722557505166f * v[12] * g[3];
-      const float w = th[19] * 0.4082482904638631f;
+      const float w = th[19 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
@@ -2487,7 +2924,7 @@ template <> struct TP<2, 2, 1> {
     { // path 21: (2, 1) x (2,1) -> (0, 1)
       const float t0 = 0.4472135954999579f * v[8] * g[4] + 0.4472135954999579f * v[9] * g[5] + 0.44721359549995804f * v[10] * g[6] + 0.4472135954999579f * v[11] * g[7] + 0.4472135954999579f * v[12] * g[8];
       s[2] = t0;
-      const float w = th[21] * 0.5773502691896258f;
+      const float w = th[21 * TS];
       vo[0] += w * t0;
     }
     { // path 23: (2, 1) x (2,1) -> (2, 1)
@@ -2496,7 +2933,7 @@ template <> struct TP<2, 2, 1> {
       const float t2 = 0.5345224838248488f * v[8] * g[4] + -0.2672612419124244f * v[9] * g[5] + -0.5345224838248489f * v[10] * g[6] + -0.2672612419124244f * v[11] * g[7] + 0.5345224838248488f * v[12] * g[8];
       const float t3 = -0.4629100498862757f * v[8] * g[5] + -0.4629100498862757f * v[9] * g[4] + -0.2672612419124244f * v[10] * g[7] + -0.2672612419124244f * v[11] * g[6] + -0.4629100498862757f * v[11] * g[8] + -0.4629100498862757f * v[12] * g[7];
       const float t4 = 0.4629100498862757f * v[9] * g[5] + 0.5345224838248488f * v[10] * g[8] + -0.4629100498862757f * v[11] * g[7] + 0.5345224838248488f * v[12] * g[6];
-      const float w = th[23] * 0.4082482904638631f;
+      const float w = th[23 * TS];
       vo[4] += w * t0;
       vo[5] += w * t1;
       vo[6] += w * t2;
@@ -2509,7 +2946,7 @@ template <> struct TP<2, 2, 1> {
       const float t2 = -0.7071067811865477f * v[14] * g[3] + 0.7071067811865477f * v[16] * g[1];
       const float t3 = -0.408248290463863f * v[13] * g[3] + 0.408248290463863f * v[14] * g[2] + -0.7071067811865477f * v[15] * g[1] + 0.408248290463863f * v[17] * g[1];
       const float t4 = 0.816496580927726f * v[13] * g[2] + -0.408248290463863f * v[14] * g[3] + -0.408248290463863f * v[16] * g[1];
-      const float w = th[26] * 0.4082482904638631f;
+      const float w = th[26 * TS];
       vo[4] += w * t0;
       vo[5] += w * t1;
       vo[6] += w * t2;
@@ -2520,245 +2957,320 @@ template <> struct TP<2, 2, 1> {
       const float t0 = 0.3162277660168379f * v[13] * g[5] + -0.3162277660168379f * v[14] * g[4] + -0.5477225575051661f * v[15] * g[7] + 0.5477225575051661f * v[16] * g[6] + -0.3162277660168379f * v[16] * g[8] + 0.3162277660168379f * v[17] * g[7];
       const float t1 = 0.6324555320336758f * v[13] * g[8] + 0.3162277660168379f * v[14] * g[7] + -0.3162277660168379f * v[16] * g[5] + -0.6324555320336758f * v[17] * g[4];
       const float t2 = -0.3162277660168379f * v[13] * g[7] + -0.5477225575051661f * v[14] * g[6] + -0.3162277660168379f * v[14] * g[8] + 0.5477225575051661f * v[15] * g[5] + 0.3162277660168379f * v[16] * g[4] + 0.3162277660168379f * v[17] * g[5];
-      const float w = th[28] * 0.4082482904638631f;
+      const float w = th[28 * TS];
       vo[1] += w * t0;
       vo[2] += w * t1;
       vo[3] += w * t2;
     }
   }
+  template <int TS>
   static __device__ __forceinline__ void bwd(const float* __restrict__ v, const float* __restrict__ g, const float* __restrict__ th, const float* __restrict__ gs, const float* __restrict__ gvo, float* gv, float* gg) {
     { // path 0
-      const float w = th[0] * 0.5773502691896258f;
+      const float w = th[0 * TS];
       const float gt0 = gs[0] + w * gvo[0];
-      gv[0] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[0];
+      const float s0_0 = gt0;
+      gv[0] = fmaf(s0_0, g[0], gv[0]); gg[0] = fmaf(s0_0, v[0], gg[0]);
     }
     { // path 1
-      const float w = th[1] * 0.4082482904638631f;
+      const float w = th[1 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[0] += 0.9999999999999999f * gt0 * g[1]; gg[1] += 0.9999999999999999f * gt0 * v[0];
-      gv[0] += 1.0000000000000002f * gt1 * g[2]; gg[2] += 1.0000000000000002f * gt1 * v[0];
-      gv[0] += 0.9999999999999999f * gt2 * g[3]; gg[3] += 0.9999999999999999f * gt2 * v[0];
+      const float s0_0 = gt0;
+      gv[0] = fmaf(s0_0, g[1], gv[0]); gg[1] = fmaf(s0_0, v[0], gg[1]);
+      const float s1_0 = gt1;
+      gv[0] = fmaf(s1_0, g[2], gv[0]); gg[2] = fmaf(s1_0, v[0], gg[2]);
+      const float s2_0 = gt2;
+      gv[0] = fmaf(s2_0, g[3], gv[0]); gg[3] = fmaf(s2_0, v[0], gg[3]);
     }
     { // path 2
-      const float w = th[2] * 0.4082482904638631f;
+      const float w = th[2 * TS];
       const float gt0 = w * gvo[4];
       const float gt1 = w * gvo[5];
       const float gt2 = w * gvo[6];
       const float gt3 = w * gvo[7];
       const float gt4 = w * gvo[8];
-      gv[0] += 1.0f * gt0 * g[4]; gg[4] += 1.0f * gt0 * v[0];
-      gv[0] += 1.0f * gt1 * g[5]; gg[5] += 1.0f * gt1 * v[0];
-      gv[0] += 1.0000000000000002f * gt2 * g[6]; gg[6] += 1.0000000000000002f * gt2 * v[0];
-      gv[0] += 1.0f * gt3 * g[7]; gg[7] += 1.0f * gt3 * v[0];
-      gv[0] += 1.0f * gt4 * g[8]; gg[8] += 1.0f * gt4 * v[0];
+      const float s0_0 = gt0;
+      gv[0] = fmaf(s0_0, g[4], gv[0]); gg[4] = fmaf(s0_0, v[0], gg[4]);
+      const float s1_0 = gt1;
+      gv[0] = fmaf(s1_0, g[5], gv[0]); gg[5] = fmaf(s1_0, v[0], gg[5]);
+      const float s2_0 = gt2;
+      gv[0] = fmaf(s2_0, g[6], gv[0]); gg[6] = fmaf(s2_0, v[0], gg[6]);
+      const float s3_0 = gt3;
+      gv[0] = fmaf(s3_0, g[7], gv[0]); gg[7] = fmaf(s3_0, v[0], gg[7]);
+      const float s4_0 = gt4;
+      gv[0] = fmaf(s4_0, g[8], gv[0]); gg[8] = fmaf(s4_0, v[0], gg[8]);
     }
     { // path 6
-      const float w = th[6] * 0.4082482904638631f;
+      const float w = th[6 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[2] += 0.9999999999999999f * gt0 * g[0]; gg[0] += 0.9999999999999999f * gt0 * v[2];
-      gv[3] += 1.0000000000000002f * gt1 * g[0]; gg[0] += 1.0000000000000002f * gt1 * v[3];
-      gv[4] += 0.9999999999999999f * gt2 * g[0]; gg[0] += 0.9999999999999999f * gt2 * v[4];
+      const float s0_0 = gt0;
+      gv[2] = fmaf(s0_0, g[0], gv[2]); gg[0] = fmaf(s0_0, v[2], gg[0]);
+      const float s1_0 = gt1;
+      gv[3] = fmaf(s1_0, g[0], gv[3]); gg[0] = fmaf(s1_0, v[3], gg[0]);
+      const float s2_0 = gt2;
+      gv[4] = fmaf(s2_0, g[0], gv[4]); gg[0] = fmaf(s2_0, v[4], gg[0]);
     }
     { // path 7
-      const float w = th[7] * 0.5773502691896258f;
+      const float w = th[7 * TS];
       const float gt0 = gs[1] + w * gvo[0];
-      gv[2] += 0.5773502691896257f * gt0 * g[1]; gg[1] += 0.5773502691896257f * gt0 * v[2];
-      gv[3] += 0.5773502691896258f * gt0 * g[2]; gg[2] += 0.5773502691896258f * gt0 * v[3];
-      gv[4] += 0.5773502691896257f * gt0 * g[3]; gg[3] += 0.5773502691896257f * gt0 * v[4];
+      const float s0_0 = 0.5773502691896257f * gt0;
+      gv[2] = fmaf(s0_0, g[1], gv[2]); gg[1] = fmaf(s0_0, v[2], gg[1]);
+      gv[3] = fmaf(s0_0, g[2], gv[3]); gg[2] = fmaf(s0_0, v[3], gg[2]);
+      gv[4] = fmaf(s0_0, g[3], gv[4]); gg[3] = fmaf(s0_0, v[4], gg[3]);
     }
     { // path 9
-      const float w = th[9] * 0.4082482904638631f;
+      const float w = th[9 * TS];
       const float gt0 = w * gvo[4];
       const float gt1 = w * gvo[5];
       const float gt2 = w * gvo[6];
       const float gt3 = w * gvo[7];
       const float gt4 = w * gvo[8];
-      gv[2] += 0.4082482904638631f * gt2 * g[1]; gg[1] += 0.4082482904638631f * gt2 * v[2];
-      gv[2] += 0.7071067811865475f * gt4 * g[1]; gg[1] += 0.7071067811865475f * gt4 * v[2];
-      gv[2] += -0.7071067811865476f * gt1 * g[2]; gg[2] += -0.7071067811865476f * gt1 * v[2];
-      gv[2] += -0.7071067811865475f * gt0 * g[3]; gg[3] += -0.7071067811865475f * gt0 * v[2];
-      gv[3] += -0.7071067811865476f * gt1 * g[1]; gg[1] += -0.7071067811865476f * gt1 * v[3];
-      gv[3] += -0.8164965809277261f * gt2 * g[2]; gg[2] += -0.8164965809277261f * gt2 * v[3];
-      gv[3] += -0.7071067811865476f * gt3 * g[3]; gg[3] += -0.7071067811865476f * gt3 * v[3];
-      gv[4] += -0.7071067811865475f * gt0 * g[1]; gg[1] += -0.7071067811865475f * gt0 * v[4];
-      gv[4] += -0.7071067811865476f * gt3 * g[2]; gg[2] += -0.7071067811865476f * gt3 * v[4];
-      gv[4] += 0.4082482904638631f * gt2 * g[3]; gg[3] += 0.4082482904638631f * gt2 * v[4];
-      gv[4] += -0.7071067811865475f * gt4 * g[3]; gg[3] += -0.7071067811865475f * gt4 * v[4];
+      const float s2_0 = 0.4082482904638631f * gt2;
+      gv[2] = fmaf(s2_0, g[1], gv[2]); gg[1] = fmaf(s2_0, v[2], gg[1]);
+      const float s4_0 = 0.7071067811865475f * gt4;
+      gv[2] = fmaf(s4_0, g[1], gv[2]); gg[1] = fmaf(s4_0, v[2], gg[1]);
+      const float s1_0 = 0.7071067811865476f * gt1;
+      gv[2] = fmaf(-s1_0, g[2], gv[2]); gg[2] = fmaf(-s1_0, v[2], gg[2]);
+      const float s0_0 = 0.7071067811865475f * gt0;
+      gv[2] = fmaf(-s0_0, g[3], gv[2]); gg[3] = fmaf(-s0_0, v[2], gg[3]);
+      gv[3] = fmaf(-s1_0, g[1], gv[3]); gg[1] = fmaf(-s1_0, v[3], gg[1]);
+      const float s2_1 = 0.8164965809277261f * gt2;
+      gv[3] = fmaf(-s2_1, g[2], gv[3]); gg[2] = fmaf(-s2_1, v[3], gg[2]);
+      const float s3_0 = 0.7071067811865476f * gt3;
+      gv[3] = fmaf(-s3_0, g[3], gv[3]); gg[3] = fmaf(-s3_0, v[3], gg[3]);
+      gv[4] = fmaf(-s0_0, g[1], gv[4]); gg[1] = fmaf(-s0_0, v[4], gg[1]);
+      gv[4] = fmaf(-s3_0, g[2], gv[4]); gg[2] = fmaf(-s3_0, v[4], gg[2]);
+      gv[4] = fmaf(s2_0, g[3], gv[4]); gg[3] = fmaf(s2_0, v[4], gg[3]);
+      gv[4] = fmaf(-s4_0, g[3], gv[4]); gg[3] = fmaf(-s4_0, v[4], gg[3]);
     }
     { // path 10
-      const float w = th[10] * 0.4082482904638631f;
+      const float w = th[10 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[2] += 0.547722557505166f * gt2 * g[4]; gg[4] += 0.547722557505166f * gt2 * v[2];
-      gv[2] += 0.547722557505166f * gt1 * g[5]; gg[5] += 0.547722557505166f * gt1 * v[2];
-      gv[2] += -0.3162277660168379f * gt0 * g[6]; gg[6] += -0.3162277660168379f * gt0 * v[2];
-      gv[2] += -0.547722557505166f * gt0 * g[8]; gg[8] += -0.547722557505166f * gt0 * v[2];
-      gv[3] += 0.547722557505166f * gt0 * g[5]; gg[5] += 0.547722557505166f * gt0 * v[3];
-      gv[3] += 0.632455532033676f * gt1 * g[6]; gg[6] += 0.632455532033676f * gt1 * v[3];
-      gv[3] += 0.547722557505166f * gt2 * g[7]; gg[7] += 0.547722557505166f * gt2 * v[3];
-      gv[4] += 0.547722557505166f * gt0 * g[4]; gg[4] += 0.547722557505166f * gt0 * v[4];
-      gv[4] += -0.3162277660168379f * gt2 * g[6]; gg[6] += -0.3162277660168379f * gt2 * v[4];
-      gv[4] += 0.547722557505166f * gt1 * g[7]; gg[7] += 0.547722557505166f * gt1 * v[4];
-      gv[4] += 0.547722557505166f * gt2 * g[8]; gg[8] += 0.547722557505166f * gt2 * v[4];
+      const float s2_0 = 0.547722557505166f * gt2;
+      gv[2] = fmaf(s2_0, g[4], gv[2]); gg[4] = fmaf(s2_0, v[2], gg[4]);
+      const float s1_0 = 0.547722557505166f * gt1;
+      gv[2] = fmaf(s1_0, g[5], gv[2]); gg[5] = fmaf(s1_0, v[2], gg[5]);
+      const float s0_0 = 0.3162277660168379f * gt0;
+      gv[2] = fmaf(-s0_0, g[6], gv[2]); gg[6] = fmaf(-s0_0, v[2], gg[6]);
+      const float s0_1 = 0.547722557505166f * gt0;
+      gv[2] = fmaf(-s0_1, g[8], gv[2]); gg[8] = fmaf(-s0_1, v[2], gg[8]);
+      gv[3] = fmaf(s0_1, g[5], gv[3]); gg[5] = fmaf(s0_1, v[3], gg[5]);
+      const float s1_1 = 0.632455532033676f * gt1;
+      gv[3] = fmaf(s1_1, g[6], gv[3]); gg[6] = fmaf(s1_1, v[3], gg[6]);
+      gv[3] = fmaf(s2_0, g[7], gv[3]); gg[7] = fmaf(s2_0, v[3], gg[7]);
+      gv[4] = fmaf(s0_1, g[4], gv[4]); gg[4] = fmaf(s0_1, v[4], gg[4]);
+      const float s2_1 = 0.3162277660168379f * gt2;
+      gv[4] = fmaf(-s2_1, g[6], gv[4]); gg[6] = fmaf(-s2_1, v[4], gg[6]);
+      gv[4] = fmaf(s1_0, g[7], gv[4]); gg[7] = fmaf(s1_0, v[4], gg[7]);
+      gv[4] = fmaf(s2_0, g[8], gv[4]); gg[8] = fmaf(s2_0, v[4], gg[8]);
     }
     { // path 14
-      const float w = th[14] * 0.4082482904638631f;
+      const float w = th[14 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[5] += 0.7071067811865476f * gt2 * g[2]; gg[2] += 0.7071067811865476f * gt2 * v[5];
-      gv[5] += -0.7071067811865476f * gt1 * g[3]; gg[3] += -0.7071067811865476f * gt1 * v[5];
-      gv[6] += -0.7071067811865476f * gt2 * g[1]; gg[1] += -0.7071067811865476f * gt2 * v[6];
-      gv[6] += 0.7071067811865476f * gt0 * g[3]; gg[3] += 0.7071067811865476f * gt0 * v[6];
-      gv[7] += 0.7071067811865476f * gt1 * g[1]; gg[1] += 0.7071067811865476f * gt1 * v[7];
-      gv[7] += -0.7071067811865476f * gt0 * g[2]; gg[2] += -0.7071067811865476f * gt0 * v[7];
+      const float s2_0 = 0.7071067811865476f * gt2;
+      gv[5] = fmaf(s2_0, g[2], gv[5]); gg[2] = fmaf(s2_0, v[5], gg[2]);
+      const float s1_0 = 0.7071067811865476f * gt1;
+      gv[5] = fmaf(-s1_0, g[3], gv[5]); gg[3] = fmaf(-s1_0, v[5], gg[3]);
+      gv[6] = fmaf(-s2_0, g[1], gv[6]); gg[1] = fmaf(-s2_0, v[6], gg[1]);
+      const float s0_0 = 0.7071067811865476f * gt0;
+      gv[6] = fmaf(s0_0, g[3], gv[6]); gg[3] = fmaf(s0_0, v[6], gg[3]);
+      gv[7] = fmaf(s1_0, g[1], gv[7]); gg[1] = fmaf(s1_0, v[7], gg[1]);
+      gv[7] = fmaf(-s0_0, g[2], gv[7]); gg[2] = fmaf(-s0_0, v[7], gg[2]);
     }
     { // path 17
-      const float w = th[17] * 0.4082482904638631f;
+      const float w = th[17 * TS];
       const float gt0 = w * gvo[4];
       const float gt1 = w * gvo[5];
       const float gt2 = w * gvo[6];
       const float gt3 = w * gvo[7];
       const float gt4 = w * gvo[8];
-      gv[5] += 0.408248290463863f * gt1 * g[4]; gg[4] += 0.408248290463863f * gt1 * v[5];
-      gv[5] += -0.408248290463863f * gt0 * g[5]; gg[5] += -0.408248290463863f * gt0 * v[5];
-      gv[5] += -0.7071067811865477f * gt3 * g[6]; gg[6] += -0.7071067811865477f * gt3 * v[5];
-      gv[5] += 0.7071067811865477f * gt2 * g[7]; gg[7] += 0.7071067811865477f * gt2 * v[5];
-      gv[5] += -0.408248290463863f * gt4 * g[7]; gg[7] += -0.408248290463863f * gt4 * v[5];
-      gv[5] += 0.408248290463863f * gt3 * g[8]; gg[8] += 0.408248290463863f * gt3 * v[5];
-      gv[6] += 0.816496580927726f * gt4 * g[4]; gg[4] += 0.816496580927726f * gt4 * v[6];
-      gv[6] += 0.408248290463863f * gt3 * g[5]; gg[5] += 0.408248290463863f * gt3 * v[6];
-      gv[6] += -0.408248290463863f * gt1 * g[7]; gg[7] += -0.408248290463863f * gt1 * v[6];
-      gv[6] += -0.816496580927726f * gt0 * g[8]; gg[8] += -0.816496580927726f * gt0 * v[6];
-      gv[7] += -0.408248290463863f * gt3 * g[4]; gg[4] += -0.408248290463863f * gt3 * v[7];
-      gv[7] += -0.7071067811865477f * gt2 * g[5]; gg[5] += -0.7071067811865477f * gt2 * v[7];
-      gv[7] += -0.408248290463863f * gt4 * g[5]; gg[5] += -0.408248290463863f * gt4 * v[7];
-      gv[7] += 0.7071067811865477f * gt1 * g[6]; gg[6] += 0.7071067811865477f * gt1 * v[7];
-      gv[7] += 0.408248290463863f * gt0 * g[7]; gg[7] += 0.408248290463863f * gt0 * v[7];
-      gv[7] += 0.408248290463863f * gt1 * g[8]; gg[8] += 0.408248290463863f * gt1 * v[7];
+      const float s1_0 = 0.408248290463863f * gt1;
+      gv[5] = fmaf(s1_0, g[4], gv[5]); gg[4] = fmaf(s1_0, v[5], gg[4]);
+      const float s0_0 = 0.408248290463863f * gt0;
+      gv[5] = fmaf(-s0_0, g[5], gv[5]); gg[5] = fmaf(-s0_0, v[5], gg[5]);
+      const float s3_0 = 0.7071067811865477f * gt3;
+      gv[5] = fmaf(-s3_0, g[6], gv[5]); gg[6] = fmaf(-s3_0, v[5], gg[6]);
+      const float s2_0 = 0.7071067811865477f * gt2;
+      gv[5] = fmaf(s2_0, g[7], gv[5]); gg[7] = fmaf(s2_0, v[5], gg[7]);
+      const float s4_0 = 0.408248290463863f * gt4;
+      gv[5] = fmaf(-s4_0, g[7], gv[5]); gg[7] = fmaf(-s4_0, v[5], gg[7]);
+      const float s3_1 = 0.408248290463863f * gt3;
+      gv[5] = fmaf(s3_1, g[8], gv[5]); gg[8] = fmaf(s3_1, v[5], gg[8]);
+      const float s4_1 = 0.816496580927726f * gt4;
+      gv[6] = fmaf(s4_1, g[4], gv[6]); gg[4] = fmaf(s4_1, v[6], gg[4]);
+      gv[6] = fmaf(s3_1, g[5], gv[6]); gg[5] = fmaf(s3_1, v[6], gg[5]);
+      gv[6] = fmaf(-s1_0, g[7], gv[6]); gg[7] = fmaf(-s1_0, v[6], gg[7]);
+      const float s0_1 = 0.816496580927726f * gt0;
+      gv[6] = fmaf(-s0_1, g[8], gv[6]); gg[8] = fmaf(-s0_1, v[6], gg[8]);
+      gv[7] = fmaf(-s3_1, g[4], gv[7]); gg[4] = fmaf(-s3_1, v[7], gg[4]);
+      gv[7] = fmaf(-s2_0, g[5], gv[7]); gg[5] = fmaf(-s2_0, v[7], gg[5]);
+      gv[7] = fmaf(-s4_0, g[5], gv[7]); gg[5] = fmaf(-s4_0, v[7], gg[5]);
+      const float s1_1 = 0.7071067811865477f * gt1;
+      gv[7] = fmaf(s1_1, g[6], gv[7]); gg[6] = fmaf(s1_1, v[7], gg[6]);
+      gv[7] = fmaf(s0_0, g[7], gv[7]); gg[7] = fmaf(s0_0, v[7], gg[7]);
+      gv[7] = fmaf(s1_0, g[8], gv[7]); gg[8] = fmaf(s1_0, v[7], gg[8]);
     }
     { // path 18
-      const float w = th[18] * 0.4082482904638631f;
+      const float w = th[18 * TS];
       const float gt0 = w * gvo[4];
       const float gt1 = w * gvo[5];
       const float gt2 = w * gvo[6];
       const float gt3 = w * gvo[7];
       const float gt4 = w * gvo[8];
-      gv[8] += 1.0f * gt0 * g[0]; gg[0] += 1.0f * gt0 * v[8];
-      gv[9] += 1.0f * gt1 * g[0]; gg[0] += 1.0f * gt1 * v[9];
-      gv[10] += 1.0000000000000002f * gt2 * g[0]; gg[0] += 1.0000000000000002f * gt2 * v[10];
-      gv[11] += 1.0f * gt3 * g[0]; gg[0] += 1.0f * gt3 * v[11];
-      gv[12] += 1.0f * gt4 * g[0]; gg[0] += 1.0f * gt4 * v[12];
+      const float s0_0 = gt0;
+      gv[8] = fmaf(s0_0, g[0], gv[8]); gg[0] = fmaf(s0_0, v[8], gg[0]);
+      const float s1_0 = gt1;
+      gv[9] = fmaf(s1_0, g[0], gv[9]); gg[0] = fmaf(s1_0, v[9], gg[0]);
+      const float s2_0 = gt2;
+      gv[10] = fmaf(s2_0, g[0], gv[10]); gg[0] = fmaf(s2_0, v[10], gg[0]);
+      const float s3_0 = gt3;
+      gv[11] = fmaf(s3_0, g[0], gv[11]); gg[0] = fmaf(s3_0, v[11], gg[0]);
+      const float s4_0 = gt4;
+      gv[12] = fmaf(s4_0, g[0], gv[12]); gg[0] = fmaf(s4_0, v[12], gg[0]);
     }
     { // path 19
-      const float w = th[19] * 0.4082482904638631f;
+      const float w = th[19 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[8] += 0.547722557505166f * gt2 * g[1]; gg[1] += 0.547722557505166f * gt2 * v[8];
-      gv[8] += 0.547722557505166f * gt0 * g[3]; gg[3] += 0.547722557505166f * gt0 * v[8];
-      gv[9] += 0.547722557505166f * gt1 * g[1]; gg[1] += 0.547722557505166f * gt1 * v[9];
-      gv[9] += 0.547722557505166f * gt0 * g[2]; gg[2] += 0.547722557505166f * gt0 * v[9];
-      gv[10] += -0.3162277660168379f * gt0 * g[1]; gg[1] += -0.3162277660168379f * gt0 * v[10];
-      gv[10] += 0.632455532033676f * gt1 * g[2]; gg[2] += 0.632455532033676f * gt1 * v[10];
-      gv[10] += -0.3162277660168379f * gt2 * g[3]; gg[3] += -0.3162277660168379f * gt2 * v[10];
-      gv[11] += 0.547722557505166f * gt2 * g[2]; gg[2] += 0.547722557505166f * gt2 * v[11];
-      gv[11] += 0.547722557505166f * gt1 * g[3]; gg[3] += 0.547722557505166f * gt1 * v[11];
-      gv[12] += -0.547722557505166f * gt0 * g[1]; gg[1] += -0.547722557505166f * gt0 * v[12];
-      gv[12] += 0.547722557505166f * gt2 * g[3]; gg[3] += 0.547722557505166f * gt2 * v[12];
+      const float s2_0 = 0.547722557505166f * gt2;
+      gv[8] = fmaf(s2_0, g[1], gv[8]); gg[1] = fmaf(s2_0, v[8], gg[1]);
+      const float s0_0 = 0.547722557505166f * gt0;
+      gv[8] = fmaf(s0_0, g[3], gv[8]); gg[3] = fmaf(s0_0, v[8], gg[3]);
+      const float s1_0 = 0.547722557505166f * gt1;
+      gv[9] = fmaf(s1_0, g[1], gv[9]); gg[1] = fmaf(s1_0, v[9], gg[1]);
+      gv[9] = fmaf(s0_0, g[2], gv[9]); gg[2] = fmaf(s0_0, v[9], gg[2]);
+      const float s0_1 = 0.3162277660168379f * gt0;
+      gv[10] = fmaf(-s0_1, g[1], gv[10]); gg[1] = fmaf(-s0_1, v[10], gg[1]);
+      const float s1_1 = 0.632455532033676f * gt1;
+      gv[10] = fmaf(s1_1, g[2], gv[10]); gg[2] = fmaf(s1_1, v[10], gg[2]);
+      const float s2_1 = 0.3162277660168379f * gt2;
+      gv[10] = fmaf(-s2_1, g[3], gv[10]); gg[3] = fmaf(-s2_1, v[10], gg[3]);
+      gv[11] = fmaf(s2_0, g[2], gv[11]); gg[2] = fmaf(s2_0, v[11], gg[2]);
+      gv[11] = fmaf(s1_0, g[3], gv[11]); gg[3] = fmaf(s1_0, v[11], gg[3]);
+      gv[12] = fmaf(-s0_0, g[1], gv[12]); gg[1] = fmaf(-s0_0, v[12], gg[1]);
+      gv[12] = fmaf(s2_0, g[3], gv[12]); gg[3] = fmaf(s2_0, v[12], gg[3]);
     }
     { // path 21
-      const float w = th[21] * 0.5773502691896258f;
+      const float w = th[21 * TS];
       const float gt0 = gs[2] + w * gvo[0];
-      gv[8] += 0.4472135954999579f * gt0 * g[4]; gg[4] += 0.4472135954999579f * gt0 * v[8];
-      gv[9] += 0.4472135954999579f * gt0 * g[5]; gg[5] += 0.4472135954999579f * gt0 * v[9];
-      gv[10] += 0.44721359549995804f * gt0 * g[6]; gg[6] += 0.44721359549995804f * gt0 * v[10];
-      gv[11] += 0.4472135954999579f * gt0 * g[7]; gg[7] += 0.4472135954999579f * gt0 * v[11];
-      gv[12] += 0.4472135954999579f * gt0 * g[8]; gg[8] += 0.4472135954999579f * gt0 * v[12];
+      const float s0_0 = 0.4472135954999579f * gt0;
+      gv[8] = fmaf(s0_0, g[4], gv[8]); gg[4] = fmaf(s0_0, v[8], gg[4]);
+      gv[9] = fmaf(s0_0, g[5], gv[9]); gg[5] = fmaf(s0_0, v[9], gg[5]);
+      gv[10] = fmaf(s0_0, g[6], gv[10]); gg[6] = fmaf(s0_0, v[10], gg[6]);
+      gv[11] = fmaf(s0_0, g[7], gv[11]); gg[7] = fmaf(s0_0, v[11], gg[7]);
+      gv[12] = fmaf(s0_0, g[8], gv[12]); gg[8] = fmaf(s0_0, v[12], gg[8]);
     }
     { // path 23
-      const float w = th[23] * 0.4082482904638631f;
+      const float w = th[23 * TS];
       const float gt0 = w * gvo[4];
       const float gt1 = w * gvo[5];
       const float gt2 = w * gvo[6];
       const float gt3 = w * gvo[7];
       const float gt4 = w * gvo[8];
-      gv[8] += 0.5345224838248488f * gt2 * g[4]; gg[4] += 0.5345224838248488f * gt2 * v[8];
-      gv[8] += -0.4629100498862757f * gt3 * g[5]; gg[5] += -0.4629100498862757f * gt3 * v[8];
-      gv[8] += 0.5345224838248488f * gt0 * g[6]; gg[6] += 0.5345224838248488f * gt0 * v[8];
-      gv[8] += -0.4629100498862757f * gt1 * g[7]; gg[7] += -0.4629100498862757f * gt1 * v[8];
-      gv[9] += -0.4629100498862757f * gt3 * g[4]; gg[4] += -0.4629100498862757f * gt3 * v[9];
-      gv[9] += -0.2672612419124244f * gt2 * g[5]; gg[5] += -0.2672612419124244f * gt2 * v[9];
-      gv[9] += 0.4629100498862757f * gt4 * g[5]; gg[5] += 0.4629100498862757f * gt4 * v[9];
-      gv[9] += -0.2672612419124244f * gt1 * g[6]; gg[6] += -0.2672612419124244f * gt1 * v[9];
-      gv[9] += -0.4629100498862757f * gt0 * g[7]; gg[7] += -0.4629100498862757f * gt0 * v[9];
-      gv[9] += 0.4629100498862757f * gt1 * g[8]; gg[8] += 0.4629100498862757f * gt1 * v[9];
-      gv[10] += 0.5345224838248488f * gt0 * g[4]; gg[4] += 0.5345224838248488f * gt0 * v[10];
-      gv[10] += -0.2672612419124244f * gt1 * g[5]; gg[5] += -0.2672612419124244f * gt1 * v[10];
-      gv[10] += -0.5345224838248489f * gt2 * g[6]; gg[6] += -0.5345224838248489f * gt2 * v[10];
-      gv[10] += -0.2672612419124244f * gt3 * g[7]; gg[7] += -0.2672612419124244f * gt3 * v[10];
-      gv[10] += 0.5345224838248488f * gt4 * g[8]; gg[8] += 0.5345224838248488f * gt4 * v[10];
-      gv[11] += -0.4629100498862757f * gt1 * g[4]; gg[4] += -0.4629100498862757f * gt1 * v[11];
-      gv[11] += -0.4629100498862757f * gt0 * g[5]; gg[5] += -0.4629100498862757f * gt0 * v[11];
-      gv[11] += -0.2672612419124244f * gt3 * g[6]; gg[6] += -0.2672612419124244f * gt3 * v[11];
-      gv[11] += -0.2672612419124244f * gt2 * g[7]; gg[7] += -0.2672612419124244f * gt2 * v[11];
-      gv[11] += -0.4629100498862757f * gt4 * g[7]; gg[7] += -0.4629100498862757f * gt4 * v[11];
-      gv[11] += -0.4629100498862757f * gt3 * g[8]; gg[8] += -0.4629100498862757f * gt3 * v[11];
-      gv[12] += 0.4629100498862757f * gt1 * g[5]; gg[5] += 0.4629100498862757f * gt1 * v[12];
-      gv[12] += 0.5345224838248488f * gt4 * g[6]; gg[6] += 0.5345224838248488f * gt4 * v[12];
-      gv[12] += -0.4629100498862757f * gt3 * g[7]; gg[7] += -0.4629100498862757f * gt3 * v[12];
-      gv[12] += 0.5345224838248488f * gt2 * g[8]; gg[8] += 0.5345224838248488f * gt2 * v[12];
+      const float s2_0 = 0.5345224838248488f * gt2;
+      gv[8] = fmaf(s2_0, g[4], gv[8]); gg[4] = fmaf(s2_0, v[8], gg[4]);
+      const float s3_0 = 0.4629100498862757f * gt3;
+      gv[8] = fmaf(-s3_0, g[5], gv[8]); gg[5] = fmaf(-s3_0, v[8], gg[5]);
+      const float s0_0 = 0.5345224838248488f * gt0;
+      gv[8] = fmaf(s0_0, g[6], gv[8]); gg[6] = fmaf(s0_0, v[8], gg[6]);
+      const float s1_0 = 0.4629100498862757f * gt1;
+      gv[8] = fmaf(-s1_0, g[7], gv[8]); gg[7] = fmaf(-s1_0, v[8], gg[7]);
+      gv[9] = fmaf(-s3_0, g[4], gv[9]); gg[4] = fmaf(-s3_0, v[9], gg[4]);
+      const float s2_1 = 0.2672612419124244f * gt2;
+      gv[9] = fmaf(-s2_1, g[5], gv[9]); gg[5] = fmaf(-s2_1, v[9], gg[5]);
+      const float s4_0 = 0.4629100498862757f * gt4;
+      gv[9] = fmaf(s4_0, g[5], gv[9]); gg[5] = fmaf(s4_0, v[9], gg[5]);
+      const float s1_1 = 0.2672612419124244f * gt1;
+      gv[9] = fmaf(-s1_1, g[6], gv[9]); gg[6] = fmaf(-s1_1, v[9], gg[6]);
+      const float s0_1 = 0.4629100498862757f * gt0;
+      gv[9] = fmaf(-s0_1, g[7], gv[9]); gg[7] = fmaf(-s0_1, v[9], gg[7]);
+      gv[9] = fmaf(s1_0, g[8], gv[9]); gg[8] = fmaf(s1_0, v[9], gg[8]);
+      gv[10] = fmaf(s0_0, g[4], gv[10]); gg[4] = fmaf(s0_0, v[10], gg[4]);
+      gv[10] = fmaf(-s1_1, g[5], gv[10]); gg[5] = fmaf(-s1_1, v[10], gg[5]);
+      gv[10] = fmaf(-s2_0, g[6], gv[10]); gg[6] = fmaf(-s2_0, v[10], gg[6]);
+      const float s3_1 = 0.2672612419124244f * gt3;
+      gv[10] = fmaf(-s3_1, g[7], gv[10]); gg[7] = fmaf(-s3_1, v[10], gg[7]);
+      const float s4_1 = 0.5345224838248488f * gt4;
+      gv[10] = fmaf(s4_1, g[8], gv[10]); gg[8] = fmaf(s4_1, v[10], gg[8]);
+      gv[11] = fmaf(-s1_0, g[4], gv[11]); gg[4] = fmaf(-s1_0, v[11], gg[4]);
+      gv[11] = fmaf(-s0_1, g[5], gv[11]); gg[5] = fmaf(-s0_1, v[11], gg[5]);
+      gv[11] = fmaf(-s3_1, g[6], gv[11]); gg[6] = fmaf(-s3_1, v[11], gg[6]);
+      gv[11] = fmaf(-s2_1, g[7], gv[11]); gg[7] = fmaf(-s2_1, v[11], gg[7]);
+      gv[11] = fmaf(-s4_0, g[7], gv[11]); gg[7] = fmaf(-s4_0, v[11], gg[7]);
+      gv[11] = fmaf(-s3_0, g[8], gv[11]); gg[8] = fmaf(-s3_0, v[11], gg[8]);
+      gv[12] = fmaf(s1_0, g[5], gv[12]); gg[5] = fmaf(s1_0, v[12], gg[5]);
+      gv[12] = fmaf(s4_1, g[6], gv[12]); gg[6] = fmaf(s4_1, v[12], gg[6]);
+      gv[12] = fmaf(-s3_0, g[7], gv[12]); gg[7] = fmaf(-s3_0, v[12], gg[7]);
+      gv[12] = fmaf(s2_0, g[8], gv[12]); gg[8] = fmaf(s2_0, v[12], gg[8]);
     }
     { // path 26
-      const float w = th[26] * 0.4082482904638631f;
+      const float w = th[26 * TS];
       const float gt0 = w * gvo[4];
       const float gt1 = w * gvo[5];
       const float gt2 = w * gvo[6];
       const float gt3 = w * gvo[7];
       const float gt4 = w * gvo[8];
-      gv[13] += 0.408248290463863f * gt1 * g[1]; gg[1] += 0.408248290463863f * gt1 * v[13];
-      gv[13] += 0.816496580927726f * gt4 * g[2]; gg[2] += 0.816496580927726f * gt4 * v[13];
-      gv[13] += -0.408248290463863f * gt3 * g[3]; gg[3] += -0.408248290463863f * gt3 * v[13];
-      gv[14] += -0.408248290463863f * gt0 * g[1]; gg[1] += -0.408248290463863f * gt0 * v[14];
-      gv[14] += 0.408248290463863f * gt3 * g[2]; gg[2] += 0.408248290463863f * gt3 * v[14];
-      gv[14] += -0.7071067811865477f * gt2 * g[3]; gg[3] += -0.7071067811865477f * gt2 * v[14];
-      gv[14] += -0.408248290463863f * gt4 * g[3]; gg[3] += -0.408248290463863f * gt4 * v[14];
-      gv[15] += -0.7071067811865477f * gt3 * g[1]; gg[1] += -0.7071067811865477f * gt3 * v[15];
-      gv[15] += 0.7071067811865477f * gt1 * g[3]; gg[3] += 0.7071067811865477f * gt1 * v[15];
-      gv[16] += 0.7071067811865477f * gt2 * g[1]; gg[1] += 0.7071067811865477f * gt2 * v[16];
-      gv[16] += -0.408248290463863f * gt4 * g[1]; gg[1] += -0.408248290463863f * gt4 * v[16];
-      gv[16] += -0.408248290463863f * gt1 * g[2]; gg[2] += -0.408248290463863f * gt1 * v[16];
-      gv[16] += 0.408248290463863f * gt0 * g[3]; gg[3] += 0.408248290463863f * gt0 * v[16];
-      gv[17] += 0.408248290463863f * gt3 * g[1]; gg[1] += 0.408248290463863f * gt3 * v[17];
-      gv[17] += -0.816496580927726f * gt0 * g[2]; gg[2] += -0.816496580927726f * gt0 * v[17];
-      gv[17] += 0.408248290463863f * gt1 * g[3]; gg[3] += 0.408248290463863f * gt1 * v[17];
+      const float s1_0 = 0.408248290463863f * gt1;
+      gv[13] = fmaf(s1_0, g[1], gv[13]); gg[1] = fmaf(s1_0, v[13], gg[1]);
+      const float s4_0 = 0.816496580927726f * gt4;
+      gv[13] = fmaf(s4_0, g[2], gv[13]); gg[2] = fmaf(s4_0, v[13], gg[2]);
+      const float s3_0 = 0.408248290463863f * gt3;
+      gv[13] = fmaf(-s3_0, g[3], gv[13]); gg[3] = fmaf(-s3_0, v[13], gg[3]);
+      const float s0_0 = 0.408248290463863f * gt0;
+      gv[14] = fmaf(-s0_0, g[1], gv[14]); gg[1] = fmaf(-s0_0, v[14], gg[1]);
+      gv[14] = fmaf(s3_0, g[2], gv[14]); gg[2] = fmaf(s3_0, v[14], gg[2]);
+      const float s2_0 = 0.7071067811865477f * gt2;
+      gv[14] = fmaf(-s2_0, g[3], gv[14]); gg[3] = fmaf(-s2_0, v[14], gg[3]);
+      const float s4_1 = 0.408248290463863f * gt4;
+      gv[14] = fmaf(-s4_1, g[3], gv[14]); gg[3] = fmaf(-s4_1, v[14], gg[3]);
+      const float s3_1 = 0.7071067811865477f * gt3;
+      gv[15] = fmaf(-s3_1, g[1], gv[15]); gg[1] = fmaf(-s3_1, v[15], gg[1]);
+      const float s1_1 = 0.7071067811865477f * gt1;
+      gv[15] = fmaf(s1_1, g[3], gv[15]); gg[3] = fmaf(s1_1, v[15], gg[3]);
+      gv[16] = fmaf(s2_0, g[1], gv[16]); gg[1] = fmaf(s2_0, v[16], gg[1]);
+      gv[16] = fmaf(-s4_1, g[1], gv[16]); gg[1] = fmaf(-s4_1, v[16], gg[1]);
+      gv[16] = fmaf(-s1_0, g[2], gv[16]); gg[2] = fmaf(-s1_0, v[16], gg[2]);
+      gv[16] = fmaf(s0_0, g[3], gv[16]); gg[3] = fmaf(s0_0, v[16], gg[3]);
+      gv[17] = fmaf(s3_0, g[1], gv[17]); gg[1] = fmaf(s3_0, v[17], gg[1]);
+      const float s0_1 = 0.816496580927726f * gt0;
+      gv[17] = fmaf(-s0_1, g[2], gv[17]); gg[2] = fmaf(-s0_1, v[17], gg[2]);
+      gv[17] = fmaf(s1_0, g[3], gv[17]); gg[3] = fmaf(s1_0, v[17], gg[3]);
     }
     { // path 28
-      const float w = th[28] * 0.4082482904638631f;
+      const float w = th[28 * TS];
       const float gt0 = w * gvo[1];
       const float gt1 = w * gvo[2];
       const float gt2 = w * gvo[3];
-      gv[13] += 0.3162277660168379f * gt0 * g[5]; gg[5] += 0.3162277660168379f * gt0 * v[13];
-      gv[13] += -0.3162277660168379f * gt2 * g[7]; gg[7] += -0.3162277660168379f * gt2 * v[13];
-      gv[13] += 0.6324555320336758f * gt1 * g[8]; gg[8] += 0.6324555320336758f * gt1 * v[13];
-      gv[14] += -0.3162277660168379f * gt0 * g[4]; gg[4] += -0.3162277660168379f * gt0 * v[14];
-      gv[14] += -0.5477225575051661f * gt2 * g[6]; gg[6] += -0.5477225575051661f * gt2 * v[14];
-      gv[14] += 0.3162277660168379f * gt1 * g[7]; gg[7] += 0.3162277660168379f * gt1 * v[14];
-      gv[14] += -0.3162277660168379f * gt2 * g[8]; gg[8] += -0.3162277660168379f * gt2 * v[14];
-      gv[15] += 0.5477225575051661f * gt2 * g[5]; gg[5] += 0.5477225575051661f * gt2 * v[15];
-      gv[15] += -0.5477225575051661f * gt0 * g[7]; gg[7] += -0.5477225575051661f * gt0 * v[15];
-      gv[16] += 0.3162277660168379f * gt2 * g[4]; gg[4] += 0.3162277660168379f * gt2 * v[16];
-      gv[16] += -0.3162277660168379f * gt1 * g[5]; gg[5] += -0.3162277660168379f * gt1 * v[16];
-      gv[16] += 0.5477225575051661f * gt0 * g[6]; gg[6] += 0.5477225575051661f * gt0 * v[16];
-      gv[16] += -0.3162277660168379f * gt0 * g[8]; gg[8] += -0.3162277660168379f * gt0 * v[16];
-      gv[17] += -0.6324555320336758f * gt1 * g[4]; gg[4] += -0.6324555320336758f * gt1 * v[17];
-      gv[17] += 0.3162277660168379f * gt2 * g[5]; gg[5] += 0.3162277660168379f * gt2 * v[17];
-      gv[17] += 0.3162277660168379f * gt0 * g[7]; gg[7] += 0.3162277660168379f * gt0 * v[17];
+      const float s0_0 = 0.3162277660168379f * gt0;
+      gv[13] = fmaf(s0_0, g[5], gv[13]); gg[5] = fmaf(s0_0, v[13], gg[5]);
+      const float s2_0 = 0.3162277660168379f * gt2;
+      gv[13] = fmaf(-s2_0, g[7], gv[13]); gg[7] = fmaf(-s2_0, v[13], gg[7]);
+      const float s1_0 = 0.6324555320336758f * gt1;
+      gv[13] = fmaf(s1_0, g[8], gv[13]); gg[8] = fmaf(s1_0, v[13], gg[8]);
+      gv[14] = fmaf(-s0_0, g[4], gv[14]); gg[4] = fmaf(-s0_0, v[14], gg[4]);
+      const float s2_1 = 0.5477225575051661f * gt2;
+      gv[14] = fmaf(-s2_1, g[6], gv[14]); gg[6] = fmaf(-s2_1, v[14], gg[6]);
+      const float s1_1 = 0.3162277660168379f * gt1;
+      gv[14] = fmaf(s1_1, g[7], gv[14]); gg[7] = fmaf(s1_1, v[14], gg[7]);
+      gv[14] = fmaf(-s2_0, g[8], gv[14]); gg[8] = fmaf(-s2_0, v[14], gg[8]);
+      gv[15] = fmaf(s2_1, g[5], gv[15]); gg[5] = fmaf(s2_1, v[15], gg[5]);
+      const float s0_1 = 0.5477225575051661f * gt0;
+      gv[15] = fmaf(-s0_1, g[7], gv[15]); gg[7] = fmaf(-s0_1, v[15], gg[7]);
+      gv[16] = fmaf(s2_0, g[4], gv[16]); gg[4] = fmaf(s2_0, v[16], gg[4]);
+      gv[16] = fmaf(-s1_1, g[5], gv[16]); gg[5] = fmaf(-s1_1, v[16], gg[5]);
+      gv[16] = fmaf(s0_1, g[6], gv[16]); gg[6] = fmaf(s0_1, v[16], gg[6]);
+      gv[16] = fmaf(-s0_0, g[8], gv[16]); gg[8] = fmaf(-s0_0, v[16], gg[8]);
+      gv[17] = fmaf(-s1_0, g[4], gv[17]); gg[4] = fmaf(-s1_0, v[17], gg[4]);
+      gv[17] = fmaf(s2_0, g[5], gv[17]); gg[5] = fmaf(s2_0, v[17], gg[5]);
+      gv[17] = fmaf(s0_0, g[7], gv[17]); gg[7] = fmaf(s0_0, v[17], gg[7]);
     }
   }
   static constexpr int NNZ = 137;

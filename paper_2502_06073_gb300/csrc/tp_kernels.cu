@@ -43,66 +43,97 @@ __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Copy `rows` rows of CT floats (16-byte aligned; source rows `stride` floats apart) into a
-// dense [rows][CT] shared buffer with the CT lanes of a team.
-template <int CT>
-__device__ __forceinline__ void stage(float* dst, const float* src, int rows, int stride,
-                                      int lane) {
+// Copy ROWS rows of CT floats (16-byte aligned; source rows `stride` floats apart) into a
+// dense [ROWS][CT] shared buffer with the CT lanes of a team.  When the rows are contiguous
+// (stride == CT: one channel group, C = CT) the copy is one unrolled run of 16-byte chunks.
+template <int CT, int ROWS>
+__device__ __forceinline__ void stage(float* dst, const float* src, int stride, int lane) {
   constexpr int CH = CT / 4;   // 16-byte chunks per row
-  for (int i = lane; i < rows * CH; i += CT) {
+  constexpr int NCH = ROWS * CH;
+  if (stride == CT) {
+#pragma unroll
+    for (int j = 0; j < (NCH + CT - 1) / CT; ++j) {
+      const int i = lane + j * CT;
+      if (NCH % CT == 0 || i < NCH) cp_async16(dst + 4 * i, src + 4 * i);
+    }
+    return;
+  }
+  for (int i = lane; i < NCH; i += CT) {
     const int r = i / CH, q = i - r * CH;
     cp_async16(dst + r * CT + 4 * q, src + (size_t)r * stride + 4 * q);
   }
 }
 
-// Sum of 16 per-lane values over the CT lanes of a team by recursive halving: each round
-// a lane keeps half of its values and sends the other half to its partner, so the team
-// needs 15 (CT = 16) or 16 (CT = 32) shuffles instead of 16 butterfly reductions.  On
-// return the lane holds the team total of value index (lane >> 1) for CT = 32 and
-// (lane & 15) for CT = 16.
-template <int CT>
-__device__ __forceinline__ float team_reduce_scatter16(const float (&p)[16], int lane) {
-  const unsigned mask = team_mask<CT>();
-  float a8[8], a4[4], a2[2];
-  {
-    constexpr int o = CT / 2;
-    const bool hi = (lane & o) != 0;
+// The NY harmonics of an edge-feature record (at FF_EF_Y = 15: one scalar load, then
+// 16-byte loads from the aligned offset 16 on).
+template <int NY>
+__device__ __forceinline__ void load_y(const float* rec, float (&y)[NY]) {
+  static_assert(FF_EF_Y == 15 && FF_EF_STRIDE >= 16 + 4 * ((NY + 2) / 4), "record layout");
+  y[0] = rec[FF_EF_Y];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const float keep = hi ? p[8 + i] : p[i], send = hi ? p[i] : p[8 + i];
-      a8[i] = keep + __shfl_xor_sync(mask, send, o, CT);
-    }
+  for (int k = 0; k < (NY + 2) / 4; ++k) {
+    const float4 q = *reinterpret_cast<const float4*>(rec + 16 + 4 * k);
+    if (1 + 4 * k < NY) y[1 + 4 * k] = q.x;
+    if (2 + 4 * k < NY) y[2 + 4 * k] = q.y;
+    if (3 + 4 * k < NY) y[3 + 4 * k] = q.z;
+    if (4 + 4 * k < NY) y[4 + 4 * k] = q.w;
   }
-  {
-    constexpr int o = CT / 4;
-    const bool hi = (lane & o) != 0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const float keep = hi ? a8[4 + i] : a8[i], send = hi ? a8[i] : a8[4 + i];
-      a4[i] = keep + __shfl_xor_sync(mask, send, o, CT);
-    }
-  }
-  {
-    constexpr int o = CT / 8;
-    const bool hi = (lane & o) != 0;
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const float keep = hi ? a4[2 + i] : a4[i], send = hi ? a4[i] : a4[2 + i];
-      a2[i] = keep + __shfl_xor_sync(mask, send, o, CT);
-    }
-  }
-  constexpr int o = CT / 16;
-  const bool hi = (lane & o) != 0;
-  float r = (hi ? a2[1] : a2[0]) + __shfl_xor_sync(mask, hi ? a2[0] : a2[1], o, CT);
-  if (CT == 32) r += __shfl_xor_sync(mask, r, 1, CT);
-  return r;
 }
 
-// Which of the 9 harmonic components a lane holds after team_reduce_scatter16 (-1: none).
-template <int CT>
+// Sum of N per-lane values over the CT lanes of a team by recursive halving with an uneven
+// split: in the round over lane bit O a lane holds S values (real ones first, zero pads
+// last), keeps the first H = ceil(S/2) (bit O clear) or the rest padded to H (bit O set)
+// and sends the other part to its partner, so a round costs H shuffles; once one value is
+// left, the remaining lane bits are summed by butterfly.  N = 9 takes 12 shuffles on 32
+// lanes (16 with a power-of-two split of 16 padded values).
+template <int CT, int O, int S>
+struct TeamRS {
+  static __device__ __forceinline__ float run(const float* a, int lane, unsigned mask) {
+    static_assert(O > 0, "fewer lanes than values");
+    constexpr int H = (S + 1) / 2;
+    const bool hi = (lane & O) != 0;
+    float b[H];
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      const float lo_v = a[i], hi_v = (H + i < S) ? a[H + i] : 0.f;
+      const float keep = hi ? hi_v : lo_v, send = hi ? lo_v : hi_v;
+      b[i] = keep + __shfl_xor_sync(mask, send, O, CT);
+    }
+    return TeamRS<CT, O / 2, H>::run(b, lane, mask);
+  }
+};
+template <int CT, int O>
+struct TeamRS<CT, O, 1> {
+  static __device__ __forceinline__ float run(const float* a, int lane, unsigned mask) {
+    float r = a[0];
+#pragma unroll
+    for (int o = O; o > 0; o >>= 1) r += __shfl_xor_sync(mask, r, o, CT);
+    return r;
+  }
+};
+template <int CT, int N>
+__device__ __forceinline__ float team_reduce_scatter(const float (&p)[N], int lane) {
+  return TeamRS<CT, CT / 2, N>::run(p, lane, team_mask<CT>());
+}
+
+// Which value a lane writes after team_reduce_scatter<CT, N> (-1: none): the split of each
+// round replayed on the lane's bits with the count of real values; of the lanes that share
+// a total after the butterfly, the one with those bits clear.
+template <int CT, int N>
 __device__ __forceinline__ int rs_index(int lane) {
-  if (CT == 32) return (lane & 1) ? -1 : ((lane >> 1) < 9 ? (lane >> 1) : -1);
-  return (lane & 15) < 9 ? (lane & 15) : -1;
+  int base = 0, real = N, s = N, o = CT / 2;
+  for (; o > 0 && s > 1; o >>= 1) {
+    const int h = (s + 1) / 2;
+    if (lane & o) {
+      base += h;
+      real = real > h ? real - h : 0;
+    } else {
+      real = real < h ? real : h;
+    }
+    s = h;
+  }
+  const int rest = o > 0 ? 2 * o - 1 : 0;
+  return (real == 1 && (lane & rest) == 0) ? base : -1;
 }
 
 // Per-edge shared-memory record of a team: for the first layer (V^0 = w (x) Y formed in
@@ -152,7 +183,7 @@ __device__ __forceinline__ void stage_ef_w(float* rec, int e, int lane, int C, i
                                            const float* ef, const float* W, int ldw) {
   if (lane < FF_EF_STRIDE / 4)
     cp_async16(rec + 4 * lane, ef + (size_t)e * FF_EF_STRIDE + 4 * lane);
-  stage<CT>(rec + FF_EF_STRIDE, W + (size_t)e * ldw + grp * CT, LMAX + 1, C, lane);
+  stage<CT, LMAX + 1>(rec + FF_EF_STRIDE, W + (size_t)e * ldw + grp * CT, C, lane);
 }
 
 template <int LMAX, int INK, int OUTK, int CT, bool BWD>
@@ -165,13 +196,14 @@ __device__ __forceinline__ void stage_edge(float* rec, int e, int lane, int C, i
   if (INK == 0) {
     if (lane < FF_EF_STRIDE / 4)
       cp_async16(rec + 4 * lane, ef + (size_t)e * FF_EF_STRIDE + 4 * lane);
-    stage<CT>(rec + R::OFF_W, W + (size_t)e * ldw + grp * CT, LMAX + 1, C, lane);
+    stage<CT, LMAX + 1>(rec + R::OFF_W, W + (size_t)e * ldw + grp * CT, C, lane);
   } else {
-    stage<CT>(rec + R::OFF_V, vin + (size_t)e * K::DIN * C, K::DIN, C, lane);
+    stage<CT, K::DIN>(rec + R::OFF_V, vin + (size_t)e * K::DIN * C, C, lane);
   }
   if (BWD) {
-    stage<CT>(rec + R::OFF_GS, GX + (size_t)e * ldx + D + grp * CT, K::NS, C, lane);
-    if (!R::LAST) stage<CT>(rec + R::OFF_GVO, gvout + (size_t)e * K::DOUT * C, K::DOUT, C, lane);
+    stage<CT, K::NS>(rec + R::OFF_GS, GX + (size_t)e * ldx + D + grp * CT, C, lane);
+    if (!R::LAST)
+      stage<CT, K::DOUT>(rec + R::OFF_GVO, gvout + (size_t)e * K::DOUT * C, C, lane);
   }
 }
 
@@ -221,11 +253,13 @@ k_env_tp_fwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
     cp_wait<NSR - 1>();
     __syncwarp(team_mask<CT>());
     const float* rec = buf + (i % NSR) * SR;
+    float y[NY];
+    load_y<NY>(rec, y);
 #pragma unroll
     for (int l = 0; l <= LMAX; ++l) {
       const float w = rec[FF_EF_STRIDE + l * CT + lane];
 #pragma unroll
-      for (int m = 0; m < 2 * l + 1; ++m) G_[l * l + m] += w * rec[FF_EF_Y + l * l + m];
+      for (int m = 0; m < 2 * l + 1; ++m) G_[l * l + m] += w * y[l * l + m];
     }
     __syncwarp(team_mask<CT>());
   }
@@ -250,18 +284,20 @@ k_env_tp_fwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
     const float* rec = buf + (i % NSTG) * SST;
     float v[K::DIN];
     if (INK == 0) {
+      float y[NY];
+      load_y<NY>(rec, y);
 #pragma unroll
       for (int l = 0; l <= LMAX; ++l) {
         const float w = rec[R::OFF_W + l * CT + lane];
 #pragma unroll
-        for (int m = 0; m < 2 * l + 1; ++m) v[l * l + m] = w * rec[FF_EF_Y + l * l + m];
+        for (int m = 0; m < 2 * l + 1; ++m) v[l * l + m] = w * y[l * l + m];
       }
     } else {
 #pragma unroll
       for (int k = 0; k < K::DIN; ++k) v[k] = rec[R::OFF_V + k * CT + lane];
     }
     float s[K::NS], vo[K::DOUT];
-    K::fwd(v, G_, th, s, vo);
+    K::template fwd<1>(v, G_, th, s, vo);
 #pragma unroll
     for (int q = 0; q < K::NS; ++q) {
       const size_t xi = (size_t)e * ldx + D + q * C + c;
@@ -323,7 +359,7 @@ k_env_tp_bwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
     gG[k] = 0.f;
   }
   const float* th = thetaT + (size_t)c * K::NP;
-  const int ridx = rs_index<CT>(lane);
+  const int ridx = rs_index<CT, NY>(lane);
   for (int e = eb; e < ee; ++e) {
     const int i = e - eb;
     if (e + NSTG - 1 < ee) fetch(e + NSTG - 1, (i + NSTG - 1) % NSTG);
@@ -332,14 +368,15 @@ k_env_tp_bwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
     __syncwarp(team_mask<CT>());
     const float* rec = buf + (i % NSTG) * SST;
     float v[K::DIN], gv[K::DIN];
-    float wl[LMAX + 1];
+    float wl[LMAX + 1], y[NY];
 #pragma unroll
     for (int l = 0; l <= LMAX; ++l) wl[l] = INK == 0 ? rec[R::OFF_W + l * CT + lane] : 0.f;
     if (INK == 0) {
+      load_y<NY>(rec, y);
 #pragma unroll
       for (int l = 0; l <= LMAX; ++l)
 #pragma unroll
-        for (int m = 0; m < 2 * l + 1; ++m) v[l * l + m] = wl[l] * rec[FF_EF_Y + l * l + m];
+        for (int m = 0; m < 2 * l + 1; ++m) v[l * l + m] = wl[l] * y[l * l + m];
     } else {
 #pragma unroll
       for (int k = 0; k < K::DIN; ++k) v[k] = rec[R::OFF_V + k * CT + lane];
@@ -351,23 +388,21 @@ k_env_tp_bwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
     for (int q = 0; q < K::NS; ++q) gs[q] = rec[R::OFF_GS + q * CT + lane];
 #pragma unroll
     for (int k = 0; k < K::DOUT; ++k) gvo[k] = LAST ? 0.f : rec[R::OFF_GVO + k * CT + lane];
-    K::bwd(v, G_, th, gs, gvo, gv, gG);
+    K::template bwd<1>(v, G_, th, gs, gvo, gv, gG);
     if (INK == 0) {
       // V^0 = w (x) Y: gradient to the env weights and to the harmonics
-      float p[16];
+      float p[NY];
 #pragma unroll
       for (int l = 0; l <= LMAX; ++l) {
         float gw = 0.f;
 #pragma unroll
         for (int m = 0; m < 2 * l + 1; ++m) {
-          gw += gv[l * l + m] * rec[FF_EF_Y + l * l + m];
+          gw += gv[l * l + m] * y[l * l + m];
           p[l * l + m] = gv[l * l + m] * wl[l];
         }
         GW[(size_t)e * ldw + l * C + c] = gw;
       }
-#pragma unroll
-      for (int k = NY; k < 16; ++k) p[k] = 0.f;
-      const float t = team_reduce_scatter16<CT>(p, lane);
+      const float t = team_reduce_scatter<CT, NY>(p, lane);
       if (ridx >= 0) gY_v0[(size_t)e * gy_stride + grp * 9 + ridx] = t;
     } else {
 #pragma unroll
@@ -406,14 +441,15 @@ k_env_tp_bwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
     cp_wait<NSR - 1>();
     __syncwarp(team_mask<CT>());
     const float* rec = buf + (i % NSR) * SR;
-    float p[16];
+    float p[NY], y[NY];
+    load_y<NY>(rec, y);
 #pragma unroll
     for (int l = 0; l <= LMAX; ++l) {
       const float wl = rec[FF_EF_STRIDE + l * CT + lane];
       float gw = 0.f;
 #pragma unroll
       for (int m = 0; m < 2 * l + 1; ++m) {
-        gw += gG[l * l + m] * rec[FF_EF_Y + l * l + m];
+        gw += gG[l * l + m] * y[l * l + m];
         p[l * l + m] = gG[l * l + m] * wl;
       }
       const float tot = gw0[l] + gw;
@@ -421,9 +457,7 @@ k_env_tp_bwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
       if (GWb) GWb[wi] = __float2bfloat16_rn(tot);
       else GW[wi] = tot;
     }
-#pragma unroll
-    for (int k = NY; k < 16; ++k) p[k] = 0.f;
-    const float t = team_reduce_scatter16<CT>(p, lane);
+    const float t = team_reduce_scatter<CT, NY>(p, lane);
     if (ridx >= 0) gY_env[(size_t)e * gy_stride + grp * 9 + ridx] = t;
     __syncwarp(team_mask<CT>());
   }
