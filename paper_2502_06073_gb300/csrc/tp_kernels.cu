@@ -168,8 +168,10 @@ struct EdgeRec {
   static constexpr int NSTG_FIT = BUDGET / (TEAMS * SST * 4);
   static constexpr int NSTG = NSTG_FIT < 2 ? 2 : (NSTG_FIT > 4 ? 4 : NSTG_FIT);
   // the passes that read only the edge-feature row and the env weights use the same
-  // buffer as a deeper ring of smaller records (2 to 8 of them)
-  static constexpr int SR = FF_EF_STRIDE + (LMAX + 1) * CT;
+  // buffer as a deeper ring of smaller records (2 to 8 of them); in the adjoint of the
+  // first layer these also carry the FP32 weight gradients of its first pass
+  static constexpr int OFF_GW1 = FF_EF_STRIDE + (LMAX + 1) * CT;
+  static constexpr int SR = OFF_GW1 + ((BWD && INK == 0) ? (LMAX + 1) * CT : 0);
   static constexpr int NSR_FIT = NSTG * SST / SR;
   static constexpr int NSR = NSR_FIT < 2 ? 2 : (NSR_FIT > 8 ? 8 : NSR_FIT);
   static constexpr int BUF = NSTG * SST > NSR * SR ? NSTG * SST : NSR * SR;
@@ -318,8 +320,11 @@ k_env_tp_fwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
 // back to every edge's env weights and harmonics.  The harmonic gradients of each (pass,
 // channel group) go to their own slice of gY (written once, no read-modify-write); the
 // geometric adjoint sums the slices in a fixed order.
+// (Resident blocks of 4 warps per SM: eight for the last layer, whose adjoint has no
+// feature gradients to keep, five for the others, the count the first layer's shared
+// memory allows; the register budget follows, at most 64 and 96 a thread.)
 template <int LMAX, int INK, int OUTK, int CT>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, OUTK == 2 ? 8 : 5)
 k_env_tp_bwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
              const float* __restrict__ ef, const float* __restrict__ W, int ldw,
              const float* __restrict__ Vin, const float* __restrict__ thetaT,
@@ -411,33 +416,29 @@ k_env_tp_bwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
     __syncwarp(team_mask<CT>());
   }
   // adjoint of the environment sum, fanned back out to every edge of the atom, over a ring
-  // of (edge-feature row, env-weight slice) records; the layer-1 weight gradients of the
-  // first pass (this lane's own stores) are read one edge ahead
+  // of (edge-feature row, env-weight slice) records; in the first layer each record also
+  // brings the weight gradients that the first pass wrote for its edge (the team's own
+  // stores, ordered before these copies by the warp barrier that ended that pass), so they
+  // are fetched as far ahead as the rest of the record
 #pragma unroll
   for (int k = 0; k < NY; ++k) gG[k] *= inv_sqrt_nu;
   constexpr int SR = R::SR, NSR = R::NSR;
   auto fetch1 = [&](int e, int slot) {
     stage_ef_w<LMAX, CT>(buf + slot * SR, e, lane, C, grp, ef, W, ldw);
+    if (INK == 0)
+      stage<CT, LMAX + 1>(buf + slot * SR + R::OFF_GW1, GW + (size_t)e * ldw + grp * CT, C,
+                          lane);
   };
+  __syncwarp(team_mask<CT>());
 #pragma unroll
   for (int p = 0; p < NSR - 1; ++p) {
     if (eb + p < ee) fetch1(eb + p, p);
     cp_commit();
   }
-  float gw_next[LMAX + 1];
-#pragma unroll
-  for (int l = 0; l <= LMAX; ++l)
-    gw_next[l] = (INK == 0 && eb < ee) ? GW[(size_t)eb * ldw + l * C + c] : 0.f;
   for (int e = eb; e < ee; ++e) {
     const int i = e - eb;
     if (e + NSR - 1 < ee) fetch1(e + NSR - 1, (i + NSR - 1) % NSR);
     cp_commit();
-    float gw0[LMAX + 1];
-#pragma unroll
-    for (int l = 0; l <= LMAX; ++l) {
-      gw0[l] = gw_next[l];
-      if (INK == 0 && e + 1 < ee) gw_next[l] = GW[(size_t)(e + 1) * ldw + l * C + c];
-    }
     cp_wait<NSR - 1>();
     __syncwarp(team_mask<CT>());
     const float* rec = buf + (i % NSR) * SR;
@@ -446,13 +447,14 @@ k_env_tp_bwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
 #pragma unroll
     for (int l = 0; l <= LMAX; ++l) {
       const float wl = rec[FF_EF_STRIDE + l * CT + lane];
+      const float gw0 = INK == 0 ? rec[R::OFF_GW1 + l * CT + lane] : 0.f;
       float gw = 0.f;
 #pragma unroll
       for (int m = 0; m < 2 * l + 1; ++m) {
         gw += gG[l * l + m] * y[l * l + m];
         p[l * l + m] = gG[l * l + m] * wl;
       }
-      const float tot = gw0[l] + gw;
+      const float tot = gw0 + gw;
       const size_t wi = (size_t)e * ldw + l * C + c;
       if (GWb) GWb[wi] = __float2bfloat16_rn(tot);
       else GW[wi] = tot;
