@@ -55,13 +55,16 @@ __global__ void k_edge_features(long long E, const int* __restrict__ src,
   const double dx = (pos[3 * (long long)j] - pos[3 * (long long)i]) + s0 * L[0];
   const double dy = (pos[3 * (long long)j + 1] - pos[3 * (long long)i + 1]) + s1 * L[1];
   const double dz = (pos[3 * (long long)j + 2] - pos[3 * (long long)i + 2]) + s2 * L[2];
-  const double rd = sqrt(dx * dx + dy * dy + dz * dz);
-  const float r = (float)rd;
-  const float ux = (float)(dx / rd), uy = (float)(dy / rd), uz = (float)(dz / rd);
-  float* o = ef + e * FF_EF_STRIDE;
+  // the displacement in FP64 (differences of FP64 positions), everything after it in FP32:
+  // the FP64 units of this part run far below its FP32 rate
+  const float r = sqrtf((float)(dx * dx + dy * dy + dz * dz));
+  const float ux = (float)dx / r, uy = (float)dy / r, uz = (float)dz / r;
+  float o[FF_EF_STRIDE];
   o[0] = ux; o[1] = uy; o[2] = uz; o[3] = r;
   const float pref = sqrtf(2.f / rc);
-  for (int n = 1; n <= n_basis; ++n) o[FF_EF_B + n - 1] = pref * sinf(n * kPi * r / rc) / r;
+#pragma unroll
+  for (int n = 1; n <= FF_EF_F - FF_EF_B; ++n)
+    o[FF_EF_B + n - 1] = n <= n_basis ? pref * sinf(n * kPi * r / rc) / r : 0.f;
   o[FF_EF_F] = envelope_f(r / rc, p);
   float* y = o + FF_EF_Y;
   y[0] = 1.f;
@@ -76,8 +79,13 @@ __global__ void k_edge_features(long long E, const int* __restrict__ src,
 #pragma unroll
     for (int k = 4; k < 9; ++k) y[k] = 0.f;
   }
-  zz[2 * e] = Z[i];
-  zz[2 * e + 1] = Z[j];
+  // the 96-byte record as six 16-byte stores
+  static_assert(FF_EF_STRIDE == 24 && FF_EF_Y + 9 == FF_EF_STRIDE, "record layout");
+  float4* dst = reinterpret_cast<float4*>(ef + e * FF_EF_STRIDE);
+#pragma unroll
+  for (int q = 0; q < FF_EF_STRIDE / 4; ++q)
+    dst[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+  *reinterpret_cast<int2*>(zz + 2 * e) = make_int2(Z[i], Z[j]);
 }
 
 // First two-body layer: one-hot(Z_i) || one-hot(Z_j) || B(r) times W0 = two table rows plus
