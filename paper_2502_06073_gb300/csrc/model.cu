@@ -115,13 +115,18 @@ __global__ void k_twobody_in(long long E, int width, int n_basis, const float* _
   const int slot = threadIdx.x / tpe, o = 4 * (threadIdx.x - slot * tpe);
   const long long e = (long long)blockIdx.x * epb + slot;
   if (slot >= epb || e >= E) return;
-  const int zi = zz[2 * e], zj = zz[2 * e + 1];
-  const float* bb = ef + e * FF_EF_STRIDE + FF_EF_B;
-  float b[10];
-#pragma unroll
-  for (int n = 0; n < 10; ++n) b[n] = n < n_basis ? bb[n] : 0.f;
-  const float4 ri = *reinterpret_cast<const float4*>(W0 + (zi - 1) * width + o);
-  const float4 rj = *reinterpret_cast<const float4*>(W0 + (FF_N_SPECIES + zj - 1) * width + o);
+  const int2 zp = *reinterpret_cast<const int2*>(zz + 2 * e);
+  // the radial basis (floats 4..13 of the record) and the envelope (float 14) as three
+  // 16-byte reads
+  static_assert(FF_EF_B == 4 && FF_EF_F == 14, "record layout");
+  const float* rec = ef + e * FF_EF_STRIDE;
+  const float4 b0 = *reinterpret_cast<const float4*>(rec + 4);
+  const float4 b1 = *reinterpret_cast<const float4*>(rec + 8);
+  const float4 b2 = *reinterpret_cast<const float4*>(rec + 12);
+  const float b[10] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w, b2.x, b2.y};
+  const float4 ri = *reinterpret_cast<const float4*>(W0 + (zp.x - 1) * width + o);
+  const float4 rj =
+      *reinterpret_cast<const float4*>(W0 + (FF_N_SPECIES + zp.y - 1) * width + o);
   float acc[4] = {ri.x + rj.x, ri.y + rj.y, ri.z + rj.z, ri.w + rj.w};
   const float* wr = W0 + 2 * FF_N_SPECIES * width + o;
 #pragma unroll
@@ -130,7 +135,7 @@ __global__ void k_twobody_in(long long E, int width, int n_basis, const float* _
     const float4 w = *reinterpret_cast<const float4*>(wr + n * width);
     acc[0] += b[n] * w.x; acc[1] += b[n] * w.y; acc[2] += b[n] * w.z; acc[3] += b[n] * w.w;
   }
-  const float f = final_layer ? ef[e * FF_EF_STRIDE + FF_EF_F] : 1.f;
+  const float f = final_layer ? b2.z : 1.f;
   float z[4], v[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -279,8 +284,8 @@ __global__ void k_edge_grad(long long E, int w0, int n_basis, float rc, int p, i
 #pragma unroll
     for (int n = 0; n < 10; ++n) {
       if (n < n_basis) {
-        const float* wr = s_wb + n * w0 + 4 * k4;
-        gB[n] += v.x * wr[0] + v.y * wr[1] + v.z * wr[2] + v.w * wr[3];
+        const float4 w = *reinterpret_cast<const float4*>(s_wb + n * w0 + 4 * k4);
+        gB[n] += v.x * w.x + v.y * w.y + v.z * w.z + v.w * w.w;
       }
     }
   }
