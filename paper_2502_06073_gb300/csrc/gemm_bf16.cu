@@ -187,7 +187,10 @@ __device__ __forceinline__ void epi_batch(const EpiParams& ep, const float4 (&ac
                                           const float* fr, Rows row, int col,
                                           bool colok, float (*racc)[2]) {
   if constexpr (MODE == EPI_HEAD) {
-    // readout: partial dot products of this lane's 4 columns, summed over rows later
+    // readout: partial dot products of this lane's 4 columns with the readout vector w,
+    // summed over the row's lanes later: racc[.][0] = sum w a (residual stream),
+    // racc[.][1] = sum w silu(v); the row's energy is beta (racc0 + f racc1), and
+    // dE/dz = beta f w silu'(v) with silu'(v) = s + silu(v) (1 - s), s = sigmoid(v)
     if (!colok) return;
     const float4 w4 = *reinterpret_cast<const float4*>(ep.wv + col);
     const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
@@ -198,14 +201,15 @@ __device__ __forceinline__ void epi_batch(const EpiParams& ep, const float4 (&ac
       const float a4[4] = {aux[i].x, aux[i].y, aux[i].z, aux[i].w};
       const float v[4] = {ep.alpha * acc[i].x, ep.alpha * acc[i].y, ep.alpha * acc[i].z,
                           ep.alpha * acc[i].w};
+      const float bf = ep.beta * fr[i];
       float g[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const float sg = sigm_fast(v[j]);
         const float sv = v[j] * sg;
-        racc[i][0] += wv[j] * (ep.beta * (a4[j] + fr[i] * sv));
+        racc[i][0] += wv[j] * a4[j];
         racc[i][1] += wv[j] * sv;
-        g[j] = ep.beta * fr[i] * (sg * (1.f + v[j] * (1.f - sg))) * wv[j];
+        g[j] = (bf * wv[j]) * (sg + sv * (1.f - sg));
       }
       __nv_bfloat162 lo = __floats2bfloat162_rn(g[0], g[1]);
       __nv_bfloat162 hi = __floats2bfloat162_rn(g[2], g[3]);
@@ -583,9 +587,9 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         const int rl = quad * 32 + 4 * i + rsub;
         const int row = m0 + rl;
         if (ok && row < M) {
-          const float e_ = racc[i][0] + red[2 * rl];
+          const float a_ = racc[i][0] + red[2 * rl];
           const float g_ = racc[i][1] + red[2 * rl + 1];
-          ep.eout[row] = e_;
+          ep.eout[row] = ep.beta * (a_ + fr[i] * g_);
           ep.gfo[row] = ep.beta * g_;
         }
       }
@@ -871,7 +875,7 @@ k_gemm_pp(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
           for (int i = 0; i < 8; ++i) {
             const int row = m0 + quad * 32 + 4 * i + (lane >> 3);
             if (row < M) {
-              atomicAdd(&ep.eout[row], racc[i][0]);
+              atomicAdd(&ep.eout[row], ep.beta * (racc[i][0] + fr[i] * racc[i][1]));
               atomicAdd(&ep.gfo[row], ep.beta * racc[i][1]);
             }
           }
