@@ -185,6 +185,7 @@ struct ff_ctx {
   void* wsp = nullptr;
   size_t wsp_bytes = 0;
   float* ef = nullptr; int* zz = nullptr;
+  float* fenv = nullptr;   // the cutoff envelope per edge, dense (one float per edge)
   float* z2b[4] = {nullptr}; float* h2b[4] = {nullptr};
   // pre-activations of the tensor-core path, kept in bf16 for the adjoint's SiLU'
   __nv_bfloat16* z2bb[4] = {nullptr};
@@ -542,6 +543,7 @@ int ensure_workspace(ff_ctx* c, long long ecap, int acap, long long budget_edges
   };
   f32(&c->ef, ecap * FF_EF_STRIDE);
   plan.push_back({(void**)&c->zz, (size_t)ecap * 8});
+  f32(&c->fenv, ecap);
   for (int k = 0; k < c->n2b; ++k) {
     if (tc) b16(&c->z2bb[k], ecap * hp.two_body[k]);
     else f32(&c->z2b[k], ecap * hp.two_body[k]);
@@ -614,7 +616,7 @@ int ensure_workspace(ff_ctx* c, long long ecap, int acap, long long budget_edges
 
 size_t bytes_per_edge(const ff_ctx* c) {
   const ff_hparams& hp = c->hp;
-  size_t b = FF_EF_STRIDE * 4 + 8;
+  size_t b = FF_EF_STRIDE * 4 + 8 + 4;
   for (int k = 0; k < c->n2b; ++k) b += (size_t)hp.two_body[k] * 4 * (k < c->n2b - 1 ? 2 : 1);
   b += (size_t)(c->NL + 1) * c->ldx * 4;
   for (int L = 1; L <= c->NL; ++L) {
@@ -824,8 +826,8 @@ void forward_chunk(ff_ctx* c, const double* pos, int a0, int a1, float* E_atom, 
   const int* rp = c->row_ptr + a0;
   const int na = a1 - a0;
   launch_edge_features(Ec, c->src + e0, c->col + e0, c->shift + e0, pos, c->L_d, 0, c->Z, hp.rc,
-                       hp.n_basis, hp.poly_p, c->lmax, c->ef, c->zz, s);
-  const float* fptr = c->ef + FF_EF_F;
+                       hp.n_basis, hp.poly_p, c->lmax, c->ef, c->zz, c->fenv, s);
+  const float* fptr = c->fenv;   // read with stride 1 by the GEMM epilogues
   // two-body latent MLP
   const int w0 = hp.two_body[0];
   const float a0f = (float)(1.0 / sqrt((double)(2 * FF_N_SPECIES + hp.n_basis)));
@@ -842,7 +844,7 @@ void forward_chunk(ff_ctx* c, const double* pos, int a0, int a1, float* E_atom, 
       ep.alpha = (float)(1.0 / sqrt((double)win));
       ep.pre = c->z2b[k]; ep.preb = c->z2bb[k]; ep.ldp = wout;
       if (last) {
-        ep.f = fptr; ep.ldf = FF_EF_STRIDE;
+        ep.f = fptr; ep.ldf = 1;
         if (tc) { ep.outb = c->Xb[0]; ep.ldob = c->ldx; }
         else { ep.out = c->X[0]; ep.ldo = c->ldx; }
       } else if (tc) {
@@ -881,7 +883,7 @@ void forward_chunk(ff_ctx* c, const double* pos, int a0, int a1, float* E_atom, 
         // envelope-gradient seed and dE/dz of this layer; x^N itself is never stored
         el.pre = nullptr; el.preb = nullptr;
         el.resb = c->Xb[L - 1]; el.ldr = c->ldx;
-        el.f = fptr; el.ldf = FF_EF_STRIDE;
+        el.f = fptr; el.ldf = 1;
         el.beta = (float)(1.0 / sqrt(2.0));
         el.wv = c->w_eff;
         el.outb = c->GZL; el.ldob = c->D;
@@ -892,7 +894,7 @@ void forward_chunk(ff_ctx* c, const double* pos, int a0, int a1, float* E_atom, 
       }
       if (lastk) {
         el.out = c->X[L]; el.ldo = c->ldx;   // null in the tensor-core path but for x^N
-        el.f = fptr; el.ldf = FF_EF_STRIDE;
+        el.f = fptr; el.ldf = 1;
         el.beta = (float)(1.0 / sqrt(2.0));
         el.ldr = c->ldx;
         if (tc) {
@@ -1014,7 +1016,7 @@ void backward_chunk(ff_ctx* c, int a0, int a1, const double* seed, cudaStream_t 
         ep.alpha2 = below_2b ? 1.f : r2;
         ep.gzo = c->GZb[gzb ^ 1]; ep.ldgzo = c->D;   // not this GEMM's own operand
         zb0 = gzb ^ 1;
-        ep.f = c->ef + FF_EF_F; ep.ldf = FF_EF_STRIDE;
+        ep.f = c->fenv; ep.ldf = 1;
         ep.gfp = c->gfp + (size_t)n_gfp * c->wcap; ep.gfp_ld = c->wcap;
         n_gfp += nsl;
         rr_done = true;

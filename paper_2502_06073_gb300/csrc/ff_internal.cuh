@@ -146,7 +146,7 @@ struct ModelDev;   // defined in ff_api.cu
 void launch_edge_features(long long E, const int* src, const int* col, const int* shift,
                           const double* pos, const double* L, int pbc_any, const int* Z,
                           float rc, int n_basis, int p, int lmax, float* ef, int* zz,
-                          cudaStream_t s);
+                          float* fenv, cudaStream_t s);
 void launch_twobody_in(long long E, int width, int n_basis, const float* ef, const int* zz,
                        const float* W0, float alpha, float* pre, __nv_bfloat16* preb,
                        float* out, int ldo, __nv_bfloat16* outb, int ldob, int final_layer,

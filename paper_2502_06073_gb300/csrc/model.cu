@@ -46,7 +46,8 @@ __global__ void k_edge_features(long long E, const int* __restrict__ src,
                                 const int* __restrict__ col, const int* __restrict__ shift,
                                 const double* __restrict__ pos, const double* __restrict__ L,
                                 const int* __restrict__ Z, float rc, int n_basis, int p,
-                                int lmax, float* __restrict__ ef, int* __restrict__ zz) {
+                                int lmax, float* __restrict__ ef, int* __restrict__ zz,
+                                float* __restrict__ fenv) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
   const int i = src[e], j = col[e];
@@ -86,6 +87,7 @@ __global__ void k_edge_features(long long E, const int* __restrict__ src,
   for (int q = 0; q < FF_EF_STRIDE / 4; ++q)
     dst[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
   *reinterpret_cast<int2*>(zz + 2 * e) = make_int2(Z[i], Z[j]);
+  fenv[e] = o[FF_EF_F];   // the envelope again, densely (the GEMM epilogues' per-row factor)
 }
 
 // First two-body layer: one-hot(Z_i) || one-hot(Z_j) || B(r) times W0 = two table rows plus
@@ -518,11 +520,11 @@ __global__ void k_check_finite(const float* __restrict__ F, long long n, int* __
 void launch_edge_features(long long E, const int* src, const int* col, const int* shift,
                           const double* pos, const double* L, int /*pbc_any*/, const int* Z,
                           float rc, int n_basis, int p, int lmax, float* ef, int* zz,
-                          cudaStream_t s) {
+                          float* fenv, cudaStream_t s) {
   ProfScope ps_(PC_EDGE_FEAT, s);
   if (E <= 0) return;
   k_edge_features<<<ff_cdiv(E, 256), 256, 0, s>>>(E, src, col, shift, pos, L, Z, rc, n_basis, p,
-                                                 lmax, ef, zz);
+                                                 lmax, ef, zz, fenv);
   ff_count_launch(1);
 }
 
