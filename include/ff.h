@@ -62,8 +62,10 @@ enum {
  *   edge_eng[]        hidden widths of the linear edge-energy MLP (output width 1 implied)
  *   avg_num_neighbors nu, normalisation of the environment sum
  *   precision         0 = FP32 everywhere; 1 = BF16 latent MLPs on the tensor cores with
- *                     FP32 accumulation: GEMM operands, the residual stream x^L and the
- *                     stored pre-activations are bf16; harmonics, edge features, CG
+ *                     FP32 accumulation: GEMM operands, the residual stream x^L, the
+ *                     stored pre-activations and the env-projection outputs (the
+ *                     env weights w^L, widened to FP32 where the tensor product reads
+ *                     them) are bf16; harmonics, edge features, CG
  *                     products, tensor-product features and every gradient accumulator
  *                     stay FP32, energy/virial/MD reductions FP64
  *   Every width must be a multiple of 16 and at most 512. */

@@ -193,6 +193,8 @@ struct ff_ctx {
   float* X[FF_MAX_LAYERS + 1] = {nullptr};
   float* zlat[FF_MAX_LAYERS + 1][4] = {{nullptr}}; float* hlat[FF_MAX_LAYERS + 1][4] = {{nullptr}};
   float* Wv[FF_MAX_LAYERS + 1] = {nullptr};
+  // env weights of the tensor-core path: the env projection's bf16 output
+  __nv_bfloat16* Wvb[FF_MAX_LAYERS + 1] = {nullptr};
   float* V[FF_MAX_LAYERS + 1] = {nullptr};
   float* Gam[FF_MAX_LAYERS + 1] = {nullptr};
   float* GX[2] = {nullptr}; float* GZ[2] = {nullptr}; float* gV[2] = {nullptr};
@@ -567,7 +569,8 @@ int ensure_workspace(ff_ctx* c, long long ecap, int acap, long long budget_edges
         else f32(&c->hlat[L][k], ecap * hp.latent[k]);
       }
     }
-    f32(&c->Wv[L], ecap * c->ldw);
+    if (tc) b16(&c->Wvb[L], ecap * c->ldw);
+    else f32(&c->Wv[L], ecap * c->ldw);
     if (L < c->NL) f32(&c->V[L], ecap * (long long)c->layer_dout[L] * c->C);
     f32(&c->Gam[L], (long long)acap * 9 * c->C);
   }
@@ -621,7 +624,7 @@ size_t bytes_per_edge(const ff_ctx* c) {
   b += (size_t)(c->NL + 1) * c->ldx * 4;
   for (int L = 1; L <= c->NL; ++L) {
     for (int k = 0; k < c->nlat; ++k) b += (size_t)hp.latent[k] * 4 * (k < c->nlat - 1 ? 2 : 1);
-    b += (size_t)c->ldw * 4;
+    b += (size_t)c->ldw * (hp.precision == 1 ? 2 : 4);
     if (L < c->NL) b += (size_t)c->layer_dout[L] * c->C * 4;
   }
   b += 2 * ((size_t)c->ldx + c->maxw + (size_t)c->maxdim * c->C) * 4;
@@ -860,12 +863,13 @@ void forward_chunk(ff_ctx* c, const double* pos, int a0, int a1, float* E_atom, 
   for (int L = 1; L <= c->NL; ++L) {
     EpiParams ep{};
     ep.alpha = (float)(1.0 / sqrt((double)c->D));
-    ep.out = c->Wv[L]; ep.ldo = c->ldw;
+    if (tc) { ep.outb = c->Wvb[L]; ep.ldob = c->ldw; }
+    else { ep.out = c->Wv[L]; ep.ldo = c->ldw; }
     mlp_gemm(c, EPI_STORE, Ec, c->ldw, c->D, c->X[L - 1], c->Xb[L - 1], c->ldx, c->Wenv[L],
              c->WenvT_b[L], ep, s);
     const int last = L == c->NL ? 1 : 0;
     launch_env_tp_fwd(c->lmax, c->layer_ink[L], c->layer_outk[L], c->C, na, rp, e0, c->ef,
-                      c->Wv[L], c->ldw, L >= 2 ? c->V[L - 1] : nullptr,
+                      tc ? (const void*)c->Wvb[L] : (const void*)c->Wv[L], tc ? 1 : 0, c->ldw, L >= 2 ? c->V[L - 1] : nullptr,
                       last ? nullptr : c->theta[L], tc ? nullptr : c->X[L - 1],
                       tc ? c->Xb[L - 1] : nullptr,
                       c->ldx, c->D, last ? nullptr : c->V[L], c->Gam[L], inv_sqrt_nu, s);
@@ -989,7 +993,7 @@ void backward_chunk(ff_ctx* c, int a0, int a1, const double* seed, cudaStream_t 
     }
     const int last = L == c->NL ? 1 : 0;
     launch_env_tp_bwd(c->lmax, c->layer_ink[L], c->layer_outk[L], c->C, na, rp, e0, c->ef,
-                      c->Wv[L], c->ldw, L >= 2 ? c->V[L - 1] : nullptr,
+                      tc ? (const void*)c->Wvb[L] : (const void*)c->Wv[L], tc ? 1 : 0, c->ldw, L >= 2 ? c->V[L - 1] : nullptr,
                       last ? nullptr : c->theta[L], c->GX[cur], c->ldx, c->D,
                       last ? nullptr : c->gV[gvb],
                       L >= 2 ? c->gV[gvb ^ 1] : nullptr, c->GW, tc ? c->GWb : nullptr,

@@ -151,13 +151,16 @@ void launch_twobody_in(long long E, int width, int n_basis, const float* ef, con
                        const float* W0, float alpha, float* pre, __nv_bfloat16* preb,
                        float* out, int ldo, __nv_bfloat16* outb, int ldob, int final_layer,
                        cudaStream_t s);
+// W: env weights [E][ldw], FP32 (w_bf16 = 0) or bf16 (w_bf16 = 1)
 void launch_env_tp_fwd(int lmax, int in_kind, int out_kind, int C, int n_atoms,
-                       const int* row_ptr, int e0, const float* ef, const float* W, int ldw,
+                       const int* row_ptr, int e0, const float* ef, const void* W, int w_bf16,
+                       int ldw,
                        const float* Vin, const float* theta, float* X, __nv_bfloat16* Xb,
                        int ldx, int D, float* Vout, float* Gam, float inv_sqrt_nu,
                        cudaStream_t s);
 void launch_env_tp_bwd(int lmax, int in_kind, int out_kind, int C, int n_atoms,
-                       const int* row_ptr, int e0, const float* ef, const float* W, int ldw,
+                       const int* row_ptr, int e0, const float* ef, const void* W, int w_bf16,
+                       int ldw,
                        const float* Vin, const float* theta, const float* GX, int ldx, int D,
                        const float* gVout, float* gVin, float* GW, __nv_bfloat16* GWb,
                        float* gY_v0, float* gY_env, int gy_stride, const float* Gam,

@@ -11,8 +11,12 @@
 //     T_path[c] = C_path (V_ij[c] x G_i[c]);  s = the 0e outputs -> latent input columns;
 //     V'_ij[c] = sum_path theta[path, c] T_path[c] / sqrt(n_paths into the irrep).
 // Layouts (channel fastest, so a team reads 64/128 contiguous bytes per component):
-//   W [E][(lmax+1) * C] env weights (column l*C + c);  V [E][dim][C];  G [atoms][9][C];
+//   W [E][(lmax+1) * C] env weights (column l*C + c; FP32, or bf16 when the env projection
+//   ran on the tensor cores: read as bf16, widened to FP32 for every product);
+//   V [E][dim][C];  G [atoms][9][C];
 //   the scalars go to X[e][D + q*C + c].
+#include <type_traits>
+
 #include "ff_internal.cuh"
 #include "tp_gen.cuh"
 
@@ -62,6 +66,46 @@ __device__ __forceinline__ void stage(float* dst, const float* src, int stride, 
     const int r = i / CH, q = i - r * CH;
     cp_async16(dst + r * CT + 4 * q, src + (size_t)r * stride + 4 * q);
   }
+}
+
+// The same for ROWS rows of CT bf16 values (source rows `stride` elements apart, 16-byte
+// aligned): a dense [ROWS][CT] bf16 block, CT / 2 floats of the record per row.
+template <int CT, int ROWS>
+__device__ __forceinline__ void stage_b16(float* dst, const __nv_bfloat16* src, int stride,
+                                          int lane) {
+  constexpr int CH = CT / 8;   // 16-byte chunks per row
+  constexpr int NCH = ROWS * CH;
+  if (stride == CT) {
+    const float* s = reinterpret_cast<const float*>(src);
+#pragma unroll
+    for (int j = 0; j < (NCH + CT - 1) / CT; ++j) {
+      const int i = lane + j * CT;
+      if (NCH % CT == 0 || i < NCH) cp_async16(dst + 4 * i, s + 4 * i);
+    }
+    return;
+  }
+  for (int i = lane; i < NCH; i += CT) {
+    const int r = i / CH, q = i - r * CH;
+    cp_async16(dst + r * (CT / 2) + 4 * q,
+               reinterpret_cast<const float*>(src + (size_t)r * stride) + 4 * q);
+  }
+}
+
+// Env-weight element k of a staged slice (FP32, or bf16 widened to FP32).
+template <bool WB>
+__device__ __forceinline__ float wget(const float* recw, int k) {
+  if constexpr (WB) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(recw)[k]);
+  else return recw[k];
+}
+
+template <int CT, int ROWS>
+__device__ __forceinline__ void stage_w(float* dst, const float* src, int stride, int lane) {
+  stage<CT, ROWS>(dst, src, stride, lane);
+}
+template <int CT, int ROWS>
+__device__ __forceinline__ void stage_w(float* dst, const __nv_bfloat16* src, int stride,
+                                        int lane) {
+  stage_b16<CT, ROWS>(dst, src, stride, lane);
 }
 
 // The NY harmonics of an edge-feature record (at FF_EF_Y = 15: one scalar load, then
@@ -152,13 +196,14 @@ __device__ __forceinline__ int rs_index(int lane) {
 template <int LMAX, int INK, int OUTK>
 using TPK = TP<LMAX, INK == 3 ? 0 : INK, OUTK>;
 
-template <int LMAX, int INK, int OUTK, int CT, bool BWD>
+template <int LMAX, int INK, int OUTK, int CT, bool BWD, bool WB>
 struct EdgeRec {
   using K = TPK<LMAX, INK, OUTK>;
   static constexpr bool LAST = OUTK == 2;
   static constexpr int TEAMS = 128 / CT;
+  static constexpr int WSZ = WB ? (LMAX + 1) * CT / 2 : (LMAX + 1) * CT;   // env-weight floats
   static constexpr int OFF_W = INK == 0 ? FF_EF_STRIDE : 0;
-  static constexpr int OFF_V = INK == 0 ? OFF_W + (LMAX + 1) * CT : 0;
+  static constexpr int OFF_V = INK == 0 ? OFF_W + WSZ : 0;
   static constexpr int OFF_GS = OFF_V + (INK > 0 ? K::DIN * CT : 0);
   static constexpr int OFF_GVO = OFF_GS + (BWD ? K::NS * CT : 0);
   static constexpr int SST = OFF_GVO + ((BWD && !LAST) ? K::DOUT * CT : 0);
@@ -170,7 +215,7 @@ struct EdgeRec {
   // the passes that read only the edge-feature row and the env weights use the same
   // buffer as a deeper ring of smaller records (2 to 8 of them); in the adjoint of the
   // first layer these also carry the FP32 weight gradients of its first pass
-  static constexpr int OFF_GW1 = FF_EF_STRIDE + (LMAX + 1) * CT;
+  static constexpr int OFF_GW1 = FF_EF_STRIDE + WSZ;
   static constexpr int SR = OFF_GW1 + ((BWD && INK == 0) ? (LMAX + 1) * CT : 0);
   static constexpr int NSR_FIT = NSTG * SST / SR;
   static constexpr int NSR = NSR_FIT < 2 ? 2 : (NSR_FIT > 8 ? 8 : NSR_FIT);
@@ -180,25 +225,25 @@ struct EdgeRec {
   static_assert(TEAMS * BUF * 4 <= 48 * 1024, "static shared memory");
 };
 
-template <int LMAX, int CT>
+template <int LMAX, int CT, typename TW>
 __device__ __forceinline__ void stage_ef_w(float* rec, int e, int lane, int C, int grp,
-                                           const float* ef, const float* W, int ldw) {
+                                           const float* ef, const TW* W, int ldw) {
   if (lane < FF_EF_STRIDE / 4)
     cp_async16(rec + 4 * lane, ef + (size_t)e * FF_EF_STRIDE + 4 * lane);
-  stage<CT, LMAX + 1>(rec + FF_EF_STRIDE, W + (size_t)e * ldw + grp * CT, C, lane);
+  stage_w<CT, LMAX + 1>(rec + FF_EF_STRIDE, W + (size_t)e * ldw + grp * CT, C, lane);
 }
 
-template <int LMAX, int INK, int OUTK, int CT, bool BWD>
+template <int LMAX, int INK, int OUTK, int CT, bool BWD, bool WB, typename TW>
 __device__ __forceinline__ void stage_edge(float* rec, int e, int lane, int C, int grp,
-                                           const float* ef, const float* W, int ldw,
+                                           const float* ef, const TW* W, int ldw,
                                            const float* vin, const float* GX, int ldx, int D,
                                            const float* gvout) {
-  using R = EdgeRec<LMAX, INK, OUTK, CT, BWD>;
+  using R = EdgeRec<LMAX, INK, OUTK, CT, BWD, WB>;
   using K = TPK<LMAX, INK, OUTK>;
   if (INK == 0) {
     if (lane < FF_EF_STRIDE / 4)
       cp_async16(rec + 4 * lane, ef + (size_t)e * FF_EF_STRIDE + 4 * lane);
-    stage<CT, LMAX + 1>(rec + R::OFF_W, W + (size_t)e * ldw + grp * CT, C, lane);
+    stage_w<CT, LMAX + 1>(rec + R::OFF_W, W + (size_t)e * ldw + grp * CT, C, lane);
   } else {
     stage<CT, K::DIN>(rec + R::OFF_V, vin + (size_t)e * K::DIN * C, C, lane);
   }
@@ -209,15 +254,17 @@ __device__ __forceinline__ void stage_edge(float* rec, int e, int lane, int C, i
   }
 }
 
-template <int LMAX, int INK, int OUTK, int CT>
+template <int LMAX, int INK, int OUTK, int CT, bool WB>
 __global__ void __launch_bounds__(128, 8)
 k_env_tp_fwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
-             const float* __restrict__ ef, const float* __restrict__ W, int ldw,
+             const float* __restrict__ ef,
+             const typename std::conditional<WB, __nv_bfloat16, float>::type* __restrict__ W,
+             int ldw,
              const float* __restrict__ Vin, const float* __restrict__ thetaT,
              float* __restrict__ X, __nv_bfloat16* __restrict__ Xb, int ldx, int D,
              float* __restrict__ Vout, float* __restrict__ Gam, float inv_sqrt_nu) {
   using K = TPK<LMAX, INK, OUTK>;
-  using R = EdgeRec<LMAX, INK, OUTK, CT, false>;
+  using R = EdgeRec<LMAX, INK, OUTK, CT, false, WB>;
   constexpr bool LAST = R::LAST;
   constexpr int NY = (LMAX + 1) * (LMAX + 1);
   constexpr int NSTG = R::NSTG, SST = R::SST;
@@ -232,8 +279,8 @@ k_env_tp_fwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
   float* buf = s_rec + team * R::BUF;
   const float* vin = Vin + grp * CT;
   auto fetch = [&](int e, int slot) {
-    stage_edge<LMAX, INK, OUTK, CT, false>(buf + slot * SST, e, lane, C, grp, ef, W, ldw, vin,
-                                           nullptr, 0, 0, nullptr);
+    stage_edge<LMAX, INK, OUTK, CT, false, WB>(buf + slot * SST, e, lane, C, grp, ef, W, ldw,
+                                               vin, nullptr, 0, 0, nullptr);
   };
   // environment sum over a ring of (edge-feature row, env-weight slice) records
   constexpr int SR = R::SR, NSR = R::NSR;
@@ -259,7 +306,7 @@ k_env_tp_fwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
     load_y<NY>(rec, y);
 #pragma unroll
     for (int l = 0; l <= LMAX; ++l) {
-      const float w = rec[FF_EF_STRIDE + l * CT + lane];
+      const float w = wget<WB>(rec + FF_EF_STRIDE, l * CT + lane);
 #pragma unroll
       for (int m = 0; m < 2 * l + 1; ++m) G_[l * l + m] += w * y[l * l + m];
     }
@@ -290,7 +337,7 @@ k_env_tp_fwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
       load_y<NY>(rec, y);
 #pragma unroll
       for (int l = 0; l <= LMAX; ++l) {
-        const float w = rec[R::OFF_W + l * CT + lane];
+        const float w = wget<WB>(rec + R::OFF_W, l * CT + lane);
 #pragma unroll
         for (int m = 0; m < 2 * l + 1; ++m) v[l * l + m] = w * y[l * l + m];
       }
@@ -323,17 +370,19 @@ k_env_tp_fwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
 // (Resident blocks of 4 warps per SM: eight for the last layer, whose adjoint has no
 // feature gradients to keep, five for the others, the count the first layer's shared
 // memory allows; the register budget follows, at most 64 and 96 a thread.)
-template <int LMAX, int INK, int OUTK, int CT>
+template <int LMAX, int INK, int OUTK, int CT, bool WB>
 __global__ void __launch_bounds__(128, OUTK == 2 ? 8 : 5)
 k_env_tp_bwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
-             const float* __restrict__ ef, const float* __restrict__ W, int ldw,
+             const float* __restrict__ ef,
+             const typename std::conditional<WB, __nv_bfloat16, float>::type* __restrict__ W,
+             int ldw,
              const float* __restrict__ Vin, const float* __restrict__ thetaT,
              const float* __restrict__ GX, int ldx, int D, const float* __restrict__ gVout,
              float* __restrict__ gVin, float* __restrict__ GW, __nv_bfloat16* __restrict__ GWb,
              float* __restrict__ gY_v0, float* __restrict__ gY_env, int gy_stride,
              const float* __restrict__ Gam, float inv_sqrt_nu) {
   using K = TPK<LMAX, INK, OUTK>;
-  using R = EdgeRec<LMAX, INK, OUTK, CT, true>;
+  using R = EdgeRec<LMAX, INK, OUTK, CT, true, WB>;
   constexpr bool LAST = R::LAST;
   constexpr int NY = (LMAX + 1) * (LMAX + 1);
   constexpr int NSTG = R::NSTG, SST = R::SST;
@@ -349,8 +398,8 @@ k_env_tp_bwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
   const float* vin = Vin + grp * CT;
   const float* gvout = gVout + grp * CT;
   auto fetch = [&](int e, int slot) {
-    stage_edge<LMAX, INK, OUTK, CT, true>(buf + slot * SST, e, lane, C, grp, ef, W, ldw, vin, GX,
-                                          ldx, D, gvout);
+    stage_edge<LMAX, INK, OUTK, CT, true, WB>(buf + slot * SST, e, lane, C, grp, ef, W, ldw,
+                                              vin, GX, ldx, D, gvout);
   };
 #pragma unroll
   for (int p = 0; p < NSTG - 1; ++p) {
@@ -375,7 +424,8 @@ k_env_tp_bwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
     float v[K::DIN], gv[K::DIN];
     float wl[LMAX + 1], y[NY];
 #pragma unroll
-    for (int l = 0; l <= LMAX; ++l) wl[l] = INK == 0 ? rec[R::OFF_W + l * CT + lane] : 0.f;
+    for (int l = 0; l <= LMAX; ++l)
+      wl[l] = INK == 0 ? wget<WB>(rec + R::OFF_W, l * CT + lane) : 0.f;
     if (INK == 0) {
       load_y<NY>(rec, y);
 #pragma unroll
@@ -446,7 +496,7 @@ k_env_tp_bwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
     load_y<NY>(rec, y);
 #pragma unroll
     for (int l = 0; l <= LMAX; ++l) {
-      const float wl = rec[FF_EF_STRIDE + l * CT + lane];
+      const float wl = wget<WB>(rec + FF_EF_STRIDE, l * CT + lane);
       const float gw0 = INK == 0 ? rec[R::OFF_GW1 + l * CT + lane] : 0.f;
       float gw = 0.f;
 #pragma unroll
@@ -466,23 +516,36 @@ k_env_tp_bwd(int n_atoms, int C, const int* __restrict__ row_ptr, int e0,
 }
 
 template <int LMAX, int INK, int OUTK, int CT>
-void fwd_one(int n_atoms, int C, const int* row_ptr, int e0, const float* ef, const float* W,
-             int ldw, const float* Vin, const float* thetaT, float* X, __nv_bfloat16* Xb,
-             int ldx, int D, float* Vout, float* Gam, float inv_sqrt_nu, cudaStream_t s) {
+void fwd_one(int n_atoms, int C, const int* row_ptr, int e0, const float* ef, const void* W,
+             int wb, int ldw, const float* Vin, const float* thetaT, float* X,
+             __nv_bfloat16* Xb, int ldx, int D, float* Vout, float* Gam, float inv_sqrt_nu,
+             cudaStream_t s) {
   const long long teams = (long long)n_atoms * (C / CT);
-  k_env_tp_fwd<LMAX, INK, OUTK, CT><<<ff_cdiv(teams * CT, 128), 128, 0, s>>>(
-      n_atoms, C, row_ptr, e0, ef, W, ldw, Vin, thetaT, X, Xb, ldx, D, Vout, Gam, inv_sqrt_nu);
+  if (wb)
+    k_env_tp_fwd<LMAX, INK, OUTK, CT, true><<<ff_cdiv(teams * CT, 128), 128, 0, s>>>(
+        n_atoms, C, row_ptr, e0, ef, (const __nv_bfloat16*)W, ldw, Vin, thetaT, X, Xb, ldx, D,
+        Vout, Gam, inv_sqrt_nu);
+  else
+    k_env_tp_fwd<LMAX, INK, OUTK, CT, false><<<ff_cdiv(teams * CT, 128), 128, 0, s>>>(
+        n_atoms, C, row_ptr, e0, ef, (const float*)W, ldw, Vin, thetaT, X, Xb, ldx, D, Vout,
+        Gam, inv_sqrt_nu);
 }
 
 template <int LMAX, int INK, int OUTK, int CT>
-void bwd_one(int n_atoms, int C, const int* row_ptr, int e0, const float* ef, const float* W,
-             int ldw, const float* Vin, const float* thetaT, const float* GX, int ldx, int D,
-             const float* gVout, float* gVin, float* GW, __nv_bfloat16* GWb, float* gY_v0,
-             float* gY_env, int gy_stride, const float* Gam, float inv_sqrt_nu, cudaStream_t s) {
+void bwd_one(int n_atoms, int C, const int* row_ptr, int e0, const float* ef, const void* W,
+             int wb, int ldw, const float* Vin, const float* thetaT, const float* GX, int ldx,
+             int D, const float* gVout, float* gVin, float* GW, __nv_bfloat16* GWb,
+             float* gY_v0, float* gY_env, int gy_stride, const float* Gam, float inv_sqrt_nu,
+             cudaStream_t s) {
   const long long teams = (long long)n_atoms * (C / CT);
-  k_env_tp_bwd<LMAX, INK, OUTK, CT><<<ff_cdiv(teams * CT, 128), 128, 0, s>>>(
-      n_atoms, C, row_ptr, e0, ef, W, ldw, Vin, thetaT, GX, ldx, D, gVout, gVin, GW, GWb, gY_v0,
-      gY_env, gy_stride, Gam, inv_sqrt_nu);
+  if (wb)
+    k_env_tp_bwd<LMAX, INK, OUTK, CT, true><<<ff_cdiv(teams * CT, 128), 128, 0, s>>>(
+        n_atoms, C, row_ptr, e0, ef, (const __nv_bfloat16*)W, ldw, Vin, thetaT, GX, ldx, D,
+        gVout, gVin, GW, GWb, gY_v0, gY_env, gy_stride, Gam, inv_sqrt_nu);
+  else
+    k_env_tp_bwd<LMAX, INK, OUTK, CT, false><<<ff_cdiv(teams * CT, 128), 128, 0, s>>>(
+        n_atoms, C, row_ptr, e0, ef, (const float*)W, ldw, Vin, thetaT, GX, ldx, D, gVout,
+        gVin, GW, GWb, gY_v0, gY_env, gy_stride, Gam, inv_sqrt_nu);
 }
 
 // (input kind, output kind) of every layer of a 1- to 4-layer model; see TPK above.
@@ -526,25 +589,27 @@ void bwd_one(int n_atoms, int C, const int* row_ptr, int e0, const float* ef, co
 
 
 void launch_env_tp_fwd(int lmax, int in_kind, int out_kind, int C, int n_atoms,
-                       const int* row_ptr, int e0, const float* ef, const float* W, int ldw,
+                       const int* row_ptr, int e0, const float* ef, const void* W, int w_bf16,
+                       int ldw,
                        const float* Vin, const float* theta, float* X, __nv_bfloat16* Xb,
                        int ldx, int D, float* Vout, float* Gam, float inv_sqrt_nu,
                        cudaStream_t s) {
   ProfScope ps_(PC_TP_FWD, s);
   if (n_atoms <= 0) return;
-  FF_TP_DISPATCH(fwd_one, n_atoms, C, row_ptr, e0, ef, W, ldw, Vin, theta, X, Xb, ldx, D, Vout,
-                 Gam, inv_sqrt_nu, s);
+  FF_TP_DISPATCH(fwd_one, n_atoms, C, row_ptr, e0, ef, W, w_bf16, ldw, Vin, theta, X, Xb, ldx,
+                 D, Vout, Gam, inv_sqrt_nu, s);
   ff_count_launch(1);
 }
 
 void launch_env_tp_bwd(int lmax, int in_kind, int out_kind, int C, int n_atoms,
-                       const int* row_ptr, int e0, const float* ef, const float* W, int ldw,
+                       const int* row_ptr, int e0, const float* ef, const void* W, int w_bf16,
+                       int ldw,
                        const float* Vin, const float* theta, const float* GX, int ldx, int D,
                        const float* gVout, float* gVin, float* GW, __nv_bfloat16* GWb, float* gY_v0, float* gY_env,
                        int gy_stride, const float* Gam, float inv_sqrt_nu, cudaStream_t s) {
   ProfScope ps_(PC_TP_BWD, s);
   if (n_atoms <= 0) return;
-  FF_TP_DISPATCH(bwd_one, n_atoms, C, row_ptr, e0, ef, W, ldw, Vin, theta, GX, ldx, D, gVout,
-                 gVin, GW, GWb, gY_v0, gY_env, gy_stride, Gam, inv_sqrt_nu, s);
+  FF_TP_DISPATCH(bwd_one, n_atoms, C, row_ptr, e0, ef, W, w_bf16, ldw, Vin, theta, GX, ldx, D,
+                 gVout, gVin, GW, GWb, gY_v0, gY_env, gy_stride, Gam, inv_sqrt_nu, s);
   ff_count_launch(1);
 }
