@@ -39,7 +39,8 @@ enum {
   FF_ERR_SPECIES = -2,   /* an atomic number outside 1..89 */
   FF_ERR_OOM = -3,       /* device allocation failed */
   FF_ERR_CUDA = -4,      /* a CUDA runtime call failed (message has the CUDA error) */
-  FF_ERR_CAPACITY = -5,  /* a neighbour count exceeded the per-atom limit FF_MAX_NEIGHBORS */
+  FF_ERR_CAPACITY = -5,  /* a neighbour count exceeded the per-atom limit FF_MAX_NEIGHBORS,
+                            or the list would exceed 2^31 - 1 edges (int32 offsets) */
   FF_ERR_NONFINITE = -6, /* non-finite position, energy or force */
   FF_ERR_STATE = -7,     /* call order violated (e.g. forces before any energy call) */
   FF_ERR_BOX = -8,       /* image shift out of range (|s| > 100 box lengths) */

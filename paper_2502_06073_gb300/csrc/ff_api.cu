@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <climits>
 #include <atomic>
 #include <mutex>
 #include <cstdlib>
@@ -748,6 +749,17 @@ int filter_edges(ff_ctx* c, const double* pos, cudaStream_t s, float r2cut) {
   FF_CK(c, cudaMemcpyAsync(c->row_ptr_h.data(), c->row_ptr, (size_t)(c->n + 1) * sizeof(int),
                            cudaMemcpyDeviceToHost, s));
   FF_CK(c, cudaStreamSynchronize(s));
+  if ((long long)c->n * c->vmax > INT32_MAX) {
+    // the int32 CSR offsets wrap beyond 2^31 - 1 edges: count the edges in 64 bits first
+    std::vector<int> cnt_h(c->n);
+    FF_CK(c, cudaMemcpy(cnt_h.data(), c->cnt, (size_t)c->n * sizeof(int),
+                        cudaMemcpyDeviceToHost));
+    long long tot = 0;
+    for (const int v : cnt_h) tot += v;
+    if (tot > INT32_MAX)
+      return set_err(c, FF_ERR_CAPACITY, "the model list has " + std::to_string(tot) +
+                                             " edges (limit 2^31 - 1)");
+  }
   c->E = c->row_ptr_h[c->n];
   if (c->E > c->ecap) {
     const long long cap = std::max(c->E + c->E / 8 + 1024, 2 * c->ecap);
