@@ -122,7 +122,8 @@ def gemm_bytes_per_edge(hp, precision):
     operand read once, each epilogue input read once, each output written once, in the
     storage types of the path.  Precision 0: FP32 everywhere; the adjoint's latent-input
     and env-weight products are two GEMMs.  Precision 1: BF16 GEMM operands, stored
-    pre-activations and residual stream, FP32 gradients; the last latent GEMM carries the
+    pre-activations, residual stream and env weights (the env projection's output), FP32
+    gradients; the last latent GEMM carries the
     edge-energy readout (per-edge energy, envelope seed and bf16 dE/dz out, no latent
     stored) when D <= 256; the adjoint computes the scalar gradients first and then one
     GEMM over the concatenated [dE/dz | dE/dw]."""
@@ -137,12 +138,13 @@ def gemm_bytes_per_edge(hp, precision):
     sz = 2 if tc else 4                      # bytes of a stored pre-activation
     cp = 2 if tc else 0                      # extra bf16 copy of the residual stream
     sx = 2 if tc else 4                      # bytes of a stored residual-stream element
+    sw = 2 if tc else 4                      # bytes of a stored env weight
     b = 0
     for k in range(1, len(tb)):              # two-body hidden layers
         b += tb[k - 1] * sa + tb[k] * sz
         b += (tb[k] * sx + 4) if k == len(tb) - 1 else tb[k] * sa
     for L in range(1, NL + 1):
-        b += D * sa + ldw * 4                # environment projection
+        b += D * sa + ldw * sw               # environment projection
         fan = ldx
         for k, w in enumerate(lat):
             b += fan * sa
