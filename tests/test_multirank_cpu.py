@@ -327,14 +327,14 @@ def _grid_worker(rank, world, port, dims, out_path):
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("dims", [(2, 2, 1), (3, 1, 2)])
+@pytest.mark.parametrize("dims", [(2, 2, 1), (3, 1, 2), (2, 2, 2)])
 def test_brick_grid_with_staged_halo_matches_whole_box(tmp_path, dims):
-    """A grid of bricks over two axes (2 x 2 along x, y: the same peer on both sides of
-    each axis; 3 x 2 along x, z: distinct peers along x), halo rc + skin = 6 A.  The halo
-    exchange runs one axis at a time and forwards the ghosts of earlier axes, so atoms of
-    diagonal bricks reach a rank through an intermediate one; the ghost forces return in
-    the reverse order through the same ranks.  Owned energies and forces equal the
-    single-process evaluation."""
+    """Grids of bricks over two or three axes (2 x 2 along x, y: the same peer on both
+    sides of each axis; 3 x 2 along x, z: distinct peers along x; 2 x 2 x 2), halo
+    rc + skin = 6 A.  The halo exchange runs one axis at a time and forwards the ghosts of
+    earlier axes, so atoms of edge- and corner-adjacent bricks reach a rank through one or
+    two intermediate ranks; the ghost forces return in the reverse order through the same
+    ranks.  Owned energies and forces equal the single-process evaluation."""
     import synth
     from oracle import Allegro64
     world = int(np.prod(dims))
