@@ -36,6 +36,14 @@ def test_every_declared_symbol_is_exported(lib):
     assert sorted(ff.ABI) == names
 
 
+def test_build_compiles_every_cuda_source():
+    """Every .cu file of csrc/ is one translation unit of libff.so, and only those."""
+    from paper_2502_06073_gb300 import _build
+    on_disk = sorted(f for f in os.listdir(CSRC) if f.endswith(".cu"))
+    assert sorted(_build.SOURCES) == on_disk
+    assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
 def _gen_module():
     spec = importlib.util.spec_from_file_location("gen_tp", os.path.join(CSRC, "gen_tp.py"))
     m = importlib.util.module_from_spec(spec)
